@@ -1,0 +1,94 @@
+"""Seeded synthetic inputs (scattering potentials, incident directions, receivers).
+
+This module holds only input generation: none of the solver's arithmetic.
+It is shared by the tests, the benchmark and the CPU oracle's callers.
+
+The paper's own potentials are analytic (Sec. 6: Gaussian bump, cavity, lens);
+the workloads here use the family below, with the shapes and smoothness of
+those experiments:
+
+* ``gaussian_bump``   -- b = a exp(-|x - c|^2 / s2) (the plain oracle-size case).
+* ``gaussian_family`` -- b = psi(x) * sum_{g<20} a_g exp(-|x - c_g|^2 / (2 w_g^2))
+  with a ~ U[-0.5, 0.5], w ~ U[0.05, 0.15], c ~ U[0.15, 0.85]^2 drawn in that
+  order from numpy.random.default_rng(seed); psi is a C-infinity cutoff that
+  vanishes with all derivatives on the boundary of the unit square (ramp over
+  a distance 0.1).  If max b >= 0.95 the field is scaled to max 0.95
+  (b <= 1 is required for uniqueness, Sec. 1).
+* ``constant_disk``   -- b = value inside a disk (closed-form pin).
+* ``plane_wave_angles`` / ``receivers_circle``.
+"""
+import numpy as np
+
+
+def grid_nodes(n, h=None, x0=0.0, y0=0.0):
+    """Cell-centred nodes of an n x n grid on [x0, x0+1] x [y0, y0+1]; returns
+    (X, Y) arrays [n][n] (row = y index, column = x index)."""
+    h = 1.0 / n if h is None else h
+    c = (np.arange(n) + 0.5) * h
+    X, Y = np.meshgrid(x0 + c, y0 + c)
+    return X, Y
+
+
+def _smooth_step(t):
+    """C-infinity step: 0 for t <= 0, 1 for t >= 1."""
+    t = np.clip(t, 0.0, 1.0)
+    with np.errstate(divide="ignore", over="ignore"):
+        a = np.where(t > 0, np.exp(-1.0 / np.where(t > 0, t, 1.0)), 0.0)
+        b = np.where(t < 1, np.exp(-1.0 / np.where(t < 1, 1.0 - t, 1.0)), 0.0)
+    return a / (a + b)
+
+
+def cutoff(X, Y, ramp=0.1):
+    return (_smooth_step(X / ramp) * _smooth_step((1 - X) / ramp)
+            * _smooth_step(Y / ramp) * _smooth_step((1 - Y) / ramp))
+
+
+def gaussian_bump(n, amp=0.5, s2=0.04, centre=(0.5, 0.5)):
+    X, Y = grid_nodes(n)
+    return amp * np.exp(-((X - centre[0]) ** 2 + (Y - centre[1]) ** 2) / s2)
+
+
+def gaussian_family(n, seed, count=20):
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(-0.5, 0.5, count)
+    w = rng.uniform(0.05, 0.15, count)
+    c = rng.uniform(0.15, 0.85, (count, 2))
+    X, Y = grid_nodes(n)
+    b = np.zeros_like(X)
+    for g in range(count):
+        b += a[g] * np.exp(-((X - c[g, 0]) ** 2 + (Y - c[g, 1]) ** 2) / (2 * w[g] ** 2))
+    b *= cutoff(X, Y)
+    mx = b.max()
+    if mx >= 0.95:
+        b *= 0.95 / mx
+    return b
+
+
+def constant_disk(n, value, radius, centre=(0.5, 0.5)):
+    X, Y = grid_nodes(n)
+    return np.where((X - centre[0]) ** 2 + (Y - centre[1]) ** 2 < radius ** 2, value, 0.0)
+
+
+def plane_wave_angles(count):
+    return 2 * np.pi * np.arange(count) / count
+
+
+def receivers_circle(count, radius=1.5, centre=(0.5, 0.5)):
+    phi = 2 * np.pi * np.arange(count) / count
+    return np.stack([centre[0] + radius * np.cos(phi), centre[1] + radius * np.sin(phi)], axis=1)
+
+
+def random_complex(shape, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+# Workloads (grid side, kappa, potential, tolerances) of the measured cases.
+WORKLOADS = {
+    "direct_n32": dict(n=32, kappa=20.0, b=lambda n: gaussian_bump(n), order_precond=10,
+                       order_matvec=10, eps=1e-10, leaf=8),
+    "precond_n256": dict(n=256, kappa=60.0, b=lambda n: gaussian_family(n, 0), order_precond=4,
+                         order_matvec=10, eps=1e-4, leaf=8),
+    "precond_n2048": dict(n=2048, kappa=400 * np.pi, b=lambda n: gaussian_family(n, 0),
+                          order_precond=4, order_matvec=10, eps=1e-4, leaf=8),
+}
