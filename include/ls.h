@@ -1,0 +1,142 @@
+/* ls.h -- C ABI of the GB300 (sm_103a) Lippmann-Schwinger HBS solver.
+ *
+ * Method: Gopal & Martinsson, "An accelerated, high-order accurate direct
+ * solver for the Lippmann-Schwinger equation for acoustic scattering in the
+ * plane" (arXiv 2007.12718).
+ *
+ *   sigma + kappa^2 b(x) int_Omega G(x,y) sigma(y) dy = -kappa^2 b(x) u_inc(x)   (Eq. 3)
+ *   G(x,y) = (i/4) H0^(1)(kappa |x-y|)                                            (Eq. 2)
+ *
+ * discretised on a regular grid with the corrected trapezoidal rule (Sec. 2.2,
+ * Eq. 8) into (I + B G_p) q = f  (Eqs. 9-10), B = diag(kappa^2 b).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Grid: nx * ny cell-centred nodes x_ij = (x0 + (i+1/2) h, y0 + (j+1/2) h).
+ *    Grid arrays are row-major [ny][nx] (x fastest).  Several right-hand
+ *    sides are stacked as [nrhs][ny][nx].
+ *  - Complex vectors are interleaved complex128 {re, im} (16 bytes/entry).
+ *  - Pointers to vectors may be device pointers or host pointers (pageable or
+ *    pinned); the library queries the pointer and stages host data through
+ *    device memory itself.  All work is ordered on `stream` (a cudaStream_t,
+ *    NULL = the legacy default stream); calls return after the work is
+ *    enqueued, except where a result must come back to the host (ranks in
+ *    ls_build, the convergence test in ls_solve, host output buffers).
+ *  - Ownership: the caller owns every buffer it passes; the library copies b
+ *    during ls_build and owns the handle's memory until ls_free.
+ *  - Errors: every int-returning call returns LS_OK (0) or a negative LS_E*
+ *    code; no call aborts the process or throws across the ABI.  The text of
+ *    the last error of the calling thread is available from ls_last_error().
+ */
+#ifndef LS_H_
+#define LS_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  LS_OK = 0,
+  LS_EINVAL = -1,     /* bad argument (sizes, b not finite or b > 1, ...) */
+  LS_ENOMEM = -2,     /* device allocation failed */
+  LS_ECUDA = -3,      /* CUDA runtime error (see ls_last_error) */
+  LS_ESINGULAR = -4,  /* zero pivot in a local inverse */
+  LS_ENOCONV = -5,    /* GMRES hit maxit; sigma and info are still written */
+  LS_ETIMEOUT = -6    /* a bounded device-side wait gave up */
+};
+
+/* Precision of the HBS preconditioner (compression, inverse build, apply).
+ * The FFT matvec and GMRES are FP64 in every mode. */
+enum { LS_FP64 = 0, LS_FP32 = 1 };
+
+typedef struct {
+  int nx, ny;        /* grid size; a tree of square leaves must fit (see ls_build) */
+  double h;          /* mesh width */
+  double x0, y0;     /* lower-left corner of the domain */
+} ls_grid;
+
+typedef struct {
+  int order_matvec;  /* corrected-quadrature order of the FFT matvec: 2,4,6,8,10 (default 10) */
+  int order_precond; /* order used inside the HBS compression: 4,6,8,10 (default 4)      */
+  int leaf_side;     /* leaf box side s (s*s points per leaf, default 8)                  */
+  int proxy_width;   /* proxy ring width in grid cells; 0 = from tol and order (default)  */
+  int precision;     /* LS_FP64 or LS_FP32 (default LS_FP32)                              */
+  int gmres_maxit;   /* default 100 (Sec. 6.3)                                            */
+  double gmres_tol;  /* relative residual, default 1e-10 (Sec. 6.3)                       */
+} ls_opts;
+
+typedef struct {
+  int iterations;     /* GMRES iterations taken */
+  int converged;      /* 1 if the residual estimate reached gmres_tol */
+  double resid_est;   /* Arnoldi residual estimate ||f - A sigma|| / ||f|| */
+  double resid_true;  /* recomputed ||f - A sigma|| / ||f|| with the FFT matvec */
+} ls_solve_info;
+
+typedef struct {
+  int levels;               /* L: the tree has 2^L leaves */
+  int ranks[32];            /* ranks[l] = skeleton size k_l of level l (ranks[0] = 0) */
+  int proxy_width;          /* ring width actually used */
+  double flops_build;       /* algorithmic real flops of the inverse build (Alg. 1) */
+  double flops_compress;    /* algorithmic real flops of the per-level IDs */
+  double bytes_apply;       /* algorithmic bytes read+written by one HBS apply */
+  double factor_bytes;      /* device bytes held by the factors */
+} ls_build_info;
+
+typedef struct ls_handle ls_handle; /* opaque, library-owned */
+
+/* Fill *o with the defaults listed above. */
+void ls_default_opts(ls_opts* o);
+
+/* ls_build -- compress G_p (Sec. 3.2) and build the HBS inverse of I + B G_p
+ * (Algorithm 1, Sec. 4.1), and set up the FFT matvec of the order_matvec
+ * operator (Sec. 5).
+ *   grid   : geometry.  nx = s * 2^ceil(L/2), ny = s * 2^floor(L/2) for the
+ *            leaf side s and some L >= 1 (cuts alternate vertical/horizontal,
+ *            Sec. 3.2), e.g. nx = ny = s * 2^(L/2).
+ *   kappa  : wavenumber > 0.
+ *   b      : scattering potential, ny*nx doubles (host or device); finite and
+ *            <= 1 (Sec. 1).
+ *   tol    : HBS compression tolerance eps in (0, 1) (Eq. 11, with the local
+ *            tolerance eps * ||proxy block||_F).
+ *   opts   : NULL for defaults.
+ *   out    : receives the handle.
+ * Returns LS_EINVAL for a bad argument, LS_ESINGULAR when a local inverse
+ * meets a zero pivot, LS_ETIMEOUT if a device-side wait gave up. */
+int ls_build(const ls_grid* grid, double kappa, const double* b, double tol,
+             const ls_opts* opts, void* stream, ls_handle** out);
+
+/* ls_apply -- q = M f, M ~ (I + B G_p)^-1 the HBS inverse (Algorithm 2,
+ * Sec. 4.1).  f, q: nrhs complex128 grid vectors.  transpose must be 0. */
+int ls_apply(ls_handle* h, const void* f, void* q, int nrhs, int transpose, void* stream);
+
+/* ls_matvec -- y = (I + B (G + T)) x, the order_matvec operator applied by a
+ * zero-padded 2D FFT convolution (Sec. 2.2 last paragraph, Sec. 5).
+ * x, y: nrhs complex128 grid vectors (may not alias).  transpose must be 0. */
+int ls_matvec(ls_handle* h, const void* x, void* y, int nrhs, int transpose, void* stream);
+
+/* ls_solve -- GMRES on (I + B (G+T)) sigma = f, right-preconditioned by the
+ * HBS inverse (Sec. 5), from sigma = 0, no restart, stopping at
+ * gmres_tol or gmres_maxit (Sec. 6.3).  f, sigma: nrhs complex128 grid
+ * vectors; info: nrhs entries (may be NULL).  Returns LS_ENOCONV if some
+ * right-hand side did not converge (sigma is still written). */
+int ls_solve(ls_handle* h, const void* f, void* sigma, int nrhs, ls_solve_info* info, void* stream);
+
+/* ls_rhs_plane_wave -- f = -kappa^2 b u_inc with u_inc = exp(i kappa (x1 cos theta
+ * + x2 sin theta)) (right-hand side of Eq. 3), one complex128 grid vector per
+ * angle.  thetas: nrhs doubles on the host. */
+int ls_rhs_plane_wave(ls_handle* h, const double* thetas, void* f, int nrhs, void* stream);
+
+/* ls_build_info -- ranks, flop and byte counts of the built handle. */
+int ls_get_build_info(const ls_handle* h, ls_build_info* info);
+
+/* ls_free -- release every resource of the handle (NULL is allowed). */
+void ls_free(ls_handle* h);
+
+/* Static text for an LS_E* code, and the last error message of this thread. */
+const char* ls_strerror(int code);
+const char* ls_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LS_H_ */

@@ -1,0 +1,216 @@
+"""GB300 (sm_103a) HBS-preconditioned solver for the 2D Lippmann-Schwinger equation.
+
+Method: Gopal & Martinsson, arXiv 2007.12718.  The compute path lives in the
+C-ABI library ``_lib/libls.so`` (CUDA kernels, see ``include/ls.h``); this
+module only marshals arguments to it through ctypes.  There is no CPU
+fallback: if the library is missing or cannot load, every call raises.
+
+Entry points (same names as the C ABI):
+  ls_build(grid_n, h, kappa, b, tol, **opts) -> Handle
+  ls_apply(handle, f, q)      q = M f       (HBS inverse, Algorithm 2)
+  ls_matvec(handle, x, y)     y = (I + B(G+T)) x   (FFT convolution, Sec. 5)
+  ls_solve(handle, f, sigma)  GMRES, right-preconditioned by M (Sec. 5)
+  ls_rhs_plane_wave(handle, thetas, f)
+  ls_free(handle)
+Vectors are complex128 arrays [nrhs][ny][nx] (or [ny][nx]); torch tensors on
+the GPU are passed as device pointers, numpy arrays / CPU tensors as host
+pointers (the library stages those itself).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libls.so")
+
+LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ESINGULAR, LS_ENOCONV, LS_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+LS_FP64, LS_FP32 = 0, 1
+
+EXPORTED = ["ls_default_opts", "ls_build", "ls_apply", "ls_matvec", "ls_solve", "ls_rhs_plane_wave",
+            "ls_get_build_info", "ls_free", "ls_strerror", "ls_last_error"]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("h", ctypes.c_double),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("order_matvec", ctypes.c_int), ("order_precond", ctypes.c_int), ("leaf_side", ctypes.c_int),
+                ("proxy_width", ctypes.c_int), ("precision", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
+                ("gmres_tol", ctypes.c_double)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("resid_est", ctypes.c_double),
+                ("resid_true", ctypes.c_double)]
+
+
+class BuildInfo(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("ranks", ctypes.c_int * 32), ("proxy_width", ctypes.c_int),
+                ("flops_build", ctypes.c_double), ("flops_compress", ctypes.c_double),
+                ("bytes_apply", ctypes.c_double), ("factor_bytes", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libls.so (raises if it is not built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is not built; run __graft_entry__.build() "
+                           "or python -m paper_2007_12718_gb300.build")
+    lib = ctypes.CDLL(path)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.ls_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    lib.ls_default_opts.restype = None
+    lib.ls_build.argtypes = [ctypes.POINTER(Grid), dp, vp, dp, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+    lib.ls_build.restype = ip
+    for name in ("ls_apply", "ls_matvec"):
+        getattr(lib, name).argtypes = [vp, vp, vp, ip, ip, vp]
+        getattr(lib, name).restype = ip
+    lib.ls_solve.argtypes = [vp, vp, vp, ip, ctypes.POINTER(SolveInfo), vp]
+    lib.ls_solve.restype = ip
+    lib.ls_rhs_plane_wave.argtypes = [vp, ctypes.POINTER(ctypes.c_double), vp, ip, vp]
+    lib.ls_rhs_plane_wave.restype = ip
+    lib.ls_get_build_info.argtypes = [vp, ctypes.POINTER(BuildInfo)]
+    lib.ls_get_build_info.restype = ip
+    lib.ls_free.argtypes = [vp]
+    lib.ls_free.restype = None
+    lib.ls_strerror.argtypes = [ip]
+    lib.ls_strerror.restype = ctypes.c_char_p
+    lib.ls_last_error.argtypes = []
+    lib.ls_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+class LSError(RuntimeError):
+    def __init__(self, code, where):
+        lib = load_library()
+        msg = lib.ls_strerror(code).decode()
+        last = lib.ls_last_error().decode()
+        super().__init__(f"{where}: {msg} ({code}) {last}")
+        self.code = code
+
+
+def _check(code, where, allow=()):
+    if code != LS_OK and code not in allow:
+        raise LSError(code, where)
+    return code
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(stream)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def _ptr(a, dtype, writable=False):
+    """(pointer, keepalive, nelem) for a torch tensor or numpy array."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            want = {np.complex128: torch.complex128, np.float64: torch.float64}[dtype]
+            if a.dtype != want or not a.is_contiguous():
+                raise TypeError(f"expected a contiguous {want} tensor")
+            return ctypes.c_void_p(a.data_ptr()), a, a.numel()
+    except ImportError:
+        pass
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"expected a C-contiguous numpy array of {np.dtype(dtype)}")
+    if writable and not a.flags["WRITEABLE"]:
+        raise TypeError("output array is read-only")
+    return ctypes.c_void_p(a.ctypes.data), a, a.size
+
+
+class Handle:
+    def __init__(self, ptr, n):
+        self.ptr = ptr
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.ls_free(self.ptr)
+            self.ptr = None
+
+    def info(self):
+        bi = BuildInfo()
+        _check(load_library().ls_get_build_info(self.ptr, ctypes.byref(bi)), "ls_get_build_info")
+        return {"levels": bi.levels, "ranks": list(bi.ranks[: bi.levels + 1]), "proxy_width": bi.proxy_width,
+                "flops_build": bi.flops_build, "flops_compress": bi.flops_compress,
+                "bytes_apply": bi.bytes_apply, "factor_bytes": bi.factor_bytes}
+
+
+def default_opts():
+    o = Opts()
+    load_library().ls_default_opts(ctypes.byref(o))
+    return o
+
+
+def ls_build(n, h, kappa, b, tol, order_matvec=10, order_precond=4, leaf_side=8, proxy_width=0,
+             precision=LS_FP32, gmres_maxit=100, gmres_tol=1e-10, x0=0.0, y0=0.0, ny=None, stream=None):
+    """Compress G and build the HBS inverse (Sec. 3.2, Algorithm 1); b is [ny][nx] float64."""
+    lib = load_library()
+    g = Grid(n, n if ny is None else ny, h, x0, y0)
+    o = Opts(order_matvec, order_precond, leaf_side, proxy_width, precision, gmres_maxit, gmres_tol)
+    bp, keep, _ = _ptr(b, np.float64)
+    out = ctypes.c_void_p()
+    _check(lib.ls_build(ctypes.byref(g), kappa, bp, tol, ctypes.byref(o), _stream(stream), ctypes.byref(out)),
+           "ls_build")
+    return Handle(out, g.nx * g.ny)
+
+
+def _nrhs(handle, nelem):
+    if nelem % handle.n:
+        raise ValueError("vector size is not a multiple of the grid size")
+    return nelem // handle.n
+
+
+def ls_apply(handle, f, q, stream=None):
+    fp, k1, n = _ptr(f, np.complex128)
+    qp, k2, _ = _ptr(q, np.complex128, True)
+    _check(load_library().ls_apply(handle.ptr, fp, qp, _nrhs(handle, n), 0, _stream(stream)), "ls_apply")
+    return q
+
+
+def ls_matvec(handle, x, y, stream=None):
+    xp, k1, n = _ptr(x, np.complex128)
+    yp, k2, _ = _ptr(y, np.complex128, True)
+    _check(load_library().ls_matvec(handle.ptr, xp, yp, _nrhs(handle, n), 0, _stream(stream)), "ls_matvec")
+    return y
+
+
+def ls_solve(handle, f, sigma, stream=None, allow_noconv=False):
+    fp, k1, n = _ptr(f, np.complex128)
+    sp_, k2, _ = _ptr(sigma, np.complex128, True)
+    nr = _nrhs(handle, n)
+    infos = (SolveInfo * nr)()
+    _check(load_library().ls_solve(handle.ptr, fp, sp_, nr, infos, _stream(stream)), "ls_solve",
+           allow=(LS_ENOCONV,) if allow_noconv else ())
+    return [{"iterations": i.iterations, "converged": bool(i.converged), "resid_est": i.resid_est,
+             "resid_true": i.resid_true} for i in infos]
+
+
+def ls_rhs_plane_wave(handle, thetas, f, stream=None):
+    th = np.ascontiguousarray(thetas, dtype=np.float64)
+    fp, k1, n = _ptr(f, np.complex128, True)
+    _check(load_library().ls_rhs_plane_wave(handle.ptr, th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), fp,
+                                            len(th), _stream(stream)), "ls_rhs_plane_wave")
+    return f
+
+
+def ls_free(handle):
+    if handle.ptr:
+        load_library().ls_free(handle.ptr)
+        handle.ptr = None

@@ -1,0 +1,132 @@
+// Shared device/host helpers for the Lippmann-Schwinger HBS library:
+// complex arithmetic templated on the real type, error codes, a bounded
+// grid barrier for cooperative kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+#include "../../include/ls.h"
+
+namespace ls {
+
+template <class R>
+struct __align__(2 * sizeof(R)) cx {
+  R re, im;
+};
+
+typedef cx<double> z64;  // complex128
+typedef cx<float> c32;   // complex64
+
+__host__ __device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
+__host__ __device__ __forceinline__ double mad(double a, double b, double c) { return ::fma(a, b, c); }
+
+template <class R>
+__host__ __device__ __forceinline__ cx<R> mk(R a, R b) {
+  cx<R> z;
+  z.re = a;
+  z.im = b;
+  return z;
+}
+template <class R>
+__host__ __device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return mk<R>(a.re + b.re, a.im + b.im); }
+template <class R>
+__host__ __device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return mk<R>(a.re - b.re, a.im - b.im); }
+template <class R>
+__host__ __device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+  return mk<R>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <class R>
+__host__ __device__ __forceinline__ cx<R> scale(cx<R> a, R s) { return mk<R>(a.re * s, a.im * s); }
+template <class R>
+__host__ __device__ __forceinline__ cx<R> conjz(cx<R> a) { return mk<R>(a.re, -a.im); }
+// acc += a * b
+template <class R>
+__host__ __device__ __forceinline__ void fma_(cx<R>& acc, cx<R> a, cx<R> b) {
+  acc.re = mad(a.re, b.re, mad(-a.im, b.im, acc.re));
+  acc.im = mad(a.re, b.im, mad(a.im, b.re, acc.im));
+}
+// acc += conj(a) * b
+template <class R>
+__host__ __device__ __forceinline__ void fmac_(cx<R>& acc, cx<R> a, cx<R> b) {
+  acc.re = mad(a.re, b.re, mad(a.im, b.im, acc.re));
+  acc.im = mad(a.re, b.im, mad(-a.im, b.re, acc.im));
+}
+template <class R>
+__host__ __device__ __forceinline__ R abs2(cx<R> a) { return a.re * a.re + a.im * a.im; }
+template <class R>
+__host__ __device__ __forceinline__ cx<R> inv(cx<R> a) {
+  R d = R(1) / abs2(a);
+  return mk<R>(a.re * d, -a.im * d);
+}
+template <class Ro, class Ri>
+__host__ __device__ __forceinline__ cx<Ro> cvt(cx<Ri> a) { return mk<Ro>((Ro)a.re, (Ro)a.im); }
+
+template <class R>
+__device__ __forceinline__ cx<R> shfl_xor(cx<R> v, int m) {
+  return mk<R>(__shfl_xor_sync(0xffffffffu, v.re, m), __shfl_xor_sync(0xffffffffu, v.im, m));
+}
+template <class R>
+__device__ __forceinline__ cx<R> warp_sum(cx<R> v) {
+  for (int m = 16; m; m >>= 1) v = v + shfl_xor(v, m);
+  return v;
+}
+template <class T>
+__device__ __forceinline__ T warp_sum_r(T v) {
+  for (int m = 16; m; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+
+// Grid-wide barrier for kernels launched with cudaLaunchCooperativeKernel
+// (all blocks co-resident).  Every spin is bounded: after `kSpinLimit` polls
+// the block raises *abort and the barrier returns false; every later barrier
+// returns false at once, so the kernel unwinds without hanging.
+struct GridSync {
+  unsigned int* count;   // arrival counter, starts at 0
+  unsigned int* gen;     // generation, starts at any value
+  int* abort;            // set to 1 by a block that timed out
+};
+
+static constexpr long long kSpinLimit = 20000000LL;  // ~ seconds of polling
+
+__device__ __forceinline__ bool grid_sync(const GridSync& g, unsigned int nblocks) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned int* vgen = g.gen;
+    volatile int* vab = g.abort;
+    unsigned int my = *vgen;
+    __threadfence();
+    unsigned int arrived = atomicAdd(g.count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(g.count, 0u);
+      __threadfence();
+      atomicAdd(g.gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == my) {
+        if (*vab) { ok = 0; break; }
+        if (++spins > kSpinLimit) { atomicExch(g.abort, 1); ok = 0; break; }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (*vab) ok = 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+}  // namespace ls
+
+#define LS_CUDA_TRY(expr)                                   \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) {                                \
+      ls_set_last_cuda_error(_e, #expr, __FILE__, __LINE__); \
+      return LS_ECUDA;                                      \
+    }                                                       \
+  } while (0)
+
+void ls_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);

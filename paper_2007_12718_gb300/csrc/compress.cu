@@ -1,0 +1,359 @@
+// HBS compression of G (Sec. 3.2): one row ID per tree level.
+//
+// For each level l = L..1 the rows are the points of one box (leaves) or the
+// two children's skeletons (Eq. 14), the columns the proxy ring of lattice
+// points at Chebyshev distance 1..w outside the box (Eq. 13).  The proxy
+// block is the same for every box of a level (translation invariance), so one
+// ID per level serves all 2^l boxes.  The ID is a column-pivoted QR of the
+// transposed block (Sec. 2.1): candidates are the rows, pivoting picks the
+// skeleton, U = P^T [I; (R11^-1 R12)^T] (U(skel,:) = I).  The rank is the
+// first k whose remaining residual has Frobenius norm <= eps ||block||_F
+// (the local tolerance rule, remark in Sec. 3.2).
+//
+// The CPQR runs as one cooperative kernel across many SMs: each block owns a
+// slice of candidate columns, one bounded grid barrier per pivot step; the
+// pivot column is read by every block straight from L2 (no broadcast copy).
+// Sibling blocks G_ab = G(skel_a, skel_b) (Eq. 15) and the leaf block
+// G(I_tau, I_tau) are evaluated on the device at the end.
+#include <algorithm>
+
+#include "handle.h"
+
+namespace ls {
+namespace {
+
+template <class R>
+__global__ void block_kernel(const int* __restrict__ rx, const int* __restrict__ ry, int m,
+                             const int* __restrict__ px, const int* __restrict__ py, int p, cx<R>* __restrict__ out,
+                             long long ld, KernelSpec ks) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)m * p) return;
+  int c = (int)(t / p), q = (int)(t % p);
+  z64 v = kernel_entry(ks, px[q] - rx[c], py[q] - ry[c]);
+  out[(long long)c * ld + q] = cvt<R>(v);
+}
+
+struct IdSlot {
+  double best;   // largest residual norm^2 among the block's active candidates
+  double total;  // sum of residual norm^2 over the block's active candidates
+  int idx;       // candidate index of best (lowest index on ties), -1 if none
+  int pad;
+};
+
+// Column-pivoted QR ID of the candidate-major matrix A (m candidates, each a
+// length-p vector at A + c*p).  Outputs: piv[0..k), rank[0] = k, and U (m x k,
+// row-major, stride k).  Rm (kmax x m) holds R; nrm (m) residual norms^2; sel
+// (m) the step at which a candidate was chosen (-1 while active).
+template <class R>
+__global__ void __launch_bounds__(256) cpqr_id_kernel(cx<R>* __restrict__ A, int m, int p, int kmax, double eps,
+                                                      cx<R>* __restrict__ Rm, R* __restrict__ nrm,
+                                                      int* __restrict__ sel, IdSlot* __restrict__ slots,
+                                                      int* __restrict__ piv, int* __restrict__ rank,
+                                                      cx<R>* __restrict__ U, GridSync gs) {
+  extern __shared__ unsigned char smraw[];
+  cx<R>* tsm = reinterpret_cast<cx<R>*>(smraw);  // per-warp back-substitution vectors
+  const int nblk = gridDim.x, blk = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const int per = (m + nblk - 1) / nblk;
+  const int c0 = blk * per, c1 = min(m, c0 + per);
+
+  // initial norms
+  for (int c = c0 + warp; c < c1; c += nwarp) {
+    const cx<R>* a = A + (long long)c * p;
+    R s = 0;
+    for (int i = lane; i < p; i += 32) s += abs2(a[i]);
+    s = warp_sum_r(s);
+    if (lane == 0) {
+      nrm[c] = s;
+      sel[c] = -1;
+    }
+  }
+  __shared__ double s_best, s_total, s_tol2;
+  __shared__ int s_idx, s_stop, s_k;
+  int k = 0;
+  for (int j = 0;; ++j) {
+    // local reduction over this block's active candidates
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double best = -1.0, total = 0.0;
+      int idx = -1;
+      for (int c = c0; c < c1; ++c) {
+        if (sel[c] != -1) continue;
+        double v = (double)nrm[c];
+        total += v;
+        if (v > best) {
+          best = v;
+          idx = c;
+        }
+      }
+      IdSlot sl;
+      sl.best = best;
+      sl.total = total;
+      sl.idx = idx;
+      sl.pad = 0;
+      slots[(j & 1) * nblk + blk] = sl;
+    }
+    if (!grid_sync(gs, nblk)) return;
+    if (threadIdx.x == 0) {
+      double best = -1.0, total = 0.0;
+      int idx = -1;
+      for (int b = 0; b < nblk; ++b) {
+        IdSlot sl = slots[(j & 1) * nblk + b];
+        total += sl.total;
+        if (sl.idx >= 0 && (sl.best > best || (sl.best == best && sl.idx < idx))) {
+          best = sl.best;
+          idx = sl.idx;
+        }
+      }
+      if (j == 0) s_tol2 = eps * eps * total;
+      s_best = best;
+      s_total = total;
+      s_idx = idx;
+      s_stop = (j == kmax) || idx < 0 || best <= 0.0 || total <= s_tol2;
+    }
+    __syncthreads();
+    if (s_stop) {
+      k = j;
+      break;
+    }
+    const int pv = s_idx;
+    const R nu = (R)sqrt(s_best);
+    const R inu = R(1) / nu;
+    const cx<R>* ap = A + (long long)pv * p;
+    if (blk == 0 && threadIdx.x == 0) {
+      piv[j] = pv;
+      Rm[(long long)j * m + pv] = mk<R>(nu, R(0));
+    }
+    if (pv >= c0 && pv < c1 && threadIdx.x == 0) sel[pv] = j;
+    // project the pivot direction q = a_pv / nu out of every active candidate (twice)
+    for (int c = c0 + warp; c < c1; c += nwarp) {
+      if (c == pv || sel[c] != -1) continue;
+      cx<R>* a = A + (long long)c * p;
+      cx<R> rsum = mk<R>(0, 0);
+      for (int pass = 0; pass < 2; ++pass) {
+        cx<R> d = mk<R>(0, 0);
+        for (int i = lane; i < p; i += 32) fmac_(d, ap[i], a[i]);
+        d = warp_sum(d);
+        d = scale(d, inu * inu);  // coefficient of a_pv
+        for (int i = lane; i < p; i += 32) {
+          cx<R> v = a[i];
+          cx<R> q = ap[i];
+          v.re -= q.re * d.re - q.im * d.im;
+          v.im -= q.re * d.im + q.im * d.re;
+          a[i] = v;
+        }
+        rsum = rsum + scale(d, nu);  // R(j, c) = q^H a = (a_pv^H a) / nu
+        __syncwarp();
+      }
+      R s = 0;
+      for (int i = lane; i < p; i += 32) s += abs2(a[i]);
+      s = warp_sum_r(s);
+      if (lane == 0) {
+        nrm[c] = s;
+        Rm[(long long)j * m + c] = rsum;
+      }
+    }
+  }
+  if (blk == 0 && threadIdx.x == 0) rank[0] = k;
+  if (threadIdx.x == 0) s_k = k;
+  __syncthreads();
+  // U rows: identity on the skeleton, T = R11^-1 R12 on the rest (one warp per candidate)
+  cx<R>* t = tsm + warp * kmax;
+  for (int c = c0 + warp; c < c1; c += nwarp) {
+    int sc = sel[c];
+    if (sc >= 0) {
+      for (int a = lane; a < k; a += 32) U[(long long)c * k + a] = mk<R>(a == sc ? R(1) : R(0), R(0));
+      continue;
+    }
+    for (int a = k - 1; a >= 0; --a) {
+      cx<R> acc = mk<R>(0, 0);
+      for (int b = a + 1 + lane; b < k; b += 32) fma_(acc, Rm[(long long)a * m + piv[b]], t[b]);
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        cx<R> rhs = Rm[(long long)a * m + c] - acc;
+        t[a] = rhs * inv(Rm[(long long)a * m + piv[a]]);
+      }
+      __syncwarp();
+    }
+    for (int a = lane; a < k; a += 32) U[(long long)c * k + a] = t[a];
+    __syncwarp();
+  }
+}
+
+template <class R>
+int upload_block(const std::vector<int>& rx, const std::vector<int>& ry, const std::vector<int>& px,
+                 const std::vector<int>& py, cx<R>* out, int* dtmp, cudaStream_t st, const KernelSpec& ks) {
+  int m = (int)rx.size(), p = (int)px.size();
+  std::vector<int> host(2 * m + 2 * p);
+  std::copy(rx.begin(), rx.end(), host.begin());
+  std::copy(ry.begin(), ry.end(), host.begin() + m);
+  std::copy(px.begin(), px.end(), host.begin() + 2 * m);
+  std::copy(py.begin(), py.end(), host.begin() + 2 * m + p);
+  LS_CUDA_TRY(cudaMemcpyAsync(dtmp, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice, st));
+  long long tot = (long long)m * p;
+  if (tot > 0)
+    block_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(dtmp, dtmp + m, m, dtmp + 2 * m, dtmp + 2 * m + p,
+                                                                   p, out, p, ks);
+  // host vector must outlive the copy
+  LS_CUDA_TRY(cudaStreamSynchronize(st));
+  return check_launch("kernel block");
+}
+
+template <class R>
+int compress_t(ls_handle* H, cudaStream_t st) {
+  const int L = H->L, s = H->s, w = H->ring;
+  int rc;
+  // workspace sizes: the largest level
+  std::vector<int> rows_x, rows_y;
+  size_t max_mp = 0, max_m = 0;
+  {
+    // sizes of every level (ranks unknown: bound m by the box points)
+    for (int l = L; l >= 1; --l) {
+      size_t m = (size_t)H->lev[l].w * H->lev[l].h;
+      size_t p = (size_t)(H->lev[l].w + 2 * w) * (H->lev[l].h + 2 * w) - (size_t)H->lev[l].w * H->lev[l].h;
+      max_m = std::max(max_m, m);
+      (void)p;
+    }
+  }
+  int* dint = nullptr;
+  for (int l = L; l >= 1; --l) {
+    LevelData& lv = H->lev[l];
+    rows_x.clear();
+    rows_y.clear();
+    if (l == L) {
+      for (int y = 0; y < s; ++y)
+        for (int x = 0; x < s; ++x) {
+          rows_x.push_back(x);
+          rows_y.push_back(y);
+        }
+    } else {
+      const LevelData& ch = H->lev[l + 1];
+      int oax, oay, obx, oby;
+      if (l % 2 == 0) {  // vertical cut: alpha left, beta right
+        oax = 0; oay = 0; obx = ch.w; oby = 0;
+      } else {           // horizontal cut: alpha upper (larger y), beta lower
+        oax = 0; oay = ch.h; obx = 0; oby = 0;
+      }
+      for (size_t i = 0; i < ch.skel_x.size(); ++i) {
+        rows_x.push_back(ch.skel_x[i] + oax);
+        rows_y.push_back(ch.skel_y[i] + oay);
+      }
+      for (size_t i = 0; i < ch.skel_x.size(); ++i) {
+        rows_x.push_back(ch.skel_x[i] + obx);
+        rows_y.push_back(ch.skel_y[i] + oby);
+      }
+    }
+    std::vector<int> px, py;
+    for (int y = -w; y < lv.h + w; ++y)
+      for (int x = -w; x < lv.w + w; ++x)
+        if (x < 0 || x >= lv.w || y < 0 || y >= lv.h) {
+          px.push_back(x);
+          py.push_back(y);
+        }
+    const int m = (int)rows_x.size(), p = (int)px.size();
+    lv.m = m;
+    lv.ring = p;
+    const int kmax = std::min(m, p);
+    if (dint) cudaFree(dint);
+    dint = nullptr;
+    if ((rc = dalloc((void**)&dint, sizeof(int) * (2 * m + 2 * p + 8)))) return rc;
+    size_t need = sizeof(cx<R>) * ((size_t)m * p + (size_t)kmax * m + (size_t)m * kmax) + sizeof(R) * m +
+                  sizeof(int) * (2 * m + 8) + sizeof(IdSlot) * 2 * 1024 + 256 * 8;
+    char* wsp = nullptr;
+    if ((rc = dalloc((void**)&wsp, need))) return rc;
+    cx<R>* A = reinterpret_cast<cx<R>*>(wsp);
+    cx<R>* Rm = A + (size_t)m * p;
+    cx<R>* Ut = Rm + (size_t)kmax * m;
+    R* nrm = reinterpret_cast<R*>(Ut + (size_t)m * kmax);
+    int* sel = reinterpret_cast<int*>(nrm + m);
+    int* piv = sel + m;
+    int* rank = piv + m;
+    IdSlot* slots = reinterpret_cast<IdSlot*>(((uintptr_t)(rank + 8) + 15) & ~(uintptr_t)15);
+    if ((rc = upload_block<R>(rows_x, rows_y, px, py, A, dint, st, H->ks_prec))) return rc;
+    // cooperative CPQR
+    int nblk = std::max(1, std::min(H->nsm, (m + 1) / 2));
+    size_t smem = sizeof(cx<R>) * (size_t)kmax * 8;
+    LS_CUDA_TRY(cudaFuncSetAttribute(cpqr_id_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cpqr_id_kernel<R>, 256, smem));
+    if (per_sm < 1) return LS_EINVAL;
+    nblk = std::min(nblk, per_sm * H->nsm);
+    LS_CUDA_TRY(cudaMemsetAsync(H->sync_buf, 0, 64, st));
+    GridSync gs;
+    gs.count = reinterpret_cast<unsigned*>(H->sync_buf);
+    gs.gen = reinterpret_cast<unsigned*>(H->sync_buf) + 1;
+    gs.abort = H->sync_buf + 2;
+    double eps = H->tol;
+    void* args[] = {&A, (void*)&m, (void*)&p, (void*)&kmax, &eps, &Rm, &nrm, &sel, &slots, &piv, &rank, &Ut, &gs};
+    LS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)cpqr_id_kernel<R>, dim3(nblk), dim3(256), args, smem, st));
+    int k = 0, abort_flag = 0;
+    LS_CUDA_TRY(cudaMemcpyAsync(&k, rank, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LS_CUDA_TRY(cudaMemcpyAsync(&abort_flag, H->sync_buf + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (abort_flag) {
+      cudaFree(wsp);
+      cudaFree(dint);
+      return LS_ETIMEOUT;
+    }
+    std::vector<int> hp(k > 0 ? k : 1);
+    if (k > 0) LS_CUDA_TRY(cudaMemcpy(hp.data(), piv, sizeof(int) * k, cudaMemcpyDeviceToHost));
+    lv.k = k;
+    lv.skel_x.resize(k);
+    lv.skel_y.resize(k);
+    for (int a = 0; a < k; ++a) {
+      lv.skel_x[a] = rows_x[hp[a]];
+      lv.skel_y[a] = rows_y[hp[a]];
+    }
+    if ((rc = dalloc(&lv.U, sizeof(cx<R>) * (size_t)m * std::max(k, 1)))) return rc;
+    if (k > 0) LS_CUDA_TRY(cudaMemcpyAsync(lv.U, Ut, sizeof(cx<R>) * (size_t)m * k, cudaMemcpyDeviceToDevice, st));
+    LS_CUDA_TRY(cudaStreamSynchronize(st));
+    H->flops_compress += 8.0 * 2.0 * (double)m * p * k;  // two projections per pivot step
+    cudaFree(wsp);
+  }
+  // sibling blocks G(skel_a, skel_b) for the two children on level l (Eq. 15)
+  for (int l = 1; l <= L; ++l) {
+    LevelData& lv = H->lev[l];
+    const int kk = lv.k;
+    int oax, oay, obx, oby;
+    if ((l - 1) % 2 == 0) {
+      oax = 0; oay = 0; obx = lv.w; oby = 0;
+    } else {
+      oax = 0; oay = lv.h; obx = 0; oby = 0;
+    }
+    std::vector<int> ax(kk), ay(kk), bx(kk), by(kk);
+    for (int i = 0; i < kk; ++i) {
+      ax[i] = lv.skel_x[i] + oax;
+      ay[i] = lv.skel_y[i] + oay;
+      bx[i] = lv.skel_x[i] + obx;
+      by[i] = lv.skel_y[i] + oby;
+    }
+    if ((rc = dalloc(&lv.Gsib, sizeof(cx<R>) * (size_t)std::max(kk * kk, 1)))) return rc;
+    if (dint) cudaFree(dint);
+    dint = nullptr;
+    if ((rc = dalloc((void**)&dint, sizeof(int) * (4 * kk + 8)))) return rc;
+    if ((rc = upload_block<R>(ax, ay, bx, by, reinterpret_cast<cx<R>*>(lv.Gsib), dint, st, H->ks_prec))) return rc;
+  }
+  {
+    std::vector<int> lx, ly;
+    for (int y = 0; y < s; ++y)
+      for (int x = 0; x < s; ++x) {
+        lx.push_back(x);
+        ly.push_back(y);
+      }
+    if ((rc = dalloc(&H->Gleaf, sizeof(cx<R>) * (size_t)s * s * s * s))) return rc;
+    if (dint) cudaFree(dint);
+    dint = nullptr;
+    if ((rc = dalloc((void**)&dint, sizeof(int) * (4 * s * s + 8)))) return rc;
+    if ((rc = upload_block<R>(lx, ly, lx, ly, reinterpret_cast<cx<R>*>(H->Gleaf), dint, st, H->ks_prec))) return rc;
+  }
+  if (dint) cudaFree(dint);
+  return LS_OK;
+}
+
+}  // namespace
+
+int compress(ls_handle* H, cudaStream_t st) {
+  return H->prec == LS_FP64 ? compress_t<double>(H, st) : compress_t<float>(H, st);
+}
+
+}  // namespace ls

@@ -1,0 +1,255 @@
+// FFT application of the corrected Nystrom operator (Sec. 2.2 last paragraph,
+// Sec. 5): y = x + kappa^2 b .* (K * x), K the discrete kernel on lattice
+// offsets |m1| < nx, |m2| < ny embedded in a (2ny) x (2nx) circulant.
+//
+// Three passes over the padded array, FP64 throughout, no cuFFT:
+//   1. rows:    zero-pad each grid row to Lx = 2nx, forward DIF FFT
+//               (natural order in, bit-reversed order out)  -> W[ny][Lx]
+//   2. columns: each block takes C adjacent columns of W, zero-pads them to
+//               Ly = 2ny, forward DIF FFT, multiplies by the kernel spectrum
+//               (looked up at the bit-reversed frequencies), inverse DIT FFT
+//               (bit-reversed in, natural out), keeps the first ny rows
+//   3. rows:    inverse DIT FFT of each W row, keeps the first nx entries and
+//               writes y = x + kappa^2 b .* conv in the same pass.
+// DIF-forward / DIT-inverse pairs need no bit-reversal permutations.  K is
+// even in m1 and m2, so its spectrum is even too and only the quarter
+// (nx+1) x (ny+1) is stored (1/(4 nx ny) folded in).
+#include "handle.h"
+
+namespace ls {
+namespace {
+
+__device__ __forceinline__ int brev(int i, int logL) { return (int)(__brev((unsigned)i) >> (32 - logL)); }
+
+// count interleaved length-L transforms s[i*stride + c]; forward DIF.
+__device__ void fft_dif(z64* s, int L, int logL, int stride, int count, const z64* tw) {
+  for (int lh = logL - 1; lh >= 0; --lh) {
+    int half = 1 << lh;
+    int tstep = L >> (lh + 1);
+    int nb = (L >> 1) * count;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+      int c = t % count, b = t / count;
+      int j = b & (half - 1), g = b >> lh;
+      int i0 = (g << (lh + 1)) + j, i1 = i0 + half;
+      z64 a = s[i0 * stride + c], bb = s[i1 * stride + c];
+      z64 w = tw[j * tstep];
+      s[i0 * stride + c] = a + bb;
+      s[i1 * stride + c] = w * (a - bb);
+    }
+    __syncthreads();
+  }
+}
+
+// inverse DIT (unnormalised), bit-reversed input, natural output.
+__device__ void fft_dit_inv(z64* s, int L, int logL, int stride, int count, const z64* tw) {
+  for (int lh = 0; lh < logL; ++lh) {
+    int half = 1 << lh;
+    int tstep = L >> (lh + 1);
+    int nb = (L >> 1) * count;
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+      int c = t % count, b = t / count;
+      int j = b & (half - 1), g = b >> lh;
+      int i0 = (g << (lh + 1)) + j, i1 = i0 + half;
+      z64 w = conjz(tw[j * tstep]);
+      z64 a = s[i0 * stride + c], tt = w * s[i1 * stride + c];
+      s[i0 * stride + c] = a + tt;
+      s[i1 * stride + c] = a - tt;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void twiddle_kernel(z64* tw, int L) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < L / 2) {
+    double sn, cs;
+    sincospi(-2.0 * (double)k / (double)L, &sn, &cs);
+    tw[k] = mk<double>(cs, sn);
+  }
+}
+
+// Pass 1: rows. in: [rhs][nrow][ld_in] (first nvalid entries used); out: [rhs][nrow][L].
+__global__ void rows_fwd_kernel(const z64* __restrict__ in, int ld_in, int nvalid, long long in_rhs_stride,
+                                z64* __restrict__ out, long long out_rhs_stride, int L, int logL,
+                                const z64* __restrict__ tw) {
+  extern __shared__ z64 sm[];
+  z64* s = sm;
+  z64* stw = sm + L;
+  int row = blockIdx.x, rhs = blockIdx.y;
+  const z64* src = in + rhs * in_rhs_stride + (long long)row * ld_in;
+  for (int i = threadIdx.x; i < L / 2; i += blockDim.x) stw[i] = tw[i];
+  for (int i = threadIdx.x; i < L; i += blockDim.x) s[i] = i < nvalid ? src[i] : mk<double>(0.0, 0.0);
+  __syncthreads();
+  fft_dif(s, L, logL, 1, 1, stw);
+  z64* dst = out + rhs * out_rhs_stride + (long long)row * L;
+  for (int i = threadIdx.x; i < L; i += blockDim.x) dst[i] = s[i];
+}
+
+// Pass 2: C columns per block.  W: [rhs][nrow_valid][Lx] (bit-reversed column order).
+// mode 0: forward, multiply by the quarter spectrum, inverse, keep first nrow rows.
+// mode 1: forward only over all Ly rows (spectrum set-up), output bit-reversed rows.
+__global__ void cols_kernel(z64* __restrict__ W, long long rhs_stride, int Lx, int logLx, int nrow, int Ly,
+                            int logLy, int C, const z64* __restrict__ tw, const z64* __restrict__ spec,
+                            int nxq, int nyq, int mode) {
+  extern __shared__ z64 sm[];
+  z64* s = sm;             // Ly * C
+  z64* stw = sm + Ly * C;  // Ly / 2
+  int c0 = blockIdx.x * C, rhs = blockIdx.y;
+  z64* base = W + rhs * rhs_stride;
+  for (int i = threadIdx.x; i < Ly / 2; i += blockDim.x) stw[i] = tw[i];
+  for (int t = threadIdx.x; t < Ly * C; t += blockDim.x) {
+    int i = t / C, c = t % C;
+    s[t] = i < nrow ? base[(long long)i * Lx + c0 + c] : mk<double>(0.0, 0.0);
+  }
+  __syncthreads();
+  fft_dif(s, Ly, logLy, C, C, stw);
+  if (mode == 1) {
+    for (int t = threadIdx.x; t < Ly * C; t += blockDim.x) {
+      int i = t / C, c = t % C;
+      base[(long long)i * Lx + c0 + c] = s[t];
+    }
+    return;
+  }
+  for (int t = threadIdx.x; t < Ly * C; t += blockDim.x) {
+    int i = t / C, c = t % C;
+    int ky = brev(i, logLy), kx = brev(c0 + c, logLx);
+    if (ky > nyq) ky = Ly - ky;
+    if (kx > nxq) kx = Lx - kx;
+    s[t] = s[t] * spec[(long long)ky * (nxq + 1) + kx];
+  }
+  __syncthreads();
+  fft_dit_inv(s, Ly, logLy, C, C, stw);
+  for (int t = threadIdx.x; t < nrow * C; t += blockDim.x) {
+    int i = t / C, c = t % C;
+    base[(long long)i * Lx + c0 + c] = s[t];
+  }
+}
+
+// Pass 3: rows inverse + epilogue y = x + kappa^2 b .* conv (or y = conv).
+__global__ void rows_inv_kernel(const z64* __restrict__ W, long long w_rhs_stride, int L, int logL,
+                                const z64* __restrict__ tw, const z64* __restrict__ x, const double* __restrict__ b,
+                                double kap2, int nx, long long g_rhs_stride, z64* __restrict__ y, int field_only) {
+  extern __shared__ z64 sm[];
+  z64* s = sm;
+  z64* stw = sm + L;
+  int row = blockIdx.x, rhs = blockIdx.y;
+  const z64* src = W + rhs * w_rhs_stride + (long long)row * L;
+  for (int i = threadIdx.x; i < L / 2; i += blockDim.x) stw[i] = tw[i];
+  for (int i = threadIdx.x; i < L; i += blockDim.x) s[i] = src[i];
+  __syncthreads();
+  fft_dit_inv(s, L, logL, 1, 1, stw);
+  long long off = rhs * g_rhs_stride + (long long)row * nx;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    z64 cv = s[i];
+    if (field_only) {
+      y[off + i] = cv;
+    } else {
+      double bb = kap2 * b[(long long)row * nx + i];
+      z64 xv = x[off + i];
+      y[off + i] = mk<double>(xv.re + bb * cv.re, xv.im + bb * cv.im);
+    }
+  }
+}
+
+// Fill the (2ny) x (2nx) circulant with K(m): index i <-> m1 = i (i < nx), i - 2nx (i > nx), 0 at i = nx.
+__global__ void circulant_kernel(z64* C, int nx, int ny, KernelSpec ks) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int Lx = 2 * nx, Ly = 2 * ny;
+  if (t >= (long long)Lx * Ly) return;
+  int i = (int)(t % Lx), j = (int)(t / Lx);
+  z64 v = mk<double>(0.0, 0.0);
+  if (i != nx && j != ny) {
+    int m1 = i < nx ? i : i - Lx;
+    int m2 = j < ny ? j : j - Ly;
+    v = kernel_entry(ks, m1, m2);
+  }
+  C[t] = v;
+}
+
+// Quarter spectrum in natural order from the bit-reversed full transform.
+__global__ void quarter_kernel(const z64* F, int Lx, int logLx, int Ly, int logLy, int nx, int ny, z64* Q,
+                               double scale) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)(nx + 1) * (ny + 1)) return;
+  int kx = (int)(t % (nx + 1)), ky = (int)(t / (nx + 1));
+  z64 v = F[(long long)brev(ky, logLy) * Lx + brev(kx, logLx)];
+  Q[t] = mk<double>(v.re * scale, v.im * scale);
+}
+
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+int cols_per_block(int Ly) {
+  // keep the column tile within ~96 KB of shared memory
+  int C = 8;
+  while (C > 1 && (size_t)Ly * C * sizeof(z64) > 96 * 1024) C >>= 1;
+  return C;
+}
+
+}  // namespace
+
+int conv_setup(ls_handle* H, cudaStream_t st) {
+  const int nx = H->grid.nx, ny = H->grid.ny;
+  H->Lx = 2 * nx;
+  H->Ly = 2 * ny;
+  H->logLx = ilog2(H->Lx);
+  H->logLy = ilog2(H->Ly);
+  if ((1 << H->logLx) != H->Lx || (1 << H->logLy) != H->Ly) return LS_EINVAL;
+  int rc;
+  if ((rc = dalloc((void**)&H->tw_x, sizeof(z64) * H->Lx / 2))) return rc;
+  if ((rc = dalloc((void**)&H->tw_y, sizeof(z64) * H->Ly / 2))) return rc;
+  if ((rc = dalloc((void**)&H->spec, sizeof(z64) * (size_t)(nx + 1) * (ny + 1)))) return rc;
+  twiddle_kernel<<<(H->Lx / 2 + 255) / 256, 256, 0, st>>>(H->tw_x, H->Lx);
+  twiddle_kernel<<<(H->Ly / 2 + 255) / 256, 256, 0, st>>>(H->tw_y, H->Ly);
+  z64* full = nullptr;
+  size_t nfull = (size_t)H->Lx * H->Ly;
+  if ((rc = dalloc((void**)&full, sizeof(z64) * nfull))) return rc;
+  circulant_kernel<<<(unsigned)((nfull + 255) / 256), 256, 0, st>>>(full, nx, ny, H->ks_mv);
+  // rows: full length, in place through the same buffer (each block owns one row)
+  size_t smr = sizeof(z64) * (H->Lx + H->Lx / 2);
+  cudaFuncSetAttribute(rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+  rows_fwd_kernel<<<dim3(H->Ly, 1), 256, smr, st>>>(full, H->Lx, H->Lx, 0, full, 0, H->Lx, H->logLx, H->tw_x);
+  int C = cols_per_block(H->Ly);
+  size_t smc = sizeof(z64) * ((size_t)H->Ly * C + H->Ly / 2);
+  cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+  cols_kernel<<<dim3(H->Lx / C, 1), 256, smc, st>>>(full, 0, H->Lx, H->logLx, H->Ly, H->Ly, H->logLy, C, H->tw_y,
+                                                    nullptr, nx, ny, 1);
+  size_t nq = (size_t)(nx + 1) * (ny + 1);
+  quarter_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(full, H->Lx, H->logLx, H->Ly, H->logLy, nx, ny,
+                                                              H->spec, 1.0 / ((double)H->Lx * H->Ly));
+  if ((rc = check_launch("conv_setup"))) return rc;
+  LS_CUDA_TRY(cudaStreamSynchronize(st));
+  cudaFree(full);
+  return LS_OK;
+}
+
+int conv_apply(ls_handle* H, const z64* x, z64* y, int nrhs, bool field_only, cudaStream_t st) {
+  const int nx = H->grid.nx, ny = H->grid.ny;
+  int rc;
+  if (H->convbuf_rhs < nrhs) {
+    if (H->convbuf) cudaFree(H->convbuf);
+    H->convbuf = nullptr;
+    H->convbuf_rhs = 0;
+    if ((rc = dalloc((void**)&H->convbuf, sizeof(z64) * (size_t)ny * H->Lx * nrhs))) return rc;
+    H->convbuf_rhs = nrhs;
+  }
+  long long g_stride = (long long)nx * ny, w_stride = (long long)ny * H->Lx;
+  size_t smr = sizeof(z64) * (H->Lx + H->Lx / 2);
+  cudaFuncSetAttribute(rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+  cudaFuncSetAttribute(rows_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+  rows_fwd_kernel<<<dim3(ny, nrhs), 256, smr, st>>>(x, nx, nx, g_stride, H->convbuf, w_stride, H->Lx, H->logLx,
+                                                    H->tw_x);
+  int C = cols_per_block(H->Ly);
+  size_t smc = sizeof(z64) * ((size_t)H->Ly * C + H->Ly / 2);
+  cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+  cols_kernel<<<dim3(H->Lx / C, nrhs), 256, smc, st>>>(H->convbuf, w_stride, H->Lx, H->logLx, ny, H->Ly, H->logLy, C,
+                                                       H->tw_y, H->spec, nx, ny, 0);
+  rows_inv_kernel<<<dim3(ny, nrhs), 256, smr, st>>>(H->convbuf, w_stride, H->Lx, H->logLx, H->tw_x, x, H->b,
+                                                    H->kappa * H->kappa, nx, g_stride, y, field_only ? 1 : 0);
+  return check_launch("conv_apply");
+}
+
+}  // namespace ls

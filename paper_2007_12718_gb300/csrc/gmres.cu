@@ -1,0 +1,294 @@
+// Right-preconditioned GMRES on the device (Sec. 5): solve A sigma = f with
+// A = I + B (G + T) applied by the FFT convolution and M the HBS inverse, as
+// A M y = f, sigma = M y.  Zero initial guess, no restart, classical
+// Gram-Schmidt applied twice, complex Givens rotations
+// Q = [[conj(c), conj(s)], [-s, c]].  All vectors and the Hessenberg matrix
+// live on the device; the host reads one residual estimate per iteration to
+// decide when to stop (gmres_tol or gmres_maxit, Sec. 6.3).  Reductions are
+// two-stage with a fixed order, so runs are bitwise reproducible.
+#include <algorithm>
+#include <vector>
+
+#include "handle.h"
+
+namespace ls {
+namespace {
+
+constexpr int kChunks = 256;  // first-stage partial sums per vector
+
+// partial[i][c] = sum over chunk c of conj(V_i[n]) w[n], i < nvec
+__global__ void dot_partials_kernel(const z64* __restrict__ V, long long ldv, const z64* __restrict__ w, long long N,
+                                    z64* __restrict__ partial) {
+  const int c = blockIdx.x, i = blockIdx.y;
+  const long long per = (N + gridDim.x - 1) / gridDim.x;
+  const long long n0 = c * per, n1 = min(N, n0 + per);
+  const z64* v = V + i * ldv;
+  z64 acc = mk<double>(0.0, 0.0);
+  for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) fmac_(acc, v[n], w[n]);
+  acc = warp_sum(acc);
+  __shared__ z64 red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    z64 v2 = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : mk<double>(0.0, 0.0);
+    v2 = warp_sum(v2);
+    if (threadIdx.x == 0) partial[(long long)i * gridDim.x + c] = v2;
+  }
+}
+
+// s_i = sum_c partial[i][c]; out[i] = s_i; if acc: acc[i * ld] += s_i
+__global__ void reduce_partials_kernel(const z64* __restrict__ partial, int nchunk, z64* __restrict__ out,
+                                       z64* __restrict__ acc, int ld) {
+  const int i = blockIdx.x;
+  z64 a = mk<double>(0.0, 0.0);
+  for (int c = threadIdx.x; c < nchunk; c += blockDim.x) a = a + partial[(long long)i * nchunk + c];
+  a = warp_sum(a);
+  __shared__ z64 red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    z64 s = mk<double>(0.0, 0.0);
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s = s + red[k];
+    out[i] = s;
+    if (acc) acc[(long long)i * ld] = acc[(long long)i * ld] + s;
+  }
+}
+
+// w -= sum_{i<nvec} V_i h_i
+__global__ void axpy_multi_kernel(const z64* __restrict__ V, long long ldv, int nvec, const z64* __restrict__ h,
+                                  z64* __restrict__ w, long long N) {
+  long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  z64 acc = w[n];
+  for (int i = 0; i < nvec; ++i) {
+    z64 c = h[i], v = V[i * ldv + n];
+    acc.re -= v.re * c.re - v.im * c.im;
+    acc.im -= v.re * c.im + v.im * c.re;
+  }
+  w[n] = acc;
+}
+
+// v = w / ||w||, with ||w||^2 in nrm2->re; optionally records ||w|| in *hout.
+__global__ void normalize_kernel(const z64* __restrict__ w, z64* __restrict__ v, long long N, const z64* nrm2,
+                                 z64* hout) {
+  long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double nr = sqrt(nrm2->re);
+  if (n == 0 && hout) *hout = mk<double>(nr, 0.0);
+  if (n >= N) return;
+  double s = nr > 0 ? 1.0 / nr : 0.0;
+  z64 x = w[n];
+  v[n] = mk<double>(x.re * s, x.im * s);
+}
+
+struct GmState {
+  double fnorm;
+  double resid;
+  int k;
+};
+
+// Column j of H: apply the earlier rotations, form the new one, update g.
+__global__ void givens_kernel(z64* H, int ldh, z64* cs, z64* sn, z64* g, int j, GmState* st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  z64* col = H + j;  // H[i][j] at H[i*ldh + j]
+  for (int i = 0; i < j; ++i) {
+    z64 a = col[(long long)i * ldh], b = col[(long long)(i + 1) * ldh];
+    z64 c = cs[i], s = sn[i];
+    z64 top = conjz(c) * a + conjz(s) * b;
+    z64 bot = mk<double>(0.0, 0.0) - s * a + c * b;
+    col[(long long)i * ldh] = top;
+    col[(long long)(i + 1) * ldh] = bot;
+  }
+  z64 a = col[(long long)j * ldh], b = col[(long long)(j + 1) * ldh];
+  double rho = sqrt(abs2(a) + abs2(b));
+  z64 c, s;
+  if (rho > 0) {
+    c = mk<double>(a.re / rho, a.im / rho);
+    s = mk<double>(b.re / rho, b.im / rho);
+  } else {
+    c = mk<double>(1.0, 0.0);
+    s = mk<double>(0.0, 0.0);
+  }
+  cs[j] = c;
+  sn[j] = s;
+  col[(long long)j * ldh] = mk<double>(rho, 0.0);
+  col[(long long)(j + 1) * ldh] = mk<double>(0.0, 0.0);
+  z64 gj = g[j];
+  g[j + 1] = mk<double>(0.0, 0.0) - s * gj;
+  g[j] = conjz(c) * gj;
+  st->resid = sqrt(abs2(g[j + 1])) / st->fnorm;
+  st->k = j + 1;
+}
+
+// Back substitution H(0:k,0:k) y = g(0:k), one thread (k <= maxit).
+__global__ void backsolve_kernel(const z64* H, int ldh, const z64* g, z64* y, int k) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; --i) {
+    z64 s = g[i];
+    for (int c = i + 1; c < k; ++c) s = s - H[(long long)i * ldh + c] * y[c];
+    y[i] = s * inv(H[(long long)i * ldh + i]);
+  }
+}
+
+// x = sum_i V_i y_i
+__global__ void combine_kernel(const z64* __restrict__ V, long long ldv, int k, const z64* __restrict__ y,
+                               z64* __restrict__ x, long long N) {
+  long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  z64 acc = mk<double>(0.0, 0.0);
+  for (int i = 0; i < k; ++i) fma_(acc, V[i * ldv + n], y[i]);
+  x[n] = acc;
+}
+
+__global__ void sub_kernel(const z64* a, const z64* b, z64* c, long long N) {
+  long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n < N) c[n] = a[n] - b[n];
+}
+
+struct Ws {
+  z64 *V, *w, *z, *Hm, *cs, *sn, *g, *y, *partial, *scal;
+  GmState* st;
+};
+
+Ws carve(ls_handle* H, long long N, int m) {
+  Ws ws;
+  char* p = reinterpret_cast<char*>(H->gm);
+  auto take = [&](size_t bytes) {
+    char* r = p;
+    p += (bytes + 255) & ~(size_t)255;
+    return r;
+  };
+  ws.V = reinterpret_cast<z64*>(take(sizeof(z64) * N * (m + 1)));
+  ws.w = reinterpret_cast<z64*>(take(sizeof(z64) * N));
+  ws.z = reinterpret_cast<z64*>(take(sizeof(z64) * N));
+  ws.Hm = reinterpret_cast<z64*>(take(sizeof(z64) * (m + 1) * m));
+  ws.cs = reinterpret_cast<z64*>(take(sizeof(z64) * m));
+  ws.sn = reinterpret_cast<z64*>(take(sizeof(z64) * m));
+  ws.g = reinterpret_cast<z64*>(take(sizeof(z64) * (m + 1)));
+  ws.y = reinterpret_cast<z64*>(take(sizeof(z64) * (m + 1)));
+  ws.partial = reinterpret_cast<z64*>(take(sizeof(z64) * kChunks * (m + 1)));
+  ws.scal = reinterpret_cast<z64*>(take(sizeof(z64) * 8));
+  ws.st = reinterpret_cast<GmState*>(take(sizeof(GmState)));
+  return ws;
+}
+
+size_t ws_bytes(long long N, int m) {
+  size_t b = 0;
+  auto add = [&](size_t x) { b += (x + 255) & ~(size_t)255; };
+  add(sizeof(z64) * N * (m + 1));
+  add(sizeof(z64) * N);
+  add(sizeof(z64) * N);
+  add(sizeof(z64) * (m + 1) * m);
+  add(sizeof(z64) * m);
+  add(sizeof(z64) * m);
+  add(sizeof(z64) * (m + 1));
+  add(sizeof(z64) * (m + 1));
+  add(sizeof(z64) * kChunks * (m + 1));
+  add(sizeof(z64) * 8);
+  add(sizeof(GmState));
+  return b;
+}
+
+// ||x||^2 into out->re (deterministic two-stage reduction)
+void norm2(const z64* x, long long N, z64* partial, z64* out, cudaStream_t st) {
+  dot_partials_kernel<<<dim3(kChunks, 1), 256, 0, st>>>(x, 0, x, N, partial);
+  reduce_partials_kernel<<<1, 256, 0, st>>>(partial, kChunks, out, nullptr, 0);
+}
+
+int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, cudaStream_t st) {
+  const long long N = (long long)H->grid.nx * H->grid.ny;
+  const int m = H->opts.gmres_maxit;
+  Ws ws = carve(H, N, m);
+  const unsigned nb = (unsigned)((N + 255) / 256);
+  int rc;
+  LS_CUDA_TRY(cudaMemsetAsync(ws.Hm, 0, sizeof(z64) * (m + 1) * m, st));
+  LS_CUDA_TRY(cudaMemsetAsync(ws.g, 0, sizeof(z64) * (m + 1), st));
+  norm2(f, N, ws.partial, ws.scal, st);
+  z64 fn2;
+  LS_CUDA_TRY(cudaMemcpyAsync(&fn2, ws.scal, sizeof(z64), cudaMemcpyDeviceToHost, st));
+  LS_CUDA_TRY(cudaStreamSynchronize(st));
+  const double fnorm = sqrt(fn2.re);
+  ls_solve_info inf;
+  inf.iterations = 0;
+  inf.converged = 1;
+  inf.resid_est = 0.0;
+  inf.resid_true = 0.0;
+  if (fnorm == 0.0) {
+    LS_CUDA_TRY(cudaMemsetAsync(sigma, 0, sizeof(z64) * N, st));
+    if (info) *info = inf;
+    return LS_OK;
+  }
+  GmState hs;
+  hs.fnorm = fnorm;
+  hs.resid = 1.0;
+  hs.k = 0;
+  LS_CUDA_TRY(cudaMemcpyAsync(ws.st, &hs, sizeof(GmState), cudaMemcpyHostToDevice, st));
+  z64 g0 = mk<double>(fnorm, 0.0);
+  LS_CUDA_TRY(cudaMemcpyAsync(ws.g, &g0, sizeof(z64), cudaMemcpyHostToDevice, st));
+  normalize_kernel<<<nb, 256, 0, st>>>(f, ws.V, N, ws.scal, nullptr);
+  int k = 0;
+  double resid = 1.0;
+  const double tol = H->opts.gmres_tol;
+  for (int j = 0; j < m; ++j) {
+    z64* vj = ws.V + (long long)j * N;
+    if ((rc = hbs_apply(H, vj, ws.z, 1, st))) return rc;
+    if ((rc = conv_apply(H, ws.z, ws.w, 1, false, st))) return rc;
+    for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+      dot_partials_kernel<<<dim3(kChunks, j + 1), 256, 0, st>>>(ws.V, N, ws.w, N, ws.partial);
+      reduce_partials_kernel<<<j + 1, 256, 0, st>>>(ws.partial, kChunks, ws.y, ws.Hm + j, m);
+      axpy_multi_kernel<<<nb, 256, 0, st>>>(ws.V, N, j + 1, ws.y, ws.w, N);
+    }
+    norm2(ws.w, N, ws.partial, ws.scal, st);
+    normalize_kernel<<<nb, 256, 0, st>>>(ws.w, ws.V + (long long)(j + 1) * N, N, ws.scal,
+                                         ws.Hm + (long long)(j + 1) * m + j);
+    givens_kernel<<<1, 32, 0, st>>>(ws.Hm, m, ws.cs, ws.sn, ws.g, j, ws.st);
+    if ((rc = check_launch("gmres iteration"))) return rc;
+    LS_CUDA_TRY(cudaMemcpyAsync(&hs, ws.st, sizeof(GmState), cudaMemcpyDeviceToHost, st));
+    LS_CUDA_TRY(cudaStreamSynchronize(st));
+    k = j + 1;
+    resid = hs.resid;
+    if (resid <= tol) break;
+  }
+  backsolve_kernel<<<1, 32, 0, st>>>(ws.Hm, m, ws.g, ws.y, k);
+  combine_kernel<<<nb, 256, 0, st>>>(ws.V, N, k, ws.y, ws.z, N);
+  if ((rc = hbs_apply(H, ws.z, sigma, 1, st))) return rc;
+  // true residual ||f - A sigma|| / ||f||
+  if ((rc = conv_apply(H, sigma, ws.w, 1, false, st))) return rc;
+  sub_kernel<<<nb, 256, 0, st>>>(f, ws.w, ws.w, N);
+  norm2(ws.w, N, ws.partial, ws.scal, st);
+  z64 rn2;
+  LS_CUDA_TRY(cudaMemcpyAsync(&rn2, ws.scal, sizeof(z64), cudaMemcpyDeviceToHost, st));
+  LS_CUDA_TRY(cudaStreamSynchronize(st));
+  if ((rc = check_launch("gmres finish"))) return rc;
+  inf.iterations = k;
+  inf.resid_est = resid;
+  inf.resid_true = sqrt(rn2.re) / fnorm;
+  inf.converged = resid <= tol;
+  if (info) *info = inf;
+  return inf.converged ? LS_OK : LS_ENOCONV;
+}
+
+}  // namespace
+
+int gmres_solve(ls_handle* H, const z64* f, z64* sigma, int nrhs, ls_solve_info* info, cudaStream_t st) {
+  const long long N = (long long)H->grid.nx * H->grid.ny;
+  const int m = H->opts.gmres_maxit;
+  size_t need = ws_bytes(N, m);
+  if (!H->gm || H->gm_bytes < need) {
+    if (H->gm) cudaFree(H->gm);
+    H->gm = nullptr;
+    int rc = dalloc(&H->gm, need);
+    if (rc) return rc;
+    H->gm_bytes = need;
+  }
+  int worst = LS_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    int rc = solve_one(H, f + r * N, sigma + r * N, info ? info + r : nullptr, st);
+    if (rc == LS_ENOCONV)
+      worst = LS_ENOCONV;
+    else if (rc)
+      return rc;
+  }
+  return worst;
+}
+
+}  // namespace ls

@@ -1,0 +1,75 @@
+// Internal state of an ls_handle and the host-side entry points of each
+// kernel family.  Not part of the public ABI.
+#pragma once
+#include <vector>
+
+#include "common.cuh"
+#include "hankel.cuh"
+
+struct LevelData {
+  int w = 0, h = 0;  // box dimensions (grid cells) of a node on this level
+  int m = 0;         // rows of this level's ID: s*s on the leaf level, 2*k_{l+1} above
+  int k = 0;         // skeleton rank k_l
+  int ring = 0;      // proxy points of this level's ring
+  std::vector<int> skel_x, skel_y;  // skeleton, local coordinates in a level-l box
+  void* U = nullptr;     // m x k, row-major (precision of the preconditioner)
+  void* Gsib = nullptr;  // k x k: G(skel_alpha, skel_beta) of two children on this level
+  void* X = nullptr;     // per node: (s^2)^2 on the leaf level, (2 k_{l+1})^2 above
+  void* S = nullptr;     // per node: k x k (levels >= 1)
+};
+
+struct ls_handle {
+  ls_grid grid;
+  double kappa = 0, tol = 0;
+  ls_opts opts;
+  int L = 0, s = 0, ring = 0;
+  int prec = LS_FP32;
+  int nsm = 0;  // SMs on the device
+  ls::KernelSpec ks_prec, ks_mv;
+
+  // FFT matvec (Sec. 5): quarter spectrum (nx+1) x (ny+1), scaled by 1/(4 nx ny)
+  ls::z64* spec = nullptr;
+  ls::z64 *tw_x = nullptr, *tw_y = nullptr;  // exp(-2 pi i k / L) for the two padded lengths
+  int Lx = 0, Ly = 0, logLx = 0, logLy = 0;
+  double* b = nullptr;          // device copy of b [ny][nx]
+  ls::z64* convbuf = nullptr;   // ny x 2nx complex per right-hand side
+  int convbuf_rhs = 0;
+
+  // HBS (Secs. 3-4)
+  std::vector<LevelData> lev;   // lev[0..L]
+  void* Gleaf = nullptr;        // s^2 x s^2
+  void* XBU = nullptr;          // per leaf s^2 x k_L: X B U (Algorithm 2, last step)
+  void* work = nullptr;         // scratch for build and apply
+  size_t work_bytes = 0;
+  int* sync_buf = nullptr;      // grid-barrier counters + error flags
+  int* d_err = nullptr;         // device status word (LS_ESINGULAR / LS_ETIMEOUT)
+  double flops_build = 0, flops_compress = 0, bytes_apply = 0, factor_bytes = 0;
+
+  // GMRES workspace (Sec. 5)
+  int gm_maxit = 0, gm_rhs = 0;
+  void* gm = nullptr;
+  size_t gm_bytes = 0;
+};
+
+namespace ls {
+
+// conv.cu
+int conv_setup(ls_handle* H, cudaStream_t st);
+// y = x + kappa^2 b .* (K * x)  (field_only: y = K * x)
+int conv_apply(ls_handle* H, const z64* x, z64* y, int nrhs, bool field_only, cudaStream_t st);
+
+// compress.cu
+int compress(ls_handle* H, cudaStream_t st);
+
+// build.cu (Algorithm 1) and apply (Algorithm 2)
+int hbs_build(ls_handle* H, cudaStream_t st);
+int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, cudaStream_t st);
+
+// gmres.cu
+int gmres_solve(ls_handle* H, const z64* f, z64* sigma, int nrhs, ls_solve_info* info, cudaStream_t st);
+
+// device allocation that records failures as LS_ENOMEM
+int dalloc(void** p, size_t bytes);
+int check_launch(const char* what);
+
+}  // namespace ls

@@ -1,0 +1,387 @@
+// C ABI of the Lippmann-Schwinger HBS solver (declared in include/ls.h).
+// Argument checking, host/device staging, and the order of the phases:
+// corrected-quadrature weights (host), FFT matvec set-up, per-level
+// compression, Algorithm 1, then apply / matvec / GMRES on request.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "handle.h"
+#include "quad.h"
+
+namespace {
+thread_local std::string g_last_error;
+
+void set_error(const char* msg) { g_last_error = msg; }
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int valid_order(int o) { return o == 2 || o == 4 || o == 6 || o == 8 || o == 10; }
+
+// Staging of host vectors through device memory.
+struct Staged {
+  ls::z64* dev = nullptr;
+  bool owned = false;
+};
+
+int stage_in(const void* p, size_t bytes, cudaStream_t st, Staged* s) {
+  if (is_device_ptr(p)) {
+    s->dev = (ls::z64*)p;
+    s->owned = false;
+    return LS_OK;
+  }
+  int rc = ls::dalloc((void**)&s->dev, bytes);
+  if (rc) return rc;
+  s->owned = true;
+  LS_CUDA_TRY(cudaMemcpyAsync(s->dev, p, bytes, cudaMemcpyHostToDevice, st));
+  return LS_OK;
+}
+
+int stage_out_alloc(void* p, size_t bytes, Staged* s) {
+  if (is_device_ptr(p)) {
+    s->dev = (ls::z64*)p;
+    s->owned = false;
+    return LS_OK;
+  }
+  int rc = ls::dalloc((void**)&s->dev, bytes);
+  if (rc) return rc;
+  s->owned = true;
+  return LS_OK;
+}
+
+int stage_out_finish(void* p, size_t bytes, cudaStream_t st, Staged* s) {
+  if (s->owned) {
+    LS_CUDA_TRY(cudaMemcpyAsync(p, s->dev, bytes, cudaMemcpyDeviceToHost, st));
+    LS_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  return LS_OK;
+}
+
+void release(Staged* s) {
+  if (s->owned && s->dev) cudaFree(s->dev);
+  s->dev = nullptr;
+  s->owned = false;
+}
+
+__global__ void rhs_kernel(const double* b, int nx, int ny, double h, double x0, double y0, double kappa, double ct,
+                           double stt, ls::z64* f) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)nx * ny) return;
+  int i = (int)(t % nx), j = (int)(t / nx);
+  double x1 = x0 + (i + 0.5) * h, x2 = y0 + (j + 0.5) * h;
+  double sn, cs;
+  sincos(kappa * (x1 * ct + x2 * stt), &sn, &cs);
+  double a = -kappa * kappa * b[t];
+  f[t] = ls::mk<double>(a * cs, a * sn);
+}
+
+__global__ void check_b_kernel(const double* b, long long n, int* bad) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double v = b[t];
+  if (!(v <= 1.0) || !isfinite(v)) atomicExch(bad, 1);
+}
+
+}  // namespace
+
+void ls_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e), what, file, line);
+  set_error(buf);
+}
+
+namespace ls {
+
+int dalloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    char buf[128];
+    snprintf(buf, sizeof(buf), "device allocation of %zu bytes failed", bytes);
+    set_error(buf);
+    *p = nullptr;
+    return LS_ENOMEM;
+  }
+  return LS_OK;
+}
+
+int check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    ls_set_last_cuda_error(e, what, __FILE__, __LINE__);
+    return LS_ECUDA;
+  }
+  return LS_OK;
+}
+
+}  // namespace ls
+
+extern "C" {
+
+void ls_default_opts(ls_opts* o) {
+  o->order_matvec = 10;
+  o->order_precond = 4;
+  o->leaf_side = 8;
+  o->proxy_width = 0;
+  o->precision = LS_FP32;
+  o->gmres_maxit = 100;
+  o->gmres_tol = 1e-10;
+}
+
+const char* ls_strerror(int code) {
+  switch (code) {
+    case LS_OK: return "ok";
+    case LS_EINVAL: return "invalid argument";
+    case LS_ENOMEM: return "device out of memory";
+    case LS_ECUDA: return "CUDA error";
+    case LS_ESINGULAR: return "zero pivot in a local inverse";
+    case LS_ENOCONV: return "GMRES did not reach the tolerance";
+    case LS_ETIMEOUT: return "device-side wait timed out";
+    default: return "unknown error";
+  }
+}
+
+const char* ls_last_error(void) { return g_last_error.c_str(); }
+
+void ls_free(ls_handle* H) {
+  if (!H) return;
+  auto f = [](void* p) {
+    if (p) cudaFree(p);
+  };
+  f(H->spec);
+  f(H->tw_x);
+  f(H->tw_y);
+  f(H->b);
+  f(H->convbuf);
+  for (auto& lv : H->lev) {
+    f(lv.U);
+    f(lv.Gsib);
+    f(lv.X);
+    f(lv.S);
+  }
+  f(H->Gleaf);
+  f(H->XBU);
+  f(H->work);
+  f(H->sync_buf);
+  f(H->d_err);
+  f(H->gm);
+  delete H;
+}
+
+static int build_impl(const ls_grid* grid, double kappa, const double* b, double tol, const ls_opts* opts,
+                      cudaStream_t st, ls_handle** out) {
+  ls_handle* H = new ls_handle();
+  *out = H;
+  H->grid = *grid;
+  H->kappa = kappa;
+  H->tol = tol;
+  if (opts)
+    H->opts = *opts;
+  else
+    ls_default_opts(&H->opts);
+  const ls_opts& o = H->opts;
+  if (!valid_order(o.order_matvec) || !valid_order(o.order_precond) || o.order_precond == 2 || o.leaf_side < 2 ||
+      o.gmres_maxit < 1 || !(o.gmres_tol > 0) || (o.precision != LS_FP64 && o.precision != LS_FP32) ||
+      o.proxy_width < 0) {
+    set_error("invalid ls_opts");
+    return LS_EINVAL;
+  }
+  H->prec = o.precision;
+  H->s = o.leaf_side;
+  // tree: cuts alternate vertical / horizontal until square leaves of side s
+  {
+    int w = grid->nx, h = grid->ny, L = 0;
+    H->lev.clear();
+    LevelData root;
+    root.w = w;
+    root.h = h;
+    H->lev.push_back(root);
+    while (!(w == H->s && h == H->s)) {
+      if (L % 2 == 0) {
+        if (w % 2 || w / 2 < H->s) break;
+        w /= 2;
+      } else {
+        if (h % 2 || h / 2 < H->s) break;
+        h /= 2;
+      }
+      ++L;
+      LevelData lv;
+      lv.w = w;
+      lv.h = h;
+      H->lev.push_back(lv);
+      if (L > 30) break;
+    }
+    if (!(w == H->s && h == H->s) || L < 1) {
+      set_error("grid does not split into 2^L square leaves of side leaf_side with alternating cuts");
+      return LS_EINVAL;
+    }
+    H->L = L;
+  }
+  // proxy ring width: Table 1 (1: ~1e-4, 2: ~1e-10, 3: full precision), and at
+  // least one uncorrected layer beyond the correction stencil radius
+  int ring = o.proxy_width;
+  if (ring == 0) {
+    ring = tol >= 1e-3 ? 1 : (tol >= 1e-9 ? 2 : 3);
+    if (tol < 1e-3 && ring < 2) ring = 2;
+    int r = o.order_precond == 4 ? 0 : o.order_precond == 6 ? 1 : o.order_precond == 8 ? 2 : 3;
+    ring = std::max(ring, r + 1);
+  }
+  H->ring = ring;
+  {
+    int dev = 0;
+    LS_CUDA_TRY(cudaGetDevice(&dev));
+    LS_CUDA_TRY(cudaDeviceGetAttribute(&H->nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  // corrected-quadrature weights (host, Sec. 2.2)
+  const double kh = kappa * grid->h;
+  for (int which = 0; which < 2; ++which) {
+    ls::QuadCorr q;
+    int order = which == 0 ? o.order_precond : o.order_matvec;
+    if (ls::quad_corrections(order, kh, &q)) {
+      set_error("unsupported quadrature order");
+      return LS_EINVAL;
+    }
+    ls::KernelSpec& ks = which == 0 ? H->ks_prec : H->ks_mv;
+    ks.kappa = kappa;
+    ks.h = grid->h;
+    ks.npts = q.npts;
+    for (int i = 0; i < 25; ++i) {
+      ks.m1[i] = q.m1[i];
+      ks.m2[i] = q.m2[i];
+      ks.wr[i] = q.wr[i];
+      ks.wi[i] = q.wi[i];
+    }
+  }
+  int rc;
+  const long long N = (long long)grid->nx * grid->ny;
+  if ((rc = ls::dalloc((void**)&H->b, sizeof(double) * N))) return rc;
+  LS_CUDA_TRY(cudaMemcpyAsync(H->b, b, sizeof(double) * N, cudaMemcpyDefault, st));
+  if ((rc = ls::dalloc((void**)&H->sync_buf, 256))) return rc;
+  if ((rc = ls::dalloc((void**)&H->d_err, sizeof(int) * 4))) return rc;
+  LS_CUDA_TRY(cudaMemsetAsync(H->d_err, 0, sizeof(int) * 4, st));
+  check_b_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(H->b, N, H->d_err + 1);
+  int bad = 0;
+  LS_CUDA_TRY(cudaMemcpyAsync(&bad, H->d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (bad) {
+    set_error("b must be finite and <= 1");
+    return LS_EINVAL;
+  }
+  if ((rc = ls::conv_setup(H, st))) return rc;
+  if ((rc = ls::compress(H, st))) return rc;
+  if ((rc = ls::hbs_build(H, st))) return rc;
+  return LS_OK;
+}
+
+int ls_build(const ls_grid* grid, double kappa, const double* b, double tol, const ls_opts* opts, void* stream,
+             ls_handle** out) {
+  if (!out) return LS_EINVAL;
+  *out = nullptr;
+  if (!grid || !b || !(kappa > 0) || !(tol > 0 && tol < 1) || grid->nx < 2 || grid->ny < 2 || !(grid->h > 0)) {
+    set_error("invalid ls_build argument");
+    return LS_EINVAL;
+  }
+  ls_handle* H = nullptr;
+  int rc = build_impl(grid, kappa, b, tol, opts, (cudaStream_t)stream, &H);
+  if (rc) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    ls_free(H);
+    return rc;
+  }
+  *out = H;
+  return LS_OK;
+}
+
+int ls_matvec(ls_handle* H, const void* x, void* y, int nrhs, int transpose, void* stream) {
+  if (!H || !x || !y || nrhs < 1 || transpose != 0) return LS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t bytes = sizeof(ls::z64) * (size_t)H->grid.nx * H->grid.ny * nrhs;
+  Staged sx, sy;
+  int rc = stage_in(x, bytes, st, &sx);
+  if (!rc) rc = stage_out_alloc(y, bytes, &sy);
+  if (!rc) rc = ls::conv_apply(H, sx.dev, sy.dev, nrhs, false, st);
+  if (!rc) rc = stage_out_finish(y, bytes, st, &sy);
+  if (sx.owned || sy.owned) cudaStreamSynchronize(st);
+  release(&sx);
+  release(&sy);
+  return rc;
+}
+
+int ls_apply(ls_handle* H, const void* f, void* q, int nrhs, int transpose, void* stream) {
+  if (!H || !f || !q || nrhs < 1 || transpose != 0) return LS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t bytes = sizeof(ls::z64) * (size_t)H->grid.nx * H->grid.ny * nrhs;
+  Staged sf, sq;
+  int rc = stage_in(f, bytes, st, &sf);
+  if (!rc) rc = stage_out_alloc(q, bytes, &sq);
+  if (!rc) rc = ls::hbs_apply(H, sf.dev, sq.dev, nrhs, st);
+  if (!rc) rc = stage_out_finish(q, bytes, st, &sq);
+  if (sf.owned || sq.owned) cudaStreamSynchronize(st);
+  release(&sf);
+  release(&sq);
+  return rc;
+}
+
+int ls_solve(ls_handle* H, const void* f, void* sigma, int nrhs, ls_solve_info* info, void* stream) {
+  if (!H || !f || !sigma || nrhs < 1) return LS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t bytes = sizeof(ls::z64) * (size_t)H->grid.nx * H->grid.ny * nrhs;
+  Staged sf, ss;
+  int rc = stage_in(f, bytes, st, &sf);
+  if (!rc) rc = stage_out_alloc(sigma, bytes, &ss);
+  int solve_rc = LS_OK;
+  if (!rc) {
+    solve_rc = ls::gmres_solve(H, sf.dev, ss.dev, nrhs, info, st);
+    if (solve_rc != LS_OK && solve_rc != LS_ENOCONV) rc = solve_rc;
+  }
+  if (!rc) rc = stage_out_finish(sigma, bytes, st, &ss);
+  if (sf.owned || ss.owned) cudaStreamSynchronize(st);
+  release(&sf);
+  release(&ss);
+  return rc ? rc : solve_rc;
+}
+
+int ls_rhs_plane_wave(ls_handle* H, const double* thetas, void* f, int nrhs, void* stream) {
+  if (!H || !thetas || !f || nrhs < 1) return LS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long N = (long long)H->grid.nx * H->grid.ny;
+  size_t bytes = sizeof(ls::z64) * N * nrhs;
+  Staged sf;
+  int rc = stage_out_alloc(f, bytes, &sf);
+  for (int r = 0; !rc && r < nrhs; ++r) {
+    rhs_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(H->b, H->grid.nx, H->grid.ny, H->grid.h, H->grid.x0,
+                                                          H->grid.y0, H->kappa, cos(thetas[r]), sin(thetas[r]),
+                                                          sf.dev + r * N);
+    rc = ls::check_launch("rhs");
+  }
+  if (!rc) rc = stage_out_finish(f, bytes, st, &sf);
+  release(&sf);
+  return rc;
+}
+
+int ls_get_build_info(const ls_handle* H, ls_build_info* info) {
+  if (!H || !info) return LS_EINVAL;
+  memset(info, 0, sizeof(*info));
+  info->levels = H->L;
+  for (int l = 0; l <= H->L && l < 32; ++l) info->ranks[l] = H->lev[l].k;
+  info->proxy_width = H->ring;
+  info->flops_build = H->flops_build;
+  info->flops_compress = H->flops_compress;
+  info->bytes_apply = H->bytes_apply;
+  info->factor_bytes = H->factor_bytes;
+  return LS_OK;
+}
+
+}  // extern "C"

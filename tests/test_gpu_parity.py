@@ -1,0 +1,199 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (all relative, 2-norm unless stated):
+* matvec (FP64 FFT convolution vs the oracle's dense matrix): 1e-12.  An FFT of
+  length L in FP64 has error ~ log2(L) * 1e-16 relative to ||K|| ||x||.
+* kernel values through the matvec impulse response: 1e-12 of max |K|.
+* HBS inverse at tolerance eps vs the dense inverse of I + B G_p: 5 eps
+  (the scheme's target, Sec. 3.2 Eq. (11) and Sec. 5); FP32 storage adds
+  ~1e-6, so FP32 runs use eps >= 1e-4.
+* preconditioned GMRES to 1e-10 vs dense LU: 1e-9 on sigma (cond(A) ~ 10 here)
+  and the true residual, measured with the oracle's own FFT matvec, <= 2e-10.
+"""
+import numpy as np
+import pytest
+
+import paper_2007_12718_gb300 as ls
+from oracle import hbs as ohbs
+from oracle import nystrom
+from paper_2007_12718_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def build(n, kappa, b, eps, order_precond=4, order_matvec=10, precision=ls.LS_FP64, ny=None, **kw):
+    return ls.ls_build(n, 1.0 / n, kappa, b, eps, order_matvec=order_matvec, order_precond=order_precond,
+                       precision=precision, ny=ny, **kw)
+
+
+@pytest.mark.parametrize("order", [2, 4, 6, 8, 10])
+def test_matvec_impulse_response_is_kernel(order):
+    """y = x + kappa^2 b (K * x) with b = 1 and x = e_c gives kappa^2 K(m) + delta:
+    every kernel value h^2 (G + tau) compared with the oracle."""
+    n, kappa = 32, 20.0
+    b = np.ones((n, n))
+    H = build(n, kappa, b, 1e-4, order_matvec=order)
+    x = np.zeros((n, n), np.complex128)
+    x[12, 9] = 1.0
+    y = host(ls.ls_matvec(H, dev(x), torch.zeros(n, n, dtype=torch.complex128, device=DEV)))
+    K = nystrom.kernel_offsets(kappa, 1.0 / n, order, n - 1, n - 1)
+    ref = np.zeros((n, n), np.complex128)
+    for j in range(n):
+        for i in range(n):
+            ref[j, i] = kappa ** 2 * K[j - 12 + n - 1, i - 9 + n - 1]
+    ref[12, 9] += 1.0
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n,ny,order,nrhs", [(32, 32, 10, 1), (64, 64, 4, 3), (32, 16, 10, 2), (128, 128, 10, 1)])
+def test_matvec_vs_dense(n, ny, order, nrhs):
+    kappa = 25.0
+    X, Y = inputs.grid_nodes(n)
+    b = inputs.gaussian_family(n, 3)[:ny, :]
+    H = build(n, kappa, b, 1e-4, order_matvec=order, ny=ny)
+    x = inputs.random_complex((nrhs, ny, n), 11)
+    y = host(ls.ls_matvec(H, dev(x), torch.zeros(nrhs, ny, n, dtype=torch.complex128, device=DEV)))
+    h = 1.0 / n
+    if n * ny <= 4096:
+        A = nystrom.dense_operator(kappa, h, b, order)
+        ref = (A @ x.reshape(nrhs, -1).T).T.reshape(x.shape)
+    else:
+        spec = nystrom.conv_kernel_spectrum(kappa, h, n, ny, order)
+        ref = nystrom.matvec_fft(spec, kappa, b, x.reshape(nrhs, -1)).reshape(x.shape)
+    for r in range(nrhs):
+        assert rel(y[r], ref[r]) < 1e-12
+
+
+def test_matvec_host_buffers_match_device():
+    n, kappa = 32, 15.0
+    b = inputs.gaussian_bump(n)
+    H = build(n, kappa, b, 1e-4)
+    x = inputs.random_complex((n, n), 4)
+    yd = host(ls.ls_matvec(H, dev(x), torch.zeros(n, n, dtype=torch.complex128, device=DEV)))
+    yh = ls.ls_matvec(H, x, np.zeros((n, n), np.complex128))
+    np.testing.assert_array_equal(yd, yh)
+
+
+@pytest.mark.parametrize("precision,eps", [(ls.LS_FP64, 1e-4), (ls.LS_FP32, 1e-4), (ls.LS_FP64, 1e-7)])
+def test_hbs_apply_vs_dense_inverse(precision, eps):
+    n, kappa = 32, 20.0
+    b = inputs.gaussian_bump(n)
+    H = build(n, kappa, b, eps, precision=precision)
+    A = nystrom.dense_operator(kappa, 1.0 / n, b, 4)
+    for seed in (1, 2):
+        f = inputs.random_complex((n, n), seed)
+        q = host(ls.ls_apply(H, dev(f), torch.zeros(n, n, dtype=torch.complex128, device=DEV)))
+        ref = nystrom.solve_dense(A, f.ravel()).reshape(n, n)
+        assert rel(q, ref) < 5 * eps
+
+
+def test_hbs_direct_solver_order10_vs_lu():
+    """Plain method at the oracle size: 32 x 32, kappa = 20, Gaussian b, 10th order,
+    eps = 1e-10, FP64: the HBS inverse applied to f is the direct solve (Sec. 4.1)."""
+    n, kappa, eps = 32, 20.0, 1e-10
+    b = inputs.gaussian_bump(n)
+    H = build(n, kappa, b, eps, order_precond=10, order_matvec=10, precision=ls.LS_FP64)
+    f = nystrom.rhs(kappa, b, n, n, 1.0 / n).reshape(n, n)
+    q = host(ls.ls_apply(H, dev(f), torch.zeros(n, n, dtype=torch.complex128, device=DEV)))
+    A = nystrom.dense_operator(kappa, 1.0 / n, b, 10)
+    ref = nystrom.solve_dense(A, f.ravel()).reshape(n, n)
+    assert rel(q, ref) < 5 * eps
+
+
+@pytest.mark.parametrize("precision", [ls.LS_FP64, ls.LS_FP32])
+def test_gmres_solve_vs_lu(precision):
+    n, kappa = 64, 40.0
+    b = inputs.gaussian_family(n, 0)
+    H = build(n, kappa, b, 1e-4, precision=precision)
+    f = nystrom.rhs(kappa, b, n, n, 1.0 / n).reshape(n, n)
+    sig = torch.zeros(n, n, dtype=torch.complex128, device=DEV)
+    info = ls.ls_solve(H, dev(f), sig)[0]
+    s = host(sig)
+    assert info["converged"] and info["resid_true"] < 2e-10
+    A = nystrom.dense_operator(kappa, 1.0 / n, b, 10)
+    ref = nystrom.solve_dense(A, f.ravel()).reshape(n, n)
+    assert rel(s, ref) < 1e-9
+    assert info["iterations"] < 30
+
+
+def test_rhs_plane_wave_matches_oracle():
+    n, kappa = 32, 20.0
+    b = inputs.gaussian_family(n, 2)
+    H = build(n, kappa, b, 1e-4)
+    th = np.array([0.0, 0.7])
+    f = host(ls.ls_rhs_plane_wave(H, th, torch.zeros(2, n, n, dtype=torch.complex128, device=DEV)))
+    for r in range(2):
+        ref = nystrom.rhs(kappa, b, n, n, 1.0 / n, th[r]).reshape(n, n)
+        assert np.abs(f[r] - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_zero_potential_gives_zero_density():
+    n = 32
+    b = np.zeros((n, n))
+    H = build(n, 20.0, b, 1e-4)
+    f = torch.zeros(n, n, dtype=torch.complex128, device=DEV)
+    sig = torch.ones(n, n, dtype=torch.complex128, device=DEV)
+    info = ls.ls_solve(H, f, sig)[0]
+    assert info["iterations"] == 0 and torch.count_nonzero(sig).item() == 0
+    x = inputs.random_complex((n, n), 3)
+    y = host(ls.ls_matvec(H, dev(x), torch.zeros(n, n, dtype=torch.complex128, device=DEV)))
+    np.testing.assert_array_equal(y, x)  # A = I when b = 0
+
+
+def test_invalid_arguments_rejected():
+    n = 32
+    with pytest.raises(ls.LSError) as e:
+        build(n, 20.0, np.full((n, n), 1.5), 1e-4)  # b > 1
+    assert e.value.code == ls.LS_EINVAL
+    with pytest.raises(ls.LSError):
+        build(n, 20.0, np.full((n, n), np.nan), 1e-4)
+    with pytest.raises(ls.LSError):
+        ls.ls_build(24, 1 / 24, 20.0, np.zeros((24, 24)), 1e-4, leaf_side=8)  # 24 = 8 * 3
+    with pytest.raises(ls.LSError):
+        build(n, 20.0, np.zeros((n, n)), 1e-4, order_matvec=7)
+
+
+def test_ranks_match_oracle_compression():
+    """Skeleton sets are not unique, but the ranks chosen by the same rule on the
+    same proxy blocks agree up to a few near-ties."""
+    n, kappa, eps = 64, 30.0, 1e-6
+    b = inputs.gaussian_bump(n)
+    H = build(n, kappa, b, eps, precision=ls.LS_FP64, proxy_width=2)
+    got = H.info()["ranks"]
+    comp = ohbs.Compression(kappa, 1.0 / n, ohbs.Tree(n, n, 8), 4, eps, 2)
+    for l in range(1, len(got)):
+        assert abs(got[l] - comp.rank[l]) <= 2, (got, comp.rank)
+
+
+@pytest.mark.slow
+def test_precond_solve_full_size_n256():
+    """The measured workload (256 x 256, kappa = 60, 20-Gaussian b, eps = 1e-4):
+    the true residual is checked with the oracle's own FFT matvec."""
+    n, kappa = 256, 60.0
+    b = inputs.gaussian_family(n, 0)
+    for precision in (ls.LS_FP32, ls.LS_FP64):
+        H = build(n, kappa, b, 1e-4, precision=precision)
+        f = nystrom.rhs(kappa, b, n, n, 1.0 / n).reshape(n, n)
+        sig = torch.zeros(n, n, dtype=torch.complex128, device=DEV)
+        info = ls.ls_solve(H, dev(f), sig)[0]
+        s = host(sig).ravel()
+        spec = nystrom.conv_kernel_spectrum(kappa, 1.0 / n, n, n, 10)
+        r = f.ravel() - nystrom.matvec_fft(spec, kappa, b, s)
+        assert info["converged"]
+        assert np.linalg.norm(r) / np.linalg.norm(f) < 2e-10
