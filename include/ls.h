@@ -132,6 +132,26 @@ int ls_get_build_info(const ls_handle* h, ls_build_info* info);
 /* ls_free -- release every resource of the handle (NULL is allowed). */
 void ls_free(ls_handle* h);
 
+/* Per-kernel timing (not part of the method; used by the benchmark).
+ * When enabled, the library records a CUDA event pair around each launch of
+ * the listed kernel families on the stream it launches them on, and
+ * accumulates launches, device milliseconds and the algorithmic bytes and
+ * flops of each launch.  ls_profile_get synchronises on the recorded events
+ * and fills up to max_entries entries; it returns the number written. */
+typedef struct {
+  char name[32];
+  long long launches;
+  double total_ms;
+  double bytes;   /* algorithmic bytes moved, summed over launches */
+  double flops;   /* algorithmic real flops, summed over launches */
+} ls_profile_entry;
+int ls_profile_enable(int on);
+int ls_profile_reset(void);
+int ls_profile_get(ls_profile_entry* out, int max_entries);
+
+/* Number of CUDA kernels this library has launched in this process so far. */
+long long ls_kernel_launches(void);
+
 /* Static text for an LS_E* code, and the last error message of this thread. */
 const char* ls_strerror(int code);
 const char* ls_last_error(void);

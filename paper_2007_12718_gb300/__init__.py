@@ -28,7 +28,8 @@ LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ESINGULAR, LS_ENOCONV, LS_ETIMEOUT = 0
 LS_FP64, LS_FP32 = 0, 1
 
 EXPORTED = ["ls_default_opts", "ls_build", "ls_apply", "ls_matvec", "ls_solve", "ls_rhs_plane_wave",
-            "ls_get_build_info", "ls_free", "ls_strerror", "ls_last_error"]
+            "ls_get_build_info", "ls_free", "ls_strerror", "ls_last_error", "ls_profile_enable",
+            "ls_profile_reset", "ls_profile_get", "ls_kernel_launches"]
 
 
 class Grid(ctypes.Structure):
@@ -51,6 +52,11 @@ class BuildInfo(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("ranks", ctypes.c_int * 32), ("proxy_width", ctypes.c_int),
                 ("flops_build", ctypes.c_double), ("flops_compress", ctypes.c_double),
                 ("bytes_apply", ctypes.c_double), ("factor_bytes", ctypes.c_double)]
+
+
+class ProfileEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong), ("total_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
 _lib = None
@@ -85,6 +91,14 @@ def load_library(path=LIB_PATH):
     lib.ls_strerror.restype = ctypes.c_char_p
     lib.ls_last_error.argtypes = []
     lib.ls_last_error.restype = ctypes.c_char_p
+    lib.ls_profile_enable.argtypes = [ip]
+    lib.ls_profile_enable.restype = ip
+    lib.ls_profile_reset.argtypes = []
+    lib.ls_profile_reset.restype = ip
+    lib.ls_profile_get.argtypes = [ctypes.POINTER(ProfileEntry), ip]
+    lib.ls_profile_get.restype = ip
+    lib.ls_kernel_launches.argtypes = []
+    lib.ls_kernel_launches.restype = ctypes.c_longlong
     _lib = lib
     return lib
 
@@ -208,6 +222,26 @@ def ls_rhs_plane_wave(handle, thetas, f, stream=None):
     _check(load_library().ls_rhs_plane_wave(handle.ptr, th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), fp,
                                             len(th), _stream(stream)), "ls_rhs_plane_wave")
     return f
+
+
+def ls_profile_enable(on=True):
+    _check(load_library().ls_profile_enable(1 if on else 0), "ls_profile_enable")
+
+
+def ls_profile_reset():
+    _check(load_library().ls_profile_reset(), "ls_profile_reset")
+
+
+def ls_profile_get():
+    """{name: {launches, total_ms, bytes, flops}} of the timed kernel families."""
+    buf = (ProfileEntry * 32)()
+    n = load_library().ls_profile_get(buf, 32)
+    return {e.name.decode(): {"launches": e.launches, "total_ms": e.total_ms, "bytes": e.bytes,
+                              "flops": e.flops} for e in buf[:n]}
+
+
+def ls_kernel_launches():
+    return int(load_library().ls_kernel_launches())
 
 
 def ls_free(handle):

@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "handle.h"
+#include "prof.h"
 
 namespace ls {
 namespace {
@@ -105,13 +106,25 @@ void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, cx<R> alpha, c
   }
   dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, batch);
   if (!ta && !tb)
-    gemm_kernel<R, false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    {
+      count_launch();
+      gemm_kernel<R, false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    }
   else if (ta && !tb)
-    gemm_kernel<R, true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    {
+      count_launch();
+      gemm_kernel<R, true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    }
   else if (!ta && tb)
-    gemm_kernel<R, false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    {
+      count_launch();
+      gemm_kernel<R, false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    }
   else
-    gemm_kernel<R, true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    {
+      count_launch();
+      gemm_kernel<R, true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    }
 }
 
 template <class R>
@@ -408,6 +421,7 @@ int invert_batch(ls_handle* H, cx<R>* X, int n, int P, cudaStream_t st) {
   if (smem_small <= 200 * 1024) {
     LS_CUDA_TRY(cudaFuncSetAttribute(inverse_smem_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem_small));
+    count_launch();
     inverse_smem_kernel<R><<<P, 256, smem_small, st>>>(X, n, H->d_err);
     return check_launch("inverse_smem");
   }
@@ -430,11 +444,13 @@ int invert_batch(ls_handle* H, cx<R>* X, int n, int P, cudaStream_t st) {
   gs.gen = reinterpret_cast<unsigned*>(H->sync_buf) + 1;
   gs.abort = H->sync_buf + 2;
   void* args[] = {&X, &X1, &n, &G, &piv, &H->d_err, &gs};
+  count_launch();
   LS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)inverse_coop_kernel<R>, dim3(nblk), dim3(256), args, smem, st));
   // result is in X (n even) or X1 (n odd)
   const cx<R>* res = (n & 1) ? X1 : X;
   cx<R>* tmp = (n & 1) ? X : X1;
   dim3 g2((unsigned)std::min<long long>(1024, ((long long)n * n + 255) / 256), P);
+  count_launch();
   unpivot_kernel<R><<<g2, 256, sizeof(int) * n, st>>>(res, tmp, n, piv);
   if (tmp != X) LS_CUDA_TRY(cudaMemcpyAsync(X, tmp, sizeof(cx<R>) * (size_t)P * n * n, cudaMemcpyDeviceToDevice, st));
   return check_launch("inverse_coop");
@@ -481,6 +497,8 @@ int build_t(ls_handle* H, cudaStream_t st) {
   TreeGeom g = make_geom(H);
   size_t smem = sizeof(cx<R>) * ((size_t)n * n + (size_t)n * kL + n) + sizeof(R) * n + sizeof(int) * n + 64;
   LS_CUDA_TRY(cudaFuncSetAttribute(leaf_build_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int tk = prof_begin(st);
+  count_launch();
   leaf_build_kernel<R><<<(unsigned)nleaf, 256, smem, st>>>(g, H->b, H->kappa * H->kappa,
                                                           reinterpret_cast<const cx<R>*>(H->Gleaf),
                                                           reinterpret_cast<const cx<R>*>(lf.U), kL,
@@ -488,7 +506,12 @@ int build_t(ls_handle* H, cudaStream_t st) {
                                                           reinterpret_cast<cx<R>*>(H->XBU),
                                                           reinterpret_cast<cx<R>*>(lf.S), H->d_err);
   if ((rc = check_launch("leaf_build"))) return rc;
-  H->flops_build += nleaf * (8.0 * n * n * n + 8.0 * n * n * kL + 8.0 * kL * n * kL);
+  {
+    double fl = nleaf * (8.0 * n * n * n + 8.0 * n * n * kL + 8.0 * kL * n * kL);
+    prof_end(tk, PR_LEAF, st, sizeof(cx<R>) * nleaf * ((double)n * n + (double)n * kL + (double)kL * kL) + 8.0 * nleaf * n,
+             fl);
+    H->flops_build += fl;
+  }
 
   // merges, level by level
   for (int l = L - 1; l >= 0; --l) {
@@ -502,6 +525,8 @@ int build_t(ls_handle* H, cudaStream_t st) {
     const cx<R>* Gs = reinterpret_cast<const cx<R>*>(ch.Gsib);
     if (kc > 0) {
       long long tot = (long long)P * n2 * kc;
+      int tg = prof_begin(st);
+      count_launch();
       merge_identity_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(X, kc, P);
       // X[0:kc, kc:] = S_a G ; X[kc:, 0:kc] = S_b G^T
       gemm<R>(st, false, false, kc, kc, kc, one<R>(), Sc, kc, 2LL * kc * kc, Gs, kc, 0, zero<R>(), X + kc, n2,
@@ -509,7 +534,10 @@ int build_t(ls_handle* H, cudaStream_t st) {
       gemm<R>(st, false, true, kc, kc, kc, one<R>(), Sc + (size_t)kc * kc, kc, 2LL * kc * kc, Gs, kc, 0, zero<R>(),
               X + (size_t)kc * n2, n2, (long long)n2 * n2, P);
       if ((rc = check_launch("merge gemm"))) return rc;
+      prof_end(tg, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * (3.0 * kc * kc), P * 2.0 * 8.0 * (double)kc * kc * kc);
+      int ti = prof_begin(st);
       if ((rc = invert_batch<R>(H, X, n2, P, st))) return rc;
+      prof_end(ti, PR_MERGE_INV, st, sizeof(cx<R>) * P * 2.0 * n2 * n2, P * 8.0 * (double)n2 * n2 * n2);
     }
     H->flops_build += P * (2.0 * 8 * (double)kc * kc * kc + 8.0 * (double)n2 * n2 * n2);
     if (l == 0) break;
@@ -521,6 +549,7 @@ int build_t(ls_handle* H, cudaStream_t st) {
     cx<R>* D = reinterpret_cast<cx<R>*>(H->work);          // P x n2 x kp
     cx<R>* E = D + (size_t)P * n2 * kp;
     // D = [S_a U_top ; S_b U_bot]
+    int ts = prof_begin(st);
     gemm<R>(st, false, false, kc, kp, kc, one<R>(), Sc, kc, 2LL * kc * kc, U, kp, 0, zero<R>(), D, kp,
             (long long)n2 * kp, P);
     gemm<R>(st, false, false, kc, kp, kc, one<R>(), Sc + (size_t)kc * kc, kc, 2LL * kc * kc, U + (size_t)kc * kp, kp,
@@ -531,7 +560,11 @@ int build_t(ls_handle* H, cudaStream_t st) {
     gemm<R>(st, true, false, kp, kp, n2, one<R>(), U, kp, 0, E, kp, (long long)n2 * kp, zero<R>(),
             reinterpret_cast<cx<R>*>(lv.S), kp, (long long)kp * kp, P);
     if ((rc = check_launch("merge S"))) return rc;
-    H->flops_build += P * (2.0 * 8 * (double)kc * kc * kp + 8.0 * (double)n2 * n2 * kp + 8.0 * (double)kp * n2 * kp);
+    {
+      double fl = P * (2.0 * 8 * (double)kc * kc * kp + 8.0 * (double)n2 * n2 * kp + 8.0 * (double)kp * n2 * kp);
+      prof_end(ts, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * ((double)n2 * n2 + 2.0 * kc * kc + (double)kp * kp), fl);
+      H->flops_build += fl;
+    }
   }
   int herr = 0;
   LS_CUDA_TRY(cudaMemcpyAsync(&herr, H->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -588,6 +621,7 @@ int apply_t(ls_handle* H, const z64* f, z64* q, cudaStream_t st) {
     tmp[l] = p;
     p += sz;
   }
+  count_launch();
   gather_leaves_kernel<R><<<(unsigned)((nleaf * n + 255) / 256), 256, 0, st>>>(g, f, F);
   const LevelData& lf = H->lev[L];
   const int kL = lf.k;
@@ -640,6 +674,7 @@ int apply_t(ls_handle* H, const z64* f, z64* q, cudaStream_t st) {
   // leaves: q = r - XBU w
   gemm<R>(st, false, false, n, 1, kL, mk<R>(R(-1), R(0)), reinterpret_cast<const cx<R>*>(H->XBU), kL,
           (long long)n * kL, wt[L], 1, kL, one<R>(), Rl, 1, n, (int)nleaf);
+  count_launch();
   scatter_leaves_kernel<R><<<(unsigned)((nleaf * n + 255) / 256), 256, 0, st>>>(g, Rl, q);
   return check_launch("hbs_apply");
 }
@@ -653,8 +688,10 @@ int hbs_build(ls_handle* H, cudaStream_t st) {
 int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, cudaStream_t st) {
   const long long N = (long long)H->grid.nx * H->grid.ny;
   for (int r = 0; r < nrhs; ++r) {
+    int tk = prof_begin(st);
     int rc = H->prec == LS_FP64 ? apply_t<double>(H, f + r * N, q + r * N, st) : apply_t<float>(H, f + r * N, q + r * N, st);
     if (rc) return rc;
+    prof_end(tk, PR_APPLY, st, H->bytes_apply, 0.0);
   }
   return LS_OK;
 }

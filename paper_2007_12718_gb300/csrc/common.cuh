@@ -118,6 +118,9 @@ __device__ __forceinline__ bool grid_sync(const GridSync& g, unsigned int nblock
   return ok != 0;
 }
 
+// Counter of kernel launches made by this library (reported by ls_kernel_launches).
+void count_launch();
+
 }  // namespace ls
 
 #define LS_CUDA_TRY(expr)                                   \

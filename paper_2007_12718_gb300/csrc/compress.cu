@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "handle.h"
+#include "prof.h"
 
 namespace ls {
 namespace {
@@ -192,8 +193,11 @@ int upload_block(const std::vector<int>& rx, const std::vector<int>& ry, const s
   LS_CUDA_TRY(cudaMemcpyAsync(dtmp, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice, st));
   long long tot = (long long)m * p;
   if (tot > 0)
-    block_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(dtmp, dtmp + m, m, dtmp + 2 * m, dtmp + 2 * m + p,
-                                                                   p, out, p, ks);
+    {
+      count_launch();
+      block_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(dtmp, dtmp + m, m, dtmp + 2 * m, dtmp + 2 * m + p,
+                                                                     p, out, p, ks);
+    }
   // host vector must outlive the copy
   LS_CUDA_TRY(cudaStreamSynchronize(st));
   return check_launch("kernel block");
@@ -285,11 +289,16 @@ int compress_t(ls_handle* H, cudaStream_t st) {
     gs.abort = H->sync_buf + 2;
     double eps = H->tol;
     void* args[] = {&A, (void*)&m, (void*)&p, (void*)&kmax, &eps, &Rm, &nrm, &sel, &slots, &piv, &rank, &Ut, &gs};
+    int tk = prof_begin(st);
+    count_launch();
     LS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)cpqr_id_kernel<R>, dim3(nblk), dim3(256), args, smem, st));
     int k = 0, abort_flag = 0;
     LS_CUDA_TRY(cudaMemcpyAsync(&k, rank, sizeof(int), cudaMemcpyDeviceToHost, st));
     LS_CUDA_TRY(cudaMemcpyAsync(&abort_flag, H->sync_buf + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
     LS_CUDA_TRY(cudaStreamSynchronize(st));
+    // CPQR work: two projections and a norm (36 p real flops) per active candidate and step
+    prof_end(tk, PR_CPQR, st, sizeof(cx<R>) * (double)m * p * 2.0 * k,
+             36.0 * p * ((double)m * k - 0.5 * (double)k * k));
     if (abort_flag) {
       cudaFree(wsp);
       cudaFree(dint);

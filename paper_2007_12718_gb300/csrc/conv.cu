@@ -15,6 +15,7 @@
 // even in m1 and m2, so its spectrum is even too and only the quarter
 // (nx+1) x (ny+1) is stored (1/(4 nx ny) folded in).
 #include "handle.h"
+#include "prof.h"
 
 namespace ls {
 namespace {
@@ -69,8 +70,7 @@ __global__ void twiddle_kernel(z64* tw, int L) {
 }
 
 // Pass 1: rows. in: [rhs][nrow][ld_in] (first nvalid entries used); out: [rhs][nrow][L].
-__global__ void rows_fwd_kernel(const z64* __restrict__ in, int ld_in, int nvalid, long long in_rhs_stride,
-                                z64* __restrict__ out, long long out_rhs_stride, int L, int logL,
+__global__ void rows_fwd_kernel(const z64* in, int ld_in, int nvalid, long long in_rhs_stride, z64* out, long long out_rhs_stride, int L, int logL,
                                 const z64* __restrict__ tw) {
   extern __shared__ z64 sm[];
   z64* s = sm;
@@ -202,22 +202,28 @@ int conv_setup(ls_handle* H, cudaStream_t st) {
   if ((rc = dalloc((void**)&H->tw_x, sizeof(z64) * H->Lx / 2))) return rc;
   if ((rc = dalloc((void**)&H->tw_y, sizeof(z64) * H->Ly / 2))) return rc;
   if ((rc = dalloc((void**)&H->spec, sizeof(z64) * (size_t)(nx + 1) * (ny + 1)))) return rc;
+  count_launch();
   twiddle_kernel<<<(H->Lx / 2 + 255) / 256, 256, 0, st>>>(H->tw_x, H->Lx);
+  count_launch();
   twiddle_kernel<<<(H->Ly / 2 + 255) / 256, 256, 0, st>>>(H->tw_y, H->Ly);
   z64* full = nullptr;
   size_t nfull = (size_t)H->Lx * H->Ly;
   if ((rc = dalloc((void**)&full, sizeof(z64) * nfull))) return rc;
+  count_launch();
   circulant_kernel<<<(unsigned)((nfull + 255) / 256), 256, 0, st>>>(full, nx, ny, H->ks_mv);
   // rows: full length, in place through the same buffer (each block owns one row)
   size_t smr = sizeof(z64) * (H->Lx + H->Lx / 2);
   cudaFuncSetAttribute(rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+  count_launch();
   rows_fwd_kernel<<<dim3(H->Ly, 1), 256, smr, st>>>(full, H->Lx, H->Lx, 0, full, 0, H->Lx, H->logLx, H->tw_x);
   int C = cols_per_block(H->Ly);
   size_t smc = sizeof(z64) * ((size_t)H->Ly * C + H->Ly / 2);
   cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+  count_launch();
   cols_kernel<<<dim3(H->Lx / C, 1), 256, smc, st>>>(full, 0, H->Lx, H->logLx, H->Ly, H->Ly, H->logLy, C, H->tw_y,
                                                     nullptr, nx, ny, 1);
   size_t nq = (size_t)(nx + 1) * (ny + 1);
+  count_launch();
   quarter_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(full, H->Lx, H->logLx, H->Ly, H->logLy, nx, ny,
                                                               H->spec, 1.0 / ((double)H->Lx * H->Ly));
   if ((rc = check_launch("conv_setup"))) return rc;
@@ -240,15 +246,27 @@ int conv_apply(ls_handle* H, const z64* x, z64* y, int nrhs, bool field_only, cu
   size_t smr = sizeof(z64) * (H->Lx + H->Lx / 2);
   cudaFuncSetAttribute(rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
   cudaFuncSetAttribute(rows_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+  // algorithmic counts per launch: 5 L log2 L flops per length-L FFT, 16-byte complex entries
+  const double N = (double)nx * ny, W = (double)ny * H->Lx, R = nrhs;
+  int tk = prof_begin(st);
+  count_launch();
   rows_fwd_kernel<<<dim3(ny, nrhs), 256, smr, st>>>(x, nx, nx, g_stride, H->convbuf, w_stride, H->Lx, H->logLx,
                                                     H->tw_x);
+  prof_end(tk, PR_MV_ROWS_FWD, st, R * (16.0 * N + 16.0 * W), R * 5.0 * W * H->logLx);
   int C = cols_per_block(H->Ly);
   size_t smc = sizeof(z64) * ((size_t)H->Ly * C + H->Ly / 2);
   cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+  tk = prof_begin(st);
+  count_launch();
   cols_kernel<<<dim3(H->Lx / C, nrhs), 256, smc, st>>>(H->convbuf, w_stride, H->Lx, H->logLx, ny, H->Ly, H->logLy, C,
                                                        H->tw_y, H->spec, nx, ny, 0);
+  prof_end(tk, PR_MV_COLS, st, R * 32.0 * W + 16.0 * (nx + 1.0) * (ny + 1.0),
+           R * (2.0 * 5.0 * H->Lx * (double)H->Ly * H->logLy + 6.0 * H->Lx * (double)H->Ly));
+  tk = prof_begin(st);
+  count_launch();
   rows_inv_kernel<<<dim3(ny, nrhs), 256, smr, st>>>(H->convbuf, w_stride, H->Lx, H->logLx, H->tw_x, x, H->b,
                                                     H->kappa * H->kappa, nx, g_stride, y, field_only ? 1 : 0);
+  prof_end(tk, PR_MV_ROWS_INV, st, R * (16.0 * W + 40.0 * N), R * 5.0 * W * H->logLx);
   return check_launch("conv_apply");
 }
 

@@ -1,6 +1,9 @@
 // Right-preconditioned GMRES on the device (Sec. 5): solve A sigma = f with
 // A = I + B (G + T) applied by the FFT convolution and M the HBS inverse, as
-// A M y = f, sigma = M y.  Zero initial guess, no restart, classical
+// A M y = f, sigma = M y.  The preconditioned vectors z_j = M v_j are kept
+// (flexible form, sigma = sum z_j y_j): an FP32 preconditioner is not exactly
+// linear in floating point, and re-applying it to V y at the end would leave
+// a residual at its rounding level.  Zero initial guess, no restart, classical
 // Gram-Schmidt applied twice, complex Givens rotations
 // Q = [[conj(c), conj(s)], [-s, c]].  All vectors and the Hessenberg matrix
 // live on the device; the host reads one residual estimate per iteration to
@@ -10,6 +13,7 @@
 #include <vector>
 
 #include "handle.h"
+#include "prof.h"
 
 namespace ls {
 namespace {
@@ -145,7 +149,7 @@ __global__ void sub_kernel(const z64* a, const z64* b, z64* c, long long N) {
 }
 
 struct Ws {
-  z64 *V, *w, *z, *Hm, *cs, *sn, *g, *y, *partial, *scal;
+  z64 *V, *Z, *w, *z, *Hm, *cs, *sn, *g, *y, *partial, *scal;
   GmState* st;
 };
 
@@ -158,6 +162,7 @@ Ws carve(ls_handle* H, long long N, int m) {
     return r;
   };
   ws.V = reinterpret_cast<z64*>(take(sizeof(z64) * N * (m + 1)));
+  ws.Z = reinterpret_cast<z64*>(take(sizeof(z64) * N * m));
   ws.w = reinterpret_cast<z64*>(take(sizeof(z64) * N));
   ws.z = reinterpret_cast<z64*>(take(sizeof(z64) * N));
   ws.Hm = reinterpret_cast<z64*>(take(sizeof(z64) * (m + 1) * m));
@@ -175,6 +180,7 @@ size_t ws_bytes(long long N, int m) {
   size_t b = 0;
   auto add = [&](size_t x) { b += (x + 255) & ~(size_t)255; };
   add(sizeof(z64) * N * (m + 1));
+  add(sizeof(z64) * N * m);
   add(sizeof(z64) * N);
   add(sizeof(z64) * N);
   add(sizeof(z64) * (m + 1) * m);
@@ -190,7 +196,9 @@ size_t ws_bytes(long long N, int m) {
 
 // ||x||^2 into out->re (deterministic two-stage reduction)
 void norm2(const z64* x, long long N, z64* partial, z64* out, cudaStream_t st) {
+  count_launch();
   dot_partials_kernel<<<dim3(kChunks, 1), 256, 0, st>>>(x, 0, x, N, partial);
+  count_launch();
   reduce_partials_kernel<<<1, 256, 0, st>>>(partial, kChunks, out, nullptr, 0);
 }
 
@@ -224,23 +232,34 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, cudaS
   LS_CUDA_TRY(cudaMemcpyAsync(ws.st, &hs, sizeof(GmState), cudaMemcpyHostToDevice, st));
   z64 g0 = mk<double>(fnorm, 0.0);
   LS_CUDA_TRY(cudaMemcpyAsync(ws.g, &g0, sizeof(z64), cudaMemcpyHostToDevice, st));
+  count_launch();
   normalize_kernel<<<nb, 256, 0, st>>>(f, ws.V, N, ws.scal, nullptr);
   int k = 0;
   double resid = 1.0;
   const double tol = H->opts.gmres_tol;
   for (int j = 0; j < m; ++j) {
     z64* vj = ws.V + (long long)j * N;
-    if ((rc = hbs_apply(H, vj, ws.z, 1, st))) return rc;
-    if ((rc = conv_apply(H, ws.z, ws.w, 1, false, st))) return rc;
+    z64* zj = ws.Z + (long long)j * N;
+    if ((rc = hbs_apply(H, vj, zj, 1, st))) return rc;
+    if ((rc = conv_apply(H, zj, ws.w, 1, false, st))) return rc;
+    int tk = prof_begin(st);
     for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+      count_launch();
       dot_partials_kernel<<<dim3(kChunks, j + 1), 256, 0, st>>>(ws.V, N, ws.w, N, ws.partial);
+      count_launch();
       reduce_partials_kernel<<<j + 1, 256, 0, st>>>(ws.partial, kChunks, ws.y, ws.Hm + j, m);
+      count_launch();
       axpy_multi_kernel<<<nb, 256, 0, st>>>(ws.V, N, j + 1, ws.y, ws.w, N);
     }
     norm2(ws.w, N, ws.partial, ws.scal, st);
+    count_launch();
     normalize_kernel<<<nb, 256, 0, st>>>(ws.w, ws.V + (long long)(j + 1) * N, N, ws.scal,
                                          ws.Hm + (long long)(j + 1) * m + j);
+    count_launch();
     givens_kernel<<<1, 32, 0, st>>>(ws.Hm, m, ws.cs, ws.sn, ws.g, j, ws.st);
+    // CGS2: per pass j+1 dot products and j+1 axpys over N complex entries, plus the norm
+    prof_end(tk, PR_GMRES_ORTH, st, 16.0 * N * (2.0 * (2.0 * (j + 1) + 2.0) + 3.0),
+             8.0 * N * (4.0 * (j + 1) + 1.0));
     if ((rc = check_launch("gmres iteration"))) return rc;
     LS_CUDA_TRY(cudaMemcpyAsync(&hs, ws.st, sizeof(GmState), cudaMemcpyDeviceToHost, st));
     LS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -248,11 +267,13 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, cudaS
     resid = hs.resid;
     if (resid <= tol) break;
   }
+  count_launch();
   backsolve_kernel<<<1, 32, 0, st>>>(ws.Hm, m, ws.g, ws.y, k);
-  combine_kernel<<<nb, 256, 0, st>>>(ws.V, N, k, ws.y, ws.z, N);
-  if ((rc = hbs_apply(H, ws.z, sigma, 1, st))) return rc;
+  count_launch();
+  combine_kernel<<<nb, 256, 0, st>>>(ws.Z, N, k, ws.y, sigma, N);
   // true residual ||f - A sigma|| / ||f||
   if ((rc = conv_apply(H, sigma, ws.w, 1, false, st))) return rc;
+  count_launch();
   sub_kernel<<<nb, 256, 0, st>>>(f, ws.w, ws.w, N);
   norm2(ws.w, N, ws.partial, ws.scal, st);
   z64 rn2;

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 
 #include "handle.h"
@@ -102,6 +103,9 @@ void ls_set_last_cuda_error(cudaError_t e, const char* what, const char* file, i
 
 namespace ls {
 
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 int dalloc(void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
@@ -154,6 +158,8 @@ const char* ls_strerror(int code) {
 }
 
 const char* ls_last_error(void) { return g_last_error.c_str(); }
+
+long long ls_kernel_launches(void) { return ls::g_launches.load(); }
 
 void ls_free(ls_handle* H) {
   if (!H) return;
@@ -271,6 +277,7 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
   if ((rc = ls::dalloc((void**)&H->sync_buf, 256))) return rc;
   if ((rc = ls::dalloc((void**)&H->d_err, sizeof(int) * 4))) return rc;
   LS_CUDA_TRY(cudaMemsetAsync(H->d_err, 0, sizeof(int) * 4, st));
+  ls::count_launch();
   check_b_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(H->b, N, H->d_err + 1);
   int bad = 0;
   LS_CUDA_TRY(cudaMemcpyAsync(&bad, H->d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -361,6 +368,7 @@ int ls_rhs_plane_wave(ls_handle* H, const double* thetas, void* f, int nrhs, voi
   Staged sf;
   int rc = stage_out_alloc(f, bytes, &sf);
   for (int r = 0; !rc && r < nrhs; ++r) {
+    ls::count_launch();
     rhs_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(H->b, H->grid.nx, H->grid.ny, H->grid.h, H->grid.x0,
                                                           H->grid.y0, H->kappa, cos(thetas[r]), sin(thetas[r]),
                                                           sf.dev + r * N);
