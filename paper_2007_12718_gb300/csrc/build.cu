@@ -283,177 +283,221 @@ __global__ void __launch_bounds__(256) leaf_build_kernel(TreeGeom g, const doubl
   }
 }
 
-// Identity blocks of K = [[I, .],[., I]] (the off-diagonal blocks are written by GEMMs).
+// Batched in-smem inverse, one block per matrix (matrix b at X + b*sX, row stride lda).
 template <class R>
-__global__ void merge_identity_kernel(cx<R>* X, int kc, int P) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  long long n2 = 2 * kc;
-  if (t >= (long long)P * n2 * kc) return;
-  long long node = t / (n2 * kc);
-  int r = (int)((t / kc) % n2), c = (int)(t % kc);
-  int cc = r < kc ? c : c + kc;  // column within the diagonal block of row r
-  X[node * n2 * n2 + (long long)r * n2 + cc] = mk<R>(r % kc == c ? R(1) : R(0), R(0));
-}
-
-// Batched in-smem inverse, one block per matrix.
-template <class R>
-__global__ void __launch_bounds__(256) inverse_smem_kernel(cx<R>* X, int n, int* err) {
+__global__ void __launch_bounds__(256) inverse_smem_kernel(cx<R>* X, int n, int lda, long long sX, int* err) {
   extern __shared__ unsigned char smraw[];
   cx<R>* a = reinterpret_cast<cx<R>*>(smraw);
   cx<R>* col = a + n * n;
   int* piv = reinterpret_cast<int*>(col + n);
-  cx<R>* M = X + (long long)blockIdx.x * n * n;
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) a[t] = M[t];
+  cx<R>* M = X + blockIdx.x * sX;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) a[t] = M[(long long)(t / n) * lda + t % n];
   __syncthreads();
   if (!gj_inverse_smem(a, n, n, piv, col)) {
     if (threadIdx.x == 0) atomicExch(err, LS_ESINGULAR);
     return;
   }
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) M[t] = a[t];
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) M[(long long)(t / n) * lda + t % n] = a[t];
 }
 
-// Cooperative Gauss-Jordan for large matrices: matrix b uses blocks
-// [b*G, (b+1)*G); each step reads buffer src and writes dst (ping-pong), so one
-// grid barrier per pivot step suffices.  piv records the row pivots.
+// Blocked Gauss-Jordan inversion, panel step (one block per matrix).  The nb
+// panel columns [k0, k0+nb) of all n rows are loaded to shared memory and
+// eliminated in place with partial row pivoting over the rows not yet used as
+// pivots; the row interchanges are recorded in piv and applied to the other
+// columns by gj_swap_extract_kernel.  On exit the panel holds the columns J of
+// the accumulated transform E (rows J: the pivot block's inverse).
 template <class R>
-__global__ void __launch_bounds__(256) inverse_coop_kernel(cx<R>* X0, cx<R>* X1, int n, int G, int* piv, int* err,
-                                                           GridSync gs) {
+__global__ void __launch_bounds__(256) gj_panel_kernel(cx<R>* X, int n, int lda, long long sX, int k0, int nb,
+                                                       int* piv, int* err) {
   extern __shared__ unsigned char smraw[];
-  cx<R>* prow = reinterpret_cast<cx<R>*>(smraw);  // n
+  cx<R>* pn = reinterpret_cast<cx<R>*>(smraw);  // n x nb
+  cx<R>* col = pn + (size_t)n * nb;             // n
+  __shared__ R s_v[8];
+  __shared__ int s_i[8];
   __shared__ int s_p;
-  __shared__ cx<R> s_d;
-  const int mat = blockIdx.x / G, gb = blockIdx.x % G;
-  const int rows_per = (n + G - 1) / G;
-  const int r0 = gb * rows_per, r1 = min(n, r0 + rows_per);
-  const long long nn = (long long)n * n;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = 0; k < n; ++k) {
-    const cx<R>* src = ((k & 1) ? X1 : X0) + mat * nn;
-    cx<R>* dst = ((k & 1) ? X0 : X1) + mat * nn;
-    if (warp == 0) {
-      R best = R(-1);
-      int bi = n;
-      for (int i = k + lane; i < n; i += 32) {
-        R v = abs2(src[(long long)i * n + k]);
-        if (v > best) {
-          best = v;
-          bi = i;
-        }
+  const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  cx<R>* M = X + b * sX;
+  for (int t = tid; t < n * nb; t += blockDim.x) pn[t] = M[(long long)(t / nb) * lda + k0 + t % nb];
+  __syncthreads();
+  for (int jj = 0; jj < nb; ++jj) {
+    const int j = k0 + jj;
+    R best = R(-1);
+    int bi = n;
+    for (int i = j + tid; i < n; i += blockDim.x) {
+      R v = abs2(pn[i * nb + jj]);
+      if (v > best) {
+        best = v;
+        bi = i;
       }
-      for (int o = 16; o; o >>= 1) {
-        R ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) {
-          best = ob;
-          bi = oi;
-        }
+    }
+    for (int o = 16; o; o >>= 1) {
+      R ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
       }
-      if (lane == 0) {
-        s_p = bi;
-        if (!(best > R(0))) {
-          s_p = -1;
-          atomicExch(err, LS_ESINGULAR);
-        } else {
-          s_d = inv(src[(long long)bi * n + k]);
-          if (gb == 0) piv[mat * n + k] = bi;
+    }
+    if (lane == 0) {
+      s_v[warp] = best;
+      s_i[warp] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      R bb = s_v[0];
+      int ii = s_i[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        if (s_v[w] > bb || (s_v[w] == bb && s_i[w] < ii)) {
+          bb = s_v[w];
+          ii = s_i[w];
         }
-      }
+      s_p = (bb > R(0)) ? ii : -1;
+      piv[(long long)b * n + j] = ii < n ? ii : j;
+      if (!(bb > R(0))) atomicExch(err, LS_ESINGULAR);
     }
     __syncthreads();
     const int p = s_p;
-    if (p < 0) {
-      // every block sees the same zero pivot and leaves together
-      return;
-    }
-    const cx<R> d = s_d;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) prow[j] = (j == k) ? d : src[(long long)p * n + j] * d;
+    if (p < 0) return;
+    if (p != j)
+      for (int c = tid; c < nb; c += blockDim.x) {
+        cx<R> t = pn[j * nb + c];
+        pn[j * nb + c] = pn[p * nb + c];
+        pn[p * nb + c] = t;
+      }
     __syncthreads();
-    for (int i = r0 + warp; i < r1; i += 8) {
-      cx<R>* out = dst + (long long)i * n;
-      if (i == k) {
-        for (int j = lane; j < n; j += 32) out[j] = prow[j];
-        continue;
-      }
-      int si = (i == p) ? k : i;
-      const cx<R>* in = src + (long long)si * n;
-      cx<R> f = in[k];
-      for (int j = lane; j < n; j += 32) {
-        if (j == k) {
-          out[j] = mk<R>(-(f.re * d.re - f.im * d.im), -(f.re * d.im + f.im * d.re));
-        } else {
-          cx<R> r = prow[j], v = in[j];
-          v.re -= f.re * r.re - f.im * r.im;
-          v.im -= f.re * r.im + f.im * r.re;
-          out[j] = v;
-        }
+    for (int i = tid; i < n; i += blockDim.x) col[i] = pn[i * nb + jj];
+    __syncthreads();
+    const cx<R> d = inv(col[j]);
+    for (int c = tid; c < nb; c += blockDim.x) pn[j * nb + c] = (c == jj) ? d : pn[j * nb + c] * d;
+    __syncthreads();
+    for (int t = tid; t < n * nb; t += blockDim.x) {
+      int i = t / nb, c = t % nb;
+      if (i == j) continue;
+      cx<R> f = col[i];
+      if (c == jj) {
+        pn[t] = mk<R>(-(f.re * d.re - f.im * d.im), -(f.re * d.im + f.im * d.re));
+      } else {
+        cx<R> r = pn[j * nb + c], v = pn[t];
+        v.re -= f.re * r.re - f.im * r.im;
+        v.im -= f.re * r.im + f.im * r.re;
+        pn[t] = v;
       }
     }
-    if (!grid_sync(gs, gridDim.x)) return;
+    __syncthreads();
+  }
+  for (int t = tid; t < n * nb; t += blockDim.x) M[(long long)(t / nb) * lda + k0 + t % nb] = pn[t];
+}
+
+// For every column c outside the panel: apply the panel's row interchanges in
+// order, move rows J = [k0, k0+nb) to Mb (nb x n, zero in the panel columns)
+// and zero them in X, so that X[:, c] += Panel * Mb[:, c] completes the step.
+template <class R>
+__global__ void gj_swap_extract_kernel(cx<R>* X, int n, int lda, long long sX, int k0, int nb, const int* piv,
+                                       cx<R>* Mb, long long sM) {
+  const int b = blockIdx.y;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  cx<R>* M = X + b * sX;
+  cx<R>* out = Mb + b * sM;
+  if (c >= k0 && c < k0 + nb) {
+    for (int jj = 0; jj < nb; ++jj) out[(long long)jj * n + c] = mk<R>(0, 0);
+    return;
+  }
+  for (int jj = 0; jj < nb; ++jj) {
+    int j = k0 + jj, p = piv[(long long)b * n + j];
+    if (p != j) {
+      cx<R> t = M[(long long)j * lda + c];
+      M[(long long)j * lda + c] = M[(long long)p * lda + c];
+      M[(long long)p * lda + c] = t;
+    }
+  }
+  for (int jj = 0; jj < nb; ++jj) {
+    out[(long long)jj * n + c] = M[(long long)(k0 + jj) * lda + c];
+    M[(long long)(k0 + jj) * lda + c] = mk<R>(0, 0);
   }
 }
 
-// Undo the row pivoting by column interchanges (in reverse order) while
-// copying the result from src to dst.
+// Undo the row pivoting by column interchanges in reverse pivot order, in
+// place, one block per (row chunk, matrix).
 template <class R>
-__global__ void unpivot_kernel(const cx<R>* src, cx<R>* dst, int n, const int* piv) {
-  extern __shared__ int idx[];
-  const long long nn = (long long)n * n;
-  const int mat = blockIdx.y;
+__global__ void unpivot_rows_kernel(cx<R>* X, int n, int lda, long long sX, const int* piv, int rows_per) {
+  extern __shared__ unsigned char smraw[];
+  int* idx = reinterpret_cast<int*>(smraw);
+  cx<R>* row = reinterpret_cast<cx<R>*>(idx + ((n + 3) & ~3));
+  const int b = blockIdx.y;
   for (int j = threadIdx.x; j < n; j += blockDim.x) idx[j] = j;
   __syncthreads();
   if (threadIdx.x == 0)
     for (int k = n - 1; k >= 0; --k) {
-      int p = piv[mat * n + k];
+      int p = piv[(long long)b * n + k];
       int t = idx[k];
       idx[k] = idx[p];
       idx[p] = t;
     }
   __syncthreads();
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nn; t += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(t / n), j = (int)(t % n);
-    dst[mat * nn + t] = src[mat * nn + (long long)i * n + idx[j]];
+  cx<R>* M = X + b * sX;
+  const int r0 = blockIdx.x * rows_per, r1 = min(n, r0 + rows_per);
+  for (int r = r0; r < r1; ++r) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) row[j] = M[(long long)r * lda + j];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) M[(long long)r * lda + j] = row[idx[j]];
+    __syncthreads();
   }
 }
 
 template <class R>
-int invert_batch(ls_handle* H, cx<R>* X, int n, int P, cudaStream_t st) {
+__global__ void set_identity_kernel(cx<R>* X, int n, int lda, long long sX, int P) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)P * n * n) return;
+  long long b = t / ((long long)n * n);
+  int i = (int)((t / n) % n), j = (int)(t % n);
+  X[b * sX + (long long)i * lda + j] = mk<R>(i == j ? R(1) : R(0), R(0));
+}
+
+// In-place inverse of P matrices (n x n, row stride lda, batch stride sX).
+// Small n: one block per matrix in shared memory.  Larger n: blocked
+// Gauss-Jordan, nb columns per panel; each panel is one panel kernel, one
+// interchange/extract kernel and one batched GEMM X += Panel * Mb, so the
+// O(n^3) work is in the GEMM.
+template <class R>
+int invert_batch(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int P, void* scratch, size_t scratch_bytes,
+                 cudaStream_t st) {
   const size_t smem_small = sizeof(cx<R>) * ((size_t)n * n + n) + sizeof(int) * n;
   if (smem_small <= 200 * 1024) {
     LS_CUDA_TRY(cudaFuncSetAttribute(inverse_smem_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem_small));
     count_launch();
-    inverse_smem_kernel<R><<<P, 256, smem_small, st>>>(X, n, H->d_err);
+    inverse_smem_kernel<R><<<P, 256, smem_small, st>>>(X, n, lda, sX, H->d_err);
     return check_launch("inverse_smem");
   }
-  // large: cooperative ping-pong
-  cx<R>* X1 = reinterpret_cast<cx<R>*>(H->work);
-  int* piv = reinterpret_cast<int*>(X1 + (size_t)P * n * n);
-  size_t need = sizeof(cx<R>) * (size_t)P * n * n + sizeof(int) * (size_t)P * n;
-  if (need > H->work_bytes) return LS_ENOMEM;
-  size_t smem = sizeof(cx<R>) * n;
-  LS_CUDA_TRY(cudaFuncSetAttribute(inverse_coop_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, inverse_coop_kernel<R>, 256, smem));
-  int maxblk = std::max(1, per_sm) * H->nsm;
-  int G = std::max(1, std::min(maxblk / P, (n + 7) / 8));
-  int nblk = G * P;
-  if (nblk > maxblk) return LS_EINVAL;
-  LS_CUDA_TRY(cudaMemsetAsync(H->sync_buf, 0, 64, st));
-  GridSync gs;
-  gs.count = reinterpret_cast<unsigned*>(H->sync_buf);
-  gs.gen = reinterpret_cast<unsigned*>(H->sync_buf) + 1;
-  gs.abort = H->sync_buf + 2;
-  void* args[] = {&X, &X1, &n, &G, &piv, &H->d_err, &gs};
+  int nb = sizeof(R) == 4 ? 32 : 16;
+  while (nb > 4 && sizeof(cx<R>) * ((size_t)n * nb + n) > 200 * 1024) nb >>= 1;
+  const size_t smem_panel = sizeof(cx<R>) * ((size_t)n * nb + n);
+  if (smem_panel > 200 * 1024) {
+    set_last_error_text("merge matrix too large for the panel kernel");
+    return LS_EINVAL;
+  }
+  cx<R>* Mb = reinterpret_cast<cx<R>*>(scratch);
+  int* piv = reinterpret_cast<int*>(Mb + (size_t)P * nb * n);
+  if (sizeof(cx<R>) * (size_t)P * nb * n + sizeof(int) * (size_t)P * n > scratch_bytes) return LS_ENOMEM;
+  LS_CUDA_TRY(cudaFuncSetAttribute(gj_panel_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_panel));
+  for (int k0 = 0; k0 < n; k0 += nb) {
+    const int w = std::min(nb, n - k0);
+    count_launch();
+    gj_panel_kernel<R><<<P, 256, smem_panel, st>>>(X, n, lda, sX, k0, w, piv, H->d_err);
+    count_launch();
+    gj_swap_extract_kernel<R><<<dim3((n + 127) / 128, P), 128, 0, st>>>(X, n, lda, sX, k0, w, piv, Mb,
+                                                                       (long long)w * n);
+    // X[:, c] += Panel (n x w, columns k0.. of X) * Mb[:, c] for the columns c outside the panel
+    gemm<R>(st, false, false, n, k0, w, one<R>(), X + k0, lda, sX, Mb, n, (long long)w * n, one<R>(), X, lda, sX, P);
+    gemm<R>(st, false, false, n, n - k0 - w, w, one<R>(), X + k0, lda, sX, Mb + k0 + w, n, (long long)w * n, one<R>(),
+            X + k0 + w, lda, sX, P);
+  }
+  const int rows_per = 16;
+  const size_t smem_u = sizeof(int) * ((n + 3) & ~3) + sizeof(cx<R>) * n;
   count_launch();
-  LS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)inverse_coop_kernel<R>, dim3(nblk), dim3(256), args, smem, st));
-  // result is in X (n even) or X1 (n odd)
-  const cx<R>* res = (n & 1) ? X1 : X;
-  cx<R>* tmp = (n & 1) ? X : X1;
-  dim3 g2((unsigned)std::min<long long>(1024, ((long long)n * n + 255) / 256), P);
-  count_launch();
-  unpivot_kernel<R><<<g2, 256, sizeof(int) * n, st>>>(res, tmp, n, piv);
-  if (tmp != X) LS_CUDA_TRY(cudaMemcpyAsync(X, tmp, sizeof(cx<R>) * (size_t)P * n * n, cudaMemcpyDeviceToDevice, st));
-  return check_launch("inverse_coop");
+  unpivot_rows_kernel<R><<<dim3((n + rows_per - 1) / rows_per, P), 256, smem_u, st>>>(X, n, lda, sX, piv, rows_per);
+  return check_launch("inverse_blocked");
 }
 
 TreeGeom make_geom(const ls_handle* H) {
@@ -524,22 +568,40 @@ int build_t(ls_handle* H, cudaStream_t st) {
     const cx<R>* Sc = reinterpret_cast<const cx<R>*>(ch.S);
     const cx<R>* Gs = reinterpret_cast<const cx<R>*>(ch.Gsib);
     if (kc > 0) {
-      long long tot = (long long)P * n2 * kc;
+      // Schur complement form of Eq. (26):  with Y1 = S_a G, Y2 = S_b G^T and
+      // W = (I - Y2 Y1)^-1,  X = [[I + Y1 W Y2, -Y1 W], [-W Y2, W]].
+      const long long sX = (long long)n2 * n2, kk = (long long)kc * kc;
+      cx<R>* Y1 = reinterpret_cast<cx<R>*>(H->work);
+      cx<R>* Y2 = Y1 + (size_t)P * kk;
+      void* scratch = Y2 + (size_t)P * kk;
+      size_t scratch_bytes = H->work_bytes - sizeof(cx<R>) * 2 * (size_t)P * kk;
+      cx<R>* X11 = X;
+      cx<R>* X12 = X + kc;
+      cx<R>* X21 = X + (size_t)kc * n2;
+      cx<R>* X22 = X21 + kc;
+      const cx<R> mone = mk<R>(R(-1), R(0));
       int tg = prof_begin(st);
+      gemm<R>(st, false, false, kc, kc, kc, one<R>(), Sc, kc, 2 * kk, Gs, kc, 0, zero<R>(), Y1, kc, kk, P);
+      gemm<R>(st, false, true, kc, kc, kc, one<R>(), Sc + kk, kc, 2 * kk, Gs, kc, 0, zero<R>(), Y2, kc, kk, P);
+      long long tot = (long long)P * kk;
       count_launch();
-      merge_identity_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(X, kc, P);
-      // X[0:kc, kc:] = S_a G ; X[kc:, 0:kc] = S_b G^T
-      gemm<R>(st, false, false, kc, kc, kc, one<R>(), Sc, kc, 2LL * kc * kc, Gs, kc, 0, zero<R>(), X + kc, n2,
-              (long long)n2 * n2, P);
-      gemm<R>(st, false, true, kc, kc, kc, one<R>(), Sc + (size_t)kc * kc, kc, 2LL * kc * kc, Gs, kc, 0, zero<R>(),
-              X + (size_t)kc * n2, n2, (long long)n2 * n2, P);
+      set_identity_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(X22, kc, n2, sX, P);
+      gemm<R>(st, false, false, kc, kc, kc, mone, Y2, kc, kk, Y1, kc, kk, one<R>(), X22, n2, sX, P);  // Z
       if ((rc = check_launch("merge gemm"))) return rc;
-      prof_end(tg, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * (3.0 * kc * kc), P * 2.0 * 8.0 * (double)kc * kc * kc);
+      prof_end(tg, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * (5.0 * kk), P * 3.0 * 8.0 * (double)kc * kc * kc);
       int ti = prof_begin(st);
-      if ((rc = invert_batch<R>(H, X, n2, P, st))) return rc;
-      prof_end(ti, PR_MERGE_INV, st, sizeof(cx<R>) * P * 2.0 * n2 * n2, P * 8.0 * (double)n2 * n2 * n2);
+      if ((rc = invert_batch<R>(H, X22, kc, n2, sX, P, scratch, scratch_bytes, st))) return rc;  // W
+      prof_end(ti, PR_MERGE_INV, st, sizeof(cx<R>) * P * 2.0 * kk, P * 8.0 * (double)kc * kc * kc);
+      tg = prof_begin(st);
+      gemm<R>(st, false, false, kc, kc, kc, mone, X22, n2, sX, Y2, kc, kk, zero<R>(), X21, n2, sX, P);  // -W Y2
+      gemm<R>(st, false, false, kc, kc, kc, mone, Y1, kc, kk, X22, n2, sX, zero<R>(), X12, n2, sX, P);  // -Y1 W
+      count_launch();
+      set_identity_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(X11, kc, n2, sX, P);
+      gemm<R>(st, false, false, kc, kc, kc, mone, Y1, kc, kk, X21, n2, sX, one<R>(), X11, n2, sX, P);  // I + Y1 W Y2
+      if ((rc = check_launch("merge blocks"))) return rc;
+      prof_end(tg, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * (4.0 * kk + (double)sX), P * 3.0 * 8.0 * (double)kc * kc * kc);
     }
-    H->flops_build += P * (2.0 * 8 * (double)kc * kc * kc + 8.0 * (double)n2 * n2 * n2);
+    H->flops_build += P * (6.0 * 8 * (double)kc * kc * kc + 8.0 * (double)kc * kc * kc);
     if (l == 0) break;
     const int kp = lv.k;
     if ((rc = dalloc(&lv.S, sizeof(cx<R>) * (size_t)P * std::max(kp * kp, 1)))) return rc;
@@ -577,12 +639,70 @@ int build_t(ls_handle* H, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------- apply
+// y[b] = alpha A[b] x[b] + beta y[b], A[b] M x K row-major: one warp per row.
 template <class R>
-__global__ void gather_leaves_kernel(TreeGeom g, const z64* __restrict__ f, cx<R>* __restrict__ F) {
+__global__ void __launch_bounds__(256) gemv_n_kernel(int M, int K, cx<R> alpha, const cx<R>* __restrict__ A, int lda,
+                                                     long long sA, const cx<R>* __restrict__ x, long long sx,
+                                                     cx<R> beta, cx<R>* __restrict__ y, long long sy) {
+  const int b = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + warp;
+  if (i >= M) return;
+  const cx<R>* a = A + b * sA + (long long)i * lda;
+  const cx<R>* xv = x + b * sx;
+  cx<R> acc = mk<R>(0, 0);
+  for (int j = lane; j < K; j += 32) fma_(acc, a[j], xv[j]);
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    cx<R> v = alpha * acc;
+    if (beta.re != R(0) || beta.im != R(0)) v = v + beta * y[b * sy + i];
+    y[b * sy + i] = v;
+  }
+}
+
+// y[b] = alpha A[b]^T x[b] + beta y[b], A[b] K x M row-major (rows i < K, columns j < M):
+// lanes over 32 adjacent columns, the 8 warps split the rows, reduced in shared memory.
+template <class R>
+__global__ void __launch_bounds__(256) gemv_t_kernel(int M, int K, cx<R> alpha, const cx<R>* __restrict__ A, int lda,
+                                                     long long sA, const cx<R>* __restrict__ x, long long sx,
+                                                     cx<R> beta, cx<R>* __restrict__ y, long long sy) {
+  __shared__ cx<R> part[8][32];
+  const int b = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = blockIdx.x * 32 + lane;
+  const cx<R>* a = A + b * sA;
+  const cx<R>* xv = x + b * sx;
+  cx<R> acc = mk<R>(0, 0);
+  if (j < M)
+    for (int i = warp; i < K; i += 8) fma_(acc, a[(long long)i * lda + j], xv[i]);
+  part[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && j < M) {
+    cx<R> v = part[0][lane];
+    for (int w = 1; w < 8; ++w) v = v + part[w][lane];
+    v = alpha * v;
+    if (beta.re != R(0) || beta.im != R(0)) v = v + beta * y[b * sy + j];
+    y[b * sy + j] = v;
+  }
+}
+
+// y = alpha op(A) x + beta y for a batch of vectors (op(A) is M x K).
+template <class R>
+void gemv(cudaStream_t st, bool ta, int M, int K, cx<R> alpha, const cx<R>* A, int lda, long long sA, const cx<R>* x,
+          long long sx, cx<R> beta, cx<R>* y, long long sy, int batch) {
+  if (M <= 0 || K <= 0 || batch <= 0) return;
+  count_launch();
+  if (!ta)
+    gemv_n_kernel<R><<<dim3((M + 7) / 8, batch), 256, 0, st>>>(M, K, alpha, A, lda, sA, x, sx, beta, y, sy);
+  else
+    gemv_t_kernel<R><<<dim3((M + 31) / 32, batch), 256, 0, st>>>(M, K, alpha, A, lda, sA, x, sx, beta, y, sy);
+}
+
+template <class R>
+__global__ void gather_leaves_kernel(TreeGeom g, const z64* const* __restrict__ fslot, cx<R>* __restrict__ F) {
   const int n = g.s * g.s;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long nl = 1LL << g.L;
   if (t >= nl * n) return;
+  const z64* f = *fslot;
   int leaf = (int)(t / n), i = (int)(t % n);
   int ox, oy;
   leaf_origin(g, leaf, ox, oy);
@@ -591,11 +711,12 @@ __global__ void gather_leaves_kernel(TreeGeom g, const z64* __restrict__ f, cx<R
 }
 
 template <class R>
-__global__ void scatter_leaves_kernel(TreeGeom g, const cx<R>* __restrict__ Q, z64* __restrict__ q) {
+__global__ void scatter_leaves_kernel(TreeGeom g, const cx<R>* __restrict__ Q, z64* const* __restrict__ qslot) {
   const int n = g.s * g.s;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long nl = 1LL << g.L;
   if (t >= nl * n) return;
+  z64* q = *qslot;
   int leaf = (int)(t / n), i = (int)(t % n);
   int ox, oy;
   leaf_origin(g, leaf, ox, oy);
@@ -603,8 +724,14 @@ __global__ void scatter_leaves_kernel(TreeGeom g, const cx<R>* __restrict__ Q, z
   q[(long long)(oy + ly) * g.nx + ox + lx] = cvt<double>(Q[t]);
 }
 
+__global__ void set_slots_kernel(z64** slots, const z64* f, z64* q) {
+  slots[0] = const_cast<z64*>(f);
+  slots[1] = q;
+}
+
+// Algorithm 2 for one right-hand side read from *slots[0], written to *slots[1].
 template <class R>
-int apply_t(ls_handle* H, const z64* f, z64* q, cudaStream_t st) {
+int apply_core(ls_handle* H, z64** slots, cudaStream_t st) {
   const int L = H->L, n = H->s * H->s;
   const long long nleaf = 1LL << L;
   TreeGeom g = make_geom(H);
@@ -621,62 +748,86 @@ int apply_t(ls_handle* H, const z64* f, z64* q, cudaStream_t st) {
     tmp[l] = p;
     p += sz;
   }
+  const cx<R> mone = mk<R>(R(-1), R(0));
   count_launch();
-  gather_leaves_kernel<R><<<(unsigned)((nleaf * n + 255) / 256), 256, 0, st>>>(g, f, F);
+  gather_leaves_kernel<R><<<(unsigned)((nleaf * n + 255) / 256), 256, 0, st>>>(g, slots, F);
   const LevelData& lf = H->lev[L];
   const int kL = lf.k;
-  const cx<R>* XL = reinterpret_cast<const cx<R>*>(lf.X);
-  gemm<R>(st, false, false, n, 1, n, one<R>(), XL, n, (long long)n * n, F, 1, n, zero<R>(), Rl, 1, n, (int)nleaf);
-  gemm<R>(st, true, false, kL, 1, n, one<R>(), reinterpret_cast<const cx<R>*>(lf.U), kL, 0, Rl, 1, n, zero<R>(), rt[L],
-          1, kL, (int)nleaf);
-  // upward pass: r_tau = U^T X [r_a; r_b]
+  // leaves: r = X f, r~ = U^T r  (Eq. (24))
+  gemv<R>(st, false, n, n, one<R>(), reinterpret_cast<const cx<R>*>(lf.X), n, (long long)n * n, F, n, zero<R>(), Rl,
+          n, (int)nleaf);
+  gemv<R>(st, true, kL, n, one<R>(), reinterpret_cast<const cx<R>*>(lf.U), kL, 0, Rl, n, zero<R>(), rt[L], kL,
+          (int)nleaf);
+  // upward pass: r~_tau = U^T X [r~_a; r~_b]  (Eq. (28)); X [.;.] goes to the child-level scratch
   for (int l = L - 1; l >= 1; --l) {
     const int P = 1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
-    const cx<R>* X = reinterpret_cast<const cx<R>*>(H->lev[l].X);
-    // X [r_a; r_b] goes to the child-level scratch, which holds 2 P n2 entries
-    gemm<R>(st, false, false, n2, 1, n2, one<R>(), X, n2, (long long)n2 * n2, rt[l + 1], 1, n2, zero<R>(), tmp[l + 1],
-            1, n2, P);
-    gemm<R>(st, true, false, kp, 1, n2, one<R>(), reinterpret_cast<const cx<R>*>(H->lev[l].U), kp, 0, tmp[l + 1], 1,
-            n2, zero<R>(), rt[l], 1, kp, P);
+    gemv<R>(st, false, n2, n2, one<R>(), reinterpret_cast<const cx<R>*>(H->lev[l].X), n2, (long long)n2 * n2,
+            rt[l + 1], n2, zero<R>(), tmp[l + 1], n2, P);
+    gemv<R>(st, true, kp, n2, one<R>(), reinterpret_cast<const cx<R>*>(H->lev[l].U), kp, 0, tmp[l + 1], n2, zero<R>(),
+            rt[l], kp, P);
   }
-  // root: q = X_0 [r_a; r_b]; w_a = G q_b, w_b = G^T q_a
+  // root: q = X_0 [r~_a; r~_b];  w~_a = G q_b, w~_b = G^T q_a  (Eq. (29), Lemma 4.1)
   {
     const int kc = H->lev[1].k, n2 = 2 * kc;
     cx<R>* qr = tmp[1];
-    gemm<R>(st, false, false, n2, 1, n2, one<R>(), reinterpret_cast<const cx<R>*>(H->lev[0].X), n2, 0, rt[1], 1, 0,
-            zero<R>(), qr, 1, 0, 1);
     const cx<R>* G1 = reinterpret_cast<const cx<R>*>(H->lev[1].Gsib);
-    gemm<R>(st, false, false, kc, 1, kc, one<R>(), G1, kc, 0, qr + kc, 1, 0, zero<R>(), wt[1], 1, 0, 1);
-    gemm<R>(st, true, false, kc, 1, kc, one<R>(), G1, kc, 0, qr, 1, 0, zero<R>(), wt[1] + kc, 1, 0, 1);
+    gemv<R>(st, false, n2, n2, one<R>(), reinterpret_cast<const cx<R>*>(H->lev[0].X), n2, 0, rt[1], 0, zero<R>(), qr,
+            0, 1);
+    gemv<R>(st, false, kc, kc, one<R>(), G1, kc, 0, qr + kc, 0, zero<R>(), wt[1], 0, 1);
+    gemv<R>(st, true, kc, kc, one<R>(), G1, kc, 0, qr, 0, zero<R>(), wt[1] + kc, 0, 1);
   }
-  // downward pass, l = 1 .. L-1
+  // downward pass, l = 1 .. L-1:  q~ = X ([r~_a; r~_b] - diag(S_a,S_b) U w~),
+  // then w~_children = offdiag(G) q~ + U w~ (Lemma 4.1)
   for (int l = 1; l <= L - 1; ++l) {
     const int P = 1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
     const cx<R>* U = reinterpret_cast<const cx<R>*>(H->lev[l].U);
     const cx<R>* Sc = reinterpret_cast<const cx<R>*>(H->lev[l + 1].S);
     const cx<R>* X = reinterpret_cast<const cx<R>*>(H->lev[l].X);
     const cx<R>* Gs = reinterpret_cast<const cx<R>*>(H->lev[l + 1].Gsib);
-    cx<R>* Uw = wt[l + 1];  // U w_tau, laid out as the children's incoming expansions
-    cx<R>* t = tmp[l + 1];  // [r_a; r_b] - diag(S_a, S_b) U w_tau
-    gemm<R>(st, false, false, n2, 1, kp, one<R>(), U, kp, 0, wt[l], 1, kp, zero<R>(), Uw, 1, n2, P);
+    cx<R>* Uw = wt[l + 1];  // U w~_tau, laid out as the children's incoming expansions
+    cx<R>* t = tmp[l + 1];
+    gemv<R>(st, false, n2, kp, one<R>(), U, kp, 0, wt[l], kp, zero<R>(), Uw, n2, P);
     LS_CUDA_TRY(cudaMemcpyAsync(t, rt[l + 1], sizeof(cx<R>) * (size_t)P * n2, cudaMemcpyDeviceToDevice, st));
-    const cx<R> mone = mk<R>(R(-1), R(0));
-    gemm<R>(st, false, false, kc, 1, kc, mone, Sc, kc, 2LL * kc * kc, Uw, 1, n2, one<R>(), t, 1, n2, P);
-    gemm<R>(st, false, false, kc, 1, kc, mone, Sc + (size_t)kc * kc, kc, 2LL * kc * kc, Uw + kc, 1, n2, one<R>(),
-            t + kc, 1, n2, P);
-    // q = X t overwrites [r_a; r_b], which no later step reads
-    cx<R>* qbuf = rt[l + 1];
-    gemm<R>(st, false, false, n2, 1, n2, one<R>(), X, n2, (long long)n2 * n2, t, 1, n2, zero<R>(), qbuf, 1, n2, P);
-    // w_a = U w_top + G q_b ; w_b = U w_bot + G^T q_a  (Uw already in place)
-    gemm<R>(st, false, false, kc, 1, kc, one<R>(), Gs, kc, 0, qbuf + kc, 1, n2, one<R>(), Uw, 1, n2, P);
-    gemm<R>(st, true, false, kc, 1, kc, one<R>(), Gs, kc, 0, qbuf, 1, n2, one<R>(), Uw + kc, 1, n2, P);
+    gemv<R>(st, false, kc, kc, mone, Sc, kc, 2LL * kc * kc, Uw, n2, one<R>(), t, n2, P);
+    gemv<R>(st, false, kc, kc, mone, Sc + (size_t)kc * kc, kc, 2LL * kc * kc, Uw + kc, n2, one<R>(), t + kc, n2, P);
+    cx<R>* qbuf = rt[l + 1];  // q~ overwrites [r~_a; r~_b], which no later step reads
+    gemv<R>(st, false, n2, n2, one<R>(), X, n2, (long long)n2 * n2, t, n2, zero<R>(), qbuf, n2, P);
+    gemv<R>(st, false, kc, kc, one<R>(), Gs, kc, 0, qbuf + kc, n2, one<R>(), Uw, n2, P);
+    gemv<R>(st, true, kc, kc, one<R>(), Gs, kc, 0, qbuf, n2, one<R>(), Uw + kc, n2, P);
   }
-  // leaves: q = r - XBU w
-  gemm<R>(st, false, false, n, 1, kL, mk<R>(R(-1), R(0)), reinterpret_cast<const cx<R>*>(H->XBU), kL,
-          (long long)n * kL, wt[L], 1, kL, one<R>(), Rl, 1, n, (int)nleaf);
+  // leaves: q = r - X B U w~
+  gemv<R>(st, false, n, kL, mone, reinterpret_cast<const cx<R>*>(H->XBU), kL, (long long)n * kL, wt[L], kL, one<R>(),
+          Rl, n, (int)nleaf);
   count_launch();
-  scatter_leaves_kernel<R><<<(unsigned)((nleaf * n + 255) / 256), 256, 0, st>>>(g, Rl, q);
+  scatter_leaves_kernel<R><<<(unsigned)((nleaf * n + 255) / 256), 256, 0, st>>>(g, Rl, slots + 1);
   return check_launch("hbs_apply");
+}
+
+// The apply is recorded once per handle as a CUDA graph on a private stream
+// (inputs and outputs are passed through two device-side pointer slots), and
+// replayed on the caller's stream.
+int hbs_apply_graph_init(ls_handle* H) {
+  if (H->apply_exec) return LS_OK;
+  int rc;
+  if (!H->slots && (rc = dalloc((void**)&H->slots, 2 * sizeof(z64*)))) return rc;
+  cudaStream_t cs;
+  LS_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  long long before = ::ls_kernel_launches();
+  cudaGraph_t graph;
+  LS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  rc = H->prec == LS_FP64 ? apply_core<double>(H, H->slots, cs) : apply_core<float>(H, H->slots, cs);
+  cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  H->apply_nodes = ::ls_kernel_launches() - before;
+  count_launch(-H->apply_nodes);  // recorded, not launched
+  if (rc) {
+    cudaStreamDestroy(cs);
+    return rc;
+  }
+  LS_CUDA_TRY(e);
+  LS_CUDA_TRY(cudaGraphInstantiate(&H->apply_exec, graph, 0));
+  cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  return LS_OK;
 }
 
 }  // namespace
@@ -687,13 +838,17 @@ int hbs_build(ls_handle* H, cudaStream_t st) {
 
 int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, cudaStream_t st) {
   const long long N = (long long)H->grid.nx * H->grid.ny;
+  int rc;
+  if ((rc = hbs_apply_graph_init(H))) return rc;
   for (int r = 0; r < nrhs; ++r) {
     int tk = prof_begin(st);
-    int rc = H->prec == LS_FP64 ? apply_t<double>(H, f + r * N, q + r * N, st) : apply_t<float>(H, f + r * N, q + r * N, st);
-    if (rc) return rc;
+    count_launch();
+    set_slots_kernel<<<1, 1, 0, st>>>(H->slots, f + r * N, q + r * N);
+    LS_CUDA_TRY(cudaGraphLaunch(H->apply_exec, st));
+    count_launch(H->apply_nodes);
     prof_end(tk, PR_APPLY, st, H->bytes_apply, 0.0);
   }
-  return LS_OK;
+  return check_launch("hbs_apply");
 }
 
 }  // namespace ls

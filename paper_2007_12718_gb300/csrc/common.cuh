@@ -119,7 +119,7 @@ __device__ __forceinline__ bool grid_sync(const GridSync& g, unsigned int nblock
 }
 
 // Counter of kernel launches made by this library (reported by ls_kernel_launches).
-void count_launch();
+void count_launch(long long n = 1);
 
 }  // namespace ls
 

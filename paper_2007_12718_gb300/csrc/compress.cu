@@ -42,45 +42,83 @@ struct IdSlot {
 };
 
 // Column-pivoted QR ID of the candidate-major matrix A (m candidates, each a
-// length-p vector at A + c*p).  Outputs: piv[0..k), rank[0] = k, and U (m x k,
-// row-major, stride k).  Rm (kmax x m) holds R; nrm (m) residual norms^2; sel
-// (m) the step at which a candidate was chosen (-1 while active).
-template <class R>
-__global__ void __launch_bounds__(256) cpqr_id_kernel(cx<R>* __restrict__ A, int m, int p, int kmax, double eps,
-                                                      cx<R>* __restrict__ Rm, R* __restrict__ nrm,
-                                                      int* __restrict__ sel, IdSlot* __restrict__ slots,
+// length-p vector at A + c*p).  Block b owns candidates [c0, c0 + mc) and keeps
+// their residual vectors in shared memory when they fit (else in the global
+// working copy Aw).  Per pivot step: every block publishes its best local
+// candidate (norm, index, vector) in a double-buffered slot, one bounded grid
+// barrier, every block picks the global winner from the slots and projects its
+// direction out of its own candidates (classical Gram-Schmidt, twice), the
+// threads of a block sweeping the vector entries for all its candidates at
+// once.  Outputs: piv[0..k), rank[0] = k, U (m x k, row-major, stride k).
+template <class R, int MC>
+__global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ A, int m, int p, int kmax,
+                                                      double eps, int use_smem, cx<R>* __restrict__ Aw,
+                                                      cx<R>* __restrict__ Rm, int* __restrict__ sel,
+                                                      IdSlot* __restrict__ slots, cx<R>* __restrict__ pslots,
                                                       int* __restrict__ piv, int* __restrict__ rank,
                                                       cx<R>* __restrict__ U, GridSync gs) {
   extern __shared__ unsigned char smraw[];
-  cx<R>* tsm = reinterpret_cast<cx<R>*>(smraw);  // per-warp back-substitution vectors
+  cx<R>* pvec = reinterpret_cast<cx<R>*>(smraw);  // p
   const int nblk = gridDim.x, blk = blockIdx.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
   const int per = (m + nblk - 1) / nblk;
-  const int c0 = blk * per, c1 = min(m, c0 + per);
-
-  // initial norms
-  for (int c = c0 + warp; c < c1; c += nwarp) {
-    const cx<R>* a = A + (long long)c * p;
-    R s = 0;
-    for (int i = lane; i < p; i += 32) s += abs2(a[i]);
-    s = warp_sum_r(s);
-    if (lane == 0) {
-      nrm[c] = s;
-      sel[c] = -1;
-    }
-  }
+  const int c0 = min(m, blk * per), c1 = min(m, c0 + per), mc = c1 - c0;
+  cx<R>* cand = use_smem ? pvec + p : Aw + (long long)c0 * p;
+  __shared__ cx<R> red[8][MC];
+  __shared__ cx<R> s_d[MC], s_d1[MC], s_d2[MC];
+  __shared__ R s_nrm[MC];
+  __shared__ int s_sel[MC];
   __shared__ double s_best, s_total, s_tol2;
-  __shared__ int s_idx, s_stop, s_k;
+  __shared__ int s_idx, s_bw, s_stop, s_lbest;
+
+  for (long long t = tid; t < (long long)mc * p; t += blockDim.x) cand[t] = A[(long long)c0 * p + t];
+  __syncthreads();
+
+  // block-wide sum of per-thread partials acc[0..mc) into s_d
+  auto block_reduce = [&](cx<R>* acc) {
+#pragma unroll
+    for (int c = 0; c < MC; ++c) {
+      if (c < mc) {
+        cx<R> v = warp_sum(acc[c]);
+        if (lane == 0) red[warp][c] = v;
+      }
+    }
+    __syncthreads();
+    if (tid < mc) {
+      cx<R> v = mk<R>(0, 0);
+      for (int w = 0; w < nwarp; ++w) v = v + red[w][tid];
+      s_d[tid] = v;
+    }
+    __syncthreads();
+  };
+
+  {
+    cx<R> acc[MC];
+#pragma unroll
+    for (int c = 0; c < MC; ++c) acc[c] = mk<R>(0, 0);
+    for (int i = tid; i < p; i += blockDim.x) {
+#pragma unroll
+      for (int c = 0; c < MC; ++c)
+        if (c < mc) acc[c].re += abs2(cand[(long long)c * p + i]);
+    }
+    block_reduce(acc);
+    if (tid < mc) {
+      s_nrm[tid] = s_d[tid].re;
+      s_sel[tid] = -1;
+      sel[c0 + tid] = -1;
+    }
+    __syncthreads();
+  }
+
   int k = 0;
   for (int j = 0;; ++j) {
-    // local reduction over this block's active candidates
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    const int par = j & 1;
+    if (tid == 0) {
       double best = -1.0, total = 0.0;
       int idx = -1;
-      for (int c = c0; c < c1; ++c) {
-        if (sel[c] != -1) continue;
-        double v = (double)nrm[c];
+      for (int c = 0; c < mc; ++c) {
+        if (s_sel[c] != -1) continue;
+        double v = (double)s_nrm[c];
         total += v;
         if (v > best) {
           best = v;
@@ -90,26 +128,35 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(cx<R>* __restrict__ A, int
       IdSlot sl;
       sl.best = best;
       sl.total = total;
-      sl.idx = idx;
+      sl.idx = idx < 0 ? -1 : c0 + idx;
       sl.pad = 0;
-      slots[(j & 1) * nblk + blk] = sl;
+      slots[par * nblk + blk] = sl;
+      s_lbest = idx;
+    }
+    __syncthreads();
+    if (s_lbest >= 0) {
+      cx<R>* dst = pslots + ((long long)par * nblk + blk) * p;
+      const cx<R>* src = cand + (long long)s_lbest * p;
+      for (int i = tid; i < p; i += blockDim.x) dst[i] = src[i];
     }
     if (!grid_sync(gs, nblk)) return;
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       double best = -1.0, total = 0.0;
-      int idx = -1;
+      int idx = -1, bw = -1;
       for (int b = 0; b < nblk; ++b) {
-        IdSlot sl = slots[(j & 1) * nblk + b];
+        IdSlot sl = slots[par * nblk + b];
         total += sl.total;
         if (sl.idx >= 0 && (sl.best > best || (sl.best == best && sl.idx < idx))) {
           best = sl.best;
           idx = sl.idx;
+          bw = b;
         }
       }
       if (j == 0) s_tol2 = eps * eps * total;
       s_best = best;
       s_total = total;
       s_idx = idx;
+      s_bw = bw;
       s_stop = (j == kmax) || idx < 0 || best <= 0.0 || total <= s_tol2;
     }
     __syncthreads();
@@ -119,49 +166,81 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(cx<R>* __restrict__ A, int
     }
     const int pv = s_idx;
     const R nu = (R)sqrt(s_best);
-    const R inu = R(1) / nu;
-    const cx<R>* ap = A + (long long)pv * p;
-    if (blk == 0 && threadIdx.x == 0) {
+    const R inu2 = R(1) / (nu * nu);
+    {
+      const cx<R>* src = pslots + ((long long)par * nblk + s_bw) * p;
+      for (int i = tid; i < p; i += blockDim.x) pvec[i] = src[i];
+    }
+    if (blk == s_bw && tid == 0) {
+      s_sel[pv - c0] = j;
+      sel[pv] = j;
       piv[j] = pv;
       Rm[(long long)j * m + pv] = mk<R>(nu, R(0));
     }
-    if (pv >= c0 && pv < c1 && threadIdx.x == 0) sel[pv] = j;
-    // project the pivot direction q = a_pv / nu out of every active candidate (twice)
-    for (int c = c0 + warp; c < c1; c += nwarp) {
-      if (c == pv || sel[c] != -1) continue;
-      cx<R>* a = A + (long long)c * p;
-      cx<R> rsum = mk<R>(0, 0);
-      for (int pass = 0; pass < 2; ++pass) {
-        cx<R> d = mk<R>(0, 0);
-        for (int i = lane; i < p; i += 32) fmac_(d, ap[i], a[i]);
-        d = warp_sum(d);
-        d = scale(d, inu * inu);  // coefficient of a_pv
-        for (int i = lane; i < p; i += 32) {
-          cx<R> v = a[i];
-          cx<R> q = ap[i];
+    __syncthreads();
+    bool act[MC];
+#pragma unroll
+    for (int c = 0; c < MC; ++c) act[c] = (c < mc) && s_sel[c] == -1;
+    cx<R> acc[MC];
+    // pass 1: d1 = pvec^H a / nu^2
+#pragma unroll
+    for (int c = 0; c < MC; ++c) acc[c] = mk<R>(0, 0);
+    for (int i = tid; i < p; i += blockDim.x) {
+      cx<R> q = pvec[i];
+#pragma unroll
+      for (int c = 0; c < MC; ++c)
+        if (act[c]) fmac_(acc[c], q, cand[(long long)c * p + i]);
+    }
+    block_reduce(acc);
+    if (tid < mc) s_d1[tid] = scale(s_d[tid], inu2);
+    __syncthreads();
+    // pass 2: a -= q d1, and d2 = pvec^H a / nu^2 on the updated vector
+#pragma unroll
+    for (int c = 0; c < MC; ++c) acc[c] = mk<R>(0, 0);
+    for (int i = tid; i < p; i += blockDim.x) {
+      cx<R> q = pvec[i];
+#pragma unroll
+      for (int c = 0; c < MC; ++c)
+        if (act[c]) {
+          cx<R> v = cand[(long long)c * p + i], d = s_d1[c];
           v.re -= q.re * d.re - q.im * d.im;
           v.im -= q.re * d.im + q.im * d.re;
-          a[i] = v;
+          cand[(long long)c * p + i] = v;
+          fmac_(acc[c], q, v);
         }
-        rsum = rsum + scale(d, nu);  // R(j, c) = q^H a = (a_pv^H a) / nu
-        __syncwarp();
-      }
-      R s = 0;
-      for (int i = lane; i < p; i += 32) s += abs2(a[i]);
-      s = warp_sum_r(s);
-      if (lane == 0) {
-        nrm[c] = s;
-        Rm[(long long)j * m + c] = rsum;
-      }
     }
+    block_reduce(acc);
+    if (tid < mc) s_d2[tid] = scale(s_d[tid], inu2);
+    __syncthreads();
+    // pass 3: a -= q d2, residual norms
+#pragma unroll
+    for (int c = 0; c < MC; ++c) acc[c] = mk<R>(0, 0);
+    for (int i = tid; i < p; i += blockDim.x) {
+      cx<R> q = pvec[i];
+#pragma unroll
+      for (int c = 0; c < MC; ++c)
+        if (act[c]) {
+          cx<R> v = cand[(long long)c * p + i], d = s_d2[c];
+          v.re -= q.re * d.re - q.im * d.im;
+          v.im -= q.re * d.im + q.im * d.re;
+          cand[(long long)c * p + i] = v;
+          acc[c].re += abs2(v);
+        }
+    }
+    block_reduce(acc);
+    if (tid < mc && act[tid]) {
+      s_nrm[tid] = s_d[tid].re;
+      Rm[(long long)j * m + c0 + tid] = scale(s_d1[tid] + s_d2[tid], nu);  // R(j, c) = q^H a = (a_pv^H a) / nu
+    }
+    __syncthreads();
   }
-  if (blk == 0 && threadIdx.x == 0) rank[0] = k;
-  if (threadIdx.x == 0) s_k = k;
+  if (blk == 0 && tid == 0) rank[0] = k;
   __syncthreads();
-  // U rows: identity on the skeleton, T = R11^-1 R12 on the rest (one warp per candidate)
-  cx<R>* t = tsm + warp * kmax;
+  // U rows: identity on the skeleton, T = R11^-1 R12 on the rest (one warp per candidate);
+  // the per-warp solution vectors reuse the shared memory of the candidates.
+  cx<R>* t = pvec + (long long)warp * kmax;
   for (int c = c0 + warp; c < c1; c += nwarp) {
-    int sc = sel[c];
+    int sc = s_sel[c - c0];
     if (sc >= 0) {
       for (int a = lane; a < k; a += 32) U[(long long)c * k + a] = mk<R>(a == sc ? R(1) : R(0), R(0));
       continue;
@@ -207,18 +286,7 @@ template <class R>
 int compress_t(ls_handle* H, cudaStream_t st) {
   const int L = H->L, s = H->s, w = H->ring;
   int rc;
-  // workspace sizes: the largest level
   std::vector<int> rows_x, rows_y;
-  size_t max_mp = 0, max_m = 0;
-  {
-    // sizes of every level (ranks unknown: bound m by the box points)
-    for (int l = L; l >= 1; --l) {
-      size_t m = (size_t)H->lev[l].w * H->lev[l].h;
-      size_t p = (size_t)(H->lev[l].w + 2 * w) * (H->lev[l].h + 2 * w) - (size_t)H->lev[l].w * H->lev[l].h;
-      max_m = std::max(max_m, m);
-      (void)p;
-    }
-  }
   int* dint = nullptr;
   for (int l = L; l >= 1; --l) {
     LevelData& lv = H->lev[l];
@@ -261,37 +329,66 @@ int compress_t(ls_handle* H, cudaStream_t st) {
     if (dint) cudaFree(dint);
     dint = nullptr;
     if ((rc = dalloc((void**)&dint, sizeof(int) * (2 * m + 2 * p + 8)))) return rc;
-    size_t need = sizeof(cx<R>) * ((size_t)m * p + (size_t)kmax * m + (size_t)m * kmax) + sizeof(R) * m +
-                  sizeof(int) * (2 * m + 8) + sizeof(IdSlot) * 2 * 1024 + 256 * 8;
+    // blocks and candidates per block
+    int nblk = std::max(1, std::min(H->nsm, (m + 1) / 2));
+    int per = (m + nblk - 1) / nblk;
+    int MC = per <= 8 ? 8 : per <= 16 ? 16 : 32;
+    if (per > 32) {
+      per = 32;
+      nblk = (m + per - 1) / per;
+      MC = 32;
+    }
+    size_t loop_smem = sizeof(cx<R>) * ((size_t)p + (size_t)per * p);
+    size_t tail_smem = sizeof(cx<R>) * (size_t)8 * kmax;
+    int use_smem = loop_smem <= 200 * 1024;
+    size_t smem = std::max(use_smem ? loop_smem : sizeof(cx<R>) * (size_t)p, tail_smem);
+    if (smem > 220 * 1024) {
+      set_last_error_text("proxy block too large for the ID kernel");
+      return LS_EINVAL;
+    }
+    size_t need = sizeof(cx<R>) * ((size_t)m * p * (use_smem ? 1 : 2) + (size_t)kmax * m + (size_t)m * kmax +
+                                   (size_t)2 * nblk * p) +
+                  sizeof(int) * (2 * m + 8) + sizeof(IdSlot) * 2 * (nblk + 1) + 1024;
     char* wsp = nullptr;
     if ((rc = dalloc((void**)&wsp, need))) return rc;
-    cx<R>* A = reinterpret_cast<cx<R>*>(wsp);
-    cx<R>* Rm = A + (size_t)m * p;
-    cx<R>* Ut = Rm + (size_t)kmax * m;
-    R* nrm = reinterpret_cast<R*>(Ut + (size_t)m * kmax);
-    int* sel = reinterpret_cast<int*>(nrm + m);
-    int* piv = sel + m;
-    int* rank = piv + m;
-    IdSlot* slots = reinterpret_cast<IdSlot*>(((uintptr_t)(rank + 8) + 15) & ~(uintptr_t)15);
+    auto carve = [&](size_t bytes) {
+      char* r = wsp;
+      wsp += (bytes + 255) & ~(size_t)255;
+      return r;
+    };
+    char* wbase = wsp;
+    cx<R>* A = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)m * p));
+    cx<R>* Aw = use_smem ? nullptr : reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)m * p));
+    cx<R>* Rm = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)kmax * m));
+    cx<R>* Ut = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)m * kmax));
+    cx<R>* pslots = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)2 * nblk * p));
+    int* sel = reinterpret_cast<int*>(carve(sizeof(int) * m));
+    int* piv = reinterpret_cast<int*>(carve(sizeof(int) * m));
+    int* rank = reinterpret_cast<int*>(carve(sizeof(int) * 8));
+    IdSlot* slots = reinterpret_cast<IdSlot*>(carve(sizeof(IdSlot) * 2 * (nblk + 1)));
+    wsp = wbase;
     if ((rc = upload_block<R>(rows_x, rows_y, px, py, A, dint, st, H->ks_prec))) return rc;
-    // cooperative CPQR
-    int nblk = std::max(1, std::min(H->nsm, (m + 1) / 2));
-    size_t smem = sizeof(cx<R>) * (size_t)kmax * 8;
-    LS_CUDA_TRY(cudaFuncSetAttribute(cpqr_id_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const void* kfn = MC == 8 ? (const void*)cpqr_id_kernel<R, 8>
+                              : MC == 16 ? (const void*)cpqr_id_kernel<R, 16> : (const void*)cpqr_id_kernel<R, 32>;
+    LS_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cpqr_id_kernel<R>, 256, smem));
-    if (per_sm < 1) return LS_EINVAL;
-    nblk = std::min(nblk, per_sm * H->nsm);
+    LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, smem));
+    if (per_sm < 1 || nblk > per_sm * H->nsm) {
+      set_last_error_text("ID kernel cannot be co-resident");
+      return LS_EINVAL;
+    }
     LS_CUDA_TRY(cudaMemsetAsync(H->sync_buf, 0, 64, st));
     GridSync gs;
     gs.count = reinterpret_cast<unsigned*>(H->sync_buf);
     gs.gen = reinterpret_cast<unsigned*>(H->sync_buf) + 1;
     gs.abort = H->sync_buf + 2;
     double eps = H->tol;
-    void* args[] = {&A, (void*)&m, (void*)&p, (void*)&kmax, &eps, &Rm, &nrm, &sel, &slots, &piv, &rank, &Ut, &gs};
+    const cx<R>* Ac = A;
+    void* args[] = {&Ac, (void*)&m, (void*)&p, (void*)&kmax, &eps, &use_smem, &Aw, &Rm, &sel, &slots, &pslots,
+                    &piv, &rank, &Ut, &gs};
     int tk = prof_begin(st);
     count_launch();
-    LS_CUDA_TRY(cudaLaunchCooperativeKernel((void*)cpqr_id_kernel<R>, dim3(nblk), dim3(256), args, smem, st));
+    LS_CUDA_TRY(cudaLaunchCooperativeKernel(kfn, dim3(nblk), dim3(256), args, smem, st));
     int k = 0, abort_flag = 0;
     LS_CUDA_TRY(cudaMemcpyAsync(&k, rank, sizeof(int), cudaMemcpyDeviceToHost, st));
     LS_CUDA_TRY(cudaMemcpyAsync(&abort_flag, H->sync_buf + 2, sizeof(int), cudaMemcpyDeviceToHost, st));

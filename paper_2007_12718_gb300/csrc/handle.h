@@ -43,6 +43,9 @@ struct ls_handle {
   size_t work_bytes = 0;
   int* sync_buf = nullptr;      // grid-barrier counters + error flags
   int* d_err = nullptr;         // device status word (LS_ESINGULAR / LS_ETIMEOUT)
+  cudaGraphExec_t apply_exec = nullptr;  // Algorithm 2 recorded as a CUDA graph
+  ls::z64** slots = nullptr;    // device-side input/output pointers of the apply graph
+  long long apply_nodes = 0;    // kernels in the apply graph
   double flops_build = 0, flops_compress = 0, bytes_apply = 0, factor_bytes = 0;
 
   // GMRES workspace (Sec. 5)
@@ -70,6 +73,7 @@ int gmres_solve(ls_handle* H, const z64* f, z64* sigma, int nrhs, ls_solve_info*
 
 // device allocation that records failures as LS_ENOMEM
 int dalloc(void** p, size_t bytes);
+void set_last_error_text(const char* msg);
 int check_launch(const char* what);
 
 }  // namespace ls

@@ -103,8 +103,10 @@ void ls_set_last_cuda_error(cudaError_t e, const char* what, const char* file, i
 
 namespace ls {
 
+void set_last_error_text(const char* msg) { set_error(msg); }
+
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 int dalloc(void** p, size_t bytes) {
   *p = nullptr;
@@ -183,6 +185,8 @@ void ls_free(ls_handle* H) {
   f(H->sync_buf);
   f(H->d_err);
   f(H->gm);
+  f(H->slots);
+  if (H->apply_exec) cudaGraphExecDestroy(H->apply_exec);
   delete H;
 }
 
