@@ -301,23 +301,27 @@ __global__ void __launch_bounds__(256) inverse_smem_kernel(cx<R>* X, int n, int 
 }
 
 // Blocked Gauss-Jordan inversion, panel step (one block per matrix).  The nb
-// panel columns [k0, k0+nb) of all n rows are loaded to shared memory and
-// eliminated in place with partial row pivoting over the rows not yet used as
-// pivots; the row interchanges are recorded in piv and applied to the other
-// columns by gj_swap_extract_kernel.  On exit the panel holds the columns J of
-// the accumulated transform E (rows J: the pivot block's inverse).
+// <= 32 panel columns [k0, k0+nb) of all n rows are loaded to shared memory
+// and eliminated in place with partial row pivoting over the rows not yet used
+// as pivots.  Warp w owns rows i = w (mod 8), lane c owns panel column c.  On
+// exit the panel holds the columns J of the accumulated transform (rows J:
+// the pivot block's inverse), piv the row interchanges, and perm (2*nb
+// (destination, source) row pairs, -1 terminated) their net permutation for
+// gj_swap_extract_kernel.
 template <class R>
 __global__ void __launch_bounds__(256) gj_panel_kernel(cx<R>* X, int n, int lda, long long sX, int k0, int nb,
-                                                       int* piv, int* err) {
+                                                       int* piv, int* perm, int* err) {
   extern __shared__ unsigned char smraw[];
   cx<R>* pn = reinterpret_cast<cx<R>*>(smraw);  // n x nb
-  cx<R>* col = pn + (size_t)n * nb;             // n
+  __shared__ cx<R> prow[32];
   __shared__ R s_v[8];
   __shared__ int s_i[8];
-  __shared__ int s_p;
+  __shared__ int s_pos[64], s_org[64];
   const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lmask = nb >= 32 ? 0xffffffffu : ((1u << nb) - 1u);
   cx<R>* M = X + b * sX;
-  for (int t = tid; t < n * nb; t += blockDim.x) pn[t] = M[(long long)(t / nb) * lda + k0 + t % nb];
+  for (int i = warp; i < n; i += 8)
+    if (lane < nb) pn[i * nb + lane] = M[(long long)i * lda + k0 + lane];
   __syncthreads();
   for (int jj = 0; jj < nb; ++jj) {
     const int j = k0 + jj;
@@ -343,74 +347,96 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(cx<R>* X, int n, int lda,
       s_i[warp] = bi;
     }
     __syncthreads();
-    if (tid == 0) {
-      R bb = s_v[0];
-      int ii = s_i[0];
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-        if (s_v[w] > bb || (s_v[w] == bb && s_i[w] < ii)) {
-          bb = s_v[w];
-          ii = s_i[w];
-        }
-      s_p = (bb > R(0)) ? ii : -1;
-      piv[(long long)b * n + j] = ii < n ? ii : j;
-      if (!(bb > R(0))) atomicExch(err, LS_ESINGULAR);
+    best = s_v[0];
+    bi = s_i[0];
+    for (int w = 1; w < 8; ++w)
+      if (s_v[w] > best || (s_v[w] == best && s_i[w] < bi)) {
+        best = s_v[w];
+        bi = s_i[w];
+      }
+    if (!(best > R(0))) {
+      if (tid == 0) atomicExch(err, LS_ESINGULAR);
+      return;  // every thread takes this branch
+    }
+    const int p = bi;
+    const cx<R> d = inv(pn[p * nb + jj]);
+    if (tid == 0) piv[(long long)b * n + j] = p;
+    if (warp == 0 && lane < nb) {
+      cx<R> a = pn[j * nb + lane], bv = pn[p * nb + lane];
+      prow[lane] = (lane == jj) ? d : bv * d;
+      if (p != j) pn[p * nb + lane] = a;
     }
     __syncthreads();
-    const int p = s_p;
-    if (p < 0) return;
-    if (p != j)
-      for (int c = tid; c < nb; c += blockDim.x) {
-        cx<R> t = pn[j * nb + c];
-        pn[j * nb + c] = pn[p * nb + c];
-        pn[p * nb + c] = t;
+    for (int i = warp; i < n; i += 8) {
+      if (lane >= nb) continue;
+      if (i == j) {
+        pn[i * nb + lane] = prow[lane];
+        continue;
       }
-    __syncthreads();
-    for (int i = tid; i < n; i += blockDim.x) col[i] = pn[i * nb + jj];
-    __syncthreads();
-    const cx<R> d = inv(col[j]);
-    for (int c = tid; c < nb; c += blockDim.x) pn[j * nb + c] = (c == jj) ? d : pn[j * nb + c] * d;
-    __syncthreads();
-    for (int t = tid; t < n * nb; t += blockDim.x) {
-      int i = t / nb, c = t % nb;
-      if (i == j) continue;
-      cx<R> f = col[i];
-      if (c == jj) {
-        pn[t] = mk<R>(-(f.re * d.re - f.im * d.im), -(f.re * d.im + f.im * d.re));
+      cx<R> f = pn[i * nb + jj];
+      __syncwarp(lmask);
+      if (lane == jj) {
+        pn[i * nb + lane] = mk<R>(-(f.re * d.re - f.im * d.im), -(f.re * d.im + f.im * d.re));
       } else {
-        cx<R> r = pn[j * nb + c], v = pn[t];
+        cx<R> r = prow[lane], v = pn[i * nb + lane];
         v.re -= f.re * r.re - f.im * r.im;
         v.im -= f.re * r.im + f.im * r.re;
-        pn[t] = v;
+        pn[i * nb + lane] = v;
       }
     }
     __syncthreads();
   }
-  for (int t = tid; t < n * nb; t += blockDim.x) M[(long long)(t / nb) * lda + k0 + t % nb] = pn[t];
+  for (int i = warp; i < n; i += 8)
+    if (lane < nb) M[(long long)i * lda + k0 + lane] = pn[i * nb + lane];
+  if (tid == 0) {  // net permutation of the panel's interchanges
+    int cnt = 0;
+    for (int jj = 0; jj < nb; ++jj) {
+      int j = k0 + jj, p = piv[(long long)b * n + j];
+      if (p == j) continue;
+      int ij = -1, ip = -1;
+      for (int t = 0; t < cnt; ++t) {
+        if (s_pos[t] == j) ij = t;
+        if (s_pos[t] == p) ip = t;
+      }
+      if (ij < 0) {
+        s_pos[cnt] = j;
+        s_org[cnt] = j;
+        ij = cnt++;
+      }
+      if (ip < 0) {
+        s_pos[cnt] = p;
+        s_org[cnt] = p;
+        ip = cnt++;
+      }
+      int t = s_org[ij];
+      s_org[ij] = s_org[ip];
+      s_org[ip] = t;
+    }
+    int* pr = perm + (long long)b * 2 * 64;
+    for (int t = 0; t < cnt; ++t) {
+      pr[2 * t] = s_pos[t];
+      pr[2 * t + 1] = s_org[t];
+    }
+    if (cnt < 64) pr[2 * cnt] = -1;
+  }
 }
 
-// For every column c outside the panel: apply the panel's row interchanges in
-// order, move rows J = [k0, k0+nb) to Mb (nb x n, zero in the panel columns)
-// and zero them in X, so that X[:, c] += Panel * Mb[:, c] completes the step.
+// For every column c outside the panel: apply the panel's net row
+// permutation, move rows J = [k0, k0+nb) to Mb (nb x n) and zero them in X, so
+// that X[:, c] += Panel * Mb[:, c] completes the step.
 template <class R>
-__global__ void gj_swap_extract_kernel(cx<R>* X, int n, int lda, long long sX, int k0, int nb, const int* piv,
+__global__ void gj_swap_extract_kernel(cx<R>* X, int n, int lda, long long sX, int k0, int nb, const int* perm,
                                        cx<R>* Mb, long long sM) {
   const int b = blockIdx.y;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
+  if (c >= n || (c >= k0 && c < k0 + nb)) return;
   cx<R>* M = X + b * sX;
   cx<R>* out = Mb + b * sM;
-  if (c >= k0 && c < k0 + nb) {
-    for (int jj = 0; jj < nb; ++jj) out[(long long)jj * n + c] = mk<R>(0, 0);
-    return;
-  }
-  for (int jj = 0; jj < nb; ++jj) {
-    int j = k0 + jj, p = piv[(long long)b * n + j];
-    if (p != j) {
-      cx<R> t = M[(long long)j * lda + c];
-      M[(long long)j * lda + c] = M[(long long)p * lda + c];
-      M[(long long)p * lda + c] = t;
-    }
-  }
+  const int* pr = perm + (long long)b * 2 * 64;
+  cx<R> vals[64];
+  int cnt = 0;
+  for (; cnt < 64 && pr[2 * cnt] >= 0; ++cnt) vals[cnt] = M[(long long)pr[2 * cnt + 1] * lda + c];
+  for (int t = 0; t < cnt; ++t) M[(long long)pr[2 * t] * lda + c] = vals[t];
   for (int jj = 0; jj < nb; ++jj) {
     out[(long long)jj * n + c] = M[(long long)(k0 + jj) * lda + c];
     M[(long long)(k0 + jj) * lda + c] = mk<R>(0, 0);
@@ -470,23 +496,24 @@ int invert_batch(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int P, vo
     inverse_smem_kernel<R><<<P, 256, smem_small, st>>>(X, n, lda, sX, H->d_err);
     return check_launch("inverse_smem");
   }
-  int nb = sizeof(R) == 4 ? 32 : 16;
-  while (nb > 4 && sizeof(cx<R>) * ((size_t)n * nb + n) > 200 * 1024) nb >>= 1;
-  const size_t smem_panel = sizeof(cx<R>) * ((size_t)n * nb + n);
+  int nb = 32;
+  while (nb > 4 && sizeof(cx<R>) * (size_t)n * nb > 200 * 1024) nb >>= 1;
+  const size_t smem_panel = sizeof(cx<R>) * (size_t)n * nb;
   if (smem_panel > 200 * 1024) {
     set_last_error_text("merge matrix too large for the panel kernel");
     return LS_EINVAL;
   }
   cx<R>* Mb = reinterpret_cast<cx<R>*>(scratch);
   int* piv = reinterpret_cast<int*>(Mb + (size_t)P * nb * n);
-  if (sizeof(cx<R>) * (size_t)P * nb * n + sizeof(int) * (size_t)P * n > scratch_bytes) return LS_ENOMEM;
+  int* perm = piv + (size_t)P * n;
+  if (sizeof(cx<R>) * (size_t)P * nb * n + sizeof(int) * (size_t)P * (n + 128) > scratch_bytes) return LS_ENOMEM;
   LS_CUDA_TRY(cudaFuncSetAttribute(gj_panel_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_panel));
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int w = std::min(nb, n - k0);
     count_launch();
-    gj_panel_kernel<R><<<P, 256, smem_panel, st>>>(X, n, lda, sX, k0, w, piv, H->d_err);
+    gj_panel_kernel<R><<<P, 256, smem_panel, st>>>(X, n, lda, sX, k0, w, piv, perm, H->d_err);
     count_launch();
-    gj_swap_extract_kernel<R><<<dim3((n + 127) / 128, P), 128, 0, st>>>(X, n, lda, sX, k0, w, piv, Mb,
+    gj_swap_extract_kernel<R><<<dim3((n + 127) / 128, P), 128, 0, st>>>(X, n, lda, sX, k0, w, perm, Mb,
                                                                        (long long)w * n);
     // X[:, c] += Panel (n x w, columns k0.. of X) * Mb[:, c] for the columns c outside the panel
     gemm<R>(st, false, false, n, k0, w, one<R>(), X + k0, lda, sX, Mb, n, (long long)w * n, one<R>(), X, lda, sX, P);

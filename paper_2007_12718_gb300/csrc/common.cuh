@@ -78,38 +78,34 @@ __device__ __forceinline__ T warp_sum_r(T v) {
 }
 
 // Grid-wide barrier for kernels launched with cudaLaunchCooperativeKernel
-// (all blocks co-resident).  Every spin is bounded: after `kSpinLimit` polls
-// the block raises *abort and the barrier returns false; every later barrier
-// returns false at once, so the kernel unwinds without hanging.
+// (all blocks co-resident).  The arrival counter only grows: barrier number
+// e (counted per block from 1) completes when it reaches e * nblocks.  Every
+// spin is bounded: after kSpinLimit polls the block raises *abort and the
+// barrier returns false; every later barrier returns false at once, so the
+// kernel unwinds without hanging.  count and abort must be zero at launch.
 struct GridSync {
-  unsigned int* count;   // arrival counter, starts at 0
-  unsigned int* gen;     // generation, starts at any value
+  unsigned int* count;   // arrival counter
+  unsigned int* gen;     // unused (kept for layout)
   int* abort;            // set to 1 by a block that timed out
 };
 
-static constexpr long long kSpinLimit = 20000000LL;  // ~ seconds of polling
+static constexpr long long kSpinLimit = 20000000LL;  // ~ a second of polling
 
-__device__ __forceinline__ bool grid_sync(const GridSync& g, unsigned int nblocks) {
+__device__ __forceinline__ bool grid_sync(const GridSync& g, unsigned int nblocks, unsigned int& epoch) {
   __shared__ int ok;
   __syncthreads();
+  ++epoch;
   if (threadIdx.x == 0) {
     ok = 1;
-    volatile unsigned int* vgen = g.gen;
+    volatile unsigned int* vc = g.count;
     volatile int* vab = g.abort;
-    unsigned int my = *vgen;
     __threadfence();
-    unsigned int arrived = atomicAdd(g.count, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(g.count, 0u);
-      __threadfence();
-      atomicAdd(g.gen, 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == my) {
-        if (*vab) { ok = 0; break; }
-        if (++spins > kSpinLimit) { atomicExch(g.abort, 1); ok = 0; break; }
-        __nanosleep(32);
-      }
+    atomicAdd(g.count, 1u);
+    const unsigned int target = epoch * nblocks;
+    long long spins = 0;
+    while ((int)(*vc - target) < 0) {
+      if (*vab) { ok = 0; break; }
+      if (++spins > kSpinLimit) { atomicExch(g.abort, 1); ok = 0; break; }
     }
     __threadfence();
     if (*vab) ok = 0;

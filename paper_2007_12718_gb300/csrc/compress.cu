@@ -45,12 +45,12 @@ struct IdSlot {
 // length-p vector at A + c*p).  Block b owns candidates [c0, c0 + mc) and keeps
 // their residual vectors in shared memory when they fit (else in the global
 // working copy Aw).  Per pivot step: every block publishes its best local
-// candidate (norm, index, vector) in a double-buffered slot, one bounded grid
-// barrier, every block picks the global winner from the slots and projects its
-// direction out of its own candidates (classical Gram-Schmidt, twice), the
-// threads of a block sweeping the vector entries for all its candidates at
-// once.  Outputs: piv[0..k), rank[0] = k, U (m x k, row-major, stride k).
-template <class R, int MC>
+// candidate (residual norm, index, vector) in a double-buffered slot; one
+// bounded grid barrier; every block reduces the slots in parallel, fetches
+// the winning vector q and projects it out of its own candidates (one warp
+// per candidate: a_c -= q (q^H a_c) / |q|^2, then the exact new norm).
+// Outputs: piv[0..k), rank[0] = k, U (m x k, row-major, stride k).
+template <class R>
 __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ A, int m, int p, int kmax,
                                                       double eps, int use_smem, cx<R>* __restrict__ Aw,
                                                       cx<R>* __restrict__ Rm, int* __restrict__ sel,
@@ -64,59 +64,33 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
   const int per = (m + nblk - 1) / nblk;
   const int c0 = min(m, blk * per), c1 = min(m, c0 + per), mc = c1 - c0;
   cx<R>* cand = use_smem ? pvec + p : Aw + (long long)c0 * p;
-  __shared__ cx<R> red[8][MC];
-  __shared__ cx<R> s_d[MC], s_d1[MC], s_d2[MC];
-  __shared__ R s_nrm[MC];
-  __shared__ int s_sel[MC];
-  __shared__ double s_best, s_total, s_tol2;
+  __shared__ R s_nrm[64];
+  __shared__ int s_sel[64];
+  __shared__ double s_best, s_tol2;
   __shared__ int s_idx, s_bw, s_stop, s_lbest;
+  unsigned int epoch = 0;
 
   for (long long t = tid; t < (long long)mc * p; t += blockDim.x) cand[t] = A[(long long)c0 * p + t];
   __syncthreads();
-
-  // block-wide sum of per-thread partials acc[0..mc) into s_d
-  auto block_reduce = [&](cx<R>* acc) {
-#pragma unroll
-    for (int c = 0; c < MC; ++c) {
-      if (c < mc) {
-        cx<R> v = warp_sum(acc[c]);
-        if (lane == 0) red[warp][c] = v;
-      }
+  for (int c = warp; c < mc; c += nwarp) {
+    R acc = 0;
+    for (int i = lane; i < p; i += 32) acc += abs2(cand[(long long)c * p + i]);
+    acc = warp_sum_r(acc);
+    if (lane == 0) {
+      s_nrm[c] = acc;
+      s_sel[c] = -1;
+      sel[c0 + c] = -1;
     }
-    __syncthreads();
-    if (tid < mc) {
-      cx<R> v = mk<R>(0, 0);
-      for (int w = 0; w < nwarp; ++w) v = v + red[w][tid];
-      s_d[tid] = v;
-    }
-    __syncthreads();
-  };
-
-  {
-    cx<R> acc[MC];
-#pragma unroll
-    for (int c = 0; c < MC; ++c) acc[c] = mk<R>(0, 0);
-    for (int i = tid; i < p; i += blockDim.x) {
-#pragma unroll
-      for (int c = 0; c < MC; ++c)
-        if (c < mc) acc[c].re += abs2(cand[(long long)c * p + i]);
-    }
-    block_reduce(acc);
-    if (tid < mc) {
-      s_nrm[tid] = s_d[tid].re;
-      s_sel[tid] = -1;
-      sel[c0 + tid] = -1;
-    }
-    __syncthreads();
   }
+  __syncthreads();
 
   int k = 0;
   for (int j = 0;; ++j) {
     const int par = j & 1;
-    if (tid == 0) {
+    if (warp == 0) {  // local best and total over this block's active candidates
       double best = -1.0, total = 0.0;
       int idx = -1;
-      for (int c = 0; c < mc; ++c) {
+      for (int c = lane; c < mc; c += 32) {
         if (s_sel[c] != -1) continue;
         double v = (double)s_nrm[c];
         total += v;
@@ -125,13 +99,24 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
           idx = c;
         }
       }
-      IdSlot sl;
-      sl.best = best;
-      sl.total = total;
-      sl.idx = idx < 0 ? -1 : c0 + idx;
-      sl.pad = 0;
-      slots[par * nblk + blk] = sl;
-      s_lbest = idx;
+      for (int o = 16; o; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        total += __shfl_xor_sync(0xffffffffu, total, o);
+        if (ob > best || (ob == best && oi >= 0 && (idx < 0 || oi < idx))) {
+          best = ob;
+          idx = oi;
+        }
+      }
+      if (lane == 0) {
+        IdSlot sl;
+        sl.best = best;
+        sl.total = total;
+        sl.idx = idx < 0 ? -1 : c0 + idx;
+        sl.pad = 0;
+        slots[par * nblk + blk] = sl;
+        s_lbest = idx;
+      }
     }
     __syncthreads();
     if (s_lbest >= 0) {
@@ -139,11 +124,11 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
       const cx<R>* src = cand + (long long)s_lbest * p;
       for (int i = tid; i < p; i += blockDim.x) dst[i] = src[i];
     }
-    if (!grid_sync(gs, nblk)) return;
-    if (tid == 0) {
+    if (!grid_sync(gs, nblk, epoch)) return;
+    if (warp == 0) {  // global winner: largest norm, lowest candidate index on ties
       double best = -1.0, total = 0.0;
       int idx = -1, bw = -1;
-      for (int b = 0; b < nblk; ++b) {
+      for (int b = lane; b < nblk; b += 32) {
         IdSlot sl = slots[par * nblk + b];
         total += sl.total;
         if (sl.idx >= 0 && (sl.best > best || (sl.best == best && sl.idx < idx))) {
@@ -152,12 +137,24 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
           bw = b;
         }
       }
-      if (j == 0) s_tol2 = eps * eps * total;
-      s_best = best;
-      s_total = total;
-      s_idx = idx;
-      s_bw = bw;
-      s_stop = (j == kmax) || idx < 0 || best <= 0.0 || total <= s_tol2;
+      for (int o = 16; o; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        int obw = __shfl_xor_sync(0xffffffffu, bw, o);
+        total += __shfl_xor_sync(0xffffffffu, total, o);
+        if (oi >= 0 && (ob > best || (ob == best && (idx < 0 || oi < idx)))) {
+          best = ob;
+          idx = oi;
+          bw = obw;
+        }
+      }
+      if (lane == 0) {
+        if (j == 0) s_tol2 = eps * eps * total;
+        s_best = best;
+        s_idx = idx;
+        s_bw = bw;
+        s_stop = (j == kmax) || idx < 0 || best <= 0.0 || total <= s_tol2;
+      }
     }
     __syncthreads();
     if (s_stop) {
@@ -166,7 +163,7 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
     }
     const int pv = s_idx;
     const R nu = (R)sqrt(s_best);
-    const R inu2 = R(1) / (nu * nu);
+    const R inu2 = R(1) / (R)s_best;
     {
       const cx<R>* src = pslots + ((long long)par * nblk + s_bw) * p;
       for (int i = tid; i < p; i += blockDim.x) pvec[i] = src[i];
@@ -178,59 +175,25 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
       Rm[(long long)j * m + pv] = mk<R>(nu, R(0));
     }
     __syncthreads();
-    bool act[MC];
-#pragma unroll
-    for (int c = 0; c < MC; ++c) act[c] = (c < mc) && s_sel[c] == -1;
-    cx<R> acc[MC];
-    // pass 1: d1 = pvec^H a / nu^2
-#pragma unroll
-    for (int c = 0; c < MC; ++c) acc[c] = mk<R>(0, 0);
-    for (int i = tid; i < p; i += blockDim.x) {
-      cx<R> q = pvec[i];
-#pragma unroll
-      for (int c = 0; c < MC; ++c)
-        if (act[c]) fmac_(acc[c], q, cand[(long long)c * p + i]);
-    }
-    block_reduce(acc);
-    if (tid < mc) s_d1[tid] = scale(s_d[tid], inu2);
-    __syncthreads();
-    // pass 2: a -= q d1, and d2 = pvec^H a / nu^2 on the updated vector
-#pragma unroll
-    for (int c = 0; c < MC; ++c) acc[c] = mk<R>(0, 0);
-    for (int i = tid; i < p; i += blockDim.x) {
-      cx<R> q = pvec[i];
-#pragma unroll
-      for (int c = 0; c < MC; ++c)
-        if (act[c]) {
-          cx<R> v = cand[(long long)c * p + i], d = s_d1[c];
-          v.re -= q.re * d.re - q.im * d.im;
-          v.im -= q.re * d.im + q.im * d.re;
-          cand[(long long)c * p + i] = v;
-          fmac_(acc[c], q, v);
-        }
-    }
-    block_reduce(acc);
-    if (tid < mc) s_d2[tid] = scale(s_d[tid], inu2);
-    __syncthreads();
-    // pass 3: a -= q d2, residual norms
-#pragma unroll
-    for (int c = 0; c < MC; ++c) acc[c] = mk<R>(0, 0);
-    for (int i = tid; i < p; i += blockDim.x) {
-      cx<R> q = pvec[i];
-#pragma unroll
-      for (int c = 0; c < MC; ++c)
-        if (act[c]) {
-          cx<R> v = cand[(long long)c * p + i], d = s_d2[c];
-          v.re -= q.re * d.re - q.im * d.im;
-          v.im -= q.re * d.im + q.im * d.re;
-          cand[(long long)c * p + i] = v;
-          acc[c].re += abs2(v);
-        }
-    }
-    block_reduce(acc);
-    if (tid < mc && act[tid]) {
-      s_nrm[tid] = s_d[tid].re;
-      Rm[(long long)j * m + c0 + tid] = scale(s_d1[tid] + s_d2[tid], nu);  // R(j, c) = q^H a = (a_pv^H a) / nu
+    for (int c = warp; c < mc; c += nwarp) {
+      if (s_sel[c] != -1) continue;
+      cx<R>* a = cand + (long long)c * p;
+      cx<R> d = mk<R>(0, 0);
+      for (int i = lane; i < p; i += 32) fmac_(d, pvec[i], a[i]);
+      d = scale(warp_sum(d), inu2);  // coefficient of the pivot vector
+      R nr = 0;
+      for (int i = lane; i < p; i += 32) {
+        cx<R> v = a[i], q = pvec[i];
+        v.re -= q.re * d.re - q.im * d.im;
+        v.im -= q.re * d.im + q.im * d.re;
+        a[i] = v;
+        nr += abs2(v);
+      }
+      nr = warp_sum_r(nr);
+      if (lane == 0) {
+        s_nrm[c] = nr;
+        Rm[(long long)j * m + c0 + c] = scale(d, nu);  // R(j, c) = q^H a = (a_pv^H a) / nu
+      }
     }
     __syncthreads();
   }
@@ -329,14 +292,12 @@ int compress_t(ls_handle* H, cudaStream_t st) {
     if (dint) cudaFree(dint);
     dint = nullptr;
     if ((rc = dalloc((void**)&dint, sizeof(int) * (2 * m + 2 * p + 8)))) return rc;
-    // blocks and candidates per block
+    // blocks and candidates per block (at most 64 per block)
     int nblk = std::max(1, std::min(H->nsm, (m + 1) / 2));
     int per = (m + nblk - 1) / nblk;
-    int MC = per <= 8 ? 8 : per <= 16 ? 16 : 32;
-    if (per > 32) {
-      per = 32;
+    if (per > 64) {
+      per = 64;
       nblk = (m + per - 1) / per;
-      MC = 32;
     }
     size_t loop_smem = sizeof(cx<R>) * ((size_t)p + (size_t)per * p);
     size_t tail_smem = sizeof(cx<R>) * (size_t)8 * kmax;
@@ -368,8 +329,7 @@ int compress_t(ls_handle* H, cudaStream_t st) {
     IdSlot* slots = reinterpret_cast<IdSlot*>(carve(sizeof(IdSlot) * 2 * (nblk + 1)));
     wsp = wbase;
     if ((rc = upload_block<R>(rows_x, rows_y, px, py, A, dint, st, H->ks_prec))) return rc;
-    const void* kfn = MC == 8 ? (const void*)cpqr_id_kernel<R, 8>
-                              : MC == 16 ? (const void*)cpqr_id_kernel<R, 16> : (const void*)cpqr_id_kernel<R, 32>;
+    const void* kfn = (const void*)cpqr_id_kernel<R>;
     LS_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, smem));

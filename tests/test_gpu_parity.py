@@ -171,14 +171,15 @@ def test_invalid_arguments_rejected():
 
 def test_ranks_match_oracle_compression():
     """Skeleton sets are not unique, but the ranks chosen by the same rule on the
-    same proxy blocks agree up to a few near-ties."""
+    same proxy blocks agree to within rounding near the threshold (CPQR by
+    projections on the GPU, Householder in LAPACK): 2% or 2, whichever is larger."""
     n, kappa, eps = 64, 30.0, 1e-6
     b = inputs.gaussian_bump(n)
     H = build(n, kappa, b, eps, precision=ls.LS_FP64, proxy_width=2)
     got = H.info()["ranks"]
     comp = ohbs.Compression(kappa, 1.0 / n, ohbs.Tree(n, n, 8), 4, eps, 2)
     for l in range(1, len(got)):
-        assert abs(got[l] - comp.rank[l]) <= 2, (got, comp.rank)
+        assert abs(got[l] - comp.rank[l]) <= max(2, 0.02 * comp.rank[l]), (got, comp.rank)
 
 
 @pytest.mark.slow
