@@ -208,7 +208,8 @@ def run_ours(args, rank, world):
 
     for _ in range(args.warmup):
         step(ls.LS_FP32)
-        step(ls.LS_FP64)
+        if not args.mixed_only:
+            step(ls.LS_FP64)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -216,15 +217,18 @@ def run_ours(args, rank, world):
         t_mixed, info_mixed, launches, prof = timed(ls.LS_FP32, args.steps, profile=True)
     if world > 1:
         torch.distributed.barrier()
-    t_fp64, info_fp64, _, prof64 = timed(ls.LS_FP64, max(1, min(args.steps, 3)), profile=True)
     steps64 = max(1, min(args.steps, 3))
+    if args.mixed_only:
+        t_fp64, info_fp64 = float("nan"), {"iterations": None, "resid_true": None}
+    else:
+        t_fp64, info_fp64, _, _ = timed(ls.LS_FP64, steps64, profile=True)
 
     # end to end through the public API with host buffers (b, f in pinned memory; sigma back)
     b_host = torch.from_numpy(b).pin_memory()
     f_host = f_dev.cpu().pin_memory()
     s_host = torch.zeros(n, n, dtype=torch.complex128).pin_memory()
     t_e2e = 0.0
-    for _ in range(args.steps):
+    for _ in range(0 if args.mixed_only else args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -242,7 +246,7 @@ def run_ours(args, rank, world):
         return
     value = world * N * args.steps / t_mixed / 1e6
     value64 = world * N * steps64 / t_fp64 / 1e6
-    e2e = world * N * args.steps / t_e2e / 1e6
+    e2e = world * N * args.steps / t_e2e / 1e6 if t_e2e > 0 else None
 
     # roofline of the kernel family with the largest device time
     pk = peaks()
@@ -288,6 +292,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mixed-only", action="store_true",
+                    help="time only the mixed path (no FP64 or end-to-end legs); for profiler runs")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

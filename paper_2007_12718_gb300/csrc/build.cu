@@ -96,35 +96,116 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, cx<R> al
     }
 }
 
+// 64 x 64 output tile per block, 4 x 4 outputs per thread (rows ty + 16 i,
+// columns tx + 16 j), K staged 16 at a time through shared memory.
+template <class R, bool TA, bool TB>
+__global__ void __launch_bounds__(256) gemm64_kernel(int M, int N, int K, cx<R> alpha, const cx<R>* __restrict__ A,
+                                                     int lda, long long sA, const cx<R>* __restrict__ B, int ldb,
+                                                     long long sB, cx<R> beta, cx<R>* __restrict__ C, int ldc,
+                                                     long long sC) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ cx<R> As[BK][BM + 1];
+  __shared__ cx<R> Bs[BK][BN + 1];
+  const int b = blockIdx.z;
+  A += b * sA;
+  B += b * sB;
+  C += b * sC;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  cx<R> acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = mk<R>(0, 0);
+  for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int t = threadIdx.x + 256 * r;
+      int kk, i;
+      if (TA) {
+        i = t % BM;
+        kk = t / BM;
+      } else {
+        kk = t % BK;
+        i = t / BK;
+      }
+      int gi = m0 + i, gk = k0 + kk;
+      cx<R> v = mk<R>(0, 0);
+      if (gi < M && gk < K) v = TA ? A[(long long)gk * lda + gi] : A[(long long)gi * lda + gk];
+      As[kk][i] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int t = threadIdx.x + 256 * r;
+      int kk, j;
+      if (TB) {
+        kk = t % BK;
+        j = t / BK;
+      } else {
+        j = t % BN;
+        kk = t / BN;
+      }
+      int gj = n0 + j, gk = k0 + kk;
+      cx<R> v = mk<R>(0, 0);
+      if (gj < N && gk < K) v = TB ? B[(long long)gj * ldb + gk] : B[(long long)gk * ldb + gj];
+      Bs[kk][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      cx<R> a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) fma_(acc[i][j], a[i], bb[j]);
+    }
+    __syncthreads();
+  }
+  const bool zb = (beta.re == R(0) && beta.im == R(0));
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int gi = m0 + ty + 16 * i, gj = n0 + tx + 16 * j;
+      if (gi < M && gj < N) {
+        cx<R> v = alpha * acc[i][j];
+        if (!zb) v = v + beta * C[(long long)gi * ldc + gj];
+        C[(long long)gi * ldc + gj] = v;
+      }
+    }
+}
+
 template <class R>
 void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, cx<R> alpha, const cx<R>* A, int lda, long long sA,
           const cx<R>* B, int ldb, long long sB, cx<R> beta, cx<R>* C, int ldc, long long sC, int batch) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
-  if (K <= 0) {
-    // C = beta C; only used with beta = 0 or 1 here
+  if (K <= 0) return;  // only reached with beta = 1 (nothing to add)
+  count_launch();
+  if (M >= 48 && N >= 48) {
+    dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
+    if (!ta && !tb)
+      gemm64_kernel<R, false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    else if (ta && !tb)
+      gemm64_kernel<R, true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    else if (!ta && tb)
+      gemm64_kernel<R, false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    else
+      gemm64_kernel<R, true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
     return;
   }
   dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, batch);
   if (!ta && !tb)
-    {
-      count_launch();
-      gemm_kernel<R, false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
-    }
+    gemm_kernel<R, false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
   else if (ta && !tb)
-    {
-      count_launch();
-      gemm_kernel<R, true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
-    }
+    gemm_kernel<R, true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
   else if (!ta && tb)
-    {
-      count_launch();
-      gemm_kernel<R, false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
-    }
+    gemm_kernel<R, false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
   else
-    {
-      count_launch();
-      gemm_kernel<R, true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
-    }
+    gemm_kernel<R, true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
 }
 
 template <class R>
@@ -312,7 +393,8 @@ template <class R>
 __global__ void __launch_bounds__(256) gj_panel_kernel(cx<R>* X, int n, int lda, long long sX, int k0, int nb,
                                                        int* piv, int* perm, int* err) {
   extern __shared__ unsigned char smraw[];
-  cx<R>* pn = reinterpret_cast<cx<R>*>(smraw);  // n x nb
+  cx<R>* pn = reinterpret_cast<cx<R>*>(smraw);  // n x nb, row stride nb + 1 (no bank conflicts)
+  const int ldp = nb + 1;
   __shared__ cx<R> prow[32];
   __shared__ R s_v[8];
   __shared__ int s_i[8];
@@ -321,14 +403,14 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(cx<R>* X, int n, int lda,
   const unsigned lmask = nb >= 32 ? 0xffffffffu : ((1u << nb) - 1u);
   cx<R>* M = X + b * sX;
   for (int i = warp; i < n; i += 8)
-    if (lane < nb) pn[i * nb + lane] = M[(long long)i * lda + k0 + lane];
+    if (lane < nb) pn[i * ldp + lane] = M[(long long)i * lda + k0 + lane];
   __syncthreads();
   for (int jj = 0; jj < nb; ++jj) {
     const int j = k0 + jj;
     R best = R(-1);
     int bi = n;
     for (int i = j + tid; i < n; i += blockDim.x) {
-      R v = abs2(pn[i * nb + jj]);
+      R v = abs2(pn[i * ldp + jj]);
       if (v > best) {
         best = v;
         bi = i;
@@ -359,35 +441,35 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(cx<R>* X, int n, int lda,
       return;  // every thread takes this branch
     }
     const int p = bi;
-    const cx<R> d = inv(pn[p * nb + jj]);
+    const cx<R> d = inv(pn[p * ldp + jj]);
     if (tid == 0) piv[(long long)b * n + j] = p;
     if (warp == 0 && lane < nb) {
-      cx<R> a = pn[j * nb + lane], bv = pn[p * nb + lane];
+      cx<R> a = pn[j * ldp + lane], bv = pn[p * ldp + lane];
       prow[lane] = (lane == jj) ? d : bv * d;
-      if (p != j) pn[p * nb + lane] = a;
+      if (p != j) pn[p * ldp + lane] = a;
     }
     __syncthreads();
     for (int i = warp; i < n; i += 8) {
       if (lane >= nb) continue;
       if (i == j) {
-        pn[i * nb + lane] = prow[lane];
+        pn[i * ldp + lane] = prow[lane];
         continue;
       }
-      cx<R> f = pn[i * nb + jj];
+      cx<R> f = pn[i * ldp + jj];
       __syncwarp(lmask);
       if (lane == jj) {
-        pn[i * nb + lane] = mk<R>(-(f.re * d.re - f.im * d.im), -(f.re * d.im + f.im * d.re));
+        pn[i * ldp + lane] = mk<R>(-(f.re * d.re - f.im * d.im), -(f.re * d.im + f.im * d.re));
       } else {
-        cx<R> r = prow[lane], v = pn[i * nb + lane];
+        cx<R> r = prow[lane], v = pn[i * ldp + lane];
         v.re -= f.re * r.re - f.im * r.im;
         v.im -= f.re * r.im + f.im * r.re;
-        pn[i * nb + lane] = v;
+        pn[i * ldp + lane] = v;
       }
     }
     __syncthreads();
   }
   for (int i = warp; i < n; i += 8)
-    if (lane < nb) M[(long long)i * lda + k0 + lane] = pn[i * nb + lane];
+    if (lane < nb) M[(long long)i * lda + k0 + lane] = pn[i * ldp + lane];
   if (tid == 0) {  // net permutation of the panel's interchanges
     int cnt = 0;
     for (int jj = 0; jj < nb; ++jj) {
@@ -497,8 +579,8 @@ int invert_batch(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int P, vo
     return check_launch("inverse_smem");
   }
   int nb = 32;
-  while (nb > 4 && sizeof(cx<R>) * (size_t)n * nb > 200 * 1024) nb >>= 1;
-  const size_t smem_panel = sizeof(cx<R>) * (size_t)n * nb;
+  while (nb > 4 && sizeof(cx<R>) * (size_t)n * (nb + 1) > 200 * 1024) nb >>= 1;
+  const size_t smem_panel = sizeof(cx<R>) * (size_t)n * (nb + 1);
   if (smem_panel > 200 * 1024) {
     set_last_error_text("merge matrix too large for the panel kernel");
     return LS_EINVAL;

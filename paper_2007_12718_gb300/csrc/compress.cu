@@ -26,11 +26,11 @@ namespace {
 template <class R>
 __global__ void block_kernel(const int* __restrict__ rx, const int* __restrict__ ry, int m,
                              const int* __restrict__ px, const int* __restrict__ py, int p, cx<R>* __restrict__ out,
-                             long long ld, KernelSpec ks) {
+                             long long ld, KernelTable kt, KernelSpec ks) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)m * p) return;
   int c = (int)(t / p), q = (int)(t % p);
-  z64 v = kernel_entry(ks, px[q] - rx[c], py[q] - ry[c]);
+  z64 v = table_entry(kt, ks, px[q] - rx[c], py[q] - ry[c]);
   out[(long long)c * ld + q] = cvt<R>(v);
 }
 
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
                                                       cx<R>* __restrict__ Rm, int* __restrict__ sel,
                                                       IdSlot* __restrict__ slots, cx<R>* __restrict__ pslots,
                                                       int* __restrict__ piv, int* __restrict__ rank,
-                                                      cx<R>* __restrict__ U, GridSync gs) {
+                                                      cx<R>* __restrict__ U, cx<R>* __restrict__ RT, GridSync gs) {
   extern __shared__ unsigned char smraw[];
   cx<R>* pvec = reinterpret_cast<cx<R>*>(smraw);  // p
   const int nblk = gridDim.x, blk = blockIdx.x;
@@ -198,9 +198,15 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
     __syncthreads();
   }
   if (blk == 0 && tid == 0) rank[0] = k;
-  __syncthreads();
-  // U rows: identity on the skeleton, T = R11^-1 R12 on the rest (one warp per candidate);
-  // the per-warp solution vectors reuse the shared memory of the candidates.
+  // R11 gathered by columns: RT[a][b] = R(b, piv[a]) for b <= a (rows of RT contiguous)
+  for (long long t = (long long)blk * blockDim.x + tid; t < (long long)k * k; t += (long long)nblk * blockDim.x) {
+    int a = (int)(t / k), bb = (int)(t % k);
+    RT[t] = bb <= a ? Rm[(long long)bb * m + piv[a]] : mk<R>(0, 0);
+  }
+  if (!grid_sync(gs, nblk, epoch)) return;
+  // U rows: identity on the skeleton, T = R11^-1 R12 on the rest: one warp per
+  // candidate, column-oriented back substitution in shared memory (the
+  // candidate vectors' space is reused).
   cx<R>* t = pvec + (long long)warp * kmax;
   for (int c = c0 + warp; c < c1; c += nwarp) {
     int sc = s_sel[c - c0];
@@ -208,14 +214,19 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
       for (int a = lane; a < k; a += 32) U[(long long)c * k + a] = mk<R>(a == sc ? R(1) : R(0), R(0));
       continue;
     }
+    for (int a = lane; a < k; a += 32) t[a] = Rm[(long long)a * m + c];
+    __syncwarp();
     for (int a = k - 1; a >= 0; --a) {
-      cx<R> acc = mk<R>(0, 0);
-      for (int b = a + 1 + lane; b < k; b += 32) fma_(acc, Rm[(long long)a * m + piv[b]], t[b]);
-      acc = warp_sum(acc);
-      if (lane == 0) {
-        cx<R> rhs = Rm[(long long)a * m + c] - acc;
-        t[a] = rhs * inv(Rm[(long long)a * m + piv[a]]);
+      const cx<R>* col = RT + (long long)a * k;
+      const cx<R> ta = t[a] * inv(col[a]);
+      __syncwarp();
+      for (int bb = lane; bb < a; bb += 32) {
+        cx<R> v = t[bb], r = col[bb];
+        v.re -= r.re * ta.re - r.im * ta.im;
+        v.im -= r.re * ta.im + r.im * ta.re;
+        t[bb] = v;
       }
+      if (lane == 0) t[a] = ta;
       __syncwarp();
     }
     for (int a = lane; a < k; a += 32) U[(long long)c * k + a] = t[a];
@@ -225,7 +236,8 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
 
 template <class R>
 int upload_block(const std::vector<int>& rx, const std::vector<int>& ry, const std::vector<int>& px,
-                 const std::vector<int>& py, cx<R>* out, int* dtmp, cudaStream_t st, const KernelSpec& ks) {
+                 const std::vector<int>& py, cx<R>* out, int* dtmp, cudaStream_t st, const KernelSpec& ks,
+                 const KernelTable& kt) {
   int m = (int)rx.size(), p = (int)px.size();
   std::vector<int> host(2 * m + 2 * p);
   std::copy(rx.begin(), rx.end(), host.begin());
@@ -238,7 +250,7 @@ int upload_block(const std::vector<int>& rx, const std::vector<int>& ry, const s
     {
       count_launch();
       block_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(dtmp, dtmp + m, m, dtmp + 2 * m, dtmp + 2 * m + p,
-                                                                     p, out, p, ks);
+                                                                     p, out, p, kt, ks);
     }
   // host vector must outlive the copy
   LS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -307,8 +319,8 @@ int compress_t(ls_handle* H, cudaStream_t st) {
       set_last_error_text("proxy block too large for the ID kernel");
       return LS_EINVAL;
     }
-    size_t need = sizeof(cx<R>) * ((size_t)m * p * (use_smem ? 1 : 2) + (size_t)kmax * m + (size_t)m * kmax +
-                                   (size_t)2 * nblk * p) +
+    size_t need = 64 * 256 + sizeof(cx<R>) * ((size_t)m * p * (use_smem ? 1 : 2) + (size_t)kmax * m + (size_t)m * kmax +
+                                   (size_t)kmax * kmax + (size_t)2 * nblk * p) +
                   sizeof(int) * (2 * m + 8) + sizeof(IdSlot) * 2 * (nblk + 1) + 1024;
     char* wsp = nullptr;
     if ((rc = dalloc((void**)&wsp, need))) return rc;
@@ -322,13 +334,14 @@ int compress_t(ls_handle* H, cudaStream_t st) {
     cx<R>* Aw = use_smem ? nullptr : reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)m * p));
     cx<R>* Rm = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)kmax * m));
     cx<R>* Ut = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)m * kmax));
+    cx<R>* RT = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)kmax * kmax));
     cx<R>* pslots = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)2 * nblk * p));
     int* sel = reinterpret_cast<int*>(carve(sizeof(int) * m));
     int* piv = reinterpret_cast<int*>(carve(sizeof(int) * m));
     int* rank = reinterpret_cast<int*>(carve(sizeof(int) * 8));
     IdSlot* slots = reinterpret_cast<IdSlot*>(carve(sizeof(IdSlot) * 2 * (nblk + 1)));
     wsp = wbase;
-    if ((rc = upload_block<R>(rows_x, rows_y, px, py, A, dint, st, H->ks_prec))) return rc;
+    if ((rc = upload_block<R>(rows_x, rows_y, px, py, A, dint, st, H->ks_prec, KernelTable{H->ktab, H->ktx, H->kty}))) return rc;
     const void* kfn = (const void*)cpqr_id_kernel<R>;
     LS_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -345,7 +358,7 @@ int compress_t(ls_handle* H, cudaStream_t st) {
     double eps = H->tol;
     const cx<R>* Ac = A;
     void* args[] = {&Ac, (void*)&m, (void*)&p, (void*)&kmax, &eps, &use_smem, &Aw, &Rm, &sel, &slots, &pslots,
-                    &piv, &rank, &Ut, &gs};
+                    &piv, &rank, &Ut, &RT, &gs};
     int tk = prof_begin(st);
     count_launch();
     LS_CUDA_TRY(cudaLaunchCooperativeKernel(kfn, dim3(nblk), dim3(256), args, smem, st));
@@ -397,7 +410,7 @@ int compress_t(ls_handle* H, cudaStream_t st) {
     if (dint) cudaFree(dint);
     dint = nullptr;
     if ((rc = dalloc((void**)&dint, sizeof(int) * (4 * kk + 8)))) return rc;
-    if ((rc = upload_block<R>(ax, ay, bx, by, reinterpret_cast<cx<R>*>(lv.Gsib), dint, st, H->ks_prec))) return rc;
+    if ((rc = upload_block<R>(ax, ay, bx, by, reinterpret_cast<cx<R>*>(lv.Gsib), dint, st, H->ks_prec, KernelTable{H->ktab, H->ktx, H->kty}))) return rc;
   }
   {
     std::vector<int> lx, ly;
@@ -410,7 +423,7 @@ int compress_t(ls_handle* H, cudaStream_t st) {
     if (dint) cudaFree(dint);
     dint = nullptr;
     if ((rc = dalloc((void**)&dint, sizeof(int) * (4 * s * s + 8)))) return rc;
-    if ((rc = upload_block<R>(lx, ly, lx, ly, reinterpret_cast<cx<R>*>(H->Gleaf), dint, st, H->ks_prec))) return rc;
+    if ((rc = upload_block<R>(lx, ly, lx, ly, reinterpret_cast<cx<R>*>(H->Gleaf), dint, st, H->ks_prec, KernelTable{H->ktab, H->ktx, H->kty}))) return rc;
   }
   if (dint) cudaFree(dint);
   return LS_OK;

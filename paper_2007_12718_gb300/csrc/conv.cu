@@ -151,8 +151,20 @@ __global__ void rows_inv_kernel(const z64* __restrict__ W, long long w_rhs_strid
   }
 }
 
+__global__ void kernel_table_kernel(z64* T, int tx, int ty, double kh, double h2) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)tx * ty) return;
+  int i = (int)(t % tx), j = (int)(t / tx);
+  z64 v = mk<double>(0.0, 0.0);
+  if (i || j) {
+    z64 g = green(kh * sqrt((double)i * i + (double)j * j));
+    v = mk<double>(g.re * h2, g.im * h2);
+  }
+  T[t] = v;
+}
+
 // Fill the (2ny) x (2nx) circulant with K(m): index i <-> m1 = i (i < nx), i - 2nx (i > nx), 0 at i = nx.
-__global__ void circulant_kernel(z64* C, int nx, int ny, KernelSpec ks) {
+__global__ void circulant_kernel(z64* C, int nx, int ny, KernelTable kt, KernelSpec ks) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   int Lx = 2 * nx, Ly = 2 * ny;
   if (t >= (long long)Lx * Ly) return;
@@ -161,7 +173,7 @@ __global__ void circulant_kernel(z64* C, int nx, int ny, KernelSpec ks) {
   if (i != nx && j != ny) {
     int m1 = i < nx ? i : i - Lx;
     int m2 = j < ny ? j : j - Ly;
-    v = kernel_entry(ks, m1, m2);
+    v = table_entry(kt, ks, m1, m2);
   }
   C[t] = v;
 }
@@ -191,6 +203,19 @@ int cols_per_block(int Ly) {
 
 }  // namespace
 
+int kernel_table_setup(ls_handle* H, cudaStream_t st) {
+  // offsets up to the grid size plus the proxy ring on both sides
+  H->ktx = H->grid.nx + 2 * H->ring + 2;
+  H->kty = H->grid.ny + 2 * H->ring + 2;
+  int rc;
+  if ((rc = dalloc((void**)&H->ktab, sizeof(z64) * (size_t)H->ktx * H->kty))) return rc;
+  long long tot = (long long)H->ktx * H->kty;
+  count_launch();
+  kernel_table_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(H->ktab, H->ktx, H->kty, H->kappa * H->grid.h,
+                                                                      H->grid.h * H->grid.h);
+  return check_launch("kernel table");
+}
+
 int conv_setup(ls_handle* H, cudaStream_t st) {
   const int nx = H->grid.nx, ny = H->grid.ny;
   H->Lx = 2 * nx;
@@ -210,7 +235,8 @@ int conv_setup(ls_handle* H, cudaStream_t st) {
   size_t nfull = (size_t)H->Lx * H->Ly;
   if ((rc = dalloc((void**)&full, sizeof(z64) * nfull))) return rc;
   count_launch();
-  circulant_kernel<<<(unsigned)((nfull + 255) / 256), 256, 0, st>>>(full, nx, ny, H->ks_mv);
+  circulant_kernel<<<(unsigned)((nfull + 255) / 256), 256, 0, st>>>(full, nx, ny, KernelTable{H->ktab, H->ktx, H->kty},
+                                                                   H->ks_mv);
   // rows: full length, in place through the same buffer (each block owns one row)
   size_t smr = sizeof(z64) * (H->Lx + H->Lx / 2);
   cudaFuncSetAttribute(rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);

@@ -32,6 +32,8 @@ struct ls_handle {
   ls::z64 *tw_x = nullptr, *tw_y = nullptr;  // exp(-2 pi i k / L) for the two padded lengths
   int Lx = 0, Ly = 0, logLx = 0, logLy = 0;
   double* b = nullptr;          // device copy of b [ny][nx]
+  ls::z64* ktab = nullptr;      // h^2 G(h |d|) for lattice offsets 0 <= d1 < ktx, 0 <= d2 < kty
+  int ktx = 0, kty = 0;
   ls::z64* convbuf = nullptr;   // ny x 2nx complex per right-hand side
   int convbuf_rhs = 0;
 
@@ -57,6 +59,7 @@ struct ls_handle {
 namespace ls {
 
 // conv.cu
+int kernel_table_setup(ls_handle* H, cudaStream_t st);
 int conv_setup(ls_handle* H, cudaStream_t st);
 // y = x + kappa^2 b .* (K * x)  (field_only: y = K * x)
 int conv_apply(ls_handle* H, const z64* x, z64* y, int nrhs, bool field_only, cudaStream_t st);

@@ -25,9 +25,10 @@ struct KernelSpec {
 __device__ __forceinline__ z64 hankel1_0(double z) {
   if (z <= 20.0) {
     int N = 2 * (int)((z + 25.0 + 4.0 * cbrt(z)) * 0.5);
+    const double tz = 2.0 / z;
     double jp1 = 0.0, j = 1e-30, norm = 0.0, neu = 0.0;
     for (int k = N; k > 0; --k) {
-      double jm1 = (2.0 * k / z) * j - jp1;
+      double jm1 = (k * tz) * j - jp1;
       if ((k & 1) == 0) {
         norm += 2.0 * j;
         int kk = k >> 1;
@@ -76,6 +77,20 @@ __device__ __forceinline__ z64 green(double z) {
   return mk<double>(-0.25 * hz.im, 0.25 * hz.re);
 }
 
+// Corrected-stencil part tau_d (zero off the stencil), times h^2.
+__device__ __forceinline__ z64 stencil_entry(const KernelSpec& ks, int d1, int d2) {
+  z64 v = mk<double>(0.0, 0.0);
+  if (abs(d1) + abs(d2) <= 3) {
+    for (int p = 0; p < ks.npts; ++p)
+      if (ks.m1[p] == d1 && ks.m2[p] == d2) {
+        v.re += ks.wr[p];
+        v.im += ks.wi[p];
+      }
+  }
+  double h2 = ks.h * ks.h;
+  return mk<double>(v.re * h2, v.im * h2);
+}
+
 // Discrete kernel entry for the lattice offset (d1, d2): h^2 (G(h|d|) + tau_d),
 // with tau only on the stencil and h^2 tau_0 on the diagonal.
 __device__ __forceinline__ z64 kernel_entry(const KernelSpec& ks, int d1, int d2) {
@@ -90,6 +105,19 @@ __device__ __forceinline__ z64 kernel_entry(const KernelSpec& ks, int d1, int d2
   }
   double h2 = ks.h * ks.h;
   return mk<double>(v.re * h2, v.im * h2);
+}
+
+// Lattice-offset table T[|d2| * tx + |d1|] = h^2 G(h |d|) (0 at d = 0): every
+// kernel block of the build is a lookup in it plus the stencil correction.
+struct KernelTable {
+  const z64* t;
+  int tx, ty;
+};
+
+__device__ __forceinline__ z64 table_entry(const KernelTable& kt, const KernelSpec& ks, int d1, int d2) {
+  z64 v = kt.t[(long long)abs(d2) * kt.tx + abs(d1)];
+  if (abs(d1) + abs(d2) <= 3) v = v + stencil_entry(ks, d1, d2);
+  return v;
 }
 
 }  // namespace ls

@@ -172,6 +172,7 @@ void ls_free(ls_handle* H) {
   f(H->tw_x);
   f(H->tw_y);
   f(H->b);
+  f(H->ktab);
   f(H->convbuf);
   for (auto& lv : H->lev) {
     f(lv.U);
@@ -290,6 +291,7 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
     set_error("b must be finite and <= 1");
     return LS_EINVAL;
   }
+  if ((rc = ls::kernel_table_setup(H, st))) return rc;
   if ((rc = ls::conv_setup(H, st))) return rc;
   if ((rc = ls::compress(H, st))) return rc;
   if ((rc = ls::hbs_build(H, st))) return rc;
