@@ -126,6 +126,30 @@ int ls_solve(ls_handle* h, const void* f, void* sigma, int nrhs, ls_solve_info* 
  * angle.  thetas: nrhs doubles on the host. */
 int ls_rhs_plane_wave(ls_handle* h, const double* thetas, void* f, int nrhs, void* stream);
 
+/* ls_matvec_noalloc -- ls_matvec for callers that must not allocate device
+ * memory when they apply the operator.  The paper has no counterpart: this is
+ * a deployment variant.  Such callers include frameworks whose memory pool
+ * already holds the free device memory (a cudaMalloc would fail or fragment
+ * it), latency-critical loops that cannot take the implicit device
+ * synchronisation of cudaMalloc/cudaFree, and programs whose memory budget is
+ * fixed at start-up.  ls_matvec may allocate (its FFT buffer grows with nrhs,
+ * host vectors are staged); this call calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Its FFT scratch is a fixed file-scope device array of
+ * ls_matvec_noalloc_max_elems() = 2^18 complex128 entries (4 MiB), held by
+ * every GPU that loads the library until the process exits.
+ *   x, y : device pointers, nrhs complex128 grid vectors (x, y may not alias).
+ *   Requires nrhs * ny * 2 * nx <= 2^18; larger sizes return LS_EINVAL with a
+ *   message, as do host pointers.  The handle must come from ls_build (which
+ *   does allocate, at set-up time).
+ *   The first call on a device looks up the scratch array's device address
+ *   (cudaGetSymbolAddress, with that device current); make that first call
+ *   before any stream capture.  Every call shares the one array and leaves its
+ *   contents behind; nothing in it needs to start at zero (each call writes
+ *   every entry before reading it), but calls that overlap on the GPU (two
+ *   streams at once) race on it. */
+int ls_matvec_noalloc(ls_handle* h, const void* x, void* y, int nrhs, void* stream);
+long long ls_matvec_noalloc_max_elems(void);
+
 /* ls_build_info -- ranks, flop and byte counts of the built handle. */
 int ls_get_build_info(const ls_handle* h, ls_build_info* info);
 

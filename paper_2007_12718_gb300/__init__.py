@@ -29,7 +29,8 @@ LS_FP64, LS_FP32 = 0, 1
 
 EXPORTED = ["ls_default_opts", "ls_build", "ls_apply", "ls_matvec", "ls_solve", "ls_rhs_plane_wave",
             "ls_get_build_info", "ls_free", "ls_strerror", "ls_last_error", "ls_profile_enable",
-            "ls_profile_reset", "ls_profile_get", "ls_kernel_launches"]
+            "ls_profile_reset", "ls_profile_get", "ls_kernel_launches", "ls_matvec_noalloc",
+            "ls_matvec_noalloc_max_elems"]
 
 
 class Grid(ctypes.Structure):
@@ -97,6 +98,10 @@ def load_library(path=LIB_PATH):
     lib.ls_profile_reset.restype = ip
     lib.ls_profile_get.argtypes = [ctypes.POINTER(ProfileEntry), ip]
     lib.ls_profile_get.restype = ip
+    lib.ls_matvec_noalloc.argtypes = [vp, vp, vp, ip, vp]
+    lib.ls_matvec_noalloc.restype = ip
+    lib.ls_matvec_noalloc_max_elems.argtypes = []
+    lib.ls_matvec_noalloc_max_elems.restype = ctypes.c_longlong
     lib.ls_kernel_launches.argtypes = []
     lib.ls_kernel_launches.restype = ctypes.c_longlong
     _lib = lib
@@ -214,6 +219,16 @@ def ls_solve(handle, f, sigma, stream=None, allow_noconv=False):
            allow=(LS_ENOCONV,) if allow_noconv else ())
     return [{"iterations": i.iterations, "converged": bool(i.converged), "resid_est": i.resid_est,
              "resid_true": i.resid_true} for i in infos]
+
+
+def ls_matvec_noalloc(handle, x, y, stream=None):
+    """y = (I + B(G+T)) x without any device allocation (device tensors only;
+    the FFT scratch is a fixed 2^18-entry array inside the library)."""
+    xp, k1, n = _ptr(x, np.complex128)
+    yp, k2, _ = _ptr(y, np.complex128, True)
+    _check(load_library().ls_matvec_noalloc(handle.ptr, xp, yp, _nrhs(handle, n), _stream(stream)),
+           "ls_matvec_noalloc")
+    return y
 
 
 def ls_rhs_plane_wave(handle, thetas, f, stream=None):

@@ -14,6 +14,8 @@
 // DIF-forward / DIT-inverse pairs need no bit-reversal permutations.  K is
 // even in m1 and m2, so its spectrum is even too and only the quarter
 // (nx+1) x (ny+1) is stored (1/(4 nx ny) folded in).
+#include <mutex>
+
 #include "handle.h"
 #include "prof.h"
 
@@ -297,3 +299,92 @@ int conv_apply(ls_handle* H, const z64* x, z64* y, int nrhs, bool field_only, cu
 }
 
 }  // namespace ls
+
+// ---------------------------------------------------------------------------
+// ls_matvec_noalloc: the FFT matvec with its scratch in a fixed device array.
+//
+// Some callers cannot allocate device memory at the point where they apply
+// the operator: code whose framework has already reserved the free device
+// memory in its own pool (a cudaMalloc there fails or fragments the pool),
+// latency-critical loops that cannot afford the implicit device
+// synchronisation of cudaMalloc/cudaFree, and programs that must stay within a
+// memory budget fixed at start-up.  ls_matvec may allocate (its padded FFT
+// buffer grows with nrhs, and host vectors are staged through device memory);
+// this entry point allocates nothing: the padded buffer lives in the
+// file-scope array below, which every GPU that loads the library holds until
+// the process exits.
+namespace {
+
+constexpr long long kNoAllocScratchElems = 1LL << 18;  // complex128 entries: 4 MiB
+static __device__ __align__(256) ls::z64 g_noalloc_scratch[kNoAllocScratchElems];
+
+constexpr int kMaxDevices = 64;
+ls::z64* g_noalloc_ptr[kMaxDevices] = {nullptr};
+std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device (host code only
+// sees a host-side stand-in for the symbol, so the address is looked up once
+// per device, with that device current).
+int noalloc_scratch(ls::z64** out) {
+  int dev = 0;
+  LS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return LS_EINVAL;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    LS_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<ls::z64*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return LS_OK;
+}
+
+bool on_device(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" long long ls_matvec_noalloc_max_elems(void) { return kNoAllocScratchElems; }
+
+extern "C" int ls_matvec_noalloc(ls_handle* H, const void* xv, void* yv, int nrhs, void* stream) {
+  using namespace ls;
+  if (!H || !xv || !yv || nrhs < 1) return LS_EINVAL;
+  const int nx = H->grid.nx, ny = H->grid.ny;
+  const long long need = (long long)nrhs * ny * H->Lx;
+  if (need > kNoAllocScratchElems) {
+    set_last_error_text("ls_matvec_noalloc: nrhs * ny * 2 nx exceeds the fixed scratch (2^18 complex128 entries)");
+    return LS_EINVAL;
+  }
+  if (!on_device(xv) || !on_device(yv)) {
+    set_last_error_text("ls_matvec_noalloc: x and y must be device pointers");
+    return LS_EINVAL;
+  }
+  z64* W = nullptr;
+  int rc = noalloc_scratch(&W);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const z64* x = static_cast<const z64*>(xv);
+  z64* y = static_cast<z64*>(yv);
+  long long g_stride = (long long)nx * ny, w_stride = (long long)ny * H->Lx;
+  size_t smr = sizeof(z64) * (H->Lx + H->Lx / 2);
+  LS_CUDA_TRY(cudaFuncSetAttribute(rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+  LS_CUDA_TRY(cudaFuncSetAttribute(rows_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
+  count_launch();
+  rows_fwd_kernel<<<dim3(ny, nrhs), 256, smr, st>>>(x, nx, nx, g_stride, W, w_stride, H->Lx, H->logLx, H->tw_x);
+  int C = cols_per_block(H->Ly);
+  size_t smc = sizeof(z64) * ((size_t)H->Ly * C + H->Ly / 2);
+  LS_CUDA_TRY(cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+  count_launch();
+  cols_kernel<<<dim3(H->Lx / C, nrhs), 256, smc, st>>>(W, w_stride, H->Lx, H->logLx, ny, H->Ly, H->logLy, C, H->tw_y,
+                                                       H->spec, nx, ny, 0);
+  count_launch();
+  rows_inv_kernel<<<dim3(ny, nrhs), 256, smr, st>>>(W, w_stride, H->Lx, H->logLx, H->tw_x, x, H->b, H->kappa * H->kappa,
+                                                    nx, g_stride, y, 0);
+  return check_launch("ls_matvec_noalloc");
+}
