@@ -15,6 +15,9 @@
 // in-shared-memory Gauss-Jordan inversion with partial pivoting (one block
 // per matrix; the leaf kernel fuses it with the X B U and S products), and a
 // cooperative multi-block Gauss-Jordan for the large top-level matrices.
+#include <cooperative_groups.h>
+#include <string.h>
+
 #include <algorithm>
 
 #include "handle.h"
@@ -503,6 +506,161 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(cx<R>* X, int n, int lda,
   }
 }
 
+// Panel step of the blocked Gauss-Jordan inverse across a thread-block
+// cluster: the CL blocks of a cluster share one matrix, block r keeping rows
+// [r*rows_per, (r+1)*rows_per) of the n x nb panel in shared memory.  Per pivot
+// column: local argmax, cluster barrier, every block reads the CL candidates
+// through distributed shared memory and takes the same winner (largest |.|,
+// lowest row on ties); the owners of the pivot row p and of row j publish the
+// scaled pivot row and old row j; cluster barrier; every block eliminates its
+// own rows.  Same result, piv and perm as gj_panel_kernel.
+template <class R>
+__global__ void __launch_bounds__(256) gj_panel_cluster_kernel(cx<R>* X, int n, int lda, long long sX, int k0, int nb,
+                                                               int* piv, int* perm, int* err) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ unsigned char smraw[];
+  const int CL = (int)cluster.num_blocks();
+  const int crank = (int)cluster.block_rank();
+  const int mat = blockIdx.x / CL;
+  const int rows_per = (n + CL - 1) / CL;
+  const int r0 = min(n, crank * rows_per), r1 = min(n, r0 + rows_per);
+  const int ldp = nb + 1;
+  cx<R>* pn = reinterpret_cast<cx<R>*>(smraw);  // (r1 - r0) x nb, stride nb + 1
+  __shared__ cx<R> s_prow[32], s_oldj[32], l_prow[32], l_oldj[32];
+  __shared__ R s_v[8];
+  __shared__ int s_i[8];
+  __shared__ R s_best;
+  __shared__ int s_bidx;
+  __shared__ int s_pos[64], s_org[64];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lmask = nb >= 32 ? 0xffffffffu : ((1u << nb) - 1u);
+  cx<R>* M = X + mat * sX;
+  for (int i = r0 + warp; i < r1; i += 8)
+    if (lane < nb) pn[(i - r0) * ldp + lane] = M[(long long)i * lda + k0 + lane];
+  __syncthreads();
+  for (int jj = 0; jj < nb; ++jj) {
+    const int j = k0 + jj;
+    R best = R(-1);
+    int bi = n;
+    for (int i = max(j, r0) + tid; i < r1; i += blockDim.x) {
+      R v = abs2(pn[(i - r0) * ldp + jj]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+    for (int o = 16; o; o >>= 1) {
+      R ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      s_v[warp] = best;
+      s_i[warp] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      R bb = s_v[0];
+      int ii = s_i[0];
+      for (int w = 1; w < 8; ++w)
+        if (s_v[w] > bb || (s_v[w] == bb && s_i[w] < ii)) {
+          bb = s_v[w];
+          ii = s_i[w];
+        }
+      s_best = bb;
+      s_bidx = ii;
+    }
+    cluster.sync();
+    best = R(-1);
+    bi = n;
+    for (int r = 0; r < CL; ++r) {
+      R ob = *cluster.map_shared_rank(&s_best, r);
+      int oi = *cluster.map_shared_rank(&s_bidx, r);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
+    if (!(best > R(0))) {
+      if (tid == 0 && crank == 0) atomicExch(err, LS_ESINGULAR);
+      return;  // every thread of every block of the cluster takes this branch
+    }
+    const int p = bi;
+    const int own_p = p / rows_per, own_j = j / rows_per;
+    if (crank == 0 && tid == 0) piv[(long long)mat * n + j] = p;
+    if (crank == own_p && warp == 0 && lane < nb) {
+      cx<R> dd = inv(pn[(p - r0) * ldp + jj]);
+      s_prow[lane] = (lane == jj) ? dd : pn[(p - r0) * ldp + lane] * dd;
+    }
+    if (crank == own_j && warp == 1 && lane < nb) s_oldj[lane] = pn[(j - r0) * ldp + lane];
+    cluster.sync();
+    if (warp == 0 && lane < nb) l_prow[lane] = *cluster.map_shared_rank(&s_prow[lane], own_p);
+    if (warp == 1 && lane < nb && p != j && p >= r0 && p < r1)
+      l_oldj[lane] = *cluster.map_shared_rank(&s_oldj[lane], own_j);
+    __syncthreads();
+    const cx<R> d = l_prow[jj];
+    for (int i = r0 + warp; i < r1; i += 8) {
+      if (lane >= nb) continue;
+      cx<R>* row = pn + (i - r0) * ldp;
+      if (i == j) {
+        row[lane] = l_prow[lane];
+        continue;
+      }
+      const bool moved = (i == p);  // old row j lands at position p
+      cx<R> f = moved ? l_oldj[jj] : row[jj];
+      cx<R> v = moved ? l_oldj[lane] : row[lane];
+      __syncwarp(lmask);
+      if (lane == jj) {
+        row[lane] = mk<R>(-(f.re * d.re - f.im * d.im), -(f.re * d.im + f.im * d.re));
+      } else {
+        cx<R> r = l_prow[lane];
+        v.re -= f.re * r.re - f.im * r.im;
+        v.im -= f.re * r.im + f.im * r.re;
+        row[lane] = v;
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = r0 + warp; i < r1; i += 8)
+    if (lane < nb) M[(long long)i * lda + k0 + lane] = pn[(i - r0) * ldp + lane];
+  if (crank == 0 && tid == 0) {  // net permutation of the panel's interchanges
+    int cnt = 0;
+    for (int jj = 0; jj < nb; ++jj) {
+      int j = k0 + jj, p = piv[(long long)mat * n + j];
+      if (p == j) continue;
+      int ij = -1, ip = -1;
+      for (int t = 0; t < cnt; ++t) {
+        if (s_pos[t] == j) ij = t;
+        if (s_pos[t] == p) ip = t;
+      }
+      if (ij < 0) {
+        s_pos[cnt] = j;
+        s_org[cnt] = j;
+        ij = cnt++;
+      }
+      if (ip < 0) {
+        s_pos[cnt] = p;
+        s_org[cnt] = p;
+        ip = cnt++;
+      }
+      int t = s_org[ij];
+      s_org[ij] = s_org[ip];
+      s_org[ip] = t;
+    }
+    int* pr = perm + (long long)mat * 2 * 64;
+    for (int t = 0; t < cnt; ++t) {
+      pr[2 * t] = s_pos[t];
+      pr[2 * t + 1] = s_org[t];
+    }
+    if (cnt < 64) pr[2 * cnt] = -1;
+  }
+  cluster.sync();  // no block leaves while others may still read its shared memory
+}
+
 // For every column c outside the panel: apply the panel's net row
 // permutation, move rows J = [k0, k0+nb) to Mb (nb x n) and zero them in X, so
 // that X[:, c] += Panel * Mb[:, c] completes the step.
@@ -590,10 +748,45 @@ int invert_batch(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int P, vo
   int* perm = piv + (size_t)P * n;
   if (sizeof(cx<R>) * (size_t)P * nb * n + sizeof(int) * (size_t)P * (n + 128) > scratch_bytes) return LS_ENOMEM;
   LS_CUDA_TRY(cudaFuncSetAttribute(gj_panel_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_panel));
+  // clusters of CL blocks share one panel when the matrix is large enough
+  int CL = n >= 512 ? 16 : (n >= 256 ? 8 : 1);
+  if (CL == 16 && cudaFuncSetAttribute(gj_panel_cluster_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                      cudaSuccess) {
+    cudaGetLastError();
+    CL = 8;
+  }
+  const size_t smem_cl = sizeof(cx<R>) * (size_t)((n + CL - 1) / CL) * (nb + 1);
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  if (CL > 1) {
+    LS_CUDA_TRY(cudaFuncSetAttribute(gj_panel_cluster_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_cl));
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(P * CL);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem_cl;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, (void*)gj_panel_cluster_kernel<R>, &cfg) != cudaSuccess ||
+        nclusters < 1) {
+      cudaGetLastError();
+      CL = 1;
+    }
+  }
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int w = std::min(nb, n - k0);
     count_launch();
-    gj_panel_kernel<R><<<P, 256, smem_panel, st>>>(X, n, lda, sX, k0, w, piv, perm, H->d_err);
+    if (CL > 1) {
+      LS_CUDA_TRY(cudaLaunchKernelEx(&cfg, gj_panel_cluster_kernel<R>, X, n, lda, sX, k0, w, piv, perm, H->d_err));
+    } else {
+      gj_panel_kernel<R><<<P, 256, smem_panel, st>>>(X, n, lda, sX, k0, w, piv, perm, H->d_err);
+    }
     count_launch();
     gj_swap_extract_kernel<R><<<dim3((n + 127) / 128, P), 128, 0, st>>>(X, n, lda, sX, k0, w, perm, Mb,
                                                                        (long long)w * n);

@@ -301,7 +301,7 @@ int compress_t(ls_handle* H, cudaStream_t st) {
     lv.m = m;
     lv.ring = p;
     const int kmax = std::min(m, p);
-    if (dint) cudaFree(dint);
+    if (dint) ls::dfree(dint);
     dint = nullptr;
     if ((rc = dalloc((void**)&dint, sizeof(int) * (2 * m + 2 * p + 8)))) return rc;
     // blocks and candidates per block (at most 64 per block)
@@ -370,12 +370,15 @@ int compress_t(ls_handle* H, cudaStream_t st) {
     prof_end(tk, PR_CPQR, st, sizeof(cx<R>) * (double)m * p * 2.0 * k,
              36.0 * p * ((double)m * k - 0.5 * (double)k * k));
     if (abort_flag) {
-      cudaFree(wsp);
-      cudaFree(dint);
+      ls::dfree(wsp);
+      ls::dfree(dint);
       return LS_ETIMEOUT;
     }
     std::vector<int> hp(k > 0 ? k : 1);
-    if (k > 0) LS_CUDA_TRY(cudaMemcpy(hp.data(), piv, sizeof(int) * k, cudaMemcpyDeviceToHost));
+    if (k > 0) {
+      LS_CUDA_TRY(cudaMemcpyAsync(hp.data(), piv, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
+      LS_CUDA_TRY(cudaStreamSynchronize(st));
+    }
     lv.k = k;
     lv.skel_x.resize(k);
     lv.skel_y.resize(k);
@@ -387,7 +390,7 @@ int compress_t(ls_handle* H, cudaStream_t st) {
     if (k > 0) LS_CUDA_TRY(cudaMemcpyAsync(lv.U, Ut, sizeof(cx<R>) * (size_t)m * k, cudaMemcpyDeviceToDevice, st));
     LS_CUDA_TRY(cudaStreamSynchronize(st));
     H->flops_compress += 8.0 * 2.0 * (double)m * p * k;  // two projections per pivot step
-    cudaFree(wsp);
+    ls::dfree(wsp);
   }
   // sibling blocks G(skel_a, skel_b) for the two children on level l (Eq. 15)
   for (int l = 1; l <= L; ++l) {
@@ -407,7 +410,7 @@ int compress_t(ls_handle* H, cudaStream_t st) {
       by[i] = lv.skel_y[i] + oby;
     }
     if ((rc = dalloc(&lv.Gsib, sizeof(cx<R>) * (size_t)std::max(kk * kk, 1)))) return rc;
-    if (dint) cudaFree(dint);
+    if (dint) ls::dfree(dint);
     dint = nullptr;
     if ((rc = dalloc((void**)&dint, sizeof(int) * (4 * kk + 8)))) return rc;
     if ((rc = upload_block<R>(ax, ay, bx, by, reinterpret_cast<cx<R>*>(lv.Gsib), dint, st, H->ks_prec, KernelTable{H->ktab, H->ktx, H->kty}))) return rc;
@@ -420,12 +423,12 @@ int compress_t(ls_handle* H, cudaStream_t st) {
         ly.push_back(y);
       }
     if ((rc = dalloc(&H->Gleaf, sizeof(cx<R>) * (size_t)s * s * s * s))) return rc;
-    if (dint) cudaFree(dint);
+    if (dint) ls::dfree(dint);
     dint = nullptr;
     if ((rc = dalloc((void**)&dint, sizeof(int) * (4 * s * s + 8)))) return rc;
     if ((rc = upload_block<R>(lx, ly, lx, ly, reinterpret_cast<cx<R>*>(H->Gleaf), dint, st, H->ks_prec, KernelTable{H->ktab, H->ktx, H->kty}))) return rc;
   }
-  if (dint) cudaFree(dint);
+  if (dint) ls::dfree(dint);
   return LS_OK;
 }
 

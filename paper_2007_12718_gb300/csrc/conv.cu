@@ -256,7 +256,7 @@ int conv_setup(ls_handle* H, cudaStream_t st) {
                                                               H->spec, 1.0 / ((double)H->Lx * H->Ly));
   if ((rc = check_launch("conv_setup"))) return rc;
   LS_CUDA_TRY(cudaStreamSynchronize(st));
-  cudaFree(full);
+  ls::dfree(full);
   return LS_OK;
 }
 
@@ -264,7 +264,7 @@ int conv_apply(ls_handle* H, const z64* x, z64* y, int nrhs, bool field_only, cu
   const int nx = H->grid.nx, ny = H->grid.ny;
   int rc;
   if (H->convbuf_rhs < nrhs) {
-    if (H->convbuf) cudaFree(H->convbuf);
+    if (H->convbuf) ls::dfree(H->convbuf);
     H->convbuf = nullptr;
     H->convbuf_rhs = 0;
     if ((rc = dalloc((void**)&H->convbuf, sizeof(z64) * (size_t)ny * H->Lx * nrhs))) return rc;

@@ -295,7 +295,7 @@ int gmres_solve(ls_handle* H, const z64* f, z64* sigma, int nrhs, ls_solve_info*
   const int m = H->opts.gmres_maxit;
   size_t need = ws_bytes(N, m);
   if (!H->gm || H->gm_bytes < need) {
-    if (H->gm) cudaFree(H->gm);
+    if (H->gm) ls::dfree(H->gm);
     H->gm = nullptr;
     int rc = dalloc(&H->gm, need);
     if (rc) return rc;

@@ -19,6 +19,7 @@ struct LevelData {
 };
 
 struct ls_handle {
+  cudaStream_t stream = nullptr;  // stream of the most recent call (ls_free orders on it)
   ls_grid grid;
   double kappa = 0, tol = 0;
   ls_opts opts;
@@ -74,8 +75,17 @@ int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, cudaStream_t st);
 // gmres.cu
 int gmres_solve(ls_handle* H, const z64* f, z64* sigma, int nrhs, ls_solve_info* info, cudaStream_t st);
 
-// device allocation that records failures as LS_ENOMEM
+// Device allocation from the library's stream-ordered memory pool (one per
+// device, memory kept in the pool between calls), ordered on the stream of the
+// current entry point; failures are recorded as LS_ENOMEM.
 int dalloc(void** p, size_t bytes);
+void dfree(void* p);
+// Sets the stream dalloc/dfree order on for the lifetime of the object.
+struct StreamScope {
+  cudaStream_t prev;
+  explicit StreamScope(cudaStream_t s);
+  ~StreamScope();
+};
 void set_last_error_text(const char* msg);
 int check_launch(const char* what);
 

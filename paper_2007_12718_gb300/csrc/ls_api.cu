@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <string>
 
 #include "handle.h"
@@ -69,7 +70,7 @@ int stage_out_finish(void* p, size_t bytes, cudaStream_t st, Staged* s) {
 }
 
 void release(Staged* s) {
-  if (s->owned && s->dev) cudaFree(s->dev);
+  if (s->owned && s->dev) ls::dfree(s->dev);
   s->dev = nullptr;
   s->owned = false;
 }
@@ -108,10 +109,41 @@ void set_last_error_text(const char* msg) { set_error(msg); }
 static std::atomic<long long> g_launches{0};
 void count_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+namespace {
+thread_local cudaStream_t g_alloc_stream = nullptr;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {nullptr};
+
+int pool_for_current_device(cudaMemPool_t* out) {
+  int dev = 0;
+  LS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return LS_EINVAL;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    LS_CUDA_TRY(cudaMemPoolCreate(&g_pools[dev], &props));
+    unsigned long long keep = ~0ULL;  // keep freed memory in the pool
+    LS_CUDA_TRY(cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+  }
+  *out = g_pools[dev];
+  return LS_OK;
+}
+}  // namespace
+
+StreamScope::StreamScope(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
+StreamScope::~StreamScope() { g_alloc_stream = prev; }
+
 int dalloc(void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaMemPool_t pool;
+  int rc = pool_for_current_device(&pool);
+  if (rc) return rc;
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, g_alloc_stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
     char buf[128];
@@ -121,6 +153,10 @@ int dalloc(void** p, size_t bytes) {
     return LS_ENOMEM;
   }
   return LS_OK;
+}
+
+void dfree(void* p) {
+  if (p) cudaFreeAsync(p, g_alloc_stream);
 }
 
 int check_launch(const char* what) {
@@ -165,9 +201,8 @@ long long ls_kernel_launches(void) { return ls::g_launches.load(); }
 
 void ls_free(ls_handle* H) {
   if (!H) return;
-  auto f = [](void* p) {
-    if (p) cudaFree(p);
-  };
+  ls::StreamScope scope(H->stream);
+  auto f = [](void* p) { ls::dfree(p); };
   f(H->spec);
   f(H->tw_x);
   f(H->tw_y);
@@ -195,6 +230,7 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
                       cudaStream_t st, ls_handle** out) {
   ls_handle* H = new ls_handle();
   *out = H;
+  H->stream = st;
   H->grid = *grid;
   H->kappa = kappa;
   H->tol = tol;
@@ -306,6 +342,7 @@ int ls_build(const ls_grid* grid, double kappa, const double* b, double tol, con
     set_error("invalid ls_build argument");
     return LS_EINVAL;
   }
+  ls::StreamScope scope((cudaStream_t)stream);
   ls_handle* H = nullptr;
   int rc = build_impl(grid, kappa, b, tol, opts, (cudaStream_t)stream, &H);
   if (rc) {
@@ -319,6 +356,8 @@ int ls_build(const ls_grid* grid, double kappa, const double* b, double tol, con
 
 int ls_matvec(ls_handle* H, const void* x, void* y, int nrhs, int transpose, void* stream) {
   if (!H || !x || !y || nrhs < 1 || transpose != 0) return LS_EINVAL;
+  ls::StreamScope scope((cudaStream_t)stream);
+  H->stream = (cudaStream_t)stream;
   cudaStream_t st = (cudaStream_t)stream;
   size_t bytes = sizeof(ls::z64) * (size_t)H->grid.nx * H->grid.ny * nrhs;
   Staged sx, sy;
@@ -334,6 +373,8 @@ int ls_matvec(ls_handle* H, const void* x, void* y, int nrhs, int transpose, voi
 
 int ls_apply(ls_handle* H, const void* f, void* q, int nrhs, int transpose, void* stream) {
   if (!H || !f || !q || nrhs < 1 || transpose != 0) return LS_EINVAL;
+  ls::StreamScope scope((cudaStream_t)stream);
+  H->stream = (cudaStream_t)stream;
   cudaStream_t st = (cudaStream_t)stream;
   size_t bytes = sizeof(ls::z64) * (size_t)H->grid.nx * H->grid.ny * nrhs;
   Staged sf, sq;
@@ -349,6 +390,8 @@ int ls_apply(ls_handle* H, const void* f, void* q, int nrhs, int transpose, void
 
 int ls_solve(ls_handle* H, const void* f, void* sigma, int nrhs, ls_solve_info* info, void* stream) {
   if (!H || !f || !sigma || nrhs < 1) return LS_EINVAL;
+  ls::StreamScope scope((cudaStream_t)stream);
+  H->stream = (cudaStream_t)stream;
   cudaStream_t st = (cudaStream_t)stream;
   size_t bytes = sizeof(ls::z64) * (size_t)H->grid.nx * H->grid.ny * nrhs;
   Staged sf, ss;
@@ -368,6 +411,8 @@ int ls_solve(ls_handle* H, const void* f, void* sigma, int nrhs, ls_solve_info* 
 
 int ls_rhs_plane_wave(ls_handle* H, const double* thetas, void* f, int nrhs, void* stream) {
   if (!H || !thetas || !f || nrhs < 1) return LS_EINVAL;
+  ls::StreamScope scope((cudaStream_t)stream);
+  H->stream = (cudaStream_t)stream;
   cudaStream_t st = (cudaStream_t)stream;
   const long long N = (long long)H->grid.nx * H->grid.ny;
   size_t bytes = sizeof(ls::z64) * N * nrhs;
