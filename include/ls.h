@@ -63,6 +63,8 @@ typedef struct {
   int precision;     /* LS_FP64 or LS_FP32 (default LS_FP32)                              */
   int gmres_maxit;   /* default 100 (Sec. 6.3)                                            */
   double gmres_tol;  /* relative residual, default 1e-10 (Sec. 6.3)                       */
+  int merge_pivoting; /* merge inverses: 0 = blocks without interchanges, checked, with the
+                         row-pivoted inverse as fallback (default); 1 = always row-pivoted   */
 } ls_opts;
 
 typedef struct {
@@ -80,6 +82,7 @@ typedef struct {
   double flops_compress;    /* algorithmic real flops of the per-level IDs */
   double bytes_apply;       /* algorithmic bytes read+written by one HBS apply */
   double factor_bytes;      /* device bytes held by the factors */
+  int pivot_fallbacks;      /* merge levels whose check sent them to the row-pivoted inverse */
 } ls_build_info;
 
 typedef struct ls_handle ls_handle; /* opaque, library-owned */

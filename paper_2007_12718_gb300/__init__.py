@@ -41,7 +41,7 @@ class Grid(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("order_matvec", ctypes.c_int), ("order_precond", ctypes.c_int), ("leaf_side", ctypes.c_int),
                 ("proxy_width", ctypes.c_int), ("precision", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
-                ("gmres_tol", ctypes.c_double)]
+                ("gmres_tol", ctypes.c_double), ("merge_pivoting", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -52,7 +52,8 @@ class SolveInfo(ctypes.Structure):
 class BuildInfo(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("ranks", ctypes.c_int * 32), ("proxy_width", ctypes.c_int),
                 ("flops_build", ctypes.c_double), ("flops_compress", ctypes.c_double),
-                ("bytes_apply", ctypes.c_double), ("factor_bytes", ctypes.c_double)]
+                ("bytes_apply", ctypes.c_double), ("factor_bytes", ctypes.c_double),
+                ("pivot_fallbacks", ctypes.c_int)]
 
 
 class ProfileEntry(ctypes.Structure):
@@ -168,7 +169,8 @@ class Handle:
         _check(load_library().ls_get_build_info(self.ptr, ctypes.byref(bi)), "ls_get_build_info")
         return {"levels": bi.levels, "ranks": list(bi.ranks[: bi.levels + 1]), "proxy_width": bi.proxy_width,
                 "flops_build": bi.flops_build, "flops_compress": bi.flops_compress,
-                "bytes_apply": bi.bytes_apply, "factor_bytes": bi.factor_bytes}
+                "bytes_apply": bi.bytes_apply, "factor_bytes": bi.factor_bytes,
+                "pivot_fallbacks": bi.pivot_fallbacks}
 
 
 def default_opts():
@@ -178,11 +180,13 @@ def default_opts():
 
 
 def ls_build(n, h, kappa, b, tol, order_matvec=10, order_precond=4, leaf_side=8, proxy_width=0,
-             precision=LS_FP32, gmres_maxit=100, gmres_tol=1e-10, x0=0.0, y0=0.0, ny=None, stream=None):
+             precision=LS_FP32, gmres_maxit=100, gmres_tol=1e-10, x0=0.0, y0=0.0, ny=None, stream=None,
+             merge_pivoting=0):
     """Compress G and build the HBS inverse (Sec. 3.2, Algorithm 1); b is [ny][nx] float64."""
     lib = load_library()
     g = Grid(n, n if ny is None else ny, h, x0, y0)
-    o = Opts(order_matvec, order_precond, leaf_side, proxy_width, precision, gmres_maxit, gmres_tol)
+    o = Opts(order_matvec, order_precond, leaf_side, proxy_width, precision, gmres_maxit, gmres_tol,
+             merge_pivoting)
     bp, keep, _ = _ptr(b, np.float64)
     out = ctypes.c_void_p()
     _check(lib.ls_build(ctypes.byref(g), kappa, bp, tol, ctypes.byref(o), _stream(stream), ctypes.byref(out)),

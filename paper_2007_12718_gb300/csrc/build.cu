@@ -725,6 +725,134 @@ __global__ void set_identity_kernel(cx<R>* X, int n, int lda, long long sX, int 
 // Gauss-Jordan, nb columns per panel; each panel is one panel kernel, one
 // interchange/extract kernel and one batched GEMM X += Panel * Mb, so the
 // O(n^3) work is in the GEMM.
+// Blocked Gauss-Jordan without interchanges between diagonal blocks (the
+// merge matrices are I plus a perturbation, Sec. 4.3; partial pivoting stays
+// inside each diagonal block).  Per diagonal block J of width w:
+//   Ab = X[J,J], Mb = X[J,:] (zero on J), Cb = X[:,J] (zero on J)  (extract)
+//   Ab = Ab^-1                                         (in shared memory)
+//   Rb = Ab Mb;   X += -Cb Rb;   X[:,J] = -Cb Ab       (three batched GEMMs)
+//   X[J,:] = Rb, X[J,J] = Ab                           (finalize)
+template <class R>
+__global__ void gjb_extract_kernel(const cx<R>* X, int n, int lda, long long sX, int k0, int w, cx<R>* Ab, cx<R>* Mb,
+                                   cx<R>* Cb) {
+  const int b = blockIdx.y;
+  const cx<R>* M = X + b * sX;
+  const long long tot = (long long)n * w;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    // Mb: w x n (row r of J, column c)
+    int r = (int)(t / n), c = (int)(t % n);
+    bool inJc = c >= k0 && c < k0 + w;
+    Mb[b * tot + t] = inJc ? mk<R>(0, 0) : M[(long long)(k0 + r) * lda + c];
+    if (inJc) Ab[(long long)b * w * w + r * w + (c - k0)] = M[(long long)(k0 + r) * lda + c];
+    // Cb: n x w (row i, column q of J)
+    int i = (int)(t / w), q = (int)(t % w);
+    bool inJr = i >= k0 && i < k0 + w;
+    Cb[b * tot + t] = inJr ? mk<R>(0, 0) : M[(long long)i * lda + k0 + q];
+  }
+}
+
+template <class R>
+__global__ void gjb_finalize_kernel(cx<R>* X, int n, int lda, long long sX, int k0, int w, const cx<R>* Ab,
+                                    const cx<R>* Rb) {
+  const int b = blockIdx.y;
+  cx<R>* M = X + b * sX;
+  const long long tot = (long long)n * w;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(t / n), c = (int)(t % n);
+    bool inJc = c >= k0 && c < k0 + w;
+    M[(long long)(k0 + r) * lda + c] = inJc ? Ab[(long long)b * w * w + r * w + (c - k0)] : Rb[b * tot + t];
+  }
+}
+
+// Probe check of an inverse W of Z = I - Y2 Y1: ||Z (W v) - v|| / ||v|| for a
+// fixed vector v, one block per matrix; the worst value goes to *worst (as
+// float bits, compared by atomicMax on non-negative floats).
+template <class R>
+__global__ void probe_residual_kernel(const cx<R>* W, int n, int lda, long long sW, const cx<R>* Y1, const cx<R>* Y2,
+                                      long long sY, cx<R>* tmp, int* worst) {
+  extern __shared__ unsigned char smraw[];
+  cx<R>* u = reinterpret_cast<cx<R>*>(smraw);  // W v
+  cx<R>* t = u + n;                             // Y1 u
+  const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const cx<R>* Wb = W + b * sW;
+  auto vv = [](int i) {  // fixed probe vector with entries of modulus 1
+    float a = 0.7548776662f * (float)(i + 1);
+    a -= floorf(a);
+    return mk<R>((R)cospif(2.f * a), (R)sinpif(2.f * a));
+  };
+  for (int i = warp; i < n; i += nw) {
+    cx<R> acc = mk<R>(0, 0);
+    for (int j = lane; j < n; j += 32) fma_(acc, Wb[(long long)i * lda + j], vv(j));
+    acc = warp_sum(acc);
+    if (lane == 0) u[i] = acc;
+  }
+  __syncthreads();
+  for (int i = warp; i < n; i += nw) {
+    cx<R> acc = mk<R>(0, 0);
+    for (int j = lane; j < n; j += 32) fma_(acc, Y1[b * sY + (long long)i * n + j], u[j]);
+    acc = warp_sum(acc);
+    if (lane == 0) t[i] = acc;
+  }
+  __syncthreads();
+  float mx = 0.f;
+  for (int i = warp; i < n; i += nw) {
+    cx<R> acc = mk<R>(0, 0);
+    for (int j = lane; j < n; j += 32) fma_(acc, Y2[b * sY + (long long)i * n + j], t[j]);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      cx<R> r = u[i] - acc - vv(i);  // (I - Y2 Y1) W v - v
+      float e = (float)sqrt(abs2(r));
+      if (!(e <= 3e38f)) e = 3e38f;  // NaN or overflow fails the check
+      mx = fmaxf(mx, e);
+    }
+  }
+  if (lane == 0 && mx > 0.f) atomicMax(worst, __float_as_int(mx));
+  (void)tmp;
+}
+
+// dst[b] (rows x cols, row stride ldd) = src[b] (row stride lds), one grid row per matrix b.
+template <class R>
+__global__ void copy_block_kernel(cx<R>* dst, int ldd, long long sD, const cx<R>* src, int lds, long long sS, int rows,
+                                  int cols) {
+  const int b = blockIdx.y;
+  const long long tot = (long long)rows * cols;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t / cols), j = (int)(t % cols);
+    dst[b * sD + (long long)i * ldd + j] = src[b * sS + (long long)i * lds + j];
+  }
+}
+
+template <class R>
+int invert_batch_nopiv(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int P, void* scratch,
+                       size_t scratch_bytes, cudaStream_t st) {
+  const int nb = sizeof(R) == 4 ? 64 : 48;
+  const size_t w_max = nb;
+  cx<R>* Ab = reinterpret_cast<cx<R>*>(scratch);
+  cx<R>* Mb = Ab + (size_t)P * w_max * w_max;
+  cx<R>* Cb = Mb + (size_t)P * w_max * n;
+  cx<R>* Rb = Cb + (size_t)P * w_max * n;
+  if (sizeof(cx<R>) * (size_t)P * (w_max * w_max + 3 * w_max * n) > scratch_bytes) return LS_ENOMEM;
+  const cx<R> mone = mk<R>(R(-1), R(0));
+  for (int k0 = 0; k0 < n; k0 += nb) {
+    const int w = std::min(nb, n - k0);
+    const long long tot = (long long)n * w;
+    dim3 g((unsigned)std::min<long long>(1024, (tot + 255) / 256), P);
+    count_launch();
+    gjb_extract_kernel<R><<<g, 256, 0, st>>>(X, n, lda, sX, k0, w, Ab, Mb, Cb);
+    const size_t smem_small = sizeof(cx<R>) * ((size_t)w * w + w) + sizeof(int) * w;
+    LS_CUDA_TRY(cudaFuncSetAttribute(inverse_smem_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_small));
+    count_launch();
+    inverse_smem_kernel<R><<<P, 256, smem_small, st>>>(Ab, w, w, (long long)w * w, H->d_err);
+    gemm<R>(st, false, false, w, n, w, one<R>(), Ab, w, (long long)w * w, Mb, n, tot, zero<R>(), Rb, n, tot, P);
+    gemm<R>(st, false, false, n, n, w, mone, Cb, w, tot, Rb, n, tot, one<R>(), X, lda, sX, P);
+    gemm<R>(st, false, false, n, w, w, mone, Cb, w, tot, Ab, w, (long long)w * w, zero<R>(), X + k0, lda, sX, P);
+    count_launch();
+    gjb_finalize_kernel<R><<<g, 256, 0, st>>>(X, n, lda, sX, k0, w, Ab, Rb);
+  }
+  return check_launch("inverse_blocked_nopiv");
+}
+
 template <class R>
 int invert_batch(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int P, void* scratch, size_t scratch_bytes,
                  cudaStream_t st) {
@@ -824,6 +952,8 @@ int build_t(ls_handle* H, cudaStream_t st) {
     size_t P = (size_t)1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = l > 0 ? H->lev[l].k : 0;
     wb = std::max(wb, sizeof(cx<R>) * P * n2 * n2 + sizeof(int) * P * n2);
     wb = std::max(wb, sizeof(cx<R>) * 2 * P * n2 * kp);
+    // Y1, Y2, a copy of Z and the blocked-inverse panels (width <= 64)
+    wb = std::max(wb, sizeof(cx<R>) * P * (3 * kc * kc + 64 * 64 + 3 * 64 * kc) + sizeof(int) * P * (n2 + 256) + 4096);
   }
   // apply temporaries (one right-hand side): leaf blocks, per-level expansions
   size_t vec = (size_t)2 * ((size_t)1 << L) * n;
@@ -892,7 +1022,37 @@ int build_t(ls_handle* H, cudaStream_t st) {
       if ((rc = check_launch("merge gemm"))) return rc;
       prof_end(tg, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * (5.0 * kk), P * 3.0 * 8.0 * (double)kc * kc * kc);
       int ti = prof_begin(st);
-      if ((rc = invert_batch<R>(H, X22, kc, n2, sX, P, scratch, scratch_bytes, st))) return rc;  // W
+      // W = Z^-1: blocks without interchanges, checked with a probe vector; the
+      // row-pivoted path is the fallback if the check fails
+      const size_t smem_small = sizeof(cx<R>) * ((size_t)kc * kc + kc) + sizeof(int) * kc;
+      if (smem_small <= 200 * 1024 || H->opts.merge_pivoting == 1) {
+        if ((rc = invert_batch<R>(H, X22, kc, n2, sX, P, scratch, scratch_bytes, st))) return rc;
+      } else {
+        cx<R>* Zc = reinterpret_cast<cx<R>*>(scratch);  // copy of Z for the fallback
+        void* scr2 = Zc + (size_t)P * kk;
+        size_t scr2_bytes = scratch_bytes - sizeof(cx<R>) * (size_t)P * kk;
+        dim3 gc((unsigned)std::min<long long>(1024, (kk + 255) / 256), P);
+        count_launch();
+        copy_block_kernel<R><<<gc, 256, 0, st>>>(Zc, kc, kk, X22, n2, sX, kc, kc);
+        if ((rc = invert_batch_nopiv<R>(H, X22, kc, n2, sX, P, scr2, scr2_bytes, st))) return rc;
+        LS_CUDA_TRY(cudaMemsetAsync(H->d_err + 2, 0, sizeof(int), st));
+        const size_t smem_p = sizeof(cx<R>) * 2 * (size_t)kc;
+        count_launch();
+        probe_residual_kernel<R><<<P, 256, smem_p, st>>>(X22, kc, n2, sX, Y1, Y2, kk, nullptr, H->d_err + 2);
+        int worst_bits = 0;
+        LS_CUDA_TRY(cudaMemcpyAsync(&worst_bits, H->d_err + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LS_CUDA_TRY(cudaStreamSynchronize(st));
+        float worst;
+        memcpy(&worst, &worst_bits, sizeof(float));
+        const float limit = sizeof(R) == 4 ? 1e-3f : 1e-9f;
+        if (!(worst <= limit * sqrtf((float)kc))) {
+          // restore Z and invert with row interchanges
+          count_launch();
+          copy_block_kernel<R><<<gc, 256, 0, st>>>(X22, n2, sX, Zc, kc, kk, kc, kc);
+          if ((rc = invert_batch<R>(H, X22, kc, n2, sX, P, scr2, scr2_bytes, st))) return rc;
+          ++H->pivot_fallbacks;
+        }
+      }
       prof_end(ti, PR_MERGE_INV, st, sizeof(cx<R>) * P * 2.0 * kk, P * 8.0 * (double)kc * kc * kc);
       tg = prof_begin(st);
       gemm<R>(st, false, false, kc, kc, kc, mone, X22, n2, sX, Y2, kc, kk, zero<R>(), X21, n2, sX, P);  // -W Y2

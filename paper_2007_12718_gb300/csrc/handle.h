@@ -50,6 +50,7 @@ struct ls_handle {
   ls::z64** slots = nullptr;    // device-side input/output pointers of the apply graph
   long long apply_nodes = 0;    // kernels in the apply graph
   double flops_build = 0, flops_compress = 0, bytes_apply = 0, factor_bytes = 0;
+  int pivot_fallbacks = 0;      // merge levels that needed the row-pivoted inverse
 
   // GMRES workspace (Sec. 5)
   int gm_maxit = 0, gm_rhs = 0;

@@ -180,6 +180,7 @@ void ls_default_opts(ls_opts* o) {
   o->precision = LS_FP32;
   o->gmres_maxit = 100;
   o->gmres_tol = 1e-10;
+  o->merge_pivoting = 0;
 }
 
 const char* ls_strerror(int code) {
@@ -241,7 +242,7 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
   const ls_opts& o = H->opts;
   if (!valid_order(o.order_matvec) || !valid_order(o.order_precond) || o.order_precond == 2 || o.leaf_side < 2 ||
       o.gmres_maxit < 1 || !(o.gmres_tol > 0) || (o.precision != LS_FP64 && o.precision != LS_FP32) ||
-      o.proxy_width < 0) {
+      o.proxy_width < 0 || o.merge_pivoting < 0 || o.merge_pivoting > 1) {
     set_error("invalid ls_opts");
     return LS_EINVAL;
   }
@@ -440,6 +441,7 @@ int ls_get_build_info(const ls_handle* H, ls_build_info* info) {
   info->flops_compress = H->flops_compress;
   info->bytes_apply = H->bytes_apply;
   info->factor_bytes = H->factor_bytes;
+  info->pivot_fallbacks = H->pivot_fallbacks;
   return LS_OK;
 }
 

@@ -95,6 +95,7 @@ def test_hbs_apply_vs_dense_inverse(precision, eps):
     n, kappa = 32, 20.0
     b = inputs.gaussian_bump(n)
     H = build(n, kappa, b, eps, precision=precision)
+    assert H.info()["pivot_fallbacks"] == 0
     A = nystrom.dense_operator(kappa, 1.0 / n, b, 4)
     for seed in (1, 2):
         f = inputs.random_complex((n, n), seed)
@@ -116,11 +117,13 @@ def test_hbs_direct_solver_order10_vs_lu():
     assert rel(q, ref) < 5 * eps
 
 
-@pytest.mark.parametrize("precision", [ls.LS_FP64, ls.LS_FP32])
-def test_gmres_solve_vs_lu(precision):
+@pytest.mark.parametrize("precision,pivoting", [(ls.LS_FP64, 0), (ls.LS_FP32, 0), (ls.LS_FP32, 1), (ls.LS_FP64, 1)])
+def test_gmres_solve_vs_lu(precision, pivoting):
+    """n = 64 has merge matrices of size ~190 (kc), large enough for the blocked
+    inverses: pivoting 0 = blocks without interchanges (checked), 1 = row-pivoted."""
     n, kappa = 64, 40.0
     b = inputs.gaussian_family(n, 0)
-    H = build(n, kappa, b, 1e-4, precision=precision)
+    H = build(n, kappa, b, 1e-4, precision=precision, merge_pivoting=pivoting)
     f = nystrom.rhs(kappa, b, n, n, 1.0 / n).reshape(n, n)
     sig = torch.zeros(n, n, dtype=torch.complex128, device=DEV)
     info = ls.ls_solve(H, dev(f), sig)[0]
@@ -130,6 +133,7 @@ def test_gmres_solve_vs_lu(precision):
     ref = nystrom.solve_dense(A, f.ravel()).reshape(n, n)
     assert rel(s, ref) < 1e-9
     assert info["iterations"] < 30
+    assert H.info()["pivot_fallbacks"] == 0
 
 
 def test_rhs_plane_wave_matches_oracle():
