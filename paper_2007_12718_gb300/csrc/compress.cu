@@ -15,6 +15,9 @@
 // pivot column is read by every block straight from L2 (no broadcast copy).
 // Sibling blocks G_ab = G(skel_a, skel_b) (Eq. 15) and the leaf block
 // G(I_tau, I_tau) are evaluated on the device at the end.
+#include <cooperative_groups.h>
+#include <string.h>
+
 #include <algorithm>
 
 #include "handle.h"
@@ -234,6 +237,184 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
   }
 }
 
+// The same ID on one thread-block cluster (CL blocks, candidates resident in
+// their shared memory) for proxy blocks that fit: the slots and the winning
+// vector are read through distributed shared memory, the per-step barrier is
+// the cluster barrier.  Slots are double-buffered by step parity so that one
+// barrier per pivot step suffices.  Same outputs as cpqr_id_kernel.
+template <class R>
+__global__ void __launch_bounds__(256) cpqr_id_cluster_kernel(const cx<R>* __restrict__ A, int m, int p, int kmax,
+                                                              double eps, cx<R>* __restrict__ Rm,
+                                                              int* __restrict__ sel, int* __restrict__ piv,
+                                                              int* __restrict__ rank, cx<R>* __restrict__ U,
+                                                              cx<R>* __restrict__ RT) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ unsigned char smraw[];
+  cx<R>* pvec = reinterpret_cast<cx<R>*>(smraw);  // p
+  cx<R>* cand = pvec + p;                          // per x p
+  const int CL = (int)cluster.num_blocks(), crank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
+  const int per = (m + CL - 1) / CL;
+  const int c0 = min(m, crank * per), c1 = min(m, c0 + per), mc = c1 - c0;
+  __shared__ double s_sbest[2], s_stotal[2];
+  __shared__ int s_sidx[2];
+  __shared__ R s_nrm[64];
+  __shared__ int s_sel[64];
+  __shared__ double s_best, s_tol2;
+  __shared__ int s_idx, s_bw, s_stop;
+
+  for (long long t = tid; t < (long long)mc * p; t += blockDim.x) cand[t] = A[(long long)c0 * p + t];
+  __syncthreads();
+  for (int c = warp; c < mc; c += nwarp) {
+    R acc = 0;
+    for (int i = lane; i < p; i += 32) acc += abs2(cand[(long long)c * p + i]);
+    acc = warp_sum_r(acc);
+    if (lane == 0) {
+      s_nrm[c] = acc;
+      s_sel[c] = -1;
+      sel[c0 + c] = -1;
+    }
+  }
+  __syncthreads();
+  int k = 0;
+  for (int j = 0;; ++j) {
+    const int par = j & 1;
+    if (warp == 0) {
+      double best = -1.0, total = 0.0;
+      int idx = -1;
+      for (int c = lane; c < mc; c += 32) {
+        if (s_sel[c] != -1) continue;
+        double v = (double)s_nrm[c];
+        total += v;
+        if (v > best) {
+          best = v;
+          idx = c;
+        }
+      }
+      for (int o = 16; o; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        total += __shfl_xor_sync(0xffffffffu, total, o);
+        if (ob > best || (ob == best && oi >= 0 && (idx < 0 || oi < idx))) {
+          best = ob;
+          idx = oi;
+        }
+      }
+      if (lane == 0) {
+        s_sbest[par] = best;
+        s_stotal[par] = total;
+        s_sidx[par] = idx < 0 ? -1 : c0 + idx;
+      }
+    }
+    cluster.sync();
+    if (warp == 0) {
+      double best = -1.0, total = 0.0;
+      int idx = -1, bw = -1;
+      for (int r = lane; r < CL; r += 32) {
+        double rb = *cluster.map_shared_rank(&s_sbest[par], r);
+        total += *cluster.map_shared_rank(&s_stotal[par], r);
+        int ri = *cluster.map_shared_rank(&s_sidx[par], r);
+        if (ri >= 0 && (rb > best || (rb == best && ri < idx))) {
+          best = rb;
+          idx = ri;
+          bw = r;
+        }
+      }
+      for (int o = 16; o; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        int obw = __shfl_xor_sync(0xffffffffu, bw, o);
+        total += __shfl_xor_sync(0xffffffffu, total, o);
+        if (oi >= 0 && (ob > best || (ob == best && (idx < 0 || oi < idx)))) {
+          best = ob;
+          idx = oi;
+          bw = obw;
+        }
+      }
+      if (lane == 0) {
+        if (j == 0) s_tol2 = eps * eps * total;
+        s_best = best;
+        s_idx = idx;
+        s_bw = bw;
+        s_stop = (j == kmax) || idx < 0 || best <= 0.0 || total <= s_tol2;
+      }
+    }
+    __syncthreads();
+    if (s_stop) {
+      k = j;
+      break;
+    }
+    const int pv = s_idx, bw = s_bw;
+    const R nu = (R)sqrt(s_best);
+    const R inu2 = R(1) / (R)s_best;
+    {
+      const cx<R>* src = cluster.map_shared_rank(cand + (long long)(pv - bw * per) * p, bw);
+      for (int i = tid; i < p; i += blockDim.x) pvec[i] = src[i];
+    }
+    if (crank == bw && tid == 0) {
+      s_sel[pv - c0] = j;
+      sel[pv] = j;
+      piv[j] = pv;
+      Rm[(long long)j * m + pv] = mk<R>(nu, R(0));
+    }
+    __syncthreads();
+    for (int c = warp; c < mc; c += nwarp) {
+      if (s_sel[c] != -1) continue;
+      cx<R>* a = cand + (long long)c * p;
+      cx<R> d = mk<R>(0, 0);
+      for (int i = lane; i < p; i += 32) fmac_(d, pvec[i], a[i]);
+      d = scale(warp_sum(d), inu2);
+      R nr = 0;
+      for (int i = lane; i < p; i += 32) {
+        cx<R> v = a[i], q = pvec[i];
+        v.re -= q.re * d.re - q.im * d.im;
+        v.im -= q.re * d.im + q.im * d.re;
+        a[i] = v;
+        nr += abs2(v);
+      }
+      nr = warp_sum_r(nr);
+      if (lane == 0) {
+        s_nrm[c] = nr;
+        Rm[(long long)j * m + c0 + c] = scale(d, nu);
+      }
+    }
+    __syncthreads();
+  }
+  if (crank == 0 && tid == 0) rank[0] = k;
+  cluster.sync();  // every remote read of candidate vectors is done; piv, Rm complete
+  for (long long t = (long long)crank * blockDim.x + tid; t < (long long)k * k; t += (long long)CL * blockDim.x) {
+    int a = (int)(t / k), bb = (int)(t % k);
+    RT[t] = bb <= a ? Rm[(long long)bb * m + piv[a]] : mk<R>(0, 0);
+  }
+  cluster.sync();
+  cx<R>* t = pvec + (long long)warp * kmax;
+  for (int c = c0 + warp; c < c1; c += nwarp) {
+    int sc = s_sel[c - c0];
+    if (sc >= 0) {
+      for (int a = lane; a < k; a += 32) U[(long long)c * k + a] = mk<R>(a == sc ? R(1) : R(0), R(0));
+      continue;
+    }
+    for (int a = lane; a < k; a += 32) t[a] = Rm[(long long)a * m + c];
+    __syncwarp();
+    for (int a = k - 1; a >= 0; --a) {
+      const cx<R>* col = RT + (long long)a * k;
+      const cx<R> ta = t[a] * inv(col[a]);
+      __syncwarp();
+      for (int bb = lane; bb < a; bb += 32) {
+        cx<R> v = t[bb], r = col[bb];
+        v.re -= r.re * ta.re - r.im * ta.im;
+        v.im -= r.re * ta.im + r.im * ta.re;
+        t[bb] = v;
+      }
+      if (lane == 0) t[a] = ta;
+      __syncwarp();
+    }
+    for (int a = lane; a < k; a += 32) U[(long long)c * k + a] = t[a];
+    __syncwarp();
+  }
+}
+
 template <class R>
 int upload_block(const std::vector<int>& rx, const std::vector<int>& ry, const std::vector<int>& px,
                  const std::vector<int>& py, cx<R>* out, int* dtmp, cudaStream_t st, const KernelSpec& ks,
@@ -342,26 +523,64 @@ int compress_t(ls_handle* H, cudaStream_t st) {
     IdSlot* slots = reinterpret_cast<IdSlot*>(carve(sizeof(IdSlot) * 2 * (nblk + 1)));
     wsp = wbase;
     if ((rc = upload_block<R>(rows_x, rows_y, px, py, A, dint, st, H->ks_prec, KernelTable{H->ktab, H->ktx, H->kty}))) return rc;
-    const void* kfn = (const void*)cpqr_id_kernel<R>;
-    LS_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, smem));
-    if (per_sm < 1 || nblk > per_sm * H->nsm) {
-      set_last_error_text("ID kernel cannot be co-resident");
-      return LS_EINVAL;
+    // one cluster when the candidates fit in the shared memory of CL blocks
+    int CL = 16;
+    if (cudaFuncSetAttribute(cpqr_id_cluster_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      CL = 8;
     }
-    LS_CUDA_TRY(cudaMemsetAsync(H->sync_buf, 0, 64, st));
-    GridSync gs;
-    gs.count = reinterpret_cast<unsigned*>(H->sync_buf);
-    gs.gen = reinterpret_cast<unsigned*>(H->sync_buf) + 1;
-    gs.abort = H->sync_buf + 2;
+    const int per_cl = (m + CL - 1) / CL;
+    const size_t smem_cl = std::max(sizeof(cx<R>) * ((size_t)p + (size_t)per_cl * p), tail_smem);
+    bool use_cluster = per_cl <= 64 && smem_cl <= 200 * 1024;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    if (use_cluster) {
+      LS_CUDA_TRY(cudaFuncSetAttribute(cpqr_id_cluster_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_cl));
+      memset(&cfg, 0, sizeof(cfg));
+      cfg.gridDim = dim3(CL);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = smem_cl;
+      cfg.stream = st;
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = CL;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int ncl = 0;
+      if (cudaOccupancyMaxActiveClusters(&ncl, (void*)cpqr_id_cluster_kernel<R>, &cfg) != cudaSuccess || ncl < 1) {
+        cudaGetLastError();
+        use_cluster = false;
+      }
+    }
     double eps = H->tol;
-    const cx<R>* Ac = A;
-    void* args[] = {&Ac, (void*)&m, (void*)&p, (void*)&kmax, &eps, &use_smem, &Aw, &Rm, &sel, &slots, &pslots,
-                    &piv, &rank, &Ut, &RT, &gs};
+    LS_CUDA_TRY(cudaMemsetAsync(H->sync_buf, 0, 64, st));
     int tk = prof_begin(st);
-    count_launch();
-    LS_CUDA_TRY(cudaLaunchCooperativeKernel(kfn, dim3(nblk), dim3(256), args, smem, st));
+    if (use_cluster) {
+      count_launch();
+      LS_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpqr_id_cluster_kernel<R>, (const cx<R>*)A, m, p, kmax, eps, Rm, sel, piv,
+                                     rank, Ut, RT));
+    } else {
+      const void* kfn = (const void*)cpqr_id_kernel<R>;
+      LS_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      int per_sm = 0;
+      LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, smem));
+      if (per_sm < 1 || nblk > per_sm * H->nsm) {
+        set_last_error_text("ID kernel cannot be co-resident");
+        return LS_EINVAL;
+      }
+      GridSync gs;
+      gs.count = reinterpret_cast<unsigned*>(H->sync_buf);
+      gs.gen = reinterpret_cast<unsigned*>(H->sync_buf) + 1;
+      gs.abort = H->sync_buf + 2;
+      const cx<R>* Ac = A;
+      void* args[] = {&Ac, (void*)&m, (void*)&p, (void*)&kmax, &eps, &use_smem, &Aw, &Rm, &sel, &slots, &pslots,
+                      &piv, &rank, &Ut, &RT, &gs};
+      count_launch();
+      LS_CUDA_TRY(cudaLaunchCooperativeKernel(kfn, dim3(nblk), dim3(256), args, smem, st));
+    }
     int k = 0, abort_flag = 0;
     LS_CUDA_TRY(cudaMemcpyAsync(&k, rank, sizeof(int), cudaMemcpyDeviceToHost, st));
     LS_CUDA_TRY(cudaMemcpyAsync(&abort_flag, H->sync_buf + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
