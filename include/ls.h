@@ -46,8 +46,12 @@ enum {
 };
 
 /* Precision of the HBS preconditioner (compression, inverse build, apply).
- * The FFT matvec and GMRES are FP64 in every mode. */
-enum { LS_FP64 = 0, LS_FP32 = 1 };
+ * The FFT matvec and GMRES are FP64 in every mode.  LS_FP32, LS_TF32 and
+ * LS_TF32X3 all store the factors in FP32; they differ in the engine of the
+ * merge GEMMs (Eqs. 26-27): FP32 SIMT cores, tensor cores with tf32 inputs
+ * (FP32 accumulation), or tensor cores with each operand split into two tf32
+ * terms (three products, ~FP32 accuracy). */
+enum { LS_FP64 = 0, LS_FP32 = 1, LS_TF32 = 2, LS_TF32X3 = 3 };
 
 typedef struct {
   int nx, ny;        /* grid size; a tree of square leaves must fit (see ls_build) */
@@ -60,7 +64,7 @@ typedef struct {
   int order_precond; /* order used inside the HBS compression: 4,6,8,10 (default 4)      */
   int leaf_side;     /* leaf box side s (s*s points per leaf, default 8)                  */
   int proxy_width;   /* proxy ring width in grid cells; 0 = from tol and order (default)  */
-  int precision;     /* LS_FP64 or LS_FP32 (default LS_FP32)                              */
+  int precision;     /* LS_FP64, LS_FP32, LS_TF32 or LS_TF32X3 (default LS_FP32)          */
   int gmres_maxit;   /* default 100 (Sec. 6.3)                                            */
   double gmres_tol;  /* relative residual, default 1e-10 (Sec. 6.3)                       */
   int merge_pivoting; /* merge inverses: 0 = blocks without interchanges, checked, with the
@@ -178,6 +182,17 @@ int ls_profile_get(ls_profile_entry* out, int max_entries);
 
 /* Number of CUDA kernels this library has launched in this process so far. */
 long long ls_kernel_launches(void);
+
+/* ls_cgemm_c64 -- building block exposed for testing: the batched complex
+ * FP32 GEMM the HBS build uses for its merge products,
+ *   C[b] = alpha op(A[b]) op(B[b]) + beta C[b],   b < batch,
+ * row-major interleaved complex64, op = transpose (no conjugate) when ta/tb.
+ * engine: 0 = FP32 SIMT, 1 = tcgen05 tf32, 2 = tcgen05 tf32x3.  alpha, beta:
+ * {re, im} pairs.  All pointers on the device.  Returns LS_EINVAL for a bad
+ * engine or size, LS_ETIMEOUT if a tensor-core wait gave up. */
+int ls_cgemm_c64(int engine, int ta, int tb, int M, int N, int K, const float* alpha, const void* A, int lda,
+                 long long sA, const void* B, int ldb, long long sB, const float* beta, void* C, int ldc,
+                 long long sC, int batch, void* stream);
 
 /* Static text for an LS_E* code, and the last error message of this thread. */
 const char* ls_strerror(int code);

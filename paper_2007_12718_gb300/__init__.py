@@ -25,12 +25,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libls.so")
 
 LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ESINGULAR, LS_ENOCONV, LS_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
-LS_FP64, LS_FP32 = 0, 1
+LS_FP64, LS_FP32, LS_TF32, LS_TF32X3 = 0, 1, 2, 3
 
 EXPORTED = ["ls_default_opts", "ls_build", "ls_apply", "ls_matvec", "ls_solve", "ls_rhs_plane_wave",
             "ls_get_build_info", "ls_free", "ls_strerror", "ls_last_error", "ls_profile_enable",
             "ls_profile_reset", "ls_profile_get", "ls_kernel_launches", "ls_matvec_noalloc",
-            "ls_matvec_noalloc_max_elems"]
+            "ls_matvec_noalloc_max_elems", "ls_cgemm_c64"]
 
 
 class Grid(ctypes.Structure):
@@ -103,6 +103,10 @@ def load_library(path=LIB_PATH):
     lib.ls_matvec_noalloc.restype = ip
     lib.ls_matvec_noalloc_max_elems.argtypes = []
     lib.ls_matvec_noalloc_max_elems.restype = ctypes.c_longlong
+    lib.ls_cgemm_c64.argtypes = [ip, ip, ip, ip, ip, ip, ctypes.POINTER(ctypes.c_float), vp, ip, ctypes.c_longlong,
+                                 vp, ip, ctypes.c_longlong, ctypes.POINTER(ctypes.c_float), vp, ip, ctypes.c_longlong,
+                                 ip, vp]
+    lib.ls_cgemm_c64.restype = ip
     lib.ls_kernel_launches.argtypes = []
     lib.ls_kernel_launches.restype = ctypes.c_longlong
     _lib = lib
@@ -257,6 +261,27 @@ def ls_profile_get():
     n = load_library().ls_profile_get(buf, 32)
     return {e.name.decode(): {"launches": e.launches, "total_ms": e.total_ms, "bytes": e.bytes,
                               "flops": e.flops} for e in buf[:n]}
+
+
+def ls_cgemm_c64(engine, A, B, C, ta=False, tb=False, alpha=1.0, beta=0.0, stream=None):
+    """C = alpha op(A) op(B) + beta C on batched complex64 device tensors [batch, rows, cols]
+    (engine 0 SIMT, 1 tcgen05 tf32, 2 tcgen05 tf32x3)."""
+    import torch
+    for t in (A, B, C):
+        if not (isinstance(t, torch.Tensor) and t.dtype == torch.complex64 and t.is_cuda and t.is_contiguous()):
+            raise TypeError("expected contiguous complex64 CUDA tensors")
+    batch = C.shape[0]
+    M, N = C.shape[1], C.shape[2]
+    K = A.shape[1] if ta else A.shape[2]
+    al = (ctypes.c_float * 2)(complex(alpha).real, complex(alpha).imag)
+    be = (ctypes.c_float * 2)(complex(beta).real, complex(beta).imag)
+    sa = A.shape[1] * A.shape[2] if A.shape[0] > 1 else 0
+    sb = B.shape[1] * B.shape[2] if B.shape[0] > 1 else 0
+    _check(load_library().ls_cgemm_c64(engine, int(ta), int(tb), M, N, K, al, ctypes.c_void_p(A.data_ptr()),
+                                       A.shape[2], sa, ctypes.c_void_p(B.data_ptr()), B.shape[2], sb, be,
+                                       ctypes.c_void_p(C.data_ptr()), C.shape[2], M * N, batch, _stream(stream)),
+           "ls_cgemm_c64")
+    return C
 
 
 def ls_kernel_launches():

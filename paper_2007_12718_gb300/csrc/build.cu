@@ -182,11 +182,22 @@ __global__ void __launch_bounds__(256) gemm64_kernel(int M, int N, int K, cx<R> 
     }
 }
 
+// Engine of the FP32 merge GEMMs for the build in progress on this thread:
+// 0 = SIMT FP32, 1 = tensor cores tf32, 2 = tensor cores tf32x3.
+thread_local int g_tc_engine = 0;
+thread_local int* g_tc_err = nullptr;
+
 template <class R>
 void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, cx<R> alpha, const cx<R>* A, int lda, long long sA,
           const cx<R>* B, int ldb, long long sB, cx<R> beta, cx<R>* C, int ldc, long long sC, int batch) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   if (K <= 0) return;  // only reached with beta = 1 (nothing to add)
+  if (sizeof(R) == 4 && g_tc_engine > 0) {
+    tc_cgemm(st, ta, tb, M, N, K, *reinterpret_cast<const c32*>(&alpha), reinterpret_cast<const c32*>(A), lda, sA,
+             reinterpret_cast<const c32*>(B), ldb, sB, *reinterpret_cast<const c32*>(&beta),
+             reinterpret_cast<c32*>(C), ldc, sC, batch, g_tc_engine == 2 ? 1 : 0, g_tc_err);
+    return;
+  }
   count_launch();
   if (M >= 48 && N >= 48) {
     dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
@@ -224,10 +235,10 @@ template <class R>
 __device__ bool gj_inverse_smem(cx<R>* a, int n, int lda, int* piv, cx<R>* col) {
   __shared__ int s_p;
   __shared__ int s_bad;
-  if (threadIdx.x == 0) s_bad = 0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ cx<R> s_d;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int k = 0; k < n; ++k) {
-    if (warp == 0) {
+    if (warp == 0) {  // pivot: largest |a(i,k)| over i >= k, lowest row on ties
       R best = R(-1);
       int bi = n;
       for (int i = k + lane; i < n; i += 32) {
@@ -248,36 +259,42 @@ __device__ bool gj_inverse_smem(cx<R>* a, int n, int lda, int* piv, cx<R>* col) 
       if (lane == 0) {
         s_p = bi;
         piv[k] = bi;
-        if (!(best > R(0))) s_bad = 1;
+        s_bad = !(best > R(0));
+        if (!s_bad) s_d = inv(a[bi * lda + k]);
       }
     }
     __syncthreads();
     if (s_bad) return false;
     const int p = s_p;
-    if (p != k)
-      for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        cx<R> t = a[k * lda + j];
-        a[k * lda + j] = a[p * lda + j];
-        a[p * lda + j] = t;
+    const cx<R> d = s_d;
+    // multipliers of column k after the interchange; rows k and p exchanged
+    // (and the new row k scaled by d) in every column except k
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      col[i] = (i == k) ? a[p * lda + k] : (i == p ? a[k * lda + k] : a[i * lda + k]);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      if (j == k) continue;
+      cx<R> tk = a[k * lda + j], tp = a[p * lda + j];
+      if (p != k) a[p * lda + j] = tk;
+      a[k * lda + j] = tp * d;
+    }
+    __syncthreads();
+    for (int i = warp; i < n; i += nwarp) {
+      cx<R>* arow = a + i * lda;
+      if (i == k) {
+        if (lane == 0) arow[k] = d;
+        continue;
       }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = a[i * lda + k];
-    __syncthreads();
-    const cx<R> d = inv(col[k]);
-    for (int j = threadIdx.x; j < n; j += blockDim.x) a[k * lda + j] = (j == k) ? d : a[k * lda + j] * d;
-    __syncthreads();
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-      int i = t / n, j = t % n;
-      if (i == k) continue;
-      cx<R> f = col[i];
-      if (j == k)
-        a[i * lda + j] = mk<R>(-(f.re * d.re - f.im * d.im), -(f.re * d.im + f.im * d.re));
-      else {
-        cx<R> r = a[k * lda + j];
-        cx<R> v = a[i * lda + j];
-        v.re -= f.re * r.re - f.im * r.im;
-        v.im -= f.re * r.im + f.im * r.re;
-        a[i * lda + j] = v;
+      const cx<R> f = col[i];
+      const cx<R>* krow = a + k * lda;
+      for (int j = lane; j < n; j += 32) {
+        if (j == k) {
+          arow[j] = mk<R>(-(f.re * d.re - f.im * d.im), -(f.re * d.im + f.im * d.re));
+        } else {
+          cx<R> r = krow[j], v = arow[j];
+          v.re -= f.re * r.re - f.im * r.im;
+          v.im -= f.re * r.im + f.im * r.re;
+          arow[j] = v;
+        }
       }
     }
     __syncthreads();
@@ -320,13 +337,14 @@ __global__ void __launch_bounds__(256) leaf_build_kernel(TreeGeom g, const doubl
                                                          int k, cx<R>* __restrict__ X, cx<R>* __restrict__ XBU,
                                                          cx<R>* __restrict__ S, int* __restrict__ err) {
   extern __shared__ unsigned char smraw[];
-  const int n = g.s * g.s;
-  cx<R>* a = reinterpret_cast<cx<R>*>(smraw);  // n x n
-  cx<R>* xbu = a + n * n;                      // n x k
+  const int n = g.s * g.s, ls = n + 1;         // odd row stride (no bank conflicts on columns)
+  cx<R>* a = reinterpret_cast<cx<R>*>(smraw);  // n x n, stride ls
+  cx<R>* xbu = a + n * ls;                     // n x k
   cx<R>* col = xbu + n * k;                    // n
   R* Bv = reinterpret_cast<R*>(col + n);       // n
   int* piv = reinterpret_cast<int*>(Bv + n);   // n
   const int leaf = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int ox, oy;
   leaf_origin(g, leaf, ox, oy);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -334,14 +352,14 @@ __global__ void __launch_bounds__(256) leaf_build_kernel(TreeGeom g, const doubl
     Bv[i] = (R)(kap2 * b[(long long)(oy + ly) * g.nx + ox + lx]);
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    int i = t / n, j = t % n;
-    cx<R> v = scale(Gleaf[t], Bv[i]);
-    if (i == j) v.re += R(1);
-    a[t] = v;
-  }
+  for (int i = warp; i < n; i += 8)
+    for (int j = lane; j < n; j += 32) {
+      cx<R> v = scale(Gleaf[i * n + j], Bv[i]);
+      if (i == j) v.re += R(1);
+      a[i * ls + j] = v;
+    }
   __syncthreads();
-  if (!gj_inverse_smem(a, n, n, piv, col)) {
+  if (!gj_inverse_smem(a, n, ls, piv, col)) {
     if (threadIdx.x == 0) atomicExch(err, LS_ESINGULAR);
     return;
   }
@@ -349,12 +367,13 @@ __global__ void __launch_bounds__(256) leaf_build_kernel(TreeGeom g, const doubl
   for (int t = threadIdx.x; t < n * k; t += blockDim.x) {
     int i = t / k, c = t % k;
     cx<R> acc = mk<R>(0, 0);
-    for (int j = 0; j < n; ++j) fma_(acc, a[i * n + j], scale(U[j * k + c], Bv[j]));
+    for (int j = 0; j < n; ++j) fma_(acc, a[i * ls + j], scale(U[j * k + c], Bv[j]));
     xbu[t] = acc;
   }
   __syncthreads();
   cx<R>* Xo = X + (long long)leaf * n * n;
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Xo[t] = a[t];
+  for (int i = warp; i < n; i += 8)
+    for (int j = lane; j < n; j += 32) Xo[i * n + j] = a[i * ls + j];
   cx<R>* XBUo = XBU + (long long)leaf * n * k;
   for (int t = threadIdx.x; t < n * k; t += blockDim.x) XBUo[t] = xbu[t];
   // S = U^T XBU
@@ -371,17 +390,21 @@ __global__ void __launch_bounds__(256) leaf_build_kernel(TreeGeom g, const doubl
 template <class R>
 __global__ void __launch_bounds__(256) inverse_smem_kernel(cx<R>* X, int n, int lda, long long sX, int* err) {
   extern __shared__ unsigned char smraw[];
+  const int ls = n + 1;  // odd row stride: column reads without bank conflicts
   cx<R>* a = reinterpret_cast<cx<R>*>(smraw);
-  cx<R>* col = a + n * n;
+  cx<R>* col = a + n * ls;
   int* piv = reinterpret_cast<int*>(col + n);
   cx<R>* M = X + blockIdx.x * sX;
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) a[t] = M[(long long)(t / n) * lda + t % n];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < n; i += 8)
+    for (int j = lane; j < n; j += 32) a[i * ls + j] = M[(long long)i * lda + j];
   __syncthreads();
-  if (!gj_inverse_smem(a, n, n, piv, col)) {
+  if (!gj_inverse_smem(a, n, ls, piv, col)) {
     if (threadIdx.x == 0) atomicExch(err, LS_ESINGULAR);
     return;
   }
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) M[(long long)(t / n) * lda + t % n] = a[t];
+  for (int i = warp; i < n; i += 8)
+    for (int j = lane; j < n; j += 32) M[(long long)i * lda + j] = a[i * ls + j];
 }
 
 // Blocked Gauss-Jordan inversion, panel step (one block per matrix).  The nb
@@ -764,50 +787,30 @@ __global__ void gjb_finalize_kernel(cx<R>* X, int n, int lda, long long sX, int 
   }
 }
 
-// Probe check of an inverse W of Z = I - Y2 Y1: ||Z (W v) - v|| / ||v|| for a
-// fixed vector v, one block per matrix; the worst value goes to *worst (as
-// float bits, compared by atomicMax on non-negative floats).
+// Probe check of an inverse W of Z = I - Y2 Y1 with a fixed vector v of
+// unit-modulus entries: r = Z (W v) - v, formed with the batched GEMV kernels;
+// probe_max_kernel folds max_i |r_i| over all matrices into *worst (float bits,
+// atomicMax on non-negative floats; NaN or overflow counts as 3e38).
 template <class R>
-__global__ void probe_residual_kernel(const cx<R>* W, int n, int lda, long long sW, const cx<R>* Y1, const cx<R>* Y2,
-                                      long long sY, cx<R>* tmp, int* worst) {
-  extern __shared__ unsigned char smraw[];
-  cx<R>* u = reinterpret_cast<cx<R>*>(smraw);  // W v
-  cx<R>* t = u + n;                             // Y1 u
-  const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const cx<R>* Wb = W + b * sW;
-  auto vv = [](int i) {  // fixed probe vector with entries of modulus 1
-    float a = 0.7548776662f * (float)(i + 1);
-    a -= floorf(a);
-    return mk<R>((R)cospif(2.f * a), (R)sinpif(2.f * a));
-  };
-  for (int i = warp; i < n; i += nw) {
-    cx<R> acc = mk<R>(0, 0);
-    for (int j = lane; j < n; j += 32) fma_(acc, Wb[(long long)i * lda + j], vv(j));
-    acc = warp_sum(acc);
-    if (lane == 0) u[i] = acc;
-  }
-  __syncthreads();
-  for (int i = warp; i < n; i += nw) {
-    cx<R> acc = mk<R>(0, 0);
-    for (int j = lane; j < n; j += 32) fma_(acc, Y1[b * sY + (long long)i * n + j], u[j]);
-    acc = warp_sum(acc);
-    if (lane == 0) t[i] = acc;
-  }
-  __syncthreads();
+__global__ void probe_vector_kernel(cx<R>* v, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float a = 0.7548776662f * (float)(i + 1);
+  a -= floorf(a);
+  v[i] = mk<R>((R)cospif(2.f * a), (R)sinpif(2.f * a));
+}
+
+template <class R>
+__global__ void probe_max_kernel(const cx<R>* r, const cx<R>* v, int n, long long total, int* worst) {
   float mx = 0.f;
-  for (int i = warp; i < n; i += nw) {
-    cx<R> acc = mk<R>(0, 0);
-    for (int j = lane; j < n; j += 32) fma_(acc, Y2[b * sY + (long long)i * n + j], t[j]);
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      cx<R> r = u[i] - acc - vv(i);  // (I - Y2 Y1) W v - v
-      float e = (float)sqrt(abs2(r));
-      if (!(e <= 3e38f)) e = 3e38f;  // NaN or overflow fails the check
-      mx = fmaxf(mx, e);
-    }
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    cx<R> e = r[t] - v[t % n];
+    float x = (float)sqrt(abs2(e));
+    if (!(x <= 3e38f)) x = 3e38f;
+    mx = fmaxf(mx, x);
   }
-  if (lane == 0 && mx > 0.f) atomicMax(worst, __float_as_int(mx));
-  (void)tmp;
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.f) atomicMax(worst, __float_as_int(mx));
 }
 
 // dst[b] (rows x cols, row stride ldd) = src[b] (row stride lds), one grid row per matrix b.
@@ -821,6 +824,10 @@ __global__ void copy_block_kernel(cx<R>* dst, int ldd, long long sD, const cx<R>
     dst[b * sD + (long long)i * ldd + j] = src[b * sS + (long long)i * lds + j];
   }
 }
+
+template <class R>
+void gemv(cudaStream_t st, bool ta, int M, int K, cx<R> alpha, const cx<R>* A, int lda, long long sA, const cx<R>* x,
+          long long sx, cx<R> beta, cx<R>* y, long long sy, int batch);
 
 template <class R>
 int invert_batch_nopiv(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int P, void* scratch,
@@ -839,7 +846,7 @@ int invert_batch_nopiv(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int
     dim3 g((unsigned)std::min<long long>(1024, (tot + 255) / 256), P);
     count_launch();
     gjb_extract_kernel<R><<<g, 256, 0, st>>>(X, n, lda, sX, k0, w, Ab, Mb, Cb);
-    const size_t smem_small = sizeof(cx<R>) * ((size_t)w * w + w) + sizeof(int) * w;
+    const size_t smem_small = sizeof(cx<R>) * ((size_t)w * (w + 1) + w) + sizeof(int) * w;
     LS_CUDA_TRY(cudaFuncSetAttribute(inverse_smem_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem_small));
     count_launch();
@@ -856,7 +863,7 @@ int invert_batch_nopiv(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int
 template <class R>
 int invert_batch(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int P, void* scratch, size_t scratch_bytes,
                  cudaStream_t st) {
-  const size_t smem_small = sizeof(cx<R>) * ((size_t)n * n + n) + sizeof(int) * n;
+  const size_t smem_small = sizeof(cx<R>) * ((size_t)n * (n + 1) + n) + sizeof(int) * n;
   if (smem_small <= 200 * 1024) {
     LS_CUDA_TRY(cudaFuncSetAttribute(inverse_smem_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem_small));
@@ -946,6 +953,16 @@ template <class R>
 int build_t(ls_handle* H, cudaStream_t st) {
   const int L = H->L, n = H->s * H->s;
   int rc;
+  struct EngineScope {
+    explicit EngineScope(ls_handle* H) {
+      g_tc_engine = H->prec == LS_TF32 ? 1 : H->prec == LS_TF32X3 ? 2 : 0;
+      g_tc_err = H->d_err;
+    }
+    ~EngineScope() {
+      g_tc_engine = 0;
+      g_tc_err = nullptr;
+    }
+  } engine_scope(H);
   // scratch: the largest of (cooperative inverse ping-pong + pivots) and the merge GEMM temporaries
   size_t wb = 0;
   for (int l = 0; l < L; ++l) {
@@ -971,7 +988,7 @@ int build_t(ls_handle* H, cudaStream_t st) {
   if ((rc = dalloc(&lf.S, sizeof(cx<R>) * nleaf * std::max(kL * kL, 1)))) return rc;
   H->factor_bytes += sizeof(cx<R>) * nleaf * ((double)n * n + (double)n * kL + (double)kL * kL);
   TreeGeom g = make_geom(H);
-  size_t smem = sizeof(cx<R>) * ((size_t)n * n + (size_t)n * kL + n) + sizeof(R) * n + sizeof(int) * n + 64;
+  size_t smem = sizeof(cx<R>) * ((size_t)n * (n + 1) + (size_t)n * kL + n) + sizeof(R) * n + sizeof(int) * n + 64;
   LS_CUDA_TRY(cudaFuncSetAttribute(leaf_build_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int tk = prof_begin(st);
   count_launch();
@@ -1024,7 +1041,7 @@ int build_t(ls_handle* H, cudaStream_t st) {
       int ti = prof_begin(st);
       // W = Z^-1: blocks without interchanges, checked with a probe vector; the
       // row-pivoted path is the fallback if the check fails
-      const size_t smem_small = sizeof(cx<R>) * ((size_t)kc * kc + kc) + sizeof(int) * kc;
+      const size_t smem_small = sizeof(cx<R>) * ((size_t)kc * (kc + 1) + kc) + sizeof(int) * kc;
       if (smem_small <= 200 * 1024 || H->opts.merge_pivoting == 1) {
         if ((rc = invert_batch<R>(H, X22, kc, n2, sX, P, scratch, scratch_bytes, st))) return rc;
       } else {
@@ -1036,9 +1053,20 @@ int build_t(ls_handle* H, cudaStream_t st) {
         copy_block_kernel<R><<<gc, 256, 0, st>>>(Zc, kc, kk, X22, n2, sX, kc, kc);
         if ((rc = invert_batch_nopiv<R>(H, X22, kc, n2, sX, P, scr2, scr2_bytes, st))) return rc;
         LS_CUDA_TRY(cudaMemsetAsync(H->d_err + 2, 0, sizeof(int), st));
-        const size_t smem_p = sizeof(cx<R>) * 2 * (size_t)kc;
-        count_launch();
-        probe_residual_kernel<R><<<P, 256, smem_p, st>>>(X22, kc, n2, sX, Y1, Y2, kk, nullptr, H->d_err + 2);
+        {
+          cx<R>* pv = reinterpret_cast<cx<R>*>(scr2);  // v (kc), then u, t, r (P kc each)
+          cx<R>* pu = pv + kc;
+          cx<R>* pt = pu + (size_t)P * kc;
+          cx<R>* pr = pt + (size_t)P * kc;
+          count_launch();
+          probe_vector_kernel<R><<<(kc + 255) / 256, 256, 0, st>>>(pv, kc);
+          gemv<R>(st, false, kc, kc, one<R>(), X22, n2, sX, pv, 0, zero<R>(), pu, kc, P);
+          gemv<R>(st, false, kc, kc, one<R>(), Y1, kc, kk, pu, kc, zero<R>(), pt, kc, P);
+          LS_CUDA_TRY(cudaMemcpyAsync(pr, pu, sizeof(cx<R>) * (size_t)P * kc, cudaMemcpyDeviceToDevice, st));
+          gemv<R>(st, false, kc, kc, mk<R>(R(-1), R(0)), Y2, kc, kk, pt, kc, one<R>(), pr, kc, P);
+          count_launch();
+          probe_max_kernel<R><<<64, 256, 0, st>>>(pr, pv, kc, (long long)P * kc, H->d_err + 2);
+        }
         int worst_bits = 0;
         LS_CUDA_TRY(cudaMemcpyAsync(&worst_bits, H->d_err + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
         LS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1296,6 +1324,12 @@ int hbs_apply_graph_init(ls_handle* H) {
 
 int hbs_build(ls_handle* H, cudaStream_t st) {
   return H->prec == LS_FP64 ? build_t<double>(H, st) : build_t<float>(H, st);
+}
+
+int simt_cgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, c32 alpha, const c32* A, int lda, long long sA,
+               const c32* B, int ldb, long long sB, c32 beta, c32* C, int ldc, long long sC, int batch) {
+  gemm<float>(st, ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
+  return check_launch("simt_cgemm");
 }
 
 int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, cudaStream_t st) {

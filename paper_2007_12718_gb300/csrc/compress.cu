@@ -37,10 +37,11 @@ __global__ void block_kernel(const int* __restrict__ rx, const int* __restrict__
   out[(long long)c * ld + q] = cvt<R>(v);
 }
 
+template <class R>
 struct IdSlot {
-  double best;   // largest residual norm^2 among the block's active candidates
-  double total;  // sum of residual norm^2 over the block's active candidates
-  int idx;       // candidate index of best (lowest index on ties), -1 if none
+  R best;   // largest residual norm^2 among the block's active candidates
+  R total;  // sum of residual norm^2 over the block's active candidates
+  int idx;  // candidate index of best (lowest index on ties), -1 if none
   int pad;
 };
 
@@ -57,7 +58,7 @@ template <class R>
 __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ A, int m, int p, int kmax,
                                                       double eps, int use_smem, cx<R>* __restrict__ Aw,
                                                       cx<R>* __restrict__ Rm, int* __restrict__ sel,
-                                                      IdSlot* __restrict__ slots, cx<R>* __restrict__ pslots,
+                                                      IdSlot<R>* __restrict__ slots, cx<R>* __restrict__ pslots,
                                                       int* __restrict__ piv, int* __restrict__ rank,
                                                       cx<R>* __restrict__ U, cx<R>* __restrict__ RT, GridSync gs) {
   extern __shared__ unsigned char smraw[];
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
   cx<R>* cand = use_smem ? pvec + p : Aw + (long long)c0 * p;
   __shared__ R s_nrm[64];
   __shared__ int s_sel[64];
-  __shared__ double s_best, s_tol2;
+  __shared__ R s_best, s_tol2;
   __shared__ int s_idx, s_bw, s_stop, s_lbest;
   unsigned int epoch = 0;
 
@@ -91,11 +92,11 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
   for (int j = 0;; ++j) {
     const int par = j & 1;
     if (warp == 0) {  // local best and total over this block's active candidates
-      double best = -1.0, total = 0.0;
+      R best = R(-1), total = R(0);
       int idx = -1;
       for (int c = lane; c < mc; c += 32) {
         if (s_sel[c] != -1) continue;
-        double v = (double)s_nrm[c];
+        R v = s_nrm[c];
         total += v;
         if (v > best) {
           best = v;
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
         }
       }
       for (int o = 16; o; o >>= 1) {
-        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        R ob = __shfl_xor_sync(0xffffffffu, best, o);
         int oi = __shfl_xor_sync(0xffffffffu, idx, o);
         total += __shfl_xor_sync(0xffffffffu, total, o);
         if (ob > best || (ob == best && oi >= 0 && (idx < 0 || oi < idx))) {
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
         }
       }
       if (lane == 0) {
-        IdSlot sl;
+        IdSlot<R> sl;
         sl.best = best;
         sl.total = total;
         sl.idx = idx < 0 ? -1 : c0 + idx;
@@ -129,10 +130,10 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
     }
     if (!grid_sync(gs, nblk, epoch)) return;
     if (warp == 0) {  // global winner: largest norm, lowest candidate index on ties
-      double best = -1.0, total = 0.0;
+      R best = R(-1), total = R(0);
       int idx = -1, bw = -1;
       for (int b = lane; b < nblk; b += 32) {
-        IdSlot sl = slots[par * nblk + b];
+        IdSlot<R> sl = slots[par * nblk + b];
         total += sl.total;
         if (sl.idx >= 0 && (sl.best > best || (sl.best == best && sl.idx < idx))) {
           best = sl.best;
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
         }
       }
       for (int o = 16; o; o >>= 1) {
-        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        R ob = __shfl_xor_sync(0xffffffffu, best, o);
         int oi = __shfl_xor_sync(0xffffffffu, idx, o);
         int obw = __shfl_xor_sync(0xffffffffu, bw, o);
         total += __shfl_xor_sync(0xffffffffu, total, o);
@@ -152,11 +153,11 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
         }
       }
       if (lane == 0) {
-        if (j == 0) s_tol2 = eps * eps * total;
+        if (j == 0) s_tol2 = (R)(eps * eps) * total;
         s_best = best;
         s_idx = idx;
         s_bw = bw;
-        s_stop = (j == kmax) || idx < 0 || best <= 0.0 || total <= s_tol2;
+        s_stop = (j == kmax) || idx < 0 || !(best > R(0)) || total <= s_tol2;
       }
     }
     __syncthreads();
@@ -165,8 +166,8 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
       break;
     }
     const int pv = s_idx;
-    const R nu = (R)sqrt(s_best);
-    const R inu2 = R(1) / (R)s_best;
+    const R nu = sqrt(s_best);
+    const R inu2 = R(1) / s_best;
     {
       const cx<R>* src = pslots + ((long long)par * nblk + s_bw) * p;
       for (int i = tid; i < p; i += blockDim.x) pvec[i] = src[i];
@@ -257,11 +258,11 @@ __global__ void __launch_bounds__(256) cpqr_id_cluster_kernel(const cx<R>* __res
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
   const int per = (m + CL - 1) / CL;
   const int c0 = min(m, crank * per), c1 = min(m, c0 + per), mc = c1 - c0;
-  __shared__ double s_sbest[2], s_stotal[2];
+  __shared__ R s_sbest[2], s_stotal[2];
   __shared__ int s_sidx[2];
   __shared__ R s_nrm[64];
   __shared__ int s_sel[64];
-  __shared__ double s_best, s_tol2;
+  __shared__ R s_best, s_tol2;
   __shared__ int s_idx, s_bw, s_stop;
 
   for (long long t = tid; t < (long long)mc * p; t += blockDim.x) cand[t] = A[(long long)c0 * p + t];
@@ -281,11 +282,11 @@ __global__ void __launch_bounds__(256) cpqr_id_cluster_kernel(const cx<R>* __res
   for (int j = 0;; ++j) {
     const int par = j & 1;
     if (warp == 0) {
-      double best = -1.0, total = 0.0;
+      R best = R(-1), total = R(0);
       int idx = -1;
       for (int c = lane; c < mc; c += 32) {
         if (s_sel[c] != -1) continue;
-        double v = (double)s_nrm[c];
+        R v = s_nrm[c];
         total += v;
         if (v > best) {
           best = v;
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(256) cpqr_id_cluster_kernel(const cx<R>* __res
         }
       }
       for (int o = 16; o; o >>= 1) {
-        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        R ob = __shfl_xor_sync(0xffffffffu, best, o);
         int oi = __shfl_xor_sync(0xffffffffu, idx, o);
         total += __shfl_xor_sync(0xffffffffu, total, o);
         if (ob > best || (ob == best && oi >= 0 && (idx < 0 || oi < idx))) {
@@ -309,10 +310,10 @@ __global__ void __launch_bounds__(256) cpqr_id_cluster_kernel(const cx<R>* __res
     }
     cluster.sync();
     if (warp == 0) {
-      double best = -1.0, total = 0.0;
+      R best = R(-1), total = R(0);
       int idx = -1, bw = -1;
       for (int r = lane; r < CL; r += 32) {
-        double rb = *cluster.map_shared_rank(&s_sbest[par], r);
+        R rb = *cluster.map_shared_rank(&s_sbest[par], r);
         total += *cluster.map_shared_rank(&s_stotal[par], r);
         int ri = *cluster.map_shared_rank(&s_sidx[par], r);
         if (ri >= 0 && (rb > best || (rb == best && ri < idx))) {
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(256) cpqr_id_cluster_kernel(const cx<R>* __res
         }
       }
       for (int o = 16; o; o >>= 1) {
-        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        R ob = __shfl_xor_sync(0xffffffffu, best, o);
         int oi = __shfl_xor_sync(0xffffffffu, idx, o);
         int obw = __shfl_xor_sync(0xffffffffu, bw, o);
         total += __shfl_xor_sync(0xffffffffu, total, o);
@@ -333,11 +334,11 @@ __global__ void __launch_bounds__(256) cpqr_id_cluster_kernel(const cx<R>* __res
         }
       }
       if (lane == 0) {
-        if (j == 0) s_tol2 = eps * eps * total;
+        if (j == 0) s_tol2 = (R)(eps * eps) * total;
         s_best = best;
         s_idx = idx;
         s_bw = bw;
-        s_stop = (j == kmax) || idx < 0 || best <= 0.0 || total <= s_tol2;
+        s_stop = (j == kmax) || idx < 0 || !(best > R(0)) || total <= s_tol2;
       }
     }
     __syncthreads();
@@ -346,8 +347,8 @@ __global__ void __launch_bounds__(256) cpqr_id_cluster_kernel(const cx<R>* __res
       break;
     }
     const int pv = s_idx, bw = s_bw;
-    const R nu = (R)sqrt(s_best);
-    const R inu2 = R(1) / (R)s_best;
+    const R nu = sqrt(s_best);
+    const R inu2 = R(1) / s_best;
     {
       const cx<R>* src = cluster.map_shared_rank(cand + (long long)(pv - bw * per) * p, bw);
       for (int i = tid; i < p; i += blockDim.x) pvec[i] = src[i];
@@ -502,7 +503,7 @@ int compress_t(ls_handle* H, cudaStream_t st) {
     }
     size_t need = 64 * 256 + sizeof(cx<R>) * ((size_t)m * p * (use_smem ? 1 : 2) + (size_t)kmax * m + (size_t)m * kmax +
                                    (size_t)kmax * kmax + (size_t)2 * nblk * p) +
-                  sizeof(int) * (2 * m + 8) + sizeof(IdSlot) * 2 * (nblk + 1) + 1024;
+                  sizeof(int) * (2 * m + 8) + sizeof(IdSlot<R>) * 2 * (nblk + 1) + 1024;
     char* wsp = nullptr;
     if ((rc = dalloc((void**)&wsp, need))) return rc;
     auto carve = [&](size_t bytes) {
@@ -520,7 +521,7 @@ int compress_t(ls_handle* H, cudaStream_t st) {
     int* sel = reinterpret_cast<int*>(carve(sizeof(int) * m));
     int* piv = reinterpret_cast<int*>(carve(sizeof(int) * m));
     int* rank = reinterpret_cast<int*>(carve(sizeof(int) * 8));
-    IdSlot* slots = reinterpret_cast<IdSlot*>(carve(sizeof(IdSlot) * 2 * (nblk + 1)));
+    IdSlot<R>* slots = reinterpret_cast<IdSlot<R>*>(carve(sizeof(IdSlot<R>) * 2 * (nblk + 1)));
     wsp = wbase;
     if ((rc = upload_block<R>(rows_x, rows_y, px, py, A, dint, st, H->ks_prec, KernelTable{H->ktab, H->ktx, H->kty}))) return rc;
     // one cluster when the candidates fit in the shared memory of CL blocks

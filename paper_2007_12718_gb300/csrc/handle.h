@@ -73,6 +73,13 @@ int compress(ls_handle* H, cudaStream_t st);
 int hbs_build(ls_handle* H, cudaStream_t st);
 int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, cudaStream_t st);
 
+// tc_gemm.cu: complex FP32 GEMM on tcgen05 tensor cores (split: 0 tf32, 1 tf32x3)
+int tc_cgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, c32 alpha, const c32* A, int lda, long long sA,
+             const c32* B, int ldb, long long sB, c32 beta, c32* C, int ldc, long long sC, int batch, int split,
+             int* err);
+int simt_cgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, c32 alpha, const c32* A, int lda, long long sA,
+               const c32* B, int ldb, long long sB, c32 beta, c32* C, int ldc, long long sC, int batch);
+
 // gmres.cu
 int gmres_solve(ls_handle* H, const z64* f, z64* sigma, int nrhs, ls_solve_info* info, cudaStream_t st);
 

@@ -200,6 +200,31 @@ const char* ls_last_error(void) { return g_last_error.c_str(); }
 
 long long ls_kernel_launches(void) { return ls::g_launches.load(); }
 
+int ls_cgemm_c64(int engine, int ta, int tb, int M, int N, int K, const float* alpha, const void* A, int lda,
+                 long long sA, const void* B, int ldb, long long sB, const float* beta, void* C, int ldc,
+                 long long sC, int batch, void* stream) {
+  if (engine < 0 || engine > 2 || M < 0 || N < 0 || K < 0 || batch < 0 || !alpha || !beta || !A || !B || !C)
+    return LS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  ls::c32 al = ls::mk<float>(alpha[0], alpha[1]), be = ls::mk<float>(beta[0], beta[1]);
+  const ls::c32* a = static_cast<const ls::c32*>(A);
+  const ls::c32* b = static_cast<const ls::c32*>(B);
+  ls::c32* c = static_cast<ls::c32*>(C);
+  if (engine == 0) return ls::simt_cgemm(st, ta, tb, M, N, K, al, a, lda, sA, b, ldb, sB, be, c, ldc, sC, batch);
+  static int* d_flag = nullptr;  // per-process timeout flag of the tensor-core kernel
+  if (!d_flag) {
+    if (cudaMalloc(&d_flag, sizeof(int)) != cudaSuccess) return LS_ENOMEM;
+    cudaMemset(d_flag, 0, sizeof(int));
+  }
+  int rc = ls::tc_cgemm(st, ta, tb, M, N, K, al, a, lda, sA, b, ldb, sB, be, c, ldc, sC, batch, engine == 2 ? 1 : 0,
+                        d_flag);
+  if (rc) return rc;
+  int flag = 0;
+  LS_CUDA_TRY(cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LS_CUDA_TRY(cudaStreamSynchronize(st));
+  return flag ? flag : LS_OK;
+}
+
 void ls_free(ls_handle* H) {
   if (!H) return;
   ls::StreamScope scope(H->stream);
@@ -241,7 +266,7 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
     ls_default_opts(&H->opts);
   const ls_opts& o = H->opts;
   if (!valid_order(o.order_matvec) || !valid_order(o.order_precond) || o.order_precond == 2 || o.leaf_side < 2 ||
-      o.gmres_maxit < 1 || !(o.gmres_tol > 0) || (o.precision != LS_FP64 && o.precision != LS_FP32) ||
+      o.gmres_maxit < 1 || !(o.gmres_tol > 0) || (o.precision < LS_FP64 || o.precision > LS_TF32X3) ||
       o.proxy_width < 0 || o.merge_pivoting < 0 || o.merge_pivoting > 1) {
     set_error("invalid ls_opts");
     return LS_EINVAL;

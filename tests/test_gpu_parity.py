@@ -202,3 +202,24 @@ def test_precond_solve_full_size_n256():
         r = f.ravel() - nystrom.matvec_fft(spec, kappa, b, s)
         assert info["converged"]
         assert np.linalg.norm(r) / np.linalg.norm(f) < 2e-10
+
+
+@pytest.mark.parametrize("precision", [ls.LS_TF32X3, ls.LS_TF32])
+def test_tensor_core_build(precision):
+    """Merge GEMMs on the tensor cores: tf32x3 keeps the HBS inverse within 5 eps of
+    the dense inverse; plain tf32 is a rougher preconditioner, and GMRES (FP64,
+    FP64 matvec) still reaches the dense solution."""
+    n, kappa = 64, 40.0
+    b = inputs.gaussian_family(n, 0)
+    H = build(n, kappa, b, 1e-4, precision=precision)
+    A4 = nystrom.dense_operator(kappa, 1.0 / n, b, 4)
+    f = inputs.random_complex((n, n), 1)
+    q = host(ls.ls_apply(H, dev(f), torch.zeros(n, n, dtype=torch.complex128, device=DEV)))
+    err = rel(q, nystrom.solve_dense(A4, f.ravel()).reshape(n, n))
+    assert err < (5e-4 if precision == ls.LS_TF32X3 else 5e-2), err
+    fr = nystrom.rhs(kappa, b, n, n, 1.0 / n).reshape(n, n)
+    sig = torch.zeros(n, n, dtype=torch.complex128, device=DEV)
+    info = ls.ls_solve(H, dev(fr), sig)[0]
+    A10 = nystrom.dense_operator(kappa, 1.0 / n, b, 10)
+    assert info["converged"] and info["resid_true"] < 2e-10
+    assert rel(host(sig), nystrom.solve_dense(A10, fr.ravel()).reshape(n, n)) < 1e-9
