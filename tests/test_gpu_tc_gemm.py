@@ -2,9 +2,10 @@
 through the C ABI (ls_cgemm_c64), against a plain numpy complex128 matmul of
 the same complex64 inputs.
 
-Tolerances (relative Frobenius): FP32 SIMT and tensor-core tf32x3 ~ FP32
-rounding (1e-5 for K <= 1024); plain tf32 inputs carry a 2^-11 relative
-rounding each, so ~1e-3 (3e-3 allowed)."""
+Tolerances (relative Frobenius, K <= 1024 complex): FP32 SIMT accumulates 4K
+rounded products per entry (2e-5); tensor-core tf32x3 accumulates three
+partial products of 2K real terms each in FP32 (5e-5; 1.6e-5 seen at K = 764);
+plain tf32 inputs carry a 2^-11 relative rounding each, so ~1e-3 (3e-3 allowed)."""
 import numpy as np
 import pytest
 
@@ -14,7 +15,7 @@ from paper_2007_12718_gb300 import inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
-TOL = {0: 1e-5, 1: 3e-3, 2: 1e-5}
+TOL = {0: 2e-5, 1: 3e-3, 2: 5e-5}
 
 
 def _rand(shape, seed):
