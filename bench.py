@@ -34,7 +34,9 @@ WORKLOAD = "precond_n256"
 WORKLOAD_TEXT = ("256x256 grid (N=65,536), kappa=60, b = 20 seeded Gaussians (seed 0) x smooth cutoff, "
                  "HBS eps=1e-4 order-4 corrections, FFT matvec order 10, plane wave theta=0, GMRES to 1e-10")
 # Roofline denominators.  FP64 ALU: 1.25 TFLOP/s dense FP64 of a GB300 (nominal).
-FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fp64_tflops": 1.25}
+# FP32 SIMT: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s (unit
+# counts and maximum clock).  TF32 tensor: half the bf16 dense rate.
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fp64_tflops": 1.25, "fp32_tflops": 80.5}
 
 
 def peaks():
@@ -44,7 +46,8 @@ def peaks():
             d = json.load(open(p))
             return {"hbm_gbs": float(d.get("hbm_gbs", FALLBACK["hbm_gbs"])),
                     "bf16_tflops": float(d.get("bf16_tflops", FALLBACK["bf16_tflops"])),
-                    "fp64_tflops": FALLBACK["fp64_tflops"], "source": "measured"}
+                    "fp64_tflops": FALLBACK["fp64_tflops"], "fp32_tflops": FALLBACK["fp32_tflops"],
+                    "source": "measured"}
         except Exception:
             pass
     return dict(FALLBACK, source="fallback")
@@ -176,6 +179,8 @@ def run_ours(args, rank, world):
     ls.ls_free(H0)
     sig = torch.zeros(n, n, dtype=torch.complex128, device=dev)
 
+    PREC = {"fp32": ls.LS_FP32, "tf32": ls.LS_TF32, "tf32x3": ls.LS_TF32X3}[args.precision]
+
     def step(precision):
         H = ls.ls_build(n, h, kappa, b_dev, 1e-4, precision=precision)
         info = ls.ls_solve(H, f_dev, sig)[0]
@@ -207,14 +212,14 @@ def run_ours(args, rank, world):
         return total, info, launches, prof
 
     for _ in range(args.warmup):
-        step(ls.LS_FP32)
+        step(PREC)
         if not args.mixed_only:
             step(ls.LS_FP64)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev.index) as clk:
-        t_mixed, info_mixed, launches, prof = timed(ls.LS_FP32, args.steps, profile=True)
+        t_mixed, info_mixed, launches, prof = timed(PREC, args.steps, profile=True)
     if world > 1:
         torch.distributed.barrier()
     steps64 = max(1, min(args.steps, 3))
@@ -232,7 +237,7 @@ def run_ours(args, rank, world):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        H = ls.ls_build(n, h, kappa, b_host, 1e-4, precision=ls.LS_FP32)
+        H = ls.ls_build(n, h, kappa, b_host, 1e-4, precision=PREC)
         ls.ls_solve(H, f_host, s_host)
         ls.ls_free(H)
         torch.cuda.synchronize()
@@ -248,24 +253,34 @@ def run_ours(args, rank, world):
     value64 = world * N * steps64 / t_fp64 / 1e6
     e2e = world * N * args.steps / t_e2e / 1e6 if t_e2e > 0 else None
 
-    # roofline of the kernel family with the largest device time
+    # roofline of every timed kernel family; the one with the largest device time is the headline
     pk = peaks()
+    tensor = args.precision in ("tf32", "tf32x3")
+
+    def roof_of(name, p):
+        avg_ms = p["total_ms"] / p["launches"]
+        if name.startswith("matvec") or name == "spectrum_setup":
+            bound, peak, unit, work = "alu", pk["fp64_tflops"], "TFLOP/s (FP64)", p["flops"]
+            src = "nominal FP64 rate"
+        elif name in ("hbs_apply", "gmres_orth"):
+            bound, peak, unit, work = "hbm", pk["hbm_gbs"], "GB/s", p["bytes"]
+            src = pk["source"]
+        elif name == "merge_gemm" and tensor:
+            bound, peak, unit, work = "tensor", pk["bf16_tflops"] / 2, "TFLOP/s (TF32)", p["flops"]
+            src = pk["source"] + " bf16 x 1/2 (nominal tf32:bf16 ratio)"
+        else:
+            bound, peak, unit, work = "alu", pk["fp32_tflops"], "TFLOP/s (FP32 SIMT)", p["flops"]
+            src = "unit counts x max clock"
+        scale = 1e9 if unit == "GB/s" else 1e12
+        achieved = work / p["launches"] / (avg_ms * 1e-3) / scale
+        return {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "peak_source": src, "avg_launch_ms": avg_ms,
+                "launches": p["launches"]}
+
+    kernels = {k: roof_of(k, v) for k, v in prof.items() if v["launches"] > 0}
     single = {k: v for k, v in prof.items() if v["launches"] > 0 and k not in ("hbs_apply", "gmres_orth")}
-    top = max(single.items(), key=lambda kv: kv[1]["total_ms"])
-    name, p = top
-    avg_ms = p["total_ms"] / p["launches"]
-    fp64_alu = name.startswith("matvec") or name == "spectrum_setup"
-    if fp64_alu:
-        achieved = p["flops"] / p["launches"] / (avg_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": name, "achieved": achieved, "peak": pk["fp64_tflops"],
-                "unit": "TFLOP/s (FP64)", "frac": achieved / pk["fp64_tflops"], "traffic": None,
-                "peak_source": "nominal FP64 rate"}
-    else:
-        achieved = p["bytes"] / p["launches"] / (avg_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk["source"]}
-    roof["avg_launch_ms"] = avg_ms
-    roof["launches"] = p["launches"]
+    top = max(single.items(), key=lambda kv: kv[1]["total_ms"])[0]
+    roof = kernels[top]
     breakdown = {k: round(v["total_ms"] / args.steps, 4) for k, v in prof.items() if v["launches"]}
 
     cpu = cpu_baseline(n, kappa, b) if not args.no_cpu_baseline else None
@@ -273,11 +288,14 @@ def run_ours(args, rank, world):
             "warmup": args.warmup, "ms_per_step": t_mixed / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 HBS + c128 FFT/GMRES", "data": "synthetic",
             "config": {"workload": WORKLOAD, "description": WORKLOAD_TEXT, "l2": "flushed between steps",
-                       "nrhs": 1, "precision": "mixed (FP32 HBS, FP64 matvec + GMRES)"},
+                       "nrhs": 1, "precision": f"mixed ({args.precision} HBS merges, FP32 HBS storage, "
+                                                        "FP64 matvec + GMRES)"},
             "fp64": {"value": value64, "unit": "Mdof/s", "ms_per_step": t_fp64 / steps64 * 1e3,
                      "iterations": info_fp64["iterations"], "resid_true": info_fp64["resid_true"]},
             "iterations": info_mixed["iterations"], "resid_true": info_mixed["resid_true"],
             "roofline": roof, "breakdown_ms_per_step": breakdown,
+            "kernel_rooflines": {k: {"bound": v["bound"], "achieved": round(v["achieved"], 3), "unit": v["unit"],
+                                     "frac": round(v["frac"], 4)} for k, v in kernels.items()},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "Mdof/s", "h2d_bytes_per_step": N * 8 + N * 16,
                     "d2h_bytes_per_step": N * 16},
@@ -292,6 +310,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32", "tf32x3"],
+                    help="engine of the mixed path's merge GEMMs (FP32 storage in all three)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="time only the mixed path (no FP64 or end-to-end legs); for profiler runs")
     args = ap.parse_args()
