@@ -233,6 +233,7 @@ cx<R> zero() { return mk<R>(R(0), R(0)); }
 // false (in every thread) on an exactly zero pivot.
 template <class R>
 __device__ bool gj_inverse_smem(cx<R>* a, int n, int lda, int* piv, cx<R>* col) {
+  if (n > 256) return false;  // the elimination keeps at most 8 x 32 pivot-row entries per lane
   __shared__ int s_p;
   __shared__ int s_bad;
   __shared__ cx<R> s_d;
@@ -278,22 +279,36 @@ __device__ bool gj_inverse_smem(cx<R>* a, int n, int lda, int* piv, cx<R>* col) 
       a[k * lda + j] = tp * d;
     }
     __syncthreads();
-    for (int i = warp; i < n; i += nwarp) {
-      cx<R>* arow = a + i * lda;
-      if (i == k) {
-        if (lane == 0) arow[k] = d;
-        continue;
+    // elimination: warp w takes rows w, w + nwarp, ...; lane takes columns lane + 32 q,
+    // the scaled pivot row is held in registers for the whole step
+    {
+      cx<R> kr[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int j = lane + 32 * q;
+        kr[q] = (j < n && j != k) ? a[k * lda + j] : mk<R>(0, 0);
       }
-      const cx<R> f = col[i];
-      const cx<R>* krow = a + k * lda;
-      for (int j = lane; j < n; j += 32) {
-        if (j == k) {
-          arow[j] = mk<R>(-(f.re * d.re - f.im * d.im), -(f.re * d.im + f.im * d.re));
-        } else {
-          cx<R> r = krow[j], v = arow[j];
-          v.re -= f.re * r.re - f.im * r.im;
-          v.im -= f.re * r.im + f.im * r.re;
-          arow[j] = v;
+      const cx<R> nd = mk<R>(-d.re, -d.im);
+      for (int i = warp; i < n; i += nwarp) {
+        cx<R>* arow = a + i * lda;
+        if (i == k) {
+          if (lane == 0) arow[k] = d;
+          continue;
+        }
+        const cx<R> f = col[i];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int j = lane + 32 * q;
+          if (j < n) {
+            if (j == k) {
+              arow[j] = f * nd;
+            } else {
+              cx<R> v = arow[j];
+              v.re -= f.re * kr[q].re - f.im * kr[q].im;
+              v.im -= f.re * kr[q].im + f.im * kr[q].re;
+              arow[j] = v;
+            }
+          }
         }
       }
     }
@@ -388,7 +403,7 @@ __global__ void __launch_bounds__(256) leaf_build_kernel(TreeGeom g, const doubl
 
 // Batched in-smem inverse, one block per matrix (matrix b at X + b*sX, row stride lda).
 template <class R>
-__global__ void __launch_bounds__(256) inverse_smem_kernel(cx<R>* X, int n, int lda, long long sX, int* err) {
+__global__ void __launch_bounds__(512) inverse_smem_kernel(cx<R>* X, int n, int lda, long long sX, int* err) {
   extern __shared__ unsigned char smraw[];
   const int ls = n + 1;  // odd row stride: column reads without bank conflicts
   cx<R>* a = reinterpret_cast<cx<R>*>(smraw);
@@ -396,14 +411,15 @@ __global__ void __launch_bounds__(256) inverse_smem_kernel(cx<R>* X, int n, int 
   int* piv = reinterpret_cast<int*>(col + n);
   cx<R>* M = X + blockIdx.x * sX;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = warp; i < n; i += 8)
+  const int nw = blockDim.x >> 5;
+  for (int i = warp; i < n; i += nw)
     for (int j = lane; j < n; j += 32) a[i * ls + j] = M[(long long)i * lda + j];
   __syncthreads();
   if (!gj_inverse_smem(a, n, ls, piv, col)) {
     if (threadIdx.x == 0) atomicExch(err, LS_ESINGULAR);
     return;
   }
-  for (int i = warp; i < n; i += 8)
+  for (int i = warp; i < n; i += nw)
     for (int j = lane; j < n; j += 32) M[(long long)i * lda + j] = a[i * ls + j];
 }
 
@@ -850,7 +866,7 @@ int invert_batch_nopiv(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int
     LS_CUDA_TRY(cudaFuncSetAttribute(inverse_smem_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem_small));
     count_launch();
-    inverse_smem_kernel<R><<<P, 256, smem_small, st>>>(Ab, w, w, (long long)w * w, H->d_err);
+    inverse_smem_kernel<R><<<P, 512, smem_small, st>>>(Ab, w, w, (long long)w * w, H->d_err);
     gemm<R>(st, false, false, w, n, w, one<R>(), Ab, w, (long long)w * w, Mb, n, tot, zero<R>(), Rb, n, tot, P);
     gemm<R>(st, false, false, n, n, w, mone, Cb, w, tot, Rb, n, tot, one<R>(), X, lda, sX, P);
     gemm<R>(st, false, false, n, w, w, mone, Cb, w, tot, Ab, w, (long long)w * w, zero<R>(), X + k0, lda, sX, P);
@@ -868,7 +884,7 @@ int invert_batch(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int P, vo
     LS_CUDA_TRY(cudaFuncSetAttribute(inverse_smem_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem_small));
     count_launch();
-    inverse_smem_kernel<R><<<P, 256, smem_small, st>>>(X, n, lda, sX, H->d_err);
+    inverse_smem_kernel<R><<<P, 512, smem_small, st>>>(X, n, lda, sX, H->d_err);
     return check_launch("inverse_smem");
   }
   int nb = 32;

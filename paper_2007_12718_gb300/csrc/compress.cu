@@ -45,6 +45,45 @@ struct IdSlot {
   int pad;
 };
 
+// Warp-level helpers of one projection a -= q (q^H a) / |q|^2 (two independent
+// accumulators per lane for instruction-level parallelism).
+template <class R>
+__device__ __forceinline__ cx<R> project_coeff(const cx<R>* q, const cx<R>* a, int p, int lane, R inu2) {
+  cx<R> d0 = mk<R>(0, 0), d1 = mk<R>(0, 0);
+  int i = lane;
+  for (; i + 32 < p; i += 64) {
+    fmac_(d0, q[i], a[i]);
+    fmac_(d1, q[i + 32], a[i + 32]);
+  }
+  if (i < p) fmac_(d0, q[i], a[i]);
+  return scale(warp_sum(d0 + d1), inu2);
+}
+
+template <class R>
+__device__ __forceinline__ R project_update(const cx<R>* q, cx<R>* a, int p, int lane, cx<R> d) {
+  R n0 = 0, n1 = 0;
+  int i = lane;
+  for (; i + 32 < p; i += 64) {
+    cx<R> v0 = a[i], q0 = q[i], v1 = a[i + 32], q1 = q[i + 32];
+    v0.re -= q0.re * d.re - q0.im * d.im;
+    v0.im -= q0.re * d.im + q0.im * d.re;
+    v1.re -= q1.re * d.re - q1.im * d.im;
+    v1.im -= q1.re * d.im + q1.im * d.re;
+    a[i] = v0;
+    a[i + 32] = v1;
+    n0 += abs2(v0);
+    n1 += abs2(v1);
+  }
+  if (i < p) {
+    cx<R> v = a[i], q0 = q[i];
+    v.re -= q0.re * d.re - q0.im * d.im;
+    v.im -= q0.re * d.im + q0.im * d.re;
+    a[i] = v;
+    n0 += abs2(v);
+  }
+  return warp_sum_r(n0 + n1);
+}
+
 // Column-pivoted QR ID of the candidate-major matrix A (m candidates, each a
 // length-p vector at A + c*p).  Block b owns candidates [c0, c0 + mc) and keeps
 // their residual vectors in shared memory when they fit (else in the global
@@ -182,18 +221,8 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
     for (int c = warp; c < mc; c += nwarp) {
       if (s_sel[c] != -1) continue;
       cx<R>* a = cand + (long long)c * p;
-      cx<R> d = mk<R>(0, 0);
-      for (int i = lane; i < p; i += 32) fmac_(d, pvec[i], a[i]);
-      d = scale(warp_sum(d), inu2);  // coefficient of the pivot vector
-      R nr = 0;
-      for (int i = lane; i < p; i += 32) {
-        cx<R> v = a[i], q = pvec[i];
-        v.re -= q.re * d.re - q.im * d.im;
-        v.im -= q.re * d.im + q.im * d.re;
-        a[i] = v;
-        nr += abs2(v);
-      }
-      nr = warp_sum_r(nr);
+      cx<R> d = project_coeff(pvec, a, p, lane, inu2);  // coefficient of the pivot vector
+      R nr = project_update(pvec, a, p, lane, d);
       if (lane == 0) {
         s_nrm[c] = nr;
         Rm[(long long)j * m + c0 + c] = scale(d, nu);  // R(j, c) = q^H a = (a_pv^H a) / nu
@@ -363,18 +392,8 @@ __global__ void __launch_bounds__(256) cpqr_id_cluster_kernel(const cx<R>* __res
     for (int c = warp; c < mc; c += nwarp) {
       if (s_sel[c] != -1) continue;
       cx<R>* a = cand + (long long)c * p;
-      cx<R> d = mk<R>(0, 0);
-      for (int i = lane; i < p; i += 32) fmac_(d, pvec[i], a[i]);
-      d = scale(warp_sum(d), inu2);
-      R nr = 0;
-      for (int i = lane; i < p; i += 32) {
-        cx<R> v = a[i], q = pvec[i];
-        v.re -= q.re * d.re - q.im * d.im;
-        v.im -= q.re * d.im + q.im * d.re;
-        a[i] = v;
-        nr += abs2(v);
-      }
-      nr = warp_sum_r(nr);
+      cx<R> d = project_coeff(pvec, a, p, lane, inu2);  // coefficient of the pivot vector
+      R nr = project_update(pvec, a, p, lane, d);
       if (lane == 0) {
         s_nrm[c] = nr;
         Rm[(long long)j * m + c0 + c] = scale(d, nu);
@@ -524,16 +543,27 @@ int compress_t(ls_handle* H, cudaStream_t st) {
     IdSlot<R>* slots = reinterpret_cast<IdSlot<R>*>(carve(sizeof(IdSlot<R>) * 2 * (nblk + 1)));
     wsp = wbase;
     if ((rc = upload_block<R>(rows_x, rows_y, px, py, A, dint, st, H->ks_prec, KernelTable{H->ktab, H->ktx, H->kty}))) return rc;
-    // one cluster when the candidates fit in the shared memory of CL blocks
-    int CL = 16;
+    // one cluster when the candidates fit in the shared memory of CL blocks: the
+    // smallest CL with at most 32 candidates per block (4 per warp), else at most 64
+    int maxcl = 16;
     if (cudaFuncSetAttribute(cpqr_id_cluster_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
         cudaSuccess) {
       cudaGetLastError();
-      CL = 8;
+      maxcl = 8;
     }
-    const int per_cl = (m + CL - 1) / CL;
-    const size_t smem_cl = std::max(sizeof(cx<R>) * ((size_t)p + (size_t)per_cl * p), tail_smem);
-    bool use_cluster = per_cl <= 64 && smem_cl <= 200 * 1024;
+    auto cl_smem = [&](int cl) {
+      const int pc = (m + cl - 1) / cl;
+      return std::max(sizeof(cx<R>) * ((size_t)p + (size_t)pc * p), tail_smem);
+    };
+    int CL = 0;
+    for (int lim : {32, 64}) {
+      for (int cl = 1; cl <= maxcl && !CL; cl *= 2)
+        if ((m + cl - 1) / cl <= lim && cl_smem(cl) <= 200 * 1024) CL = cl;
+      if (CL) break;
+    }
+    bool use_cluster = CL > 0;
+    if (!use_cluster) CL = 1;
+    const size_t smem_cl = cl_smem(CL);
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
     if (use_cluster) {
