@@ -182,7 +182,7 @@ def run_ours(args, rank, world):
     PREC = {"fp32": ls.LS_FP32, "tf32": ls.LS_TF32, "tf32x3": ls.LS_TF32X3}[args.precision]
 
     def step(precision):
-        H = ls.ls_build(n, h, kappa, b_dev, 1e-4, precision=precision)
+        H = ls.ls_build(n, h, kappa, b_dev, 1e-4, precision=precision, top_uncompressed=args.top_uncompressed)
         info = ls.ls_solve(H, f_dev, sig)[0]
         ls.ls_free(H)
         return info
@@ -237,7 +237,7 @@ def run_ours(args, rank, world):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        H = ls.ls_build(n, h, kappa, b_host, 1e-4, precision=PREC)
+        H = ls.ls_build(n, h, kappa, b_host, 1e-4, precision=PREC, top_uncompressed=args.top_uncompressed)
         ls.ls_solve(H, f_host, s_host)
         ls.ls_free(H)
         torch.cuda.synchronize()
@@ -288,6 +288,7 @@ def run_ours(args, rank, world):
             "warmup": args.warmup, "ms_per_step": t_mixed / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 HBS + c128 FFT/GMRES", "data": "synthetic",
             "config": {"workload": WORKLOAD, "description": WORKLOAD_TEXT, "l2": "flushed between steps",
+                       "top_levels_uncompressed": args.top_uncompressed,
                        "nrhs": 1, "precision": f"mixed ({args.precision} HBS merges, FP32 HBS storage, "
                                                         "FP64 matvec + GMRES)"},
             "fp64": {"value": value64, "unit": "Mdof/s", "ms_per_step": t_fp64 / steps64 * 1e3,
@@ -312,6 +313,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32", "tf32x3"],
                     help="engine of the mixed path's merge GEMMs (FP32 storage in all three)")
+    ap.add_argument("--top-uncompressed", type=int, default=1,
+                    help="tree levels kept uncompressed at the top (U = I); 0 = every level compressed")
     ap.add_argument("--mixed-only", action="store_true",
                     help="time only the mixed path (no FP64 or end-to-end legs); for profiler runs")
     args = ap.parse_args()

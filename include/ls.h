@@ -69,6 +69,8 @@ typedef struct {
   double gmres_tol;  /* relative residual, default 1e-10 (Sec. 6.3)                       */
   int merge_pivoting; /* merge inverses: 0 = blocks without interchanges, checked, with the
                          row-pivoted inverse as fallback (default); 1 = always row-pivoted   */
+  int top_uncompressed; /* levels 1..top_uncompressed keep every row as skeleton (U = I,
+                         no ID); 0 = every level compressed as in Sec. 3.2 (default)      */
 } ls_opts;
 
 typedef struct {

@@ -436,6 +436,13 @@ __global__ void __launch_bounds__(256) cpqr_id_cluster_kernel(const cx<R>* __res
 }
 
 template <class R>
+__global__ void identity_kernel(cx<R>* U, int m) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)m * m) return;
+  U[t] = mk<R>((t / m) == (t % m) ? R(1) : R(0), R(0));
+}
+
+template <class R>
 int upload_block(const std::vector<int>& rx, const std::vector<int>& ry, const std::vector<int>& px,
                  const std::vector<int>& py, cx<R>* out, int* dtmp, cudaStream_t st, const KernelSpec& ks,
                  const KernelTable& kt) {
@@ -501,6 +508,18 @@ int compress_t(ls_handle* H, cudaStream_t st) {
     const int m = (int)rows_x.size(), p = (int)px.size();
     lv.m = m;
     lv.ring = p;
+    if (l <= H->opts.top_uncompressed) {
+      // top level kept uncompressed: every row is a skeleton point and U = I
+      lv.k = m;
+      lv.skel_x = rows_x;
+      lv.skel_y = rows_y;
+      if ((rc = dalloc(&lv.U, sizeof(cx<R>) * (size_t)m * m))) return rc;
+      long long tot = (long long)m * m;
+      count_launch();
+      identity_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(reinterpret_cast<cx<R>*>(lv.U), m);
+      if ((rc = check_launch("identity U"))) return rc;
+      continue;
+    }
     const int kmax = std::min(m, p);
     if (dint) ls::dfree(dint);
     dint = nullptr;

@@ -181,6 +181,7 @@ void ls_default_opts(ls_opts* o) {
   o->gmres_maxit = 100;
   o->gmres_tol = 1e-10;
   o->merge_pivoting = 0;
+  o->top_uncompressed = 0;
 }
 
 const char* ls_strerror(int code) {
@@ -267,7 +268,8 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
   const ls_opts& o = H->opts;
   if (!valid_order(o.order_matvec) || !valid_order(o.order_precond) || o.order_precond == 2 || o.leaf_side < 2 ||
       o.gmres_maxit < 1 || !(o.gmres_tol > 0) || (o.precision < LS_FP64 || o.precision > LS_TF32X3) ||
-      o.proxy_width < 0 || o.merge_pivoting < 0 || o.merge_pivoting > 1) {
+      o.proxy_width < 0 || o.merge_pivoting < 0 || o.merge_pivoting > 1 ||
+      o.top_uncompressed < 0) {
     set_error("invalid ls_opts");
     return LS_EINVAL;
   }

@@ -223,3 +223,18 @@ def test_tensor_core_build(precision):
     A10 = nystrom.dense_operator(kappa, 1.0 / n, b, 10)
     assert info["converged"] and info["resid_true"] < 2e-10
     assert rel(host(sig), nystrom.solve_dense(A10, fr.ravel()).reshape(n, n)) < 1e-9
+
+
+@pytest.mark.parametrize("precision", [ls.LS_FP32, ls.LS_FP64])
+def test_top_level_uncompressed(precision):
+    """top_uncompressed = 1 keeps every row of level 1 (U = I): still an HBS inverse
+    of I + B G within 5 eps, with rank k_1 = m_1."""
+    n, kappa = 64, 30.0
+    b = inputs.gaussian_family(n, 4)
+    H = build(n, kappa, b, 1e-4, precision=precision, top_uncompressed=1)
+    info = H.info()
+    assert info["ranks"][1] == 2 * info["ranks"][2]
+    A4 = nystrom.dense_operator(kappa, 1.0 / n, b, 4)
+    f = inputs.random_complex((n, n), 6)
+    q = host(ls.ls_apply(H, dev(f), torch.zeros(n, n, dtype=torch.complex128, device=DEV)))
+    assert rel(q, nystrom.solve_dense(A4, f.ravel()).reshape(n, n)) < 5e-4
