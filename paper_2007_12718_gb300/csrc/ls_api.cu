@@ -207,6 +207,7 @@ int ls_cgemm_c64(int engine, int ta, int tb, int M, int N, int K, const float* a
   if (engine < 0 || engine > 2 || M < 0 || N < 0 || K < 0 || batch < 0 || !alpha || !beta || !A || !B || !C)
     return LS_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
+  ls::StreamScope scope(st);
   ls::c32 al = ls::mk<float>(alpha[0], alpha[1]), be = ls::mk<float>(beta[0], beta[1]);
   const ls::c32* a = static_cast<const ls::c32*>(A);
   const ls::c32* b = static_cast<const ls::c32*>(B);
