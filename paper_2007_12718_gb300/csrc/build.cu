@@ -1230,6 +1230,133 @@ __global__ void scatter_leaves_kernel(TreeGeom g, const cx<R>* __restrict__ Q, z
   q[(long long)(oy + ly) * g.nx + ox + lx] = cvt<double>(Q[t]);
 }
 
+// Block-level helpers for the per-node fused apply kernels (vectors in shared memory).
+// y[i] = sum_j A[i*lda + j] x[j], i < rows: one warp per row.
+template <class R, class F>
+__device__ __forceinline__ void blk_rows(const cx<R>* __restrict__ A, int lda, const cx<R>* x, int rows, int cols, F out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = warp; i < rows; i += nw) {
+    const cx<R>* a = A + (long long)i * lda;
+    cx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0);
+    int j = lane;
+    for (; j + 32 < cols; j += 64) {
+      fma_(acc0, a[j], x[j]);
+      fma_(acc1, a[j + 32], x[j + 32]);
+    }
+    if (j < cols) fma_(acc0, a[j], x[j]);
+    cx<R> acc = warp_sum(acc0 + acc1);
+    if (lane == 0) out(i, acc);
+  }
+}
+// y[j] = sum_i A[i*lda + j] x[i], j < cols (A^T x): lanes over 32 columns, warps over rows,
+// partial sums reduced in shared memory. Called by all threads of a 256-thread block.
+template <class R, class F>
+__device__ __forceinline__ void blk_cols(const cx<R>* __restrict__ A, int lda, const cx<R>* x, int rows, int cols, F out) {
+  __shared__ cx<R> part[8][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j0 = 0; j0 < cols; j0 += 32) {
+    const int j = j0 + lane;
+    cx<R> acc = mk<R>(0, 0);
+    if (j < cols)
+      for (int i = warp; i < rows; i += 8) fma_(acc, A[(long long)i * lda + j], x[i]);
+    part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && j < cols) {
+      cx<R> v = part[0][lane];
+      for (int w = 1; w < 8; ++w) v = v + part[w][lane];
+      out(j, v);
+    }
+    __syncthreads();
+  }
+}
+
+// Leaves, up: r = X f (kept for the last step), r~ = U^T r (Eq. (24)); one block per leaf.
+template <class R>
+__global__ void __launch_bounds__(256) leaf_up_kernel(TreeGeom g, const z64* const* __restrict__ fslot,
+                                                      const cx<R>* __restrict__ X, const cx<R>* __restrict__ U, int k,
+                                                      cx<R>* __restrict__ Rl, cx<R>* __restrict__ rt) {
+  __shared__ cx<R> f[256], r[256];
+  const int n = g.s * g.s, leaf = blockIdx.x;
+  int ox, oy;
+  leaf_origin(g, leaf, ox, oy);
+  const z64* fin = *fslot;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    f[i] = cvt<R>(fin[(long long)(oy + i / g.s) * g.nx + ox + i % g.s]);
+  __syncthreads();
+  cx<R>* rl = Rl + (long long)leaf * n;
+  blk_rows<R>(X + (long long)leaf * n * n, n, f, n, n, [&](int i, cx<R> v) {
+    r[i] = v;
+    rl[i] = v;
+  });
+  __syncthreads();
+  cx<R>* ro = rt + (long long)leaf * k;
+  blk_cols<R>(U, k, r, n, k, [&](int j, cx<R> v) { ro[j] = v; });
+}
+
+// Up pass for one parent: r~_tau = U^T X [r~_a; r~_b] (Eq. (28)).
+template <class R>
+__global__ void __launch_bounds__(256) up_node_kernel(int n2, int kp, const cx<R>* __restrict__ X,
+                                                      const cx<R>* __restrict__ U, const cx<R>* __restrict__ rin,
+                                                      cx<R>* __restrict__ rout) {
+  extern __shared__ unsigned char smraw[];
+  cx<R>* x = reinterpret_cast<cx<R>*>(smraw);
+  cx<R>* t = x + n2;
+  const int node = blockIdx.x;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) x[i] = rin[(long long)node * n2 + i];
+  __syncthreads();
+  blk_rows<R>(X + (long long)node * n2 * n2, n2, x, n2, n2, [&](int i, cx<R> v) { t[i] = v; });
+  __syncthreads();
+  cx<R>* ro = rout + (long long)node * kp;
+  blk_cols<R>(U, kp, t, n2, kp, [&](int j, cx<R> v) { ro[j] = v; });
+}
+
+// Down pass for one parent (Lemma 4.1): Uw = U w~, q~ = X([r~_a; r~_b] - diag(S_a, S_b) Uw),
+// w~_a = Uw_a + G q~_b, w~_b = Uw_b + G^T q~_a.
+template <class R>
+__global__ void __launch_bounds__(256) down_node_kernel(int kc, int kp, const cx<R>* __restrict__ U,
+                                                        const cx<R>* __restrict__ S, const cx<R>* __restrict__ X,
+                                                        const cx<R>* __restrict__ G, const cx<R>* __restrict__ win,
+                                                        const cx<R>* __restrict__ rab, cx<R>* __restrict__ wout) {
+  extern __shared__ unsigned char smraw[];
+  const int n2 = 2 * kc, node = blockIdx.x;
+  cx<R>* w = reinterpret_cast<cx<R>*>(smraw);  // kp
+  cx<R>* uw = w + kp;                          // n2
+  cx<R>* t = uw + n2;                          // n2
+  cx<R>* q = t + n2;                           // n2
+  for (int i = threadIdx.x; i < kp; i += blockDim.x) w[i] = win[(long long)node * kp + i];
+  __syncthreads();
+  blk_rows<R>(U, kp, w, n2, kp, [&](int i, cx<R> v) { uw[i] = v; });
+  __syncthreads();
+  const cx<R>* ra = rab + (long long)node * n2;
+  const cx<R>* Sa = S + (long long)(2 * node) * kc * kc;
+  blk_rows<R>(Sa, kc, uw, kc, kc, [&](int i, cx<R> v) { t[i] = ra[i] - v; });
+  blk_rows<R>(Sa + (long long)kc * kc, kc, uw + kc, kc, kc, [&](int i, cx<R> v) { t[kc + i] = ra[kc + i] - v; });
+  __syncthreads();
+  blk_rows<R>(X + (long long)node * n2 * n2, n2, t, n2, n2, [&](int i, cx<R> v) { q[i] = v; });
+  __syncthreads();
+  cx<R>* wo = wout + (long long)node * n2;
+  blk_rows<R>(G, kc, q + kc, kc, kc, [&](int i, cx<R> v) { wo[i] = uw[i] + v; });
+  blk_cols<R>(G, kc, q, kc, kc, [&](int j, cx<R> v) { wo[kc + j] = uw[kc + j] + v; });
+}
+
+// Leaves, last step: q = r - X B U w~, scattered to the grid.
+template <class R>
+__global__ void __launch_bounds__(256) leaf_down_kernel(TreeGeom g, z64* const* __restrict__ qslot,
+                                                        const cx<R>* __restrict__ XBU, int k,
+                                                        const cx<R>* __restrict__ wt, const cx<R>* __restrict__ Rl) {
+  __shared__ cx<R> w[256];
+  const int n = g.s * g.s, leaf = blockIdx.x;
+  int ox, oy;
+  leaf_origin(g, leaf, ox, oy);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) w[i] = wt[(long long)leaf * k + i];
+  __syncthreads();
+  z64* qo = *qslot;
+  const cx<R>* rl = Rl + (long long)leaf * n;
+  blk_rows<R>(XBU + (long long)leaf * n * k, k, w, n, k, [&](int i, cx<R> v) {
+    qo[(long long)(oy + i / g.s) * g.nx + ox + i % g.s] = cvt<double>(rl[i] - v);
+  });
+}
+
 __global__ void set_slots_kernel(z64** slots, const z64* f, z64* q) {
   slots[0] = const_cast<z64*>(f);
   slots[1] = q;
@@ -1255,18 +1382,34 @@ int apply_core(ls_handle* H, z64** slots, cudaStream_t st) {
     p += sz;
   }
   const cx<R> mone = mk<R>(R(-1), R(0));
-  count_launch();
-  gather_leaves_kernel<R><<<(unsigned)((nleaf * n + 255) / 256), 256, 0, st>>>(g, slots, F);
   const LevelData& lf = H->lev[L];
   const int kL = lf.k;
-  // leaves: r = X f, r~ = U^T r  (Eq. (24))
-  gemv<R>(st, false, n, n, one<R>(), reinterpret_cast<const cx<R>*>(lf.X), n, (long long)n * n, F, n, zero<R>(), Rl,
-          n, (int)nleaf);
-  gemv<R>(st, true, kL, n, one<R>(), reinterpret_cast<const cx<R>*>(lf.U), kL, 0, Rl, n, zero<R>(), rt[L], kL,
-          (int)nleaf);
+  // nodes of a level with at least this many parents are applied by one block each
+  const int kFusedMinNodes = 512;
+  const bool leaf_fused = n <= 256 && kL <= 256;
+  if (leaf_fused) {
+    count_launch();
+    leaf_up_kernel<R><<<(unsigned)nleaf, 256, 0, st>>>(g, slots, reinterpret_cast<const cx<R>*>(lf.X),
+                                                       reinterpret_cast<const cx<R>*>(lf.U), kL, Rl, rt[L]);
+  } else {
+    count_launch();
+    gather_leaves_kernel<R><<<(unsigned)((nleaf * n + 255) / 256), 256, 0, st>>>(g, slots, F);
+    // leaves: r = X f, r~ = U^T r  (Eq. (24))
+    gemv<R>(st, false, n, n, one<R>(), reinterpret_cast<const cx<R>*>(lf.X), n, (long long)n * n, F, n, zero<R>(),
+            Rl, n, (int)nleaf);
+    gemv<R>(st, true, kL, n, one<R>(), reinterpret_cast<const cx<R>*>(lf.U), kL, 0, Rl, n, zero<R>(), rt[L], kL,
+            (int)nleaf);
+  }
   // upward pass: r~_tau = U^T X [r~_a; r~_b]  (Eq. (28)); X [.;.] goes to the child-level scratch
   for (int l = L - 1; l >= 1; --l) {
     const int P = 1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
+    if (P >= kFusedMinNodes && sizeof(cx<R>) * 2 * n2 <= 48 * 1024) {
+      count_launch();
+      up_node_kernel<R><<<P, 256, sizeof(cx<R>) * 2 * n2, st>>>(n2, kp, reinterpret_cast<const cx<R>*>(H->lev[l].X),
+                                                                reinterpret_cast<const cx<R>*>(H->lev[l].U),
+                                                                rt[l + 1], rt[l]);
+      continue;
+    }
     gemv<R>(st, false, n2, n2, one<R>(), reinterpret_cast<const cx<R>*>(H->lev[l].X), n2, (long long)n2 * n2,
             rt[l + 1], n2, zero<R>(), tmp[l + 1], n2, P);
     gemv<R>(st, true, kp, n2, one<R>(), reinterpret_cast<const cx<R>*>(H->lev[l].U), kp, 0, tmp[l + 1], n2, zero<R>(),
@@ -1290,6 +1433,12 @@ int apply_core(ls_handle* H, z64** slots, cudaStream_t st) {
     const cx<R>* Sc = reinterpret_cast<const cx<R>*>(H->lev[l + 1].S);
     const cx<R>* X = reinterpret_cast<const cx<R>*>(H->lev[l].X);
     const cx<R>* Gs = reinterpret_cast<const cx<R>*>(H->lev[l + 1].Gsib);
+    if (P >= kFusedMinNodes && sizeof(cx<R>) * (kp + 3 * n2) <= 48 * 1024) {
+      count_launch();
+      down_node_kernel<R><<<P, 256, sizeof(cx<R>) * (kp + 3 * n2), st>>>(kc, kp, U, Sc, X, Gs, wt[l], rt[l + 1],
+                                                                          wt[l + 1]);
+      continue;
+    }
     cx<R>* Uw = wt[l + 1];  // U w~_tau, laid out as the children's incoming expansions
     cx<R>* t = tmp[l + 1];
     gemv<R>(st, false, n2, kp, one<R>(), U, kp, 0, wt[l], kp, zero<R>(), Uw, n2, P);
@@ -1302,10 +1451,16 @@ int apply_core(ls_handle* H, z64** slots, cudaStream_t st) {
     gemv<R>(st, true, kc, kc, one<R>(), Gs, kc, 0, qbuf, n2, one<R>(), Uw + kc, n2, P);
   }
   // leaves: q = r - X B U w~
-  gemv<R>(st, false, n, kL, mone, reinterpret_cast<const cx<R>*>(H->XBU), kL, (long long)n * kL, wt[L], kL, one<R>(),
-          Rl, n, (int)nleaf);
-  count_launch();
-  scatter_leaves_kernel<R><<<(unsigned)((nleaf * n + 255) / 256), 256, 0, st>>>(g, Rl, slots + 1);
+  if (leaf_fused) {
+    count_launch();
+    leaf_down_kernel<R><<<(unsigned)nleaf, 256, 0, st>>>(g, slots + 1, reinterpret_cast<const cx<R>*>(H->XBU), kL,
+                                                         wt[L], Rl);
+  } else {
+    gemv<R>(st, false, n, kL, mone, reinterpret_cast<const cx<R>*>(H->XBU), kL, (long long)n * kL, wt[L], kL,
+            one<R>(), Rl, n, (int)nleaf);
+    count_launch();
+    scatter_leaves_kernel<R><<<(unsigned)((nleaf * n + 255) / 256), 256, 0, st>>>(g, Rl, slots + 1);
+  }
   return check_launch("hbs_apply");
 }
 

@@ -267,17 +267,38 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
   }
 }
 
-// The same ID on one thread-block cluster (CL blocks, candidates resident in
-// their shared memory) for proxy blocks that fit: the slots and the winning
-// vector are read through distributed shared memory, the per-step barrier is
-// the cluster barrier.  Slots are double-buffered by step parity so that one
-// barrier per pivot step suffices.  Same outputs as cpqr_id_kernel.
+// Pivot order of the ID: larger residual norm first, lower candidate index on
+// ties; idx < 0 marks "no candidate".
 template <class R>
-__global__ void __launch_bounds__(256) cpqr_id_cluster_kernel(const cx<R>* __restrict__ A, int m, int p, int kmax,
-                                                              double eps, cx<R>* __restrict__ Rm,
-                                                              int* __restrict__ sel, int* __restrict__ piv,
-                                                              int* __restrict__ rank, cx<R>* __restrict__ U,
-                                                              cx<R>* __restrict__ RT) {
+__device__ __forceinline__ bool piv_better(R b1, int i1, R b2, int i2) {
+  return i1 >= 0 && (i2 < 0 || b1 > b2 || (b1 == b2 && i1 < i2));
+}
+template <class R>
+__device__ __forceinline__ void warp_argmax(R& best, int& idx) {
+  for (int o = 16; o; o >>= 1) {
+    R ob = __shfl_xor_sync(0xffffffffu, best, o);
+    int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (piv_better(ob, oi, best, idx)) {
+      best = ob;
+      idx = oi;
+    }
+  }
+}
+
+// The same ID on one thread-block cluster (CL <= 16 blocks of 1024 threads,
+// candidates resident in shared memory, normally one candidate per warp).
+// Per pivot step: warp 0 of each block publishes its best local candidate in
+// a parity slot; one cluster barrier; every warp reads the CL slots through
+// distributed shared memory and resolves the winner itself (no second block
+// barrier); the block copies the winning vector from the owner's shared
+// memory and projects it out of its own candidates.  Same outputs as
+// cpqr_id_kernel.
+template <class R>
+__global__ void __launch_bounds__(1024) cpqr_id_cluster_kernel(const cx<R>* __restrict__ A, int m, int p, int kmax,
+                                                               double eps, cx<R>* __restrict__ Rm,
+                                                               int* __restrict__ sel, int* __restrict__ piv,
+                                                               int* __restrict__ rank, cx<R>* __restrict__ U,
+                                                               cx<R>* __restrict__ RT) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ unsigned char smraw[];
@@ -291,8 +312,6 @@ __global__ void __launch_bounds__(256) cpqr_id_cluster_kernel(const cx<R>* __res
   __shared__ int s_sidx[2];
   __shared__ R s_nrm[64];
   __shared__ int s_sel[64];
-  __shared__ R s_best, s_tol2;
-  __shared__ int s_idx, s_bw, s_stop;
 
   for (long long t = tid; t < (long long)mc * p; t += blockDim.x) cand[t] = A[(long long)c0 * p + t];
   __syncthreads();
@@ -307,86 +326,58 @@ __global__ void __launch_bounds__(256) cpqr_id_cluster_kernel(const cx<R>* __res
     }
   }
   __syncthreads();
+  R tol2 = 0;
   int k = 0;
   for (int j = 0;; ++j) {
     const int par = j & 1;
-    if (warp == 0) {
+    if (warp == 0) {  // local best and total over the block's active candidates (mc <= 64)
       R best = R(-1), total = R(0);
       int idx = -1;
       for (int c = lane; c < mc; c += 32) {
         if (s_sel[c] != -1) continue;
-        R v = s_nrm[c];
+        const R v = s_nrm[c];
         total += v;
-        if (v > best) {
+        if (piv_better(v, c0 + c, best, idx)) {
           best = v;
-          idx = c;
+          idx = c0 + c;
         }
       }
-      for (int o = 16; o; o >>= 1) {
-        R ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-        total += __shfl_xor_sync(0xffffffffu, total, o);
-        if (ob > best || (ob == best && oi >= 0 && (idx < 0 || oi < idx))) {
-          best = ob;
-          idx = oi;
-        }
-      }
+      warp_argmax(best, idx);
+      total = warp_sum_r(total);
       if (lane == 0) {
         s_sbest[par] = best;
         s_stotal[par] = total;
-        s_sidx[par] = idx < 0 ? -1 : c0 + idx;
+        s_sidx[par] = idx;
       }
     }
     cluster.sync();
-    if (warp == 0) {
-      R best = R(-1), total = R(0);
-      int idx = -1, bw = -1;
-      for (int r = lane; r < CL; r += 32) {
-        R rb = *cluster.map_shared_rank(&s_sbest[par], r);
-        total += *cluster.map_shared_rank(&s_stotal[par], r);
-        int ri = *cluster.map_shared_rank(&s_sidx[par], r);
-        if (ri >= 0 && (rb > best || (rb == best && ri < idx))) {
-          best = rb;
-          idx = ri;
-          bw = r;
-        }
-      }
-      for (int o = 16; o; o >>= 1) {
-        R ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-        int obw = __shfl_xor_sync(0xffffffffu, bw, o);
-        total += __shfl_xor_sync(0xffffffffu, total, o);
-        if (oi >= 0 && (ob > best || (ob == best && (idx < 0 || oi < idx)))) {
-          best = ob;
-          idx = oi;
-          bw = obw;
-        }
-      }
-      if (lane == 0) {
-        if (j == 0) s_tol2 = (R)(eps * eps) * total;
-        s_best = best;
-        s_idx = idx;
-        s_bw = bw;
-        s_stop = (j == kmax) || idx < 0 || !(best > R(0)) || total <= s_tol2;
-      }
+    // every warp resolves the cluster-wide winner (lane r reads block r's slot)
+    R best = R(-1), total = R(0);
+    int idx = -1;
+    if (lane < CL) {
+      best = *cluster.map_shared_rank(&s_sbest[par], lane);
+      total = *cluster.map_shared_rank(&s_stotal[par], lane);
+      idx = *cluster.map_shared_rank(&s_sidx[par], lane);
     }
-    __syncthreads();
-    if (s_stop) {
+    warp_argmax(best, idx);
+    total = warp_sum_r(total);
+    if (j == 0) tol2 = (R)(eps * eps) * total;
+    if ((j == kmax) || idx < 0 || !(best > R(0)) || total <= tol2) {
       k = j;
       break;
     }
-    const int pv = s_idx, bw = s_bw;
-    const R nu = sqrt(s_best);
-    const R inu2 = R(1) / s_best;
+    const int bw = idx / per;
+    const R nu = sqrt(best);
+    const R inu2 = R(1) / best;
     {
-      const cx<R>* src = cluster.map_shared_rank(cand + (long long)(pv - bw * per) * p, bw);
+      const cx<R>* src = cluster.map_shared_rank(cand + (long long)(idx - bw * per) * p, bw);
       for (int i = tid; i < p; i += blockDim.x) pvec[i] = src[i];
     }
     if (crank == bw && tid == 0) {
-      s_sel[pv - c0] = j;
-      sel[pv] = j;
-      piv[j] = pv;
-      Rm[(long long)j * m + pv] = mk<R>(nu, R(0));
+      s_sel[idx - c0] = j;
+      sel[idx] = j;
+      piv[j] = idx;
+      Rm[(long long)j * m + idx] = mk<R>(nu, R(0));
     }
     __syncthreads();
     for (int c = warp; c < mc; c += nwarp) {
@@ -396,13 +387,13 @@ __global__ void __launch_bounds__(256) cpqr_id_cluster_kernel(const cx<R>* __res
       R nr = project_update(pvec, a, p, lane, d);
       if (lane == 0) {
         s_nrm[c] = nr;
-        Rm[(long long)j * m + c0 + c] = scale(d, nu);
+        Rm[(long long)j * m + c0 + c] = scale(d, nu);  // R(j, c) = q^H a = (a_pv^H a) / nu
       }
     }
     __syncthreads();
   }
   if (crank == 0 && tid == 0) rank[0] = k;
-  cluster.sync();  // every remote read of candidate vectors is done; piv, Rm complete
+  cluster.sync();  // every remote read is done; piv and Rm are complete and visible
   for (long long t = (long long)crank * blockDim.x + tid; t < (long long)k * k; t += (long long)CL * blockDim.x) {
     int a = (int)(t / k), bb = (int)(t % k);
     RT[t] = bb <= a ? Rm[(long long)bb * m + piv[a]] : mk<R>(0, 0);
@@ -570,14 +561,16 @@ int compress_t(ls_handle* H, cudaStream_t st) {
       cudaGetLastError();
       maxcl = 8;
     }
+    const size_t cl_tail_smem = sizeof(cx<R>) * (size_t)32 * kmax;
     auto cl_smem = [&](int cl) {
       const int pc = (m + cl - 1) / cl;
-      return std::max(sizeof(cx<R>) * ((size_t)p + (size_t)pc * p), tail_smem);
+      return std::max(sizeof(cx<R>) * ((size_t)p + (size_t)pc * p), cl_tail_smem);
     };
+    // the smallest cluster with at most one candidate per warp (32 per block), else at most 64 per block
     int CL = 0;
     for (int lim : {32, 64}) {
-      for (int cl = 1; cl <= maxcl && !CL; cl *= 2)
-        if ((m + cl - 1) / cl <= lim && cl_smem(cl) <= 200 * 1024) CL = cl;
+      for (int cl = 1; cl <= maxcl && !CL; ++cl)
+        if ((m + cl - 1) / cl <= lim && cl_smem(cl) <= 220 * 1024) CL = cl;
       if (CL) break;
     }
     bool use_cluster = CL > 0;
@@ -590,7 +583,7 @@ int compress_t(ls_handle* H, cudaStream_t st) {
                                        (int)smem_cl));
       memset(&cfg, 0, sizeof(cfg));
       cfg.gridDim = dim3(CL);
-      cfg.blockDim = dim3(256);
+      cfg.blockDim = dim3(1024);
       cfg.dynamicSmemBytes = smem_cl;
       cfg.stream = st;
       attr[0].id = cudaLaunchAttributeClusterDimension;
