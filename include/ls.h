@@ -196,6 +196,23 @@ int ls_cgemm_c64(int engine, int ta, int tb, int M, int N, int K, const float* a
                  long long sA, const void* B, int ldb, long long sB, const float* beta, void* C, int ldc,
                  long long sC, int batch, void* stream);
 
+/* ls_row_id -- the interpolative decomposition of Sec. 2.1 as the compression
+ * uses it (Sec. 3.2): A ~ U A(J, :) for an m x p complex matrix whose rows are
+ * the candidates, by column-pivoted QR of A^T.  Pivot j is the candidate with
+ * the largest residual norm (lowest index on ties); k is the first j at which
+ * the Frobenius norm of the remaining residual is <= eps ||A||_F.
+ *   A:    m * p complex128, row-major (row c = candidate c), host or device.
+ *   precision: LS_FP64 or LS_FP32 (the arithmetic of the device kernels; with
+ *         LS_FP32, A is rounded to complex64 on the device).
+ *   k:    out, the rank.  piv: out, host array of at least min(m, p) ints,
+ *         piv[0..k) the skeleton rows in pivot order.
+ *   U:    out (may be NULL), m * k complex128 row-major, host or device,
+ *         sized by the caller for m * min(m, p) entries; U(piv[a], a') = [a = a'].
+ * Requires 1 <= m < 2^20, p >= 1, 0 < eps < 1.  Returns LS_EINVAL for a bad
+ * argument, LS_ENOMEM, LS_ECUDA, or LS_ETIMEOUT if a grid barrier wait gave up.
+ * Synchronises the stream before returning. */
+int ls_row_id(const void* A, int m, int p, double eps, int precision, int* k, int* piv, void* U, void* stream);
+
 /* Static text for an LS_E* code, and the last error message of this thread. */
 const char* ls_strerror(int code);
 const char* ls_last_error(void);

@@ -30,7 +30,7 @@ LS_FP64, LS_FP32, LS_TF32, LS_TF32X3 = 0, 1, 2, 3
 EXPORTED = ["ls_default_opts", "ls_build", "ls_apply", "ls_matvec", "ls_solve", "ls_rhs_plane_wave",
             "ls_get_build_info", "ls_free", "ls_strerror", "ls_last_error", "ls_profile_enable",
             "ls_profile_reset", "ls_profile_get", "ls_kernel_launches", "ls_matvec_noalloc",
-            "ls_matvec_noalloc_max_elems", "ls_cgemm_c64"]
+            "ls_matvec_noalloc_max_elems", "ls_cgemm_c64", "ls_row_id"]
 
 
 class Grid(ctypes.Structure):
@@ -108,6 +108,8 @@ def load_library(path=LIB_PATH):
                                  vp, ip, ctypes.c_longlong, ctypes.POINTER(ctypes.c_float), vp, ip, ctypes.c_longlong,
                                  ip, vp]
     lib.ls_cgemm_c64.restype = ip
+    lib.ls_row_id.argtypes = [vp, ip, ip, dp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp, vp]
+    lib.ls_row_id.restype = ip
     lib.ls_kernel_launches.argtypes = []
     lib.ls_kernel_launches.restype = ctypes.c_longlong
     _lib = lib
@@ -283,6 +285,24 @@ def ls_cgemm_c64(engine, A, B, C, ta=False, tb=False, alpha=1.0, beta=0.0, strea
                                        ctypes.c_void_p(C.data_ptr()), C.shape[2], M * N, batch, _stream(stream)),
            "ls_cgemm_c64")
     return C
+
+
+def ls_row_id(A, eps, precision=LS_FP64, stream=None):
+    """Row ID A ~ U A(J, :) of an m x p complex128 matrix (rows = candidates) by
+    the device column-pivoted QR (Sec. 2.1).  A: numpy array or torch tensor
+    (host or CUDA).  Returns (k, piv[:k] as numpy int array, U as an m x k numpy array)."""
+    lib = load_library()
+    m, p = A.shape
+    ap, keep, _ = _ptr(A, np.complex128)
+    kmax = min(m, p)
+    piv = (ctypes.c_int * max(kmax, 1))()
+    U = np.zeros((m, kmax), np.complex128)
+    k = ctypes.c_int(0)
+    _check(lib.ls_row_id(ap, m, p, eps, precision, ctypes.byref(k), piv, ctypes.c_void_p(U.ctypes.data),
+                         _stream(stream)), "ls_row_id")
+    kk = k.value
+    Uk = U.reshape(-1)[: m * kk].reshape(m, kk).copy()
+    return kk, np.array(piv[:kk], dtype=np.int64), Uk
 
 
 def ls_kernel_launches():

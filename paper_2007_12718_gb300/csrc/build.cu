@@ -423,6 +423,100 @@ __global__ void __launch_bounds__(512) inverse_smem_kernel(cx<R>* X, int n, int 
     for (int j = lane; j < n; j += 32) M[(long long)i * lda + j] = a[i * ls + j];
 }
 
+// Gauss-Jordan inversion without interchanges, register resident: one block per
+// matrix, eight threads per row, thread r of a row group holding columns
+// r, r + 8, ..., r + 8 (CPT - 1) in registers.  Per elimination step the pivot
+// row is staged in a double-buffered shared row (one block barrier per step)
+// and the multiplier a(i, k) comes from a register of the row group by a
+// shuffle.  n <= 8 CPT, blockDim = 8 n rounded up to a warp.  A zero or
+// non-finite pivot sets *err = LS_ESINGULAR (the check is uniform over the
+// block).  Accuracy is checked by the caller (probe vector), with the
+// row-pivoted kernels as the fallback.
+template <class R, int CPT>
+__global__ void __launch_bounds__(1024) gj_reg_kernel(cx<R>* __restrict__ X, int n, int lda, long long sX,
+                                                      int* __restrict__ err) {
+  __shared__ cx<R> prow[2][8 * CPT];
+  const int tid = threadIdx.x, row = tid >> 3, r = tid & 7;
+  const bool live = row < n;
+  cx<R>* M = X + blockIdx.x * sX;
+  cx<R> a[CPT];
+#pragma unroll
+  for (int q = 0; q < CPT; ++q) {
+    const int j = q * 8 + r;
+    a[q] = (live && j < n) ? M[(long long)row * lda + j] : mk<R>(0, 0);
+  }
+  // the column block kq is a compile-time index, so the multiplier is read from
+  // a fixed register of thread kr of the row group
+#pragma unroll
+  for (int kq = 0; kq < CPT; ++kq) {
+    for (int kr = 0; kr < 8; ++kr) {
+      const int k = kq * 8 + kr;
+      if (k >= n) break;
+      cx<R> f;
+      f.re = __shfl_sync(0xffffffffu, a[kq].re, kr, 8);
+      f.im = __shfl_sync(0xffffffffu, a[kq].im, kr, 8);
+      cx<R>* pr = prow[k & 1];
+      if (row == k) {
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) pr[q * 8 + r] = a[q];
+      }
+      __syncthreads();
+      const cx<R> pk = pr[k];
+      const R den = abs2(pk);
+      if (!(den > R(0)) || !(den < R(INFINITY))) {
+        if (tid == 0) atomicExch(err, LS_ESINGULAR);
+        return;
+      }
+      const cx<R> d = inv(pk);
+      if (row == k) {
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) a[q] = a[q] * d;
+        if (r == kr) a[kq] = d;
+      } else {
+        const cx<R> fd = f * d;
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+          const cx<R> pj = pr[q * 8 + r];
+          a[q].re -= fd.re * pj.re - fd.im * pj.im;
+          a[q].im -= fd.re * pj.im + fd.im * pj.re;
+        }
+        if (r == kr) a[kq] = mk<R>(-fd.re, -fd.im);
+      }
+    }
+  }
+  if (live) {
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+      const int j = q * 8 + r;
+      if (j < n) M[(long long)row * lda + j] = a[q];
+    }
+  }
+}
+
+// Largest order handled by gj_reg_kernel (registers per thread: 2 CPT reals).
+template <class R>
+constexpr int gj_reg_max() {
+  return sizeof(R) == 4 ? 128 : 64;
+}
+
+template <class R>
+int invert_reg_nopiv(cx<R>* X, int n, int lda, long long sX, int P, int* err, cudaStream_t st) {
+  if (n <= 0 || P <= 0) return LS_OK;
+  const unsigned thr = (unsigned)(((n * 8 + 31) / 32) * 32);
+  count_launch();
+  if (n <= 32)
+    gj_reg_kernel<R, 4><<<P, thr, 0, st>>>(X, n, lda, sX, err);
+  else if (n <= 64)
+    gj_reg_kernel<R, 8><<<P, thr, 0, st>>>(X, n, lda, sX, err);
+  else if (sizeof(R) == 4 && n <= 96)
+    gj_reg_kernel<R, 12><<<P, thr, 0, st>>>(X, n, lda, sX, err);
+  else if (sizeof(R) == 4 && n <= 128)
+    gj_reg_kernel<R, 16><<<P, thr, 0, st>>>(X, n, lda, sX, err);
+  else
+    return LS_EINVAL;
+  return check_launch("gj_reg");
+}
+
 // Blocked Gauss-Jordan inversion, panel step (one block per matrix).  The nb
 // <= 32 panel columns [k0, k0+nb) of all n rows are loaded to shared memory
 // and eliminated in place with partial row pivoting over the rows not yet used
@@ -444,6 +538,10 @@ __global__ void __launch_bounds__(256) gj_panel_kernel(cx<R>* X, int n, int lda,
   const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lmask = nb >= 32 ? 0xffffffffu : ((1u << nb) - 1u);
   cx<R>* M = X + b * sX;
+  if (tid == 0) {  // valid (identity) interchanges even if the panel stops at a zero pivot
+    for (int jj = 0; jj < nb; ++jj) piv[(long long)b * n + k0 + jj] = k0 + jj;
+    perm[(long long)b * 2 * 64] = -1;
+  }
   for (int i = warp; i < n; i += 8)
     if (lane < nb) pn[i * ldp + lane] = M[(long long)i * lda + k0 + lane];
   __syncthreads();
@@ -575,6 +673,10 @@ __global__ void __launch_bounds__(256) gj_panel_cluster_kernel(cx<R>* X, int n, 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lmask = nb >= 32 ? 0xffffffffu : ((1u << nb) - 1u);
   cx<R>* M = X + mat * sX;
+  if (crank == 0 && tid == 0) {  // valid (identity) interchanges even if the panel stops at a zero pivot
+    for (int jj = 0; jj < nb; ++jj) piv[(long long)mat * n + k0 + jj] = k0 + jj;
+    perm[(long long)mat * 2 * 64] = -1;
+  }
   for (int i = r0 + warp; i < r1; i += 8)
     if (lane < nb) pn[(i - r0) * ldp + lane] = M[(long long)i * lda + k0 + lane];
   __syncthreads();
@@ -714,7 +816,8 @@ __global__ void gj_swap_extract_kernel(cx<R>* X, int n, int lda, long long sX, i
   const int* pr = perm + (long long)b * 2 * 64;
   cx<R> vals[64];
   int cnt = 0;
-  for (; cnt < 64 && pr[2 * cnt] >= 0; ++cnt) vals[cnt] = M[(long long)pr[2 * cnt + 1] * lda + c];
+  for (; cnt < 64 && pr[2 * cnt] >= 0 && pr[2 * cnt] < n && (unsigned)pr[2 * cnt + 1] < (unsigned)n; ++cnt)
+    vals[cnt] = M[(long long)pr[2 * cnt + 1] * lda + c];
   for (int t = 0; t < cnt; ++t) M[(long long)pr[2 * t] * lda + c] = vals[t];
   for (int jj = 0; jj < nb; ++jj) {
     out[(long long)jj * n + c] = M[(long long)(k0 + jj) * lda + c];
@@ -735,6 +838,7 @@ __global__ void unpivot_rows_kernel(cx<R>* X, int n, int lda, long long sX, cons
   if (threadIdx.x == 0)
     for (int k = n - 1; k >= 0; --k) {
       int p = piv[(long long)b * n + k];
+      if ((unsigned)p >= (unsigned)n) p = k;
       int t = idx[k];
       idx[k] = idx[p];
       idx[p] = t;
@@ -848,7 +952,7 @@ void gemv(cudaStream_t st, bool ta, int M, int K, cx<R> alpha, const cx<R>* A, i
 template <class R>
 int invert_batch_nopiv(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int P, void* scratch,
                        size_t scratch_bytes, cudaStream_t st) {
-  const int nb = sizeof(R) == 4 ? 64 : 48;
+  const int nb = gj_reg_max<R>();
   const size_t w_max = nb;
   cx<R>* Ab = reinterpret_cast<cx<R>*>(scratch);
   cx<R>* Mb = Ab + (size_t)P * w_max * w_max;
@@ -862,11 +966,8 @@ int invert_batch_nopiv(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int
     dim3 g((unsigned)std::min<long long>(1024, (tot + 255) / 256), P);
     count_launch();
     gjb_extract_kernel<R><<<g, 256, 0, st>>>(X, n, lda, sX, k0, w, Ab, Mb, Cb);
-    const size_t smem_small = sizeof(cx<R>) * ((size_t)w * (w + 1) + w) + sizeof(int) * w;
-    LS_CUDA_TRY(cudaFuncSetAttribute(inverse_smem_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_small));
-    count_launch();
-    inverse_smem_kernel<R><<<P, 512, smem_small, st>>>(Ab, w, w, (long long)w * w, H->d_err);
+    int rc = invert_reg_nopiv<R>(Ab, w, w, (long long)w * w, P, H->d_err + 3, st);
+    if (rc) return rc;
     gemm<R>(st, false, false, w, n, w, one<R>(), Ab, w, (long long)w * w, Mb, n, tot, zero<R>(), Rb, n, tot, P);
     gemm<R>(st, false, false, n, n, w, mone, Cb, w, tot, Rb, n, tot, one<R>(), X, lda, sX, P);
     gemm<R>(st, false, false, n, w, w, mone, Cb, w, tot, Ab, w, (long long)w * w, zero<R>(), X + k0, lda, sX, P);
@@ -985,8 +1086,8 @@ int build_t(ls_handle* H, cudaStream_t st) {
     size_t P = (size_t)1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = l > 0 ? H->lev[l].k : 0;
     wb = std::max(wb, sizeof(cx<R>) * P * n2 * n2 + sizeof(int) * P * n2);
     wb = std::max(wb, sizeof(cx<R>) * 2 * P * n2 * kp);
-    // Y1, Y2, a copy of Z and the blocked-inverse panels (width <= 64)
-    wb = std::max(wb, sizeof(cx<R>) * P * (3 * kc * kc + 64 * 64 + 3 * 64 * kc) + sizeof(int) * P * (n2 + 256) + 4096);
+    // Y1, Y2, a copy of Z and the blocked-inverse panels (width <= 128)
+    wb = std::max(wb, sizeof(cx<R>) * P * (3 * kc * kc + 128 * 128 + 3 * 128 * kc) + sizeof(int) * P * (n2 + 256) + 4096);
   }
   // apply temporaries (one right-hand side): leaf blocks, per-level expansions
   size_t vec = (size_t)2 * ((size_t)1 << L) * n;
@@ -1055,10 +1156,10 @@ int build_t(ls_handle* H, cudaStream_t st) {
       if ((rc = check_launch("merge gemm"))) return rc;
       prof_end(tg, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * (5.0 * kk), P * 3.0 * 8.0 * (double)kc * kc * kc);
       int ti = prof_begin(st);
-      // W = Z^-1: blocks without interchanges, checked with a probe vector; the
-      // row-pivoted path is the fallback if the check fails
-      const size_t smem_small = sizeof(cx<R>) * ((size_t)kc * (kc + 1) + kc) + sizeof(int) * kc;
-      if (smem_small <= 200 * 1024 || H->opts.merge_pivoting == 1) {
+      // W = Z^-1 without interchanges (register-resident Gauss-Jordan for small
+      // orders, blocked otherwise), checked with a probe vector; the row-pivoted
+      // kernels are the fallback, and the only path when merge_pivoting = 1
+      if (H->opts.merge_pivoting == 1) {
         if ((rc = invert_batch<R>(H, X22, kc, n2, sX, P, scratch, scratch_bytes, st))) return rc;
       } else {
         cx<R>* Zc = reinterpret_cast<cx<R>*>(scratch);  // copy of Z for the fallback
@@ -1067,8 +1168,12 @@ int build_t(ls_handle* H, cudaStream_t st) {
         dim3 gc((unsigned)std::min<long long>(1024, (kk + 255) / 256), P);
         count_launch();
         copy_block_kernel<R><<<gc, 256, 0, st>>>(Zc, kc, kk, X22, n2, sX, kc, kc);
-        if ((rc = invert_batch_nopiv<R>(H, X22, kc, n2, sX, P, scr2, scr2_bytes, st))) return rc;
-        LS_CUDA_TRY(cudaMemsetAsync(H->d_err + 2, 0, sizeof(int), st));
+        LS_CUDA_TRY(cudaMemsetAsync(H->d_err + 2, 0, 2 * sizeof(int), st));
+        if (kc <= gj_reg_max<R>()) {
+          if ((rc = invert_reg_nopiv<R>(X22, kc, n2, sX, P, H->d_err + 3, st))) return rc;
+        } else {
+          if ((rc = invert_batch_nopiv<R>(H, X22, kc, n2, sX, P, scr2, scr2_bytes, st))) return rc;
+        }
         {
           cx<R>* pv = reinterpret_cast<cx<R>*>(scr2);  // v (kc), then u, t, r (P kc each)
           cx<R>* pu = pv + kc;
@@ -1083,13 +1188,13 @@ int build_t(ls_handle* H, cudaStream_t st) {
           count_launch();
           probe_max_kernel<R><<<64, 256, 0, st>>>(pr, pv, kc, (long long)P * kc, H->d_err + 2);
         }
-        int worst_bits = 0;
-        LS_CUDA_TRY(cudaMemcpyAsync(&worst_bits, H->d_err + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+        int flags[2] = {0, 0};  // worst probe residual (float bits), zero-pivot flag
+        LS_CUDA_TRY(cudaMemcpyAsync(flags, H->d_err + 2, sizeof(flags), cudaMemcpyDeviceToHost, st));
         LS_CUDA_TRY(cudaStreamSynchronize(st));
         float worst;
-        memcpy(&worst, &worst_bits, sizeof(float));
+        memcpy(&worst, &flags[0], sizeof(float));
         const float limit = sizeof(R) == 4 ? 1e-3f : 1e-9f;
-        if (!(worst <= limit * sqrtf((float)kc))) {
+        if (flags[1] != 0 || !(worst <= limit * sqrtf((float)kc))) {
           // restore Z and invert with row interchanges
           count_launch();
           copy_block_kernel<R><<<gc, 256, 0, st>>>(X22, n2, sX, Zc, kc, kk, kc, kc);
@@ -1476,8 +1581,12 @@ int hbs_apply_graph_init(ls_handle* H) {
   long long before = ::ls_kernel_launches();
   cudaGraph_t graph;
   LS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  rc = H->prec == LS_FP64 ? apply_core<double>(H, H->slots, cs) : apply_core<float>(H, H->slots, cs);
-  cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  cudaError_t e;
+  {
+    CaptureScope capturing;
+    rc = H->prec == LS_FP64 ? apply_core<double>(H, H->slots, cs) : apply_core<float>(H, H->slots, cs);
+    e = cudaStreamEndCapture(cs, &graph);
+  }
   H->apply_nodes = ::ls_kernel_launches() - before;
   count_launch(-H->apply_nodes);  // recorded, not launched
   if (rc) {

@@ -115,7 +115,21 @@ __device__ __forceinline__ bool grid_sync(const GridSync& g, unsigned int nblock
 }
 
 // Counter of kernel launches made by this library (reported by ls_kernel_launches).
-void count_launch(long long n = 1);
+// With the environment variable LS_DEBUG_SYNC=1 every counted launch site first
+// synchronizes the device and reports (stderr) the first device error together
+// with the previous launch site, which localises an asynchronous fault.
+struct LaunchCount {
+  long long n = 1;
+  LaunchCount() {}
+  LaunchCount(long long v) : n(v) {}
+};
+void count_launch_at(const char* file, int line, LaunchCount c);
+#define count_launch(...) ::ls::count_launch_at(__FILE__, __LINE__, ::ls::LaunchCount{__VA_ARGS__})
+// Suppresses the debug synchronisation while a stream is being captured.
+struct CaptureScope {
+  CaptureScope();
+  ~CaptureScope();
+};
 
 }  // namespace ls
 

@@ -84,22 +84,53 @@ __device__ __forceinline__ R project_update(const cx<R>* q, cx<R>* a, int p, int
   return warp_sum_r(n0 + n1);
 }
 
+// 64-bit pivot key: the residual norm's leading bits (all 32 of a float, the
+// top 44 of a double; non-negative, so integer order is numeric order) above
+// 20 bits of (2^20 - 1 - index).  The integer maximum of the keys is the
+// largest norm, lowest index on ties; key 0 means "no candidate".
+__device__ __forceinline__ unsigned long long piv_key(float nrm, int idx) {
+  return ((unsigned long long)__float_as_uint(nrm) << 20) | (unsigned long long)(0xFFFFF - idx);
+}
+__device__ __forceinline__ unsigned long long piv_key(double nrm, int idx) {
+  return (((unsigned long long)__double_as_longlong(nrm) >> 20) << 20) | (unsigned long long)(0xFFFFF - idx);
+}
+__device__ __forceinline__ int piv_key_index(unsigned long long key) { return 0xFFFFF - (int)(key & 0xFFFFF); }
+
+// Loads that bypass L1 (data written by other blocks of the same grid).
+template <class R>
+__device__ __forceinline__ cx<R> ldcg_cx(const cx<R>* p);
+template <>
+__device__ __forceinline__ cx<float> ldcg_cx(const cx<float>* p) {
+  float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return mk<float>(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ cx<double> ldcg_cx(const cx<double>* p) {
+  double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return mk<double>(v.x, v.y);
+}
+
 // Column-pivoted QR ID of the candidate-major matrix A (m candidates, each a
 // length-p vector at A + c*p).  Block b owns candidates [c0, c0 + mc) and keeps
 // their residual vectors in shared memory when they fit (else in the global
 // working copy Aw).  Per pivot step: every block publishes its best local
-// candidate (residual norm, index, vector) in a double-buffered slot; one
-// bounded grid barrier; every block reduces the slots in parallel, fetches
-// the winning vector q and projects it out of its own candidates (one warp
-// per candidate: a_c -= q (q^H a_c) / |q|^2, then the exact new norm).
+// candidate (norm and block total in a parity slot, vector in a parity vector
+// slot) and folds its key into the step's global key (atomic max); one bounded
+// grid barrier; every block reads the step's key, the winner's slot and vector
+// and the block totals (fixed order: every block takes the same stopping
+// decision), and projects the winner out of its own candidates (one warp per
+// candidate: a_c -= q (q^H a_c) / |q|^2, then the exact new norm, folded into
+// the block's next key with a shared-memory atomic max).  gkey[0..kmax] must
+// be zero at launch; m < 2^20.
 // Outputs: piv[0..k), rank[0] = k, U (m x k, row-major, stride k).
 template <class R>
 __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ A, int m, int p, int kmax,
                                                       double eps, int use_smem, cx<R>* __restrict__ Aw,
                                                       cx<R>* __restrict__ Rm, int* __restrict__ sel,
                                                       IdSlot<R>* __restrict__ slots, cx<R>* __restrict__ pslots,
-                                                      int* __restrict__ piv, int* __restrict__ rank,
-                                                      cx<R>* __restrict__ U, cx<R>* __restrict__ RT, GridSync gs) {
+                                                      unsigned long long* __restrict__ gkey, int* __restrict__ piv,
+                                                      int* __restrict__ rank, cx<R>* __restrict__ U,
+                                                      cx<R>* __restrict__ RT, GridSync gs, int* __restrict__ err) {
   extern __shared__ unsigned char smraw[];
   cx<R>* pvec = reinterpret_cast<cx<R>*>(smraw);  // p
   const int nblk = gridDim.x, blk = blockIdx.x;
@@ -107,12 +138,14 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
   const int per = (m + nblk - 1) / nblk;
   const int c0 = min(m, blk * per), c1 = min(m, c0 + per), mc = c1 - c0;
   cx<R>* cand = use_smem ? pvec + p : Aw + (long long)c0 * p;
+  __shared__ unsigned long long s_key[2];
   __shared__ R s_nrm[64];
   __shared__ int s_sel[64];
   __shared__ R s_best, s_tol2;
-  __shared__ int s_idx, s_bw, s_stop, s_lbest;
+  __shared__ int s_stop;
   unsigned int epoch = 0;
 
+  if (tid < 2) s_key[tid] = 0ULL;
   for (long long t = tid; t < (long long)mc * p; t += blockDim.x) cand[t] = A[(long long)c0 * p + t];
   __syncthreads();
   for (int c = warp; c < mc; c += nwarp) {
@@ -123,6 +156,7 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
       s_nrm[c] = acc;
       s_sel[c] = -1;
       sel[c0 + c] = -1;
+      atomicMax(&s_key[0], piv_key(acc, c0 + c));
     }
   }
   __syncthreads();
@@ -130,111 +164,85 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
   int k = 0;
   for (int j = 0;; ++j) {
     const int par = j & 1;
-    if (warp == 0) {  // local best and total over this block's active candidates
-      R best = R(-1), total = R(0);
-      int idx = -1;
-      for (int c = lane; c < mc; c += 32) {
-        if (s_sel[c] != -1) continue;
-        R v = s_nrm[c];
-        total += v;
-        if (v > best) {
-          best = v;
-          idx = c;
-        }
-      }
-      for (int o = 16; o; o >>= 1) {
-        R ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-        total += __shfl_xor_sync(0xffffffffu, total, o);
-        if (ob > best || (ob == best && oi >= 0 && (idx < 0 || oi < idx))) {
-          best = ob;
-          idx = oi;
-        }
-      }
+    const unsigned long long kb = s_key[par];
+    const int lb = kb ? piv_key_index(kb) - c0 : -1;  // this block's best candidate (local index)
+    if (warp == 0) {
+      R total = R(0);
+      for (int c = lane; c < mc; c += 32)
+        if (s_sel[c] == -1) total += s_nrm[c];
+      total = warp_sum_r(total);
       if (lane == 0) {
         IdSlot<R> sl;
-        sl.best = best;
+        sl.best = lb >= 0 ? s_nrm[lb] : R(0);
         sl.total = total;
-        sl.idx = idx < 0 ? -1 : c0 + idx;
+        sl.idx = lb >= 0 ? c0 + lb : -1;
         sl.pad = 0;
         slots[par * nblk + blk] = sl;
-        s_lbest = idx;
+        if (kb) atomicMax(&gkey[j], kb);
       }
     }
-    __syncthreads();
-    if (s_lbest >= 0) {
+    if (lb >= 0) {
       cx<R>* dst = pslots + ((long long)par * nblk + blk) * p;
-      const cx<R>* src = cand + (long long)s_lbest * p;
+      const cx<R>* src = cand + (long long)lb * p;
       for (int i = tid; i < p; i += blockDim.x) dst[i] = src[i];
     }
     if (!grid_sync(gs, nblk, epoch)) return;
-    if (warp == 0) {  // global winner: largest norm, lowest candidate index on ties
-      R best = R(-1), total = R(0);
-      int idx = -1, bw = -1;
-      for (int b = lane; b < nblk; b += 32) {
-        IdSlot<R> sl = slots[par * nblk + b];
-        total += sl.total;
-        if (sl.idx >= 0 && (sl.best > best || (sl.best == best && sl.idx < idx))) {
-          best = sl.best;
-          idx = sl.idx;
-          bw = b;
-        }
-      }
-      for (int o = 16; o; o >>= 1) {
-        R ob = __shfl_xor_sync(0xffffffffu, best, o);
-        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-        int obw = __shfl_xor_sync(0xffffffffu, bw, o);
-        total += __shfl_xor_sync(0xffffffffu, total, o);
-        if (oi >= 0 && (ob > best || (ob == best && (idx < 0 || oi < idx)))) {
-          best = ob;
-          idx = oi;
-          bw = obw;
-        }
-      }
+    const unsigned long long key = __ldcg(&gkey[j]);
+    int idx = key ? piv_key_index(key) : -1;
+    const int bw = idx >= 0 ? idx / per : 0;
+    if (idx >= m || (idx >= 0 && (bw >= nblk || idx - bw * per >= 64))) {  // cannot happen; uniform over the grid
+      if (tid == 0) atomicExch(err, 1);
+      idx = -1;
+    }
+    if (warp == 0) {
+      R total = R(0);
+      for (int b = lane; b < nblk; b += 32) total += __ldcg(&slots[par * nblk + b].total);
+      total = warp_sum_r(total);
       if (lane == 0) {
         if (j == 0) s_tol2 = (R)(eps * eps) * total;
+        const R best = idx >= 0 ? __ldcg(&slots[par * nblk + bw].best) : R(0);
         s_best = best;
-        s_idx = idx;
-        s_bw = bw;
         s_stop = (j == kmax) || idx < 0 || !(best > R(0)) || total <= s_tol2;
+        s_key[par] = 0ULL;  // published; reused for step j + 2
       }
+    }
+    if (idx >= 0) {
+      const cx<R>* src = pslots + ((long long)par * nblk + bw) * p;
+      for (int i = tid; i < p; i += blockDim.x) pvec[i] = ldcg_cx(src + i);
     }
     __syncthreads();
     if (s_stop) {
       k = j;
       break;
     }
-    const int pv = s_idx;
-    const R nu = sqrt(s_best);
-    const R inu2 = R(1) / s_best;
-    {
-      const cx<R>* src = pslots + ((long long)par * nblk + s_bw) * p;
-      for (int i = tid; i < p; i += blockDim.x) pvec[i] = src[i];
+    const R best = s_best;
+    const R nu = sqrt(best);
+    const R inu2 = R(1) / best;
+    if (blk == bw && tid == 0) {
+      s_sel[idx - c0] = j;
+      sel[idx] = j;
+      piv[j] = idx;
+      Rm[(long long)j * m + idx] = mk<R>(nu, R(0));
     }
-    if (blk == s_bw && tid == 0) {
-      s_sel[pv - c0] = j;
-      sel[pv] = j;
-      piv[j] = pv;
-      Rm[(long long)j * m + pv] = mk<R>(nu, R(0));
-    }
-    __syncthreads();
     for (int c = warp; c < mc; c += nwarp) {
-      if (s_sel[c] != -1) continue;
+      if (c0 + c == idx || s_sel[c] != -1) continue;
       cx<R>* a = cand + (long long)c * p;
       cx<R> d = project_coeff(pvec, a, p, lane, inu2);  // coefficient of the pivot vector
       R nr = project_update(pvec, a, p, lane, d);
       if (lane == 0) {
         s_nrm[c] = nr;
         Rm[(long long)j * m + c0 + c] = scale(d, nu);  // R(j, c) = q^H a = (a_pv^H a) / nu
+        atomicMax(&s_key[par ^ 1], piv_key(nr, c0 + c));
       }
     }
     __syncthreads();
   }
   if (blk == 0 && tid == 0) rank[0] = k;
+  if (!grid_sync(gs, nblk, epoch)) return;  // piv and Rm complete
   // R11 gathered by columns: RT[a][b] = R(b, piv[a]) for b <= a (rows of RT contiguous)
   for (long long t = (long long)blk * blockDim.x + tid; t < (long long)k * k; t += (long long)nblk * blockDim.x) {
     int a = (int)(t / k), bb = (int)(t % k);
-    RT[t] = bb <= a ? Rm[(long long)bb * m + piv[a]] : mk<R>(0, 0);
+    RT[t] = bb <= a ? ldcg_cx(Rm + (long long)bb * m + __ldcg(piv + a)) : mk<R>(0, 0);
   }
   if (!grid_sync(gs, nblk, epoch)) return;
   // U rows: identity on the skeleton, T = R11^-1 R12 on the rest: one warp per
@@ -247,14 +255,14 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
       for (int a = lane; a < k; a += 32) U[(long long)c * k + a] = mk<R>(a == sc ? R(1) : R(0), R(0));
       continue;
     }
-    for (int a = lane; a < k; a += 32) t[a] = Rm[(long long)a * m + c];
+    for (int a = lane; a < k; a += 32) t[a] = ldcg_cx(Rm + (long long)a * m + c);
     __syncwarp();
     for (int a = k - 1; a >= 0; --a) {
       const cx<R>* col = RT + (long long)a * k;
-      const cx<R> ta = t[a] * inv(col[a]);
+      const cx<R> ta = t[a] * inv(ldcg_cx(col + a));
       __syncwarp();
       for (int bb = lane; bb < a; bb += 32) {
-        cx<R> v = t[bb], r = col[bb];
+        cx<R> v = t[bb], r = ldcg_cx(col + bb);
         v.re -= r.re * ta.re - r.im * ta.im;
         v.im -= r.re * ta.im + r.im * ta.re;
         t[bb] = v;
@@ -267,38 +275,23 @@ __global__ void __launch_bounds__(256) cpqr_id_kernel(const cx<R>* __restrict__ 
   }
 }
 
-// Pivot order of the ID: larger residual norm first, lower candidate index on
-// ties; idx < 0 marks "no candidate".
-template <class R>
-__device__ __forceinline__ bool piv_better(R b1, int i1, R b2, int i2) {
-  return i1 >= 0 && (i2 < 0 || b1 > b2 || (b1 == b2 && i1 < i2));
-}
-template <class R>
-__device__ __forceinline__ void warp_argmax(R& best, int& idx) {
-  for (int o = 16; o; o >>= 1) {
-    R ob = __shfl_xor_sync(0xffffffffu, best, o);
-    int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-    if (piv_better(ob, oi, best, idx)) {
-      best = ob;
-      idx = oi;
-    }
-  }
-}
-
 // The same ID on one thread-block cluster (CL <= 16 blocks of 1024 threads,
 // candidates resident in shared memory, normally one candidate per warp).
-// Per pivot step: warp 0 of each block publishes its best local candidate in
-// a parity slot; one cluster barrier; every warp reads the CL slots through
-// distributed shared memory and resolves the winner itself (no second block
-// barrier); the block copies the winning vector from the owner's shared
-// memory and projects it out of its own candidates.  Same outputs as
-// cpqr_id_kernel.
+// Per pivot step the critical path is: each warp projects its candidate and
+// folds the new norm's key into the block's key with a shared-memory atomic
+// max; one block barrier; lanes r < CL of warp 0 store the block's key and its
+// best norm, and lanes of warp 1 the block's residual total, into slot
+// [this block] of block r (distributed shared memory stores); one cluster
+// barrier; every block then finds the winner, its norm and the cluster total
+// in its own shared memory (fixed summation order, so every block takes the
+// same stopping decision) and copies the winning vector from the owner; one
+// block barrier.  Same outputs as cpqr_id_kernel.  Needs m < 2^20.
 template <class R>
 __global__ void __launch_bounds__(1024) cpqr_id_cluster_kernel(const cx<R>* __restrict__ A, int m, int p, int kmax,
                                                                double eps, cx<R>* __restrict__ Rm,
                                                                int* __restrict__ sel, int* __restrict__ piv,
                                                                int* __restrict__ rank, cx<R>* __restrict__ U,
-                                                               cx<R>* __restrict__ RT) {
+                                                               cx<R>* __restrict__ RT, int* __restrict__ err) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ unsigned char smraw[];
@@ -308,11 +301,16 @@ __global__ void __launch_bounds__(1024) cpqr_id_cluster_kernel(const cx<R>* __re
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarp = blockDim.x >> 5;
   const int per = (m + CL - 1) / CL;
   const int c0 = min(m, crank * per), c1 = min(m, c0 + per), mc = c1 - c0;
-  __shared__ R s_sbest[2], s_stotal[2];
-  __shared__ int s_sidx[2];
+  __shared__ unsigned long long s_key[2];     // this block's best key, by step parity
+  __shared__ unsigned long long s_ck[2][16];  // every block's best key, by step parity and block
+  __shared__ R s_cb[2][16];                   // every block's best norm
+  __shared__ R s_ct[2][16];                   // every block's residual total
+  __shared__ R s_best;                        // winner's residual norm^2
+  __shared__ int s_stop;
   __shared__ R s_nrm[64];
   __shared__ int s_sel[64];
 
+  if (tid < 2) s_key[tid] = 0ULL;
   for (long long t = tid; t < (long long)mc * p; t += blockDim.x) cand[t] = A[(long long)c0 * p + t];
   __syncthreads();
   for (int c = warp; c < mc; c += nwarp) {
@@ -323,6 +321,7 @@ __global__ void __launch_bounds__(1024) cpqr_id_cluster_kernel(const cx<R>* __re
       s_nrm[c] = acc;
       s_sel[c] = -1;
       sel[c0 + c] = -1;
+      atomicMax(&s_key[0], piv_key(acc, c0 + c));
     }
   }
   __syncthreads();
@@ -330,64 +329,73 @@ __global__ void __launch_bounds__(1024) cpqr_id_cluster_kernel(const cx<R>* __re
   int k = 0;
   for (int j = 0;; ++j) {
     const int par = j & 1;
-    if (warp == 0) {  // local best and total over the block's active candidates (mc <= 64)
-      R best = R(-1), total = R(0);
-      int idx = -1;
-      for (int c = lane; c < mc; c += 32) {
-        if (s_sel[c] != -1) continue;
-        const R v = s_nrm[c];
-        total += v;
-        if (piv_better(v, c0 + c, best, idx)) {
-          best = v;
-          idx = c0 + c;
-        }
+    // this block's key, best norm and total for step j, stored into every block
+    if (warp == 0) {
+      const unsigned long long kb = s_key[par];
+      const int lb = kb ? piv_key_index(kb) - c0 : -1;
+      const R nb = (lb >= 0 && lb < mc) ? s_nrm[lb] : R(0);
+      if (lane < CL) {
+        *cluster.map_shared_rank(&s_ck[par][crank], lane) = kb;
+        *cluster.map_shared_rank(&s_cb[par][crank], lane) = nb;
       }
-      warp_argmax(best, idx);
-      total = warp_sum_r(total);
-      if (lane == 0) {
-        s_sbest[par] = best;
-        s_stotal[par] = total;
-        s_sidx[par] = idx;
-      }
+    } else if (warp == 1) {
+      R tot = 0;
+      for (int c = lane; c < mc; c += 32)
+        if (s_sel[c] == -1) tot += s_nrm[c];
+      tot = warp_sum_r(tot);
+      if (lane < CL) *cluster.map_shared_rank(&s_ct[par][crank], lane) = tot;
     }
     cluster.sync();
-    // every warp resolves the cluster-wide winner (lane r reads block r's slot)
-    R best = R(-1), total = R(0);
-    int idx = -1;
-    if (lane < CL) {
-      best = *cluster.map_shared_rank(&s_sbest[par], lane);
-      total = *cluster.map_shared_rank(&s_stotal[par], lane);
-      idx = *cluster.map_shared_rank(&s_sidx[par], lane);
+    // winner: the largest key over the CL slots (every lane of every warp ends with it)
+    unsigned long long key = lane < CL ? s_ck[par][lane] : 0ULL;
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o);
+      key = ok > key ? ok : key;
     }
-    warp_argmax(best, idx);
-    total = warp_sum_r(total);
-    if (j == 0) tol2 = (R)(eps * eps) * total;
-    if ((j == kmax) || idx < 0 || !(best > R(0)) || total <= tol2) {
-      k = j;
-      break;
+    int idx = key ? piv_key_index(key) : -1;
+    const int bw = idx >= 0 ? idx / per : 0;
+    if (idx >= m || (idx >= 0 && (bw >= CL || idx - bw * per >= 64))) {  // cannot happen; uniform over the cluster
+      if (tid == 0) atomicExch(err, 1);
+      idx = -1;
     }
-    const int bw = idx / per;
-    const R nu = sqrt(best);
-    const R inu2 = R(1) / best;
-    {
+    if (warp == 0) {
+      R tot = lane < CL ? s_ct[par][lane] : R(0);
+      tot = warp_sum_r(tot);
+      if (lane == 0) {
+        if (j == 0) tol2 = (R)(eps * eps) * tot;
+        const R best = idx >= 0 ? s_cb[par][bw] : R(0);
+        s_best = best;
+        s_stop = (j == kmax) || idx < 0 || !(best > R(0)) || tot <= tol2;
+        s_key[par] = 0ULL;  // this block's key for step j has been published
+      }
+    }
+    if (idx >= 0) {
       const cx<R>* src = cluster.map_shared_rank(cand + (long long)(idx - bw * per) * p, bw);
       for (int i = tid; i < p; i += blockDim.x) pvec[i] = src[i];
     }
+    __syncthreads();
+    if (s_stop) {
+      k = j;
+      break;
+    }
+    const R best = s_best;
+    const R nu = sqrt(best);
+    const R inu2 = R(1) / best;
     if (crank == bw && tid == 0) {
       s_sel[idx - c0] = j;
       sel[idx] = j;
       piv[j] = idx;
       Rm[(long long)j * m + idx] = mk<R>(nu, R(0));
     }
-    __syncthreads();
     for (int c = warp; c < mc; c += nwarp) {
-      if (s_sel[c] != -1) continue;
+      if (c0 + c == idx || s_sel[c] != -1) continue;
       cx<R>* a = cand + (long long)c * p;
       cx<R> d = project_coeff(pvec, a, p, lane, inu2);  // coefficient of the pivot vector
       R nr = project_update(pvec, a, p, lane, d);
       if (lane == 0) {
         s_nrm[c] = nr;
         Rm[(long long)j * m + c0 + c] = scale(d, nu);  // R(j, c) = q^H a = (a_pv^H a) / nu
+        atomicMax(&s_key[par ^ 1], piv_key(nr, c0 + c));
       }
     }
     __syncthreads();
@@ -396,7 +404,7 @@ __global__ void __launch_bounds__(1024) cpqr_id_cluster_kernel(const cx<R>* __re
   cluster.sync();  // every remote read is done; piv and Rm are complete and visible
   for (long long t = (long long)crank * blockDim.x + tid; t < (long long)k * k; t += (long long)CL * blockDim.x) {
     int a = (int)(t / k), bb = (int)(t % k);
-    RT[t] = bb <= a ? Rm[(long long)bb * m + piv[a]] : mk<R>(0, 0);
+    RT[t] = bb <= a ? ldcg_cx(Rm + (long long)bb * m + __ldcg(piv + a)) : mk<R>(0, 0);
   }
   cluster.sync();
   cx<R>* t = pvec + (long long)warp * kmax;
@@ -406,14 +414,14 @@ __global__ void __launch_bounds__(1024) cpqr_id_cluster_kernel(const cx<R>* __re
       for (int a = lane; a < k; a += 32) U[(long long)c * k + a] = mk<R>(a == sc ? R(1) : R(0), R(0));
       continue;
     }
-    for (int a = lane; a < k; a += 32) t[a] = Rm[(long long)a * m + c];
+    for (int a = lane; a < k; a += 32) t[a] = ldcg_cx(Rm + (long long)a * m + c);
     __syncwarp();
     for (int a = k - 1; a >= 0; --a) {
       const cx<R>* col = RT + (long long)a * k;
-      const cx<R> ta = t[a] * inv(col[a]);
+      const cx<R> ta = t[a] * inv(ldcg_cx(col + a));
       __syncwarp();
       for (int bb = lane; bb < a; bb += 32) {
-        cx<R> v = t[bb], r = col[bb];
+        cx<R> v = t[bb], r = ldcg_cx(col + bb);
         v.re -= r.re * ta.re - r.im * ta.im;
         v.im -= r.re * ta.im + r.im * ta.re;
         t[bb] = v;
@@ -454,6 +462,169 @@ int upload_block(const std::vector<int>& rx, const std::vector<int>& ry, const s
   // host vector must outlive the copy
   LS_CUDA_TRY(cudaStreamSynchronize(st));
   return check_launch("kernel block");
+}
+
+// Row ID of the device matrix A (m candidates x p, candidate-major) by the
+// column-pivoted QR kernels above: one thread-block cluster when the
+// candidates fit in the shared memory of at most 16 blocks, else one
+// cooperative grid.  Returns k, the pivots (host) and, if Uout is not null,
+// U (m x k, device, row-major).  sync_buf: 64 zeroed-on-entry bytes of device
+// scratch for the grid barrier and the kernels' status words.
+template <class R>
+int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_buf, cudaStream_t st, int* k_out,
+               std::vector<int>* hp_out, cx<R>* Uout) {
+  int rc;
+  std::vector<int>& hp = *hp_out;
+  const int kmax = std::min(m, p);
+  if (m >= (1 << 20)) {  // pivot keys carry 20 index bits
+    set_last_error_text("too many ID candidates");
+    return LS_EINVAL;
+  }
+  // blocks and candidates per block (at most 64 per block)
+  int nblk = std::max(1, std::min(nsm, (m + 1) / 2));
+  int per = (m + nblk - 1) / nblk;
+  if (per > 64) {
+    per = 64;
+    nblk = (m + per - 1) / per;
+  }
+  size_t loop_smem = sizeof(cx<R>) * ((size_t)p + (size_t)per * p);
+  size_t tail_smem = sizeof(cx<R>) * (size_t)8 * kmax;
+  int use_smem = loop_smem <= 200 * 1024;
+  size_t smem = std::max(use_smem ? loop_smem : sizeof(cx<R>) * (size_t)p, tail_smem);
+  if (smem > 220 * 1024) {
+    set_last_error_text("proxy block too large for the ID kernel");
+    return LS_EINVAL;
+  }
+  size_t need = 64 * 256 + sizeof(cx<R>) * ((size_t)m * p * (use_smem ? 0 : 1) + (size_t)kmax * m + (size_t)m * kmax +
+                                 (size_t)kmax * kmax + (size_t)2 * nblk * p) +
+                sizeof(int) * (2 * m + 8) + sizeof(IdSlot<R>) * 2 * (nblk + 1) +
+                sizeof(unsigned long long) * ((size_t)kmax + 1) + 2048;
+  char* wsp = nullptr;
+  if ((rc = dalloc((void**)&wsp, need))) return rc;
+  auto carve = [&](size_t bytes) {
+    char* r = wsp;
+    wsp += (bytes + 255) & ~(size_t)255;
+    return r;
+  };
+  char* wbase = wsp;
+  cx<R>* Aw = use_smem ? nullptr : reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)m * p));
+  cx<R>* Rm = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)kmax * m));
+  cx<R>* Ut = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)m * kmax));
+  cx<R>* RT = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)kmax * kmax));
+  cx<R>* pslots = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)2 * nblk * p));
+  int* sel = reinterpret_cast<int*>(carve(sizeof(int) * m));
+  int* piv = reinterpret_cast<int*>(carve(sizeof(int) * m));
+  int* rank = reinterpret_cast<int*>(carve(sizeof(int) * 8));
+  IdSlot<R>* slots = reinterpret_cast<IdSlot<R>*>(carve(sizeof(IdSlot<R>) * 2 * (nblk + 1)));
+  unsigned long long* gkey =
+      reinterpret_cast<unsigned long long*>(carve(sizeof(unsigned long long) * ((size_t)kmax + 1)));
+  wsp = wbase;
+  // one cluster when the candidates fit in the shared memory of CL blocks: the
+  // smallest CL with at most 32 candidates per block (4 per warp), else at most 64
+  int maxcl = 16;
+  if (cudaFuncSetAttribute(cpqr_id_cluster_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    maxcl = 8;
+  }
+  const size_t cl_tail_smem = sizeof(cx<R>) * (size_t)32 * kmax;
+  auto cl_smem = [&](int cl) {
+    const int pc = (m + cl - 1) / cl;
+    return std::max(sizeof(cx<R>) * ((size_t)p + (size_t)pc * p), cl_tail_smem);
+  };
+  // the smallest cluster with at most one candidate per warp (32 per block), else at most 64 per block
+  int CL = 0;
+  for (int lim : {32, 64}) {
+    for (int cl = 1; cl <= maxcl && !CL; ++cl)
+      if ((m + cl - 1) / cl <= lim && cl_smem(cl) <= 220 * 1024) CL = cl;
+    if (CL) break;
+  }
+  bool use_cluster = CL > 0;
+  if (!use_cluster) CL = 1;
+  const size_t smem_cl = cl_smem(CL);
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  if (use_cluster) {
+    LS_CUDA_TRY(cudaFuncSetAttribute(cpqr_id_cluster_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_cl));
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = smem_cl;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, (void*)cpqr_id_cluster_kernel<R>, &cfg) != cudaSuccess || ncl < 1) {
+      cudaGetLastError();
+      use_cluster = false;
+    }
+  }
+  double eps = eps_in;
+  LS_CUDA_TRY(cudaMemsetAsync(sync_buf, 0, 64, st));
+  int tk = prof_begin(st);
+  if (use_cluster) {
+    count_launch();
+    LS_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpqr_id_cluster_kernel<R>, (const cx<R>*)A, m, p, kmax, eps, Rm, sel, piv,
+                                   rank, Ut, RT, sync_buf + 3));
+  } else {
+    const void* kfn = (const void*)cpqr_id_kernel<R>;
+    LS_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, smem));
+    if (per_sm < 1 || nblk > per_sm * nsm) {
+      set_last_error_text("ID kernel cannot be co-resident");
+      return LS_EINVAL;
+    }
+    GridSync gs;
+    gs.count = reinterpret_cast<unsigned*>(sync_buf);
+    gs.gen = reinterpret_cast<unsigned*>(sync_buf) + 1;
+    gs.abort = sync_buf + 2;
+    const cx<R>* Ac = A;
+    int* ierr = sync_buf + 3;
+    LS_CUDA_TRY(cudaMemsetAsync(gkey, 0, sizeof(unsigned long long) * ((size_t)kmax + 1), st));
+    void* args[] = {&Ac, (void*)&m, (void*)&p, (void*)&kmax, &eps, &use_smem, &Aw, &Rm, &sel, &slots, &pslots,
+                    &gkey, &piv, &rank, &Ut, &RT, &gs, &ierr};
+    count_launch();
+    LS_CUDA_TRY(cudaLaunchCooperativeKernel(kfn, dim3(nblk), dim3(256), args, smem, st));
+  }
+  int k = 0, flags[2] = {0, 0};  // abort (barrier timeout), index check
+  LS_CUDA_TRY(cudaMemcpyAsync(&k, rank, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LS_CUDA_TRY(cudaMemcpyAsync(flags, sync_buf + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  LS_CUDA_TRY(cudaStreamSynchronize(st));
+  const int abort_flag = flags[0];
+  if (flags[1]) {
+    set_last_error_text("ID kernel: pivot index check failed");
+    return LS_ECUDA;
+  }
+  // CPQR work: two projections and a norm (36 p real flops) per active candidate and step
+  prof_end(tk, PR_CPQR, st, sizeof(cx<R>) * (double)m * p * 2.0 * k,
+           36.0 * p * ((double)m * k - 0.5 * (double)k * k));
+  if (abort_flag) {
+    ls::dfree(wsp);
+    return LS_ETIMEOUT;
+  }
+  if (k < 0 || k > kmax) {
+    set_last_error_text("ID kernel returned an invalid rank");
+    return LS_ECUDA;
+  }
+  hp.assign(k > 0 ? k : 1, 0);
+  if (k > 0) LS_CUDA_TRY(cudaMemcpyAsync(hp.data(), piv, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
+  if (k > 0 && Uout)
+    LS_CUDA_TRY(cudaMemcpyAsync(Uout, Ut, sizeof(cx<R>) * (size_t)m * k, cudaMemcpyDeviceToDevice, st));
+  LS_CUDA_TRY(cudaStreamSynchronize(st));
+  ls::dfree(wsp);
+  for (int a = 0; a < k; ++a)
+    if (hp[a] < 0 || hp[a] >= m) {
+      set_last_error_text("ID kernel returned an invalid pivot");
+      return LS_ECUDA;
+    }
+  *k_out = k;
+  return LS_OK;
 }
 
 template <class R>
@@ -511,136 +682,18 @@ int compress_t(ls_handle* H, cudaStream_t st) {
       if ((rc = check_launch("identity U"))) return rc;
       continue;
     }
-    const int kmax = std::min(m, p);
+    int k = 0;
+    std::vector<int> hp;
+    cx<R>* A = nullptr;
+    if ((rc = dalloc((void**)&A, sizeof(cx<R>) * (size_t)m * p))) return rc;
     if (dint) ls::dfree(dint);
     dint = nullptr;
     if ((rc = dalloc((void**)&dint, sizeof(int) * (2 * m + 2 * p + 8)))) return rc;
-    // blocks and candidates per block (at most 64 per block)
-    int nblk = std::max(1, std::min(H->nsm, (m + 1) / 2));
-    int per = (m + nblk - 1) / nblk;
-    if (per > 64) {
-      per = 64;
-      nblk = (m + per - 1) / per;
-    }
-    size_t loop_smem = sizeof(cx<R>) * ((size_t)p + (size_t)per * p);
-    size_t tail_smem = sizeof(cx<R>) * (size_t)8 * kmax;
-    int use_smem = loop_smem <= 200 * 1024;
-    size_t smem = std::max(use_smem ? loop_smem : sizeof(cx<R>) * (size_t)p, tail_smem);
-    if (smem > 220 * 1024) {
-      set_last_error_text("proxy block too large for the ID kernel");
-      return LS_EINVAL;
-    }
-    size_t need = 64 * 256 + sizeof(cx<R>) * ((size_t)m * p * (use_smem ? 1 : 2) + (size_t)kmax * m + (size_t)m * kmax +
-                                   (size_t)kmax * kmax + (size_t)2 * nblk * p) +
-                  sizeof(int) * (2 * m + 8) + sizeof(IdSlot<R>) * 2 * (nblk + 1) + 1024;
-    char* wsp = nullptr;
-    if ((rc = dalloc((void**)&wsp, need))) return rc;
-    auto carve = [&](size_t bytes) {
-      char* r = wsp;
-      wsp += (bytes + 255) & ~(size_t)255;
-      return r;
-    };
-    char* wbase = wsp;
-    cx<R>* A = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)m * p));
-    cx<R>* Aw = use_smem ? nullptr : reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)m * p));
-    cx<R>* Rm = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)kmax * m));
-    cx<R>* Ut = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)m * kmax));
-    cx<R>* RT = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)kmax * kmax));
-    cx<R>* pslots = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)2 * nblk * p));
-    int* sel = reinterpret_cast<int*>(carve(sizeof(int) * m));
-    int* piv = reinterpret_cast<int*>(carve(sizeof(int) * m));
-    int* rank = reinterpret_cast<int*>(carve(sizeof(int) * 8));
-    IdSlot<R>* slots = reinterpret_cast<IdSlot<R>*>(carve(sizeof(IdSlot<R>) * 2 * (nblk + 1)));
-    wsp = wbase;
     if ((rc = upload_block<R>(rows_x, rows_y, px, py, A, dint, st, H->ks_prec, KernelTable{H->ktab, H->ktx, H->kty}))) return rc;
-    // one cluster when the candidates fit in the shared memory of CL blocks: the
-    // smallest CL with at most 32 candidates per block (4 per warp), else at most 64
-    int maxcl = 16;
-    if (cudaFuncSetAttribute(cpqr_id_cluster_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-        cudaSuccess) {
-      cudaGetLastError();
-      maxcl = 8;
-    }
-    const size_t cl_tail_smem = sizeof(cx<R>) * (size_t)32 * kmax;
-    auto cl_smem = [&](int cl) {
-      const int pc = (m + cl - 1) / cl;
-      return std::max(sizeof(cx<R>) * ((size_t)p + (size_t)pc * p), cl_tail_smem);
-    };
-    // the smallest cluster with at most one candidate per warp (32 per block), else at most 64 per block
-    int CL = 0;
-    for (int lim : {32, 64}) {
-      for (int cl = 1; cl <= maxcl && !CL; ++cl)
-        if ((m + cl - 1) / cl <= lim && cl_smem(cl) <= 220 * 1024) CL = cl;
-      if (CL) break;
-    }
-    bool use_cluster = CL > 0;
-    if (!use_cluster) CL = 1;
-    const size_t smem_cl = cl_smem(CL);
-    cudaLaunchConfig_t cfg;
-    cudaLaunchAttribute attr[1];
-    if (use_cluster) {
-      LS_CUDA_TRY(cudaFuncSetAttribute(cpqr_id_cluster_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_cl));
-      memset(&cfg, 0, sizeof(cfg));
-      cfg.gridDim = dim3(CL);
-      cfg.blockDim = dim3(1024);
-      cfg.dynamicSmemBytes = smem_cl;
-      cfg.stream = st;
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = CL;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      int ncl = 0;
-      if (cudaOccupancyMaxActiveClusters(&ncl, (void*)cpqr_id_cluster_kernel<R>, &cfg) != cudaSuccess || ncl < 1) {
-        cudaGetLastError();
-        use_cluster = false;
-      }
-    }
-    double eps = H->tol;
-    LS_CUDA_TRY(cudaMemsetAsync(H->sync_buf, 0, 64, st));
-    int tk = prof_begin(st);
-    if (use_cluster) {
-      count_launch();
-      LS_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpqr_id_cluster_kernel<R>, (const cx<R>*)A, m, p, kmax, eps, Rm, sel, piv,
-                                     rank, Ut, RT));
-    } else {
-      const void* kfn = (const void*)cpqr_id_kernel<R>;
-      LS_CUDA_TRY(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      int per_sm = 0;
-      LS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, smem));
-      if (per_sm < 1 || nblk > per_sm * H->nsm) {
-        set_last_error_text("ID kernel cannot be co-resident");
-        return LS_EINVAL;
-      }
-      GridSync gs;
-      gs.count = reinterpret_cast<unsigned*>(H->sync_buf);
-      gs.gen = reinterpret_cast<unsigned*>(H->sync_buf) + 1;
-      gs.abort = H->sync_buf + 2;
-      const cx<R>* Ac = A;
-      void* args[] = {&Ac, (void*)&m, (void*)&p, (void*)&kmax, &eps, &use_smem, &Aw, &Rm, &sel, &slots, &pslots,
-                      &piv, &rank, &Ut, &RT, &gs};
-      count_launch();
-      LS_CUDA_TRY(cudaLaunchCooperativeKernel(kfn, dim3(nblk), dim3(256), args, smem, st));
-    }
-    int k = 0, abort_flag = 0;
-    LS_CUDA_TRY(cudaMemcpyAsync(&k, rank, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LS_CUDA_TRY(cudaMemcpyAsync(&abort_flag, H->sync_buf + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LS_CUDA_TRY(cudaStreamSynchronize(st));
-    // CPQR work: two projections and a norm (36 p real flops) per active candidate and step
-    prof_end(tk, PR_CPQR, st, sizeof(cx<R>) * (double)m * p * 2.0 * k,
-             36.0 * p * ((double)m * k - 0.5 * (double)k * k));
-    if (abort_flag) {
-      ls::dfree(wsp);
-      ls::dfree(dint);
-      return LS_ETIMEOUT;
-    }
-    std::vector<int> hp(k > 0 ? k : 1);
-    if (k > 0) {
-      LS_CUDA_TRY(cudaMemcpyAsync(hp.data(), piv, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
-      LS_CUDA_TRY(cudaStreamSynchronize(st));
-    }
+    if ((rc = dalloc(&lv.U, sizeof(cx<R>) * (size_t)m * std::max(std::min(m, p), 1)))) return rc;
+    if ((rc = run_row_id<R>(A, m, p, H->tol, H->nsm, H->sync_buf, st, &k, &hp, reinterpret_cast<cx<R>*>(lv.U))))
+      return rc;
+    ls::dfree(A);
     lv.k = k;
     lv.skel_x.resize(k);
     lv.skel_y.resize(k);
@@ -648,11 +701,7 @@ int compress_t(ls_handle* H, cudaStream_t st) {
       lv.skel_x[a] = rows_x[hp[a]];
       lv.skel_y[a] = rows_y[hp[a]];
     }
-    if ((rc = dalloc(&lv.U, sizeof(cx<R>) * (size_t)m * std::max(k, 1)))) return rc;
-    if (k > 0) LS_CUDA_TRY(cudaMemcpyAsync(lv.U, Ut, sizeof(cx<R>) * (size_t)m * k, cudaMemcpyDeviceToDevice, st));
-    LS_CUDA_TRY(cudaStreamSynchronize(st));
     H->flops_compress += 8.0 * 2.0 * (double)m * p * k;  // two projections per pivot step
-    ls::dfree(wsp);
   }
   // sibling blocks G(skel_a, skel_b) for the two children on level l (Eq. 15)
   for (int l = 1; l <= L; ++l) {
@@ -695,6 +744,45 @@ int compress_t(ls_handle* H, cudaStream_t st) {
 }
 
 }  // namespace
+
+namespace {
+template <class Ro, class Ri>
+__global__ void convert_kernel(cx<Ro>* out, const cx<Ri>* in, long long n) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < n) out[t] = cvt<Ro>(in[t]);
+}
+}  // namespace
+
+int row_id(const z64* A, int m, int p, double eps, int precision, int nsm, int* sync_buf, cudaStream_t st, int* k,
+           int* piv, z64* U) {
+  *k = 0;
+  if (m <= 0 || p <= 0) return LS_OK;
+  std::vector<int> hp;
+  int rc;
+  if (precision == LS_FP64) {
+    rc = run_row_id<double>(A, m, p, eps, nsm, sync_buf, st, k, &hp, U);
+  } else {
+    const long long nA = (long long)m * p, nU = (long long)m * std::min(m, p);
+    c32* A32 = nullptr;
+    c32* U32 = nullptr;
+    if ((rc = dalloc((void**)&A32, sizeof(c32) * nA))) return rc;
+    if ((rc = dalloc((void**)&U32, sizeof(c32) * nU))) return rc;
+    count_launch();
+    convert_kernel<float, double><<<(unsigned)((nA + 255) / 256), 256, 0, st>>>(A32, A, nA);
+    rc = run_row_id<float>(A32, m, p, eps, nsm, sync_buf, st, k, &hp, U ? U32 : nullptr);
+    if (!rc && U && *k > 0) {
+      const long long nk = (long long)m * *k;
+      count_launch();
+      convert_kernel<double, float><<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(U, U32, nk);
+      LS_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    ls::dfree(A32);
+    ls::dfree(U32);
+  }
+  if (rc) return rc;
+  for (int a = 0; a < *k; ++a) piv[a] = hp[a];
+  return check_launch("row_id");
+}
 
 int compress(ls_handle* H, cudaStream_t st) {
   return H->prec == LS_FP64 ? compress_t<double>(H, st) : compress_t<float>(H, st);

@@ -68,6 +68,10 @@ int conv_apply(ls_handle* H, const z64* x, z64* y, int nrhs, bool field_only, cu
 
 // compress.cu
 int compress(ls_handle* H, cudaStream_t st);
+// Row ID of the device matrix A (m x p, candidate-major) in the given precision;
+// piv (host, m entries) and U (device, m x min(m, p) entries) receive k pivots / columns.
+int row_id(const z64* A, int m, int p, double eps, int precision, int nsm, int* sync_buf, cudaStream_t st, int* k,
+           int* piv, z64* U);
 
 // build.cu (Algorithm 1) and apply (Algorithm 2)
 int hbs_build(ls_handle* H, cudaStream_t st);

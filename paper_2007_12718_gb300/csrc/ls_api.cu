@@ -4,6 +4,8 @@
 // compression, Algorithm 1, then apply / matvec / GMRES on request.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -107,7 +109,35 @@ namespace ls {
 void set_last_error_text(const char* msg) { set_error(msg); }
 
 static std::atomic<long long> g_launches{0};
-void count_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+namespace {
+bool debug_sync_enabled() {
+  static const bool on = [] {
+    const char* v = getenv("LS_DEBUG_SYNC");
+    return v && v[0] && v[0] != '0';
+  }();
+  return on;
+}
+thread_local int g_capture_depth = 0;
+thread_local const char* g_prev_file = "(none)";
+thread_local int g_prev_line = 0;
+std::atomic<bool> g_debug_reported{false};
+
+void debug_sync(const char* file, int line, const char* what) {
+  if (!debug_sync_enabled() || g_capture_depth > 0) return;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess && !g_debug_reported.exchange(true))
+    fprintf(stderr, "[ls debug] device error '%s' detected at %s:%d (%s); previous launch site %s:%d\n",
+            cudaGetErrorString(e), file, line, what, g_prev_file, g_prev_line);
+}
+}  // namespace
+CaptureScope::CaptureScope() { ++g_capture_depth; }
+CaptureScope::~CaptureScope() { --g_capture_depth; }
+void count_launch_at(const char* file, int line, LaunchCount c) {
+  g_launches.fetch_add(c.n, std::memory_order_relaxed);
+  debug_sync(file, line, "before launch");
+  g_prev_file = file;
+  g_prev_line = line;
+}
 
 namespace {
 thread_local cudaStream_t g_alloc_stream = nullptr;
@@ -160,6 +190,7 @@ void dfree(void* p) {
 }
 
 int check_launch(const char* what) {
+  debug_sync(__FILE__, __LINE__, what);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     ls_set_last_cuda_error(e, what, __FILE__, __LINE__);
@@ -200,6 +231,40 @@ const char* ls_strerror(int code) {
 const char* ls_last_error(void) { return g_last_error.c_str(); }
 
 long long ls_kernel_launches(void) { return ls::g_launches.load(); }
+
+int ls_row_id(const void* A, int m, int p, double eps, int precision, int* k, int* piv, void* U, void* stream) {
+  if (!A || !k || !piv || m < 1 || m >= (1 << 20) || p < 1 || !(eps > 0 && eps < 1) ||
+      (precision != LS_FP64 && precision != LS_FP32)) {
+    set_error("invalid ls_row_id argument");
+    return LS_EINVAL;
+  }
+  *k = 0;
+  ls::StreamScope scope((cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, nsm = 0;
+  LS_CUDA_TRY(cudaGetDevice(&dev));
+  LS_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const size_t bytesA = sizeof(ls::z64) * (size_t)m * p, bytesU = sizeof(ls::z64) * (size_t)m * std::min(m, p);
+  Staged sa, su;
+  int* sync_buf = nullptr;
+  int rc = stage_in(A, bytesA, st, &sa);
+  if (!rc && U) rc = stage_out_alloc(U, bytesU, &su);
+  if (!rc) rc = ls::dalloc((void**)&sync_buf, 256);
+  if (!rc) rc = ls::row_id(sa.dev, m, p, eps, precision, nsm, sync_buf, st, k, piv, U ? su.dev : nullptr);
+  if (!rc && U && su.owned && *k > 0) {
+    cudaError_t e = cudaMemcpyAsync(U, su.dev, sizeof(ls::z64) * (size_t)m * *k, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) {
+      ls_set_last_cuda_error(e, "ls_row_id U copy", __FILE__, __LINE__);
+      rc = LS_ECUDA;
+    }
+  }
+  cudaStreamSynchronize(st);
+  release(&sa);
+  release(&su);
+  if (sync_buf) ls::dfree(sync_buf);
+  cudaStreamSynchronize(st);
+  return rc;
+}
 
 int ls_cgemm_c64(int engine, int ta, int tb, int M, int N, int K, const float* alpha, const void* A, int lda,
                  long long sA, const void* B, int ldb, long long sB, const float* beta, void* C, int ldc,
@@ -347,7 +412,7 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
   if ((rc = ls::dalloc((void**)&H->sync_buf, 256))) return rc;
   if ((rc = ls::dalloc((void**)&H->d_err, sizeof(int) * 4))) return rc;
   LS_CUDA_TRY(cudaMemsetAsync(H->d_err, 0, sizeof(int) * 4, st));
-  ls::count_launch();
+  count_launch();
   check_b_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(H->b, N, H->d_err + 1);
   int bad = 0;
   LS_CUDA_TRY(cudaMemcpyAsync(&bad, H->d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -448,7 +513,7 @@ int ls_rhs_plane_wave(ls_handle* H, const double* thetas, void* f, int nrhs, voi
   Staged sf;
   int rc = stage_out_alloc(f, bytes, &sf);
   for (int r = 0; !rc && r < nrhs; ++r) {
-    ls::count_launch();
+    count_launch();
     rhs_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(H->b, H->grid.nx, H->grid.ny, H->grid.h, H->grid.x0,
                                                           H->grid.y0, H->kappa, cos(thetas[r]), sin(thetas[r]),
                                                           sf.dev + r * N);

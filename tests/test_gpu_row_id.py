@@ -1,0 +1,70 @@
+"""Device interpolative decomposition (Sec. 2.1) against the oracle's row_id
+(scipy's column-pivoted QR).  Pivots are unique only where the residual norms
+are separated: on a random matrix they must agree step for step; on the
+symmetric proxy blocks of the compression (many exactly tied norms) the rank
+must agree within the ID tolerance and the factorisation must be a valid ID."""
+import numpy as np
+import pytest
+
+import paper_2007_12718_gb300 as ls
+from oracle import hbs
+
+pytestmark = pytest.mark.gpu
+
+
+def id_error(A, J, U):
+    return np.linalg.norm(A - U @ A[J, :]) / np.linalg.norm(A)
+
+
+def random_decaying(m, p, seed):
+    rng = np.random.default_rng(seed)
+    r = min(m, p)
+    Q1, _ = np.linalg.qr(rng.standard_normal((m, r)) + 1j * rng.standard_normal((m, r)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((p, r)) + 1j * rng.standard_normal((p, r)))
+    s = 10.0 ** (-8.0 * np.arange(r) / r)
+    return (Q1 * s) @ Q2.conj().T
+
+
+@pytest.mark.parametrize("m,p", [(60, 90), (300, 200), (700, 500)])
+def test_random_matrix_pivots_match_oracle(m, p):
+    """Distinct residual norms: the greedy pivot sequence is unique, FP64 must
+    reproduce scipy's CPQR pivots and rank exactly (sizes cover the one-block,
+    cluster and grid kernels)."""
+    A = random_decaying(m, p, 3)
+    eps = 1e-5
+    J0, U0 = hbs.row_id(A, eps)
+    k, J, U = ls.ls_row_id(A, eps, precision=ls.LS_FP64)
+    assert k == len(J0)
+    assert np.array_equal(J, J0)
+    assert np.abs(U - U0).max() <= 1e-8 * max(1.0, np.abs(U0).max())
+    assert np.allclose(U[J, :], np.eye(k), atol=0)
+
+
+@pytest.mark.parametrize("w,h,ring,prec", [(8, 8, 2, ls.LS_FP64), (16, 16, 2, ls.LS_FP64), (8, 8, 2, ls.LS_FP32),
+                                           (16, 32, 2, ls.LS_FP32)])
+def test_proxy_block_id_is_valid(w, h, ring, prec):
+    """Leaf-type proxy blocks G(box, ring) of the n = 256, kappa = 60 problem."""
+    n, kappa, eps = 256, 60.0, 1e-4
+    A = hbs.kernel_block(kappa, 1.0 / n, 4, hbs.box_points(w, h), hbs.proxy_ring(w, h, ring))
+    J0, _ = hbs.row_id(A, eps)
+    k, J, U = ls.ls_row_id(A, eps, precision=prec)
+    assert abs(k - len(J0)) <= max(2, 0.02 * len(J0)), (k, len(J0))
+    assert len(set(J.tolist())) == k
+    assert np.allclose(U[J, :], np.eye(k), atol=1e-6 if prec == ls.LS_FP32 else 0)
+    assert id_error(A, J, U) <= (3 if prec == ls.LS_FP64 else 10) * eps
+
+
+def test_host_and_device_inputs_agree():
+    import torch
+    A = random_decaying(120, 80, 5)
+    k1, J1, U1 = ls.ls_row_id(A, 1e-6)
+    k2, J2, U2 = ls.ls_row_id(torch.from_numpy(A).cuda(), 1e-6)
+    assert k1 == k2 and np.array_equal(J1, J2) and np.array_equal(U1, U2)
+
+
+def test_invalid_arguments():
+    A = np.zeros((4, 4), np.complex128)
+    with pytest.raises(ls.LSError):
+        ls.ls_row_id(A, 0.0)
+    with pytest.raises(ls.LSError):
+        ls.ls_row_id(A, 1e-3, precision=ls.LS_TF32)
