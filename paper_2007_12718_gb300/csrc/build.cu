@@ -1067,7 +1067,7 @@ TreeGeom make_geom(const ls_handle* H) {
 }
 
 template <class R>
-int build_t(ls_handle* H, cudaStream_t st) {
+int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
   const int L = H->L, n = H->s * H->s;
   int rc;
   struct EngineScope {
@@ -1080,23 +1080,8 @@ int build_t(ls_handle* H, cudaStream_t st) {
       g_tc_err = nullptr;
     }
   } engine_scope(H);
-  // scratch: the largest of (cooperative inverse ping-pong + pivots) and the merge GEMM temporaries
-  size_t wb = 0;
-  for (int l = 0; l < L; ++l) {
-    size_t P = (size_t)1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = l > 0 ? H->lev[l].k : 0;
-    wb = std::max(wb, sizeof(cx<R>) * P * n2 * n2 + sizeof(int) * P * n2);
-    wb = std::max(wb, sizeof(cx<R>) * 2 * P * n2 * kp);
-    // Y1, Y2, a copy of Z and the blocked-inverse panels (width <= 128)
-    wb = std::max(wb, sizeof(cx<R>) * P * (3 * kc * kc + 128 * 128 + 3 * 128 * kc) + sizeof(int) * P * (n2 + 256) + 4096);
-  }
-  // apply temporaries (one right-hand side): leaf blocks, per-level expansions
-  size_t vec = (size_t)2 * ((size_t)1 << L) * n;
-  for (int l = 1; l <= L; ++l) vec += (size_t)3 * ((size_t)1 << l) * std::max(1, H->lev[l].k) * 2;
-  wb = std::max(wb, sizeof(cx<R>) * vec);
-  H->work_bytes = wb;
-  if ((rc = dalloc(&H->work, wb))) return rc;
-
-  // leaves
+  // leaves (once level L is compressed)
+  if (wait_level && (rc = wait_level(L))) return rc;
   LevelData& lf = H->lev[L];
   const int kL = lf.k;
   const size_t nleaf = (size_t)1 << L;
@@ -1125,9 +1110,26 @@ int build_t(ls_handle* H, cudaStream_t st) {
 
   // merges, level by level
   for (int l = L - 1; l >= 0; --l) {
+    if (wait_level && (rc = wait_level(std::max(l, 1)))) return rc;
     LevelData& lv = H->lev[l];
     const LevelData& ch = H->lev[l + 1];
     const int P = 1 << l, kc = ch.k, n2 = 2 * kc;
+    // this level's scratch: the largest of (pivoted-inverse panels + pivots), the
+    // S products, and Y1, Y2, a copy of Z with the blocked-inverse panels (width <= 128)
+    size_t work_bytes;
+    {
+      const size_t Pz = (size_t)P, kz = (size_t)kc, nz = (size_t)n2, kpz = l > 0 ? (size_t)lv.k : 0;
+      work_bytes = sizeof(cx<R>) * Pz * nz * nz + sizeof(int) * Pz * nz;
+      work_bytes = std::max(work_bytes, sizeof(cx<R>) * 2 * Pz * nz * kpz);
+      work_bytes = std::max(work_bytes, sizeof(cx<R>) * Pz * (3 * kz * kz + 128 * 128 + 3 * 128 * kz) +
+                                            sizeof(int) * Pz * (nz + 256) + 4096);
+    }
+    void* work = nullptr;
+    if ((rc = dalloc(&work, work_bytes))) return rc;
+    struct FreeOnExit {
+      void* p;
+      ~FreeOnExit() { dfree(p); }
+    } free_work{work};
     if ((rc = dalloc(&lv.X, sizeof(cx<R>) * (size_t)P * std::max(n2 * n2, 1)))) return rc;
     H->factor_bytes += sizeof(cx<R>) * (double)P * n2 * n2;
     cx<R>* X = reinterpret_cast<cx<R>*>(lv.X);
@@ -1137,10 +1139,10 @@ int build_t(ls_handle* H, cudaStream_t st) {
       // Schur complement form of Eq. (26):  with Y1 = S_a G, Y2 = S_b G^T and
       // W = (I - Y2 Y1)^-1,  X = [[I + Y1 W Y2, -Y1 W], [-W Y2, W]].
       const long long sX = (long long)n2 * n2, kk = (long long)kc * kc;
-      cx<R>* Y1 = reinterpret_cast<cx<R>*>(H->work);
+      cx<R>* Y1 = reinterpret_cast<cx<R>*>(work);
       cx<R>* Y2 = Y1 + (size_t)P * kk;
       void* scratch = Y2 + (size_t)P * kk;
-      size_t scratch_bytes = H->work_bytes - sizeof(cx<R>) * 2 * (size_t)P * kk;
+      size_t scratch_bytes = work_bytes - sizeof(cx<R>) * 2 * (size_t)P * kk;
       cx<R>* X11 = X;
       cx<R>* X12 = X + kc;
       cx<R>* X21 = X + (size_t)kc * n2;
@@ -1188,8 +1190,9 @@ int build_t(ls_handle* H, cudaStream_t st) {
           count_launch();
           probe_max_kernel<R><<<64, 256, 0, st>>>(pr, pv, kc, (long long)P * kc, H->d_err + 2);
         }
-        int flags[2] = {0, 0};  // worst probe residual (float bits), zero-pivot flag
-        LS_CUDA_TRY(cudaMemcpyAsync(flags, H->d_err + 2, sizeof(flags), cudaMemcpyDeviceToHost, st));
+        int* flags = static_cast<int*>(pinned_scratch(2 * sizeof(int)));  // worst probe residual (float bits), zero-pivot flag
+        if (!flags) return LS_ENOMEM;
+        LS_CUDA_TRY(cudaMemcpyAsync(flags, H->d_err + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         LS_CUDA_TRY(cudaStreamSynchronize(st));
         float worst;
         memcpy(&worst, &flags[0], sizeof(float));
@@ -1219,7 +1222,7 @@ int build_t(ls_handle* H, cudaStream_t st) {
     H->factor_bytes += sizeof(cx<R>) * (double)P * kp * kp;
     if (kp == 0 || kc == 0) continue;
     const cx<R>* U = reinterpret_cast<const cx<R>*>(lv.U);  // n2 x kp
-    cx<R>* D = reinterpret_cast<cx<R>*>(H->work);          // P x n2 x kp
+    cx<R>* D = reinterpret_cast<cx<R>*>(work);             // P x n2 x kp
     cx<R>* E = D + (size_t)P * n2 * kp;
     // D = [S_a U_top ; S_b U_bot]
     int ts = prof_begin(st);
@@ -1239,10 +1242,18 @@ int build_t(ls_handle* H, cudaStream_t st) {
       H->flops_build += fl;
     }
   }
-  int herr = 0;
-  LS_CUDA_TRY(cudaMemcpyAsync(&herr, H->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  // apply temporaries (one right-hand side): leaf blocks, per-level expansions
+  {
+    size_t vec = (size_t)2 * ((size_t)1 << L) * n;
+    for (int l = 1; l <= L; ++l) vec += (size_t)3 * ((size_t)1 << l) * std::max(1, H->lev[l].k) * 2;
+    H->work_bytes = sizeof(cx<R>) * vec;
+    if ((rc = dalloc(&H->work, H->work_bytes))) return rc;
+  }
+  int* pin = static_cast<int*>(pinned_scratch(sizeof(int)));
+  if (!pin) return LS_ENOMEM;
+  LS_CUDA_TRY(cudaMemcpyAsync(pin, H->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   LS_CUDA_TRY(cudaStreamSynchronize(st));
-  if (herr) return herr;
+  if (pin[0]) return pin[0];
   // bytes of one apply: every X, S, XBU read once, plus the leaf vectors
   double fb = H->factor_bytes;
   H->bytes_apply = fb + (double)H->grid.nx * H->grid.ny * (16.0 * 2);
@@ -1602,8 +1613,8 @@ int hbs_apply_graph_init(ls_handle* H) {
 
 }  // namespace
 
-int hbs_build(ls_handle* H, cudaStream_t st) {
-  return H->prec == LS_FP64 ? build_t<double>(H, st) : build_t<float>(H, st);
+int hbs_build(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
+  return H->prec == LS_FP64 ? build_t<double>(H, st, wait_level) : build_t<float>(H, st, wait_level);
 }
 
 int simt_cgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, c32 alpha, const c32* A, int lda, long long sA,

@@ -95,6 +95,17 @@ __device__ __forceinline__ unsigned long long piv_key(double nrm, int idx) {
   return (((unsigned long long)__double_as_longlong(nrm) >> 20) << 20) | (unsigned long long)(0xFFFFF - idx);
 }
 __device__ __forceinline__ int piv_key_index(unsigned long long key) { return 0xFFFFF - (int)(key & 0xFFFFF); }
+// Warp-wide maximum of 64-bit keys: redux.sync on the high words, then on the
+// low words of the lanes that hold the maximal high word.
+__device__ __forceinline__ unsigned long long warp_max_key(unsigned long long key) {
+  const unsigned hi = (unsigned)(key >> 32);
+  const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned lo = hi == mhi ? (unsigned)key : 0u;
+  const unsigned mlo = __reduce_max_sync(0xffffffffu, lo);
+  return ((unsigned long long)mhi << 32) | mlo;
+}
+// The residual norm a float key carries (exact).
+__device__ __forceinline__ float piv_key_norm(unsigned long long key) { return __uint_as_float((unsigned)(key >> 20)); }
 
 // Loads that bypass L1 (data written by other blocks of the same grid).
 template <class R>
@@ -434,6 +445,365 @@ __global__ void __launch_bounds__(1024) cpqr_id_cluster_kernel(const cx<R>* __re
   }
 }
 
+// ---------------------------------------------------------------- register-resident ID
+// In the two kernels below every warp owns one candidate and keeps its residual
+// vector in registers (lane l holds entries l, l + 32, ..., l + 32 (T - 1)).
+// A pivot step then touches shared memory only to read the pivot vector q;
+// the block's best candidate is published by its warp (double-buffered by step
+// parity).  The coefficients R(j, c) are collected in registers (lane j mod 32
+// holds step j) and written to global memory every 32 steps, so that no global
+// store is in flight at the per-step barrier; pivots and selections are
+// written once at the end.
+
+// Projection of the pivot vector q (shared memory) out of a register vector:
+// d = q^H a / |q|^2, a -= q d; returns the new |a|^2 (warp-wide) and d.
+template <class R, int T>
+__device__ __forceinline__ R reg_project(cx<R> (&a)[T], const cx<R>* q, int p, int lane, R inu2, cx<R>& dout) {
+  cx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
+#pragma unroll
+  for (int t = 0; t < T; t += 2) {
+    const int i0 = lane + 32 * t;
+    if (i0 < p) fmac_(s0, q[i0], a[t]);
+    if (t + 1 < T) {
+      const int i1 = i0 + 32;
+      if (i1 < p) fmac_(s1, q[i1], a[t + 1]);
+    }
+  }
+  const cx<R> d = scale(warp_sum(s0 + s1), inu2);
+  R n0 = 0, n1 = 0;
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int i = lane + 32 * t;
+    if (i < p) {
+      const cx<R> qi = q[i];
+      a[t].re -= qi.re * d.re - qi.im * d.im;
+      a[t].im -= qi.re * d.im + qi.im * d.re;
+      if (t & 1)
+        n1 += abs2(a[t]);
+      else
+        n0 += abs2(a[t]);
+    }
+  }
+  dout = d;
+  return warp_sum_r(n0 + n1);
+}
+
+// Deferred write of the register-held coefficients R(t, c), steps [t0, t1).
+template <class R>
+__device__ __forceinline__ void flush_coeffs(cx<R>* Rm, int m, int c, int lane, int t0, int t1, int rsel, cx<R> rbuf) {
+  const int t = t0 + lane;
+  if (t < t1 && (rsel < 0 || t <= rsel)) Rm[(long long)t * m + c] = rbuf;
+}
+
+// U rows (identity on the skeleton, R11^-1 R12 elsewhere) by column-oriented
+// back substitution, one warp per candidate; tbuf: kmax entries per warp.
+template <class R>
+__device__ __forceinline__ void id_back_substitution(const cx<R>* Rm, const cx<R>* RT, int m, int k, int c, int sc,
+                                                     int lane, cx<R>* tbuf, cx<R>* U) {
+  if (sc >= 0) {
+    for (int a = lane; a < k; a += 32) U[(long long)c * k + a] = mk<R>(a == sc ? R(1) : R(0), R(0));
+    return;
+  }
+  for (int a = lane; a < k; a += 32) tbuf[a] = ldcg_cx(Rm + (long long)a * m + c);
+  __syncwarp();
+  for (int a = k - 1; a >= 0; --a) {
+    const cx<R>* col = RT + (long long)a * k;
+    const cx<R> ta = tbuf[a] * inv(ldcg_cx(col + a));
+    __syncwarp();
+    for (int bb = lane; bb < a; bb += 32) {
+      cx<R> v = tbuf[bb], r = ldcg_cx(col + bb);
+      v.re -= r.re * ta.re - r.im * ta.im;
+      v.im -= r.re * ta.im + r.im * ta.re;
+      tbuf[bb] = v;
+    }
+    if (lane == 0) tbuf[a] = ta;
+    __syncwarp();
+  }
+  for (int a = lane; a < k; a += 32) U[(long long)c * k + a] = tbuf[a];
+  __syncwarp();
+}
+
+// Cluster version: CL <= 16 blocks of 1024 threads, at most 32 candidates per
+// block (block r owns candidates [r per, r per + per)), p <= 32 T.  Each warp
+// keeps its candidate's key (0 once the candidate is a pivot) in a per-warp
+// slot; per step every warp reduces the block's key from the 32 slots
+// (redux.sync), the best warp publishes its vector, lanes r < CL of warp 0
+// store the block key (FP64: and the best norm), lanes of warp 1 the block
+// total, into slot [this block] of block r; one cluster barrier; every warp
+// reduces the winner from the CL slots of its own block; thread 0 sums the CL
+// totals in a fixed order and decides whether to stop (the same decision in
+// every block); the block copies the winner's vector from its owner; one
+// block barrier.  Dynamic shared memory: max(3 p, 32 kmax) entries.
+template <class R, int T>
+__global__ void __launch_bounds__(1024) cpqr_reg_cluster_kernel(const cx<R>* __restrict__ A, int m, int p, int kmax,
+                                                                double eps, cx<R>* __restrict__ Rm,
+                                                                int* __restrict__ sel, int* __restrict__ piv,
+                                                                int* __restrict__ rank, cx<R>* __restrict__ U,
+                                                                cx<R>* __restrict__ RT, int* __restrict__ err) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ unsigned char smraw[];
+  cx<R>* stage = reinterpret_cast<cx<R>*>(smraw);  // 2 x p: the block's best vector, by step parity
+  cx<R>* pvec = stage + 2 * p;                      // p: the winner's vector
+  const int CL = (int)cluster.num_blocks(), crank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int per = (m + CL - 1) / CL;
+  const int c0 = min(m, crank * per), mc = min(m, c0 + per) - c0;
+  __shared__ unsigned long long s_wkey[32];   // each warp's candidate key, 0 if none
+  __shared__ unsigned long long s_ck[2][16];  // every block's key, by step parity and block
+  __shared__ R s_cb[2][16], s_ct[2][16];      // every block's best norm (FP64) and total
+  __shared__ R s_nrm[32];
+  __shared__ int s_stop;
+
+  const bool own = warp < mc;
+  const int c = c0 + warp;
+  cx<R> a[T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int i = lane + 32 * t;
+    a[t] = (own && i < p) ? A[(long long)c * p + i] : mk<R>(0, 0);
+  }
+  R nrm = 0;
+#pragma unroll
+  for (int t = 0; t < T; ++t) nrm += abs2(a[t]);
+  nrm = warp_sum_r(nrm);
+  if (lane == 0) {
+    s_nrm[warp] = own ? nrm : R(0);
+    s_wkey[warp] = own ? piv_key(nrm, c) : 0ULL;
+  }
+  __syncthreads();
+  cx<R> rbuf = mk<R>(0, 0);
+  int rsel = -1;  // step at which this warp's candidate became a pivot
+  R tol2 = 0;
+  int k = 0;
+  for (int j = 0;; ++j) {
+    const int par = j & 1;
+    const unsigned long long kw = s_wkey[lane];
+    const unsigned long long kb = warp_max_key(kw);
+    const int lb = kb ? piv_key_index(kb) - c0 : -1;
+    if (warp == lb) {
+      cx<R>* st = stage + par * p;
+#pragma unroll
+      for (int t = 0; t < T; ++t) {
+        const int i = lane + 32 * t;
+        if (i < p) st[i] = a[t];
+      }
+    }
+    if (warp == 0) {
+      if (lane < CL) {
+        *cluster.map_shared_rank(&s_ck[par][crank], lane) = kb;
+        if constexpr (sizeof(R) == 8) *cluster.map_shared_rank(&s_cb[par][crank], lane) = lb >= 0 ? s_nrm[lb] : R(0);
+      }
+    } else if (warp == 1) {
+      R tot = kw ? s_nrm[lane] : R(0);
+      tot = warp_sum_r(tot);
+      if (lane < CL) *cluster.map_shared_rank(&s_ct[par][crank], lane) = tot;
+    }
+    cluster.sync();
+    const unsigned long long key = warp_max_key(lane < CL ? s_ck[par][lane] : 0ULL);
+    int idx = key ? piv_key_index(key) : -1;
+    const int bw = idx >= 0 ? idx / per : 0;
+    if (idx >= m || (idx >= 0 && (bw >= CL || idx - bw * per >= 32))) {  // cannot happen; uniform
+      if (tid == 0) atomicExch(err, 1);
+      idx = -1;
+    }
+    R best;
+    if constexpr (sizeof(R) == 4)
+      best = piv_key_norm(key);
+    else
+      best = idx >= 0 ? s_cb[par][bw] : R(0);
+    if (tid == 0) {
+      R tot = 0;
+      for (int r = 0; r < CL; ++r) tot += s_ct[par][r];
+      if (j == 0) tol2 = (R)(eps * eps) * tot;
+      s_stop = (j == kmax) || idx < 0 || !(best > R(0)) || tot <= tol2;
+    }
+    if (idx >= 0) {
+      const cx<R>* src = cluster.map_shared_rank(stage + par * p, bw);
+      for (int i = tid; i < p; i += blockDim.x) pvec[i] = src[i];
+    }
+    __syncthreads();
+    if (s_stop) {
+      k = j;
+      break;
+    }
+    const R nu = sqrt(best);
+    if (own && c == idx) {
+      rsel = j;
+      if (lane == (j & 31)) rbuf = mk<R>(nu, R(0));
+      if (lane == 0) s_wkey[warp] = 0ULL;
+    }
+    if (own && rsel < 0) {
+      cx<R> d;
+      const R nr = reg_project<R, T>(a, pvec, p, lane, R(1) / best, d);
+      if (lane == (j & 31)) rbuf = scale(d, nu);  // R(j, c) = q^H a = (a_pv^H a) / nu
+      if (lane == 0) {
+        s_nrm[warp] = nr;
+        s_wkey[warp] = piv_key(nr, c);
+      }
+    }
+    if ((j & 31) == 31 && own) flush_coeffs(Rm, m, c, lane, j - 31, j + 1, rsel, rbuf);
+    __syncthreads();
+  }
+  if (own) {
+    flush_coeffs(Rm, m, c, lane, k & ~31, k, rsel, rbuf);
+    if (lane == 0) {
+      sel[c] = rsel;
+      if (rsel >= 0) piv[rsel] = c;
+    }
+  }
+  if (crank == 0 && tid == 0) rank[0] = k;
+  cluster.sync();  // Rm, piv complete and visible in the cluster
+  for (long long t = (long long)crank * blockDim.x + tid; t < (long long)k * k; t += (long long)CL * blockDim.x) {
+    int aa = (int)(t / k), bb = (int)(t % k);
+    RT[t] = bb <= aa ? ldcg_cx(Rm + (long long)bb * m + __ldcg(piv + aa)) : mk<R>(0, 0);
+  }
+  cluster.sync();
+  if (own) id_back_substitution(Rm, RT, m, k, c, rsel, lane, reinterpret_cast<cx<R>*>(smraw) + (long long)warp * kmax, U);
+}
+
+// Cooperative-grid version: blocks of 256 threads (8 candidates), p <= 32 T.
+// Per step: every warp reduces the block key from the 8 per-warp slots; the
+// best warp publishes its vector to a parity vector slot; warp 0 writes the
+// block total (FP64: and best norm) to a parity slot and folds the key into
+// the step's global key; one grid barrier; every block reads the step's key
+// and (warp 0) the block totals, thread 0 decides whether to stop, the block
+// copies the winner's vector.  gkey[0..kmax] zero at launch.  Dynamic shared
+// memory: max(p, 8 kmax) entries.
+template <class R, int T>
+__global__ void __launch_bounds__(256) cpqr_reg_grid_kernel(const cx<R>* __restrict__ A, int m, int p, int kmax,
+                                                            double eps, cx<R>* __restrict__ Rm, int* __restrict__ sel,
+                                                            int* __restrict__ piv, int* __restrict__ rank,
+                                                            cx<R>* __restrict__ U, cx<R>* __restrict__ RT,
+                                                            IdSlot<R>* __restrict__ slots, cx<R>* __restrict__ pslots,
+                                                            unsigned long long* __restrict__ gkey, GridSync gs,
+                                                            int* __restrict__ err) {
+  extern __shared__ unsigned char smraw[];
+  cx<R>* pvec = reinterpret_cast<cx<R>*>(smraw);
+  const int nblk = gridDim.x, blk = blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int c0 = min(m, blk * 8), mc = min(m, c0 + 8) - c0;
+  __shared__ unsigned long long s_wkey[8];
+  __shared__ R s_nrm[8];
+  __shared__ R s_best;
+  __shared__ int s_stop;
+  unsigned int epoch = 0;
+
+  const bool own = warp < mc;
+  const int c = c0 + warp;
+  cx<R> a[T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const int i = lane + 32 * t;
+    a[t] = (own && i < p) ? A[(long long)c * p + i] : mk<R>(0, 0);
+  }
+  R nrm = 0;
+#pragma unroll
+  for (int t = 0; t < T; ++t) nrm += abs2(a[t]);
+  nrm = warp_sum_r(nrm);
+  if (lane == 0) {
+    s_nrm[warp] = own ? nrm : R(0);
+    s_wkey[warp] = own ? piv_key(nrm, c) : 0ULL;
+  }
+  __syncthreads();
+  cx<R> rbuf = mk<R>(0, 0);
+  int rsel = -1;
+  R tol2 = 0;
+  int k = 0;
+  for (int j = 0;; ++j) {
+    const int par = j & 1;
+    const unsigned long long kw = lane < 8 ? s_wkey[lane] : 0ULL;
+    const unsigned long long kb = warp_max_key(kw);
+    const int lb = kb ? piv_key_index(kb) - c0 : -1;
+    if (warp == lb) {
+      cx<R>* dst = pslots + ((long long)par * nblk + blk) * p;
+#pragma unroll
+      for (int t = 0; t < T; ++t) {
+        const int i = lane + 32 * t;
+        if (i < p) dst[i] = a[t];
+      }
+    }
+    if (warp == 0) {
+      R tot = kw ? s_nrm[lane & 7] : R(0);
+      tot = warp_sum_r(tot);
+      if (lane == 0) {
+        IdSlot<R> sl;
+        sl.best = lb >= 0 ? s_nrm[lb] : R(0);
+        sl.total = tot;
+        sl.idx = lb >= 0 ? c0 + lb : -1;
+        sl.pad = 0;
+        slots[par * nblk + blk] = sl;
+        if (kb) atomicMax(&gkey[j], kb);
+      }
+    }
+    if (!grid_sync(gs, nblk, epoch)) return;
+    const unsigned long long key = __ldcg(&gkey[j]);
+    int idx = key ? piv_key_index(key) : -1;
+    const int bw = idx >= 0 ? idx / 8 : 0;
+    if (idx >= m || (idx >= 0 && bw >= nblk)) {  // cannot happen; uniform
+      if (tid == 0) atomicExch(err, 1);
+      idx = -1;
+    }
+    if (warp == 0) {
+      R tot = 0;
+      for (int b = lane; b < nblk; b += 32) tot += __ldcg(&slots[par * nblk + b].total);
+      tot = warp_sum_r(tot);
+      if (lane == 0) {
+        R best;
+        if constexpr (sizeof(R) == 4)
+          best = piv_key_norm(key);
+        else
+          best = idx >= 0 ? __ldcg(&slots[par * nblk + bw].best) : R(0);
+        if (j == 0) tol2 = (R)(eps * eps) * tot;
+        s_best = best;
+        s_stop = (j == kmax) || idx < 0 || !(best > R(0)) || tot <= tol2;
+      }
+    }
+    if (idx >= 0) {
+      const cx<R>* src = pslots + ((long long)par * nblk + bw) * p;
+      for (int i = tid; i < p; i += blockDim.x) pvec[i] = ldcg_cx(src + i);
+    }
+    __syncthreads();
+    if (s_stop) {
+      k = j;
+      break;
+    }
+    const R best = s_best;
+    const R nu = sqrt(best);
+    if (own && c == idx) {
+      rsel = j;
+      if (lane == (j & 31)) rbuf = mk<R>(nu, R(0));
+      if (lane == 0) s_wkey[warp] = 0ULL;
+    }
+    if (own && rsel < 0) {
+      cx<R> d;
+      const R nr = reg_project<R, T>(a, pvec, p, lane, R(1) / best, d);
+      if (lane == (j & 31)) rbuf = scale(d, nu);
+      if (lane == 0) {
+        s_nrm[warp] = nr;
+        s_wkey[warp] = piv_key(nr, c);
+      }
+    }
+    if ((j & 31) == 31 && own) flush_coeffs(Rm, m, c, lane, j - 31, j + 1, rsel, rbuf);
+    __syncthreads();
+  }
+  if (own) {
+    flush_coeffs(Rm, m, c, lane, k & ~31, k, rsel, rbuf);
+    if (lane == 0) {
+      sel[c] = rsel;
+      if (rsel >= 0) piv[rsel] = c;
+    }
+  }
+  if (blk == 0 && tid == 0) rank[0] = k;
+  if (!grid_sync(gs, nblk, epoch)) return;
+  for (long long t = (long long)blk * blockDim.x + tid; t < (long long)k * k; t += (long long)nblk * blockDim.x) {
+    int aa = (int)(t / k), bb = (int)(t % k);
+    RT[t] = bb <= aa ? ldcg_cx(Rm + (long long)bb * m + __ldcg(piv + aa)) : mk<R>(0, 0);
+  }
+  if (!grid_sync(gs, nblk, epoch)) return;
+  if (own) id_back_substitution(Rm, RT, m, k, c, rsel, lane, pvec + (long long)warp * kmax, U);
+}
+
 template <class R>
 __global__ void identity_kernel(cx<R>* U, int m) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -451,7 +821,10 @@ int upload_block(const std::vector<int>& rx, const std::vector<int>& ry, const s
   std::copy(ry.begin(), ry.end(), host.begin() + m);
   std::copy(px.begin(), px.end(), host.begin() + 2 * m);
   std::copy(py.begin(), py.end(), host.begin() + 2 * m + p);
-  LS_CUDA_TRY(cudaMemcpyAsync(dtmp, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice, st));
+  int* pin = static_cast<int*>(pinned_scratch(sizeof(int) * host.size()));
+  if (!pin) return LS_ENOMEM;
+  std::copy(host.begin(), host.end(), pin);
+  LS_CUDA_TRY(cudaMemcpyAsync(dtmp, pin, sizeof(int) * host.size(), cudaMemcpyHostToDevice, st));
   long long tot = (long long)m * p;
   if (tot > 0)
     {
@@ -487,6 +860,7 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
     per = 64;
     nblk = (m + per - 1) / per;
   }
+  const int nslot = std::max(nblk, (m + 7) / 8);  // slots for either grid kernel
   size_t loop_smem = sizeof(cx<R>) * ((size_t)p + (size_t)per * p);
   size_t tail_smem = sizeof(cx<R>) * (size_t)8 * kmax;
   int use_smem = loop_smem <= 200 * 1024;
@@ -496,8 +870,8 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
     return LS_EINVAL;
   }
   size_t need = 64 * 256 + sizeof(cx<R>) * ((size_t)m * p * (use_smem ? 0 : 1) + (size_t)kmax * m + (size_t)m * kmax +
-                                 (size_t)kmax * kmax + (size_t)2 * nblk * p) +
-                sizeof(int) * (2 * m + 8) + sizeof(IdSlot<R>) * 2 * (nblk + 1) +
+                                 (size_t)kmax * kmax + (size_t)2 * nslot * p) +
+                sizeof(int) * (2 * m + 8) + sizeof(IdSlot<R>) * 2 * (nslot + 1) +
                 sizeof(unsigned long long) * ((size_t)kmax + 1) + 2048;
   char* wsp = nullptr;
   if ((rc = dalloc((void**)&wsp, need))) return rc;
@@ -511,11 +885,11 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
   cx<R>* Rm = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)kmax * m));
   cx<R>* Ut = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)m * kmax));
   cx<R>* RT = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)kmax * kmax));
-  cx<R>* pslots = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)2 * nblk * p));
+  cx<R>* pslots = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)2 * nslot * p));
   int* sel = reinterpret_cast<int*>(carve(sizeof(int) * m));
   int* piv = reinterpret_cast<int*>(carve(sizeof(int) * m));
   int* rank = reinterpret_cast<int*>(carve(sizeof(int) * 8));
-  IdSlot<R>* slots = reinterpret_cast<IdSlot<R>*>(carve(sizeof(IdSlot<R>) * 2 * (nblk + 1)));
+  IdSlot<R>* slots = reinterpret_cast<IdSlot<R>*>(carve(sizeof(IdSlot<R>) * 2 * (nslot + 1)));
   unsigned long long* gkey =
       reinterpret_cast<unsigned long long*>(carve(sizeof(unsigned long long) * ((size_t)kmax + 1)));
   wsp = wbase;
@@ -567,7 +941,85 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
   double eps = eps_in;
   LS_CUDA_TRY(cudaMemsetAsync(sync_buf, 0, 64, st));
   int tk = prof_begin(st);
-  if (use_cluster) {
+  // register-resident kernels (one candidate per warp) when the vectors fit in registers
+  const int tneed = (p + 31) / 32;
+  const int t_cl_max = sizeof(R) == 4 ? 20 : 8, t_gr_max = sizeof(R) == 4 ? 64 : 32;
+  int reg_mode = 0;  // 1 cluster, 2 grid
+  int treg = 0, clr = (m + 31) / 32, nblk_r = (m + 7) / 8;
+  const void* kreg = nullptr;
+  size_t smem_r = 0;
+  if (tneed <= t_cl_max && clr <= maxcl) {
+    treg = tneed <= 4 ? 4 : tneed <= 8 ? 8 : tneed <= 12 ? 12 : tneed <= 16 ? 16 : 20;
+    if constexpr (sizeof(R) == 4)
+      kreg = treg == 4 ? (const void*)cpqr_reg_cluster_kernel<R, 4> : treg == 8 ? (const void*)cpqr_reg_cluster_kernel<R, 8>
+           : treg == 12 ? (const void*)cpqr_reg_cluster_kernel<R, 12> : treg == 16 ? (const void*)cpqr_reg_cluster_kernel<R, 16>
+           : (const void*)cpqr_reg_cluster_kernel<R, 20>;
+    else
+      kreg = treg == 4 ? (const void*)cpqr_reg_cluster_kernel<R, 4> : (const void*)cpqr_reg_cluster_kernel<R, 8>;
+    smem_r = sizeof(cx<R>) * std::max((size_t)3 * p, (size_t)32 * kmax);
+    if (smem_r <= 220 * 1024) reg_mode = 1;
+  }
+  if (!reg_mode && tneed <= t_gr_max) {
+    treg = (tneed + 7) / 8 * 8;
+    if constexpr (sizeof(R) == 4)
+      kreg = treg == 8 ? (const void*)cpqr_reg_grid_kernel<R, 8> : treg == 16 ? (const void*)cpqr_reg_grid_kernel<R, 16>
+           : treg == 24 ? (const void*)cpqr_reg_grid_kernel<R, 24> : treg == 32 ? (const void*)cpqr_reg_grid_kernel<R, 32>
+           : treg == 40 ? (const void*)cpqr_reg_grid_kernel<R, 40> : treg == 48 ? (const void*)cpqr_reg_grid_kernel<R, 48>
+           : treg == 56 ? (const void*)cpqr_reg_grid_kernel<R, 56> : (const void*)cpqr_reg_grid_kernel<R, 64>;
+    else
+      kreg = treg == 8 ? (const void*)cpqr_reg_grid_kernel<R, 8> : treg == 16 ? (const void*)cpqr_reg_grid_kernel<R, 16>
+           : treg == 24 ? (const void*)cpqr_reg_grid_kernel<R, 24> : (const void*)cpqr_reg_grid_kernel<R, 32>;
+    smem_r = sizeof(cx<R>) * std::max((size_t)p, (size_t)8 * kmax);
+    int per_sm = 0;
+    if (smem_r <= 220 * 1024 && nblk_r <= 2 * nsm &&
+        cudaFuncSetAttribute(kreg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kreg, 256, smem_r) == cudaSuccess &&
+        nblk_r <= per_sm * nsm)
+      reg_mode = 2;
+    cudaGetLastError();
+  }
+  if (reg_mode == 1) {
+    LS_CUDA_TRY(cudaFuncSetAttribute(kreg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r));
+    if (maxcl == 16) LS_CUDA_TRY(cudaFuncSetAttribute(kreg, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t rc_cfg;
+    cudaLaunchAttribute rc_attr[1];
+    memset(&rc_cfg, 0, sizeof(rc_cfg));
+    rc_cfg.gridDim = dim3(clr);
+    rc_cfg.blockDim = dim3(1024);
+    rc_cfg.dynamicSmemBytes = smem_r;
+    rc_cfg.stream = st;
+    rc_attr[0].id = cudaLaunchAttributeClusterDimension;
+    rc_attr[0].val.clusterDim.x = clr;
+    rc_attr[0].val.clusterDim.y = 1;
+    rc_attr[0].val.clusterDim.z = 1;
+    rc_cfg.attrs = rc_attr;
+    rc_cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, kreg, &rc_cfg) != cudaSuccess || ncl < 1) {
+      cudaGetLastError();
+      reg_mode = 0;
+    } else {
+      const cx<R>* Ac = A;
+      int* ierr = sync_buf + 3;
+      void* args[] = {&Ac, (void*)&m, (void*)&p, (void*)&kmax, &eps, &Rm, &sel, &piv, &rank, &Ut, &RT, &ierr};
+      count_launch();
+      LS_CUDA_TRY(cudaLaunchKernelExC(&rc_cfg, kreg, args));
+    }
+  } else if (reg_mode == 2) {
+    GridSync gs;
+    gs.count = reinterpret_cast<unsigned*>(sync_buf);
+    gs.gen = reinterpret_cast<unsigned*>(sync_buf) + 1;
+    gs.abort = sync_buf + 2;
+    const cx<R>* Ac = A;
+    int* ierr = sync_buf + 3;
+    LS_CUDA_TRY(cudaMemsetAsync(gkey, 0, sizeof(unsigned long long) * ((size_t)kmax + 1), st));
+    void* args[] = {&Ac, (void*)&m, (void*)&p, (void*)&kmax, &eps, &Rm, &sel, &piv, &rank, &Ut, &RT,
+                    &slots, &pslots, &gkey, &gs, &ierr};
+    count_launch();
+    LS_CUDA_TRY(cudaLaunchCooperativeKernel(kreg, dim3(nblk_r), dim3(256), args, smem_r, st));
+  }
+  if (reg_mode) {
+  } else if (use_cluster) {
     count_launch();
     LS_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpqr_id_cluster_kernel<R>, (const cx<R>*)A, m, p, kmax, eps, Rm, sel, piv,
                                    rank, Ut, RT, sync_buf + 3));
@@ -592,12 +1044,13 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
     count_launch();
     LS_CUDA_TRY(cudaLaunchCooperativeKernel(kfn, dim3(nblk), dim3(256), args, smem, st));
   }
-  int k = 0, flags[2] = {0, 0};  // abort (barrier timeout), index check
-  LS_CUDA_TRY(cudaMemcpyAsync(&k, rank, sizeof(int), cudaMemcpyDeviceToHost, st));
-  LS_CUDA_TRY(cudaMemcpyAsync(flags, sync_buf + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  int* pin = static_cast<int*>(pinned_scratch(sizeof(int) * (4 + (size_t)kmax)));
+  if (!pin) return LS_ENOMEM;
+  LS_CUDA_TRY(cudaMemcpyAsync(pin, rank, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LS_CUDA_TRY(cudaMemcpyAsync(pin + 1, sync_buf + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   LS_CUDA_TRY(cudaStreamSynchronize(st));
-  const int abort_flag = flags[0];
-  if (flags[1]) {
+  const int k = pin[0], abort_flag = pin[1];  // rank, barrier timeout
+  if (pin[2]) {  // index check
     set_last_error_text("ID kernel: pivot index check failed");
     return LS_ECUDA;
   }
@@ -613,10 +1066,11 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
     return LS_ECUDA;
   }
   hp.assign(k > 0 ? k : 1, 0);
-  if (k > 0) LS_CUDA_TRY(cudaMemcpyAsync(hp.data(), piv, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
+  if (k > 0) LS_CUDA_TRY(cudaMemcpyAsync(pin + 4, piv, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
   if (k > 0 && Uout)
     LS_CUDA_TRY(cudaMemcpyAsync(Uout, Ut, sizeof(cx<R>) * (size_t)m * k, cudaMemcpyDeviceToDevice, st));
   LS_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int a = 0; a < k; ++a) hp[a] = pin[4 + a];
   ls::dfree(wsp);
   for (int a = 0; a < k; ++a)
     if (hp[a] < 0 || hp[a] >= m) {
@@ -628,11 +1082,51 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
 }
 
 template <class R>
-int compress_t(ls_handle* H, cudaStream_t st) {
+int compress_t(ls_handle* H, cudaStream_t st, const LevelDone& level_done) {
   const int L = H->L, s = H->s, w = H->ring;
   int rc;
   std::vector<int> rows_x, rows_y;
   int* dint = nullptr;
+  // kernel block on the device for the given point lists (coordinates staged in dint)
+  auto device_block = [&](const std::vector<int>& rx, const std::vector<int>& ry, const std::vector<int>& cx_,
+                          const std::vector<int>& cy_, void** out) -> int {
+    int r;
+    if ((r = dalloc(out, sizeof(cx<R>) * std::max<size_t>(rx.size() * cx_.size(), 1)))) return r;
+    if (dint) ls::dfree(dint);
+    dint = nullptr;
+    if ((r = dalloc((void**)&dint, sizeof(int) * (2 * rx.size() + 2 * cx_.size() + 8)))) return r;
+    return upload_block<R>(rx, ry, cx_, cy_, reinterpret_cast<cx<R>*>(*out), dint, st, H->ks_prec,
+                           KernelTable{H->ktab, H->ktx, H->kty});
+  };
+  // leaf self-interaction block G(I_tau, I_tau) (the same for every leaf)
+  {
+    std::vector<int> lx, ly;
+    for (int y = 0; y < s; ++y)
+      for (int x = 0; x < s; ++x) {
+        lx.push_back(x);
+        ly.push_back(y);
+      }
+    if ((rc = device_block(lx, ly, lx, ly, &H->Gleaf))) return rc;
+  }
+  // sibling block G(skel_a, skel_b) of the two children on level l (Eq. 15)
+  auto sibling_block = [&](int l) -> int {
+    LevelData& lv = H->lev[l];
+    const int kk = lv.k;
+    int oax, oay, obx, oby;
+    if ((l - 1) % 2 == 0) {
+      oax = 0; oay = 0; obx = lv.w; oby = 0;
+    } else {
+      oax = 0; oay = lv.h; obx = 0; oby = 0;
+    }
+    std::vector<int> ax(kk), ay(kk), bx(kk), by(kk);
+    for (int i = 0; i < kk; ++i) {
+      ax[i] = lv.skel_x[i] + oax;
+      ay[i] = lv.skel_y[i] + oay;
+      bx[i] = lv.skel_x[i] + obx;
+      by[i] = lv.skel_y[i] + oby;
+    }
+    return device_block(ax, ay, bx, by, &lv.Gsib);
+  };
   for (int l = L; l >= 1; --l) {
     LevelData& lv = H->lev[l];
     rows_x.clear();
@@ -680,6 +1174,8 @@ int compress_t(ls_handle* H, cudaStream_t st) {
       count_launch();
       identity_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(reinterpret_cast<cx<R>*>(lv.U), m);
       if ((rc = check_launch("identity U"))) return rc;
+      if ((rc = sibling_block(l))) return rc;
+      if (level_done) level_done(l);
       continue;
     }
     int k = 0;
@@ -702,42 +1198,8 @@ int compress_t(ls_handle* H, cudaStream_t st) {
       lv.skel_y[a] = rows_y[hp[a]];
     }
     H->flops_compress += 8.0 * 2.0 * (double)m * p * k;  // two projections per pivot step
-  }
-  // sibling blocks G(skel_a, skel_b) for the two children on level l (Eq. 15)
-  for (int l = 1; l <= L; ++l) {
-    LevelData& lv = H->lev[l];
-    const int kk = lv.k;
-    int oax, oay, obx, oby;
-    if ((l - 1) % 2 == 0) {
-      oax = 0; oay = 0; obx = lv.w; oby = 0;
-    } else {
-      oax = 0; oay = lv.h; obx = 0; oby = 0;
-    }
-    std::vector<int> ax(kk), ay(kk), bx(kk), by(kk);
-    for (int i = 0; i < kk; ++i) {
-      ax[i] = lv.skel_x[i] + oax;
-      ay[i] = lv.skel_y[i] + oay;
-      bx[i] = lv.skel_x[i] + obx;
-      by[i] = lv.skel_y[i] + oby;
-    }
-    if ((rc = dalloc(&lv.Gsib, sizeof(cx<R>) * (size_t)std::max(kk * kk, 1)))) return rc;
-    if (dint) ls::dfree(dint);
-    dint = nullptr;
-    if ((rc = dalloc((void**)&dint, sizeof(int) * (4 * kk + 8)))) return rc;
-    if ((rc = upload_block<R>(ax, ay, bx, by, reinterpret_cast<cx<R>*>(lv.Gsib), dint, st, H->ks_prec, KernelTable{H->ktab, H->ktx, H->kty}))) return rc;
-  }
-  {
-    std::vector<int> lx, ly;
-    for (int y = 0; y < s; ++y)
-      for (int x = 0; x < s; ++x) {
-        lx.push_back(x);
-        ly.push_back(y);
-      }
-    if ((rc = dalloc(&H->Gleaf, sizeof(cx<R>) * (size_t)s * s * s * s))) return rc;
-    if (dint) ls::dfree(dint);
-    dint = nullptr;
-    if ((rc = dalloc((void**)&dint, sizeof(int) * (4 * s * s + 8)))) return rc;
-    if ((rc = upload_block<R>(lx, ly, lx, ly, reinterpret_cast<cx<R>*>(H->Gleaf), dint, st, H->ks_prec, KernelTable{H->ktab, H->ktx, H->kty}))) return rc;
+    if ((rc = sibling_block(l))) return rc;
+    if (level_done) level_done(l);
   }
   if (dint) ls::dfree(dint);
   return LS_OK;
@@ -784,8 +1246,8 @@ int row_id(const z64* A, int m, int p, double eps, int precision, int nsm, int* 
   return check_launch("row_id");
 }
 
-int compress(ls_handle* H, cudaStream_t st) {
-  return H->prec == LS_FP64 ? compress_t<double>(H, st) : compress_t<float>(H, st);
+int compress(ls_handle* H, cudaStream_t st, const LevelDone& level_done) {
+  return H->prec == LS_FP64 ? compress_t<double>(H, st, level_done) : compress_t<float>(H, st, level_done);
 }
 
 }  // namespace ls

@@ -211,10 +211,13 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, cudaS
   LS_CUDA_TRY(cudaMemsetAsync(ws.Hm, 0, sizeof(z64) * (m + 1) * m, st));
   LS_CUDA_TRY(cudaMemsetAsync(ws.g, 0, sizeof(z64) * (m + 1), st));
   norm2(f, N, ws.partial, ws.scal, st);
-  z64 fn2;
-  LS_CUDA_TRY(cudaMemcpyAsync(&fn2, ws.scal, sizeof(z64), cudaMemcpyDeviceToHost, st));
+  // small host<->device transfers go through page-locked scratch
+  unsigned char* pin = static_cast<unsigned char*>(pinned_scratch(256));
+  if (!pin) return LS_ENOMEM;
+  static_assert(sizeof(GmState) + sizeof(z64) <= 256, "pinned scratch too small");
+  LS_CUDA_TRY(cudaMemcpyAsync(pin, ws.scal, sizeof(z64), cudaMemcpyDeviceToHost, st));
   LS_CUDA_TRY(cudaStreamSynchronize(st));
-  const double fnorm = sqrt(fn2.re);
+  const double fnorm = sqrt(reinterpret_cast<z64*>(pin)->re);
   ls_solve_info inf;
   inf.iterations = 0;
   inf.converged = 1;
@@ -225,13 +228,14 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, cudaS
     if (info) *info = inf;
     return LS_OK;
   }
-  GmState hs;
-  hs.fnorm = fnorm;
-  hs.resid = 1.0;
-  hs.k = 0;
-  LS_CUDA_TRY(cudaMemcpyAsync(ws.st, &hs, sizeof(GmState), cudaMemcpyHostToDevice, st));
-  z64 g0 = mk<double>(fnorm, 0.0);
-  LS_CUDA_TRY(cudaMemcpyAsync(ws.g, &g0, sizeof(z64), cudaMemcpyHostToDevice, st));
+  GmState* hs = reinterpret_cast<GmState*>(pin);
+  hs->fnorm = fnorm;
+  hs->resid = 1.0;
+  hs->k = 0;
+  LS_CUDA_TRY(cudaMemcpyAsync(ws.st, hs, sizeof(GmState), cudaMemcpyHostToDevice, st));
+  z64* g0 = reinterpret_cast<z64*>(pin + 128);
+  *g0 = mk<double>(fnorm, 0.0);
+  LS_CUDA_TRY(cudaMemcpyAsync(ws.g, g0, sizeof(z64), cudaMemcpyHostToDevice, st));
   count_launch();
   normalize_kernel<<<nb, 256, 0, st>>>(f, ws.V, N, ws.scal, nullptr);
   int k = 0;
@@ -261,10 +265,10 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, cudaS
     prof_end(tk, PR_GMRES_ORTH, st, 16.0 * N * (2.0 * (2.0 * (j + 1) + 2.0) + 3.0),
              8.0 * N * (4.0 * (j + 1) + 1.0));
     if ((rc = check_launch("gmres iteration"))) return rc;
-    LS_CUDA_TRY(cudaMemcpyAsync(&hs, ws.st, sizeof(GmState), cudaMemcpyDeviceToHost, st));
+    LS_CUDA_TRY(cudaMemcpyAsync(hs, ws.st, sizeof(GmState), cudaMemcpyDeviceToHost, st));
     LS_CUDA_TRY(cudaStreamSynchronize(st));
     k = j + 1;
-    resid = hs.resid;
+    resid = hs->resid;
     if (resid <= tol) break;
   }
   count_launch();
@@ -276,13 +280,13 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, cudaS
   count_launch();
   sub_kernel<<<nb, 256, 0, st>>>(f, ws.w, ws.w, N);
   norm2(ws.w, N, ws.partial, ws.scal, st);
-  z64 rn2;
-  LS_CUDA_TRY(cudaMemcpyAsync(&rn2, ws.scal, sizeof(z64), cudaMemcpyDeviceToHost, st));
+  z64* rn2 = reinterpret_cast<z64*>(pin + 128);
+  LS_CUDA_TRY(cudaMemcpyAsync(rn2, ws.scal, sizeof(z64), cudaMemcpyDeviceToHost, st));
   LS_CUDA_TRY(cudaStreamSynchronize(st));
   if ((rc = check_launch("gmres finish"))) return rc;
   inf.iterations = k;
   inf.resid_est = resid;
-  inf.resid_true = sqrt(rn2.re) / fnorm;
+  inf.resid_true = sqrt(rn2->re) / fnorm;
   inf.converged = resid <= tol;
   if (info) *info = inf;
   return inf.converged ? LS_OK : LS_ENOCONV;

@@ -1,6 +1,7 @@
 // Internal state of an ls_handle and the host-side entry points of each
 // kernel family.  Not part of the public ABI.
 #pragma once
+#include <functional>
 #include <vector>
 
 #include "common.cuh"
@@ -66,15 +67,27 @@ int conv_setup(ls_handle* H, cudaStream_t st);
 // y = x + kappa^2 b .* (K * x)  (field_only: y = K * x)
 int conv_apply(ls_handle* H, const z64* x, z64* y, int nrhs, bool field_only, cudaStream_t st);
 
+// Build pipeline hooks: the compression reports each finished level (its U,
+// rank, skeleton and sibling block are in place and recorded on its stream);
+// the merge stage waits for the level it needs.  Empty hooks: no pipelining.
+typedef std::function<int(int level)> LevelWait;
+typedef std::function<void(int level)> LevelDone;
+
+// Page-locked host scratch of at least `bytes` bytes, private to the calling
+// thread (grown on demand, released when the thread exits).  Small device-to-
+// host reads go through it: a copy to pageable memory is synchronous inside
+// the driver and would stall the other build thread's launches.
+void* pinned_scratch(size_t bytes);
+
 // compress.cu
-int compress(ls_handle* H, cudaStream_t st);
+int compress(ls_handle* H, cudaStream_t st, const LevelDone& level_done = LevelDone());
 // Row ID of the device matrix A (m x p, candidate-major) in the given precision;
 // piv (host, m entries) and U (device, m x min(m, p) entries) receive k pivots / columns.
 int row_id(const z64* A, int m, int p, double eps, int precision, int nsm, int* sync_buf, cudaStream_t st, int* k,
            int* piv, z64* U);
 
 // build.cu (Algorithm 1) and apply (Algorithm 2)
-int hbs_build(ls_handle* H, cudaStream_t st);
+int hbs_build(ls_handle* H, cudaStream_t st, const LevelWait& wait_level = LevelWait());
 int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, cudaStream_t st);
 
 // tc_gemm.cu: complex FP32 GEMM on tcgen05 tensor cores (split: 0 tf32, 1 tf32x3)

@@ -5,12 +5,13 @@
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
-#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <thread>
+#include <condition_variable>
 #include <string>
 
 #include "handle.h"
@@ -158,11 +159,40 @@ int pool_for_current_device(cudaMemPool_t* out) {
     LS_CUDA_TRY(cudaMemPoolCreate(&g_pools[dev], &props));
     unsigned long long keep = ~0ULL;  // keep freed memory in the pool
     LS_CUDA_TRY(cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep));
+    int no = 0;  // reuse across streams only without inserted dependencies (the build runs on two streams)
+    LS_CUDA_TRY(cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolReuseAllowInternalDependencies, &no));
   }
   *out = g_pools[dev];
   return LS_OK;
 }
 }  // namespace
+
+namespace {
+struct PinnedScratch {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~PinnedScratch() {
+    if (p) cudaFreeHost(p);
+  }
+};
+thread_local PinnedScratch g_pinned;
+}  // namespace
+
+void* pinned_scratch(size_t bytes) {
+  if (bytes > g_pinned.bytes) {
+    if (g_pinned.p) cudaFreeHost(g_pinned.p);
+    g_pinned.p = nullptr;
+    g_pinned.bytes = 0;
+    size_t want = std::max(bytes, (size_t)1 << 16);
+    if (cudaMallocHost(&g_pinned.p, want) != cudaSuccess) {
+      cudaGetLastError();
+      g_pinned.p = nullptr;
+      return nullptr;
+    }
+    g_pinned.bytes = want;
+  }
+  return g_pinned.p;
+}
 
 StreamScope::StreamScope(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
 StreamScope::~StreamScope() { g_alloc_stream = prev; }
@@ -319,6 +349,67 @@ void ls_free(ls_handle* H) {
   delete H;
 }
 
+// Compression and merges run as a two-stage pipeline: this thread compresses
+// the levels L..1 on the caller's stream (the ID kernels occupy at most one
+// thread-block cluster or one cooperative grid); a worker thread runs the leaf
+// build and the merges on a second stream, each level starting as soon as the
+// compression of the level it needs has been recorded, so that the merges of
+// the lower levels overlap the IDs of the upper ones.  The caller's stream
+// waits for the last merge.
+static int build_pipelined(ls_handle* H, cudaStream_t st) {
+  const int L = H->L;
+  cudaStream_t sm = nullptr;
+  LS_CUDA_TRY(cudaStreamCreateWithFlags(&sm, cudaStreamNonBlocking));
+  std::vector<cudaEvent_t> ev(L + 2, nullptr);
+  for (auto& e : ev) LS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  std::mutex mu;
+  std::condition_variable cv;
+  int ready = L + 1;  // the lowest level index compressed so far (levels finish from L down to 1)
+  bool abort = false;
+  int mrc = LS_OK;
+  std::string merr;
+  std::thread merger([&] {
+    ls::StreamScope scope(sm);
+    auto wait_level = [&](int level) -> int {
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return abort || ready <= level; });
+        if (abort) return LS_EINVAL;
+      }
+      LS_CUDA_TRY(cudaStreamWaitEvent(sm, ev[level], 0));
+      return LS_OK;
+    };
+    int r = ls::hbs_build(H, sm, wait_level);
+    if (r) merr = ls_last_error();
+    std::lock_guard<std::mutex> lk(mu);
+    mrc = r;
+  });
+  auto level_done = [&](int level) {
+    cudaEventRecord(ev[level], st);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      ready = level;
+    }
+    cv.notify_all();
+  };
+  int rc = ls::compress(H, st, level_done);
+  if (rc) {
+    std::lock_guard<std::mutex> lk(mu);
+    abort = true;
+  }
+  cv.notify_all();
+  merger.join();
+  if (!rc && mrc) {
+    rc = mrc;
+    set_error(merr.c_str());
+  }
+  cudaEventRecord(ev[L + 1], sm);
+  cudaStreamWaitEvent(st, ev[L + 1], 0);
+  for (auto& e : ev) cudaEventDestroy(e);
+  cudaStreamDestroy(sm);
+  return rc;
+}
+
 static int build_impl(const ls_grid* grid, double kappa, const double* b, double tol, const ls_opts* opts,
                       cudaStream_t st, ls_handle** out) {
   ls_handle* H = new ls_handle();
@@ -414,18 +505,18 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
   LS_CUDA_TRY(cudaMemsetAsync(H->d_err, 0, sizeof(int) * 4, st));
   count_launch();
   check_b_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(H->b, N, H->d_err + 1);
-  int bad = 0;
-  LS_CUDA_TRY(cudaMemcpyAsync(&bad, H->d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  int* pin = static_cast<int*>(ls::pinned_scratch(sizeof(int)));
+  if (!pin) return LS_ENOMEM;
+  LS_CUDA_TRY(cudaMemcpyAsync(pin, H->d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
   LS_CUDA_TRY(cudaStreamSynchronize(st));
+  const int bad = pin[0];
   if (bad) {
     set_error("b must be finite and <= 1");
     return LS_EINVAL;
   }
   if ((rc = ls::kernel_table_setup(H, st))) return rc;
   if ((rc = ls::conv_setup(H, st))) return rc;
-  if ((rc = ls::compress(H, st))) return rc;
-  if ((rc = ls::hbs_build(H, st))) return rc;
-  return LS_OK;
+  return build_pipelined(H, st);
 }
 
 int ls_build(const ls_grid* grid, double kappa, const double* b, double tol, const ls_opts* opts, void* stream,

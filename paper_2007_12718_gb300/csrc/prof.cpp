@@ -1,6 +1,8 @@
 // Event-based kernel timing for ls_profile_* (see prof.h).
 #include "prof.h"
 
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <mutex>
@@ -21,11 +23,23 @@ struct Pending {
   double bytes, flops;
 };
 
+// Optional timeline (environment variable LS_TRACE=1): every resolved event
+// pair is also printed to stderr as "slot start end" in ms relative to the
+// first event recorded after profiling was enabled.
+bool trace_on() {
+  static const bool on = [] {
+    const char* v = getenv("LS_TRACE");
+    return v && v[0] && v[0] != '0';
+  }();
+  return on;
+}
+
 struct State {
   bool on = false;
   std::vector<cudaEvent_t> pool;  // free events
   std::vector<cudaEvent_t> open;  // begin events by token
   std::vector<Pending> pending;
+  cudaEvent_t base = nullptr;  // trace origin
   double ms[PR_COUNT] = {0};
   long long launches[PR_COUNT] = {0};
   double bytes[PR_COUNT] = {0}, flops[PR_COUNT] = {0};
@@ -49,6 +63,11 @@ void resolve() {
     cudaEventSynchronize(p.b);
     float t = 0.f;
     cudaEventElapsedTime(&t, p.a, p.b);
+    if (trace_on() && g.base) {
+      float t0 = 0.f;
+      cudaEventElapsedTime(&t0, g.base, p.a);
+      fprintf(stderr, "[ls trace] %-16s %10.3f %10.3f\n", kNames[p.slot], t0, t0 + t);
+    }
     g.ms[p.slot] += t;
     g.launches[p.slot] += 1;
     g.bytes[p.slot] += p.bytes;
@@ -66,6 +85,10 @@ int prof_begin(cudaStream_t st) {
   if (!g.on) return -1;
   cudaEvent_t e = get_event();
   cudaEventRecord(e, st);
+  if (trace_on() && !g.base) {
+    cudaEventCreate(&g.base);
+    cudaEventRecord(g.base, st);
+  }
   g.open.push_back(e);
   return (int)g.open.size() - 1;
 }
@@ -102,6 +125,10 @@ int ls_profile_reset(void) {
   memset(ls::g.launches, 0, sizeof(ls::g.launches));
   memset(ls::g.bytes, 0, sizeof(ls::g.bytes));
   memset(ls::g.flops, 0, sizeof(ls::g.flops));
+  if (ls::g.base) {
+    cudaEventDestroy(ls::g.base);
+    ls::g.base = nullptr;
+  }
   return LS_OK;
 }
 
