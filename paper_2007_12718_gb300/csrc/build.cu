@@ -192,7 +192,9 @@ void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, cx<R> alpha, c
           const cx<R>* B, int ldb, long long sB, cx<R> beta, cx<R>* C, int ldc, long long sC, int batch) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   if (K <= 0) return;  // only reached with beta = 1 (nothing to add)
-  if (sizeof(R) == 4 && g_tc_engine > 0) {
+  // tensor cores for the large products only: below ~2.5e8 complex MACs the
+  // packing passes and launches of the tcgen05 path cost more than they save
+  if (sizeof(R) == 4 && g_tc_engine > 0 && M >= 256 && N >= 256 && (double)M * N * K * batch >= 2.5e8) {
     tc_cgemm(st, ta, tb, M, N, K, *reinterpret_cast<const c32*>(&alpha), reinterpret_cast<const c32*>(A), lda, sA,
              reinterpret_cast<const c32*>(B), ldb, sB, *reinterpret_cast<const c32*>(&beta),
              reinterpret_cast<c32*>(C), ldc, sC, batch, g_tc_engine == 2 ? 1 : 0, g_tc_err);
@@ -952,7 +954,7 @@ void gemv(cudaStream_t st, bool ta, int M, int K, cx<R> alpha, const cx<R>* A, i
 template <class R>
 int invert_batch_nopiv(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int P, void* scratch,
                        size_t scratch_bytes, cudaStream_t st) {
-  const int nb = gj_reg_max<R>();
+  const int nb = 64;  // panel width: a 64-wide panel inverse takes ~1/4 the time of a 128-wide one
   const size_t w_max = nb;
   cx<R>* Ab = reinterpret_cast<cx<R>*>(scratch);
   cx<R>* Mb = Ab + (size_t)P * w_max * w_max;

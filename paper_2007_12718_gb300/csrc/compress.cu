@@ -662,48 +662,61 @@ __global__ void __launch_bounds__(1024) cpqr_reg_cluster_kernel(const cx<R>* __r
   if (own) id_back_substitution(Rm, RT, m, k, c, rsel, lane, reinterpret_cast<cx<R>*>(smraw) + (long long)warp * kmax, U);
 }
 
-// Cooperative-grid version: blocks of 256 threads (8 candidates), p <= 32 T.
-// Per step: every warp reduces the block key from the 8 per-warp slots; the
-// best warp publishes its vector to a parity vector slot; warp 0 writes the
-// block total (FP64: and best norm) to a parity slot and folds the key into
-// the step's global key; one grid barrier; every block reads the step's key
-// and (warp 0) the block totals, thread 0 decides whether to stop, the block
-// copies the winner's vector.  gkey[0..kmax] zero at launch.  Dynamic shared
-// memory: max(p, 8 kmax) entries.
-template <class R, int T>
-__global__ void __launch_bounds__(256) cpqr_reg_grid_kernel(const cx<R>* __restrict__ A, int m, int p, int kmax,
-                                                            double eps, cx<R>* __restrict__ Rm, int* __restrict__ sel,
-                                                            int* __restrict__ piv, int* __restrict__ rank,
-                                                            cx<R>* __restrict__ U, cx<R>* __restrict__ RT,
-                                                            IdSlot<R>* __restrict__ slots, cx<R>* __restrict__ pslots,
-                                                            unsigned long long* __restrict__ gkey, GridSync gs,
-                                                            int* __restrict__ err) {
+// Cooperative-grid version: blocks of 1024 threads holding 8 candidates, four
+// warps per candidate (warp part w holds entries lane + 32 (w + 4 t), t < T4,
+// p <= 128 T4), so that each warp's dependent chain per step is a quarter of
+// the vector.  The coefficient and the new norm of a candidate are reduced
+// over its four warps through shared memory (fixed order) behind a named
+// barrier of the 128 threads.  Per step: the block's best candidate publishes
+// its vector to a parity vector slot; warp 0 writes the block total (FP64: and
+// the best norm) to a parity slot and folds the key into the step's global
+// key; one grid barrier; every block reads the step's key and (warp 0) the
+// block totals, thread 0 decides whether to stop, the block copies the
+// winner's vector.  gkey[0..kmax] zero at launch.  Dynamic shared memory:
+// max(p, 8 kmax) entries.
+template <class R, int T4>
+__global__ void __launch_bounds__(1024) cpqr_reg_grid_kernel(const cx<R>* __restrict__ A, int m, int p, int kmax,
+                                                             double eps, cx<R>* __restrict__ Rm, int* __restrict__ sel,
+                                                             int* __restrict__ piv, int* __restrict__ rank,
+                                                             cx<R>* __restrict__ U, cx<R>* __restrict__ RT,
+                                                             IdSlot<R>* __restrict__ slots, cx<R>* __restrict__ pslots,
+                                                             unsigned long long* __restrict__ gkey, GridSync gs,
+                                                             int* __restrict__ err) {
   extern __shared__ unsigned char smraw[];
   cx<R>* pvec = reinterpret_cast<cx<R>*>(smraw);
   const int nblk = gridDim.x, blk = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int cand = warp >> 2, part = warp & 3;
   const int c0 = min(m, blk * 8), mc = min(m, c0 + 8) - c0;
   __shared__ unsigned long long s_wkey[8];
   __shared__ R s_nrm[8];
+  __shared__ cx<R> s_part[8][4];
+  __shared__ R s_npart[8][4];
   __shared__ R s_best;
   __shared__ int s_stop;
   unsigned int epoch = 0;
+  const unsigned bar_id = 1 + cand;  // named barrier of this candidate's four warps
 
-  const bool own = warp < mc;
-  const int c = c0 + warp;
-  cx<R> a[T];
+  const bool own = cand < mc;
+  const int c = c0 + cand;
+  cx<R> a[T4];
 #pragma unroll
-  for (int t = 0; t < T; ++t) {
-    const int i = lane + 32 * t;
+  for (int t = 0; t < T4; ++t) {
+    const int i = lane + 32 * (part + 4 * t);
     a[t] = (own && i < p) ? A[(long long)c * p + i] : mk<R>(0, 0);
   }
-  R nrm = 0;
+  {
+    R nrm = 0;
 #pragma unroll
-  for (int t = 0; t < T; ++t) nrm += abs2(a[t]);
-  nrm = warp_sum_r(nrm);
-  if (lane == 0) {
-    s_nrm[warp] = own ? nrm : R(0);
-    s_wkey[warp] = own ? piv_key(nrm, c) : 0ULL;
+    for (int t = 0; t < T4; ++t) nrm += abs2(a[t]);
+    nrm = warp_sum_r(nrm);
+    if (lane == 0) s_npart[cand][part] = nrm;
+  }
+  __syncthreads();
+  if (part == 0 && lane == 0) {
+    const R nrm = ((s_npart[cand][0] + s_npart[cand][1]) + s_npart[cand][2]) + s_npart[cand][3];
+    s_nrm[cand] = own ? nrm : R(0);
+    s_wkey[cand] = own ? piv_key(nrm, c) : 0ULL;
   }
   __syncthreads();
   cx<R> rbuf = mk<R>(0, 0);
@@ -715,11 +728,11 @@ __global__ void __launch_bounds__(256) cpqr_reg_grid_kernel(const cx<R>* __restr
     const unsigned long long kw = lane < 8 ? s_wkey[lane] : 0ULL;
     const unsigned long long kb = warp_max_key(kw);
     const int lb = kb ? piv_key_index(kb) - c0 : -1;
-    if (warp == lb) {
+    if (cand == lb) {
       cx<R>* dst = pslots + ((long long)par * nblk + blk) * p;
 #pragma unroll
-      for (int t = 0; t < T; ++t) {
-        const int i = lane + 32 * t;
+      for (int t = 0; t < T4; ++t) {
+        const int i = lane + 32 * (part + 4 * t);
         if (i < p) dst[i] = a[t];
       }
     }
@@ -772,22 +785,53 @@ __global__ void __launch_bounds__(256) cpqr_reg_grid_kernel(const cx<R>* __restr
     const R nu = sqrt(best);
     if (own && c == idx) {
       rsel = j;
-      if (lane == (j & 31)) rbuf = mk<R>(nu, R(0));
-      if (lane == 0) s_wkey[warp] = 0ULL;
+      if (part == 0 && lane == (j & 31)) rbuf = mk<R>(nu, R(0));
+      if (part == 0 && lane == 0) s_wkey[cand] = 0ULL;
     }
     if (own && rsel < 0) {
-      cx<R> d;
-      const R nr = reg_project<R, T>(a, pvec, p, lane, R(1) / best, d);
-      if (lane == (j & 31)) rbuf = scale(d, nu);
-      if (lane == 0) {
-        s_nrm[warp] = nr;
-        s_wkey[warp] = piv_key(nr, c);
+      cx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
+#pragma unroll
+      for (int t = 0; t < T4; ++t) {
+        const int i = lane + 32 * (part + 4 * t);
+        if (i < p) {
+          if (t & 1)
+            fmac_(s1, pvec[i], a[t]);
+          else
+            fmac_(s0, pvec[i], a[t]);
+        }
+      }
+      const cx<R> ps = warp_sum(s0 + s1);
+      if (lane == 0) s_part[cand][part] = ps;
+      asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+      const cx<R> d = scale(((s_part[cand][0] + s_part[cand][1]) + s_part[cand][2]) + s_part[cand][3], R(1) / best);
+      R n0 = 0, n1 = 0;
+#pragma unroll
+      for (int t = 0; t < T4; ++t) {
+        const int i = lane + 32 * (part + 4 * t);
+        if (i < p) {
+          const cx<R> qi = pvec[i];
+          a[t].re -= qi.re * d.re - qi.im * d.im;
+          a[t].im -= qi.re * d.im + qi.im * d.re;
+          if (t & 1)
+            n1 += abs2(a[t]);
+          else
+            n0 += abs2(a[t]);
+        }
+      }
+      const R pn = warp_sum_r(n0 + n1);
+      if (lane == 0) s_npart[cand][part] = pn;
+      if (part == 0 && lane == (j & 31)) rbuf = scale(d, nu);  // R(j, c) = q^H a = (a_pv^H a) / nu
+      asm volatile("bar.sync %0, 128;" ::"r"(bar_id) : "memory");
+      if (part == 0 && lane == 0) {
+        const R nr = ((s_npart[cand][0] + s_npart[cand][1]) + s_npart[cand][2]) + s_npart[cand][3];
+        s_nrm[cand] = nr;
+        s_wkey[cand] = piv_key(nr, c);
       }
     }
-    if ((j & 31) == 31 && own) flush_coeffs(Rm, m, c, lane, j - 31, j + 1, rsel, rbuf);
+    if ((j & 31) == 31 && own && part == 0) flush_coeffs(Rm, m, c, lane, j - 31, j + 1, rsel, rbuf);
     __syncthreads();
   }
-  if (own) {
+  if (own && part == 0) {
     flush_coeffs(Rm, m, c, lane, k & ~31, k, rsel, rbuf);
     if (lane == 0) {
       sel[c] = rsel;
@@ -801,7 +845,7 @@ __global__ void __launch_bounds__(256) cpqr_reg_grid_kernel(const cx<R>* __restr
     RT[t] = bb <= aa ? ldcg_cx(Rm + (long long)bb * m + __ldcg(piv + aa)) : mk<R>(0, 0);
   }
   if (!grid_sync(gs, nblk, epoch)) return;
-  if (own) id_back_substitution(Rm, RT, m, k, c, rsel, lane, pvec + (long long)warp * kmax, U);
+  if (own && part == 0) id_back_substitution(Rm, RT, m, k, c, rsel, lane, pvec + (long long)cand * kmax, U);
 }
 
 template <class R>
@@ -943,7 +987,7 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
   int tk = prof_begin(st);
   // register-resident kernels (one candidate per warp) when the vectors fit in registers
   const int tneed = (p + 31) / 32;
-  const int t_cl_max = sizeof(R) == 4 ? 20 : 8, t_gr_max = sizeof(R) == 4 ? 64 : 32;
+  const int t_cl_max = sizeof(R) == 4 ? 20 : 8;
   int reg_mode = 0;  // 1 cluster, 2 grid
   int treg = 0, clr = (m + 31) / 32, nblk_r = (m + 7) / 8;
   const void* kreg = nullptr;
@@ -959,21 +1003,19 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
     smem_r = sizeof(cx<R>) * std::max((size_t)3 * p, (size_t)32 * kmax);
     if (smem_r <= 220 * 1024) reg_mode = 1;
   }
-  if (!reg_mode && tneed <= t_gr_max) {
-    treg = (tneed + 7) / 8 * 8;
+  const int t4need = (p + 127) / 128;
+  if (!reg_mode && t4need <= (sizeof(R) == 4 ? 16 : 8)) {
+    treg = t4need <= 4 ? 4 : t4need <= 8 ? 8 : t4need <= 12 ? 12 : 16;
     if constexpr (sizeof(R) == 4)
-      kreg = treg == 8 ? (const void*)cpqr_reg_grid_kernel<R, 8> : treg == 16 ? (const void*)cpqr_reg_grid_kernel<R, 16>
-           : treg == 24 ? (const void*)cpqr_reg_grid_kernel<R, 24> : treg == 32 ? (const void*)cpqr_reg_grid_kernel<R, 32>
-           : treg == 40 ? (const void*)cpqr_reg_grid_kernel<R, 40> : treg == 48 ? (const void*)cpqr_reg_grid_kernel<R, 48>
-           : treg == 56 ? (const void*)cpqr_reg_grid_kernel<R, 56> : (const void*)cpqr_reg_grid_kernel<R, 64>;
+      kreg = treg == 4 ? (const void*)cpqr_reg_grid_kernel<R, 4> : treg == 8 ? (const void*)cpqr_reg_grid_kernel<R, 8>
+           : treg == 12 ? (const void*)cpqr_reg_grid_kernel<R, 12> : (const void*)cpqr_reg_grid_kernel<R, 16>;
     else
-      kreg = treg == 8 ? (const void*)cpqr_reg_grid_kernel<R, 8> : treg == 16 ? (const void*)cpqr_reg_grid_kernel<R, 16>
-           : treg == 24 ? (const void*)cpqr_reg_grid_kernel<R, 24> : (const void*)cpqr_reg_grid_kernel<R, 32>;
+      kreg = treg == 4 ? (const void*)cpqr_reg_grid_kernel<R, 4> : (const void*)cpqr_reg_grid_kernel<R, 8>;
     smem_r = sizeof(cx<R>) * std::max((size_t)p, (size_t)8 * kmax);
     int per_sm = 0;
-    if (smem_r <= 220 * 1024 && nblk_r <= 2 * nsm &&
+    if (smem_r <= 220 * 1024 && nblk_r <= nsm &&
         cudaFuncSetAttribute(kreg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r) == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kreg, 256, smem_r) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kreg, 1024, smem_r) == cudaSuccess &&
         nblk_r <= per_sm * nsm)
       reg_mode = 2;
     cudaGetLastError();
@@ -1016,7 +1058,7 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
     void* args[] = {&Ac, (void*)&m, (void*)&p, (void*)&kmax, &eps, &Rm, &sel, &piv, &rank, &Ut, &RT,
                     &slots, &pslots, &gkey, &gs, &ierr};
     count_launch();
-    LS_CUDA_TRY(cudaLaunchCooperativeKernel(kreg, dim3(nblk_r), dim3(256), args, smem_r, st));
+    LS_CUDA_TRY(cudaLaunchCooperativeKernel(kreg, dim3(nblk_r), dim3(1024), args, smem_r, st));
   }
   if (reg_mode) {
   } else if (use_cluster) {
