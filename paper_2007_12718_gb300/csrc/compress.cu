@@ -662,25 +662,46 @@ __global__ void __launch_bounds__(1024) cpqr_reg_cluster_kernel(const cx<R>* __r
   if (own) id_back_substitution(Rm, RT, m, k, c, rsel, lane, reinterpret_cast<cx<R>*>(smraw) + (long long)warp * kmax, U);
 }
 
+// Per-step exchange record of the grid ID kernel.  word: bits 52..63 count the
+// blocks that have arrived, bits 0..51 hold the sum of their residual totals in
+// fixed point, unit = (eps^2 total_0) 2^-20 (the stopping threshold is 2^20
+// units; each block's term saturates at 2^40, far above it), so the barrier
+// and the total are one atomic add, and integer addition makes the sum
+// independent of the arrival order (every block takes the same stopping
+// decision, run after run).
+struct StepExchange {
+  unsigned long long key;   // largest pivot key of the step
+  unsigned long long word;  // arrivals and fixed-point total
+};
+__device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Cooperative-grid version: blocks of 1024 threads holding 8 candidates, four
 // warps per candidate (warp part w holds entries lane + 32 (w + 4 t), t < T4,
 // p <= 128 T4), so that each warp's dependent chain per step is a quarter of
 // the vector.  The coefficient and the new norm of a candidate are reduced
 // over its four warps through shared memory (fixed order) behind a named
-// barrier of the 128 threads.  Per step: the block's best candidate publishes
-// its vector to a parity vector slot; warp 0 writes the block total (FP64: and
-// the best norm) to a parity slot and folds the key into the step's global
-// key; one grid barrier; every block reads the step's key and (warp 0) the
-// block totals, thread 0 decides whether to stop, the block copies the
-// winner's vector.  gkey[0..kmax] zero at launch.  Dynamic shared memory:
-// max(p, 8 kmax) entries.
+// barrier of the 128 threads.  The initial total (the scale of the fixed-point
+// totals) is reduced once through the slots.  Per step: the block's best
+// candidate publishes its vector to a parity vector slot; thread 0 folds the
+// block key into the step's key (atomic max) and arrives with the block total
+// (release add on the step's word), then polls the word (acquire, bounded)
+// until every block has arrived; every thread reads the step's key, the block
+// copies the winner's vector.  ex[0..kmax] zero at launch.  Dynamic shared
+// memory: max(p, 8 kmax) entries.
 template <class R, int T4>
 __global__ void __launch_bounds__(1024) cpqr_reg_grid_kernel(const cx<R>* __restrict__ A, int m, int p, int kmax,
                                                              double eps, cx<R>* __restrict__ Rm, int* __restrict__ sel,
                                                              int* __restrict__ piv, int* __restrict__ rank,
                                                              cx<R>* __restrict__ U, cx<R>* __restrict__ RT,
                                                              IdSlot<R>* __restrict__ slots, cx<R>* __restrict__ pslots,
-                                                             unsigned long long* __restrict__ gkey, GridSync gs,
+                                                             StepExchange* __restrict__ ex, GridSync gs,
                                                              int* __restrict__ err) {
   extern __shared__ unsigned char smraw[];
   cx<R>* pvec = reinterpret_cast<cx<R>*>(smraw);
@@ -692,8 +713,9 @@ __global__ void __launch_bounds__(1024) cpqr_reg_grid_kernel(const cx<R>* __rest
   __shared__ R s_nrm[8];
   __shared__ cx<R> s_part[8][4];
   __shared__ R s_npart[8][4];
-  __shared__ R s_best;
-  __shared__ int s_stop;
+  __shared__ unsigned long long s_word;
+  __shared__ R s_scale;
+  __shared__ int s_fail;
   unsigned int epoch = 0;
   const unsigned bar_id = 1 + cand;  // named barrier of this candidate's four warps
 
@@ -712,6 +734,7 @@ __global__ void __launch_bounds__(1024) cpqr_reg_grid_kernel(const cx<R>* __rest
     nrm = warp_sum_r(nrm);
     if (lane == 0) s_npart[cand][part] = nrm;
   }
+  if (tid == 0) s_fail = 0;
   __syncthreads();
   if (part == 0 && lane == 0) {
     const R nrm = ((s_npart[cand][0] + s_npart[cand][1]) + s_npart[cand][2]) + s_npart[cand][3];
@@ -719,9 +742,32 @@ __global__ void __launch_bounds__(1024) cpqr_reg_grid_kernel(const cx<R>* __rest
     s_wkey[cand] = own ? piv_key(nrm, c) : 0ULL;
   }
   __syncthreads();
+  // initial total through the slots: the fixed-point unit and the tolerance
+  if (warp == 0) {
+    R tot = lane < 8 ? s_nrm[lane] : R(0);
+    tot = warp_sum_r(tot);
+    if (lane == 0) {
+      IdSlot<R> sl;
+      sl.best = R(0);
+      sl.total = tot;
+      sl.idx = -1;
+      sl.pad = 0;
+      slots[blk] = sl;
+    }
+  }
+  if (!grid_sync(gs, nblk, epoch)) return;
+  if (warp == 0) {
+    R tot = 0;
+    for (int b = lane; b < nblk; b += 32) tot += __ldcg(&slots[b].total);
+    tot = warp_sum_r(tot);
+    if (lane == 0) s_scale = tot;
+  }
+  __syncthreads();
+  const double thresh = eps * eps * (double)s_scale;          // stop when the residual total <= thresh
+  const double fx_inv = thresh > 0.0 ? 1048576.0 / thresh : 0.0;  // fixed-point units per unit total
+  const unsigned long long tol_fx = 1ULL << 20, fx_cap = 1ULL << 40;
   cx<R> rbuf = mk<R>(0, 0);
   int rsel = -1;
-  R tol2 = 0;
   int k = 0;
   for (int j = 0;; ++j) {
     const int par = j & 1;
@@ -736,58 +782,61 @@ __global__ void __launch_bounds__(1024) cpqr_reg_grid_kernel(const cx<R>* __rest
         if (i < p) dst[i] = a[t];
       }
     }
+    R btot = 0;
     if (warp == 0) {
-      R tot = kw ? s_nrm[lane & 7] : R(0);
-      tot = warp_sum_r(tot);
-      if (lane == 0) {
-        IdSlot<R> sl;
-        sl.best = lb >= 0 ? s_nrm[lb] : R(0);
-        sl.total = tot;
-        sl.idx = lb >= 0 ? c0 + lb : -1;
-        sl.pad = 0;
-        slots[par * nblk + blk] = sl;
-        if (kb) atomicMax(&gkey[j], kb);
-      }
+      btot = kw ? s_nrm[lane & 7] : R(0);
+      btot = warp_sum_r(btot);
+      if constexpr (sizeof(R) == 8)
+        if (lane == 0) slots[par * nblk + blk].best = lb >= 0 ? s_nrm[lb] : R(0);
     }
-    if (!grid_sync(gs, nblk, epoch)) return;
-    const unsigned long long key = __ldcg(&gkey[j]);
+    __syncthreads();  // the block's vector and slot are written
+    if (tid == 0) {
+      if (kb) atomicMax(&ex[j].key, kb);
+      const double fxd = (double)btot * fx_inv + 0.5;
+      const unsigned long long fx =
+          thresh > 0.0 ? (fxd >= (double)fx_cap ? fx_cap : (unsigned long long)fxd) : (btot > R(0) ? fx_cap : 0ULL);
+      red_release_add(&ex[j].word, (1ULL << 52) + fx);
+      unsigned long long v;
+      long long spins = 0;
+      while (((v = ld_acquire_u64(&ex[j].word)) >> 52) < (unsigned long long)nblk) {
+        if ((++spins & 4095) == 0 && (*(volatile int*)gs.abort || spins > kSpinLimit)) {
+          atomicExch(gs.abort, 1);
+          s_fail = 1;
+          break;
+        }
+      }
+      s_word = v;
+    }
+    __syncthreads();
+    if (s_fail) return;
+    const unsigned long long key = __ldcg(&ex[j].key);
     int idx = key ? piv_key_index(key) : -1;
     const int bw = idx >= 0 ? idx / 8 : 0;
     if (idx >= m || (idx >= 0 && bw >= nblk)) {  // cannot happen; uniform
       if (tid == 0) atomicExch(err, 1);
       idx = -1;
     }
-    if (warp == 0) {
-      R tot = 0;
-      for (int b = lane; b < nblk; b += 32) tot += __ldcg(&slots[par * nblk + b].total);
-      tot = warp_sum_r(tot);
-      if (lane == 0) {
-        R best;
-        if constexpr (sizeof(R) == 4)
-          best = piv_key_norm(key);
-        else
-          best = idx >= 0 ? __ldcg(&slots[par * nblk + bw].best) : R(0);
-        if (j == 0) tol2 = (R)(eps * eps) * tot;
-        s_best = best;
-        s_stop = (j == kmax) || idx < 0 || !(best > R(0)) || tot <= tol2;
-      }
-    }
-    if (idx >= 0) {
-      const cx<R>* src = pslots + ((long long)par * nblk + bw) * p;
-      for (int i = tid; i < p; i += blockDim.x) pvec[i] = ldcg_cx(src + i);
-    }
-    __syncthreads();
-    if (s_stop) {
+    R best;
+    if constexpr (sizeof(R) == 4)
+      best = piv_key_norm(key);
+    else
+      best = idx >= 0 ? __ldcg(&slots[par * nblk + bw].best) : R(0);
+    const unsigned long long tot_fx = s_word & ((1ULL << 52) - 1);
+    if ((j == kmax) || idx < 0 || !(best > R(0)) || tot_fx <= tol_fx) {  // the same decision everywhere
       k = j;
       break;
     }
-    const R best = s_best;
+    {
+      const cx<R>* src = pslots + ((long long)par * nblk + bw) * p;
+      for (int i = tid; i < p; i += blockDim.x) pvec[i] = ldcg_cx(src + i);
+    }
     const R nu = sqrt(best);
     if (own && c == idx) {
       rsel = j;
       if (part == 0 && lane == (j & 31)) rbuf = mk<R>(nu, R(0));
       if (part == 0 && lane == 0) s_wkey[cand] = 0ULL;
     }
+    __syncthreads();  // the winner's vector is in shared memory
     if (own && rsel < 0) {
       cx<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
 #pragma unroll
@@ -916,7 +965,7 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
   size_t need = 64 * 256 + sizeof(cx<R>) * ((size_t)m * p * (use_smem ? 0 : 1) + (size_t)kmax * m + (size_t)m * kmax +
                                  (size_t)kmax * kmax + (size_t)2 * nslot * p) +
                 sizeof(int) * (2 * m + 8) + sizeof(IdSlot<R>) * 2 * (nslot + 1) +
-                sizeof(unsigned long long) * ((size_t)kmax + 1) + 2048;
+                2 * sizeof(unsigned long long) * ((size_t)kmax + 1) + 2048;
   char* wsp = nullptr;
   if ((rc = dalloc((void**)&wsp, need))) return rc;
   auto carve = [&](size_t bytes) {
@@ -935,7 +984,7 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
   int* rank = reinterpret_cast<int*>(carve(sizeof(int) * 8));
   IdSlot<R>* slots = reinterpret_cast<IdSlot<R>*>(carve(sizeof(IdSlot<R>) * 2 * (nslot + 1)));
   unsigned long long* gkey =
-      reinterpret_cast<unsigned long long*>(carve(sizeof(unsigned long long) * ((size_t)kmax + 1)));
+      reinterpret_cast<unsigned long long*>(carve(2 * sizeof(unsigned long long) * ((size_t)kmax + 1)));
   wsp = wbase;
   // one cluster when the candidates fit in the shared memory of CL blocks: the
   // smallest CL with at most 32 candidates per block (4 per warp), else at most 64
@@ -1054,9 +1103,10 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
     gs.abort = sync_buf + 2;
     const cx<R>* Ac = A;
     int* ierr = sync_buf + 3;
-    LS_CUDA_TRY(cudaMemsetAsync(gkey, 0, sizeof(unsigned long long) * ((size_t)kmax + 1), st));
+    StepExchange* ex = reinterpret_cast<StepExchange*>(gkey);
+    LS_CUDA_TRY(cudaMemsetAsync(ex, 0, sizeof(StepExchange) * ((size_t)kmax + 1), st));
     void* args[] = {&Ac, (void*)&m, (void*)&p, (void*)&kmax, &eps, &Rm, &sel, &piv, &rank, &Ut, &RT,
-                    &slots, &pslots, &gkey, &gs, &ierr};
+                    &slots, &pslots, &ex, &gs, &ierr};
     count_launch();
     LS_CUDA_TRY(cudaLaunchCooperativeKernel(kreg, dim3(nblk_r), dim3(1024), args, smem_r, st));
   }

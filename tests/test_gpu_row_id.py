@@ -25,13 +25,14 @@ def random_decaying(m, p, seed):
     return (Q1 * s) @ Q2.conj().T
 
 
-@pytest.mark.parametrize("m,p", [(60, 90), (300, 200), (700, 500)])
-def test_random_matrix_pivots_match_oracle(m, p):
+@pytest.mark.parametrize("m,p,eps", [(60, 90, 1e-5), (300, 200, 1e-5), (700, 500, 1e-5), (700, 500, 1e-7),
+                                     (300, 200, 1e-7)])
+def test_random_matrix_pivots_match_oracle(m, p, eps):
     """Distinct residual norms: the greedy pivot sequence is unique, FP64 must
     reproduce scipy's CPQR pivots and rank exactly (sizes cover the one-block,
-    cluster and grid kernels)."""
+    cluster and grid kernels; the small tolerance pins the stopping rule far
+    below the initial total)."""
     A = random_decaying(m, p, 3)
-    eps = 1e-5
     J0, U0 = hbs.row_id(A, eps)
     k, J, U = ls.ls_row_id(A, eps, precision=ls.LS_FP64)
     assert k == len(J0)
