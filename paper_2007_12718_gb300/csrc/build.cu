@@ -1582,6 +1582,252 @@ int apply_core(ls_handle* H, z64** slots, cudaStream_t st) {
   return check_launch("hbs_apply");
 }
 
+// ------------------------------------------------- apply as one persistent kernel
+// Algorithm 2 is a fixed sequence of batched matrix-vector products between
+// which every result must be complete.  As ~60 separate launches it is bound by
+// launch and tail latency; here one cooperative kernel runs the whole sequence,
+// a phase at a time, with a grid barrier (release add / acquire poll) between
+// phases.  Within a phase every output row is one warp's dot product (lanes
+// over the row), so results do not depend on the schedule.  Transposed
+// products use the U^T and G^T copies made once per handle.
+struct ApplyOp {
+  int type;        // 0: y[b] = y0[b] + alpha A[b] x[b];  1: gather leaves (y <- f);  2: scatter leaves (q <- x)
+  int M, K, lda, batch;
+  int phase_end;   // a grid barrier follows this operation
+  long long sA, sx, sy, sy0;
+  const void* A;
+  const void* x;   // null for the gather (reads f)
+  void* y;         // null for the scatter (writes q)
+  const void* y0;  // may be null (y0 = 0)
+  double ar, ai;   // alpha
+};
+
+__device__ __forceinline__ bool apply_barrier(unsigned* count, unsigned* abort, unsigned target, int* sflag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+    unsigned v;
+    long long spins = 0;
+    int ok = 1;
+    while (true) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+      if ((int)(v - target) >= 0) break;
+      if ((++spins & 1023) == 0 && (*(volatile unsigned*)abort || spins > kSpinLimit)) {
+        atomicExch(abort, 1u);
+        ok = 0;
+        break;
+      }
+    }
+    *sflag = ok;
+  }
+  __syncthreads();
+  return *sflag != 0;
+}
+
+template <class R>
+__global__ void __launch_bounds__(1024) apply_persistent_kernel(const ApplyOp* __restrict__ ops, int nops, TreeGeom g,
+                                                                const z64* __restrict__ f, z64* __restrict__ q,
+                                                                unsigned* bar, unsigned epoch0, int* err) {
+  __shared__ int s_ok;
+  const int wpb = blockDim.x >> 5;
+  const long long nwarps = (long long)gridDim.x * wpb, nthreads = (long long)gridDim.x * blockDim.x;
+  const long long gw = (long long)blockIdx.x * wpb + (threadIdx.x >> 5);
+  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  unsigned target = epoch0;
+  for (int o = 0; o < nops; ++o) {
+    const ApplyOp op = ops[o];
+    const long long rows = (long long)op.batch * op.M;
+    if (op.type == 1 || op.type == 2) {  // leaf gather / scatter, one entry per thread
+      const int n = g.s * g.s;
+      for (long long t = gt; t < rows; t += nthreads) {
+        const int leaf = (int)(t / n), i = (int)(t % n);
+        int ox, oy;
+        leaf_origin(g, leaf, ox, oy);
+        const long long gi = (long long)(oy + i / g.s) * g.nx + ox + i % g.s;
+        if (op.type == 1)
+          reinterpret_cast<cx<R>*>(op.y)[t] = cvt<R>(f[gi]);
+        else
+          q[gi] = cvt<double>(ldcg_cx(reinterpret_cast<const cx<R>*>(op.x) + t));
+      }
+    } else {
+      const cx<R>* A = reinterpret_cast<const cx<R>*>(op.A);
+      const cx<R>* X = reinterpret_cast<const cx<R>*>(op.x);
+      const cx<R>* Y0 = reinterpret_cast<const cx<R>*>(op.y0);
+      cx<R>* Y = reinterpret_cast<cx<R>*>(op.y);
+      const cx<R> alpha = mk<R>((R)op.ar, (R)op.ai);
+      for (long long r = gw; r < rows; r += nwarps) {
+        const int b = (int)(r / op.M), i = (int)(r % op.M);
+        const cx<R>* a = A + b * op.sA + (long long)i * op.lda;
+        const cx<R>* xv = X + b * op.sx;
+        cx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0);
+        int j = lane;
+        for (; j + 32 < op.K; j += 64) {
+          fma_(acc0, a[j], ldcg_cx(xv + j));
+          fma_(acc1, a[j + 32], ldcg_cx(xv + j + 32));
+        }
+        if (j < op.K) fma_(acc0, a[j], ldcg_cx(xv + j));
+        const cx<R> v = warp_sum(acc0 + acc1);
+        if (lane == 0) {
+          cx<R> out = alpha * v;
+          if (Y0) out = out + ldcg_cx(Y0 + b * op.sy0 + i);
+          Y[b * op.sy + i] = out;
+        }
+      }
+    }
+    if (op.phase_end && o + 1 < nops) {
+      target += gridDim.x;
+      if (!apply_barrier(bar, bar + 1, target, &s_ok)) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) atomicExch(err, LS_ETIMEOUT);
+        return;
+      }
+    }
+  }
+}
+
+template <class R>
+__global__ void transpose_kernel(const cx<R>* __restrict__ A, int M, int N, cx<R>* __restrict__ T) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)M * N) return;
+  const int i = (int)(t / N), j = (int)(t % N);
+  T[(long long)j * M + i] = A[t];
+}
+
+// Operation list of Algorithm 2 (the same products as apply_core).
+template <class R>
+std::vector<ApplyOp> apply_ops(ls_handle* H) {
+  const int L = H->L, n = H->s * H->s;
+  const long long nleaf = 1LL << L;
+  cx<R>* F = reinterpret_cast<cx<R>*>(H->work);
+  cx<R>* Rl = F + nleaf * n;
+  cx<R>* p = Rl + nleaf * n;
+  std::vector<cx<R>*> rt(L + 1), wt(L + 1), tmp(L + 1);
+  for (int l = 1; l <= L; ++l) {
+    size_t sz = ((size_t)1 << l) * std::max(1, H->lev[l].k) * 2;
+    rt[l] = p;
+    p += sz;
+    wt[l] = p;
+    p += sz;
+    tmp[l] = p;
+    p += sz;
+  }
+  std::vector<ApplyOp> ops;
+  auto gemv = [&](int M, int K, const void* A, int lda, long long sA, const void* x, long long sx, void* y,
+                  long long sy, int batch, bool end, double ar = 1.0, const void* y0 = nullptr, long long sy0 = 0) {
+    ApplyOp o;
+    memset(&o, 0, sizeof(o));
+    o.type = 0;
+    o.M = M;
+    o.K = K;
+    o.A = A;
+    o.lda = lda;
+    o.sA = sA;
+    o.x = x;
+    o.sx = sx;
+    o.y = y;
+    o.sy = sy;
+    o.batch = batch;
+    o.phase_end = end ? 1 : 0;
+    o.ar = ar;
+    o.ai = 0.0;
+    o.y0 = y0;
+    o.sy0 = sy0;
+    ops.push_back(o);
+  };
+  auto leafop = [&](int type, void* y, const void* x, bool end) {
+    ApplyOp o;
+    memset(&o, 0, sizeof(o));
+    o.type = type;
+    o.M = n;
+    o.batch = (int)nleaf;
+    o.y = y;
+    o.x = x;
+    o.phase_end = end ? 1 : 0;
+    ops.push_back(o);
+  };
+  const LevelData& lf = H->lev[L];
+  const int kL = lf.k;
+  leafop(1, F, nullptr, true);                                                       // F <- f
+  gemv(n, n, lf.X, n, (long long)n * n, F, n, Rl, n, (int)nleaf, true);              // r = X f   (Eq. 24)
+  gemv(kL, n, lf.UT, n, 0, Rl, n, rt[L], kL, (int)nleaf, true);                      // r~ = U^T r
+  for (int l = L - 1; l >= 1; --l) {                                                 // up pass (Eq. 28)
+    const int P = 1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
+    gemv(n2, n2, H->lev[l].X, n2, (long long)n2 * n2, rt[l + 1], n2, tmp[l + 1], n2, P, true);
+    gemv(kp, n2, H->lev[l].UT, n2, 0, tmp[l + 1], n2, rt[l], kp, P, true);
+  }
+  {                                                                                  // root (Eq. 29)
+    const int kc = H->lev[1].k, n2 = 2 * kc;
+    gemv(n2, n2, H->lev[0].X, n2, 0, rt[1], 0, tmp[1], 0, 1, true);
+    gemv(kc, kc, H->lev[1].Gsib, kc, 0, tmp[1] + kc, 0, wt[1], 0, 1, false);
+    gemv(kc, kc, H->lev[1].GT, kc, 0, tmp[1], 0, wt[1] + kc, 0, 1, true);
+  }
+  for (int l = 1; l <= L - 1; ++l) {                                                 // down pass (Lemma 4.1)
+    const int P = 1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
+    const cx<R>* Sc = reinterpret_cast<const cx<R>*>(H->lev[l + 1].S);
+    gemv(n2, kp, H->lev[l].U, kp, 0, wt[l], kp, wt[l + 1], n2, P, true);           // U w~
+    gemv(kc, kc, Sc, kc, 2LL * kc * kc, wt[l + 1], n2, tmp[l + 1], n2, P, false, -1.0, rt[l + 1], n2);
+    gemv(kc, kc, Sc + (size_t)kc * kc, kc, 2LL * kc * kc, wt[l + 1] + kc, n2, tmp[l + 1] + kc, n2, P, true, -1.0,
+         rt[l + 1] + kc, n2);                                                        // t = r~ - diag(S) U w~
+    gemv(n2, n2, H->lev[l].X, n2, (long long)n2 * n2, tmp[l + 1], n2, rt[l + 1], n2, P, true);  // q~ = X t
+    gemv(kc, kc, H->lev[l + 1].Gsib, kc, 0, rt[l + 1] + kc, n2, wt[l + 1], n2, P, false, 1.0, wt[l + 1], n2);
+    gemv(kc, kc, H->lev[l + 1].GT, kc, 0, rt[l + 1], n2, wt[l + 1] + kc, n2, P, true, 1.0, wt[l + 1] + kc, n2);
+  }
+  gemv(n, kL, H->XBU, kL, (long long)n * kL, wt[L], kL, Rl, n, (int)nleaf, true, -1.0, Rl, n);  // q = r - XBU w~
+  leafop(2, nullptr, Rl, true);                                                      // q -> grid
+  return ops;
+}
+
+// Prepares the persistent apply (transposed U and G, the operation list, the
+// barrier); returns LS_OK without preparing it if a cooperative grid of one
+// 1024-thread block per SM cannot be co-resident (the graph path is used then).
+int apply_persistent_init(ls_handle* H, cudaStream_t st) {
+  if (H->apply_ops) return LS_OK;
+  const void* kfn = H->prec == LS_FP64 ? (const void*)apply_persistent_kernel<double>
+                                       : (const void*)apply_persistent_kernel<float>;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 1024, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return LS_OK;
+  }
+  const size_t es = H->prec == LS_FP64 ? sizeof(z64) : sizeof(c32);
+  int rc;
+  for (int l = 1; l <= H->L; ++l) {
+    LevelData& lv = H->lev[l];
+    const int m = l == H->L ? H->s * H->s : 2 * H->lev[l + 1].k, k = lv.k;
+    if (!lv.UT) {
+      if ((rc = dalloc(&lv.UT, es * (size_t)std::max(m * k, 1)))) return rc;
+      if ((rc = dalloc(&lv.GT, es * (size_t)std::max(k * k, 1)))) return rc;
+      const long long t1 = (long long)m * k, t2 = (long long)k * k;
+      if (t1 > 0) {
+        count_launch();
+        if (H->prec == LS_FP64)
+          transpose_kernel<double><<<(unsigned)((t1 + 255) / 256), 256, 0, st>>>((const z64*)lv.U, m, k, (z64*)lv.UT);
+        else
+          transpose_kernel<float><<<(unsigned)((t1 + 255) / 256), 256, 0, st>>>((const c32*)lv.U, m, k, (c32*)lv.UT);
+      }
+      if (t2 > 0) {
+        count_launch();
+        if (H->prec == LS_FP64)
+          transpose_kernel<double><<<(unsigned)((t2 + 255) / 256), 256, 0, st>>>((const z64*)lv.Gsib, k, k, (z64*)lv.GT);
+        else
+          transpose_kernel<float><<<(unsigned)((t2 + 255) / 256), 256, 0, st>>>((const c32*)lv.Gsib, k, k, (c32*)lv.GT);
+      }
+    }
+  }
+  std::vector<ApplyOp> ops = H->prec == LS_FP64 ? apply_ops<double>(H) : apply_ops<float>(H);
+  if ((rc = dalloc(&H->apply_ops, sizeof(ApplyOp) * ops.size()))) return rc;
+  if ((rc = dalloc((void**)&H->apply_bar, 2 * sizeof(unsigned)))) return rc;
+  LS_CUDA_TRY(cudaMemcpyAsync(H->apply_ops, ops.data(), sizeof(ApplyOp) * ops.size(), cudaMemcpyHostToDevice, st));
+  LS_CUDA_TRY(cudaMemsetAsync(H->apply_bar, 0, 2 * sizeof(unsigned), st));
+  LS_CUDA_TRY(cudaStreamSynchronize(st));  // the host vector is released on return
+  H->apply_nops = (int)ops.size();
+  H->apply_phases = 0;
+  for (auto& o : ops) H->apply_phases += o.phase_end;
+  H->apply_blocks = H->nsm;
+  H->apply_count = 0;
+  return check_launch("apply_persistent_init");
+}
+
 // The apply is recorded once per handle as a CUDA graph on a private stream
 // (inputs and outputs are passed through two device-side pointer slots), and
 // replayed on the caller's stream.
@@ -1628,6 +1874,29 @@ int simt_cgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, c32 alpha
 int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, cudaStream_t st) {
   const long long N = (long long)H->grid.nx * H->grid.ny;
   int rc;
+  if ((rc = apply_persistent_init(H, st))) return rc;
+  if (H->apply_ops) {
+    const TreeGeom g = make_geom(H);
+    const void* kfn = H->prec == LS_FP64 ? (const void*)apply_persistent_kernel<double>
+                                         : (const void*)apply_persistent_kernel<float>;
+    for (int r = 0; r < nrhs; ++r) {
+      int tk = prof_begin(st);
+      const ApplyOp* ops = reinterpret_cast<const ApplyOp*>(H->apply_ops);
+      int nops = H->apply_nops;
+      const z64* fr = f + r * N;
+      z64* qr = q + r * N;
+      unsigned* bar = H->apply_bar;
+      // barrier epochs continue across applies: (phases - 1) barriers of apply_blocks arrivals each
+      unsigned epoch0 = (unsigned)(H->apply_count * (unsigned long long)(H->apply_phases - 1) * H->apply_blocks);
+      int* err = H->d_err;
+      void* args[] = {&ops, &nops, (void*)&g, &fr, &qr, &bar, &epoch0, &err};
+      count_launch();
+      LS_CUDA_TRY(cudaLaunchCooperativeKernel(kfn, dim3(H->apply_blocks), dim3(1024), args, 0, st));
+      ++H->apply_count;
+      prof_end(tk, PR_APPLY, st, H->bytes_apply, 0.0);
+    }
+    return check_launch("hbs_apply");
+  }
   if ((rc = hbs_apply_graph_init(H))) return rc;
   for (int r = 0; r < nrhs; ++r) {
     int tk = prof_begin(st);

@@ -77,6 +77,20 @@ __device__ __forceinline__ T warp_sum_r(T v) {
   return v;
 }
 
+// Loads that bypass L1 (data written by other blocks of the same grid).
+template <class R>
+__device__ __forceinline__ cx<R> ldcg_cx(const cx<R>* p);
+template <>
+__device__ __forceinline__ cx<float> ldcg_cx(const cx<float>* p) {
+  float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return mk<float>(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ cx<double> ldcg_cx(const cx<double>* p) {
+  double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return mk<double>(v.x, v.y);
+}
+
 // Grid-wide barrier for kernels launched with cudaLaunchCooperativeKernel
 // (all blocks co-resident).  The arrival counter only grows: barrier number
 // e (counted per block from 1) completes when it reaches e * nblocks.  Every

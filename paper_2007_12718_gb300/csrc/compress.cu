@@ -107,20 +107,6 @@ __device__ __forceinline__ unsigned long long warp_max_key(unsigned long long ke
 // The residual norm a float key carries (exact).
 __device__ __forceinline__ float piv_key_norm(unsigned long long key) { return __uint_as_float((unsigned)(key >> 20)); }
 
-// Loads that bypass L1 (data written by other blocks of the same grid).
-template <class R>
-__device__ __forceinline__ cx<R> ldcg_cx(const cx<R>* p);
-template <>
-__device__ __forceinline__ cx<float> ldcg_cx(const cx<float>* p) {
-  float2 v = __ldcg(reinterpret_cast<const float2*>(p));
-  return mk<float>(v.x, v.y);
-}
-template <>
-__device__ __forceinline__ cx<double> ldcg_cx(const cx<double>* p) {
-  double2 v = __ldcg(reinterpret_cast<const double2*>(p));
-  return mk<double>(v.x, v.y);
-}
-
 // Column-pivoted QR ID of the candidate-major matrix A (m candidates, each a
 // length-p vector at A + c*p).  Block b owns candidates [c0, c0 + mc) and keeps
 // their residual vectors in shared memory when they fit (else in the global
@@ -1041,7 +1027,10 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
   int treg = 0, clr = (m + 31) / 32, nblk_r = (m + 7) / 8;
   const void* kreg = nullptr;
   size_t smem_r = 0;
-  if (tneed <= t_cl_max && clr <= maxcl) {
+  // clusters win while they are small (<= 6 blocks: levels with <= 192 candidates,
+  // measured ~3.5-4 us per pivot against ~4.6-5.6 on the grid); above, the grid
+  // kernel's spread over more SMs wins (~5 against ~6-8 us per pivot)
+  if (tneed <= t_cl_max && clr <= std::min(maxcl, 6)) {
     treg = tneed <= 4 ? 4 : tneed <= 8 ? 8 : tneed <= 12 ? 12 : tneed <= 16 ? 16 : 20;
     if constexpr (sizeof(R) == 4)
       kreg = treg == 4 ? (const void*)cpqr_reg_cluster_kernel<R, 4> : treg == 8 ? (const void*)cpqr_reg_cluster_kernel<R, 8>

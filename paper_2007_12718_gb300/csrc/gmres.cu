@@ -281,8 +281,11 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, cudaS
   sub_kernel<<<nb, 256, 0, st>>>(f, ws.w, ws.w, N);
   norm2(ws.w, N, ws.partial, ws.scal, st);
   z64* rn2 = reinterpret_cast<z64*>(pin + 128);
+  int* derr = reinterpret_cast<int*>(pin + 192);  // status of the preconditioner applies
   LS_CUDA_TRY(cudaMemcpyAsync(rn2, ws.scal, sizeof(z64), cudaMemcpyDeviceToHost, st));
+  LS_CUDA_TRY(cudaMemcpyAsync(derr, H->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   LS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (*derr) return *derr;
   if ((rc = check_launch("gmres finish"))) return rc;
   inf.iterations = k;
   inf.resid_est = resid;

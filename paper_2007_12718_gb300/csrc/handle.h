@@ -17,6 +17,8 @@ struct LevelData {
   void* Gsib = nullptr;  // k x k: G(skel_alpha, skel_beta) of two children on this level
   void* X = nullptr;     // per node: (s^2)^2 on the leaf level, (2 k_{l+1})^2 above
   void* S = nullptr;     // per node: k x k (levels >= 1)
+  void* UT = nullptr;    // k x m: U transposed (the apply reads every product row-wise)
+  void* GT = nullptr;    // k x k: Gsib transposed
 };
 
 struct ls_handle {
@@ -50,6 +52,10 @@ struct ls_handle {
   cudaGraphExec_t apply_exec = nullptr;  // Algorithm 2 recorded as a CUDA graph
   ls::z64** slots = nullptr;    // device-side input/output pointers of the apply graph
   long long apply_nodes = 0;    // kernels in the apply graph
+  void* apply_ops = nullptr;    // the apply as one persistent kernel: operation list (device)
+  int apply_nops = 0, apply_phases = 0, apply_blocks = 0;
+  unsigned* apply_bar = nullptr;     // its grid barrier: arrival counter and abort flag
+  unsigned long long apply_count = 0;  // applies launched (barrier epochs continue across them)
   double flops_build = 0, flops_compress = 0, bytes_apply = 0, factor_bytes = 0;
   int pivot_fallbacks = 0;      // merge levels that needed the row-pivoted inverse
 

@@ -337,6 +337,8 @@ void ls_free(ls_handle* H) {
     f(lv.Gsib);
     f(lv.X);
     f(lv.S);
+    f(lv.UT);
+    f(lv.GT);
   }
   f(H->Gleaf);
   f(H->XBU);
@@ -345,6 +347,8 @@ void ls_free(ls_handle* H) {
   f(H->d_err);
   f(H->gm);
   f(H->slots);
+  f(H->apply_ops);
+  f(H->apply_bar);
   if (H->apply_exec) cudaGraphExecDestroy(H->apply_exec);
   delete H;
 }
