@@ -1594,6 +1594,7 @@ struct ApplyOp {
   int type;        // 0: y[b] = y0[b] + alpha A[b] x[b];  1: gather leaves (y <- f);  2: scatter leaves (q <- x)
   int M, K, lda, batch;
   int phase_end;   // a grid barrier follows this operation
+  int rb;          // lanes per row (8, 16 or 32): short rows share a warp
   long long sA, sx, sy, sy0;
   const void* A;
   const void* x;   // null for the gather (reads f)
@@ -1624,6 +1625,52 @@ __device__ __forceinline__ bool apply_barrier(unsigned* count, unsigned* abort, 
   return *sflag != 0;
 }
 
+// One warp task: 32 / GS consecutive output rows of y = y0 + alpha A x, each
+// row a dot product over a group of GS lanes (GS = 8 or 16 for short rows, so
+// that lanes are not idle and the reduction takes log2(GS) shuffle rounds; 32
+// for long rows), four chunks of the row in flight per lane.
+template <class R, int GS>
+__device__ __forceinline__ void apply_rows(const ApplyOp& op, long long gw, long long nwarps, int lane) {
+  constexpr int RPW = 32 / GS;
+  const cx<R>* A = reinterpret_cast<const cx<R>*>(op.A);
+  const cx<R>* X = reinterpret_cast<const cx<R>*>(op.x);
+  const cx<R>* Y0 = reinterpret_cast<const cx<R>*>(op.y0);
+  cx<R>* Y = reinterpret_cast<cx<R>*>(op.y);
+  const cx<R> alpha = mk<R>((R)op.ar, (R)op.ai);
+  const int K = op.K, grp = lane / GS, li = lane % GS;
+  const long long rows = (long long)op.batch * op.M, tasks = (rows + RPW - 1) / RPW;
+  for (long long task = gw; task < tasks; task += nwarps) {
+    const long long r = task * RPW + grp;
+    const bool ok = r < rows;
+    const long long rc = ok ? r : 0;
+    const int b = (int)(rc / op.M), i = (int)(rc % op.M);
+    const cx<R>* a = A + b * op.sA + (long long)i * op.lda;
+    const cx<R>* xv = X + b * op.sx;
+    cx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0), acc2 = mk<R>(0, 0), acc3 = mk<R>(0, 0);
+    int j = li;
+    if (ok) {
+      for (; j + 3 * GS < K; j += 4 * GS) {
+        const cx<R> a0 = a[j], a1 = a[j + GS], a2 = a[j + 2 * GS], a3 = a[j + 3 * GS];
+        const cx<R> x0 = ldcg_cx(xv + j), x1 = ldcg_cx(xv + j + GS), x2 = ldcg_cx(xv + j + 2 * GS),
+                    x3 = ldcg_cx(xv + j + 3 * GS);
+        fma_(acc0, a0, x0);
+        fma_(acc1, a1, x1);
+        fma_(acc2, a2, x2);
+        fma_(acc3, a3, x3);
+      }
+      for (; j < K; j += GS) fma_(acc0, a[j], ldcg_cx(xv + j));
+    }
+    cx<R> v = (acc0 + acc1) + (acc2 + acc3);
+#pragma unroll
+    for (int o = GS / 2; o; o >>= 1) v = v + shfl_xor(v, o);
+    if (li == 0 && ok) {
+      cx<R> out = alpha * v;
+      if (Y0) out = out + ldcg_cx(Y0 + b * op.sy0 + i);
+      Y[b * op.sy + i] = out;
+    }
+  }
+}
+
 template <class R>
 __global__ void __launch_bounds__(1024) apply_persistent_kernel(const ApplyOp* __restrict__ ops, int nops, TreeGeom g,
                                                                 const z64* __restrict__ f, z64* __restrict__ q,
@@ -1651,29 +1698,12 @@ __global__ void __launch_bounds__(1024) apply_persistent_kernel(const ApplyOp* _
           q[gi] = cvt<double>(ldcg_cx(reinterpret_cast<const cx<R>*>(op.x) + t));
       }
     } else {
-      const cx<R>* A = reinterpret_cast<const cx<R>*>(op.A);
-      const cx<R>* X = reinterpret_cast<const cx<R>*>(op.x);
-      const cx<R>* Y0 = reinterpret_cast<const cx<R>*>(op.y0);
-      cx<R>* Y = reinterpret_cast<cx<R>*>(op.y);
-      const cx<R> alpha = mk<R>((R)op.ar, (R)op.ai);
-      for (long long r = gw; r < rows; r += nwarps) {
-        const int b = (int)(r / op.M), i = (int)(r % op.M);
-        const cx<R>* a = A + b * op.sA + (long long)i * op.lda;
-        const cx<R>* xv = X + b * op.sx;
-        cx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0);
-        int j = lane;
-        for (; j + 32 < op.K; j += 64) {
-          fma_(acc0, a[j], ldcg_cx(xv + j));
-          fma_(acc1, a[j + 32], ldcg_cx(xv + j + 32));
-        }
-        if (j < op.K) fma_(acc0, a[j], ldcg_cx(xv + j));
-        const cx<R> v = warp_sum(acc0 + acc1);
-        if (lane == 0) {
-          cx<R> out = alpha * v;
-          if (Y0) out = out + ldcg_cx(Y0 + b * op.sy0 + i);
-          Y[b * op.sy + i] = out;
-        }
-      }
+      if (op.rb == 8)
+        apply_rows<R, 8>(op, gw, nwarps, lane);
+      else if (op.rb == 16)
+        apply_rows<R, 16>(op, gw, nwarps, lane);
+      else
+        apply_rows<R, 32>(op, gw, nwarps, lane);
     }
     if (op.phase_end && o + 1 < nops) {
       target += gridDim.x;
@@ -1815,6 +1845,7 @@ int apply_persistent_init(ls_handle* H, cudaStream_t st) {
     }
   }
   std::vector<ApplyOp> ops = H->prec == LS_FP64 ? apply_ops<double>(H) : apply_ops<float>(H);
+  for (auto& o : ops) o.rb = o.K <= 64 ? 8 : o.K <= 160 ? 16 : 32;
   if ((rc = dalloc(&H->apply_ops, sizeof(ApplyOp) * ops.size()))) return rc;
   if ((rc = dalloc((void**)&H->apply_bar, 2 * sizeof(unsigned)))) return rc;
   LS_CUDA_TRY(cudaMemcpyAsync(H->apply_ops, ops.data(), sizeof(ApplyOp) * ops.size(), cudaMemcpyHostToDevice, st));
