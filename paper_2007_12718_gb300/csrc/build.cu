@@ -1083,6 +1083,7 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
     }
   } engine_scope(H);
   // leaves (once level L is compressed)
+  if ((rc = leaf_block(H, st))) return rc;
   if (wait_level && (rc = wait_level(L))) return rc;
   LevelData& lf = H->lev[L];
   const int kL = lf.k;
@@ -1113,6 +1114,7 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
   // merges, level by level
   for (int l = L - 1; l >= 0; --l) {
     if (wait_level && (rc = wait_level(std::max(l, 1)))) return rc;
+    if ((rc = sibling_block(H, l + 1, st))) return rc;  // G of the two children (Eq. 15)
     LevelData& lv = H->lev[l];
     const LevelData& ch = H->lev[l + 1];
     const int P = 1 << l, kc = ch.k, n2 = 2 * kc;

@@ -1127,8 +1127,10 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
   }
   int* pin = static_cast<int*>(pinned_scratch(sizeof(int) * (4 + (size_t)kmax)));
   if (!pin) return LS_ENOMEM;
+  // rank, status words and all kmax pivot slots (entries past the rank are unused) in one round trip
   LS_CUDA_TRY(cudaMemcpyAsync(pin, rank, sizeof(int), cudaMemcpyDeviceToHost, st));
   LS_CUDA_TRY(cudaMemcpyAsync(pin + 1, sync_buf + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (kmax > 0) LS_CUDA_TRY(cudaMemcpyAsync(pin + 4, piv, sizeof(int) * kmax, cudaMemcpyDeviceToHost, st));
   LS_CUDA_TRY(cudaStreamSynchronize(st));
   const int k = pin[0], abort_flag = pin[1];  // rank, barrier timeout
   if (pin[2]) {  // index check
@@ -1147,11 +1149,9 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
     return LS_ECUDA;
   }
   hp.assign(k > 0 ? k : 1, 0);
-  if (k > 0) LS_CUDA_TRY(cudaMemcpyAsync(pin + 4, piv, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
-  if (k > 0 && Uout)
-    LS_CUDA_TRY(cudaMemcpyAsync(Uout, Ut, sizeof(cx<R>) * (size_t)m * k, cudaMemcpyDeviceToDevice, st));
-  LS_CUDA_TRY(cudaStreamSynchronize(st));
   for (int a = 0; a < k; ++a) hp[a] = pin[4 + a];
+  if (k > 0 && Uout)  // stream-ordered: later users of U run after this copy
+    LS_CUDA_TRY(cudaMemcpyAsync(Uout, Ut, sizeof(cx<R>) * (size_t)m * k, cudaMemcpyDeviceToDevice, st));
   ls::dfree(wsp);
   for (int a = 0; a < k; ++a)
     if (hp[a] < 0 || hp[a] >= m) {
@@ -1168,46 +1168,6 @@ int compress_t(ls_handle* H, cudaStream_t st, const LevelDone& level_done) {
   int rc;
   std::vector<int> rows_x, rows_y;
   int* dint = nullptr;
-  // kernel block on the device for the given point lists (coordinates staged in dint)
-  auto device_block = [&](const std::vector<int>& rx, const std::vector<int>& ry, const std::vector<int>& cx_,
-                          const std::vector<int>& cy_, void** out) -> int {
-    int r;
-    if ((r = dalloc(out, sizeof(cx<R>) * std::max<size_t>(rx.size() * cx_.size(), 1)))) return r;
-    if (dint) ls::dfree(dint);
-    dint = nullptr;
-    if ((r = dalloc((void**)&dint, sizeof(int) * (2 * rx.size() + 2 * cx_.size() + 8)))) return r;
-    return upload_block<R>(rx, ry, cx_, cy_, reinterpret_cast<cx<R>*>(*out), dint, st, H->ks_prec,
-                           KernelTable{H->ktab, H->ktx, H->kty});
-  };
-  // leaf self-interaction block G(I_tau, I_tau) (the same for every leaf)
-  {
-    std::vector<int> lx, ly;
-    for (int y = 0; y < s; ++y)
-      for (int x = 0; x < s; ++x) {
-        lx.push_back(x);
-        ly.push_back(y);
-      }
-    if ((rc = device_block(lx, ly, lx, ly, &H->Gleaf))) return rc;
-  }
-  // sibling block G(skel_a, skel_b) of the two children on level l (Eq. 15)
-  auto sibling_block = [&](int l) -> int {
-    LevelData& lv = H->lev[l];
-    const int kk = lv.k;
-    int oax, oay, obx, oby;
-    if ((l - 1) % 2 == 0) {
-      oax = 0; oay = 0; obx = lv.w; oby = 0;
-    } else {
-      oax = 0; oay = lv.h; obx = 0; oby = 0;
-    }
-    std::vector<int> ax(kk), ay(kk), bx(kk), by(kk);
-    for (int i = 0; i < kk; ++i) {
-      ax[i] = lv.skel_x[i] + oax;
-      ay[i] = lv.skel_y[i] + oay;
-      bx[i] = lv.skel_x[i] + obx;
-      by[i] = lv.skel_y[i] + oby;
-    }
-    return device_block(ax, ay, bx, by, &lv.Gsib);
-  };
   for (int l = L; l >= 1; --l) {
     LevelData& lv = H->lev[l];
     rows_x.clear();
@@ -1255,7 +1215,6 @@ int compress_t(ls_handle* H, cudaStream_t st, const LevelDone& level_done) {
       count_launch();
       identity_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(reinterpret_cast<cx<R>*>(lv.U), m);
       if ((rc = check_launch("identity U"))) return rc;
-      if ((rc = sibling_block(l))) return rc;
       if (level_done) level_done(l);
       continue;
     }
@@ -1279,7 +1238,6 @@ int compress_t(ls_handle* H, cudaStream_t st, const LevelDone& level_done) {
       lv.skel_y[a] = rows_y[hp[a]];
     }
     H->flops_compress += 8.0 * 2.0 * (double)m * p * k;  // two projections per pivot step
-    if ((rc = sibling_block(l))) return rc;
     if (level_done) level_done(l);
   }
   if (dint) ls::dfree(dint);
@@ -1325,6 +1283,55 @@ int row_id(const z64* A, int m, int p, double eps, int precision, int nsm, int* 
   if (rc) return rc;
   for (int a = 0; a < *k; ++a) piv[a] = hp[a];
   return check_launch("row_id");
+}
+
+namespace {
+template <class R>
+int device_block_t(ls_handle* H, const std::vector<int>& rx, const std::vector<int>& ry, const std::vector<int>& cx_,
+                   const std::vector<int>& cy_, void** out, cudaStream_t st) {
+  int r;
+  if ((r = dalloc(out, sizeof(cx<R>) * std::max<size_t>(rx.size() * cx_.size(), 1)))) return r;
+  int* dint = nullptr;
+  if ((r = dalloc((void**)&dint, sizeof(int) * (2 * rx.size() + 2 * cx_.size() + 8)))) return r;
+  r = upload_block<R>(rx, ry, cx_, cy_, reinterpret_cast<cx<R>*>(*out), dint, st, H->ks_prec,
+                      KernelTable{H->ktab, H->ktx, H->kty});
+  ls::dfree(dint);
+  return r;
+}
+}  // namespace
+
+// Leaf self-interaction block G(I_tau, I_tau), the same for every leaf.
+int leaf_block(ls_handle* H, cudaStream_t st) {
+  std::vector<int> lx, ly;
+  for (int y = 0; y < H->s; ++y)
+    for (int x = 0; x < H->s; ++x) {
+      lx.push_back(x);
+      ly.push_back(y);
+    }
+  return H->prec == LS_FP64 ? device_block_t<double>(H, lx, ly, lx, ly, &H->Gleaf, st)
+                            : device_block_t<float>(H, lx, ly, lx, ly, &H->Gleaf, st);
+}
+
+// Sibling block G(skel_a, skel_b) of the two children on level l (Eq. 15); needs the
+// level's skeleton (host), not its compression kernels.
+int sibling_block(ls_handle* H, int l, cudaStream_t st) {
+  LevelData& lv = H->lev[l];
+  const int kk = lv.k;
+  int oax, oay, obx, oby;
+  if ((l - 1) % 2 == 0) {
+    oax = 0; oay = 0; obx = lv.w; oby = 0;
+  } else {
+    oax = 0; oay = lv.h; obx = 0; oby = 0;
+  }
+  std::vector<int> ax(kk), ay(kk), bx(kk), by(kk);
+  for (int i = 0; i < kk; ++i) {
+    ax[i] = lv.skel_x[i] + oax;
+    ay[i] = lv.skel_y[i] + oay;
+    bx[i] = lv.skel_x[i] + obx;
+    by[i] = lv.skel_y[i] + oby;
+  }
+  return H->prec == LS_FP64 ? device_block_t<double>(H, ax, ay, bx, by, &lv.Gsib, st)
+                            : device_block_t<float>(H, ax, ay, bx, by, &lv.Gsib, st);
 }
 
 int compress(ls_handle* H, cudaStream_t st, const LevelDone& level_done) {

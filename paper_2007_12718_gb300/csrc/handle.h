@@ -87,6 +87,10 @@ void* pinned_scratch(size_t bytes);
 
 // compress.cu
 int compress(ls_handle* H, cudaStream_t st, const LevelDone& level_done = LevelDone());
+// Kernel blocks the merges need: the leaf self-interaction block, and the sibling
+// block of level l (once the level's skeleton is known).
+int leaf_block(ls_handle* H, cudaStream_t st);
+int sibling_block(ls_handle* H, int l, cudaStream_t st);
 // Row ID of the device matrix A (m x p, candidate-major) in the given precision;
 // piv (host, m entries) and U (device, m x min(m, p) entries) receive k pivots / columns.
 int row_id(const z64* A, int m, int p, double eps, int precision, int nsm, int* sync_buf, cudaStream_t st, int* k,

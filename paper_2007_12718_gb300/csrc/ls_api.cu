@@ -362,10 +362,18 @@ void ls_free(ls_handle* H) {
 // waits for the last merge.
 static int build_pipelined(ls_handle* H, cudaStream_t st) {
   const int L = H->L;
-  cudaStream_t sm = nullptr;
-  LS_CUDA_TRY(cudaStreamCreateWithFlags(&sm, cudaStreamNonBlocking));
-  std::vector<cudaEvent_t> ev(L + 2, nullptr);
+  // the compression is the critical path: its stream gets the highest priority, so
+  // that its blocks are scheduled first when the merges occupy the SMs
+  int prio_low = 0, prio_high = 0;
+  LS_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+  cudaStream_t sm = nullptr, sc = nullptr;
+  LS_CUDA_TRY(cudaStreamCreateWithPriority(&sm, cudaStreamNonBlocking, prio_low));
+  LS_CUDA_TRY(cudaStreamCreateWithPriority(&sc, cudaStreamNonBlocking, prio_high));
+  std::vector<cudaEvent_t> ev(L + 3, nullptr);
   for (auto& e : ev) LS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  LS_CUDA_TRY(cudaEventRecord(ev[0], st));  // kernel table, spectrum, b: ready for both stages
+  LS_CUDA_TRY(cudaStreamWaitEvent(sc, ev[0], 0));
+  LS_CUDA_TRY(cudaStreamWaitEvent(sm, ev[0], 0));
   std::mutex mu;
   std::condition_variable cv;
   int ready = L + 1;  // the lowest level index compressed so far (levels finish from L down to 1)
@@ -389,14 +397,18 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
     mrc = r;
   });
   auto level_done = [&](int level) {
-    cudaEventRecord(ev[level], st);
+    cudaEventRecord(ev[level], sc);
     {
       std::lock_guard<std::mutex> lk(mu);
       ready = level;
     }
     cv.notify_all();
   };
-  int rc = ls::compress(H, st, level_done);
+  int rc;
+  {
+    ls::StreamScope scope(sc);
+    rc = ls::compress(H, sc, level_done);
+  }
   if (rc) {
     std::lock_guard<std::mutex> lk(mu);
     abort = true;
@@ -408,9 +420,12 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
     set_error(merr.c_str());
   }
   cudaEventRecord(ev[L + 1], sm);
+  cudaEventRecord(ev[L + 2], sc);
   cudaStreamWaitEvent(st, ev[L + 1], 0);
+  cudaStreamWaitEvent(st, ev[L + 2], 0);
   for (auto& e : ev) cudaEventDestroy(e);
   cudaStreamDestroy(sm);
+  cudaStreamDestroy(sc);
   return rc;
 }
 
