@@ -694,7 +694,8 @@ __global__ void __launch_bounds__(1024) cpqr_reg_grid_kernel(const cx<R>* __rest
   const int nblk = gridDim.x, blk = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cand = warp >> 2, part = warp & 3;
-  const int c0 = min(m, blk * 8), mc = min(m, c0 + 8) - c0;
+  const int cpb = blockDim.x >> 7;  // candidates per block (four warps each, at most 8)
+  const int c0 = min(m, blk * cpb), mc = min(m, c0 + cpb) - c0;
   __shared__ unsigned long long s_wkey[8];
   __shared__ R s_nrm[8];
   __shared__ cx<R> s_part[8][4];
@@ -721,6 +722,10 @@ __global__ void __launch_bounds__(1024) cpqr_reg_grid_kernel(const cx<R>* __rest
     if (lane == 0) s_npart[cand][part] = nrm;
   }
   if (tid == 0) s_fail = 0;
+  if (tid < 8) {  // slots of absent candidates stay empty
+    s_wkey[tid] = 0ULL;
+    s_nrm[tid] = R(0);
+  }
   __syncthreads();
   if (part == 0 && lane == 0) {
     const R nrm = ((s_npart[cand][0] + s_npart[cand][1]) + s_npart[cand][2]) + s_npart[cand][3];
@@ -797,7 +802,7 @@ __global__ void __launch_bounds__(1024) cpqr_reg_grid_kernel(const cx<R>* __rest
     if (s_fail) return;
     const unsigned long long key = __ldcg(&ex[j].key);
     int idx = key ? piv_key_index(key) : -1;
-    const int bw = idx >= 0 ? idx / 8 : 0;
+    const int bw = idx >= 0 ? idx / cpb : 0;
     if (idx >= m || (idx >= 0 && bw >= nblk)) {  // cannot happen; uniform
       if (tid == 0) atomicExch(err, 1);
       idx = -1;
@@ -939,7 +944,8 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
     per = 64;
     nblk = (m + per - 1) / per;
   }
-  const int nslot = std::max(nblk, (m + 7) / 8);  // slots for either grid kernel
+  const int nslot = std::max(nblk, (m + std::min(8, std::max(1, (m + nsm - 1) / nsm)) - 1) /
+                                        std::min(8, std::max(1, (m + nsm - 1) / nsm)));  // slots for either grid kernel
   size_t loop_smem = sizeof(cx<R>) * ((size_t)p + (size_t)per * p);
   size_t tail_smem = sizeof(cx<R>) * (size_t)8 * kmax;
   int use_smem = loop_smem <= 200 * 1024;
@@ -1024,7 +1030,9 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
   const int tneed = (p + 31) / 32;
   const int t_cl_max = sizeof(R) == 4 ? 20 : 8;
   int reg_mode = 0;  // 1 cluster, 2 grid
-  int treg = 0, clr = (m + 31) / 32, nblk_r = (m + 7) / 8;
+  // grid kernel: spread the candidates over all SMs (cpb per block, four warps each)
+  const int cpb = std::min(8, std::max(1, (m + nsm - 1) / nsm));
+  int treg = 0, clr = (m + 31) / 32, nblk_r = (m + cpb - 1) / cpb;
   const void* kreg = nullptr;
   size_t smem_r = 0;
   // clusters win while they are small (<= 6 blocks: levels with <= 192 candidates,
@@ -1049,11 +1057,11 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
            : treg == 12 ? (const void*)cpqr_reg_grid_kernel<R, 12> : (const void*)cpqr_reg_grid_kernel<R, 16>;
     else
       kreg = treg == 4 ? (const void*)cpqr_reg_grid_kernel<R, 4> : (const void*)cpqr_reg_grid_kernel<R, 8>;
-    smem_r = sizeof(cx<R>) * std::max((size_t)p, (size_t)8 * kmax);
+    smem_r = sizeof(cx<R>) * std::max((size_t)p, (size_t)cpb * kmax);
     int per_sm = 0;
     if (smem_r <= 220 * 1024 && nblk_r <= nsm &&
         cudaFuncSetAttribute(kreg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r) == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kreg, 1024, smem_r) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kreg, 128 * cpb, smem_r) == cudaSuccess &&
         nblk_r <= per_sm * nsm)
       reg_mode = 2;
     cudaGetLastError();
@@ -1097,7 +1105,7 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
     void* args[] = {&Ac, (void*)&m, (void*)&p, (void*)&kmax, &eps, &Rm, &sel, &piv, &rank, &Ut, &RT,
                     &slots, &pslots, &ex, &gs, &ierr};
     count_launch();
-    LS_CUDA_TRY(cudaLaunchCooperativeKernel(kreg, dim3(nblk_r), dim3(1024), args, smem_r, st));
+    LS_CUDA_TRY(cudaLaunchCooperativeKernel(kreg, dim3(nblk_r), dim3(128 * cpb), args, smem_r, st));
   }
   if (reg_mode) {
   } else if (use_cluster) {
