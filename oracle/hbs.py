@@ -24,11 +24,14 @@ Paper:
   The loop runs over every level l = L-1, ..., 0.
 * Algorithm 2 (apply): up pass (Eqs. (24), (28)), root solve (Eq. (29)), down
   pass over l = 1, ..., L-1 with Lemma 4.1 (Eq. (18)), leaf recovery.
+* The transposed apply (for the adjoint solve): the steps of Algorithm 2 in
+  reverse order, each factor transposed.
 
 Parity pins (tests/test_oracle_hbs.py): the ID property U(J,:) = I and its
 accuracy on the full complement block; the Lemma 4.1 identity; the HBS inverse
 against the dense inverse (error ~ eps, -> 0 as eps -> 0); Table 1's proxy
-accuracy.
+accuracy; the transposed apply by the bilinear identity y^T (M x) = (M^T y)^T x
+and against the dense transpose of M assembled column by column.
 """
 import numpy as np
 import scipy.linalg as sla
@@ -231,6 +234,53 @@ class Inverse:
             wt[l + 1] = self._lemma(l + 1, q, Uw)
         ql = r_leaf - self.XBU @ wt[L]
         return scatter_leaves(t, ql[..., 0])
+
+    def apply_transpose(self, g):
+        """q = M^T g for the map M of ``apply`` (plain transpose, no conjugate).
+
+        Algorithm 2 read backwards with every factor transposed (the adjoint of
+        each step, in reverse order):
+        * leaves: w~_L = -(X B U)^T g  (transpose of the leaf recovery);
+        * upward through the downward pass, l = L-1, ..., 1: with Gamma the
+          sibling map of Lemma 4.1 ([[0, G_ab], [G_ab^T, 0]], its own
+          transpose), t_l = X_l^T Gamma w~_{l+1} (kept), then
+          w~_l = U_l^T (w~_{l+1} - diag(S_a, S_b)^T t_l);
+        * root: r~_1 = X_0^T Gamma w~_1;
+        * downward through the upward pass, l = 1, ..., L-1:
+          r~_{l+1} = t_l + X_l^T U_l r~_l;
+        * leaves: q = X_L^T (g + U_L r~_L).
+        """
+        comp, t = self.comp, self.comp.tree
+        L = t.L
+
+        def T(a):
+            return np.swapaxes(a, -1, -2)
+
+        def pairs(x):  # children (2P, k, 1) -> parents (P, 2k, 1)
+            return np.concatenate([x[0::2], x[1::2]], axis=1)
+
+        def split(x):  # parents (P, 2k, 1) -> children (2P, k, 1)
+            k = x.shape[1] // 2
+            out = np.empty((2 * x.shape[0], k, x.shape[2]), dtype=x.dtype)
+            out[0::2] = x[:, :k]
+            out[1::2] = x[:, k:]
+            return out
+
+        gl = gather_leaves(t, np.asarray(g, dtype=np.complex128))[..., None]  # (2^L, n, 1)
+        w = -(T(self.XBU) @ gl)
+        tl = [None] * (L + 1)
+        for l in range(L - 1, 0, -1):
+            k = comp.rank[l + 1]
+            qbar = pairs(self._lemma(l + 1, pairs(w), None))
+            tl[l] = T(self.X[l]) @ qbar
+            Sa, Sb = self.S[l + 1][0::2], self.S[l + 1][1::2]
+            STt = np.concatenate([T(Sa) @ tl[l][:, :k], T(Sb) @ tl[l][:, k:]], axis=1)
+            w = comp.U[l].T[None] @ (pairs(w) - STt)
+        r = split(T(self.X[0]) @ pairs(self._lemma(1, pairs(w), None)))
+        for l in range(1, L):
+            r = split(tl[l] + T(self.X[l]) @ (comp.U[l][None] @ r))
+        out = T(self.X[L]) @ (gl + comp.U[L][None] @ r)
+        return scatter_leaves(t, out[..., 0])
 
     def _lemma(self, level, q, Uw):
         """Lemma 4.1: [w_a; w_b] = [[0, G_ab], [G_ba, 0]] [q_a; q_b] + U w_parent,

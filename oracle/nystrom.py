@@ -17,6 +17,7 @@ Functions:
 * ``dense_operator``  -- I + B G_p.
 * ``solve_dense``     -- LU solve (scipy).
 * ``matvec_fft``      -- (I + B G_p) x by zero-padded 2D FFT convolution.
+* ``matvec_fft_transpose`` -- (I + B G_p)^T x = x + G_p (B x).
 * ``field_at``        -- u(r) = h^2 sum_j G(|r - x_j|) sigma_j (Eq. (1)) for
                          receivers outside the domain.
 * ``rhs``             -- f = -kappa^2 b u_inc for a plane wave.
@@ -110,6 +111,15 @@ def matvec_fft(spec, kappa, b, x):
     ny, nx = b.shape
     conv = apply_conv(spec, x, nx, ny)
     return np.asarray(x) + (kappa * kappa) * b.ravel() * conv
+
+
+def matvec_fft_transpose(spec, kappa, b, x):
+    """(I + B G_p)^T x = x + G_p (B x) by FFT: G_p is complex symmetric
+    (Eq. (10): its entries depend on |x_i - x_j| and the corrections are
+    symmetric in the offset), so only the diagonal scaling moves."""
+    ny, nx = b.shape
+    bx = (kappa * kappa) * b.ravel() * np.asarray(x)
+    return np.asarray(x) + apply_conv(spec, bx, nx, ny)
 
 
 def field_at(kappa, h, nx, ny, sigma, receivers, x0=0.0, y0=0.0):
