@@ -115,13 +115,28 @@ int ls_build(const ls_grid* grid, double kappa, const double* b, double tol,
              const ls_opts* opts, void* stream, ls_handle** out);
 
 /* ls_apply -- q = M f, M ~ (I + B G_p)^-1 the HBS inverse (Algorithm 2,
- * Sec. 4.1).  f, q: nrhs complex128 grid vectors.  transpose must be 0. */
+ * Sec. 4.1); with transpose = 1, q = M^T f: the steps of Algorithm 2 in
+ * reverse order with every factor transposed (plain transpose, no
+ * conjugate), the preconditioner of the adjoint solve.  The first transposed
+ * apply on a handle makes transposed copies of the factors (as much device
+ * memory again as the factors).  f, q: nrhs complex128 grid vectors.
+ * transpose: 0 or 1, else LS_EINVAL.  Applies on one handle must not run
+ * concurrently (they share the handle's scratch). */
 int ls_apply(ls_handle* h, const void* f, void* q, int nrhs, int transpose, void* stream);
 
 /* ls_matvec -- y = (I + B (G + T)) x, the order_matvec operator applied by a
- * zero-padded 2D FFT convolution (Sec. 2.2 last paragraph, Sec. 5).
- * x, y: nrhs complex128 grid vectors (may not alias).  transpose must be 0. */
+ * zero-padded 2D FFT convolution (Sec. 2.2 last paragraph, Sec. 5); with
+ * transpose = 1, y = (I + B (G + T))^T x = x + (G + T)(B x) (G + T is
+ * complex symmetric: its entries depend on |x_i - x_j| and the correction
+ * stencil is symmetric, Eqs. 8, 10).  x, y: nrhs complex128 grid vectors (may
+ * not alias).  transpose: 0 or 1, else LS_EINVAL. */
 int ls_matvec(ls_handle* h, const void* x, void* y, int nrhs, int transpose, void* stream);
+
+/* ls_field -- u = (G + T) sigma on the grid: the scattered field at the nodes
+ * of a density sigma (Eq. 1 with the order_matvec corrected quadrature,
+ * Eqs. 8, 10), by the same FFT convolution.  sigma, u: nrhs complex128 grid
+ * vectors, host or device (may not alias). */
+int ls_field(ls_handle* h, const void* sigma, void* u, int nrhs, void* stream);
 
 /* ls_solve -- GMRES on (I + B (G+T)) sigma = f, right-preconditioned by the
  * HBS inverse (Sec. 5), from sigma = 0, no restart, stopping at
@@ -129,6 +144,45 @@ int ls_matvec(ls_handle* h, const void* x, void* y, int nrhs, int transpose, voi
  * vectors; info: nrhs entries (may be NULL).  Returns LS_ENOCONV if some
  * right-hand side did not converge (sigma is still written). */
 int ls_solve(ls_handle* h, const void* f, void* sigma, int nrhs, ls_solve_info* info, void* stream);
+
+/* ls_solve_transpose -- the same GMRES on the transposed system
+ * (I + B (G+T))^T sigma = f, right-preconditioned by M^T (ls_apply with
+ * transpose = 1): the adjoint solve of a gradient.  Arguments and return
+ * codes as ls_solve. */
+int ls_solve_transpose(ls_handle* h, const void* f, void* sigma, int nrhs, ls_solve_info* info, void* stream);
+
+/* ls_set_receivers -- receivers r_k for the calls below: the handle evaluates
+ * and keeps R[k][j] = h^2 G(|r_k - x_j|) (Eq. 1 by the trapezoidal rule, which
+ * is spectrally accurate for receivers outside the support of sigma;
+ * G = (i/4) H0(kappa r), Eq. 2), nr * N complex128 on the device.
+ *   rx: host, nr pairs (x, y).  nr = 0 clears.  A receiver on a grid node
+ *   returns LS_EINVAL.  Synchronises the stream. */
+int ls_set_receivers(ls_handle* h, const double* rx, int nr, void* stream);
+
+/* ls_receiver_field -- u[r][k] = sum_j R[k][j] sigma[r][j]: the field of
+ * nrhs densities at the receivers.  sigma: nrhs complex128 grid vectors; u:
+ * nrhs * nr complex128 ([nrhs][nr]); host or device.  LS_EINVAL without
+ * receivers. */
+int ls_receiver_field(ls_handle* h, const void* sigma, void* u, int nrhs, void* stream);
+
+/* ls_receiver_adjoint -- g[r][j] = sum_k R[k][j] v[r][k] (R^T v, no
+ * conjugate).  v: nrhs * nr complex128; g: nrhs complex128 grid vectors. */
+int ls_receiver_adjoint(ls_handle* h, const void* v, void* g, int nrhs, void* stream);
+
+/* ls_misfit_gradient -- for plane waves thetas[r] (host, nrhs angles) and
+ * data d ([nrhs][nr] complex128, host or device) at the handle's receivers:
+ *   J = sum_{r,k} |u_r(r_k) - d[r][k]|^2,  sigma_r = A^-1 f_r (ls_solve),
+ *   u_r = R sigma_r,  A = I + B (G+T),  f_r = -kappa^2 b u_inc,r (Eq. 3),
+ * and dJ/db by the adjoint method: lambda_r = A^-T R^T conj(u_r - d_r)
+ * (ls_solve_transpose), then
+ *   dJ/db_j = -2 kappa^2 sum_r Re(lambda_r[j] ((G+T) sigma_r + u_inc,r)[j]).
+ *   J: out, host double.  grad: out, ny*nx doubles, host or device.
+ *   info: NULL or 2 nrhs entries (the forward solves, then the adjoint ones).
+ * The gradient is that of the discrete system solved to gmres_tol; the HBS
+ * inverse only preconditions.  Returns LS_ENOCONV (outputs still written) if
+ * a solve did not converge, LS_EINVAL without receivers. */
+int ls_misfit_gradient(ls_handle* h, const double* thetas, int nrhs, const void* d, double* J, void* grad,
+                       ls_solve_info* info, void* stream);
 
 /* ls_rhs_plane_wave -- f = -kappa^2 b u_inc with u_inc = exp(i kappa (x1 cos theta
  * + x2 sin theta)) (right-hand side of Eq. 3), one complex128 grid vector per

@@ -7,10 +7,14 @@ fallback: if the library is missing or cannot load, every call raises.
 
 Entry points (same names as the C ABI):
   ls_build(grid_n, h, kappa, b, tol, **opts) -> Handle
-  ls_apply(handle, f, q)      q = M f       (HBS inverse, Algorithm 2)
-  ls_matvec(handle, x, y)     y = (I + B(G+T)) x   (FFT convolution, Sec. 5)
-  ls_solve(handle, f, sigma)  GMRES, right-preconditioned by M (Sec. 5)
+  ls_apply(handle, f, q, transpose=False)   q = M f or M^T f  (HBS inverse, Algorithm 2)
+  ls_matvec(handle, x, y, transpose=False)  y = A x or A^T x, A = I + B(G+T)  (FFT, Sec. 5)
+  ls_field(handle, sigma, u)                u = (G+T) sigma on the grid
+  ls_solve(handle, f, sigma)                GMRES on A, right-preconditioned by M (Sec. 5)
+  ls_solve_transpose(handle, f, sigma)      GMRES on A^T with M^T (adjoint solve)
   ls_rhs_plane_wave(handle, thetas, f)
+  ls_set_receivers / ls_receiver_field / ls_receiver_adjoint / ls_misfit_gradient
+  LSMisfit                                  torch.autograd.Function: J(b) and dJ/db
   ls_free(handle)
 Vectors are complex128 arrays [nrhs][ny][nx] (or [ny][nx]); torch tensors on
 the GPU are passed as device pointers, numpy arrays / CPU tensors as host
@@ -30,7 +34,8 @@ LS_FP64, LS_FP32, LS_TF32, LS_TF32X3 = 0, 1, 2, 3
 EXPORTED = ["ls_default_opts", "ls_build", "ls_apply", "ls_matvec", "ls_solve", "ls_rhs_plane_wave",
             "ls_get_build_info", "ls_free", "ls_strerror", "ls_last_error", "ls_profile_enable",
             "ls_profile_reset", "ls_profile_get", "ls_kernel_launches", "ls_matvec_noalloc",
-            "ls_matvec_noalloc_max_elems", "ls_cgemm_c64", "ls_row_id"]
+            "ls_matvec_noalloc_max_elems", "ls_cgemm_c64", "ls_row_id", "ls_field", "ls_solve_transpose",
+            "ls_set_receivers", "ls_receiver_field", "ls_receiver_adjoint", "ls_misfit_gradient"]
 
 
 class Grid(ctypes.Structure):
@@ -82,8 +87,17 @@ def load_library(path=LIB_PATH):
     for name in ("ls_apply", "ls_matvec"):
         getattr(lib, name).argtypes = [vp, vp, vp, ip, ip, vp]
         getattr(lib, name).restype = ip
-    lib.ls_solve.argtypes = [vp, vp, vp, ip, ctypes.POINTER(SolveInfo), vp]
-    lib.ls_solve.restype = ip
+    for name in ("ls_solve", "ls_solve_transpose"):
+        getattr(lib, name).argtypes = [vp, vp, vp, ip, ctypes.POINTER(SolveInfo), vp]
+        getattr(lib, name).restype = ip
+    for name in ("ls_field", "ls_receiver_field", "ls_receiver_adjoint"):
+        getattr(lib, name).argtypes = [vp, vp, vp, ip, vp]
+        getattr(lib, name).restype = ip
+    lib.ls_set_receivers.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ip, vp]
+    lib.ls_set_receivers.restype = ip
+    lib.ls_misfit_gradient.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ip, vp, ctypes.POINTER(ctypes.c_double),
+                                       vp, ctypes.POINTER(SolveInfo), vp]
+    lib.ls_misfit_gradient.restype = ip
     lib.ls_rhs_plane_wave.argtypes = [vp, ctypes.POINTER(ctypes.c_double), vp, ip, vp]
     lib.ls_rhs_plane_wave.restype = ip
     lib.ls_get_build_info.argtypes = [vp, ctypes.POINTER(BuildInfo)]
@@ -207,18 +221,33 @@ def _nrhs(handle, nelem):
     return nelem // handle.n
 
 
-def ls_apply(handle, f, q, stream=None):
+def ls_apply(handle, f, q, transpose=False, stream=None):
     fp, k1, n = _ptr(f, np.complex128)
     qp, k2, _ = _ptr(q, np.complex128, True)
-    _check(load_library().ls_apply(handle.ptr, fp, qp, _nrhs(handle, n), 0, _stream(stream)), "ls_apply")
+    _check(load_library().ls_apply(handle.ptr, fp, qp, _nrhs(handle, n), int(bool(transpose)), _stream(stream)),
+           "ls_apply")
     return q
 
 
-def ls_matvec(handle, x, y, stream=None):
+def ls_matvec(handle, x, y, transpose=False, stream=None):
     xp, k1, n = _ptr(x, np.complex128)
     yp, k2, _ = _ptr(y, np.complex128, True)
-    _check(load_library().ls_matvec(handle.ptr, xp, yp, _nrhs(handle, n), 0, _stream(stream)), "ls_matvec")
+    _check(load_library().ls_matvec(handle.ptr, xp, yp, _nrhs(handle, n), int(bool(transpose)), _stream(stream)),
+           "ls_matvec")
     return y
+
+
+def ls_field(handle, sigma, u, stream=None):
+    """u = (G+T) sigma on the grid (the scattered field of the density at the nodes)."""
+    sp_, k1, n = _ptr(sigma, np.complex128)
+    up, k2, _ = _ptr(u, np.complex128, True)
+    _check(load_library().ls_field(handle.ptr, sp_, up, _nrhs(handle, n), _stream(stream)), "ls_field")
+    return u
+
+
+def _infos(infos):
+    return [{"iterations": i.iterations, "converged": bool(i.converged), "resid_est": i.resid_est,
+             "resid_true": i.resid_true} for i in infos]
 
 
 def ls_solve(handle, f, sigma, stream=None, allow_noconv=False):
@@ -228,8 +257,98 @@ def ls_solve(handle, f, sigma, stream=None, allow_noconv=False):
     infos = (SolveInfo * nr)()
     _check(load_library().ls_solve(handle.ptr, fp, sp_, nr, infos, _stream(stream)), "ls_solve",
            allow=(LS_ENOCONV,) if allow_noconv else ())
-    return [{"iterations": i.iterations, "converged": bool(i.converged), "resid_est": i.resid_est,
-             "resid_true": i.resid_true} for i in infos]
+    return _infos(infos)
+
+
+def ls_solve_transpose(handle, f, sigma, stream=None, allow_noconv=False):
+    """GMRES on A^T sigma = f, right-preconditioned by M^T (the adjoint solve)."""
+    fp, k1, n = _ptr(f, np.complex128)
+    sp_, k2, _ = _ptr(sigma, np.complex128, True)
+    nr = _nrhs(handle, n)
+    infos = (SolveInfo * nr)()
+    _check(load_library().ls_solve_transpose(handle.ptr, fp, sp_, nr, infos, _stream(stream)), "ls_solve_transpose",
+           allow=(LS_ENOCONV,) if allow_noconv else ())
+    return _infos(infos)
+
+
+def ls_set_receivers(handle, receivers, stream=None):
+    """Receivers (nr x 2 array of positions, host) for the receiver calls below."""
+    rx = np.ascontiguousarray(receivers, dtype=np.float64).reshape(-1, 2)
+    _check(load_library().ls_set_receivers(handle.ptr, rx.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(rx),
+                                           _stream(stream)), "ls_set_receivers")
+    handle.nrec = len(rx)
+
+
+def ls_receiver_field(handle, sigma, u, stream=None):
+    """u[r][k] = h^2 sum_j G(|r_k - x_j|) sigma[r][j] (Eq. (1)); u has nrhs * nr entries."""
+    sp_, k1, n = _ptr(sigma, np.complex128)
+    up, k2, _ = _ptr(u, np.complex128, True)
+    _check(load_library().ls_receiver_field(handle.ptr, sp_, up, _nrhs(handle, n), _stream(stream)),
+           "ls_receiver_field")
+    return u
+
+
+def ls_receiver_adjoint(handle, v, g, stream=None):
+    """g[r][j] = h^2 sum_k G(|r_k - x_j|) v[r][k] (the transpose of ls_receiver_field)."""
+    vp_, k1, _ = _ptr(v, np.complex128)
+    gp, k2, n = _ptr(g, np.complex128, True)
+    _check(load_library().ls_receiver_adjoint(handle.ptr, vp_, gp, _nrhs(handle, n), _stream(stream)),
+           "ls_receiver_adjoint")
+    return g
+
+
+def ls_misfit_gradient(handle, thetas, data, grad, stream=None, allow_noconv=False):
+    """J = sum |u - data|^2 over plane waves `thetas` and the handle's receivers, and
+    dJ/db into `grad` (ny*nx float64) by the adjoint method.  Returns (J, infos)."""
+    th = np.ascontiguousarray(thetas, dtype=np.float64)
+    dp_, k1, _ = _ptr(data, np.complex128)
+    gp, k2, _ = _ptr(grad, np.float64, True)
+    J = ctypes.c_double(0.0)
+    infos = (SolveInfo * (2 * len(th)))()
+    _check(load_library().ls_misfit_gradient(handle.ptr, th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                             len(th), dp_, ctypes.byref(J), gp, infos, _stream(stream)),
+           "ls_misfit_gradient", allow=(LS_ENOCONV,) if allow_noconv else ())
+    return J.value, _infos(infos)
+
+
+def _make_misfit_function():
+    import torch
+
+    class LSMisfit(torch.autograd.Function):
+        """J(b) = sum over directions and receivers of |u(r_k) - d|^2 as a torch
+        function of the potential b (float64 [ny][nx], CUDA).  forward builds the
+        HBS preconditioner for b, runs the forward and adjoint solves and keeps
+        dJ/db; backward returns grad_output * dJ/db.  Usage:
+            J = LSMisfit.apply(b, h, kappa, thetas, receivers, data, build_kwargs)"""
+
+        @staticmethod
+        def forward(ctx, b, h, kappa, thetas, receivers, data, build_kwargs=None):
+            kw = dict(build_kwargs or {})
+            tol = kw.pop("tol", 1e-4)
+            H = ls_build(b.shape[1], h, kappa, b.detach().contiguous(), tol, ny=b.shape[0], **kw)
+            try:
+                ls_set_receivers(H, receivers)
+                grad = torch.empty_like(b, dtype=torch.float64)
+                J, _ = ls_misfit_gradient(H, thetas, data, grad)
+            finally:
+                ls_free(H)
+            ctx.save_for_backward(grad)
+            return torch.tensor(J, dtype=torch.float64, device=b.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (grad,) = ctx.saved_tensors
+            return gout * grad, None, None, None, None, None, None
+
+    return LSMisfit
+
+
+def __getattr__(name):
+    if name == "LSMisfit":
+        fn = _make_misfit_function()
+        globals()["LSMisfit"] = fn
+        return fn
+    raise AttributeError(name)
 
 
 def ls_matvec_noalloc(handle, x, y, stream=None):

@@ -1717,12 +1717,40 @@ __global__ void __launch_bounds__(1024) apply_persistent_kernel(const ApplyOp* _
   }
 }
 
+// T[b] = A[b]^T for a batch of row-major M x N matrices (stride M N), 32 x 32
+// tiles staged through shared memory so that reads and writes are coalesced.
 template <class R>
-__global__ void transpose_kernel(const cx<R>* __restrict__ A, int M, int N, cx<R>* __restrict__ T) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)M * N) return;
-  const int i = (int)(t / N), j = (int)(t % N);
-  T[(long long)j * M + i] = A[t];
+__global__ void __launch_bounds__(256) transpose_batch_kernel(const cx<R>* __restrict__ A, int M, int N, int batch,
+                                                              cx<R>* __restrict__ T) {
+  __shared__ cx<R> tile[32][33];
+  const long long stride = (long long)M * N;
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  for (int bi = blockIdx.z; bi < batch; bi += gridDim.z) {
+    const cx<R>* a = A + bi * stride;
+    cx<R>* t = T + bi * stride;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      const int i = i0 + r, j = j0 + threadIdx.x;
+      if (i < M && j < N) tile[r][threadIdx.x] = a[(long long)i * N + j];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      const int j = j0 + r, i = i0 + threadIdx.x;
+      if (i < M && j < N) t[(long long)j * M + i] = tile[threadIdx.x][r];
+    }
+    __syncthreads();
+  }
+}
+
+// dst (es-byte complex entries) = batch of transposed M x N blocks of src.
+int transpose_batch(bool fp64, const void* src, int M, int N, int batch, void* dst, cudaStream_t st) {
+  if ((long long)M * N <= 0 || batch <= 0) return LS_OK;
+  const dim3 grid((unsigned)((N + 31) / 32), (unsigned)((M + 31) / 32), (unsigned)std::min(batch, 65535));
+  count_launch();
+  if (fp64)
+    transpose_batch_kernel<double><<<grid, dim3(32, 8), 0, st>>>((const z64*)src, M, N, batch, (z64*)dst);
+  else
+    transpose_batch_kernel<float><<<grid, dim3(32, 8), 0, st>>>((const c32*)src, M, N, batch, (c32*)dst);
+  return check_launch("transpose_batch");
 }
 
 // Operation list of Algorithm 2 (the same products as apply_core).
@@ -1809,56 +1837,196 @@ std::vector<ApplyOp> apply_ops(ls_handle* H) {
   return ops;
 }
 
+// Operation list of the transposed apply q = M^T g: the steps of Algorithm 2
+// in reverse order, each factor transposed (plain transpose, no conjugate):
+//   leaves      w~_L = -(X B U)^T g
+//   l = L-1..1  t_l = X_l^T Gamma w~_{l+1}  (Gamma: the sibling map of Lemma 4.1,
+//               [[0, G], [G^T, 0]], its own transpose; t_l kept for later),
+//               w~_l = U_l^T (w~_{l+1} - diag(S_a, S_b)^T t_l)
+//   root        r~_1 = X_0^T Gamma w~_1
+//   l = 1..L-1  r~_{l+1} = t_l + X_l^T U_l r~_l
+//   leaves      q = X_L^T (g + U_L r~_L)
+// It reads the transposed copies XT, ST, XBUT, UT, GT and the plain U, G.
+template <class R>
+std::vector<ApplyOp> apply_ops_transpose(ls_handle* H) {
+  const int L = H->L, n = H->s * H->s;
+  const long long nleaf = 1LL << L;
+  cx<R>* F = reinterpret_cast<cx<R>*>(H->work);
+  cx<R>* Rl = F + nleaf * n;
+  cx<R>* p = Rl + nleaf * n;
+  std::vector<cx<R>*> rt(L + 1), wt(L + 1), tmp(L + 1);
+  for (int l = 1; l <= L; ++l) {
+    size_t sz = ((size_t)1 << l) * std::max(1, H->lev[l].k) * 2;
+    rt[l] = p;
+    p += sz;
+    wt[l] = p;
+    p += sz;
+    tmp[l] = p;
+    p += sz;
+  }
+  std::vector<ApplyOp> ops;
+  auto gemv = [&](int M, int K, const void* A, int lda, long long sA, const void* x, long long sx, void* y,
+                  long long sy, int batch, bool end, double ar = 1.0, const void* y0 = nullptr, long long sy0 = 0) {
+    ApplyOp o;
+    memset(&o, 0, sizeof(o));
+    o.type = 0;
+    o.M = M;
+    o.K = K;
+    o.A = A;
+    o.lda = lda;
+    o.sA = sA;
+    o.x = x;
+    o.sx = sx;
+    o.y = y;
+    o.sy = sy;
+    o.batch = batch;
+    o.phase_end = end ? 1 : 0;
+    o.ar = ar;
+    o.y0 = y0;
+    o.sy0 = sy0;
+    ops.push_back(o);
+  };
+  auto leafop = [&](int type, void* y, const void* x) {
+    ApplyOp o;
+    memset(&o, 0, sizeof(o));
+    o.type = type;
+    o.M = n;
+    o.batch = (int)nleaf;
+    o.y = y;
+    o.x = x;
+    o.phase_end = 1;
+    ops.push_back(o);
+  };
+  const LevelData& lf = H->lev[L];
+  const int kL = lf.k;
+  leafop(1, F, nullptr);                                                              // F <- g
+  gemv(kL, n, H->XBUT, n, (long long)kL * n, F, n, wt[L], kL, (int)nleaf, true, -1.0);
+  for (int l = L - 1; l >= 1; --l) {
+    const int P = 1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
+    const cx<R>* STc = reinterpret_cast<const cx<R>*>(H->lev[l + 1].ST);
+    gemv(kc, kc, H->lev[l + 1].Gsib, kc, 0, wt[l + 1] + kc, n2, tmp[l + 1], n2, P, false);       // Gamma w~
+    gemv(kc, kc, H->lev[l + 1].GT, kc, 0, wt[l + 1], n2, tmp[l + 1] + kc, n2, P, true);
+    gemv(n2, n2, H->lev[l].XT, n2, (long long)n2 * n2, tmp[l + 1], n2, rt[l + 1], n2, P, true);  // t_l
+    gemv(kc, kc, STc, kc, 2LL * kc * kc, rt[l + 1], n2, tmp[l + 1], n2, P, false, -1.0, wt[l + 1], n2);
+    gemv(kc, kc, STc + (size_t)kc * kc, kc, 2LL * kc * kc, rt[l + 1] + kc, n2, tmp[l + 1] + kc, n2, P, true, -1.0,
+         wt[l + 1] + kc, n2);                                                          // w~ - diag(S)^T t_l
+    gemv(kp, n2, H->lev[l].UT, n2, 0, tmp[l + 1], n2, wt[l], kp, P, true);            // w~_l
+  }
+  {
+    const int kc = H->lev[1].k, n2 = 2 * kc;
+    gemv(kc, kc, H->lev[1].Gsib, kc, 0, wt[1] + kc, 0, tmp[1], 0, 1, false);
+    gemv(kc, kc, H->lev[1].GT, kc, 0, wt[1], 0, tmp[1] + kc, 0, 1, true);
+    gemv(n2, n2, H->lev[0].XT, n2, 0, tmp[1], 0, rt[1], 0, 1, true);                  // r~_1
+  }
+  for (int l = 1; l <= L - 1; ++l) {
+    const int P = 1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
+    gemv(n2, kp, H->lev[l].U, kp, 0, rt[l], kp, tmp[l + 1], n2, P, true);             // U r~_l
+    gemv(n2, n2, H->lev[l].XT, n2, (long long)n2 * n2, tmp[l + 1], n2, rt[l + 1], n2, P, true, 1.0, rt[l + 1],
+         n2);                                                                          // r~_{l+1} = t_l + X^T U r~_l
+  }
+  gemv(n, kL, lf.U, kL, 0, rt[L], kL, Rl, n, (int)nleaf, true, 1.0, F, n);           // g + U r~_L
+  gemv(n, n, lf.XT, n, (long long)n * n, Rl, n, F, n, (int)nleaf, true);             // q = X^T (.)
+  leafop(2, nullptr, F);                                                              // q -> grid
+  return ops;
+}
+
+// U^T and G^T of every level (the apply reads every product row-wise).
+int level_transposes(ls_handle* H, cudaStream_t st) {
+  const bool fp64 = H->prec == LS_FP64;
+  const size_t es = fp64 ? sizeof(z64) : sizeof(c32);
+  int rc;
+  for (int l = 1; l <= H->L; ++l) {
+    LevelData& lv = H->lev[l];
+    if (lv.UT) continue;
+    const int m = l == H->L ? H->s * H->s : 2 * H->lev[l + 1].k, k = lv.k;
+    if ((rc = dalloc(&lv.UT, es * (size_t)std::max(m * k, 1)))) return rc;
+    if ((rc = dalloc(&lv.GT, es * (size_t)std::max(k * k, 1)))) return rc;
+    if ((rc = transpose_batch(fp64, lv.U, m, k, 1, lv.UT, st))) return rc;
+    if ((rc = transpose_batch(fp64, lv.Gsib, k, k, 1, lv.GT, st))) return rc;
+  }
+  return LS_OK;
+}
+
+std::vector<int> phase_ends(const std::vector<ApplyOp>& ops) {
+  std::vector<int> e;
+  for (int i = 0; i < (int)ops.size(); ++i)
+    if (ops[i].phase_end) e.push_back(i);
+  return e;
+}
+
+int upload_ops(std::vector<ApplyOp>& ops, void** dst, cudaStream_t st) {
+  for (auto& o : ops) o.rb = o.K <= 64 ? 8 : o.K <= 160 ? 16 : 32;
+  int rc;
+  if ((rc = dalloc(dst, sizeof(ApplyOp) * ops.size()))) return rc;
+  LS_CUDA_TRY(cudaMemcpyAsync(*dst, ops.data(), sizeof(ApplyOp) * ops.size(), cudaMemcpyHostToDevice, st));
+  LS_CUDA_TRY(cudaStreamSynchronize(st));  // the host vector is released by the caller
+  return LS_OK;
+}
+
 // Prepares the persistent apply (transposed U and G, the operation list, the
 // barrier); returns LS_OK without preparing it if a cooperative grid of one
 // 1024-thread block per SM cannot be co-resident (the graph path is used then).
 int apply_persistent_init(ls_handle* H, cudaStream_t st) {
-  if (H->apply_ops) return LS_OK;
+  if (H->apply_ops || H->apply_blocks < 0) return LS_OK;
   const void* kfn = H->prec == LS_FP64 ? (const void*)apply_persistent_kernel<double>
                                        : (const void*)apply_persistent_kernel<float>;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 1024, 0) != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
+    H->apply_blocks = -1;  // not co-resident: graph path (forward), one launch per phase (transposed)
     return LS_OK;
   }
-  const size_t es = H->prec == LS_FP64 ? sizeof(z64) : sizeof(c32);
   int rc;
-  for (int l = 1; l <= H->L; ++l) {
+  if ((rc = level_transposes(H, st))) return rc;
+  std::vector<ApplyOp> ops = H->prec == LS_FP64 ? apply_ops<double>(H) : apply_ops<float>(H);
+  if ((rc = upload_ops(ops, &H->apply_ops, st))) return rc;
+  if (!H->apply_bar) {
+    if ((rc = dalloc((void**)&H->apply_bar, 2 * sizeof(unsigned)))) return rc;
+    LS_CUDA_TRY(cudaMemsetAsync(H->apply_bar, 0, 2 * sizeof(unsigned), st));
+    H->apply_epoch = 0;
+  }
+  H->apply_nops = (int)ops.size();
+  H->apply_phases = (int)phase_ends(ops).size();
+  H->apply_blocks = H->nsm;
+  return check_launch("apply_persistent_init");
+}
+
+// Prepares the transposed apply: the transposed factors (once per handle; they
+// double the factor memory, so they are made only when a transposed apply is
+// asked for) and its operation list.
+int apply_transpose_init(ls_handle* H, cudaStream_t st) {
+  if (H->apply_ops_t) return LS_OK;
+  const bool fp64 = H->prec == LS_FP64;
+  const size_t es = fp64 ? sizeof(z64) : sizeof(c32);
+  const int L = H->L, n = H->s * H->s;
+  int rc;
+  if ((rc = level_transposes(H, st))) return rc;
+  for (int l = 0; l <= L; ++l) {
     LevelData& lv = H->lev[l];
-    const int m = l == H->L ? H->s * H->s : 2 * H->lev[l + 1].k, k = lv.k;
-    if (!lv.UT) {
-      if ((rc = dalloc(&lv.UT, es * (size_t)std::max(m * k, 1)))) return rc;
-      if ((rc = dalloc(&lv.GT, es * (size_t)std::max(k * k, 1)))) return rc;
-      const long long t1 = (long long)m * k, t2 = (long long)k * k;
-      if (t1 > 0) {
-        count_launch();
-        if (H->prec == LS_FP64)
-          transpose_kernel<double><<<(unsigned)((t1 + 255) / 256), 256, 0, st>>>((const z64*)lv.U, m, k, (z64*)lv.UT);
-        else
-          transpose_kernel<float><<<(unsigned)((t1 + 255) / 256), 256, 0, st>>>((const c32*)lv.U, m, k, (c32*)lv.UT);
-      }
-      if (t2 > 0) {
-        count_launch();
-        if (H->prec == LS_FP64)
-          transpose_kernel<double><<<(unsigned)((t2 + 255) / 256), 256, 0, st>>>((const z64*)lv.Gsib, k, k, (z64*)lv.GT);
-        else
-          transpose_kernel<float><<<(unsigned)((t2 + 255) / 256), 256, 0, st>>>((const c32*)lv.Gsib, k, k, (c32*)lv.GT);
-      }
+    const int nx = l == L ? n : 2 * H->lev[l + 1].k, P = 1 << l;
+    if (!lv.XT) {
+      if ((rc = dalloc(&lv.XT, es * (size_t)P * std::max(nx * nx, 1)))) return rc;
+      if ((rc = transpose_batch(fp64, lv.X, nx, nx, P, lv.XT, st))) return rc;
+    }
+    if (l >= 2 && !lv.ST) {
+      if ((rc = dalloc(&lv.ST, es * (size_t)P * std::max(lv.k * lv.k, 1)))) return rc;
+      if ((rc = transpose_batch(fp64, lv.S, lv.k, lv.k, P, lv.ST, st))) return rc;
     }
   }
-  std::vector<ApplyOp> ops = H->prec == LS_FP64 ? apply_ops<double>(H) : apply_ops<float>(H);
-  for (auto& o : ops) o.rb = o.K <= 64 ? 8 : o.K <= 160 ? 16 : 32;
-  if ((rc = dalloc(&H->apply_ops, sizeof(ApplyOp) * ops.size()))) return rc;
-  if ((rc = dalloc((void**)&H->apply_bar, 2 * sizeof(unsigned)))) return rc;
-  LS_CUDA_TRY(cudaMemcpyAsync(H->apply_ops, ops.data(), sizeof(ApplyOp) * ops.size(), cudaMemcpyHostToDevice, st));
-  LS_CUDA_TRY(cudaMemsetAsync(H->apply_bar, 0, 2 * sizeof(unsigned), st));
-  LS_CUDA_TRY(cudaStreamSynchronize(st));  // the host vector is released on return
-  H->apply_nops = (int)ops.size();
-  H->apply_phases = 0;
-  for (auto& o : ops) H->apply_phases += o.phase_end;
-  H->apply_blocks = H->nsm;
-  H->apply_count = 0;
-  return check_launch("apply_persistent_init");
+  const int kL = H->lev[L].k;
+  if ((rc = dalloc(&H->XBUT, es * ((size_t)1 << L) * n * std::max(kL, 1)))) return rc;
+  if ((rc = transpose_batch(fp64, H->XBU, n, kL, 1 << L, H->XBUT, st))) return rc;
+  std::vector<ApplyOp> ops = fp64 ? apply_ops_transpose<double>(H) : apply_ops_transpose<float>(H);
+  if ((rc = upload_ops(ops, &H->apply_ops_t, st))) return rc;
+  if (!H->apply_bar) {
+    if ((rc = dalloc((void**)&H->apply_bar, 2 * sizeof(unsigned)))) return rc;
+    LS_CUDA_TRY(cudaMemsetAsync(H->apply_bar, 0, 2 * sizeof(unsigned), st));
+    H->apply_epoch = 0;
+  }
+  H->apply_nops_t = (int)ops.size();
+  H->apply_phase_end_t = phase_ends(ops);
+  H->apply_phases_t = (int)H->apply_phase_end_t.size();
+  return check_launch("apply_transpose_init");
 }
 
 // The apply is recorded once per handle as a CUDA graph on a private stream
@@ -1904,10 +2072,52 @@ int simt_cgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, c32 alpha
   return check_launch("simt_cgemm");
 }
 
-int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, cudaStream_t st) {
+int simt_zgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, z64 alpha, const z64* A, int lda, long long sA,
+               const z64* B, int ldb, long long sB, z64 beta, z64* C, int ldc, long long sC, int batch) {
+  gemm<double>(st, ta, tb, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch);
+  return check_launch("simt_zgemm");
+}
+
+int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, int transpose, cudaStream_t st) {
   const long long N = (long long)H->grid.nx * H->grid.ny;
   int rc;
   if ((rc = apply_persistent_init(H, st))) return rc;
+  if (transpose) {
+    if ((rc = apply_transpose_init(H, st))) return rc;
+    const TreeGeom g = make_geom(H);
+    const void* kfn = H->prec == LS_FP64 ? (const void*)apply_persistent_kernel<double>
+                                         : (const void*)apply_persistent_kernel<float>;
+    const ApplyOp* ops_all = reinterpret_cast<const ApplyOp*>(H->apply_ops_t);
+    unsigned* bar = H->apply_bar;
+    int* err = H->d_err;
+    for (int r = 0; r < nrhs; ++r) {
+      int tk = prof_begin(st);
+      const z64* fr = f + r * N;
+      z64* qr = q + r * N;
+      if (H->apply_ops) {  // one cooperative launch, barriers between the phases
+        const ApplyOp* ops = ops_all;
+        int nops = H->apply_nops_t;
+        unsigned epoch0 = H->apply_epoch;
+        void* args[] = {&ops, &nops, (void*)&g, &fr, &qr, &bar, &epoch0, &err};
+        count_launch();
+        LS_CUDA_TRY(cudaLaunchCooperativeKernel(kfn, dim3(H->apply_blocks), dim3(1024), args, 0, st));
+        H->apply_epoch += (unsigned)(H->apply_phases_t - 1) * (unsigned)H->apply_blocks;
+      } else {  // one launch per phase (no barrier is reached inside a launch)
+        int start = 0;
+        for (int e : H->apply_phase_end_t) {
+          const ApplyOp* ops = ops_all + start;
+          int nops = e + 1 - start;
+          unsigned epoch0 = 0;
+          void* args[] = {&ops, &nops, (void*)&g, &fr, &qr, &bar, &epoch0, &err};
+          count_launch();
+          LS_CUDA_TRY(cudaLaunchKernel(kfn, dim3(H->nsm), dim3(1024), args, 0, st));
+          start = e + 1;
+        }
+      }
+      prof_end(tk, PR_APPLY, st, H->bytes_apply, 0.0);
+    }
+    return check_launch("hbs_apply (transposed)");
+  }
   if (H->apply_ops) {
     const TreeGeom g = make_geom(H);
     const void* kfn = H->prec == LS_FP64 ? (const void*)apply_persistent_kernel<double>
@@ -1920,12 +2130,12 @@ int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, cudaStream_t st) {
       z64* qr = q + r * N;
       unsigned* bar = H->apply_bar;
       // barrier epochs continue across applies: (phases - 1) barriers of apply_blocks arrivals each
-      unsigned epoch0 = (unsigned)(H->apply_count * (unsigned long long)(H->apply_phases - 1) * H->apply_blocks);
+      unsigned epoch0 = H->apply_epoch;
       int* err = H->d_err;
       void* args[] = {&ops, &nops, (void*)&g, &fr, &qr, &bar, &epoch0, &err};
       count_launch();
       LS_CUDA_TRY(cudaLaunchCooperativeKernel(kfn, dim3(H->apply_blocks), dim3(1024), args, 0, st));
-      ++H->apply_count;
+      H->apply_epoch += (unsigned)(H->apply_phases - 1) * (unsigned)H->apply_blocks;
       prof_end(tk, PR_APPLY, st, H->bytes_apply, 0.0);
     }
     return check_launch("hbs_apply");

@@ -72,15 +72,24 @@ __global__ void twiddle_kernel(z64* tw, int L) {
 }
 
 // Pass 1: rows. in: [rhs][nrow][ld_in] (first nvalid entries used); out: [rhs][nrow][L].
+// bsc (may be null): the input is scaled by kap2 * bsc[row][i] (the transposed
+// operator convolves B x).
 __global__ void rows_fwd_kernel(const z64* in, int ld_in, int nvalid, long long in_rhs_stride, z64* out, long long out_rhs_stride, int L, int logL,
-                                const z64* __restrict__ tw) {
+                                const z64* __restrict__ tw, const double* __restrict__ bsc, double kap2) {
   extern __shared__ z64 sm[];
   z64* s = sm;
   z64* stw = sm + L;
   int row = blockIdx.x, rhs = blockIdx.y;
   const z64* src = in + rhs * in_rhs_stride + (long long)row * ld_in;
   for (int i = threadIdx.x; i < L / 2; i += blockDim.x) stw[i] = tw[i];
-  for (int i = threadIdx.x; i < L; i += blockDim.x) s[i] = i < nvalid ? src[i] : mk<double>(0.0, 0.0);
+  for (int i = threadIdx.x; i < L; i += blockDim.x) {
+    z64 v = i < nvalid ? src[i] : mk<double>(0.0, 0.0);
+    if (bsc && i < nvalid) {
+      const double bb = kap2 * bsc[(long long)row * nvalid + i];
+      v = mk<double>(bb * v.re, bb * v.im);
+    }
+    s[i] = v;
+  }
   __syncthreads();
   fft_dif(s, L, logL, 1, 1, stw);
   z64* dst = out + rhs * out_rhs_stride + (long long)row * L;
@@ -127,10 +136,11 @@ __global__ void cols_kernel(z64* __restrict__ W, long long rhs_stride, int Lx, i
   }
 }
 
-// Pass 3: rows inverse + epilogue y = x + kappa^2 b .* conv (or y = conv).
+// Pass 3: rows inverse + epilogue (ConvMode): y = x + kappa^2 b .* conv
+// (forward), y = x + conv (transpose: B was applied to the input), y = conv (field).
 __global__ void rows_inv_kernel(const z64* __restrict__ W, long long w_rhs_stride, int L, int logL,
                                 const z64* __restrict__ tw, const z64* __restrict__ x, const double* __restrict__ b,
-                                double kap2, int nx, long long g_rhs_stride, z64* __restrict__ y, int field_only) {
+                                double kap2, int nx, long long g_rhs_stride, z64* __restrict__ y, int mode) {
   extern __shared__ z64 sm[];
   z64* s = sm;
   z64* stw = sm + L;
@@ -143,10 +153,10 @@ __global__ void rows_inv_kernel(const z64* __restrict__ W, long long w_rhs_strid
   long long off = rhs * g_rhs_stride + (long long)row * nx;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     z64 cv = s[i];
-    if (field_only) {
+    if (mode == CONV_FIELD) {
       y[off + i] = cv;
     } else {
-      double bb = kap2 * b[(long long)row * nx + i];
+      const double bb = mode == CONV_FORWARD ? kap2 * b[(long long)row * nx + i] : 1.0;
       z64 xv = x[off + i];
       y[off + i] = mk<double>(xv.re + bb * cv.re, xv.im + bb * cv.im);
     }
@@ -243,7 +253,8 @@ int conv_setup(ls_handle* H, cudaStream_t st) {
   size_t smr = sizeof(z64) * (H->Lx + H->Lx / 2);
   cudaFuncSetAttribute(rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
   count_launch();
-  rows_fwd_kernel<<<dim3(H->Ly, 1), 256, smr, st>>>(full, H->Lx, H->Lx, 0, full, 0, H->Lx, H->logLx, H->tw_x);
+  rows_fwd_kernel<<<dim3(H->Ly, 1), 256, smr, st>>>(full, H->Lx, H->Lx, 0, full, 0, H->Lx, H->logLx, H->tw_x,
+                                                    nullptr, 0.0);
   int C = cols_per_block(H->Ly);
   size_t smc = sizeof(z64) * ((size_t)H->Ly * C + H->Ly / 2);
   cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
@@ -260,7 +271,7 @@ int conv_setup(ls_handle* H, cudaStream_t st) {
   return LS_OK;
 }
 
-int conv_apply(ls_handle* H, const z64* x, z64* y, int nrhs, bool field_only, cudaStream_t st) {
+int conv_apply(ls_handle* H, const z64* x, z64* y, int nrhs, int mode, cudaStream_t st) {
   const int nx = H->grid.nx, ny = H->grid.ny;
   int rc;
   if (H->convbuf_rhs < nrhs) {
@@ -279,8 +290,10 @@ int conv_apply(ls_handle* H, const z64* x, z64* y, int nrhs, bool field_only, cu
   int tk = prof_begin(st);
   count_launch();
   rows_fwd_kernel<<<dim3(ny, nrhs), 256, smr, st>>>(x, nx, nx, g_stride, H->convbuf, w_stride, H->Lx, H->logLx,
-                                                    H->tw_x);
-  prof_end(tk, PR_MV_ROWS_FWD, st, R * (16.0 * N + 16.0 * W), R * 5.0 * W * H->logLx);
+                                                    H->tw_x, mode == CONV_TRANSPOSE ? H->b : nullptr,
+                                                    H->kappa * H->kappa);
+  prof_end(tk, PR_MV_ROWS_FWD, st, R * (16.0 * N + 16.0 * W) + (mode == CONV_TRANSPOSE ? 8.0 * N : 0.0),
+           R * 5.0 * W * H->logLx);
   int C = cols_per_block(H->Ly);
   size_t smc = sizeof(z64) * ((size_t)H->Ly * C + H->Ly / 2);
   cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
@@ -293,8 +306,10 @@ int conv_apply(ls_handle* H, const z64* x, z64* y, int nrhs, bool field_only, cu
   tk = prof_begin(st);
   count_launch();
   rows_inv_kernel<<<dim3(ny, nrhs), 256, smr, st>>>(H->convbuf, w_stride, H->Lx, H->logLx, H->tw_x, x, H->b,
-                                                    H->kappa * H->kappa, nx, g_stride, y, field_only ? 1 : 0);
-  prof_end(tk, PR_MV_ROWS_INV, st, R * (16.0 * W + 40.0 * N), R * 5.0 * W * H->logLx);
+                                                    H->kappa * H->kappa, nx, g_stride, y, mode);
+  prof_end(tk, PR_MV_ROWS_INV, st,
+           R * (16.0 * W + (mode == CONV_FIELD ? 16.0 : mode == CONV_TRANSPOSE ? 32.0 : 40.0) * N),
+           R * 5.0 * W * H->logLx);
   return check_launch("conv_apply");
 }
 
@@ -376,7 +391,8 @@ extern "C" int ls_matvec_noalloc(ls_handle* H, const void* xv, void* yv, int nrh
   LS_CUDA_TRY(cudaFuncSetAttribute(rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
   LS_CUDA_TRY(cudaFuncSetAttribute(rows_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
   count_launch();
-  rows_fwd_kernel<<<dim3(ny, nrhs), 256, smr, st>>>(x, nx, nx, g_stride, W, w_stride, H->Lx, H->logLx, H->tw_x);
+  rows_fwd_kernel<<<dim3(ny, nrhs), 256, smr, st>>>(x, nx, nx, g_stride, W, w_stride, H->Lx, H->logLx, H->tw_x,
+                                                    nullptr, 0.0);
   int C = cols_per_block(H->Ly);
   size_t smc = sizeof(z64) * ((size_t)H->Ly * C + H->Ly / 2);
   LS_CUDA_TRY(cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
@@ -385,6 +401,6 @@ extern "C" int ls_matvec_noalloc(ls_handle* H, const void* xv, void* yv, int nrh
                                                        H->spec, nx, ny, 0);
   count_launch();
   rows_inv_kernel<<<dim3(ny, nrhs), 256, smr, st>>>(W, w_stride, H->Lx, H->logLx, H->tw_x, x, H->b, H->kappa * H->kappa,
-                                                    nx, g_stride, y, 0);
+                                                    nx, g_stride, y, ls::CONV_FORWARD);
   return check_launch("ls_matvec_noalloc");
 }

@@ -1,6 +1,7 @@
 // Right-preconditioned GMRES on the device (Sec. 5): solve A sigma = f with
 // A = I + B (G + T) applied by the FFT convolution and M the HBS inverse, as
-// A M y = f, sigma = M y.  The preconditioned vectors z_j = M v_j are kept
+// A M y = f, sigma = M y; or the transposed system A^T sigma = f with M^T
+// (the adjoint solve of a misfit gradient).  The preconditioned vectors z_j = M v_j are kept
 // (flexible form, sigma = sum z_j y_j): an FP32 preconditioner is not exactly
 // linear in floating point, and re-applying it to V y at the end would leave
 // a residual at its rounding level.  Zero initial guess, no restart, classical
@@ -202,7 +203,8 @@ void norm2(const z64* x, long long N, z64* partial, z64* out, cudaStream_t st) {
   reduce_partials_kernel<<<1, 256, 0, st>>>(partial, kChunks, out, nullptr, 0);
 }
 
-int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, cudaStream_t st) {
+int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, int transpose, cudaStream_t st) {
+  const int mode = transpose ? CONV_TRANSPOSE : CONV_FORWARD;
   const long long N = (long long)H->grid.nx * H->grid.ny;
   const int m = H->opts.gmres_maxit;
   Ws ws = carve(H, N, m);
@@ -244,8 +246,8 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, cudaS
   for (int j = 0; j < m; ++j) {
     z64* vj = ws.V + (long long)j * N;
     z64* zj = ws.Z + (long long)j * N;
-    if ((rc = hbs_apply(H, vj, zj, 1, st))) return rc;
-    if ((rc = conv_apply(H, zj, ws.w, 1, false, st))) return rc;
+    if ((rc = hbs_apply(H, vj, zj, 1, transpose, st))) return rc;
+    if ((rc = conv_apply(H, zj, ws.w, 1, mode, st))) return rc;
     int tk = prof_begin(st);
     for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
       count_launch();
@@ -276,7 +278,7 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, cudaS
   count_launch();
   combine_kernel<<<nb, 256, 0, st>>>(ws.Z, N, k, ws.y, sigma, N);
   // true residual ||f - A sigma|| / ||f||
-  if ((rc = conv_apply(H, sigma, ws.w, 1, false, st))) return rc;
+  if ((rc = conv_apply(H, sigma, ws.w, 1, mode, st))) return rc;
   count_launch();
   sub_kernel<<<nb, 256, 0, st>>>(f, ws.w, ws.w, N);
   norm2(ws.w, N, ws.partial, ws.scal, st);
@@ -297,7 +299,8 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, cudaS
 
 }  // namespace
 
-int gmres_solve(ls_handle* H, const z64* f, z64* sigma, int nrhs, ls_solve_info* info, cudaStream_t st) {
+int gmres_solve(ls_handle* H, const z64* f, z64* sigma, int nrhs, ls_solve_info* info, int transpose,
+                cudaStream_t st) {
   const long long N = (long long)H->grid.nx * H->grid.ny;
   const int m = H->opts.gmres_maxit;
   size_t need = ws_bytes(N, m);
@@ -310,7 +313,7 @@ int gmres_solve(ls_handle* H, const z64* f, z64* sigma, int nrhs, ls_solve_info*
   }
   int worst = LS_OK;
   for (int r = 0; r < nrhs; ++r) {
-    int rc = solve_one(H, f + r * N, sigma + r * N, info ? info + r : nullptr, st);
+    int rc = solve_one(H, f + r * N, sigma + r * N, info ? info + r : nullptr, transpose, st);
     if (rc == LS_ENOCONV)
       worst = LS_ENOCONV;
     else if (rc)

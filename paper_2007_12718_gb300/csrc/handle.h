@@ -19,6 +19,8 @@ struct LevelData {
   void* S = nullptr;     // per node: k x k (levels >= 1)
   void* UT = nullptr;    // k x m: U transposed (the apply reads every product row-wise)
   void* GT = nullptr;    // k x k: Gsib transposed
+  void* XT = nullptr;    // per node: X transposed (made on the first transposed apply)
+  void* ST = nullptr;    // per node: S transposed (idem)
 };
 
 struct ls_handle {
@@ -55,9 +57,19 @@ struct ls_handle {
   void* apply_ops = nullptr;    // the apply as one persistent kernel: operation list (device)
   int apply_nops = 0, apply_phases = 0, apply_blocks = 0;
   unsigned* apply_bar = nullptr;     // its grid barrier: arrival counter and abort flag
-  unsigned long long apply_count = 0;  // applies launched (barrier epochs continue across them)
+  unsigned apply_epoch = 0;     // barrier arrivals so far (epochs continue across applies)
+  // the transposed apply (Algorithm 2 reversed): factors transposed, its operation list
+  void* XBUT = nullptr;         // per leaf k_L x s^2
+  void* apply_ops_t = nullptr;
+  int apply_nops_t = 0, apply_phases_t = 0;
+  std::vector<int> apply_phase_end_t;  // host copy: index of the last operation of each phase
   double flops_build = 0, flops_compress = 0, bytes_apply = 0, factor_bytes = 0;
   int pivot_fallbacks = 0;      // merge levels that needed the row-pivoted inverse
+
+  // receivers (Eq. (1)): positions (device, nr x 2) and R[k][j] = h^2 G(|r_k - x_j|)
+  double* rx = nullptr;
+  int nrec = 0;
+  ls::z64* Rrec = nullptr;      // nr x N complex128
 
   // GMRES workspace (Sec. 5)
   int gm_maxit = 0, gm_rhs = 0;
@@ -70,8 +82,10 @@ namespace ls {
 // conv.cu
 int kernel_table_setup(ls_handle* H, cudaStream_t st);
 int conv_setup(ls_handle* H, cudaStream_t st);
-// y = x + kappa^2 b .* (K * x)  (field_only: y = K * x)
-int conv_apply(ls_handle* H, const z64* x, z64* y, int nrhs, bool field_only, cudaStream_t st);
+// mode CONV_FORWARD: y = x + kappa^2 b .* (K * x) = A x;  CONV_TRANSPOSE:
+// y = x + K * (kappa^2 b .* x) = A^T x (K is complex symmetric);  CONV_FIELD: y = K * x.
+enum ConvMode { CONV_FORWARD = 0, CONV_TRANSPOSE = 1, CONV_FIELD = 2 };
+int conv_apply(ls_handle* H, const z64* x, z64* y, int nrhs, int mode, cudaStream_t st);
 
 // Build pipeline hooks: the compression reports each finished level (its U,
 // rank, skeleton and sibling block are in place and recorded on its stream);
@@ -98,7 +112,8 @@ int row_id(const z64* A, int m, int p, double eps, int precision, int nsm, int* 
 
 // build.cu (Algorithm 1) and apply (Algorithm 2)
 int hbs_build(ls_handle* H, cudaStream_t st, const LevelWait& wait_level = LevelWait());
-int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, cudaStream_t st);
+// q = M f, or q = M^T f when transpose (Algorithm 2 reversed, every factor transposed)
+int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, int transpose, cudaStream_t st);
 
 // tc_gemm.cu: complex FP32 GEMM on tcgen05 tensor cores (split: 0 tf32, 1 tf32x3)
 int tc_cgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, c32 alpha, const c32* A, int lda, long long sA,
@@ -106,9 +121,29 @@ int tc_cgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, c32 alpha, 
              int* err);
 int simt_cgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, c32 alpha, const c32* A, int lda, long long sA,
                const c32* B, int ldb, long long sB, c32 beta, c32* C, int ldc, long long sC, int batch);
+int simt_zgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, z64 alpha, const z64* A, int lda, long long sA,
+               const z64* B, int ldb, long long sB, z64 beta, z64* C, int ldc, long long sC, int batch);
+
+// adjoint.cu: u (nrhs x nr) = sigma R^T and g (nrhs x N) = v R with the handle's receivers
+int receiver_field(ls_handle* H, const z64* sigma, z64* u, int nrhs, cudaStream_t st);
+int receiver_adjoint(ls_handle* H, const z64* v, z64* g, int nrhs, cudaStream_t st);
 
 // gmres.cu
-int gmres_solve(ls_handle* H, const z64* f, z64* sigma, int nrhs, ls_solve_info* info, cudaStream_t st);
+int gmres_solve(ls_handle* H, const z64* f, z64* sigma, int nrhs, ls_solve_info* info, int transpose,
+                cudaStream_t st);
+
+// Host or device vectors at the C ABI: device pointers are used in place;
+// host vectors are staged through a device buffer (copied in on the stream,
+// copied out and synchronised by stage_out_finish).
+struct Staged {
+  z64* dev = nullptr;
+  bool owned = false;
+};
+bool is_device_pointer(const void* p);
+int stage_in(const void* p, size_t bytes, cudaStream_t st, Staged* s);
+int stage_out_alloc(void* p, size_t bytes, Staged* s);
+int stage_out_finish(void* p, size_t bytes, cudaStream_t st, Staged* s);
+void release(Staged* s);
 
 // Device allocation from the library's stream-ordered memory pool (one per
 // device, memory kept in the pool between calls), ordered on the stream of the

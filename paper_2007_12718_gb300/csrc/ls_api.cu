@@ -33,12 +33,32 @@ bool is_device_ptr(const void* p) {
 
 int valid_order(int o) { return o == 2 || o == 4 || o == 6 || o == 8 || o == 10; }
 
-// Staging of host vectors through device memory.
-struct Staged {
-  ls::z64* dev = nullptr;
-  bool owned = false;
-};
+__global__ void rhs_kernel(const double* b, int nx, int ny, double h, double x0, double y0, double kappa, double ct,
+                           double stt, ls::z64* f) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)nx * ny) return;
+  int i = (int)(t % nx), j = (int)(t / nx);
+  double x1 = x0 + (i + 0.5) * h, x2 = y0 + (j + 0.5) * h;
+  double sn, cs;
+  sincos(kappa * (x1 * ct + x2 * stt), &sn, &cs);
+  double a = -kappa * kappa * b[t];
+  f[t] = ls::mk<double>(a * cs, a * sn);
+}
 
+__global__ void check_b_kernel(const double* b, long long n, int* bad) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  double v = b[t];
+  if (!(v <= 1.0) || !isfinite(v)) atomicExch(bad, 1);
+}
+
+}  // namespace
+
+namespace ls {
+
+bool is_device_pointer(const void* p) { return is_device_ptr(p); }
+
+// Staging of host vectors through device memory.
 int stage_in(const void* p, size_t bytes, cudaStream_t st, Staged* s) {
   if (is_device_ptr(p)) {
     s->dev = (ls::z64*)p;
@@ -78,26 +98,13 @@ void release(Staged* s) {
   s->owned = false;
 }
 
-__global__ void rhs_kernel(const double* b, int nx, int ny, double h, double x0, double y0, double kappa, double ct,
-                           double stt, ls::z64* f) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)nx * ny) return;
-  int i = (int)(t % nx), j = (int)(t / nx);
-  double x1 = x0 + (i + 0.5) * h, x2 = y0 + (j + 0.5) * h;
-  double sn, cs;
-  sincos(kappa * (x1 * ct + x2 * stt), &sn, &cs);
-  double a = -kappa * kappa * b[t];
-  f[t] = ls::mk<double>(a * cs, a * sn);
-}
+}  // namespace ls
 
-__global__ void check_b_kernel(const double* b, long long n, int* bad) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  double v = b[t];
-  if (!(v <= 1.0) || !isfinite(v)) atomicExch(bad, 1);
-}
-
-}  // namespace
+using ls::release;
+using ls::stage_in;
+using ls::stage_out_alloc;
+using ls::stage_out_finish;
+using ls::Staged;
 
 void ls_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
   char buf[512];
@@ -339,9 +346,13 @@ void ls_free(ls_handle* H) {
     f(lv.S);
     f(lv.UT);
     f(lv.GT);
+    f(lv.XT);
+    f(lv.ST);
   }
   f(H->Gleaf);
   f(H->XBU);
+  f(H->XBUT);
+  f(H->apply_ops_t);
   f(H->work);
   f(H->sync_buf);
   f(H->d_err);
@@ -349,6 +360,8 @@ void ls_free(ls_handle* H) {
   f(H->slots);
   f(H->apply_ops);
   f(H->apply_bar);
+  f(H->rx);
+  f(H->Rrec);
   if (H->apply_exec) cudaGraphExecDestroy(H->apply_exec);
   delete H;
 }
@@ -558,8 +571,7 @@ int ls_build(const ls_grid* grid, double kappa, const double* b, double tol, con
   return LS_OK;
 }
 
-int ls_matvec(ls_handle* H, const void* x, void* y, int nrhs, int transpose, void* stream) {
-  if (!H || !x || !y || nrhs < 1 || transpose != 0) return LS_EINVAL;
+static int conv_entry(ls_handle* H, const void* x, void* y, int nrhs, int mode, void* stream) {
   ls::StreamScope scope((cudaStream_t)stream);
   H->stream = (cudaStream_t)stream;
   cudaStream_t st = (cudaStream_t)stream;
@@ -567,7 +579,7 @@ int ls_matvec(ls_handle* H, const void* x, void* y, int nrhs, int transpose, voi
   Staged sx, sy;
   int rc = stage_in(x, bytes, st, &sx);
   if (!rc) rc = stage_out_alloc(y, bytes, &sy);
-  if (!rc) rc = ls::conv_apply(H, sx.dev, sy.dev, nrhs, false, st);
+  if (!rc) rc = ls::conv_apply(H, sx.dev, sy.dev, nrhs, mode, st);
   if (!rc) rc = stage_out_finish(y, bytes, st, &sy);
   if (sx.owned || sy.owned) cudaStreamSynchronize(st);
   release(&sx);
@@ -575,8 +587,18 @@ int ls_matvec(ls_handle* H, const void* x, void* y, int nrhs, int transpose, voi
   return rc;
 }
 
+int ls_matvec(ls_handle* H, const void* x, void* y, int nrhs, int transpose, void* stream) {
+  if (!H || !x || !y || nrhs < 1 || (transpose != 0 && transpose != 1)) return LS_EINVAL;
+  return conv_entry(H, x, y, nrhs, transpose ? ls::CONV_TRANSPOSE : ls::CONV_FORWARD, stream);
+}
+
+int ls_field(ls_handle* H, const void* sigma, void* u, int nrhs, void* stream) {
+  if (!H || !sigma || !u || nrhs < 1) return LS_EINVAL;
+  return conv_entry(H, sigma, u, nrhs, ls::CONV_FIELD, stream);
+}
+
 int ls_apply(ls_handle* H, const void* f, void* q, int nrhs, int transpose, void* stream) {
-  if (!H || !f || !q || nrhs < 1 || transpose != 0) return LS_EINVAL;
+  if (!H || !f || !q || nrhs < 1 || (transpose != 0 && transpose != 1)) return LS_EINVAL;
   ls::StreamScope scope((cudaStream_t)stream);
   H->stream = (cudaStream_t)stream;
   cudaStream_t st = (cudaStream_t)stream;
@@ -584,7 +606,7 @@ int ls_apply(ls_handle* H, const void* f, void* q, int nrhs, int transpose, void
   Staged sf, sq;
   int rc = stage_in(f, bytes, st, &sf);
   if (!rc) rc = stage_out_alloc(q, bytes, &sq);
-  if (!rc) rc = ls::hbs_apply(H, sf.dev, sq.dev, nrhs, st);
+  if (!rc) rc = ls::hbs_apply(H, sf.dev, sq.dev, nrhs, transpose, st);
   if (!rc) rc = stage_out_finish(q, bytes, st, &sq);
   if (sf.owned || sq.owned) cudaStreamSynchronize(st);
   release(&sf);
@@ -592,7 +614,8 @@ int ls_apply(ls_handle* H, const void* f, void* q, int nrhs, int transpose, void
   return rc;
 }
 
-int ls_solve(ls_handle* H, const void* f, void* sigma, int nrhs, ls_solve_info* info, void* stream) {
+static int solve_entry(ls_handle* H, const void* f, void* sigma, int nrhs, ls_solve_info* info, int transpose,
+                       void* stream) {
   if (!H || !f || !sigma || nrhs < 1) return LS_EINVAL;
   ls::StreamScope scope((cudaStream_t)stream);
   H->stream = (cudaStream_t)stream;
@@ -603,7 +626,7 @@ int ls_solve(ls_handle* H, const void* f, void* sigma, int nrhs, ls_solve_info* 
   if (!rc) rc = stage_out_alloc(sigma, bytes, &ss);
   int solve_rc = LS_OK;
   if (!rc) {
-    solve_rc = ls::gmres_solve(H, sf.dev, ss.dev, nrhs, info, st);
+    solve_rc = ls::gmres_solve(H, sf.dev, ss.dev, nrhs, info, transpose, st);
     if (solve_rc != LS_OK && solve_rc != LS_ENOCONV) rc = solve_rc;
   }
   if (!rc) rc = stage_out_finish(sigma, bytes, st, &ss);
@@ -611,6 +634,14 @@ int ls_solve(ls_handle* H, const void* f, void* sigma, int nrhs, ls_solve_info* 
   release(&sf);
   release(&ss);
   return rc ? rc : solve_rc;
+}
+
+int ls_solve(ls_handle* H, const void* f, void* sigma, int nrhs, ls_solve_info* info, void* stream) {
+  return solve_entry(H, f, sigma, nrhs, info, 0, stream);
+}
+
+int ls_solve_transpose(ls_handle* H, const void* f, void* sigma, int nrhs, ls_solve_info* info, void* stream) {
+  return solve_entry(H, f, sigma, nrhs, info, 1, stream);
 }
 
 int ls_rhs_plane_wave(ls_handle* H, const double* thetas, void* f, int nrhs, void* stream) {
