@@ -157,6 +157,61 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------- adjoint leg
+ADJ_TEXT = ("512x512 grid, kappa=300, b = seed-0 Gaussian family, 32 plane waves theta_j = 2 pi j/32, "
+            "256 receivers on the circle r=1.5 about (0.5,0.5), data = receiver field of the seed-1 potential; "
+            "one step = ls_build + ls_set_receivers + ls_misfit_gradient (32 forward + 32 adjoint GMRES solves "
+            "to 1e-10, receiver fields, gradient) + ls_free")
+
+
+def adjoint_leg(ls, torch, dev, precision):
+    """The differentiation workload: J(b) and dJ/db through the C ABI, timed with
+    CUDA events on the current stream after one warm-up step (inputs resident)."""
+    from paper_2007_12718_gb300 import inputs
+    n, kappa, ndir, nrec = 512, 300.0, 32, 256
+    h = 1.0 / n
+    thetas = inputs.plane_wave_angles(ndir)
+    rec = inputs.receivers_circle(nrec)
+    b0 = torch.from_numpy(inputs.gaussian_family(n, 0)).to(dev)
+    b1 = torch.from_numpy(inputs.gaussian_family(n, 1)).to(dev)
+    H = ls.ls_build(n, h, kappa, b1, 1e-4, precision=precision)
+    f = torch.zeros(ndir, n, n, dtype=torch.complex128, device=dev)
+    ls.ls_rhs_plane_wave(H, thetas, f)
+    sig = torch.zeros_like(f)
+    ls.ls_solve(H, f, sig)
+    ls.ls_set_receivers(H, rec)
+    data = torch.zeros(ndir, nrec, dtype=torch.complex128, device=dev)
+    ls.ls_receiver_field(H, sig, data)
+    ls.ls_free(H)
+    del f, sig
+    grad = torch.zeros(n, n, dtype=torch.float64, device=dev)
+
+    def step():
+        Hs = ls.ls_build(n, h, kappa, b0, 1e-4, precision=precision)
+        ls.ls_set_receivers(Hs, rec)
+        out = ls.ls_misfit_gradient(Hs, thetas, data, grad)
+        ls.ls_free(Hs)
+        return out
+
+    step()
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    J, infos = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    fw = [i["iterations"] for i in infos[:ndir]]
+    ad = [i["iterations"] for i in infos[ndir:]]
+    return {"workload": "differentiation_n512", "description": ADJ_TEXT, "ms_per_gradient": ms,
+            "value": ndir * n * n / (ms * 1e-3) / 1e6, "unit": "Mdof/s (directions x dofs, forward + adjoint)",
+            "J": J, "gmres_iterations_forward_mean": float(np.mean(fw)),
+            "gmres_iterations_adjoint_mean": float(np.mean(ad)),
+            "converged": bool(all(i["converged"] for i in infos))}
+
+
 # ----------------------------------------------------------------------- ours
 def run_ours(args, rank, world):
     import torch
@@ -283,6 +338,7 @@ def run_ours(args, rank, world):
     roof = kernels[top]
     breakdown = {k: round(v["total_ms"] / args.steps, 4) for k, v in prof.items() if v["launches"]}
 
+    adj = adjoint_leg(ls, torch, dev, PREC) if not args.no_adjoint else None
     cpu = cpu_baseline(n, kappa, b) if not args.no_cpu_baseline else None
     line = {"metric": METRIC, "value": value, "unit": "Mdof/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_mixed / args.steps * 1e3, "higher_is_better": True,
@@ -300,7 +356,7 @@ def run_ours(args, rank, world):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e, "unit": "Mdof/s", "h2d_bytes_per_step": N * 8 + N * 16,
                     "d2h_bytes_per_step": N * 16},
-            "gpu_launches": launches, "clocks": clk.summary()}
+            "gpu_launches": launches, "clocks": clk.summary(), "adjoint": adj}
     print(json.dumps(line), flush=True)
 
 
@@ -311,6 +367,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the differentiation workload (512x512 misfit gradient) reported under 'adjoint'")
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32", "tf32x3"],
                     help="engine of the mixed path's merge GEMMs (FP32 storage in all three)")
     ap.add_argument("--top-uncompressed", type=int, default=1,

@@ -1648,6 +1648,8 @@ __device__ __forceinline__ void apply_rows(const ApplyOp& op, long long gw, long
     const int b = (int)(rc / op.M), i = (int)(rc % op.M);
     const cx<R>* a = A + b * op.sA + (long long)i * op.lda;
     const cx<R>* xv = X + b * op.sx;
+    // the addend is read before the dot product so that its latency overlaps it
+    const cx<R> y0v = (Y0 && ok && li == 0) ? ldcg_cx(Y0 + b * op.sy0 + i) : mk<R>(0, 0);
     cx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0), acc2 = mk<R>(0, 0), acc3 = mk<R>(0, 0);
     int j = li;
     if (ok) {
@@ -1665,19 +1667,28 @@ __device__ __forceinline__ void apply_rows(const ApplyOp& op, long long gw, long
     cx<R> v = (acc0 + acc1) + (acc2 + acc3);
 #pragma unroll
     for (int o = GS / 2; o; o >>= 1) v = v + shfl_xor(v, o);
-    if (li == 0 && ok) {
-      cx<R> out = alpha * v;
-      if (Y0) out = out + ldcg_cx(Y0 + b * op.sy0 + i);
-      Y[b * op.sy + i] = out;
-    }
+    if (li == 0 && ok) Y[b * op.sy + i] = alpha * v + y0v;
   }
 }
 
+// The operation list is copied to shared memory once per launch (dynamic
+// shared memory, nops entries), so that each operation's descriptor is a
+// shared-memory read rather than a global load on the critical path.
 template <class R>
-__global__ void __launch_bounds__(1024) apply_persistent_kernel(const ApplyOp* __restrict__ ops, int nops, TreeGeom g,
-                                                                const z64* __restrict__ f, z64* __restrict__ q,
-                                                                unsigned* bar, unsigned epoch0, int* err) {
+__global__ void __launch_bounds__(1024) apply_persistent_kernel(const ApplyOp* __restrict__ ops_g, int nops,
+                                                                TreeGeom g, const z64* __restrict__ f,
+                                                                z64* __restrict__ q, unsigned* bar, unsigned epoch0,
+                                                                int* err) {
   __shared__ int s_ok;
+  extern __shared__ unsigned char smraw[];
+  ApplyOp* ops = reinterpret_cast<ApplyOp*>(smraw);
+  {
+    const int words = nops * (int)(sizeof(ApplyOp) / sizeof(int));
+    const int* src = reinterpret_cast<const int*>(ops_g);
+    int* dst = reinterpret_cast<int*>(smraw);
+    for (int t = threadIdx.x; t < words; t += blockDim.x) dst[t] = src[t];
+  }
+  __syncthreads();
   const int wpb = blockDim.x >> 5;
   const long long nwarps = (long long)gridDim.x * wpb, nthreads = (long long)gridDim.x * blockDim.x;
   const long long gw = (long long)blockIdx.x * wpb + (threadIdx.x >> 5);
@@ -1955,7 +1966,15 @@ std::vector<int> phase_ends(const std::vector<ApplyOp>& ops) {
 }
 
 int upload_ops(std::vector<ApplyOp>& ops, void** dst, cudaStream_t st) {
-  for (auto& o : ops) o.rb = o.K <= 64 ? 8 : o.K <= 160 ? 16 : 32;
+  for (auto& o : ops) {
+    o.rb = o.K <= 64 ? 8 : o.K <= 160 ? 16 : 32;
+    const bool ok = o.type == 0 ? (o.M * (long long)o.batch == 0 || (o.y && (o.K == 0 || (o.A && o.x))))
+                                : o.type == 1 ? o.y != nullptr : o.x != nullptr;
+    if (!ok) {  // a factor or buffer the list names was never made
+      set_last_error_text("apply operation list refers to a missing buffer");
+      return LS_EINVAL;
+    }
+  }
   int rc;
   if ((rc = dalloc(dst, sizeof(ApplyOp) * ops.size()))) return rc;
   LS_CUDA_TRY(cudaMemcpyAsync(*dst, ops.data(), sizeof(ApplyOp) * ops.size(), cudaMemcpyHostToDevice, st));
@@ -1966,19 +1985,30 @@ int upload_ops(std::vector<ApplyOp>& ops, void** dst, cudaStream_t st) {
 // Prepares the persistent apply (transposed U and G, the operation list, the
 // barrier); returns LS_OK without preparing it if a cooperative grid of one
 // 1024-thread block per SM cannot be co-resident (the graph path is used then).
+// Dynamic shared memory of the persistent apply for an operation list of nops
+// entries (the attribute is raised as needed).
+size_t apply_smem(const void* kfn, int nops) {
+  const size_t bytes = sizeof(ApplyOp) * (size_t)nops;
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return bytes;
+}
+
 int apply_persistent_init(ls_handle* H, cudaStream_t st) {
   if (H->apply_ops || H->apply_blocks < 0) return LS_OK;
   const void* kfn = H->prec == LS_FP64 ? (const void*)apply_persistent_kernel<double>
                                        : (const void*)apply_persistent_kernel<float>;
+  int rc;
+  if ((rc = level_transposes(H, st))) return rc;  // the operation list reads U^T and G^T
+  std::vector<ApplyOp> ops = H->prec == LS_FP64 ? apply_ops<double>(H) : apply_ops<float>(H);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 1024, 0) != cudaSuccess || per_sm < 1) {
+  if (sizeof(ApplyOp) * ops.size() > 200 * 1024 ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 1024, apply_smem(kfn, (int)ops.size())) !=
+          cudaSuccess ||
+      per_sm < 1) {
     cudaGetLastError();
     H->apply_blocks = -1;  // not co-resident: graph path (forward), one launch per phase (transposed)
     return LS_OK;
   }
-  int rc;
-  if ((rc = level_transposes(H, st))) return rc;
-  std::vector<ApplyOp> ops = H->prec == LS_FP64 ? apply_ops<double>(H) : apply_ops<float>(H);
   if ((rc = upload_ops(ops, &H->apply_ops, st))) return rc;
   if (!H->apply_bar) {
     if ((rc = dalloc((void**)&H->apply_bar, 2 * sizeof(unsigned)))) return rc;
@@ -2017,6 +2047,10 @@ int apply_transpose_init(ls_handle* H, cudaStream_t st) {
   if ((rc = dalloc(&H->XBUT, es * ((size_t)1 << L) * n * std::max(kL, 1)))) return rc;
   if ((rc = transpose_batch(fp64, H->XBU, n, kL, 1 << L, H->XBUT, st))) return rc;
   std::vector<ApplyOp> ops = fp64 ? apply_ops_transpose<double>(H) : apply_ops_transpose<float>(H);
+  if (sizeof(ApplyOp) * ops.size() > 200 * 1024) {
+    set_last_error_text("tree too deep for the transposed apply");
+    return LS_EINVAL;
+  }
   if ((rc = upload_ops(ops, &H->apply_ops_t, st))) return rc;
   if (!H->apply_bar) {
     if ((rc = dalloc((void**)&H->apply_bar, 2 * sizeof(unsigned)))) return rc;
@@ -2100,7 +2134,8 @@ int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, int transpose, cudaS
         unsigned epoch0 = H->apply_epoch;
         void* args[] = {&ops, &nops, (void*)&g, &fr, &qr, &bar, &epoch0, &err};
         count_launch();
-        LS_CUDA_TRY(cudaLaunchCooperativeKernel(kfn, dim3(H->apply_blocks), dim3(1024), args, 0, st));
+        LS_CUDA_TRY(
+            cudaLaunchCooperativeKernel(kfn, dim3(H->apply_blocks), dim3(1024), args, apply_smem(kfn, nops), st));
         H->apply_epoch += (unsigned)(H->apply_phases_t - 1) * (unsigned)H->apply_blocks;
       } else {  // one launch per phase (no barrier is reached inside a launch)
         int start = 0;
@@ -2110,7 +2145,7 @@ int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, int transpose, cudaS
           unsigned epoch0 = 0;
           void* args[] = {&ops, &nops, (void*)&g, &fr, &qr, &bar, &epoch0, &err};
           count_launch();
-          LS_CUDA_TRY(cudaLaunchKernel(kfn, dim3(H->nsm), dim3(1024), args, 0, st));
+          LS_CUDA_TRY(cudaLaunchKernel(kfn, dim3(H->nsm), dim3(1024), args, apply_smem(kfn, nops), st));
           start = e + 1;
         }
       }
@@ -2134,7 +2169,8 @@ int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, int transpose, cudaS
       int* err = H->d_err;
       void* args[] = {&ops, &nops, (void*)&g, &fr, &qr, &bar, &epoch0, &err};
       count_launch();
-      LS_CUDA_TRY(cudaLaunchCooperativeKernel(kfn, dim3(H->apply_blocks), dim3(1024), args, 0, st));
+      LS_CUDA_TRY(
+          cudaLaunchCooperativeKernel(kfn, dim3(H->apply_blocks), dim3(1024), args, apply_smem(kfn, nops), st));
       H->apply_epoch += (unsigned)(H->apply_phases - 1) * (unsigned)H->apply_blocks;
       prof_end(tk, PR_APPLY, st, H->bytes_apply, 0.0);
     }

@@ -509,6 +509,75 @@ __device__ __forceinline__ void id_back_substitution(const cx<R>* Rm, const cx<R
   __syncwarp();
 }
 
+// U rows of the ID by a blocked back substitution: U(c, :) = (R11^-1 R(:, c))^T
+// for a candidate c that is not a pivot, e_sel(c) for a pivot (Sec. 2.1, the
+// interpolation matrix T = R11^-1 R12).  One warp per candidate, CB candidates
+// per block; the right-hand sides (column c of R, k entries) live in shared
+// memory.  Panels of kTrsmNB rows are taken from the bottom: the panel's
+// diagonal block (read from RT = R11^T, so a row of RT is a column of R11) is
+// staged in shared memory and each warp solves its candidate's panel rows with
+// warp-synchronous steps (one lane per row); then the block updates the rows
+// above the panel with the panel's solved unknowns, reading kTrsmNB rows of RT
+// (coalesced).  k is read on the device (rank[0]).
+constexpr int kTrsmNB = 32;
+template <class R, int CB>
+__global__ void __launch_bounds__(32 * CB) id_trsm_kernel(const cx<R>* __restrict__ Rm, const cx<R>* __restrict__ RT,
+                                                          const int* __restrict__ sel, const int* __restrict__ rank,
+                                                          int m, int kmax, cx<R>* __restrict__ U) {
+  extern __shared__ unsigned char smraw[];
+  cx<R>* tv = reinterpret_cast<cx<R>*>(smraw);  // CB x kmax
+  cx<R>* D = tv + (size_t)CB * kmax;             // kTrsmNB x kTrsmNB: D[q][r] = R11(i0 + r, i0 + q), r <= q
+  const int k = min(*rank, kmax);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int c = blockIdx.x * CB + warp;
+  const bool own = c < m;
+  const int sc = own ? sel[c] : 0;
+  const bool solve = own && sc < 0;
+  cx<R>* t = tv + (size_t)warp * kmax;
+  for (int a = lane; a < k; a += 32) t[a] = solve ? ldcg_cx(Rm + (long long)a * m + c) : mk<R>(0, 0);
+  __syncthreads();
+  for (int i1 = k; i1 > 0; i1 -= kTrsmNB) {
+    const int i0 = max(0, i1 - kTrsmNB), w = i1 - i0;
+    for (int e = tid; e < w * w; e += 32 * CB) {
+      const int q = e / w, r = e % w;
+      D[q * kTrsmNB + r] = r <= q ? ldcg_cx(RT + (long long)(i0 + q) * k + i0 + r) : mk<R>(0, 0);
+    }
+    __syncthreads();
+    if (solve) {  // rows i1 - 1 .. i0 of this candidate; lane r holds row i0 + r
+      cx<R> x = lane < w ? t[i0 + lane] : mk<R>(0, 0);
+      for (int q = w - 1; q >= 0; --q) {
+        const cx<R> xq = mk<R>(__shfl_sync(0xffffffffu, x.re, q), __shfl_sync(0xffffffffu, x.im, q));
+        const cx<R> tq = xq * inv(D[q * kTrsmNB + q]);
+        if (lane == q) x = tq;
+        if (lane < q) {
+          const cx<R> r = D[q * kTrsmNB + lane];
+          x.re -= r.re * tq.re - r.im * tq.im;
+          x.im -= r.re * tq.im + r.im * tq.re;
+        }
+      }
+      if (lane < w) t[i0 + lane] = x;
+    }
+    __syncthreads();
+    // rows above the panel: t[b] -= sum_{a in panel} R11(b, a) t[a] = RT[a][b] t[a]
+    for (int b = tid; b < i0; b += 32 * CB) {
+      cx<R> acc[CB];
+#pragma unroll
+      for (int j = 0; j < CB; ++j) acc[j] = mk<R>(0, 0);
+      for (int a = i0; a < i1; ++a) {
+        const cx<R> r = ldcg_cx(RT + (long long)a * k + b);
+#pragma unroll
+        for (int j = 0; j < CB; ++j) fma_(acc[j], r, tv[(size_t)j * kmax + a]);
+      }
+#pragma unroll
+      for (int j = 0; j < CB; ++j) tv[(size_t)j * kmax + b] = tv[(size_t)j * kmax + b] - acc[j];
+    }
+    __syncthreads();
+  }
+  if (own)
+    for (int a = lane; a < k; a += 32)
+      U[(long long)c * k + a] = solve ? t[a] : mk<R>(a == sc ? R(1) : R(0), R(0));
+}
+
 // Cluster version: CL <= 16 blocks of 1024 threads, at most 32 candidates per
 // block (block r owns candidates [r per, r per + per)), p <= 32 T.  Each warp
 // keeps its candidate's key (0 once the candidate is a pivot) in a per-warp
@@ -644,8 +713,7 @@ __global__ void __launch_bounds__(1024) cpqr_reg_cluster_kernel(const cx<R>* __r
     int aa = (int)(t / k), bb = (int)(t % k);
     RT[t] = bb <= aa ? ldcg_cx(Rm + (long long)bb * m + __ldcg(piv + aa)) : mk<R>(0, 0);
   }
-  cluster.sync();
-  if (own) id_back_substitution(Rm, RT, m, k, c, rsel, lane, reinterpret_cast<cx<R>*>(smraw) + (long long)warp * kmax, U);
+  // U follows from RT and R in id_trsm_kernel
 }
 
 // Per-step exchange record of the grid ID kernel.  word: bits 52..63 count the
@@ -884,8 +952,7 @@ __global__ void __launch_bounds__(1024) cpqr_reg_grid_kernel(const cx<R>* __rest
     int aa = (int)(t / k), bb = (int)(t % k);
     RT[t] = bb <= aa ? ldcg_cx(Rm + (long long)bb * m + __ldcg(piv + aa)) : mk<R>(0, 0);
   }
-  if (!grid_sync(gs, nblk, epoch)) return;
-  if (own && part == 0) id_back_substitution(Rm, RT, m, k, c, rsel, lane, pvec + (long long)cand * kmax, U);
+  // U follows from RT and R in id_trsm_kernel
 }
 
 template <class R>
@@ -1108,6 +1175,12 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
     LS_CUDA_TRY(cudaLaunchCooperativeKernel(kreg, dim3(nblk_r), dim3(128 * cpb), args, smem_r, st));
   }
   if (reg_mode) {
+    constexpr int CB = 4;
+    const size_t smt = sizeof(cx<R>) * ((size_t)CB * kmax + (size_t)kTrsmNB * kTrsmNB);
+    if (smt > 48 * 1024)
+      LS_CUDA_TRY(cudaFuncSetAttribute(id_trsm_kernel<R, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt));
+    count_launch();
+    id_trsm_kernel<R, CB><<<(unsigned)((m + CB - 1) / CB), 32 * CB, smt, st>>>(Rm, RT, sel, rank, m, kmax, Ut);
   } else if (use_cluster) {
     count_launch();
     LS_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpqr_id_cluster_kernel<R>, (const cx<R>*)A, m, p, kmax, eps, Rm, sel, piv,
