@@ -716,6 +716,10 @@ __global__ void __launch_bounds__(1024) cpqr_reg_cluster_kernel(const cx<R>* __r
   // U follows from RT and R in id_trsm_kernel
 }
 
+// Dynamic shared memory the grid ID kernel asks for at least: with it no block
+// of the merge kernels (>= 8 KB of shared memory each) fits on the same SM.
+constexpr size_t kIdSmemReserve = 220 * 1024;
+
 // Per-step exchange record of the grid ID kernel.  word: bits 52..63 count the
 // blocks that have arrived, bits 0..51 hold the sum of their residual totals in
 // fixed point, unit = (eps^2 total_0) 2^-20 (the stopping threshold is 2^20
@@ -1097,8 +1101,15 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
   const int tneed = (p + 31) / 32;
   const int t_cl_max = sizeof(R) == 4 ? 20 : 8;
   int reg_mode = 0;  // 1 cluster, 2 grid
-  // grid kernel: spread the candidates over all SMs (cpb per block, four warps each)
-  const int cpb = std::min(8, std::max(1, (m + nsm - 1) / nsm));
+  // grid kernel: spread the candidates over two thirds of the SMs (cpb per block,
+  // four warps each).  The build runs the merges of lower levels beside the ID;
+  // a merge block placed on an SM of this latency-bound kernel runs many times
+  // slower and holds up its whole launch, so the kernel also takes nearly all of
+  // its SMs' shared memory (no merge kernel fits beside it) and leaves the other
+  // third of the SMs to the merges.  Measured cost on the ID: ~5 % at 760
+  // candidates against a spread over every SM.
+  const int nsm_id = std::max(1, nsm - nsm / 3);
+  const int cpb = std::min(8, std::max(1, (m + nsm_id - 1) / nsm_id));
   int treg = 0, clr = (m + 31) / 32, nblk_r = (m + cpb - 1) / cpb;
   const void* kreg = nullptr;
   size_t smem_r = 0;
@@ -1124,7 +1135,7 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
            : treg == 12 ? (const void*)cpqr_reg_grid_kernel<R, 12> : (const void*)cpqr_reg_grid_kernel<R, 16>;
     else
       kreg = treg == 4 ? (const void*)cpqr_reg_grid_kernel<R, 4> : (const void*)cpqr_reg_grid_kernel<R, 8>;
-    smem_r = sizeof(cx<R>) * std::max((size_t)p, (size_t)cpb * kmax);
+    smem_r = std::max(sizeof(cx<R>) * std::max((size_t)p, (size_t)cpb * kmax), (size_t)kIdSmemReserve);
     int per_sm = 0;
     if (smem_r <= 220 * 1024 && nblk_r <= nsm &&
         cudaFuncSetAttribute(kreg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_r) == cudaSuccess &&
