@@ -1111,20 +1111,22 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
     H->flops_build += fl;
   }
 
-  // merges, level by level
+  // merges, level by level.  X of level l needs the children's S and sibling
+  // block (compression of level l + 1, already waited for); only S of level l
+  // needs this level's U, so the wait for compression level l sits before it
+  // and X of level l is formed while level l is being compressed.
   for (int l = L - 1; l >= 0; --l) {
-    if (wait_level && (rc = wait_level(std::max(l, 1)))) return rc;
     if ((rc = sibling_block(H, l + 1, st))) return rc;  // G of the two children (Eq. 15)
     LevelData& lv = H->lev[l];
     const LevelData& ch = H->lev[l + 1];
     const int P = 1 << l, kc = ch.k, n2 = 2 * kc;
-    // this level's scratch: the largest of (pivoted-inverse panels + pivots), the
-    // S products, and Y1, Y2, a copy of Z with the blocked-inverse panels (width <= 128)
+    // scratch of X: the larger of (pivoted-inverse panels + pivots) and Y1, Y2, a
+    // copy of Z with the blocked-inverse panels (width <= 128); the S products get
+    // their own once this level's rank is known
     size_t work_bytes;
     {
-      const size_t Pz = (size_t)P, kz = (size_t)kc, nz = (size_t)n2, kpz = l > 0 ? (size_t)lv.k : 0;
+      const size_t Pz = (size_t)P, kz = (size_t)kc, nz = (size_t)n2;
       work_bytes = sizeof(cx<R>) * Pz * nz * nz + sizeof(int) * Pz * nz;
-      work_bytes = std::max(work_bytes, sizeof(cx<R>) * 2 * Pz * nz * kpz);
       work_bytes = std::max(work_bytes, sizeof(cx<R>) * Pz * (3 * kz * kz + 128 * 128 + 3 * 128 * kz) +
                                             sizeof(int) * Pz * (nz + 256) + 4096);
     }
@@ -1221,12 +1223,16 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
     }
     H->flops_build += P * (6.0 * 8 * (double)kc * kc * kc + 8.0 * (double)kc * kc * kc);
     if (l == 0) break;
+    if (wait_level && (rc = wait_level(l))) return rc;
     const int kp = lv.k;
     if ((rc = dalloc(&lv.S, sizeof(cx<R>) * (size_t)P * std::max(kp * kp, 1)))) return rc;
     H->factor_bytes += sizeof(cx<R>) * (double)P * kp * kp;
     if (kp == 0 || kc == 0) continue;
+    void* work_s = nullptr;
+    if ((rc = dalloc(&work_s, sizeof(cx<R>) * 2 * (size_t)P * n2 * kp))) return rc;
+    FreeOnExit free_work_s{work_s};
     const cx<R>* U = reinterpret_cast<const cx<R>*>(lv.U);  // n2 x kp
-    cx<R>* D = reinterpret_cast<cx<R>*>(work);             // P x n2 x kp
+    cx<R>* D = reinterpret_cast<cx<R>*>(work_s);           // P x n2 x kp
     cx<R>* E = D + (size_t)P * n2 * kp;
     // D = [S_a U_top ; S_b U_bot]
     int ts = prof_begin(st);
