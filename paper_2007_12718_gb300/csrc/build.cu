@@ -1600,6 +1600,8 @@ int apply_core(ls_handle* H, z64** slots, cudaStream_t st) {
 // products use the U^T and G^T copies made once per handle.
 struct ApplyOp {
   int type;        // 0: y[b] = y0[b] + alpha A[b] x[b];  1: gather leaves (y <- f);  2: scatter leaves (q <- x)
+                   // 3: leaves up (r = X f -> y0, r~ = U^T r -> y; A = X, x = U^T)
+                   // 4: leaves down (q = y0 + alpha A x scattered to the grid; A = X B U, x = w~)
   int M, K, lda, batch;
   int phase_end;   // a grid barrier follows this operation
   int rb;          // lanes per row (8, 16 or 32): short rows share a warp
@@ -1677,6 +1679,89 @@ __device__ __forceinline__ void apply_rows(const ApplyOp& op, long long gw, long
   }
 }
 
+// Leaf operations of the persistent apply: four warps (a 128-thread group,
+// named barrier 1 + group) take one leaf at a time, the leaf's vectors in
+// shared memory, so that Algorithm 2's three leaf steps of each pass need no
+// grid barrier between them.  Rows of a product are dot products over groups
+// of GS lanes (8 for rows of <= 64 entries, 16 up to 128, else 32).
+template <class R, class F>
+__device__ __forceinline__ void group_rows(const cx<R>* __restrict__ A, int lda, const cx<R>* xs, int rows, int cols,
+                                           int gt, F out) {
+  const int GS = cols <= 64 ? 8 : cols <= 128 ? 16 : 32;
+  const int rpp = 128 / GS, li = gt % GS;
+  for (int r0 = 0; r0 < rows; r0 += rpp) {
+    const int r = r0 + gt / GS;
+    cx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0);
+    if (r < rows) {
+      const cx<R>* a = A + (long long)r * lda;
+      int j = li;
+      for (; j + GS < cols; j += 2 * GS) {
+        fma_(acc0, a[j], xs[j]);
+        fma_(acc1, a[j + GS], xs[j + GS]);
+      }
+      if (j < cols) fma_(acc0, a[j], xs[j]);
+    }
+    cx<R> v = acc0 + acc1;
+    for (int o = GS / 2; o; o >>= 1) v = v + shfl_xor(v, o);
+    if (li == 0 && r < rows) out(r, v);
+  }
+}
+
+// type 3: for each leaf, r = X f (kept in op.y0 for the last step), r~ = U^T r.
+template <class R>
+__device__ __forceinline__ void apply_leaf_up(const ApplyOp& op, const TreeGeom& g, const z64* __restrict__ f,
+                                              cx<R>* gs_mem) {
+  const int n = g.s * g.s, kL = op.M;
+  const int grp = threadIdx.x >> 7, gt = threadIdx.x & 127, ngrp = blockDim.x >> 7;
+  const unsigned bar = 1 + grp;
+  cx<R>* fs = gs_mem + (size_t)grp * 2 * n;
+  cx<R>* rs = fs + n;
+  const cx<R>* X = reinterpret_cast<const cx<R>*>(op.A);
+  const cx<R>* UT = reinterpret_cast<const cx<R>*>(op.x);
+  cx<R>* Rl = reinterpret_cast<cx<R>*>(const_cast<void*>(op.y0));
+  cx<R>* rt = reinterpret_cast<cx<R>*>(op.y);
+  for (long long leaf = (long long)blockIdx.x * ngrp + grp; leaf < op.batch; leaf += (long long)gridDim.x * ngrp) {
+    int ox, oy;
+    leaf_origin(g, (int)leaf, ox, oy);
+    for (int i = gt; i < n; i += 128) fs[i] = cvt<R>(f[(long long)(oy + i / g.s) * g.nx + ox + i % g.s]);
+    asm volatile("bar.sync %0, 128;" ::"r"(bar) : "memory");
+    cx<R>* rl = Rl + leaf * n;
+    group_rows<R>(X + leaf * n * n, n, fs, n, n, gt, [&](int i, cx<R> v) {
+      rs[i] = v;
+      rl[i] = v;
+    });
+    asm volatile("bar.sync %0, 128;" ::"r"(bar) : "memory");
+    cx<R>* ro = rt + leaf * kL;
+    group_rows<R>(UT, n, rs, kL, n, gt, [&](int i, cx<R> v) { ro[i] = v; });
+    asm volatile("bar.sync %0, 128;" ::"r"(bar) : "memory");  // fs, rs reused by the next leaf
+  }
+}
+
+// type 4: for each leaf, q = r + alpha X B U w~ (r = op.y0) written to the grid.
+template <class R>
+__device__ __forceinline__ void apply_leaf_down(const ApplyOp& op, const TreeGeom& g, z64* __restrict__ q,
+                                                cx<R>* gs_mem) {
+  const int n = g.s * g.s, kL = op.K;
+  const int grp = threadIdx.x >> 7, gt = threadIdx.x & 127, ngrp = blockDim.x >> 7;
+  const unsigned bar = 1 + grp;
+  cx<R>* ws = gs_mem + (size_t)grp * 2 * n;
+  const cx<R>* XBU = reinterpret_cast<const cx<R>*>(op.A);
+  const cx<R>* wt = reinterpret_cast<const cx<R>*>(op.x);
+  const cx<R>* Rl = reinterpret_cast<const cx<R>*>(op.y0);
+  const cx<R> alpha = mk<R>((R)op.ar, (R)op.ai);
+  for (long long leaf = (long long)blockIdx.x * ngrp + grp; leaf < op.batch; leaf += (long long)gridDim.x * ngrp) {
+    int ox, oy;
+    leaf_origin(g, (int)leaf, ox, oy);
+    for (int i = gt; i < kL; i += 128) ws[i] = ldcg_cx(wt + leaf * kL + i);
+    asm volatile("bar.sync %0, 128;" ::"r"(bar) : "memory");
+    const cx<R>* rl = Rl + leaf * n;
+    group_rows<R>(XBU + leaf * n * kL, kL, ws, n, kL, gt, [&](int i, cx<R> v) {
+      q[(long long)(oy + i / g.s) * g.nx + ox + i % g.s] = cvt<double>(ldcg_cx(rl + i) + alpha * v);
+    });
+    asm volatile("bar.sync %0, 128;" ::"r"(bar) : "memory");
+  }
+}
+
 // The operation list is copied to shared memory once per launch (dynamic
 // shared memory, nops entries), so that each operation's descriptor is a
 // shared-memory read rather than a global load on the critical path.
@@ -1688,6 +1773,7 @@ __global__ void __launch_bounds__(1024) apply_persistent_kernel(const ApplyOp* _
   __shared__ int s_ok;
   extern __shared__ unsigned char smraw[];
   ApplyOp* ops = reinterpret_cast<ApplyOp*>(smraw);
+  cx<R>* leaf_mem = reinterpret_cast<cx<R>*>(smraw + ((sizeof(ApplyOp) * (size_t)nops + 15) & ~(size_t)15));
   {
     const int words = nops * (int)(sizeof(ApplyOp) / sizeof(int));
     const int* src = reinterpret_cast<const int*>(ops_g);
@@ -1704,7 +1790,11 @@ __global__ void __launch_bounds__(1024) apply_persistent_kernel(const ApplyOp* _
   for (int o = 0; o < nops; ++o) {
     const ApplyOp op = ops[o];
     const long long rows = (long long)op.batch * op.M;
-    if (op.type == 1 || op.type == 2) {  // leaf gather / scatter, one entry per thread
+    if (op.type == 3) {
+      apply_leaf_up<R>(op, g, f, leaf_mem);
+    } else if (op.type == 4) {
+      apply_leaf_down<R>(op, g, q, leaf_mem);
+    } else if (op.type == 1 || op.type == 2) {  // leaf gather / scatter, one entry per thread
       const int n = g.s * g.s;
       for (long long t = gt; t < rows; t += nthreads) {
         const int leaf = (int)(t / n), i = (int)(t % n);
@@ -1824,9 +1914,20 @@ std::vector<ApplyOp> apply_ops(ls_handle* H) {
   };
   const LevelData& lf = H->lev[L];
   const int kL = lf.k;
-  leafop(1, F, nullptr, true);                                                       // F <- f
-  gemv(n, n, lf.X, n, (long long)n * n, F, n, Rl, n, (int)nleaf, true);              // r = X f   (Eq. 24)
-  gemv(kL, n, lf.UT, n, 0, Rl, n, rt[L], kL, (int)nleaf, true);                      // r~ = U^T r
+  {                                                                                  // leaves (Eq. 24)
+    ApplyOp o;                                                                       // r = X f, r~ = U^T r
+    memset(&o, 0, sizeof(o));
+    o.type = 3;
+    o.M = kL;
+    o.K = n;
+    o.batch = (int)nleaf;
+    o.A = lf.X;
+    o.x = lf.UT;
+    o.y = rt[L];
+    o.y0 = Rl;
+    o.phase_end = 1;
+    ops.push_back(o);
+  }
   for (int l = L - 1; l >= 1; --l) {                                                 // up pass (Eq. 28)
     const int P = 1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
     gemv(n2, n2, H->lev[l].X, n2, (long long)n2 * n2, rt[l + 1], n2, tmp[l + 1], n2, P, true);
@@ -1849,8 +1950,20 @@ std::vector<ApplyOp> apply_ops(ls_handle* H) {
     gemv(kc, kc, H->lev[l + 1].Gsib, kc, 0, rt[l + 1] + kc, n2, wt[l + 1], n2, P, false, 1.0, wt[l + 1], n2);
     gemv(kc, kc, H->lev[l + 1].GT, kc, 0, rt[l + 1], n2, wt[l + 1] + kc, n2, P, true, 1.0, wt[l + 1] + kc, n2);
   }
-  gemv(n, kL, H->XBU, kL, (long long)n * kL, wt[L], kL, Rl, n, (int)nleaf, true, -1.0, Rl, n);  // q = r - XBU w~
-  leafop(2, nullptr, Rl, true);                                                      // q -> grid
+  {                                                                                  // q = r - XBU w~ -> grid
+    ApplyOp o;
+    memset(&o, 0, sizeof(o));
+    o.type = 4;
+    o.M = n;
+    o.K = kL;
+    o.batch = (int)nleaf;
+    o.A = H->XBU;
+    o.x = wt[L];
+    o.y0 = Rl;
+    o.ar = -1.0;
+    o.phase_end = 1;
+    ops.push_back(o);
+  }
   return ops;
 }
 
@@ -1974,8 +2087,11 @@ std::vector<int> phase_ends(const std::vector<ApplyOp>& ops) {
 int upload_ops(std::vector<ApplyOp>& ops, void** dst, cudaStream_t st) {
   for (auto& o : ops) {
     o.rb = o.K <= 64 ? 8 : o.K <= 160 ? 16 : 32;
-    const bool ok = o.type == 0 ? (o.M * (long long)o.batch == 0 || (o.y && (o.K == 0 || (o.A && o.x))))
-                                : o.type == 1 ? o.y != nullptr : o.x != nullptr;
+    const bool ok = o.type == 0   ? (o.M * (long long)o.batch == 0 || (o.y && (o.K == 0 || (o.A && o.x))))
+                    : o.type == 1 ? o.y != nullptr
+                    : o.type == 2 ? o.x != nullptr
+                    : o.type == 3 ? (o.A && o.y0 && (o.M == 0 || (o.x && o.y)))
+                                  : (o.A || o.K == 0) && o.y0 && (o.K == 0 || o.x);
     if (!ok) {  // a factor or buffer the list names was never made
       set_last_error_text("apply operation list refers to a missing buffer");
       return LS_EINVAL;
@@ -1993,10 +2109,15 @@ int upload_ops(std::vector<ApplyOp>& ops, void** dst, cudaStream_t st) {
 // 1024-thread block per SM cannot be co-resident (the graph path is used then).
 // Dynamic shared memory of the persistent apply for an operation list of nops
 // entries (the attribute is raised as needed).
-size_t apply_smem(const void* kfn, int nops) {
-  const size_t bytes = sizeof(ApplyOp) * (size_t)nops;
+size_t apply_smem(const void* kfn, int nops, size_t leaf_bytes) {
+  const size_t bytes = ((sizeof(ApplyOp) * (size_t)nops + 15) & ~(size_t)15) + leaf_bytes;
   if (bytes > 48 * 1024) cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   return bytes;
+}
+
+// Leaf scratch of the persistent apply: eight 128-thread groups x 2 s^2 entries.
+size_t leaf_smem(const ls_handle* H) {
+  return (H->prec == LS_FP64 ? sizeof(z64) : sizeof(c32)) * 8 * 2 * (size_t)H->s * H->s;
 }
 
 int apply_persistent_init(ls_handle* H, cudaStream_t st) {
@@ -2008,7 +2129,7 @@ int apply_persistent_init(ls_handle* H, cudaStream_t st) {
   std::vector<ApplyOp> ops = H->prec == LS_FP64 ? apply_ops<double>(H) : apply_ops<float>(H);
   int per_sm = 0;
   if (sizeof(ApplyOp) * ops.size() > 200 * 1024 ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 1024, apply_smem(kfn, (int)ops.size())) !=
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 1024, apply_smem(kfn, (int)ops.size(), leaf_smem(H))) !=
           cudaSuccess ||
       per_sm < 1) {
     cudaGetLastError();
@@ -2141,7 +2262,7 @@ int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, int transpose, cudaS
         void* args[] = {&ops, &nops, (void*)&g, &fr, &qr, &bar, &epoch0, &err};
         count_launch();
         LS_CUDA_TRY(
-            cudaLaunchCooperativeKernel(kfn, dim3(H->apply_blocks), dim3(1024), args, apply_smem(kfn, nops), st));
+            cudaLaunchCooperativeKernel(kfn, dim3(H->apply_blocks), dim3(1024), args, apply_smem(kfn, nops, leaf_smem(H)), st));
         H->apply_epoch += (unsigned)(H->apply_phases_t - 1) * (unsigned)H->apply_blocks;
       } else {  // one launch per phase (no barrier is reached inside a launch)
         int start = 0;
@@ -2151,7 +2272,7 @@ int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, int transpose, cudaS
           unsigned epoch0 = 0;
           void* args[] = {&ops, &nops, (void*)&g, &fr, &qr, &bar, &epoch0, &err};
           count_launch();
-          LS_CUDA_TRY(cudaLaunchKernel(kfn, dim3(H->nsm), dim3(1024), args, apply_smem(kfn, nops), st));
+          LS_CUDA_TRY(cudaLaunchKernel(kfn, dim3(H->nsm), dim3(1024), args, apply_smem(kfn, nops, leaf_smem(H)), st));
           start = e + 1;
         }
       }
@@ -2176,7 +2297,7 @@ int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, int transpose, cudaS
       void* args[] = {&ops, &nops, (void*)&g, &fr, &qr, &bar, &epoch0, &err};
       count_launch();
       LS_CUDA_TRY(
-          cudaLaunchCooperativeKernel(kfn, dim3(H->apply_blocks), dim3(1024), args, apply_smem(kfn, nops), st));
+          cudaLaunchCooperativeKernel(kfn, dim3(H->apply_blocks), dim3(1024), args, apply_smem(kfn, nops, leaf_smem(H)), st));
       H->apply_epoch += (unsigned)(H->apply_phases - 1) * (unsigned)H->apply_blocks;
       prof_end(tk, PR_APPLY, st, H->bytes_apply, 0.0);
     }
