@@ -1234,8 +1234,21 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
     const cx<R>* U = reinterpret_cast<const cx<R>*>(lv.U);  // n2 x kp
     cx<R>* D = reinterpret_cast<cx<R>*>(work_s);           // P x n2 x kp
     cx<R>* E = D + (size_t)P * n2 * kp;
-    // D = [S_a U_top ; S_b U_bot]
     int ts = prof_begin(st);
+    if (l <= H->opts.top_uncompressed && kp == n2) {
+      // uncompressed level (U = I): S = X diag(S_a, S_b), two column blocks of X
+      cx<R>* Sl = reinterpret_cast<cx<R>*>(lv.S);
+      gemm<R>(st, false, false, n2, kc, kc, one<R>(), X, n2, (long long)n2 * n2, Sc, kc, 2LL * kc * kc, zero<R>(), Sl,
+              kp, (long long)kp * kp, P);
+      gemm<R>(st, false, false, n2, kc, kc, one<R>(), X + kc, n2, (long long)n2 * n2, Sc + (size_t)kc * kc, kc,
+              2LL * kc * kc, zero<R>(), Sl + kc, kp, (long long)kp * kp, P);
+      if ((rc = check_launch("merge S"))) return rc;
+      const double fl = P * 2.0 * 8 * (double)n2 * kc * kc;
+      prof_end(ts, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * ((double)n2 * n2 + 2.0 * kc * kc + (double)kp * kp), fl);
+      H->flops_build += fl;
+      continue;
+    }
+    // D = [S_a U_top ; S_b U_bot]
     gemm<R>(st, false, false, kc, kp, kc, one<R>(), Sc, kc, 2LL * kc * kc, U, kp, 0, zero<R>(), D, kp,
             (long long)n2 * kp, P);
     gemm<R>(st, false, false, kc, kp, kc, one<R>(), Sc + (size_t)kc * kc, kc, 2LL * kc * kc, U + (size_t)kc * kp, kp,
