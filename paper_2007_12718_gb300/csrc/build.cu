@@ -1941,8 +1941,14 @@ std::vector<ApplyOp> apply_ops(ls_handle* H) {
     o.phase_end = 1;
     ops.push_back(o);
   }
+  // an uncompressed level (U = I) skips its U and U^T products
+  auto identity_u = [&](int l) { return l <= H->opts.top_uncompressed && H->lev[l].k == 2 * H->lev[l + 1].k; };
   for (int l = L - 1; l >= 1; --l) {                                                 // up pass (Eq. 28)
     const int P = 1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
+    if (identity_u(l)) {
+      gemv(n2, n2, H->lev[l].X, n2, (long long)n2 * n2, rt[l + 1], n2, rt[l], n2, P, true);
+      continue;
+    }
     gemv(n2, n2, H->lev[l].X, n2, (long long)n2 * n2, rt[l + 1], n2, tmp[l + 1], n2, P, true);
     gemv(kp, n2, H->lev[l].UT, n2, 0, tmp[l + 1], n2, rt[l], kp, P, true);
   }
@@ -1955,13 +1961,17 @@ std::vector<ApplyOp> apply_ops(ls_handle* H) {
   for (int l = 1; l <= L - 1; ++l) {                                                 // down pass (Lemma 4.1)
     const int P = 1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
     const cx<R>* Sc = reinterpret_cast<const cx<R>*>(H->lev[l + 1].S);
-    gemv(n2, kp, H->lev[l].U, kp, 0, wt[l], kp, wt[l + 1], n2, P, true);           // U w~
-    gemv(kc, kc, Sc, kc, 2LL * kc * kc, wt[l + 1], n2, tmp[l + 1], n2, P, false, -1.0, rt[l + 1], n2);
-    gemv(kc, kc, Sc + (size_t)kc * kc, kc, 2LL * kc * kc, wt[l + 1] + kc, n2, tmp[l + 1] + kc, n2, P, true, -1.0,
+    cx<R>* Uw = wt[l + 1];  // U w~ (w~ itself when U = I)
+    if (identity_u(l))
+      Uw = wt[l];
+    else
+      gemv(n2, kp, H->lev[l].U, kp, 0, wt[l], kp, wt[l + 1], n2, P, true);         // U w~
+    gemv(kc, kc, Sc, kc, 2LL * kc * kc, Uw, n2, tmp[l + 1], n2, P, false, -1.0, rt[l + 1], n2);
+    gemv(kc, kc, Sc + (size_t)kc * kc, kc, 2LL * kc * kc, Uw + kc, n2, tmp[l + 1] + kc, n2, P, true, -1.0,
          rt[l + 1] + kc, n2);                                                        // t = r~ - diag(S) U w~
     gemv(n2, n2, H->lev[l].X, n2, (long long)n2 * n2, tmp[l + 1], n2, rt[l + 1], n2, P, true);  // q~ = X t
-    gemv(kc, kc, H->lev[l + 1].Gsib, kc, 0, rt[l + 1] + kc, n2, wt[l + 1], n2, P, false, 1.0, wt[l + 1], n2);
-    gemv(kc, kc, H->lev[l + 1].GT, kc, 0, rt[l + 1], n2, wt[l + 1] + kc, n2, P, true, 1.0, wt[l + 1] + kc, n2);
+    gemv(kc, kc, H->lev[l + 1].Gsib, kc, 0, rt[l + 1] + kc, n2, wt[l + 1], n2, P, false, 1.0, Uw, n2);
+    gemv(kc, kc, H->lev[l + 1].GT, kc, 0, rt[l + 1], n2, wt[l + 1] + kc, n2, P, true, 1.0, Uw + kc, n2);
   }
   {                                                                                  // q = r - XBU w~ -> grid
     ApplyOp o;
