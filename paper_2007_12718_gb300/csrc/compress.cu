@@ -511,38 +511,53 @@ __device__ __forceinline__ void id_back_substitution(const cx<R>* Rm, const cx<R
 
 // U rows of the ID by a blocked back substitution: U(c, :) = (R11^-1 R(:, c))^T
 // for a candidate c that is not a pivot, e_sel(c) for a pivot (Sec. 2.1, the
-// interpolation matrix T = R11^-1 R12).  One warp per candidate, CB candidates
-// per block; the right-hand sides (column c of R, k entries) live in shared
+// interpolation matrix T = R11^-1 R12).  CB candidates per block, one warp
+// each for the triangular panel solves, all kTrsmThreads threads for the
+// updates; the right-hand sides (column c of R, k entries) live in shared
 // memory.  Panels of kTrsmNB rows are taken from the bottom: the panel's
 // diagonal block (read from RT = R11^T, so a row of RT is a column of R11) is
-// staged in shared memory and each warp solves its candidate's panel rows with
+// staged in shared memory (the next panel's block is fetched during the
+// current panel's update) and each warp solves its candidate's panel rows with
 // warp-synchronous steps (one lane per row); then the block updates the rows
 // above the panel with the panel's solved unknowns, reading kTrsmNB rows of RT
-// (coalesced).  k is read on the device (rank[0]).
-constexpr int kTrsmNB = 32;
+// (coalesced, sixteen loads in flight per thread).  k is read on the device
+// (rank[0]).
+constexpr int kTrsmNB = 32, kTrsmThreads = 256;
 template <class R, int CB>
-__global__ void __launch_bounds__(32 * CB) id_trsm_kernel(const cx<R>* __restrict__ Rm, const cx<R>* __restrict__ RT,
-                                                          const int* __restrict__ sel, const int* __restrict__ rank,
-                                                          int m, int kmax, cx<R>* __restrict__ U) {
+__global__ void __launch_bounds__(kTrsmThreads) id_trsm_kernel(const cx<R>* __restrict__ Rm,
+                                                               const cx<R>* __restrict__ RT,
+                                                               const int* __restrict__ sel,
+                                                               const int* __restrict__ rank, int m, int kmax,
+                                                               cx<R>* __restrict__ U) {
   extern __shared__ unsigned char smraw[];
   cx<R>* tv = reinterpret_cast<cx<R>*>(smraw);  // CB x kmax
-  cx<R>* D = tv + (size_t)CB * kmax;             // kTrsmNB x kTrsmNB: D[q][r] = R11(i0 + r, i0 + q), r <= q
+  cx<R>* Db = tv + (size_t)CB * kmax;            // 2 x kTrsmNB^2: D[q][r] = R11(i0 + r, i0 + q), r <= q
   const int k = min(*rank, kmax);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int c = blockIdx.x * CB + warp;
-  const bool own = c < m;
+  const bool solver = warp < CB;
+  const bool own = solver && c < m;
   const int sc = own ? sel[c] : 0;
   const bool solve = own && sc < 0;
-  cx<R>* t = tv + (size_t)warp * kmax;
-  for (int a = lane; a < k; a += 32) t[a] = solve ? ldcg_cx(Rm + (long long)a * m + c) : mk<R>(0, 0);
-  __syncthreads();
-  for (int i1 = k; i1 > 0; i1 -= kTrsmNB) {
+  cx<R>* t = tv + (size_t)(solver ? warp : 0) * kmax;
+  for (int e = tid; e < CB * k; e += kTrsmThreads) {
+    const int j = e / k, a = e % k, cj = blockIdx.x * CB + j;
+    const bool sj = cj < m && sel[cj] < 0;
+    tv[(size_t)j * kmax + a] = sj ? ldcg_cx(Rm + (long long)a * m + cj) : mk<R>(0, 0);
+  }
+  auto load_diag = [&](int i1, cx<R>* D) {
     const int i0 = max(0, i1 - kTrsmNB), w = i1 - i0;
-    for (int e = tid; e < w * w; e += 32 * CB) {
+    for (int e = tid; e < w * w; e += kTrsmThreads) {
       const int q = e / w, r = e % w;
       D[q * kTrsmNB + r] = r <= q ? ldcg_cx(RT + (long long)(i0 + q) * k + i0 + r) : mk<R>(0, 0);
     }
-    __syncthreads();
+  };
+  if (k > 0) load_diag(k, Db);
+  __syncthreads();
+  int buf = 0;
+  for (int i1 = k; i1 > 0; i1 -= kTrsmNB) {
+    const int i0 = max(0, i1 - kTrsmNB), w = i1 - i0;
+    const cx<R>* D = Db + buf * kTrsmNB * kTrsmNB;
     if (solve) {  // rows i1 - 1 .. i0 of this candidate; lane r holds row i0 + r
       cx<R> x = lane < w ? t[i0 + lane] : mk<R>(0, 0);
       for (int q = w - 1; q >= 0; --q) {
@@ -558,20 +573,28 @@ __global__ void __launch_bounds__(32 * CB) id_trsm_kernel(const cx<R>* __restric
       if (lane < w) t[i0 + lane] = x;
     }
     __syncthreads();
+    if (i0 > 0) load_diag(i0, Db + (buf ^ 1) * kTrsmNB * kTrsmNB);  // next panel's block, during the update
     // rows above the panel: t[b] -= sum_{a in panel} R11(b, a) t[a] = RT[a][b] t[a]
-    for (int b = tid; b < i0; b += 32 * CB) {
+    for (int b = tid; b < i0; b += kTrsmThreads) {
       cx<R> acc[CB];
 #pragma unroll
       for (int j = 0; j < CB; ++j) acc[j] = mk<R>(0, 0);
-      for (int a = i0; a < i1; ++a) {
-        const cx<R> r = ldcg_cx(RT + (long long)a * k + b);
+      for (int a0 = i0; a0 < i1; a0 += 16) {
+        cx<R> rv[16];
 #pragma unroll
-        for (int j = 0; j < CB; ++j) fma_(acc[j], r, tv[(size_t)j * kmax + a]);
+        for (int u = 0; u < 16; ++u) rv[u] = a0 + u < i1 ? ldcg_cx(RT + (long long)(a0 + u) * k + b) : mk<R>(0, 0);
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+          if (a0 + u < i1) {
+#pragma unroll
+            for (int j = 0; j < CB; ++j) fma_(acc[j], rv[u], tv[(size_t)j * kmax + a0 + u]);
+          }
       }
 #pragma unroll
       for (int j = 0; j < CB; ++j) tv[(size_t)j * kmax + b] = tv[(size_t)j * kmax + b] - acc[j];
     }
     __syncthreads();
+    buf ^= 1;
   }
   if (own)
     for (int a = lane; a < k; a += 32)
@@ -1187,11 +1210,11 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
   }
   if (reg_mode) {
     constexpr int CB = 4;
-    const size_t smt = sizeof(cx<R>) * ((size_t)CB * kmax + (size_t)kTrsmNB * kTrsmNB);
+    const size_t smt = sizeof(cx<R>) * ((size_t)CB * kmax + (size_t)2 * kTrsmNB * kTrsmNB);
     if (smt > 48 * 1024)
       LS_CUDA_TRY(cudaFuncSetAttribute(id_trsm_kernel<R, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt));
     count_launch();
-    id_trsm_kernel<R, CB><<<(unsigned)((m + CB - 1) / CB), 32 * CB, smt, st>>>(Rm, RT, sel, rank, m, kmax, Ut);
+    id_trsm_kernel<R, CB><<<(unsigned)((m + CB - 1) / CB), kTrsmThreads, smt, st>>>(Rm, RT, sel, rank, m, kmax, Ut);
   } else if (use_cluster) {
     count_launch();
     LS_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpqr_id_cluster_kernel<R>, (const cx<R>*)A, m, p, kmax, eps, Rm, sel, piv,
