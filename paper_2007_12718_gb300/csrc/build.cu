@@ -201,7 +201,8 @@ void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, cx<R> alpha, c
     return;
   }
   count_launch();
-  if (M >= 48 && N >= 48) {
+  // 64 x 64 tiles unless they leave most SMs idle (then 32 x 32 tiles: four times the blocks)
+  if (M >= 48 && N >= 48 && (long long)((N + 63) / 64) * ((M + 63) / 64) * batch >= 128) {
     dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
     if (!ta && !tb)
       gemm64_kernel<R, false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
@@ -877,35 +878,44 @@ __global__ void set_identity_kernel(cx<R>* X, int n, int lda, long long sX, int 
 //   Ab = Ab^-1                                         (in shared memory)
 //   Rb = Ab Mb;   X += -Cb Rb;   X[:,J] = -Cb Ab       (three batched GEMMs)
 //   X[J,:] = Rb, X[J,J] = Ab                           (finalize)
+// Panel J = [k0, k0 + w) of the blocked Gauss-Jordan inverse: Ab = X[J, J];
+// Mb = X[J, :] with the columns J replaced by the identity (so that
+// Rb = Ab^-1 Mb carries Ab^-1 in those columns); Cb = X[:, J] with the rows J
+// zeroed, and X[i, J] = 0 for rows i outside J (the single update
+// X -= Cb Rb then leaves -X[:, J] Ab^-1 there).
 template <class R>
-__global__ void gjb_extract_kernel(const cx<R>* X, int n, int lda, long long sX, int k0, int w, cx<R>* Ab, cx<R>* Mb,
+__global__ void gjb_extract_kernel(cx<R>* X, int n, int lda, long long sX, int k0, int w, cx<R>* Ab, cx<R>* Mb,
                                    cx<R>* Cb) {
   const int b = blockIdx.y;
-  const cx<R>* M = X + b * sX;
+  cx<R>* M = X + b * sX;
   const long long tot = (long long)n * w;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     // Mb: w x n (row r of J, column c)
     int r = (int)(t / n), c = (int)(t % n);
     bool inJc = c >= k0 && c < k0 + w;
-    Mb[b * tot + t] = inJc ? mk<R>(0, 0) : M[(long long)(k0 + r) * lda + c];
+    Mb[b * tot + t] = inJc ? mk<R>(c - k0 == r ? R(1) : R(0), R(0)) : M[(long long)(k0 + r) * lda + c];
     if (inJc) Ab[(long long)b * w * w + r * w + (c - k0)] = M[(long long)(k0 + r) * lda + c];
     // Cb: n x w (row i, column q of J)
     int i = (int)(t / w), q = (int)(t % w);
     bool inJr = i >= k0 && i < k0 + w;
-    Cb[b * tot + t] = inJr ? mk<R>(0, 0) : M[(long long)i * lda + k0 + q];
+    if (inJr) {
+      Cb[b * tot + t] = mk<R>(0, 0);
+    } else {
+      cx<R>* e = M + (long long)i * lda + k0 + q;
+      Cb[b * tot + t] = *e;
+      *e = mk<R>(0, 0);
+    }
   }
 }
 
 template <class R>
-__global__ void gjb_finalize_kernel(cx<R>* X, int n, int lda, long long sX, int k0, int w, const cx<R>* Ab,
-                                    const cx<R>* Rb) {
+__global__ void gjb_finalize_kernel(cx<R>* X, int n, int lda, long long sX, int k0, int w, const cx<R>* Rb) {
   const int b = blockIdx.y;
   cx<R>* M = X + b * sX;
   const long long tot = (long long)n * w;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     int r = (int)(t / n), c = (int)(t % n);
-    bool inJc = c >= k0 && c < k0 + w;
-    M[(long long)(k0 + r) * lda + c] = inJc ? Ab[(long long)b * w * w + r * w + (c - k0)] : Rb[b * tot + t];
+    M[(long long)(k0 + r) * lda + c] = Rb[b * tot + t];  // rows J: Ab^-1 X[J, :] (Ab^-1 in the columns J)
   }
 }
 
@@ -972,9 +982,8 @@ int invert_batch_nopiv(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int
     if (rc) return rc;
     gemm<R>(st, false, false, w, n, w, one<R>(), Ab, w, (long long)w * w, Mb, n, tot, zero<R>(), Rb, n, tot, P);
     gemm<R>(st, false, false, n, n, w, mone, Cb, w, tot, Rb, n, tot, one<R>(), X, lda, sX, P);
-    gemm<R>(st, false, false, n, w, w, mone, Cb, w, tot, Ab, w, (long long)w * w, zero<R>(), X + k0, lda, sX, P);
     count_launch();
-    gjb_finalize_kernel<R><<<g, 256, 0, st>>>(X, n, lda, sX, k0, w, Ab, Rb);
+    gjb_finalize_kernel<R><<<g, 256, 0, st>>>(X, n, lda, sX, k0, w, Rb);
   }
   return check_launch("inverse_blocked_nopiv");
 }
