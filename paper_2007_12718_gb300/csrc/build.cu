@@ -1222,13 +1222,27 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
       }
       prof_end(ti, PR_MERGE_INV, st, sizeof(cx<R>) * P * 2.0 * kk, P * 8.0 * (double)kc * kc * kc);
       tg = prof_begin(st);
-      gemm<R>(st, false, false, kc, kc, kc, mone, X22, n2, sX, Y2, kc, kk, zero<R>(), X21, n2, sX, P);  // -W Y2
-      gemm<R>(st, false, false, kc, kc, kc, mone, Y1, kc, kk, X22, n2, sX, zero<R>(), X12, n2, sX, P);  // -Y1 W
-      count_launch();
-      set_identity_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(X11, kc, n2, sX, P);
-      gemm<R>(st, false, false, kc, kc, kc, mone, Y1, kc, kk, X21, n2, sX, one<R>(), X11, n2, sX, P);  // I + Y1 W Y2
-      if ((rc = check_launch("merge blocks"))) return rc;
-      prof_end(tg, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * (4.0 * kk + (double)sX), P * 3.0 * 8.0 * (double)kc * kc * kc);
+      if (l == 0) {
+        // the root's X is only ever applied: it is kept as W, Y1 (in the X12 block) and
+        // Y2 (in the X21 block), and X [r_a; r_b] = [r_a - Y1 u; u], u = W (r_b - Y2 r_a)
+        dim3 gc((unsigned)std::min<long long>(1024, (kk + 255) / 256), P);
+        count_launch();
+        copy_block_kernel<R><<<gc, 256, 0, st>>>(X21, n2, sX, Y2, kc, kk, kc, kc);
+        count_launch();
+        copy_block_kernel<R><<<gc, 256, 0, st>>>(X12, n2, sX, Y1, kc, kk, kc, kc);
+        if ((rc = check_launch("root blocks"))) return rc;
+        prof_end(tg, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * 4.0 * kk, 0.0);
+        H->factor_bytes -= sizeof(cx<R>) * (double)kk;  // the X11 block is not read
+      } else {
+        gemm<R>(st, false, false, kc, kc, kc, mone, X22, n2, sX, Y2, kc, kk, zero<R>(), X21, n2, sX, P);  // -W Y2
+        gemm<R>(st, false, false, kc, kc, kc, mone, Y1, kc, kk, X22, n2, sX, zero<R>(), X12, n2, sX, P);  // -Y1 W
+        count_launch();
+        set_identity_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(X11, kc, n2, sX, P);
+        gemm<R>(st, false, false, kc, kc, kc, mone, Y1, kc, kk, X21, n2, sX, one<R>(), X11, n2, sX, P);  // I + Y1 W Y2
+        if ((rc = check_launch("merge blocks"))) return rc;
+        prof_end(tg, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * (4.0 * kk + (double)sX),
+                 P * 3.0 * 8.0 * (double)kc * kc * kc);
+      }
     }
     H->flops_build += P * (6.0 * 8 * (double)kc * kc * kc + 8.0 * (double)kc * kc * kc);
     if (l == 0) break;
@@ -1568,8 +1582,13 @@ int apply_core(ls_handle* H, z64** slots, cudaStream_t st) {
     const int kc = H->lev[1].k, n2 = 2 * kc;
     cx<R>* qr = tmp[1];
     const cx<R>* G1 = reinterpret_cast<const cx<R>*>(H->lev[1].Gsib);
-    gemv<R>(st, false, n2, n2, one<R>(), reinterpret_cast<const cx<R>*>(H->lev[0].X), n2, 0, rt[1], 0, zero<R>(), qr,
-            0, 1);
+    const cx<R>* X0 = reinterpret_cast<const cx<R>*>(H->lev[0].X);  // [., Y1; Y2, W]
+    cx<R>* tb = wt[1] + kc;
+    LS_CUDA_TRY(cudaMemcpyAsync(tb, rt[1] + kc, sizeof(cx<R>) * kc, cudaMemcpyDeviceToDevice, st));
+    gemv<R>(st, false, kc, kc, mone, X0 + (size_t)kc * n2, n2, 0, rt[1], 0, one<R>(), tb, 0, 1);  // r_b - Y2 r_a
+    gemv<R>(st, false, kc, kc, one<R>(), X0 + (size_t)kc * n2 + kc, n2, 0, tb, 0, zero<R>(), qr + kc, 0, 1);
+    LS_CUDA_TRY(cudaMemcpyAsync(qr, rt[1], sizeof(cx<R>) * kc, cudaMemcpyDeviceToDevice, st));
+    gemv<R>(st, false, kc, kc, mone, X0 + kc, n2, 0, qr + kc, 0, one<R>(), qr, 0, 1);  // q_a = r_a - Y1 q_b
     gemv<R>(st, false, kc, kc, one<R>(), G1, kc, 0, qr + kc, 0, zero<R>(), wt[1], 0, 1);
     gemv<R>(st, true, kc, kc, one<R>(), G1, kc, 0, qr, 0, zero<R>(), wt[1] + kc, 0, 1);
   }
@@ -1963,7 +1982,10 @@ std::vector<ApplyOp> apply_ops(ls_handle* H) {
   }
   {                                                                                  // root (Eq. 29)
     const int kc = H->lev[1].k, n2 = 2 * kc;
-    gemv(n2, n2, H->lev[0].X, n2, 0, rt[1], 0, tmp[1], 0, 1, true);
+    const cx<R>* X0 = reinterpret_cast<const cx<R>*>(H->lev[0].X);  // [., Y1; Y2, W]
+    gemv(kc, kc, X0 + (size_t)kc * n2, n2, 0, rt[1], 0, wt[1] + kc, 0, 1, true, -1.0, rt[1] + kc, 0);  // r_b - Y2 r_a
+    gemv(kc, kc, X0 + (size_t)kc * n2 + kc, n2, 0, wt[1] + kc, 0, tmp[1] + kc, 0, 1, true);           // q_b = W (.)
+    gemv(kc, kc, X0 + kc, n2, 0, tmp[1] + kc, 0, tmp[1], 0, 1, true, -1.0, rt[1], 0);                 // q_a = r_a - Y1 q_b
     gemv(kc, kc, H->lev[1].Gsib, kc, 0, tmp[1] + kc, 0, wt[1], 0, 1, false);
     gemv(kc, kc, H->lev[1].GT, kc, 0, tmp[1], 0, wt[1] + kc, 0, 1, true);
   }
@@ -2078,7 +2100,12 @@ std::vector<ApplyOp> apply_ops_transpose(ls_handle* H) {
     const int kc = H->lev[1].k, n2 = 2 * kc;
     gemv(kc, kc, H->lev[1].Gsib, kc, 0, wt[1] + kc, 0, tmp[1], 0, 1, false);
     gemv(kc, kc, H->lev[1].GT, kc, 0, wt[1], 0, tmp[1] + kc, 0, 1, true);
-    gemv(n2, n2, H->lev[0].XT, n2, 0, tmp[1], 0, rt[1], 0, 1, true);                  // r~_1
+    // r~_1 = X_0^T v with X_0 kept as [., Y1; Y2, W] (so X_0^T's blocks are [., Y2^T; Y1^T, W^T]):
+    // [v_a - Y2^T u; u], u = W^T (v_b - Y1^T v_a)
+    const cx<R>* XT0 = reinterpret_cast<const cx<R>*>(H->lev[0].XT);
+    gemv(kc, kc, XT0 + (size_t)kc * n2, n2, 0, tmp[1], 0, wt[1], 0, 1, true, -1.0, tmp[1] + kc, 0);
+    gemv(kc, kc, XT0 + (size_t)kc * n2 + kc, n2, 0, wt[1], 0, rt[1] + kc, 0, 1, true);
+    gemv(kc, kc, XT0 + kc, n2, 0, rt[1] + kc, 0, rt[1], 0, 1, true, -1.0, tmp[1], 0);
   }
   for (int l = 1; l <= L - 1; ++l) {
     const int P = 1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
@@ -2154,6 +2181,10 @@ size_t leaf_smem(const ls_handle* H) {
 
 int apply_persistent_init(ls_handle* H, cudaStream_t st) {
   if (H->apply_ops || H->apply_blocks < 0) return LS_OK;
+  if (getenv("LS_APPLY_GRAPH")) {  // diagnostic: the CUDA-graph path, as when the grid cannot be co-resident
+    H->apply_blocks = -1;
+    return LS_OK;
+  }
   const void* kfn = H->prec == LS_FP64 ? (const void*)apply_persistent_kernel<double>
                                        : (const void*)apply_persistent_kernel<float>;
   int rc;

@@ -238,3 +238,24 @@ def test_top_level_uncompressed(precision):
     f = inputs.random_complex((n, n), 6)
     q = host(ls.ls_apply(H, dev(f), torch.zeros(n, n, dtype=torch.complex128, device=DEV)))
     assert rel(q, nystrom.solve_dense(A4, f.ravel()).reshape(n, n)) < 5e-4
+
+
+@pytest.mark.parametrize("precision", [ls.LS_FP32, ls.LS_FP64])
+def test_apply_graph_path_matches_persistent(precision, monkeypatch):
+    """The CUDA-graph apply (used when the persistent grid cannot be co-resident,
+    forced here with LS_APPLY_GRAPH) computes the same Algorithm 2: forward and
+    transposed applies agree with the persistent kernel's to rounding."""
+    n, kappa = 64, 40.0
+    b = inputs.gaussian_family(n, 3)
+    f = inputs.random_complex((n, n), 8)
+    out = {}
+    for mode in ("persistent", "graph"):
+        if mode == "graph":
+            monkeypatch.setenv("LS_APPLY_GRAPH", "1")
+        H = build(n, kappa, b, 1e-4, precision=precision, top_uncompressed=1)
+        out[mode] = (host(ls.ls_apply(H, dev(f), torch.zeros(n, n, dtype=torch.complex128, device=DEV))),
+                     host(ls.ls_apply(H, dev(f), torch.zeros(n, n, dtype=torch.complex128, device=DEV), transpose=True)))
+        ls.ls_free(H)
+    tol = 1e-5 if precision == ls.LS_FP32 else 1e-12
+    assert rel(out["graph"][0], out["persistent"][0]) < tol
+    assert rel(out["graph"][1], out["persistent"][1]) < tol
