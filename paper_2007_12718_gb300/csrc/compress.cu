@@ -1023,7 +1023,7 @@ int upload_block(const std::vector<int>& rx, const std::vector<int>& ry, const s
 // scratch for the grid barrier and the kernels' status words.
 template <class R>
 int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_buf, cudaStream_t st, int* k_out,
-               std::vector<int>* hp_out, cx<R>* Uout) {
+               std::vector<int>* hp_out, cx<R>* Uout, cudaStream_t su = nullptr) {
   int rc;
   std::vector<int>& hp = *hp_out;
   const int kmax = std::min(m, p);
@@ -1048,30 +1048,40 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
     set_last_error_text("proxy block too large for the ID kernel");
     return LS_EINVAL;
   }
-  size_t need = 64 * 256 + sizeof(cx<R>) * ((size_t)m * p * (use_smem ? 0 : 1) + (size_t)kmax * m + (size_t)m * kmax +
-                                 (size_t)kmax * kmax + (size_t)2 * nslot * p) +
-                sizeof(int) * (2 * m + 8) + sizeof(IdSlot<R>) * 2 * (nslot + 1) +
+  size_t need = 64 * 256 + sizeof(cx<R>) * ((size_t)m * p * (use_smem ? 0 : 1) + (size_t)m * kmax +
+                                 (size_t)2 * nslot * p) +
+                sizeof(int) * (m + 8) + sizeof(IdSlot<R>) * 2 * (nslot + 1) +
                 2 * sizeof(unsigned long long) * ((size_t)kmax + 1) + 2048;
+  // R, R11^T, the selection and the rank (what the back substitution reads) in an
+  // allocation of their own: with an auxiliary stream su the back substitution runs
+  // there, beside the next level's ID, and this allocation is released on su
+  const size_t need_t = 4 * 256 + sizeof(cx<R>) * ((size_t)kmax * m + (size_t)kmax * kmax) + sizeof(int) * (m + 8);
   char* wsp = nullptr;
+  char* tsp = nullptr;
   if ((rc = dalloc((void**)&wsp, need))) return rc;
+  if ((rc = dalloc((void**)&tsp, need_t))) {
+    dfree(wsp);
+    return rc;
+  }
+  char* cur = nullptr;
   auto carve = [&](size_t bytes) {
-    char* r = wsp;
-    wsp += (bytes + 255) & ~(size_t)255;
+    char* r = cur;
+    cur += (bytes + 255) & ~(size_t)255;
     return r;
   };
-  char* wbase = wsp;
-  cx<R>* Aw = use_smem ? nullptr : reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)m * p));
+  cur = tsp;
   cx<R>* Rm = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)kmax * m));
-  cx<R>* Ut = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)m * kmax));
   cx<R>* RT = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)kmax * kmax));
-  cx<R>* pslots = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)2 * nslot * p));
   int* sel = reinterpret_cast<int*>(carve(sizeof(int) * m));
-  int* piv = reinterpret_cast<int*>(carve(sizeof(int) * m));
   int* rank = reinterpret_cast<int*>(carve(sizeof(int) * 8));
+  cur = wsp;
+  cx<R>* Aw = use_smem ? nullptr : reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)m * p));
+  cx<R>* Ut = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)m * kmax));
+  cx<R>* pslots = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)2 * nslot * p));
+  int* piv = reinterpret_cast<int*>(carve(sizeof(int) * m));
   IdSlot<R>* slots = reinterpret_cast<IdSlot<R>*>(carve(sizeof(IdSlot<R>) * 2 * (nslot + 1)));
   unsigned long long* gkey =
       reinterpret_cast<unsigned long long*>(carve(2 * sizeof(unsigned long long) * ((size_t)kmax + 1)));
-  wsp = wbase;
   // one cluster when the candidates fit in the shared memory of CL blocks: the
   // smallest CL with at most 32 candidates per block (4 per warp), else at most 64
   int maxcl = 16;
@@ -1208,13 +1218,26 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
     count_launch();
     LS_CUDA_TRY(cudaLaunchCooperativeKernel(kreg, dim3(nblk_r), dim3(128 * cpb), args, smem_r, st));
   }
+  bool u_on_aux = false;  // U written by the back substitution on su
   if (reg_mode) {
     constexpr int CB = 4;
     const size_t smt = sizeof(cx<R>) * ((size_t)CB * kmax + (size_t)2 * kTrsmNB * kTrsmNB);
     if (smt > 48 * 1024)
       LS_CUDA_TRY(cudaFuncSetAttribute(id_trsm_kernel<R, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt));
+    cudaStream_t sb = st;
+    cx<R>* Udst = Ut;
+    if (su && Uout) {  // U straight into Uout on the auxiliary stream, after the ID kernel
+      cudaEvent_t e;
+      LS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      LS_CUDA_TRY(cudaEventRecord(e, st));
+      LS_CUDA_TRY(cudaStreamWaitEvent(su, e, 0));
+      cudaEventDestroy(e);
+      sb = su;
+      Udst = Uout;
+      u_on_aux = true;
+    }
     count_launch();
-    id_trsm_kernel<R, CB><<<(unsigned)((m + CB - 1) / CB), kTrsmThreads, smt, st>>>(Rm, RT, sel, rank, m, kmax, Ut);
+    id_trsm_kernel<R, CB><<<(unsigned)((m + CB - 1) / CB), kTrsmThreads, smt, sb>>>(Rm, RT, sel, rank, m, kmax, Udst);
   } else if (use_cluster) {
     count_launch();
     LS_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpqr_id_cluster_kernel<R>, (const cx<R>*)A, m, p, kmax, eps, Rm, sel, piv,
@@ -1255,8 +1278,17 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
   // CPQR work: two projections and a norm (36 p real flops) per active candidate and step
   prof_end(tk, PR_CPQR, st, sizeof(cx<R>) * (double)m * p * 2.0 * k,
            36.0 * p * ((double)m * k - 0.5 * (double)k * k));
+  auto release_tsp = [&] {
+    if (u_on_aux) {
+      ls::StreamScope scope(su);
+      ls::dfree(tsp);
+    } else {
+      ls::dfree(tsp);
+    }
+  };
   if (abort_flag) {
     ls::dfree(wsp);
+    release_tsp();
     return LS_ETIMEOUT;
   }
   if (k < 0 || k > kmax) {
@@ -1265,9 +1297,10 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
   }
   hp.assign(k > 0 ? k : 1, 0);
   for (int a = 0; a < k; ++a) hp[a] = pin[4 + a];
-  if (k > 0 && Uout)  // stream-ordered: later users of U run after this copy
+  if (k > 0 && Uout && !u_on_aux)  // stream-ordered: later users of U run after this copy
     LS_CUDA_TRY(cudaMemcpyAsync(Uout, Ut, sizeof(cx<R>) * (size_t)m * k, cudaMemcpyDeviceToDevice, st));
   ls::dfree(wsp);
+  release_tsp();
   for (int a = 0; a < k; ++a)
     if (hp[a] < 0 || hp[a] >= m) {
       set_last_error_text("ID kernel returned an invalid pivot");
@@ -1278,9 +1311,22 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
 }
 
 template <class R>
-int compress_t(ls_handle* H, cudaStream_t st, const LevelDone& level_done) {
+int compress_t(ls_handle* H, cudaStream_t st, const LevelDone& level_done, cudaStream_t su) {
   const int L = H->L, s = H->s, w = H->ring;
   int rc;
+  // with an auxiliary stream the U of a level is finished there; the level is
+  // reported done once su has also passed everything issued on st so far
+  auto done = [&](int l) -> int {
+    if (su) {
+      cudaEvent_t e;
+      LS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      LS_CUDA_TRY(cudaEventRecord(e, st));
+      LS_CUDA_TRY(cudaStreamWaitEvent(su, e, 0));
+      cudaEventDestroy(e);
+    }
+    if (level_done) level_done(l);
+    return LS_OK;
+  };
   std::vector<int> rows_x, rows_y;
   int* dint = nullptr;
   for (int l = L; l >= 1; --l) {
@@ -1330,7 +1376,7 @@ int compress_t(ls_handle* H, cudaStream_t st, const LevelDone& level_done) {
       count_launch();
       identity_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(reinterpret_cast<cx<R>*>(lv.U), m);
       if ((rc = check_launch("identity U"))) return rc;
-      if (level_done) level_done(l);
+      if ((rc = done(l))) return rc;
       continue;
     }
     int k = 0;
@@ -1342,7 +1388,7 @@ int compress_t(ls_handle* H, cudaStream_t st, const LevelDone& level_done) {
     if ((rc = dalloc((void**)&dint, sizeof(int) * (2 * m + 2 * p + 8)))) return rc;
     if ((rc = upload_block<R>(rows_x, rows_y, px, py, A, dint, st, H->ks_prec, KernelTable{H->ktab, H->ktx, H->kty}))) return rc;
     if ((rc = dalloc(&lv.U, sizeof(cx<R>) * (size_t)m * std::max(std::min(m, p), 1)))) return rc;
-    if ((rc = run_row_id<R>(A, m, p, H->tol, H->nsm, H->sync_buf, st, &k, &hp, reinterpret_cast<cx<R>*>(lv.U))))
+    if ((rc = run_row_id<R>(A, m, p, H->tol, H->nsm, H->sync_buf, st, &k, &hp, reinterpret_cast<cx<R>*>(lv.U), su)))
       return rc;
     ls::dfree(A);
     lv.k = k;
@@ -1353,7 +1399,7 @@ int compress_t(ls_handle* H, cudaStream_t st, const LevelDone& level_done) {
       lv.skel_y[a] = rows_y[hp[a]];
     }
     H->flops_compress += 8.0 * 2.0 * (double)m * p * k;  // two projections per pivot step
-    if (level_done) level_done(l);
+    if ((rc = done(l))) return rc;
   }
   if (dint) ls::dfree(dint);
   return LS_OK;
@@ -1449,8 +1495,8 @@ int sibling_block(ls_handle* H, int l, cudaStream_t st) {
                             : device_block_t<float>(H, ax, ay, bx, by, &lv.Gsib, st);
 }
 
-int compress(ls_handle* H, cudaStream_t st, const LevelDone& level_done) {
-  return H->prec == LS_FP64 ? compress_t<double>(H, st, level_done) : compress_t<float>(H, st, level_done);
+int compress(ls_handle* H, cudaStream_t st, const LevelDone& level_done, cudaStream_t su) {
+  return H->prec == LS_FP64 ? compress_t<double>(H, st, level_done, su) : compress_t<float>(H, st, level_done, su);
 }
 
 }  // namespace ls

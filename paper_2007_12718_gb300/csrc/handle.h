@@ -100,7 +100,10 @@ typedef std::function<void(int level)> LevelDone;
 void* pinned_scratch(size_t bytes);
 
 // compress.cu
-int compress(ls_handle* H, cudaStream_t st, const LevelDone& level_done = LevelDone());
+// With an auxiliary stream su, each level's U (the ID's back substitution) is
+// finished on su, beside the next level's ID; level_done must then order its
+// users after su.
+int compress(ls_handle* H, cudaStream_t st, const LevelDone& level_done = LevelDone(), cudaStream_t su = nullptr);
 // Kernel blocks the merges need: the leaf self-interaction block, and the sibling
 // block of level l (once the level's skeleton is known).
 int leaf_block(ls_handle* H, cudaStream_t st);

@@ -379,10 +379,12 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
   // that its blocks are scheduled first when the merges occupy the SMs
   int prio_low = 0, prio_high = 0;
   LS_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
-  cudaStream_t sm = nullptr, sc = nullptr;
+  // su: the ID back substitutions (a level's U), beside the next level's ID on sc
+  cudaStream_t sm = nullptr, sc = nullptr, su = nullptr;
   LS_CUDA_TRY(cudaStreamCreateWithPriority(&sm, cudaStreamNonBlocking, prio_low));
   LS_CUDA_TRY(cudaStreamCreateWithPriority(&sc, cudaStreamNonBlocking, prio_high));
-  std::vector<cudaEvent_t> ev(L + 3, nullptr);
+  LS_CUDA_TRY(cudaStreamCreateWithPriority(&su, cudaStreamNonBlocking, prio_high));
+  std::vector<cudaEvent_t> ev(L + 4, nullptr);
   for (auto& e : ev) LS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   LS_CUDA_TRY(cudaEventRecord(ev[0], st));  // kernel table, spectrum, b: ready for both stages
   LS_CUDA_TRY(cudaStreamWaitEvent(sc, ev[0], 0));
@@ -410,7 +412,7 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
     mrc = r;
   });
   auto level_done = [&](int level) {
-    cudaEventRecord(ev[level], sc);
+    cudaEventRecord(ev[level], su);  // su has passed sc's work of this level (compress orders it)
     {
       std::lock_guard<std::mutex> lk(mu);
       ready = level;
@@ -420,7 +422,7 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
   int rc;
   {
     ls::StreamScope scope(sc);
-    rc = ls::compress(H, sc, level_done);
+    rc = ls::compress(H, sc, level_done, su);
   }
   if (rc) {
     std::lock_guard<std::mutex> lk(mu);
@@ -434,11 +436,14 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
   }
   cudaEventRecord(ev[L + 1], sm);
   cudaEventRecord(ev[L + 2], sc);
+  cudaEventRecord(ev[L + 3], su);
+  cudaStreamWaitEvent(st, ev[L + 3], 0);
   cudaStreamWaitEvent(st, ev[L + 1], 0);
   cudaStreamWaitEvent(st, ev[L + 2], 0);
   for (auto& e : ev) cudaEventDestroy(e);
   cudaStreamDestroy(sm);
   cudaStreamDestroy(sc);
+  cudaStreamDestroy(su);
   return rc;
 }
 
