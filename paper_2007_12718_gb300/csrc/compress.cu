@@ -1134,14 +1134,15 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
   const int tneed = (p + 31) / 32;
   const int t_cl_max = sizeof(R) == 4 ? 20 : 8;
   int reg_mode = 0;  // 1 cluster, 2 grid
-  // grid kernel: spread the candidates over two thirds of the SMs (cpb per block,
-  // four warps each).  The build runs the merges of lower levels beside the ID;
-  // a merge block placed on an SM of this latency-bound kernel runs many times
-  // slower and holds up its whole launch, so the kernel also takes nearly all of
-  // its SMs' shared memory (no merge kernel fits beside it) and leaves the other
-  // third of the SMs to the merges.  Measured cost on the ID: ~5 % at 760
-  // candidates against a spread over every SM.
-  const int nsm_id = std::max(1, nsm - nsm / 3);
+  // grid kernel: spread the candidates over two fifths of the SMs (cpb per block,
+  // at most 8, four warps each).  The build runs the merges of lower levels beside
+  // the ID, and with the back substitution moved beside the next level's ID the
+  // merge chain became the longer path: leaving three fifths of the SMs to the
+  // merges measured best (15.0 -> 14.7 ms per build + solve at 256^2; a third:
+  // slower merges, three quarters: slower IDs).  A merge block placed on an SM of
+  // this latency-bound kernel runs many times slower and holds up its whole
+  // launch, so the kernel also takes nearly all of its SMs' shared memory.
+  const int nsm_id = std::max(1, nsm - (nsm * 3) / 5);
   const int cpb = std::min(8, std::max(1, (m + nsm_id - 1) / nsm_id));
   int treg = 0, clr = (m + 31) / 32, nblk_r = (m + cpb - 1) / cpb;
   const void* kreg = nullptr;
