@@ -182,6 +182,104 @@ __global__ void __launch_bounds__(256) gemm64_kernel(int M, int N, int K, cx<R> 
     }
 }
 
+// FP32 complex GEMM with packed two-lane FMAs (fma.rn.f32x2): the same 64 x 64
+// tile, 4 x 4 outputs per thread and K loop as gemm64_kernel, with each complex
+// multiply-add as two packed FMAs on (re, im) pairs instead of four scalar ones
+// (in the same order as fma_, so the results are the same bits):
+//   acc += (-a.im, a.im) * (b.im, b.re);  acc += (a.re, a.re) * (b.re, b.im).
+// The operand tiles are staged in shared memory already in those forms.
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+  return ((unsigned long long)__float_as_uint(hi) << 32) | (unsigned long long)__float_as_uint(lo);
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) gemm64x2_kernel(int M, int N, int K, c32 alpha, const c32* __restrict__ A,
+                                                       int lda, long long sA, const c32* __restrict__ B, int ldb,
+                                                       long long sB, c32 beta, c32* __restrict__ C, int ldc,
+                                                       long long sC) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ ulonglong2 As[BK][BM + 1];  // x = (re, re), y = (-im, im)
+  __shared__ ulonglong2 Bs[BK][BN + 1];  // x = (re, im), y = (im, re)
+  const int b = blockIdx.z;
+  A += b * sA;
+  B += b * sB;
+  C += b * sC;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  unsigned long long acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0ULL;
+  for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int t = threadIdx.x + 256 * r;
+      int kk, i;
+      if (TA) {
+        i = t % BM;
+        kk = t / BM;
+      } else {
+        kk = t % BK;
+        i = t / BK;
+      }
+      int gi = m0 + i, gk = k0 + kk;
+      c32 v = mk<float>(0, 0);
+      if (gi < M && gk < K) v = TA ? A[(long long)gk * lda + gi] : A[(long long)gi * lda + gk];
+      As[kk][i] = make_ulonglong2(pk2(v.re, v.re), pk2(-v.im, v.im));
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int t = threadIdx.x + 256 * r;
+      int kk, j;
+      if (TB) {
+        kk = t % BK;
+        j = t / BK;
+      } else {
+        j = t % BN;
+        kk = t / BN;
+      }
+      int gj = n0 + j, gk = k0 + kk;
+      c32 v = mk<float>(0, 0);
+      if (gj < N && gk < K) v = TB ? B[(long long)gj * ldb + gk] : B[(long long)gk * ldb + gj];
+      Bs[kk][j] = make_ulonglong2(pk2(v.re, v.im), pk2(v.im, v.re));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      ulonglong2 a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = ffma2(a[i].x, bb[j].x, ffma2(a[i].y, bb[j].y, acc[i][j]));
+    }
+    __syncthreads();
+  }
+  const bool zb = (beta.re == 0.0f && beta.im == 0.0f);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int gi = m0 + ty + 16 * i, gj = n0 + tx + 16 * j;
+      if (gi < M && gj < N) {
+        const c32 av = mk<float>(__uint_as_float((unsigned)acc[i][j]), __uint_as_float((unsigned)(acc[i][j] >> 32)));
+        c32 v = alpha * av;
+        if (!zb) v = v + beta * C[(long long)gi * ldc + gj];
+        C[(long long)gi * ldc + gj] = v;
+      }
+    }
+}
+
 // Engine of the FP32 merge GEMMs for the build in progress on this thread:
 // 0 = SIMT FP32, 1 = tensor cores tf32, 2 = tensor cores tf32x3.
 thread_local int g_tc_engine = 0;
@@ -204,6 +302,21 @@ void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, cx<R> alpha, c
   // 64 x 64 tiles unless they leave most SMs idle (then 32 x 32 tiles: four times the blocks)
   if (M >= 48 && N >= 48 && (long long)((N + 63) / 64) * ((M + 63) / 64) * batch >= 128) {
     dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
+    if constexpr (sizeof(R) == 4) {
+      const c32* A2 = reinterpret_cast<const c32*>(A);
+      const c32* B2 = reinterpret_cast<const c32*>(B);
+      c32* C2 = reinterpret_cast<c32*>(C);
+      const c32 al = *reinterpret_cast<const c32*>(&alpha), be = *reinterpret_cast<const c32*>(&beta);
+      if (!ta && !tb)
+        gemm64x2_kernel<false, false><<<grid, 256, 0, st>>>(M, N, K, al, A2, lda, sA, B2, ldb, sB, be, C2, ldc, sC);
+      else if (ta && !tb)
+        gemm64x2_kernel<true, false><<<grid, 256, 0, st>>>(M, N, K, al, A2, lda, sA, B2, ldb, sB, be, C2, ldc, sC);
+      else if (!ta && tb)
+        gemm64x2_kernel<false, true><<<grid, 256, 0, st>>>(M, N, K, al, A2, lda, sA, B2, ldb, sB, be, C2, ldc, sC);
+      else
+        gemm64x2_kernel<true, true><<<grid, 256, 0, st>>>(M, N, K, al, A2, lda, sA, B2, ldb, sB, be, C2, ldc, sC);
+      return;
+    }
     if (!ta && !tb)
       gemm64_kernel<R, false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
     else if (ta && !tb)
