@@ -29,12 +29,18 @@ namespace {
 // ---------------------------------------------------------------- GEMM
 constexpr int TM = 32, TN = 32, TK = 16;
 
+// Outputs a GEMM leaves untouched: rows and columns in [lo, hi) (empty by default).
+struct Band {
+  int lo = 0, hi = 0;
+  __host__ __device__ bool skip(int i, int j) const { return (i >= lo && i < hi) || (j >= lo && j < hi); }
+};
+
 // C[b] = alpha op(A[b]) op(B[b]) + beta C[b]   (row-major, op = N or T)
 template <class R, bool TA, bool TB>
 __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, cx<R> alpha, const cx<R>* __restrict__ A,
                                                    int lda, long long sA, const cx<R>* __restrict__ B, int ldb,
                                                    long long sB, cx<R> beta, cx<R>* __restrict__ C, int ldc,
-                                                   long long sC) {
+                                                   long long sC, Band bd) {
   __shared__ cx<R> As[TK][TM + 1];
   __shared__ cx<R> Bs[TK][TN + 1];
   const int b = blockIdx.z;
@@ -91,7 +97,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, cx<R> al
   for (int i = 0; i < 2; ++i)
     for (int j = 0; j < 2; ++j) {
       int gi = m0 + ty + 16 * i, gj = n0 + tx + 16 * j;
-      if (gi < M && gj < N) {
+      if (gi < M && gj < N && !bd.skip(gi, gj)) {
         cx<R> v = alpha * acc[i][j];
         if (!zb) v = v + beta * C[(long long)gi * ldc + gj];
         C[(long long)gi * ldc + gj] = v;
@@ -105,7 +111,7 @@ template <class R, bool TA, bool TB>
 __global__ void __launch_bounds__(256) gemm64_kernel(int M, int N, int K, cx<R> alpha, const cx<R>* __restrict__ A,
                                                      int lda, long long sA, const cx<R>* __restrict__ B, int ldb,
                                                      long long sB, cx<R> beta, cx<R>* __restrict__ C, int ldc,
-                                                     long long sC) {
+                                                     long long sC, Band bd) {
   constexpr int BM = 64, BN = 64, BK = 16;
   __shared__ cx<R> As[BK][BM + 1];
   __shared__ cx<R> Bs[BK][BN + 1];
@@ -174,7 +180,7 @@ __global__ void __launch_bounds__(256) gemm64_kernel(int M, int N, int K, cx<R> 
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int gi = m0 + ty + 16 * i, gj = n0 + tx + 16 * j;
-      if (gi < M && gj < N) {
+      if (gi < M && gj < N && !bd.skip(gi, gj)) {
         cx<R> v = alpha * acc[i][j];
         if (!zb) v = v + beta * C[(long long)gi * ldc + gj];
         C[(long long)gi * ldc + gj] = v;
@@ -202,7 +208,7 @@ template <bool TA, bool TB>
 __global__ void __launch_bounds__(256) gemm64x2_kernel(int M, int N, int K, c32 alpha, const c32* __restrict__ A,
                                                        int lda, long long sA, const c32* __restrict__ B, int ldb,
                                                        long long sB, c32 beta, c32* __restrict__ C, int ldc,
-                                                       long long sC) {
+                                                       long long sC, Band bd) {
   constexpr int BM = 64, BN = 64, BK = 16;
   __shared__ ulonglong2 As[BK][BM + 1];  // x = (re, re), y = (-im, im)
   __shared__ ulonglong2 Bs[BK][BN + 1];  // x = (re, im), y = (im, re)
@@ -271,7 +277,7 @@ __global__ void __launch_bounds__(256) gemm64x2_kernel(int M, int N, int K, c32 
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int gi = m0 + ty + 16 * i, gj = n0 + tx + 16 * j;
-      if (gi < M && gj < N) {
+      if (gi < M && gj < N && !bd.skip(gi, gj)) {
         const c32 av = mk<float>(__uint_as_float((unsigned)acc[i][j]), __uint_as_float((unsigned)(acc[i][j] >> 32)));
         c32 v = alpha * av;
         if (!zb) v = v + beta * C[(long long)gi * ldc + gj];
@@ -287,12 +293,15 @@ thread_local int* g_tc_err = nullptr;
 
 template <class R>
 void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, cx<R> alpha, const cx<R>* A, int lda, long long sA,
-          const cx<R>* B, int ldb, long long sB, cx<R> beta, cx<R>* C, int ldc, long long sC, int batch) {
+          const cx<R>* B, int ldb, long long sB, cx<R> beta, cx<R>* C, int ldc, long long sC, int batch,
+          Band bd = Band()) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   if (K <= 0) return;  // only reached with beta = 1 (nothing to add)
   // tensor cores for the large products only: below ~2.5e8 complex MACs the
   // packing passes and launches of the tcgen05 path cost more than they save
-  if (sizeof(R) == 4 && g_tc_engine > 0 && M >= 256 && N >= 256 && (double)M * N * K * batch >= 2.5e8) {
+  // (a product with a band left untouched stays on the SIMT kernels)
+  if (sizeof(R) == 4 && g_tc_engine > 0 && bd.hi <= bd.lo && M >= 256 && N >= 256 &&
+      (double)M * N * K * batch >= 2.5e8) {
     tc_cgemm(st, ta, tb, M, N, K, *reinterpret_cast<const c32*>(&alpha), reinterpret_cast<const c32*>(A), lda, sA,
              reinterpret_cast<const c32*>(B), ldb, sB, *reinterpret_cast<const c32*>(&beta),
              reinterpret_cast<c32*>(C), ldc, sC, batch, g_tc_engine == 2 ? 1 : 0, g_tc_err);
@@ -308,34 +317,34 @@ void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, cx<R> alpha, c
       c32* C2 = reinterpret_cast<c32*>(C);
       const c32 al = *reinterpret_cast<const c32*>(&alpha), be = *reinterpret_cast<const c32*>(&beta);
       if (!ta && !tb)
-        gemm64x2_kernel<false, false><<<grid, 256, 0, st>>>(M, N, K, al, A2, lda, sA, B2, ldb, sB, be, C2, ldc, sC);
+        gemm64x2_kernel<false, false><<<grid, 256, 0, st>>>(M, N, K, al, A2, lda, sA, B2, ldb, sB, be, C2, ldc, sC, bd);
       else if (ta && !tb)
-        gemm64x2_kernel<true, false><<<grid, 256, 0, st>>>(M, N, K, al, A2, lda, sA, B2, ldb, sB, be, C2, ldc, sC);
+        gemm64x2_kernel<true, false><<<grid, 256, 0, st>>>(M, N, K, al, A2, lda, sA, B2, ldb, sB, be, C2, ldc, sC, bd);
       else if (!ta && tb)
-        gemm64x2_kernel<false, true><<<grid, 256, 0, st>>>(M, N, K, al, A2, lda, sA, B2, ldb, sB, be, C2, ldc, sC);
+        gemm64x2_kernel<false, true><<<grid, 256, 0, st>>>(M, N, K, al, A2, lda, sA, B2, ldb, sB, be, C2, ldc, sC, bd);
       else
-        gemm64x2_kernel<true, true><<<grid, 256, 0, st>>>(M, N, K, al, A2, lda, sA, B2, ldb, sB, be, C2, ldc, sC);
+        gemm64x2_kernel<true, true><<<grid, 256, 0, st>>>(M, N, K, al, A2, lda, sA, B2, ldb, sB, be, C2, ldc, sC, bd);
       return;
     }
     if (!ta && !tb)
-      gemm64_kernel<R, false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+      gemm64_kernel<R, false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, bd);
     else if (ta && !tb)
-      gemm64_kernel<R, true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+      gemm64_kernel<R, true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, bd);
     else if (!ta && tb)
-      gemm64_kernel<R, false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+      gemm64_kernel<R, false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, bd);
     else
-      gemm64_kernel<R, true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+      gemm64_kernel<R, true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, bd);
     return;
   }
   dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, batch);
   if (!ta && !tb)
-    gemm_kernel<R, false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    gemm_kernel<R, false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, bd);
   else if (ta && !tb)
-    gemm_kernel<R, true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    gemm_kernel<R, true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, bd);
   else if (!ta && tb)
-    gemm_kernel<R, false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    gemm_kernel<R, false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, bd);
   else
-    gemm_kernel<R, true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+    gemm_kernel<R, true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, bd);
 }
 
 template <class R>
@@ -991,44 +1000,81 @@ __global__ void set_identity_kernel(cx<R>* X, int n, int lda, long long sX, int 
 //   Ab = Ab^-1                                         (in shared memory)
 //   Rb = Ab Mb;   X += -Cb Rb;   X[:,J] = -Cb Ab       (three batched GEMMs)
 //   X[J,:] = Rb, X[J,J] = Ab                           (finalize)
-// Panel J = [k0, k0 + w) of the blocked Gauss-Jordan inverse: Ab = X[J, J];
-// Mb = X[J, :] with the columns J replaced by the identity (so that
-// Rb = Ab^-1 Mb carries Ab^-1 in those columns); Cb = X[:, J] with the rows J
-// zeroed, and X[i, J] = 0 for rows i outside J (the single update
-// X -= Cb Rb then leaves -X[:, J] Ab^-1 there).
+// Lookahead form of the blocked Gauss-Jordan sweep (invert_batch_lookahead):
+// the rank-w update of panel J = [k0, k0 + w) (X -= Cb Rb with the columns J of
+// Rb zero, then X[:, J] = -Cb A^-1 and X[J, :] = Rb, A^-1 in the columns J)
+// leaves the rows and columns of the next panel J' = [k1, k1 + w1) untouched;
+// this kernel forms panel J''s operands with that update applied on the fly,
+// so that J' is inverted while the rest of the update runs on a second stream:
+//   Ab = X[J', J'] - Cb[J', :] Rb[:, J'],
+//   Mb = X[J', :] - Cb[J', :] Rb (columns J: -Cb[J', :] A^-1; columns J': 0),
+//   Cb' = X[:, J'] - Cb Rb[:, J'] (rows J: Rb[:, J']; rows J': 0).
+// With w = 0 (no pending panel) it is the plain extract.
 template <class R>
-__global__ void gjb_extract_kernel(cx<R>* X, int n, int lda, long long sX, int k0, int w, cx<R>* Ab, cx<R>* Mb,
-                                   cx<R>* Cb) {
+__global__ void gjb_extract_la_kernel(const cx<R>* __restrict__ X, int n, int lda, long long sX, int k0, int w,
+                                      const cx<R>* __restrict__ Cbp, const cx<R>* __restrict__ Rbp,
+                                      const cx<R>* __restrict__ Aip, int k1, int w1, cx<R>* __restrict__ Ab,
+                                      cx<R>* __restrict__ Mb, cx<R>* __restrict__ Cb) {
   const int b = blockIdx.y;
-  cx<R>* M = X + b * sX;
-  const long long tot = (long long)n * w;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    // Mb: w x n (row r of J, column c)
-    int r = (int)(t / n), c = (int)(t % n);
-    bool inJc = c >= k0 && c < k0 + w;
-    Mb[b * tot + t] = inJc ? mk<R>(c - k0 == r ? R(1) : R(0), R(0)) : M[(long long)(k0 + r) * lda + c];
-    if (inJc) Ab[(long long)b * w * w + r * w + (c - k0)] = M[(long long)(k0 + r) * lda + c];
-    // Cb: n x w (row i, column q of J)
-    int i = (int)(t / w), q = (int)(t % w);
-    bool inJr = i >= k0 && i < k0 + w;
-    if (inJr) {
-      Cb[b * tot + t] = mk<R>(0, 0);
-    } else {
-      cx<R>* e = M + (long long)i * lda + k0 + q;
-      Cb[b * tot + t] = *e;
-      *e = mk<R>(0, 0);
+  const cx<R>* M = X + b * sX;
+  const cx<R>* cbp = Cbp + (long long)b * n * w;  // n x w
+  const cx<R>* rbp = Rbp + (long long)b * w * n;  // w x n
+  const cx<R>* aip = Aip + (long long)b * w * w;  // w x w
+  const long long t1 = (long long)w1 * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 2 * t1;
+       t += (long long)gridDim.x * blockDim.x) {
+    if (t < t1) {  // Mb: row r of J', column c
+      const int r = (int)(t / n), c = (int)(t % n);
+      const cx<R>* crow = cbp + (long long)(k1 + r) * w;
+      cx<R> v;
+      if (c >= k0 && c < k0 + w) {
+        cx<R> acc = mk<R>(0, 0);
+#pragma unroll 8
+        for (int q = 0; q < w; ++q) fma_(acc, crow[q], aip[q * w + (c - k0)]);
+        v = mk<R>(-acc.re, -acc.im);
+      } else {
+        cx<R> acc = mk<R>(0, 0);
+#pragma unroll 8
+        for (int q = 0; q < w; ++q) fma_(acc, crow[q], rbp[(long long)q * n + c]);
+        v = M[(long long)(k1 + r) * lda + c] - acc;
+      }
+      if (c >= k1 && c < k1 + w1) {
+        Ab[(long long)b * w1 * w1 + r * w1 + (c - k1)] = v;
+        Mb[b * t1 + t] = mk<R>(0, 0);
+      } else {
+        Mb[b * t1 + t] = v;
+      }
+    } else {  // Cb': row i, column q of J'
+      const long long u = t - t1;
+      const int i = (int)(u / w1), q = (int)(u % w1);
+      cx<R> v;
+      if (i >= k1 && i < k1 + w1) {
+        v = mk<R>(0, 0);
+      } else if (i >= k0 && i < k0 + w) {
+        v = rbp[(long long)(i - k0) * n + k1 + q];
+      } else {
+        const cx<R>* crow = cbp + (long long)i * w;
+        cx<R> acc = mk<R>(0, 0);
+#pragma unroll 8
+        for (int p = 0; p < w; ++p) fma_(acc, crow[p], rbp[(long long)p * n + k1 + q]);
+        v = M[(long long)i * lda + k1 + q] - acc;
+      }
+      Cb[b * t1 + u] = v;
     }
   }
 }
 
+// Rows J of the lookahead sweep: X[J, :] = Rb, with A^-1 in the columns J.
 template <class R>
-__global__ void gjb_finalize_kernel(cx<R>* X, int n, int lda, long long sX, int k0, int w, const cx<R>* Rb) {
+__global__ void gjb_finalize_la_kernel(cx<R>* X, int n, int lda, long long sX, int k0, int w,
+                                       const cx<R>* __restrict__ Ai, const cx<R>* __restrict__ Rb) {
   const int b = blockIdx.y;
   cx<R>* M = X + b * sX;
   const long long tot = (long long)n * w;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    int r = (int)(t / n), c = (int)(t % n);
-    M[(long long)(k0 + r) * lda + c] = Rb[b * tot + t];  // rows J: Ab^-1 X[J, :] (Ab^-1 in the columns J)
+    const int r = (int)(t / n), c = (int)(t % n);
+    M[(long long)(k0 + r) * lda + c] =
+        (c >= k0 && c < k0 + w) ? Ai[(long long)b * w * w + r * w + (c - k0)] : Rb[b * tot + t];
   }
 }
 
@@ -1077,27 +1123,80 @@ void gemv(cudaStream_t st, bool ta, int M, int K, cx<R> alpha, const cx<R>* A, i
 template <class R>
 int invert_batch_nopiv(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int P, void* scratch,
                        size_t scratch_bytes, cudaStream_t st) {
+  // Blocked Gauss-Jordan sweep over 64-wide panels with one panel of lookahead:
+  // on st, panel i's operands are formed (with panel i-1's pending update applied
+  // on the fly), its diagonal block inverted and Rb = A^-1 Mb formed; on a second
+  // stream, panel i's update of everything but the rows and columns of panel i+1,
+  // then X[:, J] = -Cb A^-1 and X[J, :] = Rb.  So each panel's inverse runs while
+  // the previous panel's update does.  Panel buffers alternate by parity.
   const int nb = 64;  // panel width: a 64-wide panel inverse takes ~1/4 the time of a 128-wide one
-  const size_t w_max = nb;
-  cx<R>* Ab = reinterpret_cast<cx<R>*>(scratch);
-  cx<R>* Mb = Ab + (size_t)P * w_max * w_max;
-  cx<R>* Cb = Mb + (size_t)P * w_max * n;
-  cx<R>* Rb = Cb + (size_t)P * w_max * n;
-  if (sizeof(cx<R>) * (size_t)P * (w_max * w_max + 3 * w_max * n) > scratch_bytes) return LS_ENOMEM;
-  const cx<R> mone = mk<R>(R(-1), R(0));
-  for (int k0 = 0; k0 < n; k0 += nb) {
-    const int w = std::min(nb, n - k0);
-    const long long tot = (long long)n * w;
-    dim3 g((unsigned)std::min<long long>(1024, (tot + 255) / 256), P);
-    count_launch();
-    gjb_extract_kernel<R><<<g, 256, 0, st>>>(X, n, lda, sX, k0, w, Ab, Mb, Cb);
-    int rc = invert_reg_nopiv<R>(Ab, w, w, (long long)w * w, P, H->d_err + 3, st);
-    if (rc) return rc;
-    gemm<R>(st, false, false, w, n, w, one<R>(), Ab, w, (long long)w * w, Mb, n, tot, zero<R>(), Rb, n, tot, P);
-    gemm<R>(st, false, false, n, n, w, mone, Cb, w, tot, Rb, n, tot, one<R>(), X, lda, sX, P);
-    count_launch();
-    gjb_finalize_kernel<R><<<g, 256, 0, st>>>(X, n, lda, sX, k0, w, Rb);
+  const int np = (n + nb - 1) / nb;
+  const size_t wm = nb;
+  if (sizeof(cx<R>) * (size_t)P * (2 * wm * wm + 5 * wm * (size_t)n) > scratch_bytes) return LS_ENOMEM;
+  cx<R>* p = reinterpret_cast<cx<R>*>(scratch);
+  cx<R>* Ab[2];
+  cx<R>* Cb[2];
+  cx<R>* Rb[2];
+  for (int q = 0; q < 2; ++q) {
+    Ab[q] = p;
+    p += (size_t)P * wm * wm;
+    Cb[q] = p;
+    p += (size_t)P * wm * n;
+    Rb[q] = p;
+    p += (size_t)P * wm * n;
   }
+  cx<R>* Mb = p;
+  if (!H->inv_stream) LS_CUDA_TRY(cudaStreamCreateWithFlags(&H->inv_stream, cudaStreamNonBlocking));
+  cudaStream_t sb = H->inv_stream;
+  std::vector<cudaEvent_t> evR(np), evU(np);
+  cudaEvent_t ev0;
+  LS_CUDA_TRY(cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming));
+  for (int i = 0; i < np; ++i) {
+    LS_CUDA_TRY(cudaEventCreateWithFlags(&evR[i], cudaEventDisableTiming));
+    LS_CUDA_TRY(cudaEventCreateWithFlags(&evU[i], cudaEventDisableTiming));
+  }
+  struct Events {
+    std::vector<cudaEvent_t>& a;
+    std::vector<cudaEvent_t>& b;
+    cudaEvent_t e;
+    ~Events() {
+      for (auto x : a) cudaEventDestroy(x);
+      for (auto x : b) cudaEventDestroy(x);
+      cudaEventDestroy(e);
+    }
+  } events{evR, evU, ev0};
+  LS_CUDA_TRY(cudaEventRecord(ev0, st));
+  LS_CUDA_TRY(cudaStreamWaitEvent(sb, ev0, 0));
+  const cx<R> mone = mk<R>(R(-1), R(0));
+  for (int i = 0; i < np; ++i) {
+    const int k1 = i * nb, w1 = std::min(nb, n - k1), par = i & 1;
+    const int k0 = (i - 1) * nb, w = i > 0 ? nb : 0;  // the pending panel (all but the last are full)
+    const long long t1 = (long long)n * w1;
+    if (i >= 2) LS_CUDA_TRY(cudaStreamWaitEvent(st, evU[i - 2], 0));  // X after panel i-2; its buffers free
+    dim3 g((unsigned)std::min<long long>(1024, (2 * t1 + 255) / 256), P);
+    count_launch();
+    gjb_extract_la_kernel<R><<<g, 256, 0, st>>>(X, n, lda, sX, k0, w, Cb[par ^ 1], Rb[par ^ 1], Ab[par ^ 1], k1,
+                                                 w1, Ab[par], Mb, Cb[par]);
+    int rc = invert_reg_nopiv<R>(Ab[par], w1, w1, (long long)w1 * w1, P, H->d_err + 3, st);
+    if (rc) return rc;
+    gemm<R>(st, false, false, w1, n, w1, one<R>(), Ab[par], w1, (long long)w1 * w1, Mb, n, t1, zero<R>(), Rb[par], n,
+            t1, P);
+    LS_CUDA_TRY(cudaEventRecord(evR[i], st));
+    LS_CUDA_TRY(cudaStreamWaitEvent(sb, evR[i], 0));
+    Band band;  // the next panel's rows and columns: its operands carry this update
+    if (i + 1 < np) {
+      band.lo = k1 + w1;
+      band.hi = std::min(n, k1 + w1 + nb);
+    }
+    gemm<R>(sb, false, false, n, n, w1, mone, Cb[par], w1, t1, Rb[par], n, t1, one<R>(), X, lda, sX, P, band);
+    gemm<R>(sb, false, false, n, w1, w1, mone, Cb[par], w1, t1, Ab[par], w1, (long long)w1 * w1, zero<R>(), X + k1,
+            lda, sX, P);
+    dim3 gf((unsigned)std::min<long long>(1024, (t1 + 255) / 256), P);
+    count_launch();
+    gjb_finalize_la_kernel<R><<<gf, 256, 0, sb>>>(X, n, lda, sX, k1, w1, Ab[par], Rb[par]);
+    LS_CUDA_TRY(cudaEventRecord(evU[i], sb));
+  }
+  LS_CUDA_TRY(cudaStreamWaitEvent(st, evU[np - 1], 0));
   return check_launch("inverse_blocked_nopiv");
 }
 

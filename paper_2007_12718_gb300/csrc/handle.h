@@ -65,6 +65,7 @@ struct ls_handle {
   std::vector<int> apply_phase_end_t;  // host copy: index of the last operation of each phase
   double flops_build = 0, flops_compress = 0, bytes_apply = 0, factor_bytes = 0;
   int pivot_fallbacks = 0;      // merge levels that needed the row-pivoted inverse
+  cudaStream_t inv_stream = nullptr;  // second stream of the blocked inverse (panel updates)
 
   // receivers (Eq. (1)): positions (device, nr x 2) and R[k][j] = h^2 G(|r_k - x_j|)
   double* rx = nullptr;

@@ -363,6 +363,7 @@ void ls_free(ls_handle* H) {
   f(H->rx);
   f(H->Rrec);
   if (H->apply_exec) cudaGraphExecDestroy(H->apply_exec);
+  if (H->inv_stream) cudaStreamDestroy(H->inv_stream);
   delete H;
 }
 
