@@ -1289,6 +1289,8 @@ TreeGeom make_geom(const ls_handle* H) {
   return g;
 }
 
+int apply_persistent_init(ls_handle* H, cudaStream_t st);
+
 template <class R>
 int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
   const int L = H->L, n = H->s * H->s;
@@ -1507,6 +1509,9 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
     H->work_bytes = sizeof(cx<R>) * vec;
     if ((rc = dalloc(&H->work, H->work_bytes))) return rc;
   }
+  // the persistent apply's transposes and operation list, here rather than at the
+  // first apply: the build already ends with a synchronisation
+  if ((rc = apply_persistent_init(H, st))) return rc;
   int* pin = static_cast<int*>(pinned_scratch(sizeof(int)));
   if (!pin) return LS_ENOMEM;
   LS_CUDA_TRY(cudaMemcpyAsync(pin, H->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -266,8 +266,7 @@ int conv_setup(ls_handle* H, cudaStream_t st) {
   quarter_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(full, H->Lx, H->logLx, H->Ly, H->logLy, nx, ny,
                                                               H->spec, 1.0 / ((double)H->Lx * H->Ly));
   if ((rc = check_launch("conv_setup"))) return rc;
-  LS_CUDA_TRY(cudaStreamSynchronize(st));
-  ls::dfree(full);
+  ls::dfree(full);  // stream-ordered: released after the kernels above
   return LS_OK;
 }
 

@@ -331,6 +331,11 @@ int ls_cgemm_c64(int engine, int ta, int tb, int M, int N, int K, const float* a
 
 void ls_free(ls_handle* H) {
   if (!H) return;
+  if (H->side_stream) {  // the spectrum set-up may still run after a failed build
+    cudaStreamSynchronize(H->side_stream);
+    cudaStreamDestroy(H->side_stream);
+    H->side_stream = nullptr;
+  }
   ls::StreamScope scope(H->stream);
   auto f = [](void* p) { ls::dfree(p); };
   f(H->spec);
@@ -543,18 +548,37 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
   LS_CUDA_TRY(cudaMemsetAsync(H->d_err, 0, sizeof(int) * 4, st));
   count_launch();
   check_b_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(H->b, N, H->d_err + 1);
+  if ((rc = ls::kernel_table_setup(H, st))) return rc;
+  // the FFT matvec's kernel spectrum is needed by the solve, not by the build:
+  // it is computed on a side stream beside the build
+  LS_CUDA_TRY(cudaStreamCreateWithFlags(&H->side_stream, cudaStreamNonBlocking));
+  cudaEvent_t ev_side;
+  LS_CUDA_TRY(cudaEventCreateWithFlags(&ev_side, cudaEventDisableTiming));
+  LS_CUDA_TRY(cudaEventRecord(ev_side, st));
+  LS_CUDA_TRY(cudaStreamWaitEvent(H->side_stream, ev_side, 0));
+  {
+    ls::StreamScope side(H->side_stream);
+    rc = ls::conv_setup(H, H->side_stream);
+  }
+  if (rc) {
+    cudaEventDestroy(ev_side);
+    return rc;
+  }
   int* pin = static_cast<int*>(ls::pinned_scratch(sizeof(int)));
   if (!pin) return LS_ENOMEM;
   LS_CUDA_TRY(cudaMemcpyAsync(pin, H->d_err + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
   LS_CUDA_TRY(cudaStreamSynchronize(st));
   const int bad = pin[0];
   if (bad) {
+    cudaEventDestroy(ev_side);
     set_error("b must be finite and <= 1");
     return LS_EINVAL;
   }
-  if ((rc = ls::kernel_table_setup(H, st))) return rc;
-  if ((rc = ls::conv_setup(H, st))) return rc;
-  return build_pipelined(H, st);
+  rc = build_pipelined(H, st);
+  // long finished by now: the handle is complete on return, for any stream
+  cudaStreamSynchronize(H->side_stream);
+  cudaEventDestroy(ev_side);
+  return rc;
 }
 
 int ls_build(const ls_grid* grid, double kappa, const double* b, double tol, const ls_opts* opts, void* stream,
