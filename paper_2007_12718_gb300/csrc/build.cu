@@ -1290,6 +1290,7 @@ TreeGeom make_geom(const ls_handle* H) {
 }
 
 int apply_persistent_init(ls_handle* H, cudaStream_t st);
+int level_transpose(ls_handle* H, int l, cudaStream_t st);
 
 template <class R>
 int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
@@ -1340,6 +1341,7 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
   // and X of level l is formed while level l is being compressed.
   for (int l = L - 1; l >= 0; --l) {
     if ((rc = sibling_block(H, l + 1, st))) return rc;  // G of the two children (Eq. 15)
+    if ((rc = level_transpose(H, l + 1, st))) return rc;  // U^T, G^T of level l + 1 for the apply
     LevelData& lv = H->lev[l];
     const LevelData& ch = H->lev[l + 1];
     const int P = 1 << l, kc = ch.k, n2 = 2 * kc;
@@ -2337,19 +2339,25 @@ std::vector<ApplyOp> apply_ops_transpose(ls_handle* H) {
 }
 
 // U^T and G^T of every level (the apply reads every product row-wise).
-int level_transposes(ls_handle* H, cudaStream_t st) {
+// U^T and G^T of level l (the build makes them as soon as U and G of the level
+// exist, off the end of the build).
+int level_transpose(ls_handle* H, int l, cudaStream_t st) {
   const bool fp64 = H->prec == LS_FP64;
   const size_t es = fp64 ? sizeof(z64) : sizeof(c32);
+  LevelData& lv = H->lev[l];
+  if (lv.UT) return LS_OK;
+  const int m = l == H->L ? H->s * H->s : 2 * H->lev[l + 1].k, k = lv.k;
   int rc;
-  for (int l = 1; l <= H->L; ++l) {
-    LevelData& lv = H->lev[l];
-    if (lv.UT) continue;
-    const int m = l == H->L ? H->s * H->s : 2 * H->lev[l + 1].k, k = lv.k;
-    if ((rc = dalloc(&lv.UT, es * (size_t)std::max(m * k, 1)))) return rc;
-    if ((rc = dalloc(&lv.GT, es * (size_t)std::max(k * k, 1)))) return rc;
-    if ((rc = transpose_batch(fp64, lv.U, m, k, 1, lv.UT, st))) return rc;
-    if ((rc = transpose_batch(fp64, lv.Gsib, k, k, 1, lv.GT, st))) return rc;
-  }
+  if ((rc = dalloc(&lv.UT, es * (size_t)std::max(m * k, 1)))) return rc;
+  if ((rc = dalloc(&lv.GT, es * (size_t)std::max(k * k, 1)))) return rc;
+  if ((rc = transpose_batch(fp64, lv.U, m, k, 1, lv.UT, st))) return rc;
+  return transpose_batch(fp64, lv.Gsib, k, k, 1, lv.GT, st);
+}
+
+int level_transposes(ls_handle* H, cudaStream_t st) {
+  int rc;
+  for (int l = 1; l <= H->L; ++l)
+    if ((rc = level_transpose(H, l, st))) return rc;
   return LS_OK;
 }
 

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <mutex>
 #include <thread>
 #include <condition_variable>
@@ -32,6 +33,18 @@ bool is_device_ptr(const void* p) {
 }
 
 int valid_order(int o) { return o == 2 || o == 4 || o == 6 || o == 8 || o == 10; }
+
+// Host-side build timeline (LS_TRACE=1): "ls host <label> <ms since the build started>".
+std::chrono::steady_clock::time_point g_build_t0;
+void host_mark(const char* label) {
+  static const bool on = [] {
+    const char* v = getenv("LS_TRACE");
+    return v && v[0] && v[0] != '0';
+  }();
+  if (!on) return;
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - g_build_t0).count();
+  fprintf(stderr, "ls host %s %.3f\n", label, ms);
+}
 
 __global__ void rhs_kernel(const double* b, int nx, int ny, double h, double x0, double y0, double kappa, double ct,
                            double stt, ls::z64* f) {
@@ -426,16 +439,19 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
     cv.notify_all();
   };
   int rc;
+  host_mark("pipeline_started");
   {
     ls::StreamScope scope(sc);
     rc = ls::compress(H, sc, level_done, su);
   }
+  host_mark("compress_returned");
   if (rc) {
     std::lock_guard<std::mutex> lk(mu);
     abort = true;
   }
   cv.notify_all();
   merger.join();
+  host_mark("merges_joined");
   if (!rc && mrc) {
     rc = mrc;
     set_error(merr.c_str());
@@ -455,6 +471,7 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
 
 static int build_impl(const ls_grid* grid, double kappa, const double* b, double tol, const ls_opts* opts,
                       cudaStream_t st, ls_handle** out) {
+  g_build_t0 = std::chrono::steady_clock::now();
   ls_handle* H = new ls_handle();
   *out = H;
   H->stream = st;
@@ -574,7 +591,9 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
     set_error("b must be finite and <= 1");
     return LS_EINVAL;
   }
+  host_mark("setup_done");
   rc = build_pipelined(H, st);
+  host_mark("pipeline_done");
   // long finished by now: the handle is complete on return, for any stream
   cudaStreamSynchronize(H->side_stream);
   cudaEventDestroy(ev_side);
