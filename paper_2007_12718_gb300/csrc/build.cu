@@ -1519,8 +1519,13 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
   LS_CUDA_TRY(cudaMemcpyAsync(pin, H->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   LS_CUDA_TRY(cudaStreamSynchronize(st));
   if (pin[0]) return pin[0];
-  // bytes of one apply: every X, S, XBU read once, plus the leaf vectors
+  // bytes of one apply (Algorithm 2): every factor once, the X of levels L-1..1
+  // a second time (the upward and the downward pass both apply it), the grid vectors
   double fb = H->factor_bytes;
+  for (int l = 1; l <= L - 1; ++l) {
+    const double n2 = 2.0 * H->lev[l + 1].k;
+    fb += sizeof(cx<R>) * (double)(1 << l) * n2 * n2;
+  }
   H->bytes_apply = fb + (double)H->grid.nx * H->grid.ny * (16.0 * 2);
   return LS_OK;
 }
