@@ -223,40 +223,43 @@ __global__ void __launch_bounds__(256) gemm64x2_kernel(int M, int N, int K, c32 
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0ULL;
+  // the next K tile is loaded into registers while the current one is used
+  c32 pa[4], pb[4];
+  auto load_tiles = [&](int k0) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int t = threadIdx.x + 256 * r;
+      const int kk = TA ? t / BM : t % BK, i = TA ? t % BM : t / BK;
+      const int gi = m0 + i, gk = k0 + kk;
+      pa[r] = (gi < M && gk < K) ? (TA ? A[(long long)gk * lda + gi] : A[(long long)gi * lda + gk]) : mk<float>(0, 0);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int t = threadIdx.x + 256 * r;
+      const int kk = TB ? t % BK : t / BN, j = TB ? t / BK : t % BN;
+      const int gj = n0 + j, gk = k0 + kk;
+      pb[r] = (gj < N && gk < K) ? (TB ? B[(long long)gj * ldb + gk] : B[(long long)gk * ldb + gj]) : mk<float>(0, 0);
+    }
+  };
+  auto store_tiles = [&]() {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int t = threadIdx.x + 256 * r;
+      const int kk = TA ? t / BM : t % BK, i = TA ? t % BM : t / BK;
+      As[kk][i] = make_ulonglong2(pk2(pa[r].re, pa[r].re), pk2(-pa[r].im, pa[r].im));
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int t = threadIdx.x + 256 * r;
+      const int kk = TB ? t % BK : t / BN, j = TB ? t / BK : t % BN;
+      Bs[kk][j] = make_ulonglong2(pk2(pb[r].re, pb[r].im), pk2(pb[r].im, pb[r].re));
+    }
+  };
+  load_tiles(0);
   for (int k0 = 0; k0 < K; k0 += BK) {
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      int t = threadIdx.x + 256 * r;
-      int kk, i;
-      if (TA) {
-        i = t % BM;
-        kk = t / BM;
-      } else {
-        kk = t % BK;
-        i = t / BK;
-      }
-      int gi = m0 + i, gk = k0 + kk;
-      c32 v = mk<float>(0, 0);
-      if (gi < M && gk < K) v = TA ? A[(long long)gk * lda + gi] : A[(long long)gi * lda + gk];
-      As[kk][i] = make_ulonglong2(pk2(v.re, v.re), pk2(-v.im, v.im));
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      int t = threadIdx.x + 256 * r;
-      int kk, j;
-      if (TB) {
-        kk = t % BK;
-        j = t / BK;
-      } else {
-        j = t % BN;
-        kk = t / BN;
-      }
-      int gj = n0 + j, gk = k0 + kk;
-      c32 v = mk<float>(0, 0);
-      if (gj < N && gk < K) v = TB ? B[(long long)gj * ldb + gk] : B[(long long)gk * ldb + gj];
-      Bs[kk][j] = make_ulonglong2(pk2(v.re, v.im), pk2(v.im, v.re));
-    }
+    store_tiles();
     __syncthreads();
+    if (k0 + BK < K) load_tiles(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       ulonglong2 a[4], bb[4];
