@@ -621,6 +621,122 @@ __global__ void __launch_bounds__(1024) gj_reg_kernel(cx<R>* __restrict__ X, int
   }
 }
 
+// Register-blocked Gauss-Jordan inverse without interchanges (FP32), one
+// block per matrix: a TR x TC thread grid, each thread an RM x RN block of the
+// zero-padded matrix in registers.  At step k the owners of row k and of column
+// k put them in shared memory (row k's entry k replaced by 1, column k's by -1)
+// and the owner of entry (k, k) its reciprocal d; then every element becomes
+//   a[i][j] = z[i][j] - c[i] (d r[j]),   z = a with row k and column k zeroed,
+// which is the whole Gauss-Jordan step as one rank-1 formula: row k scaled by
+// d, column k set to -a[i][k] d, a[k][k] = d, the Schur update elsewhere.  Per
+// step a thread reads RN + RM values from shared memory for RM RN updates, each
+// two packed FMAs on (re, im) pairs.  A zero or non-finite pivot sets
+// *err = LS_ESINGULAR; the sweep runs on, and the caller's probe check rejects
+// the result.
+template <int TR, int TC, int RM, int RN>
+__global__ void __launch_bounds__(TR * TC) gj2d_kernel(c32* __restrict__ X, int n, int lda, long long sX,
+                                                       int* __restrict__ err) {
+  constexpr int KU = RM > RN ? RM : RN;
+  static_assert(KU % RM == 0 && KU % RN == 0 && KU % 2 == 0 && RN % 2 == 0 && RM % 2 == 0, "block shape");
+  __shared__ __align__(16) c32 rowk[2][TC * RN];
+  __shared__ __align__(16) c32 colk[2][TR * RM];
+  __shared__ c32 dk[2];
+  const int tid = threadIdx.x, tc = tid % TC, tr = tid / TC;
+  c32* M = X + blockIdx.x * sX;
+  unsigned long long a[RM][RN];
+#pragma unroll
+  for (int i = 0; i < RM; ++i) {
+    const int row = tr * RM + i;
+#pragma unroll
+    for (int j = 0; j < RN; ++j) {
+      const int col = tc * RN + j;
+      const c32 v = (row < n && col < n) ? M[(long long)row * lda + col] : mk<float>(0.f, 0.f);
+      a[i][j] = pk2(v.re, v.im);
+    }
+  }
+  const int nk = (n + KU - 1) / KU;
+  for (int kb = 0; kb < nk; ++kb) {
+#pragma unroll
+    for (int u = 0; u < KU; ++u) {
+      if (kb * KU + u >= n) break;
+      const int rg = kb * (KU / RM) + u / RM, ur = u % RM;  // owner row group and register row of k
+      const int cg = kb * (KU / RN) + u / RN, uc = u % RN;
+      const int buf = u & 1;
+      const bool rown = tr == rg, cown = tc == cg;
+      if (rown) {
+#pragma unroll
+        for (int v = 0; v < RN; ++v) {
+          float lo, hi;
+          asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a[ur][v]));
+          rowk[buf][tc * RN + v] = (cown && v == uc) ? mk<float>(1.f, 0.f) : mk<float>(lo, hi);
+        }
+      }
+      if (cown) {
+#pragma unroll
+        for (int v = 0; v < RM; ++v) {
+          float lo, hi;
+          asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a[v][uc]));
+          colk[buf][tr * RM + v] = (rown && v == ur) ? mk<float>(-1.f, 0.f) : mk<float>(lo, hi);
+        }
+        if (rown) {
+          float lo, hi;
+          asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a[ur][uc]));
+          const c32 p = mk<float>(lo, hi);
+          const float den = abs2(p);
+          if (!(den > 0.f) || !(den < INFINITY)) atomicExch(err, LS_ESINGULAR);
+          dk[buf] = inv(p);
+        }
+      }
+      __syncthreads();
+      const c32 d = dk[buf];
+      unsigned long long R1[RN], R2[RN];
+      const float4* rp = reinterpret_cast<const float4*>(&rowk[buf][tc * RN]);
+#pragma unroll
+      for (int v = 0; v < RN / 2; ++v) {
+        const float4 q = rp[v];
+        const c32 s0 = d * mk<float>(q.x, q.y), s1 = d * mk<float>(q.z, q.w);
+        R1[2 * v] = pk2(s0.re, s0.im);
+        R2[2 * v] = pk2(s0.im, s0.re);
+        R1[2 * v + 1] = pk2(s1.re, s1.im);
+        R2[2 * v + 1] = pk2(s1.im, s1.re);
+      }
+      if (rown) {
+#pragma unroll
+        for (int v = 0; v < RN; ++v) a[ur][v] = 0ull;
+      }
+      if (cown) {
+#pragma unroll
+        for (int v = 0; v < RM; ++v) a[v][uc] = 0ull;
+      }
+      const float4* cp = reinterpret_cast<const float4*>(&colk[buf][tr * RM]);
+#pragma unroll
+      for (int i2 = 0; i2 < RM / 2; ++i2) {
+        const float4 q = cp[i2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float cre = h ? q.z : q.x, cim = h ? q.w : q.y;
+          const unsigned long long C1 = pk2(-cre, -cre), C2 = pk2(cim, -cim);
+#pragma unroll
+          for (int j = 0; j < RN; ++j) a[2 * i2 + h][j] = ffma2(C1, R1[j], ffma2(C2, R2[j], a[2 * i2 + h][j]));
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < RM; ++i) {
+    const int row = tr * RM + i;
+#pragma unroll
+    for (int j = 0; j < RN; ++j) {
+      const int col = tc * RN + j;
+      if (row < n && col < n) {
+        float lo, hi;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a[i][j]));
+        M[(long long)row * lda + col] = mk<float>(lo, hi);
+      }
+    }
+  }
+}
+
 // Largest order handled by gj_reg_kernel (registers per thread: 2 CPT reals).
 template <class R>
 constexpr int gj_reg_max() {
@@ -632,6 +748,19 @@ int invert_reg_nopiv(cx<R>* X, int n, int lda, long long sX, int P, int* err, cu
   if (n <= 0 || P <= 0) return LS_OK;
   const unsigned thr = (unsigned)(((n * 8 + 31) / 32) * 32);
   count_launch();
+  if constexpr (sizeof(R) == 4) {
+    if (n <= 32)
+      gj2d_kernel<8, 8, 4, 4><<<P, 64, 0, st>>>(X, n, lda, sX, err);
+    else if (n <= 64)
+      gj2d_kernel<16, 16, 4, 4><<<P, 256, 0, st>>>(X, n, lda, sX, err);
+    else if (n <= 96)
+      gj2d_kernel<12, 24, 8, 4><<<P, 288, 0, st>>>(X, n, lda, sX, err);
+    else if (n <= 128)
+      gj2d_kernel<16, 32, 8, 4><<<P, 512, 0, st>>>(X, n, lda, sX, err);
+    else
+      return LS_EINVAL;
+    return check_launch("gj2d");
+  }
   if (n <= 32)
     gj_reg_kernel<R, 4><<<P, thr, 0, st>>>(X, n, lda, sX, err);
   else if (n <= 64)
@@ -996,88 +1125,81 @@ __global__ void set_identity_kernel(cx<R>* X, int n, int lda, long long sX, int 
 // Gauss-Jordan, nb columns per panel; each panel is one panel kernel, one
 // interchange/extract kernel and one batched GEMM X += Panel * Mb, so the
 // O(n^3) work is in the GEMM.
-// Blocked Gauss-Jordan without interchanges between diagonal blocks (the
-// merge matrices are I plus a perturbation, Sec. 4.3; partial pivoting stays
-// inside each diagonal block).  Per diagonal block J of width w:
-//   Ab = X[J,J], Mb = X[J,:] (zero on J), Cb = X[:,J] (zero on J)  (extract)
-//   Ab = Ab^-1                                         (in shared memory)
-//   Rb = Ab Mb;   X += -Cb Rb;   X[:,J] = -Cb Ab       (three batched GEMMs)
-//   X[J,:] = Rb, X[J,J] = Ab                           (finalize)
-// Lookahead form of the blocked Gauss-Jordan sweep (invert_batch_lookahead):
-// the rank-w update of panel J = [k0, k0 + w) (X -= Cb Rb with the columns J of
-// Rb zero, then X[:, J] = -Cb A^-1 and X[J, :] = Rb, A^-1 in the columns J)
-// leaves the rows and columns of the next panel J' = [k1, k1 + w1) untouched;
-// this kernel forms panel J''s operands with that update applied on the fly,
-// so that J' is inverted while the rest of the update runs on a second stream:
-//   Ab = X[J', J'] - Cb[J', :] Rb[:, J'],
-//   Mb = X[J', :] - Cb[J', :] Rb (columns J: -Cb[J', :] A^-1; columns J': 0),
-//   Cb' = X[:, J'] - Cb Rb[:, J'] (rows J: Rb[:, J']; rows J': 0).
-// With w = 0 (no pending panel) it is the plain extract.
+// Blocked Gauss-Jordan without interchanges (the merge matrices are I plus a
+// perturbation, Sec. 4.3; a probe check decides whether the pivoted sweep is
+// needed).  Per diagonal block J of width w: A = X[J,J], A^-1 in registers,
+// then one rank-w update of all of X.
+// Lookahead form of the blocked Gauss-Jordan sweep.  Panel J = [k0, k0 + w)
+// leaves Cb (n x w: X[:, J] with rows J set to -I) and Rb = A^-1 Mb (w x n:
+// the rows X[J, :] with columns J set to I, so Rb[:, J] = A^-1); with X[J, :]
+// and X[:, J] zeroed when they were read, the single update X -= Cb Rb writes
+// X[J, :] = Rb, X[:, J] = -Cb A^-1 and the Schur complement elsewhere.  That
+// update skips the rows and columns of the next panel J' = [k1, k1 + w1),
+// whose operands are formed with it applied on the fly:
+//   Ab = X[J', J'] - Cb[J', :] Rb[:, J']                 (gjb_diag_kernel)
+//   Mb = X[J', :] - Cb[J', :] Rb, columns J' set to I    (gjb_extract_kernel)
+//   Cb' = X[:, J'] - Cb Rb[:, J'], rows J' set to -I
+// With w = 0 (the first panel) there is no pending update.
 template <class R>
-__global__ void gjb_extract_la_kernel(const cx<R>* __restrict__ X, int n, int lda, long long sX, int k0, int w,
-                                      const cx<R>* __restrict__ Cbp, const cx<R>* __restrict__ Rbp,
-                                      const cx<R>* __restrict__ Aip, int k1, int w1, cx<R>* __restrict__ Ab,
-                                      cx<R>* __restrict__ Mb, cx<R>* __restrict__ Cb) {
+__global__ void gjb_diag_kernel(const cx<R>* __restrict__ X, int n, int lda, long long sX, int w,
+                                const cx<R>* __restrict__ Cbp, const cx<R>* __restrict__ Rbp, int k1, int w1,
+                                cx<R>* __restrict__ Ab) {
   const int b = blockIdx.y;
-  const cx<R>* M = X + b * sX;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= w1 * w1) return;
+  const int r = t / w1, q = t % w1;
+  const cx<R>* crow = Cbp + (long long)b * n * w + (long long)(k1 + r) * w;
+  const cx<R>* rcol = Rbp + (long long)b * w * n + k1 + q;
+  cx<R> acc = mk<R>(0, 0);
+#pragma unroll 8
+  for (int p = 0; p < w; ++p) fma_(acc, crow[p], rcol[(long long)p * n]);
+  Ab[(long long)b * w1 * w1 + t] = X[b * sX + (long long)(k1 + r) * lda + k1 + q] - acc;
+}
+
+// Mb and Cb' of panel J' (above); X[J', :] and X[:, J'] are zeroed once read.
+// The pending update skips these rows and columns, and each element is read
+// and zeroed by the same thread, so the kernel may run beside that update.
+template <class R>
+__global__ void gjb_extract_kernel(cx<R>* __restrict__ X, int n, int lda, long long sX, int w,
+                                   const cx<R>* __restrict__ Cbp, const cx<R>* __restrict__ Rbp, int k1, int w1,
+                                   cx<R>* __restrict__ Mb, cx<R>* __restrict__ Cb) {
+  const int b = blockIdx.y;
+  cx<R>* M = X + b * sX;
   const cx<R>* cbp = Cbp + (long long)b * n * w;  // n x w
   const cx<R>* rbp = Rbp + (long long)b * w * n;  // w x n
-  const cx<R>* aip = Aip + (long long)b * w * w;  // w x w
   const long long t1 = (long long)w1 * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 2 * t1;
        t += (long long)gridDim.x * blockDim.x) {
     if (t < t1) {  // Mb: row r of J', column c
       const int r = (int)(t / n), c = (int)(t % n);
-      const cx<R>* crow = cbp + (long long)(k1 + r) * w;
       cx<R> v;
-      if (c >= k0 && c < k0 + w) {
-        cx<R> acc = mk<R>(0, 0);
-#pragma unroll 8
-        for (int q = 0; q < w; ++q) fma_(acc, crow[q], aip[q * w + (c - k0)]);
-        v = mk<R>(-acc.re, -acc.im);
+      if (c >= k1 && c < k1 + w1) {
+        v = mk<R>(c - k1 == r ? R(1) : R(0), R(0));
       } else {
+        const cx<R>* crow = cbp + (long long)(k1 + r) * w;
         cx<R> acc = mk<R>(0, 0);
 #pragma unroll 8
         for (int q = 0; q < w; ++q) fma_(acc, crow[q], rbp[(long long)q * n + c]);
         v = M[(long long)(k1 + r) * lda + c] - acc;
       }
-      if (c >= k1 && c < k1 + w1) {
-        Ab[(long long)b * w1 * w1 + r * w1 + (c - k1)] = v;
-        Mb[b * t1 + t] = mk<R>(0, 0);
-      } else {
-        Mb[b * t1 + t] = v;
-      }
+      M[(long long)(k1 + r) * lda + c] = mk<R>(0, 0);
+      Mb[b * t1 + t] = v;
     } else {  // Cb': row i, column q of J'
       const long long u = t - t1;
       const int i = (int)(u / w1), q = (int)(u % w1);
       cx<R> v;
       if (i >= k1 && i < k1 + w1) {
-        v = mk<R>(0, 0);
-      } else if (i >= k0 && i < k0 + w) {
-        v = rbp[(long long)(i - k0) * n + k1 + q];
+        v = mk<R>(i - k1 == q ? R(-1) : R(0), R(0));
       } else {
         const cx<R>* crow = cbp + (long long)i * w;
         cx<R> acc = mk<R>(0, 0);
 #pragma unroll 8
         for (int p = 0; p < w; ++p) fma_(acc, crow[p], rbp[(long long)p * n + k1 + q]);
         v = M[(long long)i * lda + k1 + q] - acc;
+        M[(long long)i * lda + k1 + q] = mk<R>(0, 0);
       }
       Cb[b * t1 + u] = v;
     }
-  }
-}
-
-// Rows J of the lookahead sweep: X[J, :] = Rb, with A^-1 in the columns J.
-template <class R>
-__global__ void gjb_finalize_la_kernel(cx<R>* X, int n, int lda, long long sX, int k0, int w,
-                                       const cx<R>* __restrict__ Ai, const cx<R>* __restrict__ Rb) {
-  const int b = blockIdx.y;
-  cx<R>* M = X + b * sX;
-  const long long tot = (long long)n * w;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(t / n), c = (int)(t % n);
-    M[(long long)(k0 + r) * lda + c] =
-        (c >= k0 && c < k0 + w) ? Ai[(long long)b * w * w + r * w + (c - k0)] : Rb[b * tot + t];
   }
 }
 
@@ -1126,12 +1248,12 @@ void gemv(cudaStream_t st, bool ta, int M, int K, cx<R> alpha, const cx<R>* A, i
 template <class R>
 int invert_batch_nopiv(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int P, void* scratch,
                        size_t scratch_bytes, cudaStream_t st) {
-  // Blocked Gauss-Jordan sweep over 64-wide panels with one panel of lookahead:
-  // on st, panel i's operands are formed (with panel i-1's pending update applied
-  // on the fly), its diagonal block inverted and Rb = A^-1 Mb formed; on a second
-  // stream, panel i's update of everything but the rows and columns of panel i+1,
-  // then X[:, J] = -Cb A^-1 and X[J, :] = Rb.  So each panel's inverse runs while
-  // the previous panel's update does.  Panel buffers alternate by parity.
+  // Blocked Gauss-Jordan sweep over 64-wide panels with one panel of lookahead
+  // on three streams.  On st (the chain): panel i's diagonal block with panel
+  // i-1's pending update applied, its inverse, and Rb = A^-1 Mb.  On se: panel
+  // i's Mb and Cb (beside the inverse).  On sb: panel i's update X -= Cb Rb,
+  // which skips panel i+1's rows and columns, so that panel i+1's chain runs
+  // beside it.  Panel buffers alternate by parity.
   const int nb = 64;  // panel width: a 64-wide panel inverse takes ~1/4 the time of a 128-wide one
   const int np = (n + nb - 1) / nb;
   const size_t wm = nb;
@@ -1150,38 +1272,46 @@ int invert_batch_nopiv(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int
   }
   cx<R>* Mb = p;
   if (!H->inv_stream) LS_CUDA_TRY(cudaStreamCreateWithFlags(&H->inv_stream, cudaStreamNonBlocking));
-  cudaStream_t sb = H->inv_stream;
-  std::vector<cudaEvent_t> evR(np), evU(np);
+  if (!H->ext_stream) LS_CUDA_TRY(cudaStreamCreateWithFlags(&H->ext_stream, cudaStreamNonBlocking));
+  cudaStream_t sb = H->inv_stream, se = H->ext_stream;
+  std::vector<cudaEvent_t> evA(np), evE(np), evR(np), evU(np);
   cudaEvent_t ev0;
   LS_CUDA_TRY(cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming));
   for (int i = 0; i < np; ++i) {
+    LS_CUDA_TRY(cudaEventCreateWithFlags(&evA[i], cudaEventDisableTiming));
+    LS_CUDA_TRY(cudaEventCreateWithFlags(&evE[i], cudaEventDisableTiming));
     LS_CUDA_TRY(cudaEventCreateWithFlags(&evR[i], cudaEventDisableTiming));
     LS_CUDA_TRY(cudaEventCreateWithFlags(&evU[i], cudaEventDisableTiming));
   }
   struct Events {
-    std::vector<cudaEvent_t>& a;
-    std::vector<cudaEvent_t>& b;
+    std::vector<cudaEvent_t>* v[4];
     cudaEvent_t e;
     ~Events() {
-      for (auto x : a) cudaEventDestroy(x);
-      for (auto x : b) cudaEventDestroy(x);
+      for (auto* a : v)
+        for (auto x : *a) cudaEventDestroy(x);
       cudaEventDestroy(e);
     }
-  } events{evR, evU, ev0};
+  } events{{&evA, &evE, &evR, &evU}, ev0};
   LS_CUDA_TRY(cudaEventRecord(ev0, st));
   LS_CUDA_TRY(cudaStreamWaitEvent(sb, ev0, 0));
   const cx<R> mone = mk<R>(R(-1), R(0));
   for (int i = 0; i < np; ++i) {
     const int k1 = i * nb, w1 = std::min(nb, n - k1), par = i & 1;
-    const int k0 = (i - 1) * nb, w = i > 0 ? nb : 0;  // the pending panel (all but the last are full)
+    const int w = i > 0 ? nb : 0;  // the pending panel (all but the last are full)
     const long long t1 = (long long)n * w1;
     if (i >= 2) LS_CUDA_TRY(cudaStreamWaitEvent(st, evU[i - 2], 0));  // X after panel i-2; its buffers free
+    count_launch();
+    gjb_diag_kernel<R><<<dim3((unsigned)((w1 * w1 + 255) / 256), P), 256, 0, st>>>(
+        X, n, lda, sX, w, Cb[par ^ 1], Rb[par ^ 1], k1, w1, Ab[par]);
+    LS_CUDA_TRY(cudaEventRecord(evA[i], st));
+    LS_CUDA_TRY(cudaStreamWaitEvent(se, evA[i], 0));
     dim3 g((unsigned)std::min<long long>(1024, (2 * t1 + 255) / 256), P);
     count_launch();
-    gjb_extract_la_kernel<R><<<g, 256, 0, st>>>(X, n, lda, sX, k0, w, Cb[par ^ 1], Rb[par ^ 1], Ab[par ^ 1], k1,
-                                                 w1, Ab[par], Mb, Cb[par]);
+    gjb_extract_kernel<R><<<g, 256, 0, se>>>(X, n, lda, sX, w, Cb[par ^ 1], Rb[par ^ 1], k1, w1, Mb, Cb[par]);
+    LS_CUDA_TRY(cudaEventRecord(evE[i], se));
     int rc = invert_reg_nopiv<R>(Ab[par], w1, w1, (long long)w1 * w1, P, H->d_err + 3, st);
     if (rc) return rc;
+    LS_CUDA_TRY(cudaStreamWaitEvent(st, evE[i], 0));
     gemm<R>(st, false, false, w1, n, w1, one<R>(), Ab[par], w1, (long long)w1 * w1, Mb, n, t1, zero<R>(), Rb[par], n,
             t1, P);
     LS_CUDA_TRY(cudaEventRecord(evR[i], st));
@@ -1192,11 +1322,6 @@ int invert_batch_nopiv(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int
       band.hi = std::min(n, k1 + w1 + nb);
     }
     gemm<R>(sb, false, false, n, n, w1, mone, Cb[par], w1, t1, Rb[par], n, t1, one<R>(), X, lda, sX, P, band);
-    gemm<R>(sb, false, false, n, w1, w1, mone, Cb[par], w1, t1, Ab[par], w1, (long long)w1 * w1, zero<R>(), X + k1,
-            lda, sX, P);
-    dim3 gf((unsigned)std::min<long long>(1024, (t1 + 255) / 256), P);
-    count_launch();
-    gjb_finalize_la_kernel<R><<<gf, 256, 0, sb>>>(X, n, lda, sX, k1, w1, Ab[par], Rb[par]);
     LS_CUDA_TRY(cudaEventRecord(evU[i], sb));
   }
   LS_CUDA_TRY(cudaStreamWaitEvent(st, evU[np - 1], 0));
@@ -1947,6 +2072,69 @@ __device__ __forceinline__ void apply_rows(const ApplyOp& op, long long gw, long
   }
 }
 
+// Rows of more than 128 entries (rb = 32): split-K form.  A block takes a tile
+// of RT consecutive rows; each warp one (row, 256-entry chunk) pair with all
+// eight of a lane's loads issued before the first multiply-add, so that one
+// memory round trip serves a whole tile even when the rows are too few to give
+// every warp a row; the chunk sums are added in chunk order through shared
+// memory (part, kSplitParts entries), so the result does not depend on timing.
+constexpr int kSplitParts = 1024;
+template <class R>
+__device__ __forceinline__ void apply_rows_split(const ApplyOp& op, cx<R>* part, int lane) {
+  constexpr int U = sizeof(R) == 4 ? 8 : 4, CH = 32 * U;
+  const cx<R>* A = reinterpret_cast<const cx<R>*>(op.A);
+  const cx<R>* X = reinterpret_cast<const cx<R>*>(op.x);
+  const cx<R>* Y0 = reinterpret_cast<const cx<R>*>(op.y0);
+  cx<R>* Y = reinterpret_cast<cx<R>*>(op.y);
+  const cx<R> alpha = mk<R>((R)op.ar, (R)op.ai);
+  const int K = op.K, M = op.M, nch = (K + CH - 1) / CH;
+  const long long rows = (long long)op.batch * M;
+  const long long per_block = (rows + gridDim.x - 1) / gridDim.x;
+  const int RT = (int)max(1LL, min((long long)(kSplitParts / nch), per_block));
+  const long long ntiles = (rows + RT - 1) / RT;
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();  // part may still be read by the previous operation
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long r0 = tile * RT;
+    const int nr = (int)min((long long)RT, rows - r0);
+    for (int it = warp; it < nr * nch; it += nw) {
+      const int rl = it / nch, c = it % nch;
+      const long long r = r0 + rl;
+      const int b = (int)(r / M), i = (int)(r % M);
+      const cx<R>* a = A + b * op.sA + (long long)i * op.lda;
+      const cx<R>* xv = X + b * op.sx;
+      const int j0 = c * CH + lane;
+      cx<R> av[U], xw[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int j = j0 + 32 * u;
+        av[u] = j < K ? a[j] : mk<R>(0, 0);
+        xw[u] = j < K ? ldcg_cx(xv + j) : mk<R>(0, 0);
+      }
+      cx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0);
+#pragma unroll
+      for (int u = 0; u < U; u += 2) {
+        fma_(acc0, av[u], xw[u]);
+        fma_(acc1, av[u + 1], xw[u + 1]);
+      }
+      cx<R> v = acc0 + acc1;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) v = v + shfl_xor(v, o);
+      if (lane == 0) part[rl * nch + c] = v;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+      cx<R> v = part[t * nch];
+      for (int c = 1; c < nch; ++c) v = v + part[t * nch + c];
+      const long long r = r0 + t;
+      const int b = (int)(r / M), i = (int)(r % M);
+      const cx<R> y0v = Y0 ? ldcg_cx(Y0 + b * op.sy0 + i) : mk<R>(0, 0);
+      Y[b * op.sy + i] = alpha * v + y0v;
+    }
+    __syncthreads();  // part is reused by the next tile
+  }
+}
+
 // Leaf operations of the persistent apply: four warps (a 128-thread group,
 // named barrier 1 + group) take one leaf at a time, the leaf's vectors in
 // shared memory, so that Algorithm 2's three leaf steps of each pass need no
@@ -2056,7 +2244,7 @@ __global__ void __launch_bounds__(1024) apply_persistent_kernel(const ApplyOp* _
   const int lane = threadIdx.x & 31;
   unsigned target = epoch0;
   for (int o = 0; o < nops; ++o) {
-    const ApplyOp op = ops[o];
+    const ApplyOp& op = ops[o];  // fields read from shared memory where used
     const long long rows = (long long)op.batch * op.M;
     if (op.type == 3) {
       apply_leaf_up<R>(op, g, f, leaf_mem);
@@ -2080,7 +2268,7 @@ __global__ void __launch_bounds__(1024) apply_persistent_kernel(const ApplyOp* _
       else if (op.rb == 16)
         apply_rows<R, 16>(op, gw, nwarps, lane);
       else
-        apply_rows<R, 32>(op, gw, nwarps, lane);
+        apply_rows_split<R>(op, leaf_mem, lane);
     }
     if (op.phase_end && o + 1 < nops) {
       target += gridDim.x;
@@ -2407,9 +2595,11 @@ size_t apply_smem(const void* kfn, int nops, size_t leaf_bytes) {
   return bytes;
 }
 
-// Leaf scratch of the persistent apply: eight 128-thread groups x 2 s^2 entries.
+// Scratch of the persistent apply: eight 128-thread groups x 2 s^2 leaf entries,
+// or the kSplitParts chunk sums of the split-K rows.
 size_t leaf_smem(const ls_handle* H) {
-  return (H->prec == LS_FP64 ? sizeof(z64) : sizeof(c32)) * 8 * 2 * (size_t)H->s * H->s;
+  const size_t e = H->prec == LS_FP64 ? sizeof(z64) : sizeof(c32);
+  return e * std::max<size_t>(8 * 2 * (size_t)H->s * H->s, kSplitParts);
 }
 
 int apply_persistent_init(ls_handle* H, cudaStream_t st) {

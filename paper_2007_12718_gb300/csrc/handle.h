@@ -66,6 +66,7 @@ struct ls_handle {
   double flops_build = 0, flops_compress = 0, bytes_apply = 0, factor_bytes = 0;
   int pivot_fallbacks = 0;      // merge levels that needed the row-pivoted inverse
   cudaStream_t inv_stream = nullptr;  // second stream of the blocked inverse (panel updates)
+  cudaStream_t ext_stream = nullptr;  // third stream of the blocked inverse (panel operands)
   cudaStream_t side_stream = nullptr; // the FFT spectrum set-up beside the build
 
   // receivers (Eq. (1)): positions (device, nr x 2) and R[k][j] = h^2 G(|r_k - x_j|)

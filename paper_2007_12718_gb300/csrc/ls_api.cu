@@ -382,6 +382,7 @@ void ls_free(ls_handle* H) {
   f(H->Rrec);
   if (H->apply_exec) cudaGraphExecDestroy(H->apply_exec);
   if (H->inv_stream) cudaStreamDestroy(H->inv_stream);
+  if (H->ext_stream) cudaStreamDestroy(H->ext_stream);
   delete H;
 }
 
