@@ -633,27 +633,15 @@ __global__ void __launch_bounds__(1024) gj_reg_kernel(cx<R>* __restrict__ X, int
 // two packed FMAs on (re, im) pairs.  A zero or non-finite pivot sets
 // *err = LS_ESINGULAR; the sweep runs on, and the caller's probe check rejects
 // the result.
+// The sweep of gj2d_kernel on the register blocks a (thread (tr, tc) of the
+// TR x TC grid); shared by the plain kernel and the blocked sweep's panel kernel.
 template <int TR, int TC, int RM, int RN>
-__global__ void __launch_bounds__(TR * TC) gj2d_kernel(c32* __restrict__ X, int n, int lda, long long sX,
-                                                       int* __restrict__ err) {
+__device__ __forceinline__ void gj2d_sweep(unsigned long long (&a)[RM][RN], int n, int tr, int tc, int* err) {
   constexpr int KU = RM > RN ? RM : RN;
   static_assert(KU % RM == 0 && KU % RN == 0 && KU % 2 == 0 && RN % 2 == 0 && RM % 2 == 0, "block shape");
   __shared__ __align__(16) c32 rowk[2][TC * RN];
   __shared__ __align__(16) c32 colk[2][TR * RM];
   __shared__ c32 dk[2];
-  const int tid = threadIdx.x, tc = tid % TC, tr = tid / TC;
-  c32* M = X + blockIdx.x * sX;
-  unsigned long long a[RM][RN];
-#pragma unroll
-  for (int i = 0; i < RM; ++i) {
-    const int row = tr * RM + i;
-#pragma unroll
-    for (int j = 0; j < RN; ++j) {
-      const int col = tc * RN + j;
-      const c32 v = (row < n && col < n) ? M[(long long)row * lda + col] : mk<float>(0.f, 0.f);
-      a[i][j] = pk2(v.re, v.im);
-    }
-  }
   const int nk = (n + KU - 1) / KU;
   for (int kb = 0; kb < nk; ++kb) {
 #pragma unroll
@@ -722,6 +710,25 @@ __global__ void __launch_bounds__(TR * TC) gj2d_kernel(c32* __restrict__ X, int 
       }
     }
   }
+}
+
+template <int TR, int TC, int RM, int RN>
+__global__ void __launch_bounds__(TR * TC) gj2d_kernel(c32* __restrict__ X, int n, int lda, long long sX,
+                                                       int* __restrict__ err) {
+  const int tid = threadIdx.x, tc = tid % TC, tr = tid / TC;
+  c32* M = X + blockIdx.x * sX;
+  unsigned long long a[RM][RN];
+#pragma unroll
+  for (int i = 0; i < RM; ++i) {
+    const int row = tr * RM + i;
+#pragma unroll
+    for (int j = 0; j < RN; ++j) {
+      const int col = tc * RN + j;
+      const c32 v = (row < n && col < n) ? M[(long long)row * lda + col] : mk<float>(0.f, 0.f);
+      a[i][j] = pk2(v.re, v.im);
+    }
+  }
+  gj2d_sweep<TR, TC, RM, RN>(a, n, tr, tc, err);
 #pragma unroll
   for (int i = 0; i < RM; ++i) {
     const int row = tr * RM + i;
@@ -735,6 +742,119 @@ __global__ void __launch_bounds__(TR * TC) gj2d_kernel(c32* __restrict__ X, int 
       }
     }
   }
+}
+
+// Panel kernel of the FP32 blocked sweep (one block of 16 x 16 threads per
+// matrix, 4 x 4 entries each).  From the pending panel's A^-1 (Aip, w x w), Mb
+// (Mbp, w x n) and Cb (Cbp, n x w) it forms
+//   t  = A^-1 Mb[:, J]             (the columns J of the pending panel's Rb)
+//   Ab = X[J, J] - Cb[J, :] t
+// as two 64^3 products from shared memory (operands stored in the two packed
+// forms of gemm64x2_kernel), zeroes X[J, J] (the pending update skips it; this
+// panel's update writes A^-1 there) and inverts Ab in registers into Aout
+// (w1 x w1).  With w = 0 it is Ab = X[J, J].  Dynamic shared memory:
+// kPanelSmem bytes.
+// PA rows are padded to 65 entries (its transposed stores then fall in distinct
+// banks); PB stores column j of a row at slot (j % 4) * 16 + j / 4, so that the
+// four columns tc * 4 + jj a thread reads are 16 slots apart and the 16
+// threads of a half-warp read consecutive slots.
+constexpr int kPanelNB = 64, kPanelLdA = kPanelNB + 1;
+constexpr size_t kPanelSmem = sizeof(ulonglong2) * (kPanelLdA + kPanelNB) * kPanelNB;
+__device__ __forceinline__ int panel_bslot(int j) { return (j & 3) * 16 + (j >> 2); }
+
+__device__ __forceinline__ void panel_mma(const ulonglong2* __restrict__ PA, const ulonglong2* __restrict__ PB, int K,
+                                          int tr, int tc, unsigned long long (&acc)[4][4]) {
+#pragma unroll 2
+  for (int q = 0; q < K; ++q) {
+    ulonglong2 av[4], bv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) av[i] = PA[q * kPanelLdA + tr * 4 + i];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) bv[j] = PB[q * kPanelNB + j * 16 + tc];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = ffma2(av[i].x, bv[j].x, ffma2(av[i].y, bv[j].y, acc[i][j]));
+  }
+}
+
+__global__ void __launch_bounds__(256) gjb_panel_kernel(c32* __restrict__ X, int n, int lda, long long sX, int w,
+                                                        const c32* __restrict__ Aip, const c32* __restrict__ Mbp,
+                                                        const c32* __restrict__ Cbp, int k1, int w1,
+                                                        c32* __restrict__ Aout, int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char panel_sm[];
+  ulonglong2* PA = reinterpret_cast<ulonglong2*>(panel_sm);  // PA[q][i]: A operand entry (i, q)
+  ulonglong2* PB = PA + kPanelLdA * kPanelNB;                // PB[q][slot(j)]: B operand entry (q, j)
+  const int b = blockIdx.x, tid = threadIdx.x, tc = tid % 16, tr = tid / 16;
+  c32* M = X + b * sX;
+  unsigned long long a[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = tr * 4 + i, c = tc * 4 + j;
+      c32 v = mk<float>(0.f, 0.f);
+      if (r < w1 && c < w1) {
+        c32* e = M + (long long)(k1 + r) * lda + k1 + c;
+        v = *e;
+        *e = mk<float>(0.f, 0.f);
+      }
+      a[i][j] = pk2(v.re, v.im);
+    }
+  if (w > 0) {
+    const c32* aip = Aip + (long long)b * w * w;
+    const c32* mbp = Mbp + (long long)b * w * n;
+    const c32* cbp = Cbp + (long long)b * n * w;
+    for (int t = tid; t < kPanelNB * kPanelNB; t += blockDim.x) {
+      const int r = t / kPanelNB, c = t % kPanelNB;
+      const c32 x = (r < w && c < w) ? aip[r * w + c] : mk<float>(0.f, 0.f);
+      PA[c * kPanelLdA + r] = make_ulonglong2(pk2(x.re, x.re), pk2(-x.im, x.im));
+      const c32 y = (r < w && c < w1) ? mbp[(long long)r * n + k1 + c] : mk<float>(0.f, 0.f);
+      PB[r * kPanelNB + panel_bslot(c)] = make_ulonglong2(pk2(y.re, y.im), pk2(y.im, y.re));
+    }
+    __syncthreads();
+    unsigned long long acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0ull;
+    panel_mma(PA, PB, w, tr, tc, acc);  // t = A^-1 Mb[:, J]
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float re, im;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(re), "=f"(im) : "l"(acc[i][j]));
+        PB[(tr * 4 + i) * kPanelNB + j * 16 + tc] = make_ulonglong2(pk2(re, im), pk2(im, re));
+        acc[i][j] = 0ull;
+      }
+    for (int t = tid; t < kPanelNB * kPanelNB; t += blockDim.x) {
+      const int r = t / kPanelNB, c = t % kPanelNB;
+      const c32 x = (r < w1 && c < w) ? cbp[(long long)(k1 + r) * w + c] : mk<float>(0.f, 0.f);
+      PA[c * kPanelLdA + r] = make_ulonglong2(pk2(x.re, x.re), pk2(-x.im, x.im));
+    }
+    __syncthreads();
+    panel_mma(PA, PB, w, tr, tc, acc);  // Cb[J, :] t
+    const unsigned long long mone2 = pk2(-1.f, -1.f);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a[i][j] = ffma2(mone2, acc[i][j], a[i][j]);
+  }
+  gj2d_sweep<16, 16, 4, 4>(a, w1, tr, tc, err);
+  c32* out = Aout + (long long)b * w1 * w1;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = tr * 4 + i, c = tc * 4 + j;
+      if (r < w1 && c < w1) {
+        float lo, hi;
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a[i][j]));
+        out[r * w1 + c] = mk<float>(lo, hi);
+      }
+    }
 }
 
 // Largest order handled by gj_reg_kernel (registers per thread: 2 CPT reals).
@@ -1156,13 +1276,14 @@ __global__ void gjb_diag_kernel(const cx<R>* __restrict__ X, int n, int lda, lon
   Ab[(long long)b * w1 * w1 + t] = X[b * sX + (long long)(k1 + r) * lda + k1 + q] - acc;
 }
 
-// Mb and Cb' of panel J' (above); X[J', :] and X[:, J'] are zeroed once read.
+// Mb and Cb' of panel J' (above); X[J', :] and X[:, J'] are zeroed once read
+// (X[J', J'] only with zero_diag: the FP32 panel kernel zeroes it itself).
 // The pending update skips these rows and columns, and each element is read
 // and zeroed by the same thread, so the kernel may run beside that update.
 template <class R>
 __global__ void gjb_extract_kernel(cx<R>* __restrict__ X, int n, int lda, long long sX, int w,
                                    const cx<R>* __restrict__ Cbp, const cx<R>* __restrict__ Rbp, int k1, int w1,
-                                   cx<R>* __restrict__ Mb, cx<R>* __restrict__ Cb) {
+                                   cx<R>* __restrict__ Mb, cx<R>* __restrict__ Cb, int zero_diag) {
   const int b = blockIdx.y;
   cx<R>* M = X + b * sX;
   const cx<R>* cbp = Cbp + (long long)b * n * w;  // n x w
@@ -1173,7 +1294,8 @@ __global__ void gjb_extract_kernel(cx<R>* __restrict__ X, int n, int lda, long l
     if (t < t1) {  // Mb: row r of J', column c
       const int r = (int)(t / n), c = (int)(t % n);
       cx<R> v;
-      if (c >= k1 && c < k1 + w1) {
+      const bool diag = c >= k1 && c < k1 + w1;
+      if (diag) {
         v = mk<R>(c - k1 == r ? R(1) : R(0), R(0));
       } else {
         const cx<R>* crow = cbp + (long long)(k1 + r) * w;
@@ -1182,7 +1304,7 @@ __global__ void gjb_extract_kernel(cx<R>* __restrict__ X, int n, int lda, long l
         for (int q = 0; q < w; ++q) fma_(acc, crow[q], rbp[(long long)q * n + c]);
         v = M[(long long)(k1 + r) * lda + c] - acc;
       }
-      M[(long long)(k1 + r) * lda + c] = mk<R>(0, 0);
+      if (!diag || zero_diag) M[(long long)(k1 + r) * lda + c] = mk<R>(0, 0);
       Mb[b * t1 + t] = v;
     } else {  // Cb': row i, column q of J'
       const long long u = t - t1;
@@ -1245,9 +1367,95 @@ template <class R>
 void gemv(cudaStream_t st, bool ta, int M, int K, cx<R> alpha, const cx<R>* A, int lda, long long sA, const cx<R>* x,
           long long sx, cx<R> beta, cx<R>* y, long long sy, int batch);
 
+// FP32 form of the lookahead sweep: the chain (st) is one panel kernel per
+// panel, which forms its diagonal block from the pending panel's A^-1, Mb and
+// Cb itself; on se, each panel's Mb and Cb (beside its panel kernel) and then
+// Rb = A^-1 Mb; on sb, its update X -= Cb Rb, which skips the next panel's rows
+// and columns.  Buffers alternate by panel parity.
+int invert_batch_nopiv_f32(ls_handle* H, c32* X, int n, int lda, long long sX, int P, void* scratch,
+                           size_t scratch_bytes, cudaStream_t st) {
+  const int nb = kPanelNB, np = (n + nb - 1) / nb;
+  const size_t wm = nb;
+  if (sizeof(c32) * (size_t)P * (2 * wm * wm + 6 * wm * (size_t)n) > scratch_bytes) return LS_ENOMEM;
+  c32* p = reinterpret_cast<c32*>(scratch);
+  c32 *Ab[2], *Cb[2], *Rb[2], *Mb[2];
+  for (int q = 0; q < 2; ++q) {
+    Ab[q] = p;
+    p += (size_t)P * wm * wm;
+    Cb[q] = p;
+    p += (size_t)P * wm * n;
+    Rb[q] = p;
+    p += (size_t)P * wm * n;
+    Mb[q] = p;
+    p += (size_t)P * wm * n;
+  }
+  if (!H->inv_stream) LS_CUDA_TRY(cudaStreamCreateWithFlags(&H->inv_stream, cudaStreamNonBlocking));
+  if (!H->ext_stream) LS_CUDA_TRY(cudaStreamCreateWithFlags(&H->ext_stream, cudaStreamNonBlocking));
+  LS_CUDA_TRY(cudaFuncSetAttribute(gjb_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmem));
+  cudaStream_t sb = H->inv_stream, se = H->ext_stream;
+  std::vector<cudaEvent_t> evG(np), evE(np), evR(np), evU(np);
+  cudaEvent_t ev0;
+  LS_CUDA_TRY(cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming));
+  for (int i = 0; i < np; ++i) {
+    LS_CUDA_TRY(cudaEventCreateWithFlags(&evG[i], cudaEventDisableTiming));
+    LS_CUDA_TRY(cudaEventCreateWithFlags(&evE[i], cudaEventDisableTiming));
+    LS_CUDA_TRY(cudaEventCreateWithFlags(&evR[i], cudaEventDisableTiming));
+    LS_CUDA_TRY(cudaEventCreateWithFlags(&evU[i], cudaEventDisableTiming));
+  }
+  struct Events {
+    std::vector<cudaEvent_t>* v[4];
+    cudaEvent_t e;
+    ~Events() {
+      for (auto* a : v)
+        for (auto x : *a) cudaEventDestroy(x);
+      cudaEventDestroy(e);
+    }
+  } events{{&evG, &evE, &evR, &evU}, ev0};
+  LS_CUDA_TRY(cudaEventRecord(ev0, st));
+  LS_CUDA_TRY(cudaStreamWaitEvent(se, ev0, 0));
+  LS_CUDA_TRY(cudaStreamWaitEvent(sb, ev0, 0));
+  const c32 one1 = mk<float>(1.f, 0.f), zero1 = mk<float>(0.f, 0.f), mone = mk<float>(-1.f, 0.f);
+  for (int i = 0; i < np; ++i) {
+    const int k1 = i * nb, w1 = std::min(nb, n - k1), par = i & 1;
+    const int w = i > 0 ? nb : 0;  // the pending panel (all but the last are full)
+    const long long t1 = (long long)n * w1;
+    // chain: X[J, J] after panel i-2's update; the pending panel's Mb and Cb
+    if (i >= 2) LS_CUDA_TRY(cudaStreamWaitEvent(st, evU[i - 2], 0));
+    if (i >= 1) LS_CUDA_TRY(cudaStreamWaitEvent(st, evE[i - 1], 0));
+    count_launch();
+    gjb_panel_kernel<<<P, 256, kPanelSmem, st>>>(X, n, lda, sX, w, Ab[par ^ 1], Mb[par ^ 1], Cb[par ^ 1], k1, w1,
+                                                 Ab[par], H->d_err + 3);
+    LS_CUDA_TRY(cudaEventRecord(evG[i], st));
+    // operands: X[J, :] and X[:, J] after panel i-2's update
+    if (i >= 2) LS_CUDA_TRY(cudaStreamWaitEvent(se, evU[i - 2], 0));
+    dim3 g((unsigned)std::min<long long>(1024, (2 * t1 + 255) / 256), P);
+    count_launch();
+    gjb_extract_kernel<float><<<g, 256, 0, se>>>(X, n, lda, sX, w, Cb[par ^ 1], Rb[par ^ 1], k1, w1, Mb[par],
+                                                 Cb[par], 0);
+    LS_CUDA_TRY(cudaEventRecord(evE[i], se));
+    LS_CUDA_TRY(cudaStreamWaitEvent(se, evG[i], 0));
+    gemm<float>(se, false, false, w1, n, w1, one1, Ab[par], w1, (long long)w1 * w1, Mb[par], n, t1, zero1, Rb[par],
+                n, t1, P);
+    LS_CUDA_TRY(cudaEventRecord(evR[i], se));
+    // update, leaving the next panel's rows and columns to its own kernels
+    LS_CUDA_TRY(cudaStreamWaitEvent(sb, evR[i], 0));
+    Band band;
+    if (i + 1 < np) {
+      band.lo = k1 + w1;
+      band.hi = std::min(n, k1 + w1 + nb);
+    }
+    gemm<float>(sb, false, false, n, n, w1, mone, Cb[par], w1, t1, Rb[par], n, t1, one1, X, lda, sX, P, band);
+    LS_CUDA_TRY(cudaEventRecord(evU[i], sb));
+  }
+  LS_CUDA_TRY(cudaStreamWaitEvent(st, evU[np - 1], 0));
+  return check_launch("inverse_blocked_nopiv");
+}
+
 template <class R>
 int invert_batch_nopiv(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int P, void* scratch,
                        size_t scratch_bytes, cudaStream_t st) {
+  if constexpr (sizeof(R) == 4)
+    return invert_batch_nopiv_f32(H, reinterpret_cast<c32*>(X), n, lda, sX, P, scratch, scratch_bytes, st);
   // Blocked Gauss-Jordan sweep over 64-wide panels with one panel of lookahead
   // on three streams.  On st (the chain): panel i's diagonal block with panel
   // i-1's pending update applied, its inverse, and Rb = A^-1 Mb.  On se: panel
@@ -1307,7 +1515,7 @@ int invert_batch_nopiv(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int
     LS_CUDA_TRY(cudaStreamWaitEvent(se, evA[i], 0));
     dim3 g((unsigned)std::min<long long>(1024, (2 * t1 + 255) / 256), P);
     count_launch();
-    gjb_extract_kernel<R><<<g, 256, 0, se>>>(X, n, lda, sX, w, Cb[par ^ 1], Rb[par ^ 1], k1, w1, Mb, Cb[par]);
+    gjb_extract_kernel<R><<<g, 256, 0, se>>>(X, n, lda, sX, w, Cb[par ^ 1], Rb[par ^ 1], k1, w1, Mb, Cb[par], 1);
     LS_CUDA_TRY(cudaEventRecord(evE[i], se));
     int rc = invert_reg_nopiv<R>(Ab[par], w1, w1, (long long)w1 * w1, P, H->d_err + 3, st);
     if (rc) return rc;
