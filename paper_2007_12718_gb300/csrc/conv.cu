@@ -24,8 +24,11 @@ namespace {
 
 __device__ __forceinline__ int brev(int i, int logL) { return (int)(__brev((unsigned)i) >> (32 - logL)); }
 
-// count interleaved length-L transforms s[i*stride + c]; forward DIF.
-__device__ void fft_dif(z64* s, int L, int logL, int stride, int count, const z64* tw) {
+// COUNT interleaved length-L transforms s[i*stride + c]; forward DIF.  COUNT is
+// a compile-time constant so that the transform index needs no division.
+template <int COUNT>
+__device__ void fft_dif(z64* s, int L, int logL, int stride, const z64* tw) {
+  constexpr int count = COUNT;
   for (int lh = logL - 1; lh >= 0; --lh) {
     int half = 1 << lh;
     int tstep = L >> (lh + 1);
@@ -44,7 +47,9 @@ __device__ void fft_dif(z64* s, int L, int logL, int stride, int count, const z6
 }
 
 // inverse DIT (unnormalised), bit-reversed input, natural output.
-__device__ void fft_dit_inv(z64* s, int L, int logL, int stride, int count, const z64* tw) {
+template <int COUNT>
+__device__ void fft_dit_inv(z64* s, int L, int logL, int stride, const z64* tw) {
+  constexpr int count = COUNT;
   for (int lh = 0; lh < logL; ++lh) {
     int half = 1 << lh;
     int tstep = L >> (lh + 1);
@@ -91,17 +96,19 @@ __global__ void rows_fwd_kernel(const z64* in, int ld_in, int nvalid, long long 
     s[i] = v;
   }
   __syncthreads();
-  fft_dif(s, L, logL, 1, 1, stw);
+  fft_dif<1>(s, L, logL, 1, stw);
   z64* dst = out + rhs * out_rhs_stride + (long long)row * L;
   for (int i = threadIdx.x; i < L; i += blockDim.x) dst[i] = s[i];
 }
 
-// Pass 2: C columns per block.  W: [rhs][nrow_valid][Lx] (bit-reversed column order).
+// Pass 2: C columns per block (C = 2: a 512-column array is 256 blocks, so every
+// SM takes part in the FP64 butterflies).  W: [rhs][nrow_valid][Lx] (bit-reversed column order).
 // mode 0: forward, multiply by the quarter spectrum, inverse, keep first nrow rows.
 // mode 1: forward only over all Ly rows (spectrum set-up), output bit-reversed rows.
+template <int C>
 __global__ void cols_kernel(z64* __restrict__ W, long long rhs_stride, int Lx, int logLx, int nrow, int Ly,
-                            int logLy, int C, const z64* __restrict__ tw, const z64* __restrict__ spec,
-                            int nxq, int nyq, int mode) {
+                            int logLy, const z64* __restrict__ tw, const z64* __restrict__ spec, int nxq, int nyq,
+                            int mode) {
   extern __shared__ z64 sm[];
   z64* s = sm;             // Ly * C
   z64* stw = sm + Ly * C;  // Ly / 2
@@ -113,7 +120,7 @@ __global__ void cols_kernel(z64* __restrict__ W, long long rhs_stride, int Lx, i
     s[t] = i < nrow ? base[(long long)i * Lx + c0 + c] : mk<double>(0.0, 0.0);
   }
   __syncthreads();
-  fft_dif(s, Ly, logLy, C, C, stw);
+  fft_dif<C>(s, Ly, logLy, C, stw);
   if (mode == 1) {
     for (int t = threadIdx.x; t < Ly * C; t += blockDim.x) {
       int i = t / C, c = t % C;
@@ -129,7 +136,7 @@ __global__ void cols_kernel(z64* __restrict__ W, long long rhs_stride, int Lx, i
     s[t] = s[t] * spec[(long long)ky * (nxq + 1) + kx];
   }
   __syncthreads();
-  fft_dit_inv(s, Ly, logLy, C, C, stw);
+  fft_dit_inv<C>(s, Ly, logLy, C, stw);
   for (int t = threadIdx.x; t < nrow * C; t += blockDim.x) {
     int i = t / C, c = t % C;
     base[(long long)i * Lx + c0 + c] = s[t];
@@ -149,7 +156,7 @@ __global__ void rows_inv_kernel(const z64* __restrict__ W, long long w_rhs_strid
   for (int i = threadIdx.x; i < L / 2; i += blockDim.x) stw[i] = tw[i];
   for (int i = threadIdx.x; i < L; i += blockDim.x) s[i] = src[i];
   __syncthreads();
-  fft_dit_inv(s, L, logL, 1, 1, stw);
+  fft_dit_inv<1>(s, L, logL, 1, stw);
   long long off = rhs * g_rhs_stride + (long long)row * nx;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     z64 cv = s[i];
@@ -206,11 +213,18 @@ int ilog2(int v) {
   return l;
 }
 
-int cols_per_block(int Ly) {
-  // keep the column tile within ~96 KB of shared memory
-  int C = 8;
-  while (C > 1 && (size_t)Ly * C * sizeof(z64) > 96 * 1024) C >>= 1;
-  return C;
+int cols_per_block(int Ly) { return (size_t)Ly * 2 * sizeof(z64) <= 96 * 1024 ? 2 : 1; }
+
+cudaError_t launch_cols(int C, unsigned nblk, unsigned nrhs, cudaStream_t st, z64* W, long long rhs_stride, int Lx,
+                        int logLx, int nrow, int Ly, int logLy, const z64* tw, const z64* spec, int nxq, int nyq,
+                        int mode) {
+  const size_t smc = sizeof(z64) * ((size_t)Ly * C + Ly / 2);
+  auto kfn = C == 2 ? cols_kernel<2> : cols_kernel<1>;
+  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  kfn<<<dim3(nblk, nrhs), 256, smc, st>>>(W, rhs_stride, Lx, logLx, nrow, Ly, logLy, tw, spec, nxq, nyq, mode);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -256,11 +270,8 @@ int conv_setup(ls_handle* H, cudaStream_t st) {
   rows_fwd_kernel<<<dim3(H->Ly, 1), 256, smr, st>>>(full, H->Lx, H->Lx, 0, full, 0, H->Lx, H->logLx, H->tw_x,
                                                     nullptr, 0.0);
   int C = cols_per_block(H->Ly);
-  size_t smc = sizeof(z64) * ((size_t)H->Ly * C + H->Ly / 2);
-  cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
-  count_launch();
-  cols_kernel<<<dim3(H->Lx / C, 1), 256, smc, st>>>(full, 0, H->Lx, H->logLx, H->Ly, H->Ly, H->logLy, C, H->tw_y,
-                                                    nullptr, nx, ny, 1);
+  LS_CUDA_TRY(launch_cols(C, H->Lx / C, 1, st, full, 0, H->Lx, H->logLx, H->Ly, H->Ly, H->logLy, H->tw_y, nullptr, nx,
+                          ny, 1));
   size_t nq = (size_t)(nx + 1) * (ny + 1);
   count_launch();
   quarter_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(full, H->Lx, H->logLx, H->Ly, H->logLy, nx, ny,
@@ -294,12 +305,9 @@ int conv_apply(ls_handle* H, const z64* x, z64* y, int nrhs, int mode, cudaStrea
   prof_end(tk, PR_MV_ROWS_FWD, st, R * (16.0 * N + 16.0 * W) + (mode == CONV_TRANSPOSE ? 8.0 * N : 0.0),
            R * 5.0 * W * H->logLx);
   int C = cols_per_block(H->Ly);
-  size_t smc = sizeof(z64) * ((size_t)H->Ly * C + H->Ly / 2);
-  cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
   tk = prof_begin(st);
-  count_launch();
-  cols_kernel<<<dim3(H->Lx / C, nrhs), 256, smc, st>>>(H->convbuf, w_stride, H->Lx, H->logLx, ny, H->Ly, H->logLy, C,
-                                                       H->tw_y, H->spec, nx, ny, 0);
+  LS_CUDA_TRY(launch_cols(C, H->Lx / C, nrhs, st, H->convbuf, w_stride, H->Lx, H->logLx, ny, H->Ly, H->logLy, H->tw_y,
+                          H->spec, nx, ny, 0));
   prof_end(tk, PR_MV_COLS, st, R * 32.0 * W + 16.0 * (nx + 1.0) * (ny + 1.0),
            R * (2.0 * 5.0 * H->Lx * (double)H->Ly * H->logLy + 6.0 * H->Lx * (double)H->Ly));
   tk = prof_begin(st);
@@ -393,11 +401,8 @@ extern "C" int ls_matvec_noalloc(ls_handle* H, const void* xv, void* yv, int nrh
   rows_fwd_kernel<<<dim3(ny, nrhs), 256, smr, st>>>(x, nx, nx, g_stride, W, w_stride, H->Lx, H->logLx, H->tw_x,
                                                     nullptr, 0.0);
   int C = cols_per_block(H->Ly);
-  size_t smc = sizeof(z64) * ((size_t)H->Ly * C + H->Ly / 2);
-  LS_CUDA_TRY(cudaFuncSetAttribute(cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
-  count_launch();
-  cols_kernel<<<dim3(H->Lx / C, nrhs), 256, smc, st>>>(W, w_stride, H->Lx, H->logLx, ny, H->Ly, H->logLy, C, H->tw_y,
-                                                       H->spec, nx, ny, 0);
+  LS_CUDA_TRY(launch_cols(C, H->Lx / C, nrhs, st, W, w_stride, H->Lx, H->logLx, ny, H->Ly, H->logLy, H->tw_y, H->spec,
+                          nx, ny, 0));
   count_launch();
   rows_inv_kernel<<<dim3(ny, nrhs), 256, smr, st>>>(W, w_stride, H->Lx, H->logLx, H->tw_x, x, H->b, H->kappa * H->kappa,
                                                     nx, g_stride, y, ls::CONV_FORWARD);
