@@ -1628,6 +1628,22 @@ TreeGeom make_geom(const ls_handle* H) {
 int apply_persistent_init(ls_handle* H, cudaStream_t st);
 int level_transpose(ls_handle* H, int l, cudaStream_t st);
 
+// The apply's temporaries (one right-hand side: leaf blocks, per-level
+// expansions) and the persistent apply's transposes and operation list, made at
+// the end of the build rather than at the first apply.  Needs every level's
+// ranks and factor pointers, not their contents; a second call does nothing.
+template <class R>
+int apply_prepare(ls_handle* H, cudaStream_t st) {
+  if (H->work) return LS_OK;
+  const int L = H->L, n = H->s * H->s;
+  size_t vec = (size_t)2 * ((size_t)1 << L) * n;
+  for (int l = 1; l <= L; ++l) vec += (size_t)3 * ((size_t)1 << l) * std::max(1, H->lev[l].k) * 2;
+  H->work_bytes = sizeof(cx<R>) * vec;
+  int rc;
+  if ((rc = dalloc(&H->work, H->work_bytes))) return rc;
+  return apply_persistent_init(H, st);
+}
+
 template <class R>
 int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
   const int L = H->L, n = H->s * H->s;
@@ -1757,6 +1773,9 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
           count_launch();
           probe_max_kernel<R><<<64, 256, 0, st>>>(pr, pv, kc, (long long)P * kc, H->d_err + 2);
         }
+        // the root: the persistent apply's operation list (pointers only) is made and
+        // uploaded while the GPU still runs the inverse, before the host waits for it
+        if (l == 0 && (rc = apply_prepare<R>(H, st))) return rc;
         int* flags = static_cast<int*>(pinned_scratch(2 * sizeof(int)));  // worst probe residual (float bits), zero-pivot flag
         if (!flags) return LS_ENOMEM;
         LS_CUDA_TRY(cudaMemcpyAsync(flags, H->d_err + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1840,16 +1859,7 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
       H->flops_build += fl;
     }
   }
-  // apply temporaries (one right-hand side): leaf blocks, per-level expansions
-  {
-    size_t vec = (size_t)2 * ((size_t)1 << L) * n;
-    for (int l = 1; l <= L; ++l) vec += (size_t)3 * ((size_t)1 << l) * std::max(1, H->lev[l].k) * 2;
-    H->work_bytes = sizeof(cx<R>) * vec;
-    if ((rc = dalloc(&H->work, H->work_bytes))) return rc;
-  }
-  // the persistent apply's transposes and operation list, here rather than at the
-  // first apply: the build already ends with a synchronisation
-  if ((rc = apply_persistent_init(H, st))) return rc;
+  if ((rc = apply_prepare<R>(H, st))) return rc;  // no-op when the root merge made it
   int* pin = static_cast<int*>(pinned_scratch(sizeof(int)));
   if (!pin) return LS_ENOMEM;
   LS_CUDA_TRY(cudaMemcpyAsync(pin, H->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
