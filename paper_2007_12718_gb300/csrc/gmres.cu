@@ -92,8 +92,7 @@ struct GmState {
 };
 
 // Column j of H: apply the earlier rotations, form the new one, update g.
-__global__ void givens_kernel(z64* H, int ldh, z64* cs, z64* sn, z64* g, int j, GmState* st) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void givens_step(z64* H, int ldh, z64* cs, z64* sn, z64* g, int j, GmState* st) {
   z64* col = H + j;  // H[i][j] at H[i*ldh + j]
   for (int i = 0; i < j; ++i) {
     z64 a = col[(long long)i * ldh], b = col[(long long)(i + 1) * ldh];
@@ -124,6 +123,120 @@ __global__ void givens_kernel(z64* H, int ldh, z64* cs, z64* sn, z64* g, int j, 
   st->k = j + 1;
 }
 
+__global__ void givens_kernel(z64* H, int ldh, z64* cs, z64* sn, z64* g, int j, GmState* st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  givens_step(H, ldh, cs, sn, g, j, st);
+}
+
+// Block sum in the order of dot_partials_kernel (warp sums, then the warp
+// totals by the first warp); the result is valid in thread 0.
+__device__ __forceinline__ z64 block_sum_dp(z64 acc, z64* red) {
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  z64 v2 = mk<double>(0.0, 0.0);
+  if (threadIdx.x < 32) {
+    v2 = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : mk<double>(0.0, 0.0);
+    v2 = warp_sum(v2);
+  }
+  __syncthreads();  // red is reused
+  return v2;
+}
+
+// Sum of the nchunk partials of row i in the order of reduce_partials_kernel
+// (valid in thread 0).
+__device__ __forceinline__ z64 reduce_row(const z64* __restrict__ partial, int nchunk, int i, z64* red) {
+  z64 a = mk<double>(0.0, 0.0);
+  for (int c = threadIdx.x; c < nchunk; c += blockDim.x) a = a + partial[(long long)i * nchunk + c];
+  a = warp_sum(a);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  z64 s = mk<double>(0.0, 0.0);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s = s + red[k];
+  __syncthreads();
+  return s;
+}
+
+// One iteration's orthogonalisation in one cooperative launch of kChunks
+// blocks (block b owns the entries of chunk b, as in dot_partials_kernel):
+// classical Gram-Schmidt twice against V_0..V_j, ||w||, V_{j+1} = w / ||w||,
+// and the Givens step in block 0 (the only writer of column j of H).  The same
+// operations in the same order as the separate kernels, so the results are the
+// same bits; three grid barriers (bounded waits: a block that gives up sets
+// *err = LS_ETIMEOUT).  Dynamic shared memory: (j + 1) coefficients.
+__global__ void __launch_bounds__(256) gmres_orth_kernel(const z64* __restrict__ V, long long ldv, int j, z64* w,
+                                                         long long N, z64* Hm, int ldh, z64* part0, z64* part1,
+                                                         z64* cs, z64* sn, z64* g, GmState* st, GridSync gs,
+                                                         unsigned epoch0, int* err) {
+  extern __shared__ z64 hc[];
+  __shared__ z64 red[32];
+  __shared__ z64 bc;
+  const int b = blockIdx.x, G = gridDim.x, nvec = j + 1;
+  const long long per = (N + G - 1) / G;
+  const long long n0 = b * per, n1 = min(N, n0 + per);
+  unsigned epoch = epoch0;
+  for (int pass = 0; pass < 2; ++pass) {
+    z64* part = pass ? part1 : part0;
+    for (int i = 0; i < nvec; ++i) {
+      const z64* v = V + i * ldv;
+      z64 acc = mk<double>(0.0, 0.0);
+      for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) fmac_(acc, v[n], w[n]);
+      const z64 t = block_sum_dp(acc, red);
+      if (threadIdx.x == 0) part[(long long)i * G + b] = t;
+    }
+    if (!grid_sync(gs, G, epoch)) {
+      if (threadIdx.x == 0) atomicExch(err, LS_ETIMEOUT);
+      return;
+    }
+    for (int i = 0; i < nvec; ++i) {
+      const z64 s = reduce_row(part, G, i, red);
+      if (threadIdx.x == 0) {
+        hc[i] = s;
+        if (b == 0) Hm[(long long)i * ldh + j] = Hm[(long long)i * ldh + j] + s;
+      }
+    }
+    __syncthreads();
+    for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+      z64 acc = w[n];
+      for (int i = 0; i < nvec; ++i) {
+        const z64 c = hc[i], v = V[i * ldv + n];
+        acc.re -= v.re * c.re - v.im * c.im;
+        acc.im -= v.re * c.im + v.im * c.re;
+      }
+      w[n] = acc;
+    }
+    __syncthreads();
+  }
+  // ||w||^2: part0 is free again (every block read it before the second barrier)
+  {
+    z64 acc = mk<double>(0.0, 0.0);
+    for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) fmac_(acc, w[n], w[n]);
+    const z64 t = block_sum_dp(acc, red);
+    if (threadIdx.x == 0) part0[b] = t;
+  }
+  if (!grid_sync(gs, G, epoch)) {
+    if (threadIdx.x == 0) atomicExch(err, LS_ETIMEOUT);
+    return;
+  }
+  {
+    const z64 s = reduce_row(part0, G, 0, red);
+    if (threadIdx.x == 0) bc = s;
+    __syncthreads();
+  }
+  const double nr = sqrt(bc.re);
+  const double sc = nr > 0 ? 1.0 / nr : 0.0;
+  z64* vn = const_cast<z64*>(V) + (long long)(j + 1) * ldv;
+  for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
+    const z64 x = w[n];
+    vn[n] = mk<double>(x.re * sc, x.im * sc);
+  }
+  if (b == 0 && threadIdx.x == 0) {
+    Hm[(long long)(j + 1) * ldh + j] = mk<double>(nr, 0.0);
+    givens_step(Hm, ldh, cs, sn, g, j, st);
+  }
+}
+
 // Back substitution H(0:k,0:k) y = g(0:k), one thread (k <= maxit).
 __global__ void backsolve_kernel(const z64* H, int ldh, const z64* g, z64* y, int k) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -150,8 +263,9 @@ __global__ void sub_kernel(const z64* a, const z64* b, z64* c, long long N) {
 }
 
 struct Ws {
-  z64 *V, *Z, *w, *z, *Hm, *cs, *sn, *g, *y, *partial, *scal;
+  z64 *V, *Z, *w, *z, *Hm, *cs, *sn, *g, *y, *partial, *partial1, *scal;
   GmState* st;
+  unsigned* sync;  // grid barrier of gmres_orth_kernel: arrival count, abort flag
 };
 
 Ws carve(ls_handle* H, long long N, int m) {
@@ -172,8 +286,10 @@ Ws carve(ls_handle* H, long long N, int m) {
   ws.g = reinterpret_cast<z64*>(take(sizeof(z64) * (m + 1)));
   ws.y = reinterpret_cast<z64*>(take(sizeof(z64) * (m + 1)));
   ws.partial = reinterpret_cast<z64*>(take(sizeof(z64) * kChunks * (m + 1)));
+  ws.partial1 = reinterpret_cast<z64*>(take(sizeof(z64) * kChunks * (m + 1)));
   ws.scal = reinterpret_cast<z64*>(take(sizeof(z64) * 8));
   ws.st = reinterpret_cast<GmState*>(take(sizeof(GmState)));
+  ws.sync = reinterpret_cast<unsigned*>(take(4 * sizeof(unsigned)));
   return ws;
 }
 
@@ -190,8 +306,10 @@ size_t ws_bytes(long long N, int m) {
   add(sizeof(z64) * (m + 1));
   add(sizeof(z64) * (m + 1));
   add(sizeof(z64) * kChunks * (m + 1));
+  add(sizeof(z64) * kChunks * (m + 1));
   add(sizeof(z64) * 8);
   add(sizeof(GmState));
+  add(4 * sizeof(unsigned));
   return b;
 }
 
@@ -212,6 +330,18 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, int t
   int rc;
   LS_CUDA_TRY(cudaMemsetAsync(ws.Hm, 0, sizeof(z64) * (m + 1) * m, st));
   LS_CUDA_TRY(cudaMemsetAsync(ws.g, 0, sizeof(z64) * (m + 1), st));
+  // the orthogonalisation as one cooperative launch per iteration when its
+  // kChunks blocks can all be resident (else the separate kernels)
+  bool fused = false;
+  {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gmres_orth_kernel, 256,
+                                                      sizeof(z64) * (size_t)(m + 1)) == cudaSuccess)
+      fused = (long long)per_sm * H->nsm >= kChunks;
+    cudaGetLastError();
+  }
+  if (fused) LS_CUDA_TRY(cudaMemsetAsync(ws.sync, 0, 4 * sizeof(unsigned), st));
+  unsigned orth_epoch = 0;  // grid barriers passed so far (three per launch)
   norm2(f, N, ws.partial, ws.scal, st);
   // small host<->device transfers go through page-locked scratch
   unsigned char* pin = static_cast<unsigned char*>(pinned_scratch(256));
@@ -249,20 +379,36 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, int t
     if ((rc = hbs_apply(H, vj, zj, 1, transpose, st))) return rc;
     if ((rc = conv_apply(H, zj, ws.w, 1, mode, st))) return rc;
     int tk = prof_begin(st);
-    for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+    if (fused) {
+      const z64* Vc = ws.V;
+      z64* wv = ws.w;
+      long long ldv = N, Nn = N;
+      int jj = j, ldh = m;
+      GridSync gs{ws.sync, ws.sync + 1, reinterpret_cast<int*>(ws.sync + 2)};
+      unsigned e0 = orth_epoch;
+      int* err = H->d_err;
+      void* args[] = {&Vc, &ldv, &jj, &wv, &Nn, &ws.Hm, &ldh, &ws.partial, &ws.partial1, &ws.cs, &ws.sn, &ws.g, &ws.st,
+                      &gs, &e0, &err};
       count_launch();
-      dot_partials_kernel<<<dim3(kChunks, j + 1), 256, 0, st>>>(ws.V, N, ws.w, N, ws.partial);
+      LS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)gmres_orth_kernel, dim3(kChunks), dim3(256), args,
+                                              sizeof(z64) * (size_t)(j + 1), st));
+      orth_epoch += 3;
+    } else {
+      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+        count_launch();
+        dot_partials_kernel<<<dim3(kChunks, j + 1), 256, 0, st>>>(ws.V, N, ws.w, N, ws.partial);
+        count_launch();
+        reduce_partials_kernel<<<j + 1, 256, 0, st>>>(ws.partial, kChunks, ws.y, ws.Hm + j, m);
+        count_launch();
+        axpy_multi_kernel<<<nb, 256, 0, st>>>(ws.V, N, j + 1, ws.y, ws.w, N);
+      }
+      norm2(ws.w, N, ws.partial, ws.scal, st);
       count_launch();
-      reduce_partials_kernel<<<j + 1, 256, 0, st>>>(ws.partial, kChunks, ws.y, ws.Hm + j, m);
+      normalize_kernel<<<nb, 256, 0, st>>>(ws.w, ws.V + (long long)(j + 1) * N, N, ws.scal,
+                                           ws.Hm + (long long)(j + 1) * m + j);
       count_launch();
-      axpy_multi_kernel<<<nb, 256, 0, st>>>(ws.V, N, j + 1, ws.y, ws.w, N);
+      givens_kernel<<<1, 32, 0, st>>>(ws.Hm, m, ws.cs, ws.sn, ws.g, j, ws.st);
     }
-    norm2(ws.w, N, ws.partial, ws.scal, st);
-    count_launch();
-    normalize_kernel<<<nb, 256, 0, st>>>(ws.w, ws.V + (long long)(j + 1) * N, N, ws.scal,
-                                         ws.Hm + (long long)(j + 1) * m + j);
-    count_launch();
-    givens_kernel<<<1, 32, 0, st>>>(ws.Hm, m, ws.cs, ws.sn, ws.g, j, ws.st);
     // CGS2: per pass j+1 dot products and j+1 axpys over N complex entries, plus the norm
     prof_end(tk, PR_GMRES_ORTH, st, 16.0 * N * (2.0 * (2.0 * (j + 1) + 2.0) + 3.0),
              8.0 * N * (4.0 * (j + 1) + 1.0));

@@ -188,20 +188,25 @@ def test_ranks_match_oracle_compression():
 
 @pytest.mark.slow
 def test_precond_solve_full_size_n256():
-    """The measured workload (256 x 256, kappa = 60, 20-Gaussian b, eps = 1e-4):
-    the true residual is checked with the oracle's own FFT matvec."""
+    """The measured workload (256 x 256, kappa = 60, 20-Gaussian b, eps = 1e-4), also
+    in the measured configuration (tf32x3 merges, level 1 uncompressed): the true
+    residual is checked with the oracle's own FFT matvec."""
     n, kappa = 256, 60.0
     b = inputs.gaussian_family(n, 0)
-    for precision in (ls.LS_FP32, ls.LS_FP64):
-        H = build(n, kappa, b, 1e-4, precision=precision)
-        f = nystrom.rhs(kappa, b, n, n, 1.0 / n).reshape(n, n)
+    spec = nystrom.conv_kernel_spectrum(kappa, 1.0 / n, n, n, 10)
+    f = nystrom.rhs(kappa, b, n, n, 1.0 / n).reshape(n, n)
+    for precision, kw in ((ls.LS_FP32, {}), (ls.LS_FP64, {}), (ls.LS_TF32X3, {"top_uncompressed": 1})):
+        H = build(n, kappa, b, 1e-4, precision=precision, **kw)
         sig = torch.zeros(n, n, dtype=torch.complex128, device=DEV)
         info = ls.ls_solve(H, dev(f), sig)[0]
         s = host(sig).ravel()
-        spec = nystrom.conv_kernel_spectrum(kappa, 1.0 / n, n, n, 10)
         r = f.ravel() - nystrom.matvec_fft(spec, kappa, b, s)
         assert info["converged"]
         assert np.linalg.norm(r) / np.linalg.norm(f) < 2e-10
+        # the merge inverses of orders up to 1014 (16 panels, a ragged last one) pass
+        # their probe check without the row-pivoted fallback
+        assert H.info()["pivot_fallbacks"] == 0, (precision, kw)
+        ls.ls_free(H)
 
 
 @pytest.mark.parametrize("precision", [ls.LS_TF32X3, ls.LS_TF32])
