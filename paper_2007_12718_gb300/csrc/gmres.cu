@@ -143,28 +143,15 @@ __device__ __forceinline__ z64 block_sum_dp(z64 acc, z64* red) {
   return v2;
 }
 
-// Sum of the nchunk partials of row i in the order of reduce_partials_kernel
-// (valid in thread 0).
-__device__ __forceinline__ z64 reduce_row(const z64* __restrict__ partial, int nchunk, int i, z64* red) {
-  z64 a = mk<double>(0.0, 0.0);
-  for (int c = threadIdx.x; c < nchunk; c += blockDim.x) a = a + partial[(long long)i * nchunk + c];
-  a = warp_sum(a);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
-  __syncthreads();
-  z64 s = mk<double>(0.0, 0.0);
-  if (threadIdx.x == 0)
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s = s + red[k];
-  __syncthreads();
-  return s;
-}
-
 // One iteration's orthogonalisation in one cooperative launch of kChunks
 // blocks (block b owns the entries of chunk b, as in dot_partials_kernel):
 // classical Gram-Schmidt twice against V_0..V_j, ||w||, V_{j+1} = w / ||w||,
-// and the Givens step in block 0 (the only writer of column j of H).  The same
-// operations in the same order as the separate kernels, so the results are the
-// same bits; three grid barriers (bounded waits: a block that gives up sets
-// *err = LS_ETIMEOUT).  Dynamic shared memory: (j + 1) coefficients.
+// and the Givens step in block 0 (the only writer of column j of H).  Warp q of
+// a block takes the vectors i = q (mod warps): their dot products over the
+// block's chunk, then (after the grid barrier) their sums over all chunks in a
+// fixed order (read through L2: other blocks wrote them), so no block barrier
+// is needed per vector and runs are bitwise reproducible.  Three grid barriers (bounded waits: a block that gives up
+// sets *err = LS_ETIMEOUT).  Dynamic shared memory: (j + 1) coefficients.
 __global__ void __launch_bounds__(256) gmres_orth_kernel(const z64* __restrict__ V, long long ldv, int j, z64* w,
                                                          long long N, z64* Hm, int ldh, z64* part0, z64* part1,
                                                          z64* cs, z64* sn, z64* g, GmState* st, GridSync gs,
@@ -173,27 +160,30 @@ __global__ void __launch_bounds__(256) gmres_orth_kernel(const z64* __restrict__
   __shared__ z64 red[32];
   __shared__ z64 bc;
   const int b = blockIdx.x, G = gridDim.x, nvec = j + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const long long per = (N + G - 1) / G;
   const long long n0 = b * per, n1 = min(N, n0 + per);
   unsigned epoch = epoch0;
   for (int pass = 0; pass < 2; ++pass) {
     z64* part = pass ? part1 : part0;
-    for (int i = 0; i < nvec; ++i) {
+    for (int i = warp; i < nvec; i += nw) {
       const z64* v = V + i * ldv;
       z64 acc = mk<double>(0.0, 0.0);
-      for (long long n = n0 + threadIdx.x; n < n1; n += blockDim.x) fmac_(acc, v[n], w[n]);
-      const z64 t = block_sum_dp(acc, red);
-      if (threadIdx.x == 0) part[(long long)i * G + b] = t;
+      for (long long n = n0 + lane; n < n1; n += 32) fmac_(acc, v[n], w[n]);
+      acc = warp_sum(acc);
+      if (lane == 0) part[(long long)i * G + b] = acc;
     }
     if (!grid_sync(gs, G, epoch)) {
       if (threadIdx.x == 0) atomicExch(err, LS_ETIMEOUT);
       return;
     }
-    for (int i = 0; i < nvec; ++i) {
-      const z64 s = reduce_row(part, G, i, red);
-      if (threadIdx.x == 0) {
-        hc[i] = s;
-        if (b == 0) Hm[(long long)i * ldh + j] = Hm[(long long)i * ldh + j] + s;
+    for (int i = warp; i < nvec; i += nw) {
+      z64 a = mk<double>(0.0, 0.0);
+      for (int c = lane; c < G; c += 32) a = a + ldcg_cx(part + (long long)i * G + c);
+      a = warp_sum(a);
+      if (lane == 0) {
+        hc[i] = a;
+        if (b == 0) Hm[(long long)i * ldh + j] = Hm[(long long)i * ldh + j] + a;
       }
     }
     __syncthreads();
@@ -219,11 +209,13 @@ __global__ void __launch_bounds__(256) gmres_orth_kernel(const z64* __restrict__
     if (threadIdx.x == 0) atomicExch(err, LS_ETIMEOUT);
     return;
   }
-  {
-    const z64 s = reduce_row(part0, G, 0, red);
-    if (threadIdx.x == 0) bc = s;
-    __syncthreads();
+  if (warp == 0) {
+    z64 a = mk<double>(0.0, 0.0);
+    for (int c = lane; c < G; c += 32) a = a + ldcg_cx(part0 + c);
+    a = warp_sum(a);
+    if (lane == 0) bc = a;
   }
+  __syncthreads();
   const double nr = sqrt(bc.re);
   const double sc = nr > 0 ? 1.0 / nr : 0.0;
   z64* vn = const_cast<z64*>(V) + (long long)(j + 1) * ldv;
