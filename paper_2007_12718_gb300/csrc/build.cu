@@ -1780,6 +1780,7 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
         if (!flags) return LS_ENOMEM;
         LS_CUDA_TRY(cudaMemcpyAsync(flags, H->d_err + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         LS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (l == 0) host_mark("root_inverse_checked");
         float worst;
         memcpy(&worst, &flags[0], sizeof(float));
         const float limit = sizeof(R) == 4 ? 1e-3f : 1e-9f;
@@ -1864,6 +1865,7 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
   if (!pin) return LS_ENOMEM;
   LS_CUDA_TRY(cudaMemcpyAsync(pin, H->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
   LS_CUDA_TRY(cudaStreamSynchronize(st));
+  host_mark("build_checked");
   if (pin[0]) return pin[0];
   // bytes of one apply (Algorithm 2): every factor once, the X of levels L-1..1
   // a second time (the upward and the downward pass both apply it), the grid vectors

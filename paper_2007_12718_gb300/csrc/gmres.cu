@@ -341,6 +341,7 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, int t
   static_assert(sizeof(GmState) + sizeof(z64) <= 256, "pinned scratch too small");
   LS_CUDA_TRY(cudaMemcpyAsync(pin, ws.scal, sizeof(z64), cudaMemcpyDeviceToHost, st));
   LS_CUDA_TRY(cudaStreamSynchronize(st));
+  host_mark("gmres_rhs_norm");
   const double fnorm = sqrt(reinterpret_cast<z64*>(pin)->re);
   ls_solve_info inf;
   inf.iterations = 0;
@@ -449,6 +450,7 @@ int gmres_solve(ls_handle* H, const z64* f, z64* sigma, int nrhs, ls_solve_info*
     if (rc) return rc;
     H->gm_bytes = need;
   }
+  host_mark("gmres_workspace");
   int worst = LS_OK;
   for (int r = 0; r < nrhs; ++r) {
     int rc = solve_one(H, f + r * N, sigma + r * N, info ? info + r : nullptr, transpose, st);

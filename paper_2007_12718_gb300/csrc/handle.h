@@ -101,6 +101,8 @@ typedef std::function<void(int level)> LevelDone;
 // host reads go through it: a copy to pageable memory is synchronous inside
 // the driver and would stall the other build thread's launches.
 void* pinned_scratch(size_t bytes);
+// LS_TRACE=1: prints "ls host <label> <ms since the last ls_build started>" to stderr.
+void host_mark(const char* label);
 
 // compress.cu
 // With an auxiliary stream su, each level's U (the ID's back substitution) is

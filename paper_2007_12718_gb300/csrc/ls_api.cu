@@ -11,6 +11,7 @@
 #include <atomic>
 #include <chrono>
 #include <mutex>
+#include <vector>
 #include <thread>
 #include <condition_variable>
 #include <string>
@@ -34,17 +35,6 @@ bool is_device_ptr(const void* p) {
 
 int valid_order(int o) { return o == 2 || o == 4 || o == 6 || o == 8 || o == 10; }
 
-// Host-side build timeline (LS_TRACE=1): "ls host <label> <ms since the build started>".
-std::chrono::steady_clock::time_point g_build_t0;
-void host_mark(const char* label) {
-  static const bool on = [] {
-    const char* v = getenv("LS_TRACE");
-    return v && v[0] && v[0] != '0';
-  }();
-  if (!on) return;
-  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - g_build_t0).count();
-  fprintf(stderr, "ls host %s %.3f\n", label, ms);
-}
 
 __global__ void rhs_kernel(const double* b, int nx, int ny, double h, double x0, double y0, double kappa, double ct,
                            double stt, ls::z64* f) {
@@ -188,30 +178,66 @@ int pool_for_current_device(cudaMemPool_t* out) {
 }  // namespace
 
 namespace {
-struct PinnedScratch {
+// Page-locked scratch, one buffer per thread.  Each build runs its merges on a
+// thread of its own, so a thread's buffer goes back to a process-wide free
+// list when the thread ends (cudaFreeHost there would stall the end of every
+// build) and the next thread takes it from there.
+struct PinnedBuf {
   void* p = nullptr;
   size_t bytes = 0;
+};
+std::mutex g_pinned_mu;
+std::vector<PinnedBuf>& pinned_free_list() {
+  static std::vector<PinnedBuf>* v = new std::vector<PinnedBuf>();  // kept until process exit
+  return *v;
+}
+struct PinnedScratch {
+  PinnedBuf b;
   ~PinnedScratch() {
-    if (p) cudaFreeHost(p);
+    if (!b.p) return;
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    pinned_free_list().push_back(b);
   }
 };
 thread_local PinnedScratch g_pinned;
 }  // namespace
 
 void* pinned_scratch(size_t bytes) {
-  if (bytes > g_pinned.bytes) {
-    if (g_pinned.p) cudaFreeHost(g_pinned.p);
-    g_pinned.p = nullptr;
-    g_pinned.bytes = 0;
+  PinnedBuf& b = g_pinned.b;
+  if (!b.p) {
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    auto& fl = pinned_free_list();
+    if (!fl.empty()) {
+      b = fl.back();
+      fl.pop_back();
+    }
+  }
+  if (bytes > b.bytes) {
+    if (b.p) cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
     size_t want = std::max(bytes, (size_t)1 << 16);
-    if (cudaMallocHost(&g_pinned.p, want) != cudaSuccess) {
+    if (cudaMallocHost(&b.p, want) != cudaSuccess) {
       cudaGetLastError();
-      g_pinned.p = nullptr;
+      b.p = nullptr;
       return nullptr;
     }
-    g_pinned.bytes = want;
+    b.bytes = want;
   }
-  return g_pinned.p;
+  return b.p;
+}
+
+// Host-side build timeline (LS_TRACE=1): "ls host <label> <ms since the build started>".
+std::chrono::steady_clock::time_point g_build_t0;
+
+void host_mark(const char* label) {
+  static const bool on = [] {
+    const char* v = getenv("LS_TRACE");
+    return v && v[0] && v[0] != '0';
+  }();
+  if (!on) return;
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - g_build_t0).count();
+  fprintf(stderr, "ls host %s %.3f\n", label, ms);
 }
 
 StreamScope::StreamScope(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
@@ -440,19 +466,19 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
     cv.notify_all();
   };
   int rc;
-  host_mark("pipeline_started");
+  ls::host_mark("pipeline_started");
   {
     ls::StreamScope scope(sc);
     rc = ls::compress(H, sc, level_done, su);
   }
-  host_mark("compress_returned");
+  ls::host_mark("compress_returned");
   if (rc) {
     std::lock_guard<std::mutex> lk(mu);
     abort = true;
   }
   cv.notify_all();
   merger.join();
-  host_mark("merges_joined");
+  ls::host_mark("merges_joined");
   if (!rc && mrc) {
     rc = mrc;
     set_error(merr.c_str());
@@ -472,7 +498,7 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
 
 static int build_impl(const ls_grid* grid, double kappa, const double* b, double tol, const ls_opts* opts,
                       cudaStream_t st, ls_handle** out) {
-  g_build_t0 = std::chrono::steady_clock::now();
+  ls::g_build_t0 = std::chrono::steady_clock::now();
   ls_handle* H = new ls_handle();
   *out = H;
   H->stream = st;
@@ -592,9 +618,9 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
     set_error("b must be finite and <= 1");
     return LS_EINVAL;
   }
-  host_mark("setup_done");
+  ls::host_mark("setup_done");
   rc = build_pipelined(H, st);
-  host_mark("pipeline_done");
+  ls::host_mark("pipeline_done");
   // long finished by now: the handle is complete on return, for any stream
   cudaStreamSynchronize(H->side_stream);
   cudaEventDestroy(ev_side);
@@ -667,6 +693,7 @@ int ls_apply(ls_handle* H, const void* f, void* q, int nrhs, int transpose, void
 static int solve_entry(ls_handle* H, const void* f, void* sigma, int nrhs, ls_solve_info* info, int transpose,
                        void* stream) {
   if (!H || !f || !sigma || nrhs < 1) return LS_EINVAL;
+  ls::host_mark("solve_entered");
   ls::StreamScope scope((cudaStream_t)stream);
   H->stream = (cudaStream_t)stream;
   cudaStream_t st = (cudaStream_t)stream;
