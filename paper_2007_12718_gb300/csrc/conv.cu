@@ -38,9 +38,15 @@ __device__ void fft_dif(z64* s, int L, int logL, int stride, const z64* tw) {
       int j = b & (half - 1), g = b >> lh;
       int i0 = (g << (lh + 1)) + j, i1 = i0 + half;
       z64 a = s[i0 * stride + c], bb = s[i1 * stride + c];
-      z64 w = tw[j * tstep];
       s[i0 * stride + c] = a + bb;
-      s[i1 * stride + c] = w * (a - bb);
+      const z64 d = a - bb;
+      // the last two stages' twiddles are 1 and e^{-i pi/2} = -i: no multiply
+      if (lh == 0)
+        s[i1 * stride + c] = d;
+      else if (lh == 1)
+        s[i1 * stride + c] = j ? mk<double>(d.im, -d.re) : d;
+      else
+        s[i1 * stride + c] = tw[j * tstep] * d;
     }
     __syncthreads();
   }
@@ -58,8 +64,15 @@ __device__ void fft_dit_inv(z64* s, int L, int logL, int stride, const z64* tw) 
       int c = t % count, b = t / count;
       int j = b & (half - 1), g = b >> lh;
       int i0 = (g << (lh + 1)) + j, i1 = i0 + half;
-      z64 w = conjz(tw[j * tstep]);
-      z64 a = s[i0 * stride + c], tt = w * s[i1 * stride + c];
+      const z64 a = s[i0 * stride + c], x = s[i1 * stride + c];
+      // the first two stages' twiddles are 1 and e^{i pi/2} = i: no multiply
+      z64 tt;
+      if (lh == 0)
+        tt = x;
+      else if (lh == 1)
+        tt = j ? mk<double>(-x.im, x.re) : x;
+      else
+        tt = conjz(tw[j * tstep]) * x;
       s[i0 * stride + c] = a + tt;
       s[i1 * stride + c] = a - tt;
     }
