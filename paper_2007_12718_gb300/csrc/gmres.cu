@@ -91,6 +91,16 @@ struct GmState {
   int k;
 };
 
+// GMRES start on the device: ||f|| from nrm2->re, residual estimate 1, g = (||f||, 0, ...).
+__global__ void gmres_init_kernel(const z64* nrm2, GmState* st, z64* g) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double fnorm = sqrt(nrm2->re);
+  st->fnorm = fnorm;
+  st->resid = 1.0;
+  st->k = 0;
+  g[0] = mk<double>(fnorm, 0.0);
+}
+
 // Column j of H: apply the earlier rotations, form the new one, update g.
 __device__ void givens_step(z64* H, int ldh, z64* cs, z64* sn, z64* g, int j, GmState* st) {
   z64* col = H + j;  // H[i][j] at H[i*ldh + j]
@@ -339,30 +349,19 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, int t
   unsigned char* pin = static_cast<unsigned char*>(pinned_scratch(256));
   if (!pin) return LS_ENOMEM;
   static_assert(sizeof(GmState) + sizeof(z64) <= 256, "pinned scratch too small");
-  LS_CUDA_TRY(cudaMemcpyAsync(pin, ws.scal, sizeof(z64), cudaMemcpyDeviceToHost, st));
-  LS_CUDA_TRY(cudaStreamSynchronize(st));
-  host_mark("gmres_rhs_norm");
-  const double fnorm = sqrt(reinterpret_cast<z64*>(pin)->re);
+  // ||f|| stays on the device (state and g_0 set there, v_0 = f / ||f||, zero for
+  // f = 0); the host learns it with the first iteration's state
+  count_launch();
+  gmres_init_kernel<<<1, 32, 0, st>>>(ws.scal, ws.st, ws.g);
+  count_launch();
+  normalize_kernel<<<nb, 256, 0, st>>>(f, ws.V, N, ws.scal, nullptr);
+  GmState* hs = reinterpret_cast<GmState*>(pin);
+  double fnorm = 0.0;
   ls_solve_info inf;
   inf.iterations = 0;
   inf.converged = 1;
   inf.resid_est = 0.0;
   inf.resid_true = 0.0;
-  if (fnorm == 0.0) {
-    LS_CUDA_TRY(cudaMemsetAsync(sigma, 0, sizeof(z64) * N, st));
-    if (info) *info = inf;
-    return LS_OK;
-  }
-  GmState* hs = reinterpret_cast<GmState*>(pin);
-  hs->fnorm = fnorm;
-  hs->resid = 1.0;
-  hs->k = 0;
-  LS_CUDA_TRY(cudaMemcpyAsync(ws.st, hs, sizeof(GmState), cudaMemcpyHostToDevice, st));
-  z64* g0 = reinterpret_cast<z64*>(pin + 128);
-  *g0 = mk<double>(fnorm, 0.0);
-  LS_CUDA_TRY(cudaMemcpyAsync(ws.g, g0, sizeof(z64), cudaMemcpyHostToDevice, st));
-  count_launch();
-  normalize_kernel<<<nb, 256, 0, st>>>(f, ws.V, N, ws.scal, nullptr);
   int k = 0;
   double resid = 1.0;
   const double tol = H->opts.gmres_tol;
@@ -408,6 +407,14 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, int t
     if ((rc = check_launch("gmres iteration"))) return rc;
     LS_CUDA_TRY(cudaMemcpyAsync(hs, ws.st, sizeof(GmState), cudaMemcpyDeviceToHost, st));
     LS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (j == 0) {
+      fnorm = hs->fnorm;
+      if (fnorm == 0.0) {  // f = 0: sigma = 0 (the iteration ran on zero vectors)
+        LS_CUDA_TRY(cudaMemsetAsync(sigma, 0, sizeof(z64) * N, st));
+        if (info) *info = inf;
+        return LS_OK;
+      }
+    }
     k = j + 1;
     resid = hs->resid;
     if (resid <= tol) break;
