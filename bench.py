@@ -39,6 +39,22 @@ WORKLOAD_TEXT = ("256x256 grid (N=65,536), kappa=60, b = 20 seeded Gaussians (se
 FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fp64_tflops": 1.25, "fp32_tflops": 80.5}
 
 
+def max_over_ranks(values, world, device=None):
+    """Per-rank times (s) reduced to their maximum over all ranks (every rank gets
+    the result; an all-reduce on the default process group); unchanged at world 1."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_rate(world, units_per_rank, seconds):
+    """Whole-job throughput in millions of units per second: every rank (a replica)
+    processed units_per_rank within `seconds`, the max over ranks."""
+    return world * units_per_rank / seconds / 1e6
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -298,15 +314,12 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         t_e2e += time.perf_counter() - t0
 
-    times = torch.tensor([t_mixed, t_fp64, t_e2e], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
-    t_mixed, t_fp64, t_e2e = times.tolist()
+    t_mixed, t_fp64, t_e2e = max_over_ranks([t_mixed, t_fp64, t_e2e], world, dev)
     if rank != 0:
         return
-    value = world * N * args.steps / t_mixed / 1e6
-    value64 = world * N * steps64 / t_fp64 / 1e6
-    e2e = world * N * args.steps / t_e2e / 1e6 if t_e2e > 0 else None
+    value = job_rate(world, N * args.steps, t_mixed)
+    value64 = job_rate(world, N * steps64, t_fp64)
+    e2e = job_rate(world, N * args.steps, t_e2e) if t_e2e > 0 else None
 
     # roofline of every timed kernel family; the one with the largest device time is the headline
     pk = peaks()
