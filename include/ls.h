@@ -71,7 +71,24 @@ typedef struct {
                          row-pivoted inverse as fallback (default); 1 = always row-pivoted   */
   int top_uncompressed; /* levels 1..top_uncompressed keep every row as skeleton (U = I,
                          no ID); 0 = every level compressed as in Sec. 3.2 (default)      */
+  int id_method;      /* per-level ID (Sec. 2.1): LS_ID_AUTO (default), LS_ID_GREEDY or
+                         LS_ID_BLOCKED, see ls_row_id_ex                                  */
 } ls_opts;
+
+/* Pivot selection of the row ID (ls_opts.id_method, ls_row_id_ex).
+ *  LS_ID_GREEDY : one pivot per step, the candidate of largest residual norm --
+ *                 the pivots of a column-pivoted QR (Sec. 2.1).
+ *  LS_ID_BLOCKED: pivots in blocks of up to 32.  Each block considers the 64
+ *                 candidates of largest residual norm, orders them by a greedy
+ *                 pivoted Cholesky of their Gram matrix (the column-pivoted QR
+ *                 restricted to those 64) and accepts a candidate while its
+ *                 residual norm is at least half the largest residual norm of
+ *                 the candidates left out; the other candidates are then updated
+ *                 by GEMM-shaped kernels.  The rank is decided by the same
+ *                 Frobenius-norm rule, on the explicit residual.
+ *  LS_ID_AUTO   : blocked for 256 candidates or more (and wherever a candidate's
+ *                 vector is too long for the greedy kernels), greedy below. */
+enum { LS_ID_AUTO = 0, LS_ID_GREEDY = 1, LS_ID_BLOCKED = 2 };
 
 typedef struct {
   int iterations;     /* GMRES iterations taken */
@@ -266,6 +283,13 @@ int ls_cgemm_c64(int engine, int ta, int tb, int M, int N, int K, const float* a
  * argument, LS_ENOMEM, LS_ECUDA, or LS_ETIMEOUT if a grid barrier wait gave up.
  * Synchronises the stream before returning. */
 int ls_row_id(const void* A, int m, int p, double eps, int precision, int* k, int* piv, void* U, void* stream);
+
+/* ls_row_id_ex -- ls_row_id with the pivot selection chosen by method
+ * (LS_ID_AUTO, LS_ID_GREEDY or LS_ID_BLOCKED; ls_row_id is LS_ID_GREEDY).  With
+ * LS_ID_BLOCKED the pivots are a valid skeleton but need not be the greedy
+ * ones; the rank rule and the outputs are the same.  A is not modified. */
+int ls_row_id_ex(const void* A, int m, int p, double eps, int precision, int method, int* k, int* piv, void* U,
+                 void* stream);
 
 /* Static text for an LS_E* code, and the last error message of this thread. */
 const char* ls_strerror(int code);

@@ -30,11 +30,12 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libls.so")
 
 LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ESINGULAR, LS_ENOCONV, LS_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 LS_FP64, LS_FP32, LS_TF32, LS_TF32X3 = 0, 1, 2, 3
+LS_ID_AUTO, LS_ID_GREEDY, LS_ID_BLOCKED = 0, 1, 2
 
 EXPORTED = ["ls_default_opts", "ls_build", "ls_apply", "ls_matvec", "ls_solve", "ls_rhs_plane_wave",
             "ls_get_build_info", "ls_free", "ls_strerror", "ls_last_error", "ls_profile_enable",
             "ls_profile_reset", "ls_profile_get", "ls_kernel_launches", "ls_matvec_noalloc",
-            "ls_matvec_noalloc_max_elems", "ls_cgemm_c64", "ls_row_id", "ls_field", "ls_solve_transpose",
+            "ls_matvec_noalloc_max_elems", "ls_cgemm_c64", "ls_row_id", "ls_row_id_ex", "ls_field", "ls_solve_transpose",
             "ls_set_receivers", "ls_receiver_field", "ls_receiver_adjoint", "ls_misfit_gradient"]
 
 
@@ -47,7 +48,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("order_matvec", ctypes.c_int), ("order_precond", ctypes.c_int), ("leaf_side", ctypes.c_int),
                 ("proxy_width", ctypes.c_int), ("precision", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("merge_pivoting", ctypes.c_int),
-                ("top_uncompressed", ctypes.c_int)]
+                ("top_uncompressed", ctypes.c_int), ("id_method", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -124,6 +125,9 @@ def load_library(path=LIB_PATH):
     lib.ls_cgemm_c64.restype = ip
     lib.ls_row_id.argtypes = [vp, ip, ip, dp, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp, vp]
     lib.ls_row_id.restype = ip
+    lib.ls_row_id_ex.argtypes = [vp, ip, ip, dp, ip, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                 vp, vp]
+    lib.ls_row_id_ex.restype = ip
     lib.ls_kernel_launches.argtypes = []
     lib.ls_kernel_launches.restype = ctypes.c_longlong
     _lib = lib
@@ -202,12 +206,12 @@ def default_opts():
 
 def ls_build(n, h, kappa, b, tol, order_matvec=10, order_precond=4, leaf_side=8, proxy_width=0,
              precision=LS_FP32, gmres_maxit=100, gmres_tol=1e-10, x0=0.0, y0=0.0, ny=None, stream=None,
-             merge_pivoting=0, top_uncompressed=0):
+             merge_pivoting=0, top_uncompressed=0, id_method=LS_ID_AUTO):
     """Compress G and build the HBS inverse (Sec. 3.2, Algorithm 1); b is [ny][nx] float64."""
     lib = load_library()
     g = Grid(n, n if ny is None else ny, h, x0, y0)
     o = Opts(order_matvec, order_precond, leaf_side, proxy_width, precision, gmres_maxit, gmres_tol,
-             merge_pivoting, top_uncompressed)
+             merge_pivoting, top_uncompressed, id_method)
     bp, keep, _ = _ptr(b, np.float64)
     out = ctypes.c_void_p()
     _check(lib.ls_build(ctypes.byref(g), kappa, bp, tol, ctypes.byref(o), _stream(stream), ctypes.byref(out)),
@@ -406,10 +410,11 @@ def ls_cgemm_c64(engine, A, B, C, ta=False, tb=False, alpha=1.0, beta=0.0, strea
     return C
 
 
-def ls_row_id(A, eps, precision=LS_FP64, stream=None):
+def ls_row_id(A, eps, precision=LS_FP64, stream=None, method=LS_ID_GREEDY):
     """Row ID A ~ U A(J, :) of an m x p complex128 matrix (rows = candidates) by
-    the device column-pivoted QR (Sec. 2.1).  A: numpy array or torch tensor
-    (host or CUDA).  Returns (k, piv[:k] as numpy int array, U as an m x k numpy array)."""
+    the device column-pivoted QR (Sec. 2.1), greedy (one pivot per step) or in
+    blocks of pivots (method).  A: numpy array or torch tensor (host or CUDA).
+    Returns (k, piv[:k] as numpy int array, U as an m x k numpy array)."""
     lib = load_library()
     m, p = A.shape
     ap, keep, _ = _ptr(A, np.complex128)
@@ -417,8 +422,8 @@ def ls_row_id(A, eps, precision=LS_FP64, stream=None):
     piv = (ctypes.c_int * max(kmax, 1))()
     U = np.zeros((m, kmax), np.complex128)
     k = ctypes.c_int(0)
-    _check(lib.ls_row_id(ap, m, p, eps, precision, ctypes.byref(k), piv, ctypes.c_void_p(U.ctypes.data),
-                         _stream(stream)), "ls_row_id")
+    _check(lib.ls_row_id_ex(ap, m, p, eps, precision, method, ctypes.byref(k), piv, ctypes.c_void_p(U.ctypes.data),
+                            _stream(stream)), "ls_row_id_ex")
     kk = k.value
     Uk = U.reshape(-1)[: m * kk].reshape(m, kk).copy()
     return kk, np.array(piv[:kk], dtype=np.int64), Uk

@@ -12,8 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libls.so")
-SOURCES = ["ls_api.cu", "conv.cu", "compress.cu", "build.cu", "gmres.cu", "tc_gemm.cu", "adjoint.cu", "quad.cpp",
-           "prof.cpp"]
+SOURCES = ["ls_api.cu", "conv.cu", "compress.cu", "build.cu", "gmres.cu", "tc_gemm.cu", "adjoint.cu", "id_blocked.cu",
+           "quad.cpp", "prof.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

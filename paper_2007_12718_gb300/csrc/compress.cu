@@ -1015,6 +1015,71 @@ int upload_block(const std::vector<int>& rx, const std::vector<int>& ry, const s
   return check_launch("kernel block");
 }
 
+// Row ID by blocks of pivots (id_blocked.cu) followed by the same back
+// substitution as the greedy kernels' (on su when given, like them).  A is
+// overwritten.
+template <class R>
+int run_row_id_blocked(cx<R>* A, int m, int p, double eps, cudaStream_t st, int* k_out, std::vector<int>* hp,
+                       cx<R>* Uout, cudaStream_t su) {
+  int rc;
+  const int kmax = std::min(m, p);
+  const size_t need_t = 5 * 256 + sizeof(cx<R>) * ((size_t)kmax * m + (size_t)kmax * kmax) + sizeof(int) * (2 * (size_t)m + 8);
+  char* tsp = nullptr;
+  if ((rc = dalloc((void**)&tsp, need_t))) return rc;
+  char* cur = tsp;
+  auto carve = [&](size_t bytes) {
+    char* r = cur;
+    cur += (bytes + 255) & ~(size_t)255;
+    return r;
+  };
+  cx<R>* Rm = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)kmax * m));
+  cx<R>* RT = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)kmax * kmax));
+  int* sel = reinterpret_cast<int*>(carve(sizeof(int) * m));
+  int* piv = reinterpret_cast<int*>(carve(sizeof(int) * m));
+  int* rank = reinterpret_cast<int*>(carve(sizeof(int) * 8));
+  int tk = prof_begin(st);
+  int k = 0;
+  rc = blocked_row_id<R>(A, m, p, eps, st, Rm, RT, sel, rank, piv, &k, hp);
+  // algorithmic work of the ID: ~8 m p k real flops (one projection of every
+  // candidate on every pivot direction); one read of the block
+  prof_end(tk, PR_CPQR, st, sizeof(cx<R>) * (double)m * p, 8.0 * m * (double)p * k);
+  if (rc) {
+    dfree(tsp);
+    return rc;
+  }
+  cudaStream_t sb = st;
+  if (su && Uout && k > 0) {
+    cudaEvent_t e;
+    LS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    LS_CUDA_TRY(cudaEventRecord(e, st));
+    LS_CUDA_TRY(cudaStreamWaitEvent(su, e, 0));
+    cudaEventDestroy(e);
+    sb = su;
+  }
+  if (Uout && k > 0) {
+    constexpr int CB = 4;
+    const size_t smt = sizeof(cx<R>) * ((size_t)CB * kmax + (size_t)2 * kTrsmNB * kTrsmNB);
+    if (smt > 48 * 1024)
+      LS_CUDA_TRY(cudaFuncSetAttribute(id_trsm_kernel<R, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt));
+    count_launch();
+    id_trsm_kernel<R, CB><<<(unsigned)((m + CB - 1) / CB), kTrsmThreads, smt, sb>>>(Rm, RT, sel, rank, m, kmax, Uout);
+    if ((rc = check_launch("blocked ID back substitution"))) return rc;
+  }
+  if (sb != st) {
+    ls::StreamScope scope(sb);
+    dfree(tsp);
+  } else {
+    dfree(tsp);
+  }
+  *k_out = k;
+  return LS_OK;
+}
+
+// Candidates from which the blocked ID takes over from the greedy kernels
+// (ID_AUTO), and above which only the blocked ID applies (the greedy kernels
+// keep a candidate's residual in registers or one block's shared memory).
+constexpr int kBlockedMinRows = 256;
+
 // Row ID of the device matrix A (m candidates x p, candidate-major) by the
 // column-pivoted QR kernels above: one thread-block cluster when the
 // candidates fit in the shared memory of at most 16 blocks, else one
@@ -1023,8 +1088,19 @@ int upload_block(const std::vector<int>& rx, const std::vector<int>& ry, const s
 // scratch for the grid barrier and the kernels' status words.
 template <class R>
 int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_buf, cudaStream_t st, int* k_out,
-               std::vector<int>* hp_out, cx<R>* Uout, cudaStream_t su = nullptr) {
+               std::vector<int>* hp_out, cx<R>* Uout, cudaStream_t su = nullptr, int method = ID_GREEDY,
+               bool a_mutable = false) {
   int rc;
+  const bool greedy_fits = (p + 127) / 128 <= (sizeof(R) == 4 ? 16 : 8);
+  if (method == ID_BLOCKED || (method == ID_AUTO && (m >= kBlockedMinRows || !greedy_fits))) {
+    if (a_mutable) return run_row_id_blocked<R>(const_cast<cx<R>*>(A), m, p, eps_in, st, k_out, hp_out, Uout, su);
+    cx<R>* Aw = nullptr;
+    if ((rc = dalloc((void**)&Aw, sizeof(cx<R>) * (size_t)m * p))) return rc;
+    LS_CUDA_TRY(cudaMemcpyAsync(Aw, A, sizeof(cx<R>) * (size_t)m * p, cudaMemcpyDeviceToDevice, st));
+    rc = run_row_id_blocked<R>(Aw, m, p, eps_in, st, k_out, hp_out, Uout, su);
+    dfree(Aw);
+    return rc;
+  }
   std::vector<int>& hp = *hp_out;
   const int kmax = std::min(m, p);
   if (m >= (1 << 20)) {  // pivot keys carry 20 index bits
@@ -1389,7 +1465,8 @@ int compress_t(ls_handle* H, cudaStream_t st, const LevelDone& level_done, cudaS
     if ((rc = dalloc((void**)&dint, sizeof(int) * (2 * m + 2 * p + 8)))) return rc;
     if ((rc = upload_block<R>(rows_x, rows_y, px, py, A, dint, st, H->ks_prec, KernelTable{H->ktab, H->ktx, H->kty}))) return rc;
     if ((rc = dalloc(&lv.U, sizeof(cx<R>) * (size_t)m * std::max(std::min(m, p), 1)))) return rc;
-    if ((rc = run_row_id<R>(A, m, p, H->tol, H->nsm, H->sync_buf, st, &k, &hp, reinterpret_cast<cx<R>*>(lv.U), su)))
+    if ((rc = run_row_id<R>(A, m, p, H->tol, H->nsm, H->sync_buf, st, &k, &hp, reinterpret_cast<cx<R>*>(lv.U), su,
+                            H->opts.id_method, true)))
       return rc;
     ls::dfree(A);
     lv.k = k;
@@ -1416,14 +1493,14 @@ __global__ void convert_kernel(cx<Ro>* out, const cx<Ri>* in, long long n) {
 }
 }  // namespace
 
-int row_id(const z64* A, int m, int p, double eps, int precision, int nsm, int* sync_buf, cudaStream_t st, int* k,
-           int* piv, z64* U) {
+int row_id(const z64* A, int m, int p, double eps, int precision, int method, int nsm, int* sync_buf,
+           cudaStream_t st, int* k, int* piv, z64* U) {
   *k = 0;
   if (m <= 0 || p <= 0) return LS_OK;
   std::vector<int> hp;
   int rc;
   if (precision == LS_FP64) {
-    rc = run_row_id<double>(A, m, p, eps, nsm, sync_buf, st, k, &hp, U);
+    rc = run_row_id<double>(A, m, p, eps, nsm, sync_buf, st, k, &hp, U, nullptr, method, false);
   } else {
     const long long nA = (long long)m * p, nU = (long long)m * std::min(m, p);
     c32* A32 = nullptr;
@@ -1432,7 +1509,7 @@ int row_id(const z64* A, int m, int p, double eps, int precision, int nsm, int* 
     if ((rc = dalloc((void**)&U32, sizeof(c32) * nU))) return rc;
     count_launch();
     convert_kernel<float, double><<<(unsigned)((nA + 255) / 256), 256, 0, st>>>(A32, A, nA);
-    rc = run_row_id<float>(A32, m, p, eps, nsm, sync_buf, st, k, &hp, U ? U32 : nullptr);
+    rc = run_row_id<float>(A32, m, p, eps, nsm, sync_buf, st, k, &hp, U ? U32 : nullptr, nullptr, method, true);
     if (!rc && U && *k > 0) {
       const long long nk = (long long)m * *k;
       count_launch();

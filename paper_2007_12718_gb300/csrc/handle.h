@@ -115,8 +115,19 @@ int leaf_block(ls_handle* H, cudaStream_t st);
 int sibling_block(ls_handle* H, int l, cudaStream_t st);
 // Row ID of the device matrix A (m x p, candidate-major) in the given precision;
 // piv (host, m entries) and U (device, m x min(m, p) entries) receive k pivots / columns.
-int row_id(const z64* A, int m, int p, double eps, int precision, int nsm, int* sync_buf, cudaStream_t st, int* k,
-           int* piv, z64* U);
+// method: ID_AUTO (blocked above a size threshold), ID_GREEDY (one pivot per
+// step, the same pivots as a column-pivoted QR), ID_BLOCKED (id_blocked.cu).
+enum IdMethod { ID_AUTO = 0, ID_GREEDY = 1, ID_BLOCKED = 2 };
+int row_id(const z64* A, int m, int p, double eps, int precision, int method, int nsm, int* sync_buf,
+           cudaStream_t st, int* k, int* piv, z64* U);
+
+// id_blocked.cu: the row ID in blocks of pivots (A is overwritten by the trailing
+// residual).  Writes what the ID's back substitution reads -- Rm (k x m), RT
+// (k x k), sel (m), rank (1) -- and the pivots piv (device, m entries); returns
+// k and the pivots on the host.
+template <class R>
+int blocked_row_id(cx<R>* A, int m, int p, double eps, cudaStream_t st, cx<R>* Rm, cx<R>* RT, int* sel, int* rank,
+                   int* piv, int* k_out, std::vector<int>* hp);
 
 // build.cu (Algorithm 1) and apply (Algorithm 2)
 int hbs_build(ls_handle* H, cudaStream_t st, const LevelWait& wait_level = LevelWait());

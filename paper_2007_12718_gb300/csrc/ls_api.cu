@@ -289,6 +289,7 @@ void ls_default_opts(ls_opts* o) {
   o->gmres_tol = 1e-10;
   o->merge_pivoting = 0;
   o->top_uncompressed = 0;
+  o->id_method = LS_ID_AUTO;
 }
 
 const char* ls_strerror(int code) {
@@ -309,8 +310,13 @@ const char* ls_last_error(void) { return g_last_error.c_str(); }
 long long ls_kernel_launches(void) { return ls::g_launches.load(); }
 
 int ls_row_id(const void* A, int m, int p, double eps, int precision, int* k, int* piv, void* U, void* stream) {
+  return ls_row_id_ex(A, m, p, eps, precision, LS_ID_GREEDY, k, piv, U, stream);
+}
+
+int ls_row_id_ex(const void* A, int m, int p, double eps, int precision, int method, int* k, int* piv, void* U,
+                 void* stream) {
   if (!A || !k || !piv || m < 1 || m >= (1 << 20) || p < 1 || !(eps > 0 && eps < 1) ||
-      (precision != LS_FP64 && precision != LS_FP32)) {
+      (precision != LS_FP64 && precision != LS_FP32) || method < LS_ID_AUTO || method > LS_ID_BLOCKED) {
     set_error("invalid ls_row_id argument");
     return LS_EINVAL;
   }
@@ -326,7 +332,7 @@ int ls_row_id(const void* A, int m, int p, double eps, int precision, int* k, in
   int rc = stage_in(A, bytesA, st, &sa);
   if (!rc && U) rc = stage_out_alloc(U, bytesU, &su);
   if (!rc) rc = ls::dalloc((void**)&sync_buf, 256);
-  if (!rc) rc = ls::row_id(sa.dev, m, p, eps, precision, nsm, sync_buf, st, k, piv, U ? su.dev : nullptr);
+  if (!rc) rc = ls::row_id(sa.dev, m, p, eps, precision, method, nsm, sync_buf, st, k, piv, U ? su.dev : nullptr);
   if (!rc && U && su.owned && *k > 0) {
     cudaError_t e = cudaMemcpyAsync(U, su.dev, sizeof(ls::z64) * (size_t)m * *k, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) {
@@ -513,7 +519,7 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
   if (!valid_order(o.order_matvec) || !valid_order(o.order_precond) || o.order_precond == 2 || o.leaf_side < 2 ||
       o.gmres_maxit < 1 || !(o.gmres_tol > 0) || (o.precision < LS_FP64 || o.precision > LS_TF32X3) ||
       o.proxy_width < 0 || o.merge_pivoting < 0 || o.merge_pivoting > 1 ||
-      o.top_uncompressed < 0) {
+      o.top_uncompressed < 0 || o.id_method < LS_ID_AUTO || o.id_method > LS_ID_BLOCKED) {
     set_error("invalid ls_opts");
     return LS_EINVAL;
   }

@@ -69,3 +69,95 @@ def test_invalid_arguments():
         ls.ls_row_id(A, 0.0)
     with pytest.raises(ls.LSError):
         ls.ls_row_id(A, 1e-3, precision=ls.LS_TF32)
+
+
+# ------------------------------------------------------------------ blocked pivot selection
+def level_rows(n, kappa, level, eps=1e-4, ring=2, order=4):
+    """Rows (candidates) of the level-`level` proxy block of an n x n grid: the
+    children's skeletons from the oracle's greedy IDs of the levels below."""
+    t = hbs.Tree(n, n, 8)
+    h = 1.0 / n
+    skel = None
+    for l in range(t.L, level - 1, -1):
+        w, hh = t.dims[l]
+        if l == t.L:
+            rows = hbs.box_points(w, hh)
+        else:
+            oa, ob = t.offsets[l]
+            rows = np.concatenate([skel + oa, skel + ob])
+        A = hbs.kernel_block(kappa, h, order, rows, hbs.proxy_ring(w, hh, ring))
+        if l == level:
+            return A
+        J, _ = hbs.row_id(A, eps)
+        skel = rows[J]
+
+
+@pytest.mark.parametrize("m,p,eps,prec", [(60, 90, 1e-5, ls.LS_FP64), (300, 200, 1e-5, ls.LS_FP64),
+                                          (700, 500, 1e-7, ls.LS_FP64), (1500, 900, 1e-6, ls.LS_FP64),
+                                          (700, 500, 1e-4, ls.LS_FP32), (1500, 900, 1e-4, ls.LS_FP32)])
+def test_blocked_id_random_matrix(m, p, eps, prec):
+    """Blocked pivots on matrices with distinct, geometrically decaying singular
+    values: the rank is decided on the explicit residual, so the ID error is
+    within the tolerance and the rank within 2 % of the greedy one."""
+    A = random_decaying(m, p, 3)
+    J0, _ = hbs.row_id(A, eps)
+    k, J, U = ls.ls_row_id(A, eps, precision=prec, method=ls.LS_ID_BLOCKED)
+    assert abs(k - len(J0)) <= max(2, 0.02 * len(J0)), (k, len(J0))
+    assert len(set(J.tolist())) == k
+    assert np.allclose(U[J, :], np.eye(k), atol=0)
+    assert id_error(A, J, U) <= (1.5 if prec == ls.LS_FP64 else 10) * eps
+
+
+@pytest.mark.parametrize("n,kappa,level,prec", [(64, 40.0, 3, ls.LS_FP64), (128, 78.5, 3, ls.LS_FP32),
+                                                (128, 78.5, 2, ls.LS_FP64), (256, 157.0, 4, ls.LS_FP32)])
+def test_blocked_id_proxy_blocks(n, kappa, level, prec):
+    """Upper-level proxy blocks (rows: the children's skeletons) at ~10 points per
+    wavelength, the regime of the 2048^2 workload: rank within 2 % of the
+    oracle's CPQR, ID error <= 3 eps (FP64) / 10 eps (FP32)."""
+    eps = 1e-4
+    A = level_rows(n, kappa, level, eps)
+    J0, _ = hbs.row_id(A, eps)
+    for method in (ls.LS_ID_BLOCKED, ls.LS_ID_AUTO):
+        k, J, U = ls.ls_row_id(A, eps, precision=prec, method=method)
+        assert abs(k - len(J0)) <= max(2, 0.02 * len(J0)), (method, k, len(J0))
+        assert len(set(J.tolist())) == k
+        assert np.allclose(U[J, :], np.eye(k), atol=0)
+        assert id_error(A, J, U) <= (3 if prec == ls.LS_FP64 else 10) * eps
+
+
+def test_blocked_id_edge_cases():
+    """One candidate, one proxy, fewer proxies than candidates (rank capped at p),
+    exact low rank, a zero block, and fewer candidates than the pool."""
+    rng = np.random.default_rng(11)
+    for prec in (ls.LS_FP64, ls.LS_FP32):
+        tol = 1e-10 if prec == ls.LS_FP64 else 1e-5
+        A = rng.standard_normal((1, 7)) + 1j * rng.standard_normal((1, 7))
+        k, J, U = ls.ls_row_id(A, 1e-6, precision=prec, method=ls.LS_ID_BLOCKED)
+        assert k == 1 and J[0] == 0 and U[0, 0] == 1
+        A = rng.standard_normal((9, 1)) + 1j * rng.standard_normal((9, 1))
+        k, J, U = ls.ls_row_id(A, 1e-6, precision=prec, method=ls.LS_ID_BLOCKED)
+        assert k == 1 and id_error(A, J, U) <= tol
+        A = rng.standard_normal((300, 40)) + 1j * rng.standard_normal((300, 40))
+        k, J, U = ls.ls_row_id(A, 1e-6, precision=prec, method=ls.LS_ID_BLOCKED)
+        assert k <= 40 and id_error(A, J, U) <= 1e-6 + tol
+        B = (rng.standard_normal((400, 17)) + 1j * rng.standard_normal((400, 17))) @ \
+            (rng.standard_normal((17, 250)) + 1j * rng.standard_normal((17, 250)))
+        k, J, U = ls.ls_row_id(B, 1e-6, precision=prec, method=ls.LS_ID_BLOCKED)
+        assert k == 17 and id_error(B, J, U) <= 1e-6
+        k, J, U = ls.ls_row_id(np.zeros((50, 30), np.complex128), 1e-6, precision=prec, method=ls.LS_ID_BLOCKED)
+        assert k == 0
+        A = random_decaying(40, 70, 2)
+        J0, _ = hbs.row_id(A, 1e-4)
+        k, J, U = ls.ls_row_id(A, 1e-4, precision=prec, method=ls.LS_ID_BLOCKED)
+        assert abs(k - len(J0)) <= 2 and id_error(A, J, U) <= 1.5e-4
+
+
+def test_blocked_id_does_not_modify_input_and_repeats():
+    """The caller's device matrix is left as it was, and two calls give the same pivots."""
+    import torch
+    A = random_decaying(900, 600, 8)
+    At = torch.from_numpy(A).cuda()
+    k1, J1, U1 = ls.ls_row_id(At, 1e-6, method=ls.LS_ID_BLOCKED)
+    k2, J2, U2 = ls.ls_row_id(At, 1e-6, method=ls.LS_ID_BLOCKED)
+    assert np.array_equal(At.cpu().numpy(), A)
+    assert k1 == k2 and np.array_equal(J1, J2) and np.array_equal(U1, U2)
