@@ -601,6 +601,34 @@ __global__ void __launch_bounds__(kTrsmThreads) id_trsm_kernel(const cx<R>* __re
       U[(long long)c * k + a] = solve ? t[a] : mk<R>(a == sc ? R(1) : R(0), R(0));
 }
 
+// Launch of id_trsm_kernel with as many candidates per block (4, 2 or 1) as
+// their right-hand sides (kmax entries each) leave room for in shared memory.
+template <class R>
+int launch_id_trsm(const cx<R>* Rm, const cx<R>* RT, const int* sel, const int* rank, int m, int kmax, cx<R>* U,
+                   cudaStream_t sb) {
+  const size_t diag = sizeof(cx<R>) * (size_t)2 * kTrsmNB * kTrsmNB;
+  auto smem = [&](int cb) { return sizeof(cx<R>) * (size_t)cb * kmax + diag; };
+  const size_t limit = 227 * 1024;
+  const int CB = smem(4) <= limit ? 4 : smem(2) <= limit ? 2 : smem(1) <= limit ? 1 : 0;
+  if (!CB) {
+    set_last_error_text("ID rank too large for the back substitution's shared memory");
+    return LS_EINVAL;
+  }
+  const size_t smt = smem(CB);
+  const void* fn = CB == 4 ? (const void*)id_trsm_kernel<R, 4> : CB == 2 ? (const void*)id_trsm_kernel<R, 2>
+                                                                          : (const void*)id_trsm_kernel<R, 1>;
+  if (smt > 48 * 1024) LS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt));
+  count_launch();
+  const unsigned grid = (unsigned)((m + CB - 1) / CB);
+  if (CB == 4)
+    id_trsm_kernel<R, 4><<<grid, kTrsmThreads, smt, sb>>>(Rm, RT, sel, rank, m, kmax, U);
+  else if (CB == 2)
+    id_trsm_kernel<R, 2><<<grid, kTrsmThreads, smt, sb>>>(Rm, RT, sel, rank, m, kmax, U);
+  else
+    id_trsm_kernel<R, 1><<<grid, kTrsmThreads, smt, sb>>>(Rm, RT, sel, rank, m, kmax, U);
+  return check_launch("ID back substitution");
+}
+
 // Cluster version: CL <= 16 blocks of 1024 threads, at most 32 candidates per
 // block (block r owns candidates [r per, r per + per)), p <= 32 T.  Each warp
 // keeps its candidate's key (0 once the candidate is a pivot) in a per-warp
@@ -1056,15 +1084,7 @@ int run_row_id_blocked(cx<R>* A, int m, int p, double eps, cudaStream_t st, int*
     cudaEventDestroy(e);
     sb = su;
   }
-  if (Uout && k > 0) {
-    constexpr int CB = 4;
-    const size_t smt = sizeof(cx<R>) * ((size_t)CB * kmax + (size_t)2 * kTrsmNB * kTrsmNB);
-    if (smt > 48 * 1024)
-      LS_CUDA_TRY(cudaFuncSetAttribute(id_trsm_kernel<R, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt));
-    count_launch();
-    id_trsm_kernel<R, CB><<<(unsigned)((m + CB - 1) / CB), kTrsmThreads, smt, sb>>>(Rm, RT, sel, rank, m, kmax, Uout);
-    if ((rc = check_launch("blocked ID back substitution"))) return rc;
-  }
+  if (Uout && k > 0 && (rc = launch_id_trsm<R>(Rm, RT, sel, rank, m, kmax, Uout, sb))) return rc;
   if (sb != st) {
     ls::StreamScope scope(sb);
     dfree(tsp);
@@ -1297,10 +1317,6 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
   }
   bool u_on_aux = false;  // U written by the back substitution on su
   if (reg_mode) {
-    constexpr int CB = 4;
-    const size_t smt = sizeof(cx<R>) * ((size_t)CB * kmax + (size_t)2 * kTrsmNB * kTrsmNB);
-    if (smt > 48 * 1024)
-      LS_CUDA_TRY(cudaFuncSetAttribute(id_trsm_kernel<R, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt));
     cudaStream_t sb = st;
     cx<R>* Udst = Ut;
     if (su && Uout) {  // U straight into Uout on the auxiliary stream, after the ID kernel
@@ -1313,8 +1329,7 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
       Udst = Uout;
       u_on_aux = true;
     }
-    count_launch();
-    id_trsm_kernel<R, CB><<<(unsigned)((m + CB - 1) / CB), kTrsmThreads, smt, sb>>>(Rm, RT, sel, rank, m, kmax, Udst);
+    if ((rc = launch_id_trsm<R>(Rm, RT, sel, rank, m, kmax, Udst, sb))) return rc;
   } else if (use_cluster) {
     count_launch();
     LS_CUDA_TRY(cudaLaunchKernelEx(&cfg, cpqr_id_cluster_kernel<R>, (const cx<R>*)A, m, p, kmax, eps, Rm, sel, piv,

@@ -57,10 +57,12 @@ namespace bid {
 
 constexpr int kB = 32;          // pivots per block, at most
 constexpr int kPool = 64;       // pool rows per block
-constexpr int kUR = 16;         // rows per block of update_kernel
+constexpr int kTR = 64;         // rows per block of update_kernel
+constexpr int kTC = 64;         // columns per chunk of update_kernel
 constexpr int kCR = 64;         // rows per block of proj_kernel
 constexpr int kGramMax = 32;    // blocks of gram_kernel, at most
 constexpr int kGramCols = 32;   // columns per stage of gram_kernel
+constexpr int kMaxSplit = 8;    // column slices of proj_kernel, at most
 constexpr double kAlpha2 = 0.25;
 
 struct State {
@@ -74,12 +76,20 @@ struct State {
   double tot;   // ||A_trail||_F^2 at the start of the block
   double outside;   // largest residual norm^2 of a trailing row outside the pool
   int pool[kPool];  // positions of the pool rows, largest norm first
-  int swp[kB];      // position k + i is swapped with swp[i], in the order i = 0, 1, ...
+  int nu;           // positions the block's swaps touch
+  int upos[2 * kB]; // those positions: k .. k + be - 1 first, then the pivots' old positions
+  int usrc[2 * kB]; // after the swaps, position upos[t] holds the row that was at upos[usrc[t]]
 };
 
 template <class R>
 __device__ __forceinline__ cx<R> czero() {
   return mk<R>(R(0), R(0));
+}
+
+// L2 load of a complex value written by another block of the same launch.
+template <class R>
+__device__ __forceinline__ cx<R> __ldcg_cx_any(const cx<R>* p) {
+  return ldcg_cx(p);
 }
 
 // Block-wide sum of one double per thread in a fixed order (blockDim.x = 256).
@@ -101,20 +111,11 @@ __device__ double block_sum256(double v, double* sh) {
 }
 
 // Order of candidates for the pool: larger norm first, lower position on ties.
-__device__ __forceinline__ bool better(double na, int pa, double nb, int pb) {
-  return na > nb || (na == nb && pa < pb);
-}
-
-// The last block of a launch: every block fences its results and takes a
-// ticket; the block that takes ticket gridDim.x - 1 sees all of them.
-__device__ __forceinline__ bool last_block(unsigned* ticket) {
-  __shared__ int s_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (s_last) __threadfence();
-  return s_last != 0;
+// Norms are compared through their bit patterns (non-negative doubles order like
+// the unsigned integers of their bits; integer compares avoid the FP64 pipe);
+// key 0 (a zero norm) is never a candidate.
+__device__ __forceinline__ bool better(unsigned long long ka, int pa, unsigned long long kb, int pb) {
+  return ka > kb || (ka == kb && pa < pb);
 }
 
 // Pool selection over the trailing norms (last block of update_kernel, 256
@@ -123,14 +124,16 @@ __device__ __forceinline__ bool last_block(unsigned* ticket) {
 // the pool, and `outside` is the largest norm left out (sorted entries past
 // kPool and every thread's third).
 __device__ void select_pool(const double* __restrict__ norms, int k, int m, State* S) {
-  __shared__ double sn[512];
+  typedef unsigned long long u64;
+  __shared__ u64 sn[512];
   __shared__ int sp[512];
-  __shared__ double s_third[256];
+  __shared__ u64 s_third[256];
   const int tid = threadIdx.x;
-  double n0 = -1, n1 = -1, n2 = -1;
+  u64 n0 = 0, n1 = 0, n2 = 0;
   int p0 = 0x7fffffff, p1 = 0x7fffffff, p2 = 0x7fffffff;
   for (int q = k + tid; q < m; q += 256) {
-    const double v = __ldcg(norms + q);
+    const u64 v = (u64)__double_as_longlong(__ldcg(norms + q));
+    if (v == 0) continue;
     if (better(v, q, n0, p0)) {
       n2 = n1; p2 = p1; n1 = n0; p1 = p0; n0 = v; p0 = q;
     } else if (better(v, q, n1, p1)) {
@@ -146,25 +149,24 @@ __device__ void select_pool(const double* __restrict__ norms, int k, int m, Stat
   // bitonic sort of 512 entries, best first
   for (int size = 2; size <= 512; size <<= 1)
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int e = tid; e < 256; e += 256) {
-        const int i = 2 * stride * (e / stride) + (e % stride), j = i + stride;
-        const bool desc = ((i / size) & 1) == 0;  // best-first runs in even segments
-        const bool swap_ = desc ? better(sn[j], sp[j], sn[i], sp[i]) : better(sn[i], sp[i], sn[j], sp[j]);
-        if (swap_) {
-          double tn = sn[i]; sn[i] = sn[j]; sn[j] = tn;
-          int tp = sp[i]; sp[i] = sp[j]; sp[j] = tp;
-        }
+      const int e = tid;
+      const int i = 2 * stride * (e / stride) + (e % stride), j = i + stride;
+      const bool desc = ((i / size) & 1) == 0;  // best-first runs in even segments
+      const bool swap_ = desc ? better(sn[j], sp[j], sn[i], sp[i]) : better(sn[i], sp[i], sn[j], sp[j]);
+      if (swap_) {
+        const u64 tn = sn[i]; sn[i] = sn[j]; sn[j] = tn;
+        const int tp = sp[i]; sp[i] = sp[j]; sp[j] = tp;
       }
       __syncthreads();
     }
   if (tid < kPool) S->pool[tid] = sp[tid];
   if (tid == 0) {
     int np = 0;
-    while (np < kPool && sn[np] >= 0) ++np;
-    double out = np < 512 && sn[kPool] > 0 ? sn[kPool] : 0.0;
-    for (int t = 0; t < 256; ++t) out = fmax(out, s_third[t]);
+    while (np < kPool && sn[np] > 0) ++np;
+    u64 out = sn[kPool];
+    for (int t = 0; t < 256; ++t) out = out > s_third[t] ? out : s_third[t];
     S->npool = np;
-    S->outside = out;
+    S->outside = __longlong_as_double((long long)out);
   }
   __syncthreads();
 }
@@ -172,73 +174,120 @@ __device__ void select_pool(const double* __restrict__ norms, int k, int m, Stat
 // A_trail(r, :) -= sum_{i < jb} L(r, k0 + i) Q(i, :) for the trailing rows
 // r >= k0 + jb (nothing to subtract when first), then every such row's norm^2,
 // the trailing total and, in the last block, the stopping test and the next
-// pool.  kUR rows per block, columns strided over the 256 threads.
+// pool.  Block (x, y): row tile x (kTR rows), slice y of the columns (whole
+// 64-column chunks), 4 x 4 entries per thread per chunk; the block's C rows stay
+// in shared memory, each chunk of Q is staged there.  Row norms: every slice
+// writes its partial sums, the last block of a tile to finish adds them in
+// slice order; the last tile to finish takes the total (tiles in order).
 template <class R>
 __global__ void __launch_bounds__(256) update_kernel(cx<R>* __restrict__ A, int m, int p, int kmax,
                                                      const cx<R>* __restrict__ Lm, int ldl,
                                                      const cx<R>* __restrict__ Q, double* __restrict__ norms,
+                                                     double* __restrict__ npart, unsigned* __restrict__ tile_ticket,
                                                      double* __restrict__ part, State* __restrict__ S, double eps2,
                                                      int first) {
-  __shared__ cx<R> Cs[kUR][kB];
-  __shared__ double red[8][kUR];
+  extern __shared__ unsigned char smraw[];
+  auto Cs = reinterpret_cast<cx<R>(*)[kB + 1]>(smraw);                                   // kTR x (kB + 1)
+  auto Qs = reinterpret_cast<cx<R>(*)[kTC + 1]>(smraw + sizeof(cx<R>) * kTR * (kB + 1));  // kB x (kTC + 1)
+  __shared__ double rs[kTR];
   __shared__ double sh[8];
+  __shared__ int s_last;
   if (S->done) return;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int k0 = first ? 0 : S->k;
   const int jb = first ? 0 : S->jb;
-  const int r0 = k0 + jb + blockIdx.x * kUR;
-  const int nr = max(0, min(kUR, m - r0));
-  for (int e = tid; e < kUR * kB; e += 256) {
+  const int tile = blockIdx.x, nsl = gridDim.y, sl = blockIdx.y;
+  const int r0 = k0 + jb + tile * kTR;
+  const int nr = max(0, min(kTR, m - r0));
+  const int nch = (p + kTC - 1) / kTC, per = (nch + nsl - 1) / nsl;
+  const int c_lo = min(p, sl * per * kTC), c_hi = min(p, c_lo + per * kTC);
+  for (int e = tid; e < kTR * kB; e += 256) {
     const int r = e / kB, i = e % kB;
     Cs[r][i] = (r < nr && i < jb) ? Lm[(long long)(r0 + r) * ldl + k0 + i] : czero<R>();
   }
-  __syncthreads();
-  R nrm[kUR];
-#pragma unroll
-  for (int r = 0; r < kUR; ++r) nrm[r] = R(0);
+  R nrm[4] = {R(0), R(0), R(0), R(0)};
   if (nr > 0) {
-    for (int c = tid; c < p; c += 256) {
-      cx<R> a[kUR];
+    for (int c0 = c_lo; c0 < c_hi; c0 += kTC) {
+      __syncthreads();
+      for (int e = tid; e < jb * kTC; e += 256) {
+        const int i = e / kTC, c = e % kTC;
+        Qs[i][c] = c0 + c < c_hi ? Q[(long long)i * p + c0 + c] : czero<R>();
+      }
+      cx<R> a[4][4];
 #pragma unroll
-      for (int r = 0; r < kUR; ++r) a[r] = r < nr ? A[(long long)(r0 + r) * p + c] : czero<R>();
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int r = ty + 16 * u, c = c0 + tx + 16 * v;
+          a[u][v] = (r < nr && c < c_hi) ? A[(long long)(r0 + r) * p + c] : czero<R>();
+        }
+      __syncthreads();
       if (jb > 0) {
         for (int i = 0; i < jb; ++i) {
-          const cx<R> q = Q[(long long)i * p + c];
+          cx<R> cu[4], qv[4];
 #pragma unroll
-          for (int r = 0; r < kUR; ++r) {
-            const cx<R> cc = Cs[r][i];
-            a[r].re -= cc.re * q.re - cc.im * q.im;
-            a[r].im -= cc.re * q.im + cc.im * q.re;
-          }
+          for (int u = 0; u < 4; ++u) cu[u] = Cs[ty + 16 * u][i];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) qv[v] = Qs[i][tx + 16 * v];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              a[u][v].re -= cu[u].re * qv[v].re - cu[u].im * qv[v].im;
+              a[u][v].im -= cu[u].re * qv[v].im + cu[u].im * qv[v].re;
+            }
         }
 #pragma unroll
-        for (int r = 0; r < kUR; ++r)
-          if (r < nr) A[(long long)(r0 + r) * p + c] = a[r];
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int r = ty + 16 * u, c = c0 + tx + 16 * v;
+            if (r < nr && c < c_hi) A[(long long)(r0 + r) * p + c] = a[u][v];
+          }
       }
 #pragma unroll
-      for (int r = 0; r < kUR; ++r) nrm[r] += abs2(a[r]);
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) nrm[u] += abs2(a[u][v]);
     }
   }
+  // row partials: the 16 threads of a row (same ty, one half-warp) in a fixed order
 #pragma unroll
-  for (int r = 0; r < kUR; ++r) {
-    double v = (double)nrm[r];
-    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp][r] = v;
+  for (int u = 0; u < 4; ++u) {
+    double v = (double)nrm[u];
+    for (int o = 8; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (tx == 0) rs[ty + 16 * u] = v;
   }
   __syncthreads();
-  if (tid < kUR) {
-    double v = 0;
-    for (int w = 0; w < 8; ++w) v += red[w][tid];
-    red[0][tid] = v;
-    if (tid < nr) norms[r0 + tid] = v;
+  if (nsl > 1) {
+    if (tid < nr) npart[(size_t)sl * m + r0 + tid] = rs[tid];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(tile_ticket + tile, 1u) == (unsigned)nsl - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (tid < kTR) {
+      double t = 0;
+      if (tid < nr)
+        for (int q = 0; q < nsl; ++q) t += __ldcg(npart + (size_t)q * m + r0 + tid);
+      rs[tid] = t;
+    }
+    if (tid == 0) tile_ticket[tile] = 0;
+    __syncthreads();
   }
-  __syncthreads();
+  if (tid < nr) norms[r0 + tid] = rs[tid];
   if (tid == 0) {
     double t = 0;
-    for (int r = 0; r < nr; ++r) t += red[0][r];
-    part[blockIdx.x] = t;
+    for (int r = 0; r < nr; ++r) t += rs[r];
+    part[tile] = t;
   }
-  if (!last_block(&S->ticket)) return;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(&S->ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
   double v = 0;
   for (int b = tid; b < (int)gridDim.x; b += 256) v += __ldcg(part + b);
   const double tot = block_sum256(v, sh);
@@ -260,94 +309,122 @@ __global__ void __launch_bounds__(256) update_kernel(cx<R>* __restrict__ A, int 
 
 // Partial Gram matrices of the pool rows over column slices:
 // gp[b][i * kPool + j] = sum_{t in slice b} A(pool_i, t) conj(A(pool_j, t)).
-// 256 threads, a 4 x 4 tile of (i, j) per thread.
+// Block (x, y): slice x of the columns, quadrant y of the 64 x 64 matrix (32 x 32
+// entries, 4 per thread).
 template <class R>
 __global__ void __launch_bounds__(256) gram_kernel(const cx<R>* __restrict__ A, int p,
                                                    const State* __restrict__ S, cx<R>* __restrict__ gp) {
-  __shared__ cx<R> T[kPool][kGramCols + 1];
-  __shared__ int pool[kPool];
+  constexpr int H = kPool / 2;
+  __shared__ cx<R> T[2][H][kGramCols + 1];
+  __shared__ int rows[2][H];
   if (S->done) return;
   const int tid = threadIdx.x, np = S->npool;
-  if (tid < kPool) pool[tid] = tid < np ? S->pool[tid] : -1;
-  const int ti = tid >> 4, tj = tid & 15;
-  cx<R> acc[4][4];
+  const int qi = blockIdx.y >> 1, qj = blockIdx.y & 1;  // quadrant: rows qi * H.., columns qj * H..
+  if (tid < 2 * H) {
+    const int side = tid / H, r = tid % H, idx = (side ? qj : qi) * H + r;
+    rows[side][r] = idx < np ? S->pool[idx] : -1;
+  }
+  const int ti = tid >> 4, tj = tid & 15;  // entries (ti + 16 u, tj + 16 v), u, v < 2
+  cx<R> acc[2][2];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < 2; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = czero<R>();
+    for (int v = 0; v < 2; ++v) acc[u][v] = czero<R>();
   const int nst = (p + kGramCols - 1) / kGramCols;  // column stages
   const int per = (nst + gridDim.x - 1) / gridDim.x;
   const int s0 = blockIdx.x * per, s1 = min(nst, s0 + per);
   __syncthreads();
-  for (int s = s0; s < s1; ++s) {
-    const int c0 = s * kGramCols;
-    for (int e = tid; e < kPool * kGramCols; e += 256) {
-      const int r = e / kGramCols, c = e % kGramCols;
-      const int row = pool[r];
-      T[r][c] = (row >= 0 && c0 + c < p) ? A[(long long)row * p + c0 + c] : czero<R>();
+  for (int st = s0; st < s1; ++st) {
+    const int c0 = st * kGramCols;
+    for (int e = tid; e < 2 * H * kGramCols; e += 256) {
+      const int side = e / (H * kGramCols), r = (e / kGramCols) % H, c = e % kGramCols;
+      const int row = rows[side][r];
+      T[side][r][c] = (row >= 0 && c0 + c < p) ? A[(long long)row * p + c0 + c] : czero<R>();
     }
     __syncthreads();
-#pragma unroll 4
+#pragma unroll 8
     for (int c = 0; c < kGramCols; ++c) {
-      cx<R> a[4], b[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = T[4 * ti + u][c];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) b[v] = T[4 * tj + v][c];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) fmac_(acc[u][v], b[v], a[u]);  // a_i conj(a_j)
+      const cx<R> a0 = T[0][ti][c], a1 = T[0][ti + 16][c];
+      const cx<R> b0 = T[1][tj][c], b1 = T[1][tj + 16][c];
+      fmac_(acc[0][0], b0, a0);  // a_i conj(a_j)
+      fmac_(acc[0][1], b1, a0);
+      fmac_(acc[1][0], b0, a1);
+      fmac_(acc[1][1], b1, a1);
     }
     __syncthreads();
   }
   cx<R>* g = gp + (size_t)blockIdx.x * kPool * kPool;
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < 2; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) g[(4 * ti + u) * kPool + 4 * tj + v] = acc[u][v];
+    for (int v = 0; v < 2; ++v) g[(qi * H + ti + 16 * u) * kPool + qj * H + tj + 16 * v] = acc[u][v];
 }
 
-// Greedy pivoted Cholesky of the pool's Gram matrix (one block of 256
+// Greedy pivoted Cholesky of the pool's Gram matrix (one block of 1024
 // threads): the pivot is the pool row of largest residual norm^2 d_i (lowest
 // pool index on ties); the block ends at kB pivots, when d_best < kAlpha2 *
 // outside, when d_best <= drange * d_first (beyond that the Gram matrix's
 // rounding would decide the order), at the rank limit, or at a non-positive d.
-// Writes the accepted pivots' Cholesky rows L_bb (be x be, lower), be, and the
-// swap sequence that brings the pivots to positions [k, k + be); applies it to perm.
+// The partial Gram matrices are summed in a fixed order (four entries per
+// thread, the loads of eight partials in flight) and the factorisation runs in
+// the working precision R: its rounding only perturbs the pivot order among
+// nearly equal candidates and the orthonormality of Q_b, which the explicit
+// trailing update absorbs (FP64 arithmetic here would cost more than the rest
+// of the block on a GPU whose FP64 rate is a small fraction of its FP32 rate).  Writes the accepted
+// pivots' Cholesky rows L_bb (be x be, lower), be, and the swap sequence that
+// brings the pivots to positions [k, k + be); applies it to perm.
 template <class R>
-__global__ void __launch_bounds__(256) pchol_kernel(const cx<R>* __restrict__ gp, int ngp, int kmax,
-                                                    State* __restrict__ S, int* __restrict__ perm,
-                                                    cx<R>* __restrict__ Lbb, double drange) {
+__global__ void __launch_bounds__(1024) pchol_kernel(const cx<R>* __restrict__ gp, int ngp, int kmax,
+                                                     State* __restrict__ S, int* __restrict__ perm,
+                                                     cx<R>* __restrict__ Lbb, double drange) {
   extern __shared__ unsigned char smraw[];
-  cx<double>* G = reinterpret_cast<cx<double>*>(smraw);  // kPool x kPool
-  cx<double>* Lc = G + kPool * kPool;                     // kPool x kB
-  __shared__ double d[kPool];
+  constexpr int LG = kPool + 1, LL = kB + 1;    // padded row strides (no bank conflicts down a column)
+  cx<R>* G = reinterpret_cast<cx<R>*>(smraw);  // kPool x LG
+  cx<R>* Lc = G + kPool * LG;                   // kPool x LL
+  __shared__ R d[kPool];
   __shared__ int chosen[kPool], order[kB];
   __shared__ int s_best, s_stop, s_be;
-  __shared__ double s_dbest, s_d0;
+  __shared__ R s_dbest, s_d0;
   if (S->done) return;
   const int tid = threadIdx.x;
   const int np = S->npool, k = S->k;
   const double outside = S->outside;
-  for (int e = tid; e < kPool * kPool; e += 256) {
-    cx<double> s = mk<double>(0.0, 0.0);
-    for (int b = 0; b < ngp; ++b) s = s + cvt<double>(gp[(size_t)b * kPool * kPool + e]);
-    G[e] = s;
+  {
+    constexpr int E = kPool * kPool / 1024;  // entries per thread
+    cx<R> acc[E];
+#pragma unroll
+    for (int u = 0; u < E; ++u) acc[u] = czero<R>();
+    int b = 0;
+    for (; b + 8 <= ngp; b += 8) {
+      cx<R> v[8][E];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int u = 0; u < E; ++u) v[q][u] = gp[(size_t)(b + q) * kPool * kPool + tid + 1024 * u];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+#pragma unroll
+        for (int u = 0; u < E; ++u) acc[u] = acc[u] + v[q][u];
+    }
+    for (; b < ngp; ++b)
+#pragma unroll
+      for (int u = 0; u < E; ++u) acc[u] = acc[u] + gp[(size_t)b * kPool * kPool + tid + 1024 * u];
+#pragma unroll
+    for (int u = 0; u < E; ++u) {
+      const int e = tid + 1024 * u;
+      G[(e / kPool) * LG + e % kPool] = acc[u];
+    }
   }
-  for (int e = tid; e < kPool * kB; e += 256) Lc[e] = mk<double>(0.0, 0.0);
-  if (tid < kPool) {
-    chosen[tid] = tid < np ? 0 : 1;
-    d[tid] = 0;
-  }
+  for (int e = tid; e < kPool * LL; e += 1024) Lc[e] = czero<R>();
+  if (tid < kPool) chosen[tid] = tid < np ? 0 : 1;
   __syncthreads();
-  if (tid < np) d[tid] = G[tid * kPool + tid].re;
+  if (tid < kPool) d[tid] = tid < np ? G[tid * LG + tid].re : R(0);
   __syncthreads();
   const int jmax = min(kB, min(np, kmax - k));
   int j = 0;
   for (; j < jmax; ++j) {
     if (tid < 32) {  // warp 0: argmax over the pool
-      double bv = -1;
+      R bv = R(-1);
       int bi = 0x7fffffff;
       for (int i = tid; i < kPool; i += 32)
         if (!chosen[i] && (d[i] > bv || (d[i] == bv && i < bi))) {
@@ -355,7 +432,7 @@ __global__ void __launch_bounds__(256) pchol_kernel(const cx<R>* __restrict__ gp
           bi = i;
         }
       for (int o = 16; o; o >>= 1) {
-        const double ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const R ov = __shfl_down_sync(0xffffffffu, bv, o);
         const int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (ov > bv || (ov == bv && oi < bi)) {
           bv = ov;
@@ -364,8 +441,8 @@ __global__ void __launch_bounds__(256) pchol_kernel(const cx<R>* __restrict__ gp
       }
       if (tid == 0) {
         if (j == 0) s_d0 = bv;
-        const bool stop = bi >= kPool || !(bv > 0) || (outside > 0 && bv < kAlpha2 * outside) ||
-                          (j > 0 && bv <= drange * s_d0);
+        const bool stop = bi >= kPool || !(bv > R(0)) || (outside > 0 && (double)bv < kAlpha2 * outside) ||
+                          (j > 0 && (double)bv <= drange * (double)s_d0);
         s_stop = stop ? 1 : 0;
         s_best = bi;
         s_dbest = bv;
@@ -374,19 +451,20 @@ __global__ void __launch_bounds__(256) pchol_kernel(const cx<R>* __restrict__ gp
     __syncthreads();
     if (s_stop) break;
     const int best = s_best;
-    const double sd = sqrt(s_dbest);
+    const R sd = sqrt(s_dbest);
     if (tid < np) {
-      cx<double> v = G[tid * kPool + best];  // <a_i, a_best>
+      cx<R> v = G[tid * LG + best];  // <a_i, a_best>
       for (int jj = 0; jj < j; ++jj) {
-        const cx<double> a = Lc[tid * kB + jj], bconj = conjz(Lc[best * kB + jj]);
-        v = v - a * bconj;
+        const cx<R> a = Lc[tid * LL + jj], bc = Lc[best * LL + jj];
+        v.re -= a.re * bc.re + a.im * bc.im;  // v -= a conj(bc)
+        v.im -= a.im * bc.re - a.re * bc.im;
       }
-      v = scale(v, 1.0 / sd);
-      if (tid == best) v = mk<double>(sd, 0.0);
-      Lc[tid * kB + j] = v;
+      v = scale(v, R(1) / sd);
+      if (tid == best) v = mk<R>(sd, R(0));
+      Lc[tid * LL + j] = v;
     }
     __syncthreads();
-    if (tid < np) d[tid] = chosen[tid] || tid == best ? 0.0 : d[tid] - abs2(Lc[tid * kB + j]);
+    if (tid < np) d[tid] = chosen[tid] || tid == best ? R(0) : d[tid] - abs2(Lc[tid * LL + j]);
     if (tid == 0) {
       chosen[best] = 1;
       order[j] = best;
@@ -396,63 +474,101 @@ __global__ void __launch_bounds__(256) pchol_kernel(const cx<R>* __restrict__ gp
   if (tid == 0) s_be = j;
   __syncthreads();
   const int be = s_be;
-  for (int e = tid; e < kB * kB; e += 256) {
+  for (int e = tid; e < kB * kB; e += 1024) {
     const int i = e / kB, jj = e % kB;
-    cx<double> v = mk<double>(0.0, 0.0);
-    if (i < be && jj <= i) v = Lc[order[i] * kB + jj];
-    Lbb[e] = cvt<R>(v);
+    Lbb[e] = (i < be && jj <= i) ? Lc[order[i] * LL + jj] : czero<R>();
   }
+  // swap sequence in shared memory: position k + i receives the pivot order[i]
+  // (a pivot that sat at k + i', i' < i, was moved to the partner of swap i');
+  // the positions it touches, and where each of their final rows comes from
+  __shared__ int s_swp[kB], s_upos[2 * kB], s_cur[2 * kB], s_ia[kB], s_ix[kB], s_val[2 * kB], s_nu;
+  __shared__ int s_pool[kPool];
+  if (tid < kPool) s_pool[tid] = S->pool[tid];
+  __syncthreads();
   if (tid == 0) {
-    // swap sequence: position k + i receives the pivot order[i]; a pivot that
-    // sat at k + i' (i' < i) was moved to swp[i'] by swap i'
+    int nu = 0;
+    for (int i = 0; i < be; ++i) s_upos[nu++] = k + i;
     for (int i = 0; i < be; ++i) {
-      int x = S->pool[order[i]];
+      int x = s_pool[order[i]];
       for (int i2 = 0; i2 < i; ++i2)
-        if (x == k + i2) x = S->swp[i2];
-      S->swp[i] = x;
-      const int a = k + i;
-      if (x != a) {
-        const int t = perm[a];
-        perm[a] = perm[x];
-        perm[x] = t;
+        if (x == k + i2) x = s_swp[i2];
+      s_swp[i] = x;
+      int ix = -1;
+      for (int t = 0; t < nu; ++t)
+        if (s_upos[t] == x) ix = t;
+      if (ix < 0) {
+        ix = nu;
+        s_upos[nu++] = x;
       }
+      s_ia[i] = i;  // position k + i is upos[i]
+      s_ix[i] = ix;
     }
+    for (int t = 0; t < nu; ++t) s_cur[t] = t;
+    for (int i = 0; i < be; ++i) {
+      const int a = s_ia[i], b = s_ix[i];
+      const int tmp = s_cur[a];
+      s_cur[a] = s_cur[b];
+      s_cur[b] = tmp;
+    }
+    s_nu = nu;
     S->be = be;
+    S->nu = nu;
     if (be == 0) S->done = 1;  // no admissible pivot left (the Gram matrix is numerically zero)
   }
+  __syncthreads();
+  const int nu = s_nu;
+  if (tid < nu) {
+    S->upos[tid] = s_upos[tid];
+    S->usrc[tid] = s_cur[tid];
+    s_val[tid] = perm[s_upos[tid]];
+  }
+  __syncthreads();
+  if (tid < nu) perm[s_upos[tid]] = s_val[s_cur[tid]];
 }
 
-// Swaps of the accepted rows into positions [k, k + be) and Q_b = L_bb^-1 A(J_b)
-// (blocks [0, nqa): one column of A per thread), and the same swaps in the
-// columns [0, k) of L plus the block's diagonal L_bb (blocks [nqa, ...): one
-// column of L per thread).
+// The block's row permutation and Q_b = L_bb^-1 A(J_b): blocks [0, nqa) take
+// 128 columns of A each -- the rows at the touched positions are staged in
+// shared memory and written back permuted (position upos[t] receives the row
+// from upos[usrc[t]]), then one thread per column forward-substitutes the
+// pivot rows (now at k .. k + be - 1).  Blocks [nqa, ...) do the same
+// permutation in columns [0, k) of L, 128 columns each, and the first of them
+// writes the block's diagonal L_bb.
 template <class R>
 __global__ void __launch_bounds__(256) swapq_kernel(cx<R>* __restrict__ A, int p, cx<R>* __restrict__ Lm, int ldl,
                                                     const cx<R>* __restrict__ Lbb, cx<R>* __restrict__ Q,
                                                     cx<R>* __restrict__ Qc, const State* __restrict__ S, int nqa) {
-  __shared__ int sw[kB];
+  constexpr int CW = 128;
+  extern __shared__ unsigned char smraw[];
+  cx<R>* stage = reinterpret_cast<cx<R>*>(smraw);  // 2 kB x CW
+  __shared__ int upos[2 * kB], usrc[2 * kB];
   __shared__ cx<R> Lb[kB][kB + 1];
   if (S->done) return;
-  const int tid = threadIdx.x, k = S->k, be = S->be;
-  if (tid < kB) sw[tid] = tid < be ? S->swp[tid] : 0;
+  const int tid = threadIdx.x, k = S->k, be = S->be, nu = S->nu;
+  if (tid < nu) {
+    upos[tid] = S->upos[tid];
+    usrc[tid] = S->usrc[tid];
+  }
   for (int e = tid; e < kB * kB; e += 256) Lb[e / kB][e % kB] = Lbb[e];
   __syncthreads();
   if ((int)blockIdx.x < nqa) {
-    const int c = blockIdx.x * 256 + tid;
-    if (c >= p) return;
-    for (int i = 0; i < be; ++i) {
-      const int a = k + i, x = sw[i];
-      if (x != a) {
-        const cx<R> t = A[(long long)a * p + c];
-        A[(long long)a * p + c] = A[(long long)x * p + c];
-        A[(long long)x * p + c] = t;
-      }
+    const int c0 = blockIdx.x * CW;
+    for (int e = tid; e < nu * CW; e += 256) {
+      const int t = e / CW, c = e % CW;
+      if (c0 + c < p) stage[t * CW + c] = A[(long long)upos[t] * p + c0 + c];
     }
+    __syncthreads();
+    for (int e = tid; e < nu * CW; e += 256) {
+      const int t = e / CW, c = e % CW;
+      if (c0 + c < p) A[(long long)upos[t] * p + c0 + c] = stage[usrc[t] * CW + c];
+    }
+    if (tid >= CW) return;
+    const int c = c0 + tid;
+    if (c >= p) return;
     cx<R> q[kB];
 #pragma unroll
     for (int i = 0; i < kB; ++i) {
       if (i < be) {
-        cx<R> x = A[(long long)(k + i) * p + c];
+        cx<R> x = stage[usrc[i] * CW + tid];  // the row now at position k + i (upos[i] = k + i)
 #pragma unroll
         for (int jj = 0; jj < i; ++jj) {
           const cx<R> l = Lb[i][jj];
@@ -467,42 +583,51 @@ __global__ void __launch_bounds__(256) swapq_kernel(cx<R>* __restrict__ A, int p
       }
     }
   } else {
-    const int c = (blockIdx.x - nqa) * 256 + tid;
-    if (c < k) {
-      for (int i = 0; i < be; ++i) {
-        const int a = k + i, x = sw[i];
-        if (x != a) {
-          const cx<R> t = Lm[(long long)a * ldl + c];
-          Lm[(long long)a * ldl + c] = Lm[(long long)x * ldl + c];
-          Lm[(long long)x * ldl + c] = t;
-        }
-      }
-    } else if (c < k + be) {
-      const int jj = c - k;
-      for (int i = 0; i < be; ++i) Lm[(long long)(k + i) * ldl + c] = jj <= i ? Lb[i][jj] : czero<R>();
+    const int c0 = (blockIdx.x - nqa) * CW;
+    for (int e = tid; e < nu * CW; e += 256) {
+      const int t = e / CW, c = e % CW;
+      if (c0 + c < k) stage[t * CW + c] = Lm[(long long)upos[t] * ldl + c0 + c];
     }
+    __syncthreads();
+    for (int e = tid; e < nu * CW; e += 256) {
+      const int t = e / CW, c = e % CW;
+      if (c0 + c < k) Lm[(long long)upos[t] * ldl + c0 + c] = stage[usrc[t] * CW + c];
+    }
+    if (blockIdx.x == nqa)  // the block's diagonal L_bb in columns [k, k + be)
+      for (int e = tid; e < be * be; e += 256) {
+        const int i = e / be, jj = e % be;
+        Lm[(long long)(k + i) * ldl + k + jj] = jj <= i ? Lb[i][jj] : czero<R>();
+      }
   }
 }
 
 // C = A_trail(rows, :) Q_b^H for the trailing rows after the block's pivots
-// (positions [k + be, m)), written to L(rows, k .. k + be).  kCR x kB outputs
-// per block, 8 per thread, K (= p) staged 16 columns at a time.  Each block
-// also writes the column sums of |C|^2; the last block adds the pivot rows'
-// part (the columns of L_bb) and finds the first j at which the residual
-// ||A_trail||^2 - sum_{i <= j} ||C(:, i)||^2 is within the tolerance.
+// (positions [k + be, m)), written to L(rows, k .. k + be).  Block (x, y):
+// row tile x (kCR rows), slice y of the p columns (split K; gridDim.y slices,
+// multiples of 16 columns), kCR x kB outputs per block, 8 per thread.  With
+// more than one slice the partial products go to Cp and the last block of a
+// tile to finish adds them in slice order; the tile's finishing block writes
+// L and the column sums of |C|^2 of its rows.  The last tile to finish adds
+// the pivot rows' part (the columns of L_bb) and finds the first j at which the
+// residual ||A_trail||^2 - sum_{i <= j} ||C(:, i)||^2 is within the tolerance.
 template <class R>
 __global__ void __launch_bounds__(256) proj_kernel(const cx<R>* __restrict__ A, int m, int p,
                                                    cx<R>* __restrict__ Lm, int ldl, const cx<R>* __restrict__ Qc,
-                                                   const cx<R>* __restrict__ Lbb, double* __restrict__ cpart,
+                                                   const cx<R>* __restrict__ Lbb, cx<R>* __restrict__ Cp,
+                                                   unsigned* __restrict__ tile_ticket, double* __restrict__ cpart,
                                                    State* __restrict__ S) {
   constexpr int KC = 16;
   __shared__ cx<R> As[KC][kCR + 1];
   __shared__ cx<R> Bs[KC][kB + 1];
   __shared__ double cs[32][kB + 1];
+  __shared__ int s_last;
   if (S->done) return;
   const int tid = threadIdx.x, k = S->k, be = S->be;
-  const int r0 = k + be + blockIdx.x * kCR;
+  const int tile = blockIdx.x, nsl = gridDim.y, sl = blockIdx.y;
+  const int r0 = k + be + tile * kCR;
   const int nr = max(0, min(kCR, m - r0));
+  const int kc = ((p + nsl - 1) / nsl + KC - 1) / KC * KC;
+  const int t_lo = min(p, sl * kc), t_hi = min(p, t_lo + kc);
   const int tx = tid & 7, ty = tid >> 3;  // rows ty, ty + 32; columns tx + 8 v
   cx<R> acc[2][4];
 #pragma unroll
@@ -510,16 +635,16 @@ __global__ void __launch_bounds__(256) proj_kernel(const cx<R>* __restrict__ A, 
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[u][v] = czero<R>();
   if (nr > 0) {
-    for (int t0 = 0; t0 < p; t0 += KC) {
+    for (int t0 = t_lo; t0 < t_hi; t0 += KC) {
 #pragma unroll
       for (int r = 0; r < (KC * kCR) / 256; ++r) {
         const int e = tid + 256 * r, kk = e % KC, i = e / KC;
-        As[kk][i] = (i < nr && t0 + kk < p) ? A[(long long)(r0 + i) * p + t0 + kk] : czero<R>();
+        As[kk][i] = (i < nr && t0 + kk < t_hi) ? A[(long long)(r0 + i) * p + t0 + kk] : czero<R>();
       }
 #pragma unroll
       for (int r = 0; r < (KC * kB) / 256; ++r) {
         const int e = tid + 256 * r, kk = e % KC, j = e / KC;
-        Bs[kk][j] = (j < be && t0 + kk < p) ? Qc[(long long)j * p + t0 + kk] : czero<R>();
+        Bs[kk][j] = (j < be && t0 + kk < t_hi) ? Qc[(long long)j * p + t0 + kk] : czero<R>();
       }
       __syncthreads();
 #pragma unroll
@@ -534,6 +659,30 @@ __global__ void __launch_bounds__(256) proj_kernel(const cx<R>* __restrict__ A, 
       }
       __syncthreads();
     }
+  }
+  if (nsl > 1) {
+    // partial products of this slice; the tile's last block adds them in slice order
+    cx<R>* cp = Cp + ((size_t)sl * gridDim.x + tile) * kCR * kB;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) cp[(ty + 32 * u) * kB + tx + 8 * v] = acc[u][v];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(tile_ticket + tile, 1u) == (unsigned)nsl - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        cx<R> a = czero<R>();
+        for (int q = 0; q < nsl; ++q)
+          a = a + __ldcg_cx_any(Cp + ((size_t)q * gridDim.x + tile) * kCR * kB + (ty + 32 * u) * kB + tx + 8 * v);
+        acc[u][v] = a;
+      }
+    if (tid == 0) tile_ticket[tile] = 0;
   }
   double csum[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -554,9 +703,15 @@ __global__ void __launch_bounds__(256) proj_kernel(const cx<R>* __restrict__ A, 
   if (tid < kB) {
     double t = 0;
     for (int y = 0; y < 32; ++y) t += cs[y][tid];
-    cpart[(size_t)blockIdx.x * kB + tid] = t;
+    cpart[(size_t)tile * kB + tid] = t;
   }
-  if (!last_block(&S->ticket)) return;
+  // the last tile: the stopping test
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(&S->ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
   if (tid < kB) {
     double t = 0;
     for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(cpart + (size_t)b * kB + tid);
@@ -636,12 +791,15 @@ template <class R>
 int blocked_row_id(cx<R>* A, int m, int p, double eps, cudaStream_t st, cx<R>* Rm, cx<R>* RT, int* sel, int* rank,
                    int* piv, int* k_out, std::vector<int>* hp) {
   using namespace bid;
+  int dev = 0, nsm = 148;
+  LS_CUDA_TRY(cudaGetDevice(&dev));
+  LS_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const int kmax = std::min(m, p);
   const int ldl = std::max(kmax, 1);
-  const int nU = (m + kUR - 1) / kUR, nC = (m + kCR - 1) / kCR;
+  const int nU = (m + kTR - 1) / kTR, nC = (m + kCR - 1) / kCR;
   const int nst = (p + kGramCols - 1) / kGramCols;
   const int ngp = std::max(1, std::min(kGramMax, nst));
-  const int nqa = (p + 255) / 256, nql = (kmax + 255) / 256;
+  const int nqa = (p + 127) / 128, nql = (kmax + 127) / 128;
   size_t off = 0;
   auto carve = [&](size_t bytes) {
     size_t o = off;
@@ -652,7 +810,9 @@ int blocked_row_id(cx<R>* A, int m, int p, double eps, cudaStream_t st, cx<R>* R
                oQc = carve(sizeof(cx<R>) * (size_t)kB * p), oLbb = carve(sizeof(cx<R>) * kB * kB),
                oN = carve(sizeof(double) * m), oPerm = carve(sizeof(int) * m), oPos = carve(sizeof(int) * m),
                oS = carve(sizeof(State)), oUp = carve(sizeof(double) * nU), oCp = carve(sizeof(double) * nC * kB),
-               oG = carve(sizeof(cx<R>) * (size_t)ngp * kPool * kPool);
+               oG = carve(sizeof(cx<R>) * (size_t)ngp * kPool * kPool),
+               oCs = carve(sizeof(cx<R>) * (size_t)kMaxSplit * nC * kCR * kB), oTk = carve(sizeof(unsigned) * nC),
+               oNp = carve(sizeof(double) * (size_t)kMaxSplit * m), oTu = carve(sizeof(unsigned) * nU);
   char* w = nullptr;
   int rc = dalloc((void**)&w, off);
   if (rc) return rc;
@@ -667,7 +827,27 @@ int blocked_row_id(cx<R>* A, int m, int p, double eps, cudaStream_t st, cx<R>* R
   double* upart = reinterpret_cast<double*>(w + oUp);
   double* cpart = reinterpret_cast<double*>(w + oCp);
   cx<R>* gp = reinterpret_cast<cx<R>*>(w + oG);
-  const size_t chol_smem = sizeof(cx<double>) * (size_t)kPool * (kPool + kB);
+  cx<R>* Cs = reinterpret_cast<cx<R>*>(w + oCs);
+  unsigned* tickets = reinterpret_cast<unsigned*>(w + oTk);
+  double* npart = reinterpret_cast<double*>(w + oNp);
+  unsigned* uticket = reinterpret_cast<unsigned*>(w + oTu);
+  // column slices of the update: about two blocks per SM, at least four 64-column chunks each
+  const size_t upd_smem = sizeof(cx<R>) * ((size_t)kTR * (kB + 1) + (size_t)kB * (kTC + 1));
+  if (cudaFuncSetAttribute(update_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem) !=
+      cudaSuccess) {
+    dfree(w);
+    LS_CUDA_TRY(cudaGetLastError());
+  }
+  const size_t swap_smem = sizeof(cx<R>) * 2 * kB * 128;
+  if (cudaFuncSetAttribute(swapq_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)swap_smem) !=
+      cudaSuccess) {
+    dfree(w);
+    LS_CUDA_TRY(cudaGetLastError());
+  }
+  auto usplit = [&](int tiles) {
+    return std::max(1, std::min({kMaxSplit, (2 * nsm + tiles - 1) / tiles, (p + 4 * kTC - 1) / (4 * kTC)}));
+  };
+  const size_t chol_smem = sizeof(cx<R>) * (size_t)kPool * (kPool + 1 + kB + 1);
   if (cudaFuncSetAttribute(pchol_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_smem) !=
       cudaSuccess) {
     dfree(w);
@@ -678,11 +858,15 @@ int blocked_row_id(cx<R>* A, int m, int p, double eps, cudaStream_t st, cx<R>* R
     dfree(w);
     return r;
   };
-  if (cudaMemsetAsync(S, 0, sizeof(State), st) != cudaSuccess) return fail(check_launch("blocked ID state"));
+  if (cudaMemsetAsync(S, 0, sizeof(State), st) != cudaSuccess ||
+      cudaMemsetAsync(tickets, 0, sizeof(unsigned) * nC, st) != cudaSuccess ||
+      cudaMemsetAsync(uticket, 0, sizeof(unsigned) * nU, st) != cudaSuccess)
+    return fail(check_launch("blocked ID state"));
   count_launch();
   iota_kernel<<<(m + 255) / 256, 256, 0, st>>>(perm, m);
   count_launch();
-  update_kernel<R><<<nU, 256, 0, st>>>(A, m, p, kmax, Lm, ldl, Q, norms, upart, S, eps * eps, 1);
+  update_kernel<R><<<dim3(nU, usplit(nU)), 256, upd_smem, st>>>(A, m, p, kmax, Lm, ldl, Q, norms, npart, uticket, upart, S,
+                                                         eps * eps, 1);
   if ((rc = check_launch("blocked ID norms"))) return fail(rc);
   // host loop: D blocks in flight; the state (k, done) of block n - D is read
   // back (pinned copy recorded behind it) before block n is queued
@@ -705,12 +889,20 @@ int blocked_row_id(cx<R>* A, int m, int p, double eps, cudaStream_t st, cx<R>* R
     if (nblk > kmax + D) break;  // every queued block accepts a pivot or ends the factorisation
     const int rows = m - k_lb;
     count_launch(5);
-    gram_kernel<R><<<ngp, 256, 0, st>>>(A, p, S, gp);
-    pchol_kernel<R><<<1, 256, chol_smem, st>>>(gp, ngp, kmax, S, perm, Lbb, drange);
-    swapq_kernel<R><<<nqa + nql, 256, 0, st>>>(A, p, Lm, ldl, Lbb, Q, Qc, S, nqa);
-    proj_kernel<R><<<std::max(1, (rows + kCR - 1) / kCR), 256, 0, st>>>(A, m, p, Lm, ldl, Qc, Lbb, cpart, S);
-    update_kernel<R><<<std::max(1, (rows + kUR - 1) / kUR), 256, 0, st>>>(A, m, p, kmax, Lm, ldl, Q, norms, upart, S,
-                                                                         0.0, 0);
+    gram_kernel<R><<<dim3(ngp, 4), 256, 0, st>>>(A, p, S, gp);
+    pchol_kernel<R><<<1, 1024, chol_smem, st>>>(gp, ngp, kmax, S, perm, Lbb, drange);
+    swapq_kernel<R><<<nqa + nql, 256, swap_smem, st>>>(A, p, Lm, ldl, Lbb, Q, Qc, S, nqa);
+    {
+      // split K so that the projection fills about two blocks per SM (slices of at least 512 columns)
+      const int tiles = std::max(1, (rows + kCR - 1) / kCR);
+      const int nsl = std::max(1, std::min({kMaxSplit, (2 * nsm + tiles - 1) / tiles, (p + 511) / 512}));
+      proj_kernel<R><<<dim3(tiles, nsl), 256, 0, st>>>(A, m, p, Lm, ldl, Qc, Lbb, Cs, tickets, cpart, S);
+    }
+    {
+      const int tiles = std::max(1, (rows + kTR - 1) / kTR);
+      update_kernel<R><<<dim3(tiles, usplit(tiles)), 256, upd_smem, st>>>(A, m, p, kmax, Lm, ldl, Q, norms, npart, uticket,
+                                                                   upart, S, 0.0, 0);
+    }
     if ((rc = check_launch("blocked ID block"))) break;
     const int s = nblk % (D + 1);
     if (cudaMemcpyAsync(pin + 4 * s, &S->k, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
