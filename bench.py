@@ -1,18 +1,25 @@
-"""Benchmark: HBS build + preconditioned GMRES solve to 1e-10, in Mdof/s.
+"""Benchmark: HBS build + preconditioned GMRES solve to 1e-10, in Mdof/s, mixed vs FP64.
 
-One step = ls_build (kernel spectrum, per-level compression, Algorithm 1) +
-ls_solve (GMRES on the 10th-order FFT operator, right-preconditioned by the
-HBS inverse, to relative residual 1e-10) + ls_free, on the workload
-  precond_n256: 256 x 256 grid (N = 65,536) on the unit square, kappa = 60,
-  b = 20 seeded Gaussians (seed 0) with a smooth cutoff, HBS eps = 1e-4 with
-  4th-order corrections, matvec with 10th-order corrections, u_inc = e^{i kappa x1}.
-value = N / (time per step) in Mdof/s for the mixed path (FP32 HBS, FP64 FFT
-matvec and GMRES); the FP64 path is reported beside it.  Inputs (b, f) are
-resident in device memory before the timed region; L2 is flushed (a 512 MB
-write) between timed steps, outside the timed events.
+One step = ls_build (corrected-quadrature weights, kernel spectrum, per-level
+compression, Algorithm 1) + ls_solve (GMRES on the 10th-order FFT operator,
+right-preconditioned by the HBS inverse, to relative residual 1e-10) + ls_free.
 
---impl reference runs the CPU oracle (HBS + GMRES in numpy/scipy) on the same
-workload on the host cores.
+Headline workload precond_n2048: 2048 x 2048 grid (N = 4,194,304) on the unit
+square, kappa = 400 pi (200 wavelengths across, 10.24 points per wavelength),
+b = 20 seeded Gaussians (seed 0) with a smooth cutoff, HBS eps = 1e-4 with
+4th-order corrections, matvec with 10th-order corrections, u_inc = e^{i kappa x1}.
+value = N / (device time per step) in Mdof/s for the mixed path (FP32 HBS with
+tf32x3 tensor-core merge GEMMs, FP64 FFT matvec and GMRES), timed with CUDA
+events with no per-kernel profiling; the plain FP64 path is measured on the same
+workload beside it (`fp64`).  A separate profiled pass gives the per-phase and
+end-to-end rooflines.  Inputs (b, f) are resident in device memory before the
+timed region; L2 is flushed (a 512 MB write) between timed steps, outside the
+timed events (the factors, ~30 GB, are far larger than L2 anyway).
+Secondary legs: precond_n256 (256^2, kappa 60), direct_n32 (HBS direct solve at
+eps 1e-10), differentiation_n512 (misfit gradient by the adjoint method).
+
+--impl reference runs the CPU oracle (HBS + GMRES in numpy/scipy) on bounded
+samples of the workload on the host cores (see cpu_sample_step).
 Multi-GPU: one process per GPU, each solving its own copy (replicas; the
 path has no data exchange), value = all ranks' dofs / max-over-ranks time.
 """
@@ -30,13 +37,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "HBS build+GMRES solve to 1e-10 (Mdof/s), mixed vs FP64 on GB300, % roofline"
-WORKLOAD = "precond_n256"
-WORKLOAD_TEXT = ("256x256 grid (N=65,536), kappa=60, b = 20 seeded Gaussians (seed 0) x smooth cutoff, "
-                 "HBS eps=1e-4 order-4 corrections, FFT matvec order 10, plane wave theta=0, GMRES to 1e-10")
-# Roofline denominators.  FP64 ALU: 1.25 TFLOP/s dense FP64 of a GB300 (nominal).
-# FP32 SIMT: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz = 80.5 TFLOP/s (unit
-# counts and maximum clock).  TF32 tensor: half the bf16 dense rate.
-FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fp64_tflops": 1.25, "fp32_tflops": 80.5}
+WORKLOAD = "precond_n2048"
+WORKLOAD_TEXT = ("2048x2048 grid (N=4,194,304), kappa=400 pi (200 wavelengths, 10.24 points per wavelength), "
+                 "b = 20 seeded Gaussians (seed 0) x smooth cutoff, HBS eps=1e-4 order-4 corrections, FFT matvec "
+                 "order 10, plane wave theta=0, GMRES to 1e-10")
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 
 
 def max_over_ranks(values, world, device=None):
@@ -55,18 +60,17 @@ def job_rate(world, units_per_rank, seconds):
     return world * units_per_rank / seconds / 1e6
 
 
-def peaks():
+def file_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         try:
             d = json.load(open(p))
-            return {"hbm_gbs": float(d.get("hbm_gbs", FALLBACK["hbm_gbs"])),
-                    "bf16_tflops": float(d.get("bf16_tflops", FALLBACK["bf16_tflops"])),
-                    "fp64_tflops": FALLBACK["fp64_tflops"], "fp32_tflops": FALLBACK["fp32_tflops"],
-                    "source": "measured"}
+            return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                    "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                    "source": "of measured (MEASURED_PEAKS.json)"}
         except Exception:
             pass
-    return dict(FALLBACK, source="fallback")
+    return dict(FALLBACK, bf16_tflops_sustained=1700.0, source="of fallback")
 
 
 class ClockSampler:
@@ -124,51 +128,61 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def workload_inputs():
+def workload(name):
     from paper_2007_12718_gb300 import inputs
-    n, kappa = 256, 60.0
-    return n, kappa, inputs.gaussian_family(n, 0)
+    w = inputs.WORKLOADS[name]
+    return w["n"], w["kappa"], w["b"](w["n"]), w
 
 
 # ----------------------------------------------------------------- reference
-def oracle_step(n, kappa, b):
+CPU_SAMPLE = "precond_n256_10ppw"
+CPU_SAMPLE_TEXT = ("one full HBS build + preconditioned GMRES solve by the numpy/scipy oracle on the 256x256 member "
+                   "of the same workload family at the same kappa h (kappa = 50 pi, 10.24 points per wavelength, "
+                   "seed-0 potential, eps 1e-4); Mdof/s = 256^2 / its time.  The oracle's cost grows like N^1.5, so "
+                   "this sample overstates its rate at 2048^2")
+
+
+def cpu_sample_step():
+    """The oracle's complete method (Algorithms 1-2 with scipy CPQR, FFT matvec,
+    GMRES) on the bounded sample; returns (seconds, iterations)."""
     from oracle import gmres, hbs, nystrom
+    n, kappa, b, w = workload(CPU_SAMPLE)
     h = 1.0 / n
-    comp = hbs.Compression(kappa, h, hbs.Tree(n, n, 8), 4, 1e-4, 2)
+    t0 = time.perf_counter()
+    comp = hbs.Compression(kappa, h, hbs.Tree(n, n, w["leaf"]), w["order_precond"], w["eps"], 2)
     inv = hbs.Inverse(comp, b)
-    spec = nystrom.conv_kernel_spectrum(kappa, h, n, n, 10)
+    spec = nystrom.conv_kernel_spectrum(kappa, h, n, n, w["order_matvec"])
     f = nystrom.rhs(kappa, b, n, n, h)
     s, k, hist = gmres.gmres(lambda v: nystrom.matvec_fft(spec, kappa, b, v), f, apply_M=inv.apply, tol=1e-10)
-    return k
+    return time.perf_counter() - t0, k
 
 
-def cpu_baseline(n, kappa, b, reps=1):
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        oracle_step(n, kappa, b)
-    dt = (time.perf_counter() - t0) / reps
+def cpu_baseline():
+    dt, k = cpu_sample_step()
+    n = workload(CPU_SAMPLE)[0]
     return {"value": n * n / dt / 1e6, "unit": "Mdof/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{reps} full build+solve of the same workload with the numpy/scipy oracle "
-                      f"(BLAS/FFT threads: all {os.cpu_count()} cores), {dt:.2f} s each"}
+            "sample": CPU_SAMPLE_TEXT + f"; {dt:.2f} s, {k} GMRES iterations, BLAS/FFT threads: all "
+                                        f"{os.cpu_count()} cores"}
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
-    n, kappa, b = workload_inputs()
+    n = workload(CPU_SAMPLE)[0]
     for _ in range(args.warmup):
-        oracle_step(n, kappa, b)
-    t0 = time.perf_counter()
+        cpu_sample_step()
+    t = 0.0
     for _ in range(args.steps):
-        oracle_step(n, kappa, b)
-    dt = (time.perf_counter() - t0) / args.steps
+        dt, k = cpu_sample_step()
+        t += dt
+    dt = t / args.steps
     v = n * n / dt / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Mdof/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "description": WORKLOAD_TEXT},
+            "config": {"workload": WORKLOAD, "description": WORKLOAD_TEXT, "sample": CPU_SAMPLE_TEXT},
             "cpu_baseline": {"value": v, "unit": "Mdof/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{args.steps} full build+solve steps on the host cores"},
+                             "sample": CPU_SAMPLE_TEXT + f"; {args.steps} timed samples after {args.warmup}"},
             "e2e": {"value": v, "unit": "Mdof/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -229,38 +243,37 @@ def adjoint_leg(ls, torch, dev, precision):
 
 
 # ----------------------------------------------------------------------- ours
-def run_ours(args, rank, world):
-    import torch
+class Leg:
+    """One workload on the device: inputs resident, steps of build + solve + free."""
 
-    import paper_2007_12718_gb300 as ls
+    def __init__(self, ls, torch, dev, name, precision, **build_kw):
+        self.ls, self.torch, self.dev = ls, torch, dev
+        self.n, self.kappa, b, self.w = workload(name)
+        self.N = self.n * self.n
+        self.h = 1.0 / self.n
+        self.precision = precision
+        self.kw = dict(order_precond=self.w["order_precond"], order_matvec=self.w["order_matvec"],
+                       leaf_side=self.w["leaf"], **build_kw)
+        self.b_np = b
+        self.b = torch.from_numpy(b).to(dev)
+        self.f = None
+        self.sig = torch.zeros(self.n, self.n, dtype=torch.complex128, device=dev)
 
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
-    n, kappa, b = workload_inputs()
-    N = n * n
-    h = 1.0 / n
-    stream = torch.cuda.current_stream()
-    b_dev = torch.from_numpy(b).to(dev)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    # f = -kappa^2 b u_inc computed once on the device (input preparation, untimed)
-    H0 = ls.ls_build(n, h, kappa, b_dev, 1e-4, precision=ls.LS_FP32)
-    f_dev = torch.zeros(n, n, dtype=torch.complex128, device=dev)
-    ls.ls_rhs_plane_wave(H0, [0.0], f_dev)
-    ls.ls_free(H0)
-    sig = torch.zeros(n, n, dtype=torch.complex128, device=dev)
-
-    PREC = {"fp32": ls.LS_FP32, "tf32": ls.LS_TF32, "tf32x3": ls.LS_TF32X3}[args.precision]
-
-    def step(precision):
-        H = ls.ls_build(n, h, kappa, b_dev, 1e-4, precision=precision, top_uncompressed=args.top_uncompressed)
-        info = ls.ls_solve(H, f_dev, sig)[0]
+    def step(self, precision=None):
+        ls = self.ls
+        H = ls.ls_build(self.n, self.h, self.kappa, self.b, self.w["eps"],
+                        precision=self.precision if precision is None else precision, **self.kw)
+        if self.f is None:  # f = -kappa^2 b u_inc on the device, once (input preparation, untimed warm-up)
+            self.f = self.torch.zeros(self.n, self.n, dtype=self.torch.complex128, device=self.dev)
+            ls.ls_rhs_plane_wave(H, [0.0], self.f)
+        info = ls.ls_solve(H, self.f, self.sig)[0]
+        binfo = H.info()
         ls.ls_free(H)
-        return info
+        return info, binfo
 
-    def timed(precision, steps, profile=False):
-        total = 0.0
-        info = None
+    def timed(self, steps, flush, stream, precision=None, profile=False):
+        ls, torch = self.ls, self.torch
+        total, info, binfo = 0.0, None, None
         if profile:
             ls.ls_profile_reset()
             ls.ls_profile_enable(True)
@@ -271,7 +284,7 @@ def run_ours(args, rank, world):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            info = step(precision)
+            info, binfo = self.step(precision)
             e1.record(stream)
             torch.cuda.synchronize()
             total += e0.elapsed_time(e1) / 1e3
@@ -280,96 +293,180 @@ def run_ours(args, rank, world):
         if profile:
             prof = ls.ls_profile_get()
             ls.ls_profile_enable(False)
-        return total, info, launches, prof
+        return total, info, binfo, launches, prof
 
+    def e2e(self, steps, flush):
+        """Through the C ABI with host buffers: b and f from pinned host memory,
+        sigma back to pinned host memory, copies inside the timed region."""
+        ls, torch = self.ls, self.torch
+        b_host = torch.from_numpy(self.b_np).pin_memory()
+        f_host = self.f.cpu().pin_memory()
+        s_host = torch.zeros(self.n, self.n, dtype=torch.complex128).pin_memory()
+        t = 0.0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            H = ls.ls_build(self.n, self.h, self.kappa, b_host, self.w["eps"], precision=self.precision, **self.kw)
+            ls.ls_solve(H, f_host, s_host)
+            ls.ls_free(H)
+            torch.cuda.synchronize()
+            t += time.perf_counter() - t0
+        return t, {"h2d_bytes_per_step": self.N * 8 + self.N * 16, "d2h_bytes_per_step": self.N * 16}
+
+
+# phases of the method (Sec. 8(d) of the build's survey) and the kernel families of each
+PHASES = {
+    "compress": ["cpqr_id"],
+    "merges": ["leaf_build", "merge_gemm", "merge_inverse"],
+    "apply": ["hbs_apply"],
+    "matvec": ["matvec_rows_fwd", "matvec_cols", "matvec_rows_inv", "spectrum_setup"],
+    "gmres": ["gmres_orth"],
+}
+
+
+def family_peak(name, pk, tensor):
+    """(bound, peak, unit, source) of a kernel family's roofline."""
+    if name.startswith("matvec") or name == "spectrum_setup":
+        return "alu", pk["fp64_tflops"], "TFLOP/s (FP64)", "of measured (ls_measure_peak FP64 FMA loop)"
+    if name in ("hbs_apply", "gmres_orth"):
+        return "hbm", pk["hbm_gbs"], "GB/s", pk["source"]
+    if name == "merge_gemm" and tensor:
+        return ("tensor", pk["bf16_tflops"] / 2, "TFLOP/s (TF32 dense)",
+                pk["source"] + " bf16 x 1/2 (nominal tf32:bf16 ratio)")
+    return "alu", pk["fp32_tflops"], "TFLOP/s (FP32)", "of measured (ls_measure_peak packed FP32 FMA loop)"
+
+
+def rooflines(prof, pk, tensor, t_total, steps):
+    fams = {}
+    for k, v in prof.items():
+        if v["launches"] <= 0 or v["total_ms"] <= 0:
+            continue
+        bound, peak, unit, src = family_peak(k, pk, tensor)
+        work = v["bytes"] if unit == "GB/s" else v["flops"]
+        scale = 1e9 if unit == "GB/s" else 1e12
+        achieved = work / (v["total_ms"] * 1e-3) / scale
+        fams[k] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                   "peak_source": src, "ms_per_step": v["total_ms"] / steps, "launches": v["launches"],
+                   "work_per_step": work / steps, "min_s_per_step": work / steps / (peak * scale)}
+    phases = {}
+    ideal = 0.0
+    for ph, names in PHASES.items():
+        sel = [fams[n] for n in names if n in fams]
+        if not sel:
+            continue
+        ms = sum(f["ms_per_step"] for f in sel)
+        mins = sum(f["min_s_per_step"] for f in sel)
+        ideal += mins
+        phases[ph] = {"ms_per_step": ms, "min_ms_at_peak": mins * 1e3, "frac": mins / (ms * 1e-3)}
+    e2e = {"t_step_s": t_total, "min_s_at_peaks": ideal, "frac": ideal / t_total,
+           "note": "sum over phases of (algorithmic work / peak), over the measured step time"}
+    return fams, phases, e2e
+
+
+def measured_peaks(ls):
+    pk = file_peaks()
+    pk["fp64_tflops"] = ls.ls_measure_peak(0)
+    pk["fp32_scalar_tflops"] = ls.ls_measure_peak(1)
+    pk["fp32_tflops"] = max(pk["fp32_scalar_tflops"], ls.ls_measure_peak(2))
+    return pk
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_2007_12718_gb300 as ls
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    PREC = {"fp32": ls.LS_FP32, "tf32": ls.LS_TF32, "tf32x3": ls.LS_TF32X3}[args.precision]
+    tensor = args.precision in ("tf32", "tf32x3")
+    pk = measured_peaks(ls)
+
+    main = Leg(ls, torch, dev, args.workload, PREC)
     for _ in range(args.warmup):
-        step(PREC)
-        if not args.mixed_only:
-            step(ls.LS_FP64)
+        main.step()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev.index) as clk:
-        t_mixed, info_mixed, launches, prof = timed(PREC, args.steps, profile=True)
+        t_mixed, info_mixed, binfo, launches, _ = main.timed(args.steps, flush, stream)
     if world > 1:
         torch.distributed.barrier()
-    steps64 = max(1, min(args.steps, 3))
-    if args.mixed_only:
-        t_fp64, info_fp64 = float("nan"), {"iterations": None, "resid_true": None}
-    else:
-        t_fp64, info_fp64, _, _ = timed(ls.LS_FP64, steps64, profile=True)
-
-    # end to end through the public API with host buffers (b, f in pinned memory; sigma back)
-    b_host = torch.from_numpy(b).pin_memory()
-    f_host = f_dev.cpu().pin_memory()
-    s_host = torch.zeros(n, n, dtype=torch.complex128).pin_memory()
-    t_e2e = 0.0
-    for _ in range(0 if args.mixed_only else args.steps):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        H = ls.ls_build(n, h, kappa, b_host, 1e-4, precision=PREC, top_uncompressed=args.top_uncompressed)
-        ls.ls_solve(H, f_host, s_host)
-        ls.ls_free(H)
-        torch.cuda.synchronize()
-        t_e2e += time.perf_counter() - t0
+    sig_mixed = main.sig.clone()
+    # profiled pass (per-launch events on): the phase breakdown and the rooflines
+    t_prof, _, _, _, prof = main.timed(1, flush, stream, profile=True)
+    # the plain FP64 path on the same workload
+    t_fp64, info_fp64, fp64_steps = float("nan"), None, 0
+    agree = None
+    if args.fp64_steps > 0:
+        for _ in range(args.fp64_warmup):
+            main.step(ls.LS_FP64)
+        t_fp64, info_fp64, _, _, _ = main.timed(args.fp64_steps, flush, stream, precision=ls.LS_FP64)
+        fp64_steps = args.fp64_steps
+        agree = float(torch.linalg.norm(main.sig - sig_mixed) / torch.linalg.norm(main.sig))
+    t_e2e, e2e_bytes = main.e2e(args.e2e_steps, flush) if args.e2e_steps > 0 else (0.0, None)
 
     t_mixed, t_fp64, t_e2e = max_over_ranks([t_mixed, t_fp64, t_e2e], world, dev)
     if rank != 0:
         return
+    N = main.N
     value = job_rate(world, N * args.steps, t_mixed)
-    value64 = job_rate(world, N * steps64, t_fp64)
-    e2e = job_rate(world, N * args.steps, t_e2e) if t_e2e > 0 else None
+    value64 = job_rate(world, N * fp64_steps, t_fp64) if fp64_steps else None
+    e2e = job_rate(world, N * args.e2e_steps, t_e2e) if t_e2e > 0 else None
+    fams, phases, e2e_roof = rooflines(prof, pk, tensor, t_mixed / args.steps, 1)
+    top = max((k for k in fams if k not in ("hbs_apply", "gmres_orth")), key=lambda k: fams[k]["ms_per_step"])
+    f = fams[top]
+    roof = {"bound": f["bound"], "kernel": top, "achieved": f["achieved"], "peak": f["peak"], "unit": f["unit"],
+            "frac": f["frac"], "traffic": None, "peak_source": f["peak_source"],
+            "note": "achieved = the family's algorithmic work over its device time in the profiled pass"}
 
-    # roofline of every timed kernel family; the one with the largest device time is the headline
-    pk = peaks()
-    tensor = args.precision in ("tf32", "tf32x3")
-
-    def roof_of(name, p):
-        avg_ms = p["total_ms"] / p["launches"]
-        if name.startswith("matvec") or name == "spectrum_setup":
-            bound, peak, unit, work = "alu", pk["fp64_tflops"], "TFLOP/s (FP64)", p["flops"]
-            src = "nominal FP64 rate"
-        elif name in ("hbs_apply", "gmres_orth"):
-            bound, peak, unit, work = "hbm", pk["hbm_gbs"], "GB/s", p["bytes"]
-            src = pk["source"]
-        elif name == "merge_gemm" and tensor:
-            bound, peak, unit, work = "tensor", pk["bf16_tflops"] / 2, "TFLOP/s (TF32)", p["flops"]
-            src = pk["source"] + " bf16 x 1/2 (nominal tf32:bf16 ratio)"
-        else:
-            bound, peak, unit, work = "alu", pk["fp32_tflops"], "TFLOP/s (FP32 SIMT)", p["flops"]
-            src = "unit counts x max clock"
-        scale = 1e9 if unit == "GB/s" else 1e12
-        achieved = work / p["launches"] / (avg_ms * 1e-3) / scale
-        return {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "peak_source": src, "avg_launch_ms": avg_ms,
-                "launches": p["launches"]}
-
-    kernels = {k: roof_of(k, v) for k, v in prof.items() if v["launches"] > 0}
-    single = {k: v for k, v in prof.items() if v["launches"] > 0 and k not in ("hbs_apply", "gmres_orth")}
-    top = max(single.items(), key=lambda kv: kv[1]["total_ms"])[0]
-    roof = kernels[top]
-    breakdown = {k: round(v["total_ms"] / args.steps, 4) for k, v in prof.items() if v["launches"]}
-
+    secondary = {}
+    if not args.no_secondary:
+        for name, prec_list in (("precond_n256", [PREC, ls.LS_FP64]),):
+            leg = Leg(ls, torch, dev, name, PREC)
+            out = {}
+            for pr in prec_list:
+                for _ in range(2):
+                    leg.step(pr)
+                t, info, bi, _, _ = leg.timed(3, flush, stream, precision=pr)
+                out["mixed" if pr == PREC else "fp64"] = {
+                    "value": leg.N * 3 / t / 1e6, "unit": "Mdof/s", "ms_per_step": t / 3 * 1e3,
+                    "iterations": info["iterations"], "resid_true": info["resid_true"], "ranks": bi["ranks"]}
+            secondary[name] = out
+        leg = Leg(ls, torch, dev, "direct_n32", ls.LS_FP64)
+        leg.step()
+        t, info, bi, _, _ = leg.timed(3, flush, stream)
+        secondary["direct_n32"] = {"value": leg.N * 3 / t / 1e6, "unit": "Mdof/s", "ms_per_step": t / 3 * 1e3,
+                                   "precision": "FP64, eps 1e-10, order-10 corrections inside the HBS",
+                                   "iterations": info["iterations"], "resid_true": info["resid_true"]}
     adj = adjoint_leg(ls, torch, dev, PREC) if not args.no_adjoint else None
-    cpu = cpu_baseline(n, kappa, b) if not args.no_cpu_baseline else None
+    if adj:
+        secondary["differentiation_n512"] = adj
+    cpu = cpu_baseline() if not args.no_cpu_baseline else None
     line = {"metric": METRIC, "value": value, "unit": "Mdof/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_mixed / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64 HBS + c128 FFT/GMRES", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "description": WORKLOAD_TEXT, "l2": "flushed between steps",
-                       "top_levels_uncompressed": args.top_uncompressed,
-                       "nrhs": 1, "precision": f"mixed ({args.precision} HBS merges, FP32 HBS storage, "
-                                                        "FP64 matvec + GMRES)"},
-            "fp64": {"value": value64, "unit": "Mdof/s", "ms_per_step": t_fp64 / steps64 * 1e3,
-                     "iterations": info_fp64["iterations"], "resid_true": info_fp64["resid_true"]},
+            "config": {"workload": args.workload, "description": WORKLOAD_TEXT if args.workload == WORKLOAD else
+                       args.workload, "l2": "flushed between steps (inputs and factors also far larger than L2)",
+                       "nrhs": 1, "precision": f"mixed ({args.precision} merge GEMMs, FP32 HBS, FP64 matvec + GMRES)"},
             "iterations": info_mixed["iterations"], "resid_true": info_mixed["resid_true"],
-            "roofline": roof, "breakdown_ms_per_step": breakdown,
-            "kernel_rooflines": {k: {"bound": v["bound"], "achieved": round(v["achieved"], 3), "unit": v["unit"],
-                                     "frac": round(v["frac"], 4)} for k, v in kernels.items()},
+            "ranks": binfo["ranks"], "factor_GB": binfo["factor_bytes"] / 1e9,
+            "fp64": {"value": value64, "unit": "Mdof/s", "steps": fp64_steps, "warmup": args.fp64_warmup,
+                     "ms_per_step": t_fp64 / fp64_steps * 1e3 if fp64_steps else None,
+                     "iterations": info_fp64["iterations"] if info_fp64 else None,
+                     "resid_true": info_fp64["resid_true"] if info_fp64 else None,
+                     "sigma_rel_diff_mixed_vs_fp64": agree},
+            "roofline": roof, "phase_rooflines": phases, "e2e_roofline": e2e_roof,
+            "kernel_rooflines": {k: {kk: (round(vv, 5) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                                 for k, v in fams.items()},
+            "profiled_step_ms": t_prof * 1e3,
+            "peaks": pk,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e, "unit": "Mdof/s", "h2d_bytes_per_step": N * 8 + N * 16,
-                    "d2h_bytes_per_step": N * 16},
-            "gpu_launches": launches, "clocks": clk.summary(), "adjoint": adj}
+            "e2e": dict({"value": e2e, "unit": "Mdof/s", "steps": args.e2e_steps}, **(e2e_bytes or {})),
+            "gpu_launches": launches, "clocks": clk.summary(), "secondary": secondary}
     print(json.dumps(line), flush=True)
 
 
@@ -379,15 +476,17 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, help="headline workload (paper_2007_12718_gb300.inputs.WORKLOADS)")
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the plain FP64 leg (0 = skip)")
+    ap.add_argument("--fp64-warmup", type=int, default=0,
+                    help="untimed FP64 steps first (the mixed warm-up already loaded every shared kernel)")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the host-buffer end-to-end leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 256^2 and 32^2 legs")
     ap.add_argument("--no-adjoint", action="store_true",
-                    help="skip the differentiation workload (512x512 misfit gradient) reported under 'adjoint'")
+                    help="skip the differentiation workload (512x512 misfit gradient)")
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32", "tf32x3"],
                     help="engine of the mixed path's merge GEMMs (FP32 storage in all three)")
-    ap.add_argument("--top-uncompressed", type=int, default=1,
-                    help="tree levels kept uncompressed at the top (U = I); 0 = every level compressed")
-    ap.add_argument("--mixed-only", action="store_true",
-                    help="time only the mixed path (no FP64 or end-to-end legs); for profiler runs")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

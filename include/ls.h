@@ -253,6 +253,14 @@ int ls_profile_enable(int on);
 int ls_profile_reset(void);
 int ls_profile_get(ls_profile_entry* out, int max_entries);
 
+/* ls_measure_peak -- arithmetic rate of this GPU for the roofline denominators
+ * (not part of the method): long chains of independent fused multiply-adds,
+ * timed with CUDA events on `stream` (best of three launches after one warm-up).
+ *   kind: 0 = FP64 FMA, 1 = FP32 FMA, 2 = packed FP32 FMA (two lanes per
+ *         instruction, the form the FP32 GEMMs use).  tflops: out, 2 flops/FMA.
+ * Returns LS_EINVAL for a bad kind.  Synchronises the stream. */
+int ls_measure_peak(int kind, double* tflops, void* stream);
+
 /* Number of CUDA kernels this library has launched in this process so far. */
 long long ls_kernel_launches(void);
 

@@ -36,7 +36,8 @@ EXPORTED = ["ls_default_opts", "ls_build", "ls_apply", "ls_matvec", "ls_solve", 
             "ls_get_build_info", "ls_free", "ls_strerror", "ls_last_error", "ls_profile_enable",
             "ls_profile_reset", "ls_profile_get", "ls_kernel_launches", "ls_matvec_noalloc",
             "ls_matvec_noalloc_max_elems", "ls_cgemm_c64", "ls_row_id", "ls_row_id_ex", "ls_field", "ls_solve_transpose",
-            "ls_set_receivers", "ls_receiver_field", "ls_receiver_adjoint", "ls_misfit_gradient"]
+            "ls_set_receivers", "ls_receiver_field", "ls_receiver_adjoint", "ls_misfit_gradient",
+            "ls_measure_peak"]
 
 
 class Grid(ctypes.Structure):
@@ -128,6 +129,8 @@ def load_library(path=LIB_PATH):
     lib.ls_row_id_ex.argtypes = [vp, ip, ip, dp, ip, ip, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                  vp, vp]
     lib.ls_row_id_ex.restype = ip
+    lib.ls_measure_peak.argtypes = [ip, ctypes.POINTER(ctypes.c_double), vp]
+    lib.ls_measure_peak.restype = ip
     lib.ls_kernel_launches.argtypes = []
     lib.ls_kernel_launches.restype = ctypes.c_longlong
     _lib = lib
@@ -427,6 +430,13 @@ def ls_row_id(A, eps, precision=LS_FP64, stream=None, method=LS_ID_GREEDY):
     kk = k.value
     Uk = U.reshape(-1)[: m * kk].reshape(m, kk).copy()
     return kk, np.array(piv[:kk], dtype=np.int64), Uk
+
+
+def ls_measure_peak(kind, stream=None):
+    """Measured arithmetic rate in TFLOP/s: kind 0 FP64 FMA, 1 FP32 FMA, 2 packed FP32 FMA."""
+    v = ctypes.c_double(0.0)
+    _check(load_library().ls_measure_peak(kind, ctypes.byref(v), _stream(stream)), "ls_measure_peak")
+    return v.value
 
 
 def ls_kernel_launches():

@@ -91,4 +91,10 @@ WORKLOADS = {
                          order_matvec=10, eps=1e-4, leaf=8),
     "precond_n2048": dict(n=2048, kappa=400 * np.pi, b=lambda n: gaussian_family(n, 0),
                           order_precond=4, order_matvec=10, eps=1e-4, leaf=8),
+    # the 2048^2 workload's regime (kappa h = 0.614, 10.24 points per wavelength) at
+    # smaller sizes: the CPU oracle's bounded samples and intermediate checks
+    "precond_n256_10ppw": dict(n=256, kappa=50 * np.pi, b=lambda n: gaussian_family(n, 0), order_precond=4,
+                               order_matvec=10, eps=1e-4, leaf=8),
+    "precond_n1024_10ppw": dict(n=1024, kappa=200 * np.pi, b=lambda n: gaussian_family(n, 0), order_precond=4,
+                                order_matvec=10, eps=1e-4, leaf=8),
 }
