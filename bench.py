@@ -381,8 +381,8 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    PREC = {"fp32": ls.LS_FP32, "tf32": ls.LS_TF32, "tf32x3": ls.LS_TF32X3}[args.precision]
-    tensor = args.precision in ("tf32", "tf32x3")
+    PREC = {"fp32": ls.LS_FP32, "tf32x3": ls.LS_TF32X3}[args.precision]
+    tensor = args.precision == "tf32x3"
     pk = measured_peaks(ls)
 
     main = Leg(ls, torch, dev, args.workload, PREC)
@@ -485,7 +485,7 @@ def main():
     ap.add_argument("--no-secondary", action="store_true", help="skip the 256^2 and 32^2 legs")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the differentiation workload (512x512 misfit gradient)")
-    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32", "tf32x3"],
+    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3"],
                     help="engine of the mixed path's merge GEMMs (FP32 storage in all three)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

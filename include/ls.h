@@ -46,11 +46,13 @@ enum {
 };
 
 /* Precision of the HBS preconditioner (compression, inverse build, apply).
- * The FFT matvec and GMRES are FP64 in every mode.  LS_FP32, LS_TF32 and
- * LS_TF32X3 all store the factors in FP32; they differ in the engine of the
- * merge GEMMs (Eqs. 26-27): FP32 SIMT cores, tensor cores with tf32 inputs
- * (FP32 accumulation), or tensor cores with each operand split into two tf32
- * terms (three products, ~FP32 accuracy). */
+ * The FFT matvec and GMRES are FP64 in every mode.  LS_FP32 and LS_TF32X3 store
+ * the factors in FP32; they differ in the engine of the large merge GEMMs
+ * (Eqs. 26-27): FP32 SIMT cores, or tensor cores with each operand split into
+ * two tf32 terms (three products, ~FP32 accuracy).  LS_TF32 (one tf32 product,
+ * ~1e-3 relative error) names a GEMM engine of ls_cgemm_c64 only: its
+ * preconditioner misses the HBS tolerance by orders of magnitude, so ls_build
+ * rejects it (LS_EINVAL). */
 enum { LS_FP64 = 0, LS_FP32 = 1, LS_TF32 = 2, LS_TF32X3 = 3 };
 
 typedef struct {
@@ -64,7 +66,7 @@ typedef struct {
   int order_precond; /* order used inside the HBS compression: 4,6,8,10 (default 4)      */
   int leaf_side;     /* leaf box side s (s*s points per leaf, default 8)                  */
   int proxy_width;   /* proxy ring width in grid cells; 0 = from tol and order (default)  */
-  int precision;     /* LS_FP64, LS_FP32, LS_TF32 or LS_TF32X3 (default LS_FP32)          */
+  int precision;     /* LS_FP64, LS_FP32 or LS_TF32X3 (default LS_FP32)                    */
   int gmres_maxit;   /* default 100 (Sec. 6.3)                                            */
   double gmres_tol;  /* relative residual, default 1e-10 (Sec. 6.3)                       */
   int merge_pivoting; /* merge inverses: 0 = blocks without interchanges, checked, with the
@@ -73,6 +75,10 @@ typedef struct {
                          no ID); 0 = every level compressed as in Sec. 3.2 (default)      */
   int id_method;      /* per-level ID (Sec. 2.1): LS_ID_AUTO (default), LS_ID_GREEDY or
                          LS_ID_BLOCKED, see ls_row_id_ex                                  */
+  int wait_limit;     /* polls of a device-side wait (grid barriers of the ID, apply and GMRES
+                         kernels) before it gives up and the call returns LS_ETIMEOUT; 0 =
+                         default (2e7 polls, about a second).  After LS_ETIMEOUT the handle's
+                         barrier state is spent: free the handle.                          */
 } ls_opts;
 
 /* Pivot selection of the row ID (ls_opts.id_method, ls_row_id_ex).
@@ -106,6 +112,9 @@ typedef struct {
   double bytes_apply;       /* algorithmic bytes read+written by one HBS apply */
   double factor_bytes;      /* device bytes held by the factors */
   int pivot_fallbacks;      /* merge levels whose check sent them to the row-pivoted inverse */
+  double probe_resid_max;   /* largest max_i |(Z W v - v)_i| over the merge inverses W = Z^-1
+                               formed without interchanges, v a unit-modulus probe; W is accepted
+                               when it is <= max(tol, 10 u k), u the unit roundoff, k the order */
 } ls_build_info;
 
 typedef struct ls_handle ls_handle; /* opaque, library-owned */
@@ -138,7 +147,8 @@ int ls_build(const ls_grid* grid, double kappa, const double* b, double tol,
  * apply on a handle makes transposed copies of the factors (as much device
  * memory again as the factors).  f, q: nrhs complex128 grid vectors.
  * transpose: 0 or 1, else LS_EINVAL.  Applies on one handle must not run
- * concurrently (they share the handle's scratch). */
+ * concurrently (they share the handle's scratch).  The call is asynchronous: a
+ * device-side timeout of its barriers shows in ls_sync or the next ls_solve. */
 int ls_apply(ls_handle* h, const void* f, void* q, int nrhs, int transpose, void* stream);
 
 /* ls_matvec -- y = (I + B (G + T)) x, the order_matvec operator applied by a
@@ -193,7 +203,8 @@ int ls_receiver_adjoint(ls_handle* h, const void* v, void* g, int nrhs, void* st
  * and dJ/db by the adjoint method: lambda_r = A^-T R^T conj(u_r - d_r)
  * (ls_solve_transpose), then
  *   dJ/db_j = -2 kappa^2 sum_r Re(lambda_r[j] ((G+T) sigma_r + u_inc,r)[j]).
- *   J: out, host double.  grad: out, ny*nx doubles, host or device.
+ *   J: out, host double.  grad: out, ny*nx doubles, host or device; NULL
+ *   computes J alone (the forward solves only, no adjoint solve).
  *   info: NULL or 2 nrhs entries (the forward solves, then the adjoint ones).
  * The gradient is that of the discrete system solved to gmres_tol; the HBS
  * inverse only preconditions.  Returns LS_ENOCONV (outputs still written) if
@@ -217,24 +228,39 @@ int ls_rhs_plane_wave(ls_handle* h, const double* thetas, void* f, int nrhs, voi
  * allocating routine.  Its FFT scratch is a fixed file-scope device array of
  * ls_matvec_noalloc_max_elems() = 2^18 complex128 entries (4 MiB), held by
  * every GPU that loads the library until the process exits.
- *   x, y : device pointers, nrhs complex128 grid vectors (x, y may not alias).
+ *   x, y : device pointers of the current device (the handle's), nrhs
+ *   complex128 grid vectors (x, y may not alias).
  *   Requires nrhs * ny * 2 * nx <= 2^18; larger sizes return LS_EINVAL with a
- *   message, as do host pointers.  The handle must come from ls_build (which
- *   does allocate, at set-up time).
+ *   message, as do host pointers and pointers of another device.  The handle
+ *   must come from ls_build (which does allocate, at set-up time).
  *   The first call on a device looks up the scratch array's device address
- *   (cudaGetSymbolAddress, with that device current); make that first call
- *   before any stream capture.  Every call shares the one array and leaves its
+ *   (cudaGetSymbolAddress, with that device current) and keeps it for the life
+ *   of the process; make that first call before any stream capture.  The kept
+ *   address does not survive a cudaDeviceReset of that device (the library's
+ *   module is loaded anew there): such a program must not call this entry point
+ *   after the reset.  Every call shares the one array and leaves its
  *   contents behind; nothing in it needs to start at zero (each call writes
  *   every entry before reading it), but calls that overlap on the GPU (two
  *   streams at once) race on it. */
 int ls_matvec_noalloc(ls_handle* h, const void* x, void* y, int nrhs, void* stream);
 long long ls_matvec_noalloc_max_elems(void);
 
+/* ls_sync -- wait for the work queued on `stream` and return the handle's
+ * device status: LS_OK, or LS_ETIMEOUT / LS_ESINGULAR if a device-side wait or
+ * a local inverse of an earlier asynchronous call (ls_apply, ls_matvec, ...)
+ * failed.  ls_solve and ls_build report the status themselves.  The status is
+ * not cleared: a handle whose wait timed out is spent. */
+int ls_sync(ls_handle* h, void* stream);
+
 /* ls_build_info -- ranks, flop and byte counts of the built handle. */
 int ls_get_build_info(const ls_handle* h, ls_build_info* info);
 
 /* ls_free -- release every resource of the handle (NULL is allowed). */
 void ls_free(ls_handle* h);
+
+/* Every call taking a handle must run with the handle's device current (the
+ * device current at ls_build); otherwise it returns LS_EINVAL without touching
+ * the GPU.  ls_free releases the handle on its own device. */
 
 /* Per-kernel timing (not part of the method; used by the benchmark).
  * When enabled, the library records a CUDA event pair around each launch of
@@ -260,6 +286,22 @@ int ls_profile_get(ls_profile_entry* out, int max_entries);
  *         instruction, the form the FP32 GEMMs use).  tflops: out, 2 flops/FMA.
  * Returns LS_EINVAL for a bad kind.  Synchronises the stream. */
 int ls_measure_peak(int kind, double* tflops, void* stream);
+
+/* Device and page-locked host allocations this library has made in this
+ * process so far (every stream-ordered pool allocation counts, also when the
+ * pool serves it from memory it already holds). */
+long long ls_allocations(void);
+
+/* ls_fault_inject -- host-side failure injection for tests of the error paths
+ * (not part of the method; no GPU fault is ever caused).  spec:
+ *   "alloc:N"  the N-th device allocation from now on (N >= 1) fails as if the
+ *              device were out of memory (LS_ENOMEM), once;
+ *   "nan_b"    the next ls_build sees a NaN in b, as if the caller had passed
+ *              one (LS_EINVAL from the finiteness check), once;
+ *   "" or NULL clears a pending injection.
+ * The environment variable LS_FAULT, read once when the library loads, takes
+ * the same spec.  Returns LS_EINVAL for a spec it does not know. */
+int ls_fault_inject(const char* spec);
 
 /* Number of CUDA kernels this library has launched in this process so far. */
 long long ls_kernel_launches(void);

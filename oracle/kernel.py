@@ -4,7 +4,7 @@ Test infrastructure only (see ``oracle/__init__``).
 
 H0^(1) (outgoing) is the reading that satisfies the radiation condition the
 paper relies on (Sec. 1).  Evaluated with scipy's Hankel function.
-Parity pins: the constant-b disk closed form (tests/test_oracle_disk.py) fixes
+Parity pins: the constant-b disk closed form (tests/test_oracle_nystrom.py, test_disk_closed_form) fixes
 the kind, sign and scale of the kernel through the scattered field.
 """
 import numpy as np

@@ -38,7 +38,7 @@ Z'(0), Z'(-1), Z'(-2), Z'(-3) are taken from the closed forms of zeta and
 Dirichlet beta at non-positive integers; Z_H4'(0), Z_H4'(-1) from the Mellin
 split of the theta series (exponentially convergent).
 
-Parity pins (tests/test_oracle_lattice.py, tests/test_oracle_convergence.py):
+Parity pins (tests/test_oracle_lattice.py; the solve orders in tests/test_oracle_nystrom.py):
 closed forms vs an independent numerical derivative of 4 zeta beta; the H4
 constants vs Gaussian-regularised lattice sums; the observed convergence
 orders 2/4/6/8/10 of the full discretisation.  Agreement with Duan-Rokhlin's own

@@ -22,7 +22,7 @@ Functions:
                          receivers outside the domain.
 * ``rhs``             -- f = -kappa^2 b u_inc for a plane wave.
 Parity pins: tests/test_oracle_nystrom.py (FFT vs dense, symmetry, b = 0),
-tests/test_oracle_convergence.py (observed orders), tests/test_oracle_disk.py.
+tests/test_oracle_nystrom.py (test_solve_convergence_orders: observed orders; test_disk_closed_form).
 """
 import numpy as np
 import scipy.linalg as sla

@@ -37,7 +37,7 @@ EXPORTED = ["ls_default_opts", "ls_build", "ls_apply", "ls_matvec", "ls_solve", 
             "ls_profile_reset", "ls_profile_get", "ls_kernel_launches", "ls_matvec_noalloc",
             "ls_matvec_noalloc_max_elems", "ls_cgemm_c64", "ls_row_id", "ls_row_id_ex", "ls_field", "ls_solve_transpose",
             "ls_set_receivers", "ls_receiver_field", "ls_receiver_adjoint", "ls_misfit_gradient",
-            "ls_measure_peak"]
+            "ls_measure_peak", "ls_allocations", "ls_fault_inject", "ls_sync"]
 
 
 class Grid(ctypes.Structure):
@@ -49,7 +49,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("order_matvec", ctypes.c_int), ("order_precond", ctypes.c_int), ("leaf_side", ctypes.c_int),
                 ("proxy_width", ctypes.c_int), ("precision", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("merge_pivoting", ctypes.c_int),
-                ("top_uncompressed", ctypes.c_int), ("id_method", ctypes.c_int)]
+                ("top_uncompressed", ctypes.c_int), ("id_method", ctypes.c_int), ("wait_limit", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -61,7 +61,7 @@ class BuildInfo(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("ranks", ctypes.c_int * 32), ("proxy_width", ctypes.c_int),
                 ("flops_build", ctypes.c_double), ("flops_compress", ctypes.c_double),
                 ("bytes_apply", ctypes.c_double), ("factor_bytes", ctypes.c_double),
-                ("pivot_fallbacks", ctypes.c_int)]
+                ("pivot_fallbacks", ctypes.c_int), ("probe_resid_max", ctypes.c_double)]
 
 
 class ProfileEntry(ctypes.Structure):
@@ -131,6 +131,12 @@ def load_library(path=LIB_PATH):
     lib.ls_row_id_ex.restype = ip
     lib.ls_measure_peak.argtypes = [ip, ctypes.POINTER(ctypes.c_double), vp]
     lib.ls_measure_peak.restype = ip
+    lib.ls_sync.argtypes = [vp, vp]
+    lib.ls_sync.restype = ip
+    lib.ls_allocations.argtypes = []
+    lib.ls_allocations.restype = ctypes.c_longlong
+    lib.ls_fault_inject.argtypes = [ctypes.c_char_p]
+    lib.ls_fault_inject.restype = ip
     lib.ls_kernel_launches.argtypes = []
     lib.ls_kernel_launches.restype = ctypes.c_longlong
     _lib = lib
@@ -198,7 +204,7 @@ class Handle:
         return {"levels": bi.levels, "ranks": list(bi.ranks[: bi.levels + 1]), "proxy_width": bi.proxy_width,
                 "flops_build": bi.flops_build, "flops_compress": bi.flops_compress,
                 "bytes_apply": bi.bytes_apply, "factor_bytes": bi.factor_bytes,
-                "pivot_fallbacks": bi.pivot_fallbacks}
+                "pivot_fallbacks": bi.pivot_fallbacks, "probe_resid_max": bi.probe_resid_max}
 
 
 def default_opts():
@@ -209,12 +215,12 @@ def default_opts():
 
 def ls_build(n, h, kappa, b, tol, order_matvec=10, order_precond=4, leaf_side=8, proxy_width=0,
              precision=LS_FP32, gmres_maxit=100, gmres_tol=1e-10, x0=0.0, y0=0.0, ny=None, stream=None,
-             merge_pivoting=0, top_uncompressed=0, id_method=LS_ID_AUTO):
+             merge_pivoting=0, top_uncompressed=0, id_method=LS_ID_AUTO, wait_limit=0):
     """Compress G and build the HBS inverse (Sec. 3.2, Algorithm 1); b is [ny][nx] float64."""
     lib = load_library()
     g = Grid(n, n if ny is None else ny, h, x0, y0)
     o = Opts(order_matvec, order_precond, leaf_side, proxy_width, precision, gmres_maxit, gmres_tol,
-             merge_pivoting, top_uncompressed, id_method)
+             merge_pivoting, top_uncompressed, id_method, wait_limit)
     bp, keep, _ = _ptr(b, np.float64)
     out = ctypes.c_void_p()
     _check(lib.ls_build(ctypes.byref(g), kappa, bp, tol, ctypes.byref(o), _stream(stream), ctypes.byref(out)),
@@ -306,10 +312,11 @@ def ls_receiver_adjoint(handle, v, g, stream=None):
 
 def ls_misfit_gradient(handle, thetas, data, grad, stream=None, allow_noconv=False):
     """J = sum |u - data|^2 over plane waves `thetas` and the handle's receivers, and
-    dJ/db into `grad` (ny*nx float64) by the adjoint method.  Returns (J, infos)."""
+    dJ/db into `grad` (ny*nx float64) by the adjoint method; grad=None computes J
+    alone (no adjoint solve).  Returns (J, infos)."""
     th = np.ascontiguousarray(thetas, dtype=np.float64)
     dp_, k1, _ = _ptr(data, np.complex128)
-    gp, k2, _ = _ptr(grad, np.float64, True)
+    gp, k2 = (ctypes.c_void_p(None), None) if grad is None else _ptr(grad, np.float64, True)[:2]
     J = ctypes.c_double(0.0)
     infos = (SolveInfo * (2 * len(th)))()
     _check(load_library().ls_misfit_gradient(handle.ptr, th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
@@ -324,8 +331,9 @@ def _make_misfit_function():
     class LSMisfit(torch.autograd.Function):
         """J(b) = sum over directions and receivers of |u(r_k) - d|^2 as a torch
         function of the potential b (float64 [ny][nx], CUDA).  forward builds the
-        HBS preconditioner for b, runs the forward and adjoint solves and keeps
-        dJ/db; backward returns grad_output * dJ/db.  Usage:
+        HBS preconditioner for b and runs the forward solves; when b requires a
+        gradient it also runs the adjoint solves and keeps dJ/db, which backward
+        returns times grad_output.  Usage:
             J = LSMisfit.apply(b, h, kappa, thetas, receivers, data, build_kwargs)"""
 
         @staticmethod
@@ -333,13 +341,14 @@ def _make_misfit_function():
             kw = dict(build_kwargs or {})
             tol = kw.pop("tol", 1e-4)
             H = ls_build(b.shape[1], h, kappa, b.detach().contiguous(), tol, ny=b.shape[0], **kw)
+            want_grad = bool(ctx.needs_input_grad[0])
             try:
                 ls_set_receivers(H, receivers)
-                grad = torch.empty_like(b, dtype=torch.float64)
+                grad = torch.empty_like(b, dtype=torch.float64) if want_grad else None
                 J, _ = ls_misfit_gradient(H, thetas, data, grad)
             finally:
                 ls_free(H)
-            ctx.save_for_backward(grad)
+            ctx.save_for_backward(grad if want_grad else torch.zeros(0, dtype=torch.float64, device=b.device))
             return torch.tensor(J, dtype=torch.float64, device=b.device)
 
         @staticmethod
@@ -437,6 +446,22 @@ def ls_measure_peak(kind, stream=None):
     v = ctypes.c_double(0.0)
     _check(load_library().ls_measure_peak(kind, ctypes.byref(v), _stream(stream)), "ls_measure_peak")
     return v.value
+
+
+def ls_sync(handle, stream=None):
+    """Wait for the stream; raise LSError if an earlier asynchronous call of the
+    handle failed on the device (LS_ETIMEOUT, LS_ESINGULAR)."""
+    _check(load_library().ls_sync(handle.ptr, _stream(stream)), "ls_sync")
+
+
+def ls_allocations():
+    """Device and page-locked host allocations the library has made so far."""
+    return int(load_library().ls_allocations())
+
+
+def ls_fault_inject(spec):
+    """Host-side failure injection for error-path tests: "alloc:N", "nan_b" or ""."""
+    _check(load_library().ls_fault_inject(spec.encode() if spec is not None else None), "ls_fault_inject")
 
 
 def ls_kernel_launches():

@@ -130,6 +130,7 @@ using ls::z64;
 
 int ls_set_receivers(ls_handle* H, const double* rx, int nr, void* stream) {
   if (!H || nr < 0 || (nr > 0 && !rx)) return LS_EINVAL;
+  if (int rc = ls::check_device(H)) return rc;
   ls::StreamScope scope((cudaStream_t)stream);
   H->stream = (cudaStream_t)stream;
   cudaStream_t st = (cudaStream_t)stream;
@@ -165,6 +166,7 @@ int ls_set_receivers(ls_handle* H, const double* rx, int nr, void* stream) {
 
 int ls_receiver_field(ls_handle* H, const void* sigma, void* u, int nrhs, void* stream) {
   if (!H || !sigma || !u || nrhs < 1 || H->nrec < 1) return LS_EINVAL;
+  if (int rc = ls::check_device(H)) return rc;
   ls::StreamScope scope((cudaStream_t)stream);
   H->stream = (cudaStream_t)stream;
   cudaStream_t st = (cudaStream_t)stream;
@@ -182,6 +184,7 @@ int ls_receiver_field(ls_handle* H, const void* sigma, void* u, int nrhs, void* 
 
 int ls_receiver_adjoint(ls_handle* H, const void* v, void* g, int nrhs, void* stream) {
   if (!H || !v || !g || nrhs < 1 || H->nrec < 1) return LS_EINVAL;
+  if (int rc = ls::check_device(H)) return rc;
   ls::StreamScope scope((cudaStream_t)stream);
   H->stream = (cudaStream_t)stream;
   cudaStream_t st = (cudaStream_t)stream;
@@ -200,7 +203,9 @@ int ls_receiver_adjoint(ls_handle* H, const void* v, void* g, int nrhs, void* st
 
 int ls_misfit_gradient(ls_handle* H, const double* thetas, int nrhs, const void* d, double* J, void* grad,
                        ls_solve_info* info, void* stream) {
-  if (!H || !thetas || nrhs < 1 || !d || !J || !grad || H->nrec < 1) return LS_EINVAL;
+  if (!H || !thetas || nrhs < 1 || !d || !J || H->nrec < 1) return LS_EINVAL;
+  if (int rc = ls::check_device(H)) return rc;
+  const bool want_grad = grad != nullptr;  // without it only J: no adjoint solve
   ls::StreamScope scope((cudaStream_t)stream);
   H->stream = (cudaStream_t)stream;
   cudaStream_t st = (cudaStream_t)stream;
@@ -216,13 +221,13 @@ int ls_misfit_gradient(ls_handle* H, const double* thetas, int nrhs, const void*
   };
   fail(ls::dalloc((void**)&f, bvec));
   if (!rc) fail(ls::dalloc((void**)&sig, bvec));
-  if (!rc) fail(ls::dalloc((void**)&lam, bvec));
-  if (!rc) fail(ls::dalloc((void**)&v, bvec));
+  if (!rc && want_grad) fail(ls::dalloc((void**)&lam, bvec));
+  if (!rc && want_grad) fail(ls::dalloc((void**)&v, bvec));
   if (!rc) fail(ls::dalloc((void**)&u, sizeof(z64) * (size_t)n));
   if (!rc) fail(ls::dalloc((void**)&res, sizeof(z64) * (size_t)n));
   if (!rc) fail(ls::dalloc((void**)&dev_small, sizeof(double) * (1 + 2 * (size_t)nrhs)));
   if (!rc) fail(ls::stage_in(d, sizeof(z64) * (size_t)n, st, &sd));
-  if (!rc) fail(ls::stage_out_alloc(grad, sizeof(double) * (size_t)N, &sg));
+  if (!rc && want_grad) fail(ls::stage_out_alloc(grad, sizeof(double) * (size_t)N, &sg));
   double* pin = nullptr;
   if (!rc) {
     pin = static_cast<double*>(ls::pinned_scratch(sizeof(double) * (1 + 2 * (size_t)nrhs)));
@@ -253,8 +258,8 @@ int ls_misfit_gradient(ls_handle* H, const double* thetas, int nrhs, const void*
     ls::residual_kernel<<<1, 1024, 0, st>>>(u, sd.dev, n, res, dev_small);
     fail(ls::check_launch("misfit residual"));
   }
-  if (!rc) fail(ls::receiver_adjoint(H, res, f, nrhs, st));
-  if (!rc) {
+  if (!rc && want_grad) fail(ls::receiver_adjoint(H, res, f, nrhs, st));
+  if (!rc && want_grad) {
     int s = ls::gmres_solve(H, f, lam, nrhs, info ? info + nrhs : nullptr, 1, st);
     if (s == LS_ENOCONV)
       solve_rc = s;
@@ -262,8 +267,8 @@ int ls_misfit_gradient(ls_handle* H, const double* thetas, int nrhs, const void*
       fail(s);
   }
   // dJ/db = -2 kappa^2 sum_r Re(lambda_r ((G + T) sigma_r + u_inc,r))
-  if (!rc) fail(ls::conv_apply(H, sig, v, nrhs, ls::CONV_FIELD, st));
-  if (!rc) {
+  if (!rc && want_grad) fail(ls::conv_apply(H, sig, v, nrhs, ls::CONV_FIELD, st));
+  if (!rc && want_grad) {
     count_launch();
     ls::gradient_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(lam, v, dev_small + 1, nrhs, gr.nx, gr.ny, gr.h,
                                                                      gr.x0, gr.y0, H->kappa,
@@ -278,7 +283,7 @@ int ls_misfit_gradient(ls_handle* H, const double* thetas, int nrhs, const void*
     else
       *J = pin[0];
   }
-  if (!rc) fail(ls::stage_out_finish(grad, sizeof(double) * (size_t)N, st, &sg));
+  if (!rc && want_grad) fail(ls::stage_out_finish(grad, sizeof(double) * (size_t)N, st, &sg));
   cudaStreamSynchronize(st);
   ls::release(&sd);
   ls::release(&sg);

@@ -1608,6 +1608,8 @@ int invert_batch(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int P, vo
   }
   const int rows_per = 16;
   const size_t smem_u = sizeof(int) * ((n + 3) & ~3) + sizeof(cx<R>) * n;
+  if (smem_u > 48 * 1024)
+    LS_CUDA_TRY(cudaFuncSetAttribute(unpivot_rows_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_u));
   count_launch();
   unpivot_rows_kernel<R><<<dim3((n + rows_per - 1) / rows_per, P), 256, smem_u, st>>>(X, n, lda, sX, piv, rows_per);
   return check_launch("inverse_blocked");
@@ -1783,8 +1785,17 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
         if (l == 0) host_mark("root_inverse_checked");
         float worst;
         memcpy(&worst, &flags[0], sizeof(float));
-        const float limit = sizeof(R) == 4 ? 1e-3f : 1e-9f;
-        if (flags[1] != 0 || !(worst <= limit * sqrtf((float)kc))) {
+        H->probe_resid_max = std::max(H->probe_resid_max, (double)worst);
+        // W is accepted when max_i |(Z W v - v)_i| (|v_i| = 1) is within the HBS
+        // tolerance, so that the inverse adds no more error than the compression,
+        // or within 10 k_c units of the working precision, what a stable
+        // elimination of order k_c attains (in FP32 that is above the tolerance
+        // from k_c ~ 170 on; a row-pivoted inverse in the same precision would
+        // not do better).  A larger residual means growth in the elimination
+        // without interchanges: the row-pivoted inverse replaces it.
+        const double unit = sizeof(R) == 4 ? 5.96e-8 : 1.11e-16;
+        const double limit = std::max(H->tol, 10.0 * unit * kc);
+        if (flags[1] != 0 || !((double)worst <= limit)) {
           // restore Z and invert with row interchanges
           count_launch();
           copy_block_kernel<R><<<gc, 256, 0, st>>>(X22, n2, sX, Zc, kc, kk, kc, kc);
@@ -2226,7 +2237,8 @@ struct ApplyOp {
   double ar, ai;   // alpha
 };
 
-__device__ __forceinline__ bool apply_barrier(unsigned* count, unsigned* abort, unsigned target, int* sflag) {
+__device__ __forceinline__ bool apply_barrier(unsigned* count, unsigned* abort, unsigned target, int* sflag,
+                                              long long limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
@@ -2236,7 +2248,7 @@ __device__ __forceinline__ bool apply_barrier(unsigned* count, unsigned* abort, 
     while (true) {
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
       if ((int)(v - target) >= 0) break;
-      if ((++spins & 1023) == 0 && (*(volatile unsigned*)abort || spins > kSpinLimit)) {
+      if (++spins >= limit || ((spins & 1023) == 0 && *(volatile unsigned*)abort)) {
         atomicExch(abort, 1u);
         ok = 0;
         break;
@@ -2445,7 +2457,7 @@ template <class R>
 __global__ void __launch_bounds__(1024) apply_persistent_kernel(const ApplyOp* __restrict__ ops_g, int nops,
                                                                 TreeGeom g, const z64* __restrict__ f,
                                                                 z64* __restrict__ q, unsigned* bar, unsigned epoch0,
-                                                                int* err) {
+                                                                int* err, long long spin_limit) {
   __shared__ int s_ok;
   extern __shared__ unsigned char smraw[];
   ApplyOp* ops = reinterpret_cast<ApplyOp*>(smraw);
@@ -2492,7 +2504,7 @@ __global__ void __launch_bounds__(1024) apply_persistent_kernel(const ApplyOp* _
     }
     if (op.phase_end && o + 1 < nops) {
       target += gridDim.x;
-      if (!apply_barrier(bar, bar + 1, target, &s_ok)) {
+      if (!apply_barrier(bar, bar + 1, target, &s_ok, spin_limit)) {
         if (threadIdx.x == 0 && blockIdx.x == 0) atomicExch(err, LS_ETIMEOUT);
         return;
       }
@@ -2965,7 +2977,8 @@ int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, int transpose, cudaS
         const ApplyOp* ops = ops_all;
         int nops = H->apply_nops_t;
         unsigned epoch0 = H->apply_epoch;
-        void* args[] = {&ops, &nops, (void*)&g, &fr, &qr, &bar, &epoch0, &err};
+        long long spin = H->spin_limit;
+        void* args[] = {&ops, &nops, (void*)&g, &fr, &qr, &bar, &epoch0, &err, &spin};
         count_launch();
         LS_CUDA_TRY(
             cudaLaunchCooperativeKernel(kfn, dim3(H->apply_blocks), dim3(1024), args, apply_smem(kfn, nops, leaf_smem(H)), st));
@@ -2976,7 +2989,8 @@ int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, int transpose, cudaS
           const ApplyOp* ops = ops_all + start;
           int nops = e + 1 - start;
           unsigned epoch0 = 0;
-          void* args[] = {&ops, &nops, (void*)&g, &fr, &qr, &bar, &epoch0, &err};
+          long long spin = H->spin_limit;
+        void* args[] = {&ops, &nops, (void*)&g, &fr, &qr, &bar, &epoch0, &err, &spin};
           count_launch();
           LS_CUDA_TRY(cudaLaunchKernel(kfn, dim3(H->nsm), dim3(1024), args, apply_smem(kfn, nops, leaf_smem(H)), st));
           start = e + 1;
@@ -3000,7 +3014,8 @@ int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, int transpose, cudaS
       // barrier epochs continue across applies: (phases - 1) barriers of apply_blocks arrivals each
       unsigned epoch0 = H->apply_epoch;
       int* err = H->d_err;
-      void* args[] = {&ops, &nops, (void*)&g, &fr, &qr, &bar, &epoch0, &err};
+      long long spin = H->spin_limit;
+        void* args[] = {&ops, &nops, (void*)&g, &fr, &qr, &bar, &epoch0, &err, &spin};
       count_launch();
       LS_CUDA_TRY(
           cudaLaunchCooperativeKernel(kfn, dim3(H->apply_blocks), dim3(1024), args, apply_smem(kfn, nops, leaf_smem(H)), st));

@@ -94,16 +94,26 @@ __device__ __forceinline__ cx<double> ldcg_cx(const cx<double>* p) {
 // Grid-wide barrier for kernels launched with cudaLaunchCooperativeKernel
 // (all blocks co-resident).  The arrival counter only grows: barrier number
 // e (counted per block from 1) completes when it reaches e * nblocks.  Every
-// spin is bounded: after kSpinLimit polls the block raises *abort and the
+// spin is bounded: after `limit` polls the block raises *abort and the
 // barrier returns false; every later barrier returns false at once, so the
 // kernel unwinds without hanging.  count and abort must be zero at launch.
 struct GridSync {
   unsigned int* count;   // arrival counter
   unsigned int* gen;     // unused (kept for layout)
   int* abort;            // set to 1 by a block that timed out
+  long long limit;       // polls before giving up (ls_opts.wait_limit, default kSpinLimit)
 };
 
 static constexpr long long kSpinLimit = 20000000LL;  // ~ a second of polling
+
+// Host side: the poll limit of the device waits launched by the calling thread
+// (set from ls_opts.wait_limit for the duration of an entry point).
+long long spin_limit();
+struct SpinLimitScope {
+  long long prev;
+  explicit SpinLimitScope(long long limit);
+  ~SpinLimitScope();
+};
 
 __device__ __forceinline__ bool grid_sync(const GridSync& g, unsigned int nblocks, unsigned int& epoch) {
   __shared__ int ok;
@@ -119,7 +129,7 @@ __device__ __forceinline__ bool grid_sync(const GridSync& g, unsigned int nblock
     long long spins = 0;
     while ((int)(*vc - target) < 0) {
       if (*vab) { ok = 0; break; }
-      if (++spins > kSpinLimit) { atomicExch(g.abort, 1); ok = 0; break; }
+      if (++spins >= g.limit) { atomicExch(g.abort, 1); ok = 0; break; }
     }
     __threadfence();
     if (*vab) ok = 0;

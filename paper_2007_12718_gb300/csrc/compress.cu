@@ -913,7 +913,7 @@ __global__ void __launch_bounds__(1024) cpqr_reg_grid_kernel(const cx<R>* __rest
       unsigned long long v;
       long long spins = 0;
       while (((v = ld_acquire_u64(&ex[j].word)) >> 52) < (unsigned long long)nblk) {
-        if ((++spins & 4095) == 0 && (*(volatile int*)gs.abort || spins > kSpinLimit)) {
+        if (++spins >= gs.limit || ((spins & 4095) == 0 && *(volatile int*)gs.abort)) {
           atomicExch(gs.abort, 1);
           s_fail = 1;
           break;
@@ -1306,6 +1306,7 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
     gs.count = reinterpret_cast<unsigned*>(sync_buf);
     gs.gen = reinterpret_cast<unsigned*>(sync_buf) + 1;
     gs.abort = sync_buf + 2;
+    gs.limit = spin_limit();
     const cx<R>* Ac = A;
     int* ierr = sync_buf + 3;
     StepExchange* ex = reinterpret_cast<StepExchange*>(gkey);
@@ -1347,6 +1348,7 @@ int run_row_id(const cx<R>* A, int m, int p, double eps_in, int nsm, int* sync_b
     gs.count = reinterpret_cast<unsigned*>(sync_buf);
     gs.gen = reinterpret_cast<unsigned*>(sync_buf) + 1;
     gs.abort = sync_buf + 2;
+    gs.limit = spin_limit();
     const cx<R>* Ac = A;
     int* ierr = sync_buf + 3;
     LS_CUDA_TRY(cudaMemsetAsync(gkey, 0, sizeof(unsigned long long) * ((size_t)kmax + 1), st));

@@ -374,13 +374,17 @@ int noalloc_scratch(ls::z64** out) {
   return LS_OK;
 }
 
+// Device (or managed) memory of the current device, the device the scratch
+// array's address belongs to.
 bool on_device(const void* p) {
   cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+  int dev = -1;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -390,6 +394,7 @@ extern "C" long long ls_matvec_noalloc_max_elems(void) { return kNoAllocScratchE
 extern "C" int ls_matvec_noalloc(ls_handle* H, const void* xv, void* yv, int nrhs, void* stream) {
   using namespace ls;
   if (!H || !xv || !yv || nrhs < 1) return LS_EINVAL;
+  if (int rc = check_device(H)) return rc;
   const int nx = H->grid.nx, ny = H->grid.ny;
   const long long need = (long long)nrhs * ny * H->Lx;
   if (need > kNoAllocScratchElems) {
@@ -397,7 +402,7 @@ extern "C" int ls_matvec_noalloc(ls_handle* H, const void* xv, void* yv, int nrh
     return LS_EINVAL;
   }
   if (!on_device(xv) || !on_device(yv)) {
-    set_last_error_text("ls_matvec_noalloc: x and y must be device pointers");
+    set_last_error_text("ls_matvec_noalloc: x and y must be device pointers of the current device");
     return LS_EINVAL;
   }
   z64* W = nullptr;

@@ -129,7 +129,7 @@ __device__ void givens_step(z64* H, int ldh, z64* cs, z64* sn, z64* g, int j, Gm
   z64 gj = g[j];
   g[j + 1] = mk<double>(0.0, 0.0) - s * gj;
   g[j] = conjz(c) * gj;
-  st->resid = sqrt(abs2(g[j + 1])) / st->fnorm;
+  st->resid = st->fnorm > 0.0 ? sqrt(abs2(g[j + 1])) / st->fnorm : 0.0;
   st->k = j + 1;
 }
 
@@ -376,7 +376,7 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, int t
       z64* wv = ws.w;
       long long ldv = N, Nn = N;
       int jj = j, ldh = m;
-      GridSync gs{ws.sync, ws.sync + 1, reinterpret_cast<int*>(ws.sync + 2)};
+      GridSync gs{ws.sync, ws.sync + 1, reinterpret_cast<int*>(ws.sync + 2), H->spin_limit};
       unsigned e0 = orth_epoch;
       int* err = H->d_err;
       void* args[] = {&Vc, &ldv, &jj, &wv, &Nn, &ws.Hm, &ldh, &ws.partial, &ws.partial1, &ws.cs, &ws.sn, &ws.g, &ws.st,
@@ -411,6 +411,10 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, int t
       fnorm = hs->fnorm;
       if (fnorm == 0.0) {  // f = 0: sigma = 0 (the iteration ran on zero vectors)
         LS_CUDA_TRY(cudaMemsetAsync(sigma, 0, sizeof(z64) * N, st));
+        int* derr = reinterpret_cast<int*>(pin + 192);  // status of that iteration's apply
+        LS_CUDA_TRY(cudaMemcpyAsync(derr, H->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        LS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (*derr) return *derr;
         if (info) *info = inf;
         return LS_OK;
       }

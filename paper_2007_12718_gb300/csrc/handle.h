@@ -25,6 +25,7 @@ struct LevelData {
 
 struct ls_handle {
   cudaStream_t stream = nullptr;  // stream of the most recent call (ls_free orders on it)
+  int device = -1;                // the device the handle was built on (every call must have it current)
   ls_grid grid;
   double kappa = 0, tol = 0;
   ls_opts opts;
@@ -65,6 +66,8 @@ struct ls_handle {
   std::vector<int> apply_phase_end_t;  // host copy: index of the last operation of each phase
   double flops_build = 0, flops_compress = 0, bytes_apply = 0, factor_bytes = 0;
   int pivot_fallbacks = 0;      // merge levels that needed the row-pivoted inverse
+  double probe_resid_max = 0;   // largest probe residual max_i |(Z W v - v)_i| of the merge inverses
+  long long spin_limit = ls::kSpinLimit;  // polls of a bounded device wait (ls_opts.wait_limit)
   cudaStream_t inv_stream = nullptr;  // second stream of the blocked inverse (panel updates)
   cudaStream_t ext_stream = nullptr;  // third stream of the blocked inverse (panel operands)
   cudaStream_t side_stream = nullptr; // the FFT spectrum set-up beside the build
@@ -178,4 +181,15 @@ struct StreamScope {
 void set_last_error_text(const char* msg);
 int check_launch(const char* what);
 
+}  // namespace ls
+
+namespace ls {
+// LS_OK when the calling thread's current device is the handle's, else LS_EINVAL
+// with a message (the handle's memory and kernels belong to its device).
+int check_device(const ls_handle* H);
+// Device and pinned host allocations made by the library so far (ls_allocations).
+long long allocation_count();
+// Failure injection (ls_fault_inject): parse a spec; consume a pending NaN-in-b fault.
+int parse_fault(const char* spec);
+bool take_nan_b_fault();
 }  // namespace ls

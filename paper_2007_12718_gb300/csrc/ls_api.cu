@@ -15,6 +15,7 @@
 #include <thread>
 #include <condition_variable>
 #include <string>
+#include <limits>
 
 #include "handle.h"
 #include "quad.h"
@@ -120,6 +121,7 @@ namespace ls {
 void set_last_error_text(const char* msg) { set_error(msg); }
 
 static std::atomic<long long> g_launches{0};
+static std::atomic<long long> g_allocs{0};  // device and pinned host allocations (ls_allocations)
 namespace {
 bool debug_sync_enabled() {
   static const bool on = [] {
@@ -217,6 +219,7 @@ void* pinned_scratch(size_t bytes) {
     b.p = nullptr;
     b.bytes = 0;
     size_t want = std::max(bytes, (size_t)1 << 16);
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
     if (cudaMallocHost(&b.p, want) != cudaSuccess) {
       cudaGetLastError();
       b.p = nullptr;
@@ -240,11 +243,83 @@ void host_mark(const char* label) {
   fprintf(stderr, "ls host %s %.3f\n", label, ms);
 }
 
+namespace {
+thread_local long long g_spin_limit = kSpinLimit;
+}
+long long spin_limit() { return g_spin_limit; }
+SpinLimitScope::SpinLimitScope(long long limit) : prev(g_spin_limit) { g_spin_limit = limit; }
+SpinLimitScope::~SpinLimitScope() { g_spin_limit = prev; }
+
 StreamScope::StreamScope(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
 StreamScope::~StreamScope() { g_alloc_stream = prev; }
 
+long long allocation_count() { return g_allocs.load(); }
+
+// Host-side failure injection (ls_fault_inject, LS_FAULT): the countdown of
+// device allocations to the one that fails (0 = none), and a pending NaN in b.
+static std::atomic<long long> g_fail_alloc_in{0};
+static std::atomic<int> g_fail_nan_b{0};
+int parse_fault(const char* spec) {
+  if (!spec || !spec[0]) {
+    g_fail_alloc_in = 0;
+    g_fail_nan_b = 0;
+    return LS_OK;
+  }
+  if (!strncmp(spec, "alloc:", 6)) {
+    char* end = nullptr;
+    const long long nth = strtoll(spec + 6, &end, 10);
+    if (nth < 1 || !end || *end) return LS_EINVAL;
+    g_fail_alloc_in = nth;
+    return LS_OK;
+  }
+  if (!strcmp(spec, "nan_b")) {
+    g_fail_nan_b = 1;
+    return LS_OK;
+  }
+  return LS_EINVAL;
+}
+bool take_nan_b_fault() { return g_fail_nan_b.exchange(0) != 0; }
+namespace {
+struct FaultFromEnv {
+  FaultFromEnv() {
+    if (const char* v = getenv("LS_FAULT")) parse_fault(v);
+  }
+} g_fault_from_env;
+// True when this allocation is the injected failure.
+bool injected_alloc_failure() {
+  long long c = g_fail_alloc_in.load();
+  while (c > 0) {
+    if (g_fail_alloc_in.compare_exchange_weak(c, c - 1)) return c == 1;
+  }
+  return false;
+}
+}  // namespace
+
+int check_device(const ls_handle* H) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("no current CUDA device");
+    return LS_ECUDA;
+  }
+  if (dev != H->device) {
+    char buf[128];
+    snprintf(buf, sizeof(buf), "handle was built on device %d but device %d is current", H->device, dev);
+    set_error(buf);
+    return LS_EINVAL;
+  }
+  return LS_OK;
+}
+
 int dalloc(void** p, size_t bytes) {
   *p = nullptr;
+  g_allocs.fetch_add(1, std::memory_order_relaxed);
+  if (injected_alloc_failure()) {
+    char buf[96];
+    snprintf(buf, sizeof(buf), "device allocation of %zu bytes failed (injected)", bytes);
+    set_error(buf);
+    return LS_ENOMEM;
+  }
   if (bytes == 0) bytes = 16;
   cudaMemPool_t pool;
   int rc = pool_for_current_device(&pool);
@@ -290,6 +365,7 @@ void ls_default_opts(ls_opts* o) {
   o->merge_pivoting = 0;
   o->top_uncompressed = 0;
   o->id_method = LS_ID_AUTO;
+  o->wait_limit = 0;
 }
 
 const char* ls_strerror(int code) {
@@ -308,6 +384,16 @@ const char* ls_strerror(int code) {
 const char* ls_last_error(void) { return g_last_error.c_str(); }
 
 long long ls_kernel_launches(void) { return ls::g_launches.load(); }
+
+long long ls_allocations(void) { return ls::allocation_count(); }
+
+int ls_fault_inject(const char* spec) {
+  if (ls::parse_fault(spec)) {
+    set_error("unknown fault spec");
+    return LS_EINVAL;
+  }
+  return LS_OK;
+}
 
 int ls_row_id(const void* A, int m, int p, double eps, int precision, int* k, int* piv, void* U, void* stream) {
   return ls_row_id_ex(A, m, p, eps, precision, LS_ID_GREEDY, k, piv, U, stream);
@@ -376,6 +462,8 @@ int ls_cgemm_c64(int engine, int ta, int tb, int M, int N, int K, const float* a
 
 void ls_free(ls_handle* H) {
   if (!H) return;
+  int cur = -1;
+  if (H->device >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != H->device) cudaSetDevice(H->device);
   if (H->side_stream) {  // the spectrum set-up may still run after a failed build
     cudaStreamSynchronize(H->side_stream);
     cudaStreamDestroy(H->side_stream);
@@ -415,7 +503,9 @@ void ls_free(ls_handle* H) {
   if (H->apply_exec) cudaGraphExecDestroy(H->apply_exec);
   if (H->inv_stream) cudaStreamDestroy(H->inv_stream);
   if (H->ext_stream) cudaStreamDestroy(H->ext_stream);
+  const int dev = H->device;
   delete H;
+  if (dev >= 0 && cur >= 0 && cur != dev) cudaSetDevice(cur);  // the caller's current device is left as it was
 }
 
 // Compression and merges run as a two-stage pipeline: this thread compresses
@@ -518,13 +608,16 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
   const ls_opts& o = H->opts;
   if (!valid_order(o.order_matvec) || !valid_order(o.order_precond) || o.order_precond == 2 || o.leaf_side < 2 ||
       o.gmres_maxit < 1 || !(o.gmres_tol > 0) || (o.precision < LS_FP64 || o.precision > LS_TF32X3) ||
+      o.precision == LS_TF32 ||
       o.proxy_width < 0 || o.merge_pivoting < 0 || o.merge_pivoting > 1 ||
-      o.top_uncompressed < 0 || o.id_method < LS_ID_AUTO || o.id_method > LS_ID_BLOCKED) {
+      o.top_uncompressed < 0 || o.id_method < LS_ID_AUTO || o.id_method > LS_ID_BLOCKED || o.wait_limit < 0) {
     set_error("invalid ls_opts");
     return LS_EINVAL;
   }
   H->prec = o.precision;
   H->s = o.leaf_side;
+  H->spin_limit = o.wait_limit > 0 ? (long long)o.wait_limit : ls::kSpinLimit;
+  ls::SpinLimitScope spin_scope(H->spin_limit);
   // tree: cuts alternate vertical / horizontal until square leaves of side s
   {
     int w = grid->nx, h = grid->ny, L = 0;
@@ -568,6 +661,7 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
     int dev = 0;
     LS_CUDA_TRY(cudaGetDevice(&dev));
     LS_CUDA_TRY(cudaDeviceGetAttribute(&H->nsm, cudaDevAttrMultiProcessorCount, dev));
+    H->device = dev;
   }
   // corrected-quadrature weights (host, Sec. 2.2)
   const double kh = kappa * grid->h;
@@ -593,6 +687,11 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
   const long long N = (long long)grid->nx * grid->ny;
   if ((rc = ls::dalloc((void**)&H->b, sizeof(double) * N))) return rc;
   LS_CUDA_TRY(cudaMemcpyAsync(H->b, b, sizeof(double) * N, cudaMemcpyDefault, st));
+  if (ls::take_nan_b_fault()) {  // injected: as if b held a NaN
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    LS_CUDA_TRY(cudaMemcpyAsync(H->b, &nan, sizeof(double), cudaMemcpyHostToDevice, st));
+    LS_CUDA_TRY(cudaStreamSynchronize(st));
+  }
   if ((rc = ls::dalloc((void**)&H->sync_buf, 256))) return rc;
   if ((rc = ls::dalloc((void**)&H->d_err, sizeof(int) * 4))) return rc;
   LS_CUDA_TRY(cudaMemsetAsync(H->d_err, 0, sizeof(int) * 4, st));
@@ -654,6 +753,7 @@ int ls_build(const ls_grid* grid, double kappa, const double* b, double tol, con
 }
 
 static int conv_entry(ls_handle* H, const void* x, void* y, int nrhs, int mode, void* stream) {
+  if (int rc = ls::check_device(H)) return rc;
   ls::StreamScope scope((cudaStream_t)stream);
   H->stream = (cudaStream_t)stream;
   cudaStream_t st = (cudaStream_t)stream;
@@ -681,6 +781,7 @@ int ls_field(ls_handle* H, const void* sigma, void* u, int nrhs, void* stream) {
 
 int ls_apply(ls_handle* H, const void* f, void* q, int nrhs, int transpose, void* stream) {
   if (!H || !f || !q || nrhs < 1 || (transpose != 0 && transpose != 1)) return LS_EINVAL;
+  if (int rc = ls::check_device(H)) return rc;
   ls::StreamScope scope((cudaStream_t)stream);
   H->stream = (cudaStream_t)stream;
   cudaStream_t st = (cudaStream_t)stream;
@@ -699,6 +800,7 @@ int ls_apply(ls_handle* H, const void* f, void* q, int nrhs, int transpose, void
 static int solve_entry(ls_handle* H, const void* f, void* sigma, int nrhs, ls_solve_info* info, int transpose,
                        void* stream) {
   if (!H || !f || !sigma || nrhs < 1) return LS_EINVAL;
+  if (int rc = ls::check_device(H)) return rc;
   ls::host_mark("solve_entered");
   ls::StreamScope scope((cudaStream_t)stream);
   H->stream = (cudaStream_t)stream;
@@ -729,6 +831,7 @@ int ls_solve_transpose(ls_handle* H, const void* f, void* sigma, int nrhs, ls_so
 
 int ls_rhs_plane_wave(ls_handle* H, const double* thetas, void* f, int nrhs, void* stream) {
   if (!H || !thetas || !f || nrhs < 1) return LS_EINVAL;
+  if (int rc = ls::check_device(H)) return rc;
   ls::StreamScope scope((cudaStream_t)stream);
   H->stream = (cudaStream_t)stream;
   cudaStream_t st = (cudaStream_t)stream;
@@ -748,6 +851,18 @@ int ls_rhs_plane_wave(ls_handle* H, const double* thetas, void* f, int nrhs, voi
   return rc;
 }
 
+int ls_sync(ls_handle* H, void* stream) {
+  if (!H) return LS_EINVAL;
+  if (int rc = ls::check_device(H)) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* pin = static_cast<int*>(ls::pinned_scratch(sizeof(int)));
+  if (!pin) return LS_ENOMEM;
+  LS_CUDA_TRY(cudaMemcpyAsync(pin, H->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (pin[0]) set_error("a device-side wait or local inverse of this handle failed");
+  return pin[0];
+}
+
 int ls_get_build_info(const ls_handle* H, ls_build_info* info) {
   if (!H || !info) return LS_EINVAL;
   memset(info, 0, sizeof(*info));
@@ -759,6 +874,7 @@ int ls_get_build_info(const ls_handle* H, ls_build_info* info) {
   info->bytes_apply = H->bytes_apply;
   info->factor_bytes = H->factor_bytes;
   info->pivot_fallbacks = H->pivot_fallbacks;
+  info->probe_resid_max = H->probe_resid_max;
   return LS_OK;
 }
 

@@ -57,3 +57,27 @@ def _load_fresh(path):
         return ls.load_library(path)
     finally:
         ls._lib = saved
+
+
+def test_fault_injection_specs(lib):
+    """Host-side only: the injection hook parses its specs (nothing runs on a GPU)."""
+    for spec in ("alloc:1", "alloc:25", "nan_b", ""):
+        ls.ls_fault_inject(spec)
+    for spec in ("alloc:0", "alloc:-3", "alloc:x", "oom", "nan_b "):
+        with pytest.raises(ls.LSError) as e:
+            ls.ls_fault_inject(spec)
+        assert e.value.code == ls.LS_EINVAL
+    ls.ls_fault_inject("")
+    assert ls.ls_allocations() >= 0
+
+
+def test_no_gpu_build_fails_cleanly(lib):
+    """Without a CUDA device the entry points return an error code (no crash, no
+    exception across the ABI); on a GPU machine this is covered by the GPU tests."""
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(ls.LSError) as e:
+        ls.ls_build(32, 1 / 32, 20.0, np.zeros((32, 32)), 1e-4)
+    assert e.value.code in (ls.LS_ECUDA, ls.LS_ENOMEM)

@@ -209,25 +209,32 @@ def test_precond_solve_full_size_n256():
         ls.ls_free(H)
 
 
-@pytest.mark.parametrize("precision", [ls.LS_TF32X3, ls.LS_TF32])
-def test_tensor_core_build(precision):
-    """Merge GEMMs on the tensor cores: tf32x3 keeps the HBS inverse within 5 eps of
-    the dense inverse; plain tf32 is a rougher preconditioner, and GMRES (FP64,
-    FP64 matvec) still reaches the dense solution."""
+def test_tensor_core_build():
+    """Merge GEMMs on the tensor cores (tf32x3): the HBS inverse stays within 5 eps
+    of the dense inverse, and GMRES (FP64, FP64 matvec) reaches the dense solution."""
     n, kappa = 64, 40.0
     b = inputs.gaussian_family(n, 0)
-    H = build(n, kappa, b, 1e-4, precision=precision)
+    H = build(n, kappa, b, 1e-4, precision=ls.LS_TF32X3)
     A4 = nystrom.dense_operator(kappa, 1.0 / n, b, 4)
     f = inputs.random_complex((n, n), 1)
     q = host(ls.ls_apply(H, dev(f), torch.zeros(n, n, dtype=torch.complex128, device=DEV)))
     err = rel(q, nystrom.solve_dense(A4, f.ravel()).reshape(n, n))
-    assert err < (5e-4 if precision == ls.LS_TF32X3 else 5e-2), err
+    assert err < 5e-4, err
     fr = nystrom.rhs(kappa, b, n, n, 1.0 / n).reshape(n, n)
     sig = torch.zeros(n, n, dtype=torch.complex128, device=DEV)
     info = ls.ls_solve(H, dev(fr), sig)[0]
     A10 = nystrom.dense_operator(kappa, 1.0 / n, b, 10)
     assert info["converged"] and info["resid_true"] < 2e-10
     assert rel(host(sig), nystrom.solve_dense(A10, fr.ravel()).reshape(n, n)) < 1e-9
+
+
+def test_plain_tf32_preconditioner_rejected():
+    """One tf32 product per merge GEMM (~1e-3 relative error) cannot keep the HBS
+    inverse within its tolerance: ls_build refuses the mode."""
+    n = 32
+    with pytest.raises(ls.LSError) as e:
+        build(n, 20.0, inputs.gaussian_bump(n), 1e-4, precision=ls.LS_TF32)
+    assert e.value.code == ls.LS_EINVAL
 
 
 @pytest.mark.parametrize("precision", [ls.LS_FP32, ls.LS_FP64])

@@ -26,8 +26,11 @@ def test_noalloc_matvec_matches_matvec_twice():
     for seed, nrhs in ((5, 1), (6, 2)):  # two calls in a row; the second reuses the array
         x = torch.from_numpy(inputs.random_complex((nrhs, n, n), seed)).to(DEV)
         y_ref = ls.ls_matvec(H, x, torch.zeros_like(x))
-        y = ls.ls_matvec_noalloc(H, x, torch.full_like(x, 7.0))
+        y0 = torch.full_like(x, 7.0)
+        allocs = ls.ls_allocations()  # the library's own count of its device and pinned allocations
+        y = ls.ls_matvec_noalloc(H, x, y0)
         torch.cuda.synchronize()
+        assert ls.ls_allocations() == allocs
         a, r = y.cpu().numpy(), y_ref.cpu().numpy()
         for k in range(nrhs):
             assert np.linalg.norm(a[k] - r[k]) / np.linalg.norm(r[k]) < 1e-12
