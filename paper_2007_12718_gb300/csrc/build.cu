@@ -300,14 +300,14 @@ void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, cx<R> alpha, c
           Band bd = Band()) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   if (K <= 0) return;  // only reached with beta = 1 (nothing to add)
-  // tensor cores for the large products only: below ~2.5e8 complex MACs the
-  // packing passes and launches of the tcgen05 path cost more than they save
-  // (a product with a band left untouched stays on the SIMT kernels)
-  if (sizeof(R) == 4 && g_tc_engine > 0 && bd.hi <= bd.lo && M >= 256 && N >= 256 &&
-      (double)M * N * K * batch >= 2.5e8) {
+  // tensor cores for every product with at least one 128 x 128 tile and ~2^25
+  // complex MACs: measured 2x (K = 64 updates) to 4x (K in the thousands) the
+  // SIMT kernel's rate in tf32x3; smaller products stay on the SIMT kernels
+  if (sizeof(R) == 4 && g_tc_engine > 0 && M >= 128 && N >= 128 && K >= 32 &&
+      (double)M * N * K * batch >= 3.3e7) {
     tc_cgemm(st, ta, tb, M, N, K, *reinterpret_cast<const c32*>(&alpha), reinterpret_cast<const c32*>(A), lda, sA,
              reinterpret_cast<const c32*>(B), ldb, sB, *reinterpret_cast<const c32*>(&beta),
-             reinterpret_cast<c32*>(C), ldc, sC, batch, g_tc_engine == 2 ? 1 : 0, g_tc_err);
+             reinterpret_cast<c32*>(C), ldc, sC, batch, g_tc_engine == 2 ? 1 : 0, g_tc_err, bd.lo, bd.hi);
     return;
   }
   count_launch();

@@ -1043,54 +1043,19 @@ int upload_block(const std::vector<int>& rx, const std::vector<int>& ry, const s
   return check_launch("kernel block");
 }
 
-// Row ID by blocks of pivots (id_blocked.cu) followed by the same back
-// substitution as the greedy kernels' (on su when given, like them).  A is
-// overwritten.
+// Row ID by blocks of pivots (id_blocked.cu), its interpolation matrix by a
+// blocked back substitution (on su when given, like the greedy kernels' U).  A
+// is overwritten.
 template <class R>
 int run_row_id_blocked(cx<R>* A, int m, int p, double eps, cudaStream_t st, int* k_out, std::vector<int>* hp,
                        cx<R>* Uout, cudaStream_t su) {
-  int rc;
-  const int kmax = std::min(m, p);
-  const size_t need_t = 5 * 256 + sizeof(cx<R>) * ((size_t)kmax * m + (size_t)kmax * kmax) + sizeof(int) * (2 * (size_t)m + 8);
-  char* tsp = nullptr;
-  if ((rc = dalloc((void**)&tsp, need_t))) return rc;
-  char* cur = tsp;
-  auto carve = [&](size_t bytes) {
-    char* r = cur;
-    cur += (bytes + 255) & ~(size_t)255;
-    return r;
-  };
-  cx<R>* Rm = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)kmax * m));
-  cx<R>* RT = reinterpret_cast<cx<R>*>(carve(sizeof(cx<R>) * (size_t)kmax * kmax));
-  int* sel = reinterpret_cast<int*>(carve(sizeof(int) * m));
-  int* piv = reinterpret_cast<int*>(carve(sizeof(int) * m));
-  int* rank = reinterpret_cast<int*>(carve(sizeof(int) * 8));
   int tk = prof_begin(st);
   int k = 0;
-  rc = blocked_row_id<R>(A, m, p, eps, st, Rm, RT, sel, rank, piv, &k, hp);
+  int rc = blocked_row_id<R>(A, m, p, eps, st, su, Uout, &k, hp);
   // algorithmic work of the ID: ~8 m p k real flops (one projection of every
   // candidate on every pivot direction); one read of the block
   prof_end(tk, PR_CPQR, st, sizeof(cx<R>) * (double)m * p, 8.0 * m * (double)p * k);
-  if (rc) {
-    dfree(tsp);
-    return rc;
-  }
-  cudaStream_t sb = st;
-  if (su && Uout && k > 0) {
-    cudaEvent_t e;
-    LS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    LS_CUDA_TRY(cudaEventRecord(e, st));
-    LS_CUDA_TRY(cudaStreamWaitEvent(su, e, 0));
-    cudaEventDestroy(e);
-    sb = su;
-  }
-  if (Uout && k > 0 && (rc = launch_id_trsm<R>(Rm, RT, sel, rank, m, kmax, Uout, sb))) return rc;
-  if (sb != st) {
-    ls::StreamScope scope(sb);
-    dfree(tsp);
-  } else {
-    dfree(tsp);
-  }
+  if (rc) return rc;
   *k_out = k;
   return LS_OK;
 }

@@ -125,12 +125,11 @@ int row_id(const z64* A, int m, int p, double eps, int precision, int method, in
            cudaStream_t st, int* k, int* piv, z64* U);
 
 // id_blocked.cu: the row ID in blocks of pivots (A is overwritten by the trailing
-// residual).  Writes what the ID's back substitution reads -- Rm (k x m), RT
-// (k x k), sel (m), rank (1) -- and the pivots piv (device, m entries); returns
-// k and the pivots on the host.
+// residual).  Returns k and the pivots (host); with U non-null also U (m x k,
+// row-major, device), written on su when given (else on st).
 template <class R>
-int blocked_row_id(cx<R>* A, int m, int p, double eps, cudaStream_t st, cx<R>* Rm, cx<R>* RT, int* sel, int* rank,
-                   int* piv, int* k_out, std::vector<int>* hp);
+int blocked_row_id(cx<R>* A, int m, int p, double eps, cudaStream_t st, cudaStream_t su, cx<R>* U, int* k_out,
+                   std::vector<int>* hp);
 
 // build.cu (Algorithm 1) and apply (Algorithm 2)
 int hbs_build(ls_handle* H, cudaStream_t st, const LevelWait& wait_level = LevelWait());
@@ -140,7 +139,7 @@ int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, int transpose, cudaS
 // tc_gemm.cu: complex FP32 GEMM on tcgen05 tensor cores (split: 0 tf32, 1 tf32x3)
 int tc_cgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, c32 alpha, const c32* A, int lda, long long sA,
              const c32* B, int ldb, long long sB, c32 beta, c32* C, int ldc, long long sC, int batch, int split,
-             int* err);
+             int* err, int band_lo = 0, int band_hi = 0);
 int simt_cgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, c32 alpha, const c32* A, int lda, long long sA,
                const c32* B, int ldb, long long sB, c32 beta, c32* C, int ldc, long long sC, int batch);
 int simt_zgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, z64 alpha, const z64* A, int lda, long long sA,

@@ -35,9 +35,9 @@
 //      explicit residual is below the tolerance), and the next pool.
 //
 // At the end R = L^T in the column-pivoted QR's terms (A^T(:, J) = Q^T L_JJ^T):
-// R11 = L(J, :)^T, R12 = L(J^c, :)^T, and the interpolation matrix T =
-// R11^-1 R12 is formed by the same blocked back substitution as the greedy
-// kernels use (the caller launches it on Rm, RT, sel, rank written here).
+// R11 = L(J, :)^T, R12 = L(J^c, :)^T, and the interpolation matrix T^T =
+// R11^-1 R12, i.e. T = L(J^c, :) L(J, :)^-1, is formed by a blocked back
+// substitution in place in L (diagonal blocks solved per row, GEMM updates).
 //
 // Every kernel reads the block's sizes from the device state and returns at
 // once when the factorisation is done, so the host queues blocks without
@@ -735,45 +735,59 @@ __global__ void __launch_bounds__(256) proj_kernel(const cx<R>* __restrict__ A, 
   }
 }
 
-// R = L^T in the column-pivoted QR's terms, for the back substitution:
-// Rm[a][c] = L(pos(c), a) (a < k, candidate c), 32 x 32 tiles through shared memory.
+// The interpolation matrix by blocked back substitution on L: the rows of the
+// candidates that are not pivots, T = L(J^c, :) L(J, :)^-1 (L(J, :) lower
+// triangular), in place in rows [k, m) of L, 64 columns at a time from the
+// right.  trsm_diag_kernel solves the diagonal block: 128 rows per block, one
+// thread per row, the block of L and the rows' segments in shared memory (row
+// stride 65); the GEMM update of the columns on the left follows on the host.
+constexpr int kTN = 64;
 template <class R>
-__global__ void finish_rm_kernel(const cx<R>* __restrict__ Lm, int ldl, const int* __restrict__ pos, int m,
-                                 const State* __restrict__ S, cx<R>* __restrict__ Rm) {
-  __shared__ cx<R> t[32][33];
-  const int k = S->k;
-  const int c0 = blockIdx.x * 32, a0 = blockIdx.y * 32;
-  if (a0 >= k) return;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
-  for (int y = ty; y < 32; y += 8) {
-    const int c = c0 + y, a = a0 + tx;
-    t[y][tx] = (c < m && a < k) ? Lm[(long long)pos[c] * ldl + a] : czero<R>();
+__global__ void __launch_bounds__(128) trsm_diag_kernel(cx<R>* __restrict__ Lm, int ldl, int m, int k, int j0,
+                                                        int w) {
+  extern __shared__ unsigned char smraw[];
+  cx<R>* Ld = reinterpret_cast<cx<R>*>(smraw);  // kTN x (kTN + 1)
+  cx<R>* Bt = Ld + kTN * (kTN + 1);              // 128 x (kTN + 1)
+  const int tid = threadIdx.x, r0 = k + blockIdx.x * 128;
+  const int nr = min(128, m - r0);
+  for (int e = tid; e < w * w; e += 128) {
+    const int i = e / w, c = e % w;
+    Ld[i * (kTN + 1) + c] = c <= i ? Lm[(long long)(j0 + i) * ldl + j0 + c] : czero<R>();
+  }
+  for (int e = tid; e < nr * w; e += 128) {
+    const int rr = e / w, c = e % w;
+    Bt[rr * (kTN + 1) + c] = Lm[(long long)(r0 + rr) * ldl + j0 + c];
   }
   __syncthreads();
-  for (int y = ty; y < 32; y += 8) {
-    const int a = a0 + y, c = c0 + tx;
-    if (a < k && c < m) Rm[(long long)a * m + c] = t[tx][y];
+  if (tid < nr) {
+    cx<R>* b = Bt + tid * (kTN + 1);
+    for (int j = w - 1; j >= 0; --j) {
+      cx<R> x = b[j];
+      for (int i = j + 1; i < w; ++i) {
+        const cx<R> t = b[i], l = Ld[i * (kTN + 1) + j];
+        x.re -= t.re * l.re - t.im * l.im;
+        x.im -= t.re * l.im + t.im * l.re;
+      }
+      b[j] = x * inv(Ld[j * (kTN + 1) + j]);
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < nr * w; e += 128) {
+    const int rr = e / w, c = e % w;
+    Lm[(long long)(r0 + rr) * ldl + j0 + c] = Bt[rr * (kTN + 1) + c];
   }
 }
 
-// pos = perm^-1, sel, piv, rank; RT[q][r] = L(q, r) (r <= q < k, stride k).
+// U (m x k, row-major, candidate order): the pivot at position q < k has the
+// unit row e_q; the candidate at position q >= k has row T(q - k, :).
 template <class R>
-__global__ void finish_meta_kernel(const cx<R>* __restrict__ Lm, int ldl, const int* __restrict__ perm, int m,
-                                   const State* __restrict__ S, int* __restrict__ pos, int* __restrict__ sel,
-                                   int* __restrict__ piv, int* __restrict__ rank, cx<R>* __restrict__ RT) {
-  const int k = S->k;
+__global__ void scatter_u_kernel(const cx<R>* __restrict__ Lm, int ldl, const int* __restrict__ perm, int m, int k,
+                                 cx<R>* __restrict__ U) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t < m) {
-    const int q = (int)t, c = perm[q];
-    pos[c] = q;
-    sel[c] = q < k ? q : -1;
-    if (q < k) piv[q] = c;
-  }
-  if (t == 0) rank[0] = k;
-  if (t < (long long)k * k) {
-    const int q = (int)(t / k), r = (int)(t % k);
-    RT[t] = r <= q ? Lm[(long long)q * ldl + r] : czero<R>();
-  }
+  if (t >= (long long)m * k) return;
+  const int q = (int)(t / k), a = (int)(t % k);
+  const int c = perm[q];
+  U[(long long)c * k + a] = q < k ? mk<R>(a == q ? R(1) : R(0), R(0)) : Lm[(long long)q * ldl + a];
 }
 
 __global__ void iota_kernel(int* v, int m) {
@@ -784,12 +798,11 @@ __global__ void iota_kernel(int* v, int m) {
 }  // namespace bid
 
 // Blocked row ID of the candidate-major matrix A (m x p, overwritten by the
-// trailing residual).  Writes what the back substitution reads: Rm (kmax x m),
-// RT (kmax x kmax, stride k), sel (m), rank (1), and the pivots piv (m, first
-// k used) on the device; returns k and the pivots on the host.
+// trailing residual): returns k and the pivots (host); with U non-null writes U
+// (m x k, row-major, device) on su (after the factorisation on st), or on st.
 template <class R>
-int blocked_row_id(cx<R>* A, int m, int p, double eps, cudaStream_t st, cx<R>* Rm, cx<R>* RT, int* sel, int* rank,
-                   int* piv, int* k_out, std::vector<int>* hp) {
+int blocked_row_id(cx<R>* A, int m, int p, double eps, cudaStream_t st, cudaStream_t su, cx<R>* U, int* k_out,
+                   std::vector<int>* hp) {
   using namespace bid;
   int dev = 0, nsm = 148;
   LS_CUDA_TRY(cudaGetDevice(&dev));
@@ -808,7 +821,7 @@ int blocked_row_id(cx<R>* A, int m, int p, double eps, cudaStream_t st, cx<R>* R
   };
   const size_t oL = carve(sizeof(cx<R>) * (size_t)m * ldl), oQ = carve(sizeof(cx<R>) * (size_t)kB * p),
                oQc = carve(sizeof(cx<R>) * (size_t)kB * p), oLbb = carve(sizeof(cx<R>) * kB * kB),
-               oN = carve(sizeof(double) * m), oPerm = carve(sizeof(int) * m), oPos = carve(sizeof(int) * m),
+               oN = carve(sizeof(double) * m), oPerm = carve(sizeof(int) * m),
                oS = carve(sizeof(State)), oUp = carve(sizeof(double) * nU), oCp = carve(sizeof(double) * nC * kB),
                oG = carve(sizeof(cx<R>) * (size_t)ngp * kPool * kPool),
                oCs = carve(sizeof(cx<R>) * (size_t)kMaxSplit * nC * kCR * kB), oTk = carve(sizeof(unsigned) * nC),
@@ -822,7 +835,6 @@ int blocked_row_id(cx<R>* A, int m, int p, double eps, cudaStream_t st, cx<R>* R
   cx<R>* Lbb = reinterpret_cast<cx<R>*>(w + oLbb);
   double* norms = reinterpret_cast<double*>(w + oN);
   int* perm = reinterpret_cast<int*>(w + oPerm);
-  int* pos = reinterpret_cast<int*>(w + oPos);
   State* S = reinterpret_cast<State*>(w + oS);
   double* upart = reinterpret_cast<double*>(w + oUp);
   double* cpart = reinterpret_cast<double*>(w + oCp);
@@ -924,26 +936,58 @@ int blocked_row_id(cx<R>* A, int m, int p, double eps, cudaStream_t st, cx<R>* R
     set_last_error_text("blocked ID did not finish");
     return fail(LS_ECUDA);
   }
-  count_launch(2);
-  finish_meta_kernel<R><<<(unsigned)((std::max((long long)m, (long long)k * k) + 255) / 256), 256, 0, st>>>(
-      Lm, ldl, perm, m, S, pos, sel, piv, rank, RT);
-  if (k > 0)
-    finish_rm_kernel<R><<<dim3((m + 31) / 32, (k + 31) / 32), 256, 0, st>>>(Lm, ldl, pos, m, S, Rm);
-  if ((rc = check_launch("blocked ID finish"))) return fail(rc);
   int* pv = static_cast<int*>(pinned_scratch(sizeof(int) * (size_t)std::max(k, 1)));
   if (!pv) return fail(LS_ENOMEM);
-  if (k > 0) LS_CUDA_TRY(cudaMemcpyAsync(pv, piv, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
+  if (k > 0) LS_CUDA_TRY(cudaMemcpyAsync(pv, perm, sizeof(int) * k, cudaMemcpyDeviceToHost, st));
   LS_CUDA_TRY(cudaStreamSynchronize(st));
   hp->assign(std::max(k, 1), 0);
   for (int a = 0; a < k; ++a) (*hp)[a] = pv[a];
   *k_out = k;
+  if (!U || k == 0) {
+    dfree(w);
+    return LS_OK;
+  }
+  // T and U on su (beside the next ID) when given; the workspace is released there
+  cudaStream_t sb = st;
+  if (su) {
+    cudaEvent_t e;
+    LS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    LS_CUDA_TRY(cudaEventRecord(e, st));
+    LS_CUDA_TRY(cudaStreamWaitEvent(su, e, 0));
+    cudaEventDestroy(e);
+    sb = su;
+  }
+  StreamScope scope(sb);
+  if (m > k) {
+    const size_t dsm = sizeof(cx<R>) * (size_t)(kTN + 128) * (kTN + 1);
+    LS_CUDA_TRY(cudaFuncSetAttribute(trsm_diag_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+    const cx<R> mone = mk<R>(R(-1), R(0)), one = mk<R>(R(1), R(0));
+    cx<R>* T = Lm + (size_t)k * ldl;
+    for (int j0 = ((k - 1) / kTN) * kTN; j0 >= 0; j0 -= kTN) {
+      const int wd = std::min(kTN, k - j0);
+      count_launch();
+      trsm_diag_kernel<R><<<(m - k + 127) / 128, 128, dsm, sb>>>(Lm, ldl, m, k, j0, wd);
+      if (j0 > 0) {  // T(:, 0:j0) -= T(:, j0:j0+w) L(j0:j0+w, 0:j0)
+        if constexpr (sizeof(R) == 4)
+          rc = simt_cgemm(sb, false, false, m - k, j0, wd, mone, T + j0, ldl, 0, Lm + (size_t)j0 * ldl, ldl, 0, one, T,
+                          ldl, 0, 1);
+        else
+          rc = simt_zgemm(sb, false, false, m - k, j0, wd, mone, T + j0, ldl, 0, Lm + (size_t)j0 * ldl, ldl, 0, one, T,
+                          ldl, 0, 1);
+        if (rc) return rc;
+      }
+    }
+  }
+  count_launch();
+  scatter_u_kernel<R><<<(unsigned)(((long long)m * k + 255) / 256), 256, 0, sb>>>(Lm, ldl, perm, m, k, U);
+  if ((rc = check_launch("blocked ID interpolation matrix"))) return rc;
   dfree(w);
   return LS_OK;
 }
 
-template int blocked_row_id<float>(c32*, int, int, double, cudaStream_t, c32*, c32*, int*, int*, int*, int*,
+template int blocked_row_id<float>(c32*, int, int, double, cudaStream_t, cudaStream_t, c32*, int*,
                                    std::vector<int>*);
-template int blocked_row_id<double>(z64*, int, int, double, cudaStream_t, z64*, z64*, int*, int*, int*, int*,
+template int blocked_row_id<double>(z64*, int, int, double, cudaStream_t, cudaStream_t, z64*, int*,
                                     std::vector<int>*);
 
 }  // namespace ls

@@ -3,24 +3,28 @@
 // (Eqs. 26-27: S G, S G^T, Y2 Y1, the Schur-complement blocks, X diag(S) U,
 // U^T (.), and the trailing updates of the blocked inverse).
 //
-// A complex product is one real product of twice the size: with A stored
-// interleaved (re, im), row i of A is the real row (a_r0, a_i0, a_r1, ...)
-// of length 2K, and every complex entry b = (br, bi) of B becomes the 2x2 real
-// block [[br, bi], [-bi, br]] of a 2K x 2N real matrix B'.  Then A' B' is C
-// interleaved.  In tf32x3 mode each operand is split into a tf32 head and a
-// tf32 tail (x = hi + lo) and the K loop runs over [A_hi A_hi A_lo] x
-// [B_hi; B_lo; B_hi] (~FP32 accuracy; the lo*lo term is dropped).
+// C = alpha op(A) op(B) + beta C with complex operands is computed from real
+// products of the real and imaginary planes (the 4M form):
+//   re(C) = Ar Br - Ai Bi,   im(C) = Ar Bi + Ai Br,
+// accumulated in three FP32 accumulators in tensor memory (Ar Br, Ai Bi and
+// the imaginary part), combined in the epilogue.  In tf32x3 mode every plane
+// is split into a tf32 head and a tf32 tail, x = hi + lo (round to nearest),
+// and each real product P Q is P_hi Q_hi + P_hi Q_lo + P_lo Q_hi (the lo lo
+// term, ~2^-22 of |P||Q|, is dropped): twelve MMAs per k step instead of four.
 //
-// Data path: two packing kernels write op(A) and op(B) as "stage images",
-// each stage (128 rows x 64 real k, 32 KB) already in the K-major no-swizzle
-// shared-memory layout of 8-row x 16-byte core matrices.  The GEMM kernel
-// (one 128 x 128-real tile per block) moves each stage with two 32 KB
-// cp.async.bulk copies into a ring of three 64 KB buffers (full/empty
-// mbarriers), one thread issues eight m128n128k8 MMAs per stage and commits
-// them to the buffer's "empty" barrier, and the 128 x 128 FP32 accumulator is
-// read back from tensor memory with tcgen05.ld.  Every mbarrier wait is
-// bounded: on timeout the block sets *err, issues nothing more, frees its
-// tensor memory and returns.
+// One CTA computes a 128 x 128 complex tile.  Eight converter warps read the
+// FP32 operands straight from global memory (per thread one row of op(A) and
+// one column of op(B), half of a stage's 16 complex k, coalesced for either
+// storage order; the next stage's values are loaded while the current ones are
+// converted), split them and store the planes in the K-major no-swizzle layout
+// of 8-row x 16-byte core matrices (a fence makes them visible to the tensor
+// cores), then arrive on the stage's "full" mbarrier; one thread of the ninth
+// warp issues the MMAs of a stage and commits them to its "empty" mbarrier.
+// Three stages of 64 KB.  The converter warps then read the accumulators back
+// with tcgen05.ld, combine them into a tile in shared memory and write C
+// coalesced.  Every mbarrier wait is bounded: on timeout the
+// block records LS_ETIMEOUT in *err, issues nothing more, frees its tensor
+// memory and returns.
 #include <string.h>
 
 #include <algorithm>
@@ -30,21 +34,26 @@
 namespace ls {
 namespace {
 
-constexpr int TC_BM = 128;                      // rows per tile
-constexpr int TC_BN = 128;                      // real columns per tile (64 complex)
-constexpr int TC_BK = 64;                       // real k per stage (32 complex)
-constexpr int TC_IMG = TC_BM * TC_BK;           // floats per stage image (32 KB)
-constexpr int TC_NBUF = 3;                      // ring of stage buffers
-constexpr int TC_THREADS = 128;
+constexpr int TC_BM = 128;                     // rows of C per tile
+constexpr int TC_BN = 128;                     // complex columns of C per tile
+constexpr int TC_BK = 16;                      // complex k per stage
+constexpr int TC_PLANE = TC_BM * TC_BK;        // floats per real plane (8 KB)
+constexpr int TC_STAGE = 8 * TC_PLANE;         // Ar hi/lo, Ai hi/lo, Br hi/lo, Bi hi/lo: 64 KB
+constexpr int TC_NS = 3;                       // stages in flight
+constexpr int TC_CONV = 256;                   // converter / epilogue threads (warps 0-7)
+constexpr int TC_KH = TC_BK / 2;               // complex k per converter thread and stage
+constexpr int TC_THREADS = TC_CONV + 32;       // + the MMA warp (warp 8)
+constexpr uint32_t TC_TMEM_COLS = 512;         // three 128-column accumulators
 constexpr long long kMbarSpin = 1LL << 26;
+
+enum { P_AR_HI = 0, P_AR_LO, P_AI_HI, P_AI_LO, P_BR_HI, P_BR_LO, P_BI_HI, P_BI_LO };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// K-major no-swizzle layout: core matrix = 8 rows x 16 bytes; LBO = 128 B
-// between K-adjacent core matrices, SBO = 2048 B between M/N-adjacent ones.
-__device__ __forceinline__ int kmaj(int row, int k) {
-  return (row >> 3) * (TC_BK * 8) + (k >> 2) * 32 + (row & 7) * 4 + (k & 3);
-}
+// K-major no-swizzle layout of one 128 x 16 plane: core matrix = 8 rows x 16
+// bytes (4 tf32); LBO = 128 B between K-adjacent core matrices, SBO = 512 B
+// between row-adjacent groups of eight rows.
+__device__ __forceinline__ int kmaj(int row, int k) { return (row >> 3) * (TC_BK * 8) + (k >> 2) * 32 + (row & 7) * 4 + (k & 3); }
 
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
@@ -66,76 +75,6 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
-__device__ __forceinline__ void split2(float x, bool lo, float& out) {
-  float h = to_tf32(x);
-  out = lo ? to_tf32(x - h) : h;
-}
-
-// imgA[part][b][mt][ks]: op(A)(row, kc) -> real (row, 2kc + {0: re, 1: im}).
-template <bool TA>
-__global__ void pack_a_kernel(const c32* __restrict__ A, int lda, long long sA, int M, int K, int MT, int KS,
-                              int nparts, float* __restrict__ img, long long s_img_b) {
-  const int b = blockIdx.y;
-  const long long per_part = s_img_b * gridDim.y;
-  const long long total = (long long)MT * TC_BM * KS * (TC_BK / 2);
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    // consecutive threads along k (row-major A) or along rows (transposed A)
-    int row, kc;
-    if (TA) {
-      row = (int)(t % (MT * TC_BM));
-      kc = (int)(t / (MT * TC_BM));
-    } else {
-      kc = (int)(t % (KS * (TC_BK / 2)));
-      row = (int)(t / (KS * (TC_BK / 2)));
-    }
-    c32 v = mk<float>(0.f, 0.f);
-    if (row < M && kc < K) v = TA ? A[b * sA + (long long)kc * lda + row] : A[b * sA + (long long)row * lda + kc];
-    const int mt = row / TC_BM, r = row % TC_BM, ks = kc / (TC_BK / 2), k2 = 2 * (kc % (TC_BK / 2));
-    const long long base = b * s_img_b + ((long long)mt * KS + ks) * TC_IMG;
-    for (int part = 0; part < nparts; ++part) {
-      float re, im;
-      split2(v.re, part == 1, re);
-      split2(v.im, part == 1, im);
-      img[part * per_part + base + kmaj(r, k2)] = re;
-      img[part * per_part + base + kmaj(r, k2 + 1)] = im;
-    }
-  }
-}
-
-// imgB[part][b][nt][ks]: op(B)(q, j) -> 2x2 real block of B'^T rows 2j, 2j+1, k 2q, 2q+1.
-template <bool TB>
-__global__ void pack_b_kernel(const c32* __restrict__ B, int ldb, long long sB, int K, int N, int NT, int KS,
-                              int nparts, float* __restrict__ img, long long s_img_b) {
-  const int b = blockIdx.y;
-  const long long per_part = s_img_b * gridDim.y;
-  const int NC = NT * (TC_BN / 2), KC = KS * (TC_BK / 2);
-  const long long total = (long long)NC * KC;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
-    int j, q;
-    if (TB) {  // B stored N x K: consecutive threads along K
-      q = (int)(t % KC);
-      j = (int)(t / KC);
-    } else {   // B stored K x N: consecutive threads along N
-      j = (int)(t % NC);
-      q = (int)(t / NC);
-    }
-    c32 v = mk<float>(0.f, 0.f);
-    if (j < N && q < K) v = TB ? B[b * sB + (long long)j * ldb + q] : B[b * sB + (long long)q * ldb + j];
-    const int nt = j / (TC_BN / 2), jl = j % (TC_BN / 2), ks = q / (TC_BK / 2), ql = q % (TC_BK / 2);
-    const long long base = b * s_img_b + ((long long)nt * KS + ks) * TC_IMG;
-    for (int part = 0; part < nparts; ++part) {
-      float br, bi;
-      split2(v.re, part == 1, br);
-      split2(v.im, part == 1, bi);
-      float* o = img + part * per_part + base;
-      o[kmaj(2 * jl, 2 * ql)] = br;
-      o[kmaj(2 * jl, 2 * ql + 1)] = -bi;
-      o[kmaj(2 * jl + 1, 2 * ql)] = bi;
-      o[kmaj(2 * jl + 1, 2 * ql + 1)] = br;
-    }
-  }
-}
-
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   uint32_t done = 0;
   long long spins = 0;
@@ -150,31 +89,72 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return true;
 }
 
-// C[b] (M x N complex) = alpha A'B' + beta C[b], from the stage images.
-__global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int KS, int nparts, const float* __restrict__ imgA,
-                                                             long long sIA, long long partA, const float* __restrict__ imgB,
-                                                             long long sIB, long long partB, int MT, int NT, c32 alpha,
-                                                             c32 beta, c32* __restrict__ C, int ldc, long long sC,
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+}
+
+// Store the 8 complex values k = kb .. kb + 7 of one row as the four planes
+// (re hi, re lo, im hi, im lo) starting at plane p0; without `split` only the
+// heads are stored.
+__device__ __forceinline__ void store_row(float* stage, int p0, int row, int kb, const c32 (&v)[TC_KH], bool split) {
+#pragma unroll
+  for (int q = 0; q < TC_KH / 4; ++q) {
+    float4 rh, rl, ih, il;
+    float* prh = &rh.x;
+    float* prl = &rl.x;
+    float* pih = &ih.x;
+    float* pil = &il.x;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const c32 x = v[4 * q + e];
+      const float hr = to_tf32(x.re), hi = to_tf32(x.im);
+      prh[e] = hr;
+      pih[e] = hi;
+      prl[e] = split ? to_tf32(x.re - hr) : 0.f;
+      pil[e] = split ? to_tf32(x.im - hi) : 0.f;
+    }
+    const int o = kmaj(row, kb + 4 * q);
+    *reinterpret_cast<float4*>(stage + (p0 + 0) * TC_PLANE + o) = rh;
+    *reinterpret_cast<float4*>(stage + (p0 + 2) * TC_PLANE + o) = ih;
+    if (split) {
+      *reinterpret_cast<float4*>(stage + (p0 + 1) * TC_PLANE + o) = rl;
+      *reinterpret_cast<float4*>(stage + (p0 + 3) * TC_PLANE + o) = il;
+    }
+  }
+}
+
+// C[b] (M x N complex) = alpha op(A[b]) op(B[b]) + beta C[b]; row-major
+// complex64 operands, op = transpose (no conjugate) when TA / TB.
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K, c32 alpha, const c32* __restrict__ A,
+                                                             int lda, long long sA, const c32* __restrict__ B, int ldb,
+                                                             long long sB, c32 beta, c32* __restrict__ C, int ldc,
+                                                             long long sC, int split, int band_lo, int band_hi,
                                                              int* err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
-  float* buf = reinterpret_cast<float*>(smraw);  // TC_NBUF x (A image | B image)
-  __shared__ __align__(8) uint64_t full_bar[TC_NBUF], empty_bar[TC_NBUF], done_bar;
+  float* stages = reinterpret_cast<float*>(smraw);  // TC_NS x TC_STAGE floats
+  __shared__ __align__(8) uint64_t full_bar[TC_NS], empty_bar[TC_NS], done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nt = blockIdx.x, mt = blockIdx.y, bz = blockIdx.z;
-  const float* gA = imgA + bz * sIA + (long long)mt * KS * TC_IMG;
-  const float* gB = imgB + bz * sIB + (long long)nt * KS * TC_IMG;
+  const int n0 = blockIdx.x * TC_BN, m0 = blockIdx.y * TC_BM, bz = blockIdx.z;
+  A += bz * sA;
+  B += bz * sB;
   C += bz * sC;
+  const int S = (K + TC_BK - 1) / TC_BK;
+  const bool sp = split != 0;
 
-  if (warp == 0) {
+  if (warp == 8) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"(TC_BN));
+                 "r"(TC_TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int i = 0; i < TC_NBUF; ++i) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full_bar[i])), "r"(1));
+    for (int i = 0; i < TC_NS; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full_bar[i])), "r"(TC_CONV));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty_bar[i])), "r"(1));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&done_bar)), "r"(1));
@@ -185,68 +165,81 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
-  const int S = KS * nparts;
 
-  if (tid == 0) {  // producer: stage s into buffer s % NBUF
+  if (warp < 8) {  // converters: row r of op(A) and of op(B)^T, k-half kh of every stage
+    const int r = tid & (TC_BM - 1), kh = (tid >> 7) * TC_KH;
+    const int ra = m0 + r, cb = n0 + r;
+    c32 va[TC_KH], vb[TC_KH];  // the operands of the next stage, loaded ahead
+    auto load = [&](int s) {
+      const int k0 = s * TC_BK + kh;
+#pragma unroll
+      for (int j = 0; j < TC_KH; ++j) {
+        const int k = k0 + j;
+        va[j] = (ra < M && k < K) ? (TA ? A[(long long)k * lda + ra] : A[(long long)ra * lda + k]) : mk<float>(0.f, 0.f);
+        vb[j] = (cb < N && k < K) ? (TB ? B[(long long)cb * ldb + k] : B[(long long)k * ldb + cb]) : mk<float>(0.f, 0.f);
+      }
+    };
+    load(0);
     for (int s = 0; s < S; ++s) {
-      const int bi = s % TC_NBUF;
-      if (s >= TC_NBUF && !mbar_wait(smem_u32(&empty_bar[bi]), ((s / TC_NBUF) - 1) & 1)) {
+      const int bi = s % TC_NS;
+      if (s >= TC_NS && !mbar_wait(smem_u32(&empty_bar[bi]), ((s / TC_NS) - 1) & 1)) {
         atomicExch(&s_fail, 1);
         break;
       }
       if (*(volatile int*)&s_fail) break;
-      const int part = s / KS, ks = s % KS;
-      const int pa = (nparts == 3 && part == 2) ? 1 : 0;  // A: hi, hi, lo
-      const int pb = (nparts == 3 && part == 1) ? 1 : 0;  // B: hi, lo, hi
-      const float* srcA = gA + pa * partA + (long long)ks * TC_IMG;
-      const float* srcB = gB + pb * partB + (long long)ks * TC_IMG;
-      float* dA = buf + (long long)bi * 2 * TC_IMG;
-      float* dB = dA + TC_IMG;
-      const uint32_t fb = smem_u32(&full_bar[bi]);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(2 * TC_IMG * 4)
-                   : "memory");
-      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                       smem_u32(dA)),
-                   "l"(srcA), "r"(TC_IMG * 4), "r"(fb)
-                   : "memory");
-      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                       smem_u32(dB)),
-                   "l"(srcB), "r"(TC_IMG * 4), "r"(fb)
-                   : "memory");
+      float* stage = stages + (size_t)bi * TC_STAGE;
+      store_row(stage, P_AR_HI, r, kh, va, sp);
+      store_row(stage, P_BR_HI, r, kh, vb, sp);
+      // generic-proxy stores -> visible to the tensor cores (async proxy)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[bi])) : "memory");
+      if (s + 1 < S) load(s + 1);
     }
-  } else if (tid == 32) {  // MMA issuer
+  } else if (lane == 0) {  // MMA issuer
     const uint32_t idesc = make_idesc_tf32(TC_BM, TC_BN);
+    const uint32_t acc_rr = tmem, acc_ii = tmem + 128, acc_im = tmem + 256;
     bool ok = true;
     for (int s = 0; s < S; ++s) {
-      const int bi = s % TC_NBUF;
-      if (!mbar_wait(smem_u32(&full_bar[bi]), (s / TC_NBUF) & 1) || *(volatile int*)&s_fail) {
+      const int bi = s % TC_NS;
+      if (!mbar_wait(smem_u32(&full_bar[bi]), (s / TC_NS) & 1) || *(volatile int*)&s_fail) {
         atomicExch(&s_fail, 1);
         ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a0 = smem_u32(buf + (long long)bi * 2 * TC_IMG), b0 = a0 + TC_IMG * 4;
+      const uint32_t base = smem_u32(stages + (size_t)bi * TC_STAGE);
+      auto pd = [&](int plane, int kk) { return make_desc(base + plane * TC_PLANE * 4 + kk * 256, 128, TC_BK * 8 * 4); };
 #pragma unroll
       for (int kk = 0; kk < TC_BK / 8; ++kk) {
-        const uint64_t ad = make_desc(a0 + kk * 256, 128, TC_BK * 8 * 4);
-        const uint64_t bd = make_desc(b0 + kk * 256, 128, TC_BK * 8 * 4);
-        const uint32_t accum = (s > 0 || kk > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+        const uint32_t first = (s == 0 && kk == 0) ? 0u : 1u;
+        // Ar Br
+        mma_tf32(acc_rr, pd(P_AR_HI, kk), pd(P_BR_HI, kk), idesc, first);
+        // Ai Bi
+        mma_tf32(acc_ii, pd(P_AI_HI, kk), pd(P_BI_HI, kk), idesc, first);
+        // Ar Bi + Ai Br
+        mma_tf32(acc_im, pd(P_AR_HI, kk), pd(P_BI_HI, kk), idesc, first);
+        mma_tf32(acc_im, pd(P_AI_HI, kk), pd(P_BR_HI, kk), idesc, 1u);
+        if (sp) {
+          mma_tf32(acc_rr, pd(P_AR_HI, kk), pd(P_BR_LO, kk), idesc, 1u);
+          mma_tf32(acc_rr, pd(P_AR_LO, kk), pd(P_BR_HI, kk), idesc, 1u);
+          mma_tf32(acc_ii, pd(P_AI_HI, kk), pd(P_BI_LO, kk), idesc, 1u);
+          mma_tf32(acc_ii, pd(P_AI_LO, kk), pd(P_BI_HI, kk), idesc, 1u);
+          mma_tf32(acc_im, pd(P_AR_HI, kk), pd(P_BI_LO, kk), idesc, 1u);
+          mma_tf32(acc_im, pd(P_AR_LO, kk), pd(P_BI_HI, kk), idesc, 1u);
+          mma_tf32(acc_im, pd(P_AI_HI, kk), pd(P_BR_LO, kk), idesc, 1u);
+          mma_tf32(acc_im, pd(P_AI_LO, kk), pd(P_BR_HI, kk), idesc, 1u);
+        }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(&empty_bar[bi])));
     }
-    if (ok) {
+    if (ok)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(&done_bar)));
-    }
   }
-  // everyone: wait for the last MMA (or a failure)
+  // the converter warps wait for the last MMA (or a failure), then the epilogue
   bool ok = true;
-  if (S > 0) {
+  if (warp < 8 && S > 0) {
     uint32_t done = 0;
     long long spins = 0;
     while (!done) {
@@ -262,88 +255,96 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K
       }
     }
   }
+  if (!ok) atomicExch(&s_fail, 1);  // one decision for the whole block after the barrier
   asm volatile("tcgen05.fence::after_thread_sync;");
   __syncthreads();
-  if (!ok || s_fail) {
-    if (tid == 0) atomicExch(err, LS_ETIMEOUT);
-  } else if (S > 0) {
-    const int row = mt * TC_BM + warp * 32 + lane;
-    const int n0 = nt * (TC_BN / 2);
-    const bool zb = (beta.re == 0.f && beta.im == 0.f);
+  if (warp < 8) {
+    // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. (rows of the tile),
+    // columns 64 (w / 4) .. of the three accumulators, and stores the combined
+    // values in the stage buffers (free once the last MMA is done), rows padded
+    // to 129 entries; then the 256 threads write C row by row, coalesced.
+    if (*(volatile int*)&s_fail) {
+      if (tid == 0) atomicExch(err, LS_ETIMEOUT);
+    } else if (S > 0) {
+      c32* tile = reinterpret_cast<c32*>(stages);  // 128 x 129 complex, 132 KB
+      constexpr int TLD = TC_BN + 1;
+      const int q = warp & 3, ch = warp >> 2;
+      const int rl = q * 32 + lane;
 #pragma unroll 1
-    for (int c0 = 0; c0 < TC_BN; c0 += 16) {
-      uint32_t v[16];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (row < M) {
+      for (int c0 = ch * (TC_BN / 2); c0 < (ch + 1) * (TC_BN / 2); c0 += 16) {
+        uint32_t vr[16], vi[16], vm[16];
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]), "=r"(vr[7]),
+              "=r"(vr[8]), "=r"(vr[9]), "=r"(vr[10]), "=r"(vr[11]), "=r"(vr[12]), "=r"(vr[13]), "=r"(vr[14]),
+              "=r"(vr[15])
+            : "r"(taddr));
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]), "=r"(vi[7]),
+              "=r"(vi[8]), "=r"(vi[9]), "=r"(vi[10]), "=r"(vi[11]), "=r"(vi[12]), "=r"(vi[13]), "=r"(vi[14]),
+              "=r"(vi[15])
+            : "r"(taddr + 128u));
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(vm[0]), "=r"(vm[1]), "=r"(vm[2]), "=r"(vm[3]), "=r"(vm[4]), "=r"(vm[5]), "=r"(vm[6]), "=r"(vm[7]),
+              "=r"(vm[8]), "=r"(vm[9]), "=r"(vm[10]), "=r"(vm[11]), "=r"(vm[12]), "=r"(vm[13]), "=r"(vm[14]),
+              "=r"(vm[15])
+            : "r"(taddr + 256u));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int col = n0 + c0 / 2 + e;
-          if (col < N) {
-            c32 acc = mk<float>(__uint_as_float(v[2 * e]), __uint_as_float(v[2 * e + 1]));
-            c32 out = alpha * acc;
-            if (!zb) out = out + beta * C[(long long)row * ldc + col];
-            C[(long long)row * ldc + col] = out;
-          }
+        for (int e = 0; e < 16; ++e)
+          tile[rl * TLD + c0 + e] = mk<float>(__uint_as_float(vr[e]) - __uint_as_float(vi[e]), __uint_as_float(vm[e]));
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(TC_CONV) : "memory");  // the converter warps only
+      const bool zb = (beta.re == 0.f && beta.im == 0.f);
+      for (int e = tid; e < TC_BM * TC_BN; e += TC_CONV) {
+        const int r = e / TC_BN, c = e % TC_BN, row = m0 + r, col = n0 + c;
+        const bool band = (row >= band_lo && row < band_hi) || (col >= band_lo && col < band_hi);
+        if (row < M && col < N && !band) {
+          c32 out = alpha * tile[r * TLD + c];
+          if (!zb) out = out + beta * C[(long long)row * ldc + col];
+          C[(long long)row * ldc + col] = out;
         }
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN));
+  if (warp == 8) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
 }
 
 }  // namespace
 
-// Host entry: same contract as the SIMT gemm (batched, row-major, op N/T).
-// Operands shared by the whole batch (stride 0) are packed once.
+// Host entry: same contract as the SIMT gemm (batched, row-major, op N/T, a
+// stride of 0 shares an operand across the batch).  split: 0 tf32, 1 tf32x3.
+// Entries in rows or columns [band_lo, band_hi) of C are left untouched.
 int tc_cgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, c32 alpha, const c32* A, int lda, long long sA,
              const c32* B, int ldb, long long sB, c32 beta, c32* C, int ldc, long long sC, int batch, int split,
-             int* err) {
+             int* err, int band_lo, int band_hi) {
   if (M <= 0 || N <= 0 || batch <= 0 || K <= 0) return LS_OK;
-  const int MT = (M + TC_BM - 1) / TC_BM, NT = (N + TC_BN / 2 - 1) / (TC_BN / 2);
-  const int KS = (2 * K + TC_BK - 1) / TC_BK;
-  const int nparts = split ? 3 : 1, nimg = split ? 2 : 1;
-  const int batchA = sA ? batch : 1, batchB = sB ? batch : 1;
-  const long long sIA = (long long)MT * KS * TC_IMG, sIB = (long long)NT * KS * TC_IMG;
-  float* img = nullptr;
-  int rc = dalloc((void**)&img, sizeof(float) * (size_t)nimg * ((size_t)sIA * batchA + (size_t)sIB * batchB));
-  if (rc) return rc;
-  float* imgA = img;
-  float* imgB = img + (size_t)nimg * sIA * batchA;
-  {
-    long long tot = (long long)MT * TC_BM * KS * (TC_BK / 2);
-    dim3 g((unsigned)std::min<long long>(4096, (tot + 255) / 256), batchA);
-    count_launch();
-    if (ta)
-      pack_a_kernel<true><<<g, 256, 0, st>>>(A, lda, sA, M, K, MT, KS, nimg, imgA, sIA);
-    else
-      pack_a_kernel<false><<<g, 256, 0, st>>>(A, lda, sA, M, K, MT, KS, nimg, imgA, sIA);
-  }
-  {
-    long long tot = (long long)NT * (TC_BN / 2) * KS * (TC_BK / 2);
-    dim3 g((unsigned)std::min<long long>(4096, (tot + 255) / 256), batchB);
-    count_launch();
-    if (tb)
-      pack_b_kernel<true><<<g, 256, 0, st>>>(B, ldb, sB, K, N, NT, KS, nimg, imgB, sIB);
-    else
-      pack_b_kernel<false><<<g, 256, 0, st>>>(B, ldb, sB, K, N, NT, KS, nimg, imgB, sIB);
-  }
-  const size_t smem = sizeof(float) * (size_t)TC_NBUF * 2 * TC_IMG;
-  LS_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid(NT, MT, batch);
+  const size_t smem = sizeof(float) * (size_t)TC_NS * TC_STAGE;
+  const void* fn = !ta && !tb ? (const void*)tc_gemm_kernel<false, false>
+                 : ta && !tb  ? (const void*)tc_gemm_kernel<true, false>
+                 : !ta && tb  ? (const void*)tc_gemm_kernel<false, true>
+                              : (const void*)tc_gemm_kernel<true, true>;
+  LS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, batch);
   count_launch();
-  tc_gemm_kernel<<<grid, TC_THREADS, smem, st>>>(M, N, KS, nparts, imgA, sA ? sIA : 0, sIA * batchA, imgB,
-                                                  sB ? sIB : 0, sIB * batchB, MT, NT, alpha, beta, C, ldc, sC, err);
-  rc = check_launch("tc_cgemm");
-  dfree(img);
-  return rc;
+  if (!ta && !tb)
+    tc_gemm_kernel<false, false><<<grid, TC_THREADS, smem, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
+                                                                sC, split, band_lo, band_hi, err);
+  else if (ta && !tb)
+    tc_gemm_kernel<true, false><<<grid, TC_THREADS, smem, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
+                                                               sC, split, band_lo, band_hi, err);
+  else if (!ta && tb)
+    tc_gemm_kernel<false, true><<<grid, TC_THREADS, smem, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
+                                                               sC, split, band_lo, band_hi, err);
+  else
+    tc_gemm_kernel<true, true><<<grid, TC_THREADS, smem, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
+                                                              sC, split, band_lo, band_hi, err);
+  return check_launch("tc_cgemm");
 }
 
 }  // namespace ls
