@@ -92,7 +92,7 @@ typedef struct {
  *                 the candidates left out; the other candidates are then updated
  *                 by GEMM-shaped kernels.  The rank is decided by the same
  *                 Frobenius-norm rule, on the explicit residual.
- *  LS_ID_AUTO   : blocked for 256 candidates or more (and wherever a candidate's
+ *  LS_ID_AUTO   : blocked above 1024 candidates (and wherever a candidate's
  *                 vector is too long for the greedy kernels), greedy below. */
 enum { LS_ID_AUTO = 0, LS_ID_GREEDY = 1, LS_ID_BLOCKED = 2 };
 

@@ -1063,7 +1063,7 @@ int run_row_id_blocked(cx<R>* A, int m, int p, double eps, cudaStream_t st, int*
 // Candidates from which the blocked ID takes over from the greedy kernels
 // (ID_AUTO), and above which only the blocked ID applies (the greedy kernels
 // keep a candidate's residual in registers or one block's shared memory).
-constexpr int kBlockedMinRows = 256;
+constexpr int kBlockedMinRows = 1024;
 
 // Row ID of the device matrix A (m candidates x p, candidate-major) by the
 // column-pivoted QR kernels above: one thread-block cluster when the
