@@ -381,6 +381,8 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    if args.precision == "fp64":
+        raise SystemExit("--precision fp64 is for --sweep; the benchmark measures the FP64 path beside the mixed one")
     PREC = {"fp32": ls.LS_FP32, "tf32x3": ls.LS_TF32X3}[args.precision]
     tensor = args.precision == "tf32x3"
     pk = measured_peaks(ls)
@@ -471,6 +473,73 @@ def run_ours(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# The paper's cavity table (Sec. 6.3, preconditioned solver, 10 points per
+# wavelength): N, kappa, T_skel + T_build, T_gmres (s, 36-core workstation), iterations.
+PAPER_CAVITY = {6400: (0.47, 0.20, 4), 25600: (1.64, 0.62, 5), 102400: (6.62, 2.49, 6), 409600: (34.97, 9.78, 6),
+                1638400: (190.38, 56.13, 9), 6553600: (829.48, 330.91, 13), 26214400: (5126.25, 2698.53, 22)}
+
+
+def run_sweep(args):
+    """The cavity sweep of Sec. 6.3 on one GPU: for n = 80 2^j (kappa = 2 pi n / 10,
+    100-point leaves), one warm-up and `--steps` timed build + solve steps of the mixed
+    path; build and solve timed separately with CUDA events.  One JSON line."""
+    import torch
+
+    import paper_2007_12718_gb300 as ls
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    PREC = {"fp32": ls.LS_FP32, "tf32x3": ls.LS_TF32X3, "fp64": ls.LS_FP64}[args.precision]
+    rows = []
+    for j in range(args.sweep_first, args.sweep_levels):
+        name = f"cavity_n{80 << j}"
+        n, kappa, b, w = workload(name)
+        h = 1.0 / n
+        bd = torch.from_numpy(b).to(dev)
+        f = torch.zeros(n, n, dtype=torch.complex128, device=dev)
+        sig = torch.zeros_like(f)
+        kw = dict(leaf_side=w["leaf"], order_precond=w["order_precond"], order_matvec=w["order_matvec"],
+                  precision=PREC, top_uncompressed=args.top_uncompressed, gmres_maxit=args.sweep_maxit)
+        tb = ts = 0.0
+        info = bi = None
+        for it in range(1 + args.steps):
+            torch.cuda.synchronize()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            H = ls.ls_build(n, h, kappa, bd, w["eps"], **kw)
+            e[1].record(stream)
+            if it == 0:
+                ls.ls_rhs_plane_wave(H, [0.0], f)
+                torch.cuda.synchronize()
+                e[1].record(stream)
+            info = ls.ls_solve(H, f, sig)[0]
+            e[2].record(stream)
+            bi = H.info()
+            ls.ls_free(H)
+            torch.cuda.synchronize()
+            if it > 0:
+                tb += e[0].elapsed_time(e[1]) / 1e3
+                ts += e[1].elapsed_time(e[2]) / 1e3
+        tb /= args.steps
+        ts /= args.steps
+        N = n * n
+        paper = PAPER_CAVITY.get(N)
+        rows.append({"workload": name, "N": N, "kappa": kappa, "t_build_s": tb, "t_solve_s": ts,
+                     "mdofs": N / (tb + ts) / 1e6, "iterations": info["iterations"],
+                     "resid_true": info["resid_true"], "ranks_top": bi["ranks"][1:4],
+                     "factor_GB": bi["factor_bytes"] / 1e9, "pivot_fallbacks": bi["pivot_fallbacks"],
+                     "probe_resid_max": bi["probe_resid_max"],
+                     "paper": None if paper is None else {"t_build_s": paper[0], "t_gmres_s": paper[1],
+                                                          "iterations": paper[2]}})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        del bd, f, sig
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": METRIC, "sweep": "cavity, 10 points per wavelength (Sec. 6.3)", "unit": "Mdof/s",
+                      "steps": args.steps, "warmup": 1, "precision": args.precision,
+                      "top_levels_uncompressed": args.top_uncompressed, "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -489,13 +558,23 @@ def main():
     ap.add_argument("--top-uncompressed", type=int, default=1,
                     help="tree levels kept uncompressed at the top (U = I, the ID of full rank); measured faster at "
                          "2048^2 (1.20 s against 1.31 s per step) and at 256^2; 0 compresses every level")
-    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3"],
-                    help="engine of the mixed path's merge GEMMs (FP32 storage in all three)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="run the cavity sweep of Sec. 6.3 (10 points per wavelength) instead of the benchmark")
+    ap.add_argument("--sweep-levels", type=int, default=6, help="sizes of the sweep: n = 80, 160, ..., 80 2^(levels-1)")
+    ap.add_argument("--sweep-first", type=int, default=0, help="first size of the sweep: n = 80 2^first")
+    ap.add_argument("--sweep-maxit", type=int, default=100, help="GMRES iteration limit in the sweep (memory: "
+                    "(maxit + 1) N complex128 twice)")
+    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "fp64"],
+                    help="engine of the mixed path's merge GEMMs (FP32 storage in both); fp64 (the plain "
+                         "FP64 path) only with --sweep")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     if world > 1:
         import torch

@@ -1547,26 +1547,23 @@ int invert_batch(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int P, vo
     inverse_smem_kernel<R><<<P, 512, smem_small, st>>>(X, n, lda, sX, H->d_err);
     return check_launch("inverse_smem");
   }
-  int nb = 32;
-  while (nb > 4 && sizeof(cx<R>) * (size_t)n * (nb + 1) > 200 * 1024) nb >>= 1;
-  const size_t smem_panel = sizeof(cx<R>) * (size_t)n * (nb + 1);
-  if (smem_panel > 200 * 1024) {
-    set_last_error_text("merge matrix too large for the panel kernel");
-    return LS_EINVAL;
-  }
-  cx<R>* Mb = reinterpret_cast<cx<R>*>(scratch);
-  int* piv = reinterpret_cast<int*>(Mb + (size_t)P * nb * n);
-  int* perm = piv + (size_t)P * n;
-  if (sizeof(cx<R>) * (size_t)P * nb * n + sizeof(int) * (size_t)P * (n + 128) > scratch_bytes) return LS_ENOMEM;
-  LS_CUDA_TRY(cudaFuncSetAttribute(gj_panel_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_panel));
-  // clusters of CL blocks share one panel when the matrix is large enough
+  // clusters of CL blocks share one panel when the matrix is large enough; the
+  // panel width nb (<= 32) is the largest whose rows fit the shared memory of the
+  // kernel that will run (a block of the cluster holds n / CL rows)
   int CL = n >= 512 ? 16 : (n >= 256 ? 8 : 1);
   if (CL == 16 && cudaFuncSetAttribute(gj_panel_cluster_kernel<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                       cudaSuccess) {
     cudaGetLastError();
     CL = 8;
   }
-  const size_t smem_cl = sizeof(cx<R>) * (size_t)((n + CL - 1) / CL) * (nb + 1);
+  auto panel_smem = [&](int cl, int w) { return sizeof(cx<R>) * (size_t)((n + cl - 1) / cl) * (w + 1); };
+  auto pick_nb = [&](int cl) {
+    int w = 32;
+    while (w > 4 && panel_smem(cl, w) > 200 * 1024) w >>= 1;
+    return w;
+  };
+  int nb = pick_nb(CL);
+  size_t smem_cl = panel_smem(CL, nb);
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
   if (CL > 1) {
@@ -1590,6 +1587,18 @@ int invert_batch(ls_handle* H, cx<R>* X, int n, int lda, long long sX, int P, vo
       CL = 1;
     }
   }
+  if (CL == 1) nb = pick_nb(1);
+  const size_t smem_panel = panel_smem(1, nb);
+  if (panel_smem(CL, nb) > 200 * 1024) {
+    set_last_error_text("merge matrix too large for the panel kernel");
+    return LS_EINVAL;
+  }
+  if (CL == 1)
+    LS_CUDA_TRY(cudaFuncSetAttribute(gj_panel_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_panel));
+  cx<R>* Mb = reinterpret_cast<cx<R>*>(scratch);
+  int* piv = reinterpret_cast<int*>(Mb + (size_t)P * nb * n);
+  int* perm = piv + (size_t)P * n;
+  if (sizeof(cx<R>) * (size_t)P * nb * n + sizeof(int) * (size_t)P * (n + 128) > scratch_bytes) return LS_ENOMEM;
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int w = std::min(nb, n - k0);
     count_launch();

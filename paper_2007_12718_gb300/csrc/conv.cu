@@ -1,19 +1,21 @@
 // FFT application of the corrected Nystrom operator (Sec. 2.2 last paragraph,
 // Sec. 5): y = x + kappa^2 b .* (K * x), K the discrete kernel on lattice
-// offsets |m1| < nx, |m2| < ny embedded in a (2ny) x (2nx) circulant.
+// offsets |m1| < nx, |m2| < ny embedded in an Ly x Lx circulant, Lx and Ly the
+// powers of two >= 2nx, 2ny (any length >= 2n - 1 holds the linear convolution;
+// zeros between the positive and the negative offsets).
 //
 // Three passes over the padded array, FP64 throughout, no cuFFT:
-//   1. rows:    zero-pad each grid row to Lx = 2nx, forward DIF FFT
+//   1. rows:    zero-pad each grid row to Lx, forward DIF FFT
 //               (natural order in, bit-reversed order out)  -> W[ny][Lx]
 //   2. columns: each block takes C adjacent columns of W, zero-pads them to
-//               Ly = 2ny, forward DIF FFT, multiplies by the kernel spectrum
+//               Ly, forward DIF FFT, multiplies by the kernel spectrum
 //               (looked up at the bit-reversed frequencies), inverse DIT FFT
 //               (bit-reversed in, natural out), keeps the first ny rows
 //   3. rows:    inverse DIT FFT of each W row, keeps the first nx entries and
 //               writes y = x + kappa^2 b .* conv in the same pass.
 // DIF-forward / DIT-inverse pairs need no bit-reversal permutations.  K is
 // even in m1 and m2, so its spectrum is even too and only the quarter
-// (nx+1) x (ny+1) is stored (1/(4 nx ny) folded in).
+// (Lx/2 + 1) x (Ly/2 + 1) is stored (1/(Lx Ly) folded in).
 #include <mutex>
 
 #include "handle.h"
@@ -195,14 +197,15 @@ __global__ void kernel_table_kernel(z64* T, int tx, int ty, double kh, double h2
   T[t] = v;
 }
 
-// Fill the (2ny) x (2nx) circulant with K(m): index i <-> m1 = i (i < nx), i - 2nx (i > nx), 0 at i = nx.
-__global__ void circulant_kernel(z64* C, int nx, int ny, KernelTable kt, KernelSpec ks) {
+// Fill the Ly x Lx circulant with K(m): index i <-> m1 = i (i < nx), i - Lx
+// (i > Lx - nx), no offset (zero) in between.
+__global__ void circulant_kernel(z64* C, int nx, int ny, int Lx, int Ly, KernelTable kt, KernelSpec ks) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  int Lx = 2 * nx, Ly = 2 * ny;
   if (t >= (long long)Lx * Ly) return;
   int i = (int)(t % Lx), j = (int)(t / Lx);
   z64 v = mk<double>(0.0, 0.0);
-  if (i != nx && j != ny) {
+  const bool ix = i < nx || i > Lx - nx, jy = j < ny || j > Ly - ny;
+  if (ix && jy) {
     int m1 = i < nx ? i : i - Lx;
     int m2 = j < ny ? j : j - Ly;
     v = table_entry(kt, ks, m1, m2);
@@ -210,12 +213,13 @@ __global__ void circulant_kernel(z64* C, int nx, int ny, KernelTable kt, KernelS
   C[t] = v;
 }
 
-// Quarter spectrum in natural order from the bit-reversed full transform.
-__global__ void quarter_kernel(const z64* F, int Lx, int logLx, int Ly, int logLy, int nx, int ny, z64* Q,
+// Quarter spectrum (frequencies 0..nxq, 0..nyq; nxq = Lx / 2, nyq = Ly / 2) in
+// natural order from the bit-reversed full transform.
+__global__ void quarter_kernel(const z64* F, int Lx, int logLx, int Ly, int logLy, int nxq, int nyq, z64* Q,
                                double scale) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)(nx + 1) * (ny + 1)) return;
-  int kx = (int)(t % (nx + 1)), ky = (int)(t / (nx + 1));
+  if (t >= (long long)(nxq + 1) * (nyq + 1)) return;
+  int kx = (int)(t % (nxq + 1)), ky = (int)(t / (nxq + 1));
   z64 v = F[(long long)brev(ky, logLy) * Lx + brev(kx, logLx)];
   Q[t] = mk<double>(v.re * scale, v.im * scale);
 }
@@ -257,15 +261,20 @@ int kernel_table_setup(ls_handle* H, cudaStream_t st) {
 
 int conv_setup(ls_handle* H, cudaStream_t st) {
   const int nx = H->grid.nx, ny = H->grid.ny;
-  H->Lx = 2 * nx;
-  H->Ly = 2 * ny;
-  H->logLx = ilog2(H->Lx);
-  H->logLy = ilog2(H->Ly);
-  if ((1 << H->logLx) != H->Lx || (1 << H->logLy) != H->Ly) return LS_EINVAL;
+  H->logLx = ilog2(2 * nx);
+  H->logLy = ilog2(2 * ny);
+  H->Lx = 1 << H->logLx;
+  H->Ly = 1 << H->logLy;
+  // one padded row (and column) with its twiddles must fit in a block's shared memory
+  if (sizeof(z64) * ((size_t)std::max(H->Lx, H->Ly) * 3 / 2) > 200 * 1024) {
+    set_last_error_text("grid too large for the FFT matvec (padded length above 8192)");
+    return LS_EINVAL;
+  }
+  const int nxq = H->Lx / 2, nyq = H->Ly / 2;
   int rc;
   if ((rc = dalloc((void**)&H->tw_x, sizeof(z64) * H->Lx / 2))) return rc;
   if ((rc = dalloc((void**)&H->tw_y, sizeof(z64) * H->Ly / 2))) return rc;
-  if ((rc = dalloc((void**)&H->spec, sizeof(z64) * (size_t)(nx + 1) * (ny + 1)))) return rc;
+  if ((rc = dalloc((void**)&H->spec, sizeof(z64) * (size_t)(nxq + 1) * (nyq + 1)))) return rc;
   count_launch();
   twiddle_kernel<<<(H->Lx / 2 + 255) / 256, 256, 0, st>>>(H->tw_x, H->Lx);
   count_launch();
@@ -274,8 +283,8 @@ int conv_setup(ls_handle* H, cudaStream_t st) {
   size_t nfull = (size_t)H->Lx * H->Ly;
   if ((rc = dalloc((void**)&full, sizeof(z64) * nfull))) return rc;
   count_launch();
-  circulant_kernel<<<(unsigned)((nfull + 255) / 256), 256, 0, st>>>(full, nx, ny, KernelTable{H->ktab, H->ktx, H->kty},
-                                                                   H->ks_mv);
+  circulant_kernel<<<(unsigned)((nfull + 255) / 256), 256, 0, st>>>(full, nx, ny, H->Lx, H->Ly,
+                                                                   KernelTable{H->ktab, H->ktx, H->kty}, H->ks_mv);
   // rows: full length, in place through the same buffer (each block owns one row)
   size_t smr = sizeof(z64) * (H->Lx + H->Lx / 2);
   cudaFuncSetAttribute(rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
@@ -283,11 +292,11 @@ int conv_setup(ls_handle* H, cudaStream_t st) {
   rows_fwd_kernel<<<dim3(H->Ly, 1), 256, smr, st>>>(full, H->Lx, H->Lx, 0, full, 0, H->Lx, H->logLx, H->tw_x,
                                                     nullptr, 0.0);
   int C = cols_per_block(H->Ly);
-  LS_CUDA_TRY(launch_cols(C, H->Lx / C, 1, st, full, 0, H->Lx, H->logLx, H->Ly, H->Ly, H->logLy, H->tw_y, nullptr, nx,
-                          ny, 1));
-  size_t nq = (size_t)(nx + 1) * (ny + 1);
+  LS_CUDA_TRY(launch_cols(C, H->Lx / C, 1, st, full, 0, H->Lx, H->logLx, H->Ly, H->Ly, H->logLy, H->tw_y, nullptr,
+                          nxq, nyq, 1));
+  size_t nq = (size_t)(nxq + 1) * (nyq + 1);
   count_launch();
-  quarter_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(full, H->Lx, H->logLx, H->Ly, H->logLy, nx, ny,
+  quarter_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(full, H->Lx, H->logLx, H->Ly, H->logLy, nxq, nyq,
                                                               H->spec, 1.0 / ((double)H->Lx * H->Ly));
   if ((rc = check_launch("conv_setup"))) return rc;
   ls::dfree(full);  // stream-ordered: released after the kernels above
@@ -320,8 +329,8 @@ int conv_apply(ls_handle* H, const z64* x, z64* y, int nrhs, int mode, cudaStrea
   int C = cols_per_block(H->Ly);
   tk = prof_begin(st);
   LS_CUDA_TRY(launch_cols(C, H->Lx / C, nrhs, st, H->convbuf, w_stride, H->Lx, H->logLx, ny, H->Ly, H->logLy, H->tw_y,
-                          H->spec, nx, ny, 0));
-  prof_end(tk, PR_MV_COLS, st, R * 32.0 * W + 16.0 * (nx + 1.0) * (ny + 1.0),
+                          H->spec, H->Lx / 2, H->Ly / 2, 0));
+  prof_end(tk, PR_MV_COLS, st, R * 32.0 * W + 16.0 * (H->Lx / 2 + 1.0) * (H->Ly / 2 + 1.0),
            R * (2.0 * 5.0 * H->Lx * (double)H->Ly * H->logLy + 6.0 * H->Lx * (double)H->Ly));
   tk = prof_begin(st);
   count_launch();
@@ -420,7 +429,7 @@ extern "C" int ls_matvec_noalloc(ls_handle* H, const void* xv, void* yv, int nrh
                                                     nullptr, 0.0);
   int C = cols_per_block(H->Ly);
   LS_CUDA_TRY(launch_cols(C, H->Lx / C, nrhs, st, W, w_stride, H->Lx, H->logLx, ny, H->Ly, H->logLy, H->tw_y, H->spec,
-                          nx, ny, 0));
+                          H->Lx / 2, H->Ly / 2, 0));
   count_launch();
   rows_inv_kernel<<<dim3(ny, nrhs), 256, smr, st>>>(W, w_stride, H->Lx, H->logLx, H->tw_x, x, H->b, H->kappa * H->kappa,
                                                     nx, g_stride, y, ls::CONV_FORWARD);

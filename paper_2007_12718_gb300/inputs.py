@@ -64,6 +64,18 @@ def gaussian_family(n, seed, count=20):
     return b
 
 
+def cavity(n, centre=(0.5, 0.5)):
+    """The cavity of the paper's numerical experiments (Sec. 6.2): in polar
+    coordinates (r, theta) about the domain centre,
+    b = (1 - sin(theta / 2)^500) exp(-2000 (0.1 - r^2)^2), in [0, 1]; a ring of
+    radius ~0.32 open towards -x1 (theta = pi)."""
+    X, Y = grid_nodes(n)
+    dx, dy = X - centre[0], Y - centre[1]
+    r2 = dx * dx + dy * dy
+    th = np.arctan2(dy, dx)
+    return (1.0 - np.sin(0.5 * th) ** 500) * np.exp(-2000.0 * (0.1 - r2) ** 2)
+
+
 def constant_disk(n, value, radius, centre=(0.5, 0.5)):
     X, Y = grid_nodes(n)
     return np.where((X - centre[0]) ** 2 + (Y - centre[1]) ** 2 < radius ** 2, value, 0.0)
@@ -98,3 +110,10 @@ WORKLOADS = {
     "precond_n1024_10ppw": dict(n=1024, kappa=200 * np.pi, b=lambda n: gaussian_family(n, 0), order_precond=4,
                                 order_matvec=10, eps=1e-4, leaf=8),
 }
+# The cavity sweep of Sec. 6.3 (preconditioned solver, 10 points per wavelength,
+# 100-point leaves): n = 80 2^j, kappa = 2 pi n / 10 (the domain is n / 10
+# wavelengths across; kappa = 50.27 at n = 80), eps 1e-4, order 4 / 10.
+for _j in range(7):
+    _n = 80 << _j
+    WORKLOADS[f"cavity_n{_n}"] = dict(n=_n, kappa=2 * np.pi * _n / 10, b=lambda n: cavity(n), order_precond=4,
+                                      order_matvec=10, eps=1e-4, leaf=10)

@@ -111,3 +111,29 @@ def test_precond_n2048_true_residual():
     assert info["iterations"] <= 12
     assert bi["pivot_fallbacks"] == 0
     assert bi["levels"] == 16 and bi["ranks"][16] > 0
+
+
+@pytest.mark.parametrize("n", [80, 160])
+def test_cavity_sweep_members(n):
+    """The cavity of Sec. 6.2-6.3 at 10 points per wavelength with 100-point leaves
+    (the paper's sweep, Table of Sec. 6.3): at 80^2 sigma matches the oracle's dense
+    LU of the 10th-order system; at 160^2 the true residual by the oracle's FFT
+    matvec is <= 1e-10; GMRES iterations within one of the paper's (4, 5)."""
+    w = inputs.WORKLOADS[f"cavity_n{n}"]
+    kappa = w["kappa"]
+    h = 1.0 / n
+    b = w["b"](n)
+    f = nystrom.rhs(kappa, b, n, n, h)
+    for precision in (ls.LS_TF32X3, ls.LS_FP64):
+        H = ls.ls_build(n, h, kappa, b, w["eps"], leaf_side=w["leaf"], precision=precision)
+        sig = torch.zeros(n, n, dtype=torch.complex128, device=DEV)
+        info = ls.ls_solve(H, dev(f.reshape(n, n)), sig)[0]
+        ls.ls_free(H)
+        s = host(sig).ravel()
+        assert info["converged"] and abs(info["iterations"] - {80: 4, 160: 5}[n]) <= 1, info
+        if n == 80:
+            A = nystrom.dense_operator(kappa, h, b, 10)
+            assert rel(s, nystrom.solve_dense(A, f)) <= 1e-9
+        else:
+            spec = nystrom.conv_kernel_spectrum(kappa, h, n, n, 10)
+            assert np.linalg.norm(f - nystrom.matvec_fft(spec, kappa, b, s)) / np.linalg.norm(f) <= 1e-10

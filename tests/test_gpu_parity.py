@@ -80,6 +80,22 @@ def test_matvec_vs_dense(n, ny, order, nrhs):
         assert rel(y[r], ref[r]) < 1e-12
 
 
+@pytest.mark.parametrize("n,ny,leaf", [(40, 40, 5), (80, 40, 10), (48, 24, 6)])
+def test_matvec_non_power_of_two_grid(n, ny, leaf):
+    """Grids whose padded FFT length is not 2n (the circulant embedded at the next
+    power of two, zeros between the positive and negative offsets): the matvec
+    still equals the oracle's dense 10th-order operator."""
+    kappa = 25.0
+    b = inputs.gaussian_family(n, 5)[:ny, :]
+    H = build(n, kappa, b, 1e-4, order_matvec=10, ny=ny, leaf_side=leaf)
+    x = inputs.random_complex((2, ny, n), 12)
+    y = host(ls.ls_matvec(H, dev(x), torch.zeros(2, ny, n, dtype=torch.complex128, device=DEV)))
+    A = nystrom.dense_operator(kappa, 1.0 / n, b, 10)
+    ref = (A @ x.reshape(2, -1).T).T.reshape(x.shape)
+    for r in range(2):
+        assert rel(y[r], ref[r]) < 1e-12
+
+
 def test_matvec_host_buffers_match_device():
     n, kappa = 32, 15.0
     b = inputs.gaussian_bump(n)

@@ -131,3 +131,25 @@ def test_spectrum_example_soft_pin():
     assert 50 <= k_plain <= 110 and k_prec <= 10
     M = np.stack([inv.apply(e) for e in np.eye(n * n)], axis=1)
     assert np.abs(np.linalg.eigvals(A @ M) - 1).max() < 0.15
+
+
+def test_cavity_preconditioned_iterations_match_paper():
+    """Sec. 6.3, cavity table: at N = 6400 (80 x 80, kappa = 50.27, 10 points per
+    wavelength, 100-point leaves, eps = 1e-4, 4th-order corrections in the HBS,
+    10th-order FFT operator) the preconditioned GMRES reaches 1e-10 in 4 iterations.
+    The oracle's HBS + GMRES must land within one iteration of that."""
+    from oracle import gmres as ogmres
+    from oracle import nystrom
+    from paper_2007_12718_gb300 import inputs
+    w = inputs.WORKLOADS["cavity_n80"]
+    n, kappa = w["n"], w["kappa"]
+    h = 1.0 / n
+    b = w["b"](n)
+    comp = hbs.Compression(kappa, h, hbs.Tree(n, n, w["leaf"]), 4, w["eps"], 2)
+    inv = hbs.Inverse(comp, b)
+    spec = nystrom.conv_kernel_spectrum(kappa, h, n, n, 10)
+    f = nystrom.rhs(kappa, b, n, n, h)
+    s, k, hist = ogmres.gmres(lambda v: nystrom.matvec_fft(spec, kappa, b, v), f, apply_M=inv.apply, tol=1e-10)
+    r = np.linalg.norm(f - nystrom.matvec_fft(spec, kappa, b, s)) / np.linalg.norm(f)
+    assert r < 2e-10
+    assert 3 <= k <= 5, k
