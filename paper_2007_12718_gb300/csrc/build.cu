@@ -294,11 +294,20 @@ __global__ void __launch_bounds__(256) gemm64x2_kernel(int M, int N, int K, c32 
 thread_local int g_tc_engine = 0;
 thread_local int* g_tc_err = nullptr;
 
+// Batches beyond the grid's y / z limit are launched in chunks.
+constexpr int kMaxGridYZ = 65535;
+
 template <class R>
 void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, cx<R> alpha, const cx<R>* A, int lda, long long sA,
           const cx<R>* B, int ldb, long long sB, cx<R> beta, cx<R>* C, int ldc, long long sC, int batch,
           Band bd = Band()) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
+  if (batch > kMaxGridYZ) {
+    for (int b0 = 0; b0 < batch; b0 += kMaxGridYZ)
+      gemm<R>(st, ta, tb, M, N, K, alpha, A + b0 * sA, lda, sA, B + b0 * sB, ldb, sB, beta, C + b0 * sC, ldc, sC,
+              std::min(kMaxGridYZ, batch - b0), bd);
+    return;
+  }
   if (K <= 0) return;  // only reached with beta = 1 (nothing to add)
   // tensor cores for every product with at least one 128 x 128 tile and ~2^25
   // complex MACs: measured 2x (K = 64 updates) to 4x (K in the thousands) the
@@ -1761,9 +1770,12 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
         cx<R>* Zc = reinterpret_cast<cx<R>*>(scratch);  // copy of Z for the fallback
         void* scr2 = Zc + (size_t)P * kk;
         size_t scr2_bytes = scratch_bytes - sizeof(cx<R>) * (size_t)P * kk;
-        dim3 gc((unsigned)std::min<long long>(1024, (kk + 255) / 256), P);
-        count_launch();
-        copy_block_kernel<R><<<gc, 256, 0, st>>>(Zc, kc, kk, X22, n2, sX, kc, kc);
+        dim3 gc((unsigned)std::min<long long>(1024, (kk + 255) / 256), std::min(P, kMaxGridYZ));
+        for (int b0 = 0; b0 < P; b0 += kMaxGridYZ) {
+          gc.y = std::min(kMaxGridYZ, P - b0);
+          count_launch();
+          copy_block_kernel<R><<<gc, 256, 0, st>>>(Zc + (size_t)b0 * kk, kc, kk, X22 + (size_t)b0 * sX, n2, sX, kc, kc);
+        }
         LS_CUDA_TRY(cudaMemsetAsync(H->d_err + 2, 0, 2 * sizeof(int), st));
         if (kc <= gj_reg_max<R>()) {
           if ((rc = invert_reg_nopiv<R>(X22, kc, n2, sX, P, H->d_err + 3, st))) return rc;
@@ -1806,8 +1818,11 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
         const double limit = std::max(H->tol, 10.0 * unit * kc);
         if (flags[1] != 0 || !((double)worst <= limit)) {
           // restore Z and invert with row interchanges
-          count_launch();
-          copy_block_kernel<R><<<gc, 256, 0, st>>>(X22, n2, sX, Zc, kc, kk, kc, kc);
+          for (int b0 = 0; b0 < P; b0 += kMaxGridYZ) {
+            gc.y = std::min(kMaxGridYZ, P - b0);
+            count_launch();
+            copy_block_kernel<R><<<gc, 256, 0, st>>>(X22 + (size_t)b0 * sX, n2, sX, Zc + (size_t)b0 * kk, kc, kk, kc, kc);
+          }
           if ((rc = invert_batch<R>(H, X22, kc, n2, sX, P, scr2, scr2_bytes, st))) return rc;
           ++H->pivot_fallbacks;
         }
@@ -1949,6 +1964,12 @@ template <class R>
 void gemv(cudaStream_t st, bool ta, int M, int K, cx<R> alpha, const cx<R>* A, int lda, long long sA, const cx<R>* x,
           long long sx, cx<R> beta, cx<R>* y, long long sy, int batch) {
   if (M <= 0 || K <= 0 || batch <= 0) return;
+  if (batch > kMaxGridYZ) {
+    for (int b0 = 0; b0 < batch; b0 += kMaxGridYZ)
+      gemv<R>(st, ta, M, K, alpha, A + b0 * sA, lda, sA, x + b0 * sx, sx, beta, y + b0 * sy, sy,
+              std::min(kMaxGridYZ, batch - b0));
+    return;
+  }
   count_launch();
   if (!ta)
     gemv_n_kernel<R><<<dim3((M + 7) / 8, batch), 256, 0, st>>>(M, K, alpha, A, lda, sA, x, sx, beta, y, sy);

@@ -324,6 +324,14 @@ int tc_cgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, c32 alpha, 
              const c32* B, int ldb, long long sB, c32 beta, c32* C, int ldc, long long sC, int batch, int split,
              int* err, int band_lo, int band_hi) {
   if (M <= 0 || N <= 0 || batch <= 0 || K <= 0) return LS_OK;
+  if (batch > 65535) {  // the batch is the grid's z dimension
+    for (int b0 = 0; b0 < batch; b0 += 65535) {
+      int rc = tc_cgemm(st, ta, tb, M, N, K, alpha, A + b0 * sA, lda, sA, B + b0 * sB, ldb, sB, beta, C + b0 * sC, ldc,
+                        sC, std::min(65535, batch - b0), split, err, band_lo, band_hi);
+      if (rc) return rc;
+    }
+    return LS_OK;
+  }
   const size_t smem = sizeof(float) * (size_t)TC_NS * TC_STAGE;
   const void* fn = !ta && !tb ? (const void*)tc_gemm_kernel<false, false>
                  : ta && !tb  ? (const void*)tc_gemm_kernel<true, false>

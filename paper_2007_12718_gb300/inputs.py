@@ -109,6 +109,10 @@ WORKLOADS = {
                                order_matvec=10, eps=1e-4, leaf=8),
     "precond_n1024_10ppw": dict(n=1024, kappa=200 * np.pi, b=lambda n: gaussian_family(n, 0), order_precond=4,
                                 order_matvec=10, eps=1e-4, leaf=8),
+    # the largest grid of the family the FFT matvec takes (padded rows of 8192):
+    # N = 16,777,216, 400 wavelengths across
+    "precond_n4096": dict(n=4096, kappa=800 * np.pi, b=lambda n: gaussian_family(n, 0), order_precond=4,
+                          order_matvec=10, eps=1e-4, leaf=8),
 }
 # The cavity sweep of Sec. 6.3 (preconditioned solver, 10 points per wavelength,
 # 100-point leaves): n = 80 2^j, kappa = 2 pi n / 10 (the domain is n / 10
