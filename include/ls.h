@@ -79,6 +79,15 @@ typedef struct {
                          kernels) before it gives up and the call returns LS_ETIMEOUT; 0 =
                          default (2e7 polls, about a second).  After LS_ETIMEOUT the handle's
                          barrier state is spent: free the handle.                          */
+  int rhs_block;      /* right-hand sides that ls_apply / ls_solve / ls_solve_transpose treat
+                         as one block: the apply runs each product as a GEMM over the block
+                         (every factor read once per block), GMRES keeps one Krylov space per
+                         right-hand side and applies the preconditioner and the operator to
+                         the block's current vectors together.  0 = automatic (up to 256, and
+                         nb * nx * ny * 16 bytes within 1 GiB); 1 = one right-hand side at a
+                         time (the persistent one-vector apply).  Block GMRES allocates one
+                         slab of nb grid vectors per Krylov vector and per preconditioned
+                         vector as the iterations reach them (kept by the handle).         */
 } ls_opts;
 
 /* Pivot selection of the row ID (ls_opts.id_method, ls_row_id_ex).

@@ -49,7 +49,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("order_matvec", ctypes.c_int), ("order_precond", ctypes.c_int), ("leaf_side", ctypes.c_int),
                 ("proxy_width", ctypes.c_int), ("precision", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("merge_pivoting", ctypes.c_int),
-                ("top_uncompressed", ctypes.c_int), ("id_method", ctypes.c_int), ("wait_limit", ctypes.c_int)]
+                ("top_uncompressed", ctypes.c_int), ("id_method", ctypes.c_int), ("wait_limit", ctypes.c_int),
+                ("rhs_block", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -215,12 +216,13 @@ def default_opts():
 
 def ls_build(n, h, kappa, b, tol, order_matvec=10, order_precond=4, leaf_side=8, proxy_width=0,
              precision=LS_FP32, gmres_maxit=100, gmres_tol=1e-10, x0=0.0, y0=0.0, ny=None, stream=None,
-             merge_pivoting=0, top_uncompressed=0, id_method=LS_ID_AUTO, wait_limit=0):
-    """Compress G and build the HBS inverse (Sec. 3.2, Algorithm 1); b is [ny][nx] float64."""
+             merge_pivoting=0, top_uncompressed=0, id_method=LS_ID_AUTO, wait_limit=0, rhs_block=0):
+    """Compress G and build the HBS inverse (Sec. 3.2, Algorithm 1); b is [ny][nx] float64.
+    rhs_block: right-hand sides per block of ls_apply / ls_solve (0 automatic, 1 one at a time)."""
     lib = load_library()
     g = Grid(n, n if ny is None else ny, h, x0, y0)
     o = Opts(order_matvec, order_precond, leaf_side, proxy_width, precision, gmres_maxit, gmres_tol,
-             merge_pivoting, top_uncompressed, id_method, wait_limit)
+             merge_pivoting, top_uncompressed, id_method, wait_limit, rhs_block)
     bp, keep, _ = _ptr(b, np.float64)
     out = ctypes.c_void_p()
     _check(lib.ls_build(ctypes.byref(g), kappa, bp, tol, ctypes.byref(o), _stream(stream), ctypes.byref(out)),

@@ -2969,7 +2969,194 @@ int hbs_apply_graph_init(ls_handle* H) {
   return LS_OK;
 }
 
+// ------------------------------------------------- apply to a block of right-hand sides
+// Algorithm 2 for nb right-hand sides at once.  It runs the operation list of
+// the one-vector apply (forward or transposed), every batched matrix-vector
+// product y[b] = y0[b] + alpha A[b] x[b] becoming a batched matrix product with
+// nb columns, so each factor is read once for the whole block (on the GEMM
+// engines of the build: tcgen05 tf32x3 for the large products of a LS_TF32X3
+// handle, the SIMT kernels otherwise).  The block workspace stores each entry
+// of the one-vector workspace as a row of nb entries, so every vector of the
+// list maps to a row block with row stride nb at nb times its offset.
+
+// F[e][r] = f[r][grid index of leaf entry e], 32 entries x 32 right-hand sides
+// per block through shared memory (reads follow the grid rows, writes the block rows).
+template <class R>
+__global__ void __launch_bounds__(256) gather_block_kernel(TreeGeom g, const z64* __restrict__ f, long long N, int nb,
+                                                           cx<R>* __restrict__ F) {
+  __shared__ cx<R> tile[32][33];
+  const int n = g.s * g.s;
+  const long long tot = (1LL << g.L) * n, e0 = (long long)blockIdx.x * 32;
+  const int r0 = blockIdx.y * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const long long e = e0 + tx;
+  long long gi = -1;
+  if (e < tot) {
+    const int leaf = (int)(e / n), i = (int)(e % n);
+    int ox, oy;
+    leaf_origin(g, leaf, ox, oy);
+    gi = (long long)(oy + i / g.s) * g.nx + ox + i % g.s;
+  }
+  for (int rr = ty; rr < 32; rr += 8)
+    if (gi >= 0 && r0 + rr < nb) tile[rr][tx] = cvt<R>(f[(long long)(r0 + rr) * N + gi]);
+  __syncthreads();
+  for (int ee = ty; ee < 32; ee += 8)
+    if (e0 + ee < tot && r0 + tx < nb) F[(e0 + ee) * nb + r0 + tx] = tile[tx][ee];
+}
+
+// q[r][grid index of leaf entry e] = Q[e][r] (the inverse of gather_block_kernel).
+template <class R>
+__global__ void __launch_bounds__(256) scatter_block_kernel(TreeGeom g, const cx<R>* __restrict__ Q, long long N,
+                                                            int nb, z64* __restrict__ q) {
+  __shared__ cx<R> tile[32][33];
+  const int n = g.s * g.s;
+  const long long tot = (1LL << g.L) * n, e0 = (long long)blockIdx.x * 32;
+  const int r0 = blockIdx.y * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int ee = ty; ee < 32; ee += 8)
+    if (e0 + ee < tot && r0 + tx < nb) tile[tx][ee] = Q[(e0 + ee) * nb + r0 + tx];
+  __syncthreads();
+  const long long e = e0 + tx;
+  if (e >= tot) return;
+  const int leaf = (int)(e / n), i = (int)(e % n);
+  int ox, oy;
+  leaf_origin(g, leaf, ox, oy);
+  const long long gi = (long long)(oy + i / g.s) * g.nx + ox + i % g.s;
+  for (int rr = ty; rr < 32; rr += 8)
+    if (r0 + rr < nb) q[(long long)(r0 + rr) * N + gi] = cvt<double>(tile[rr][tx]);
+}
+
+// Entries of the one-vector apply workspace (its layout is fixed by apply_prepare).
+size_t apply_work_entries(const ls_handle* H) {
+  size_t vec = (size_t)2 * ((size_t)1 << H->L) * H->s * H->s;
+  for (int l = 1; l <= H->L; ++l) vec += (size_t)3 * ((size_t)1 << l) * std::max(1, H->lev[l].k) * 2;
+  return vec;
+}
+
+// Sets the calling thread's GEMM engine to the handle's for the lifetime of the object.
+struct EngineScope {
+  int prev_engine;
+  int* prev_err;
+  explicit EngineScope(const ls_handle* H) : prev_engine(g_tc_engine), prev_err(g_tc_err) {
+    g_tc_engine = H->prec == LS_TF32X3 ? 2 : 0;
+    g_tc_err = H->d_err;
+  }
+  ~EngineScope() {
+    g_tc_engine = prev_engine;
+    g_tc_err = prev_err;
+  }
+};
+
+// rows x cols row blocks, batch of them: dst[b] = src[b] (src null: zero), strides in entries.
+template <class R>
+int copy_rows(cx<R>* dst, long long sd, const cx<R>* src, long long ss, long long rows_cols, int batch, cudaStream_t st) {
+  const size_t w = sizeof(cx<R>) * (size_t)rows_cols;
+  if (w == 0 || batch <= 0) return LS_OK;
+  const size_t dp = batch > 1 ? sizeof(cx<R>) * (size_t)sd : w, sp = batch > 1 ? sizeof(cx<R>) * (size_t)ss : w;
+  if (src)
+    LS_CUDA_TRY(cudaMemcpy2DAsync(dst, dp, src, sp, w, batch, cudaMemcpyDeviceToDevice, st));
+  else
+    LS_CUDA_TRY(cudaMemset2DAsync(dst, dp, 0, w, batch, st));
+  return LS_OK;
+}
+
+template <class R>
+int apply_block_t(ls_handle* H, const std::vector<ApplyOp>& ops, const z64* f, z64* q, int nb, cudaStream_t st,
+                  double* flops) {
+  const int L = H->L, n = H->s * H->s;
+  const long long nleaf = 1LL << L, N = (long long)H->grid.nx * H->grid.ny;
+  const size_t went = apply_work_entries(H);
+  const size_t need = sizeof(cx<R>) * went * (size_t)nb;
+  int rc;
+  if (H->bwork_bytes < need) {
+    if (H->bwork) dfree(H->bwork);
+    H->bwork = nullptr;
+    H->bwork_bytes = 0;
+    if ((rc = dalloc(&H->bwork, need))) return rc;
+    H->bwork_bytes = need;
+  }
+  const cx<R>* base = reinterpret_cast<const cx<R>*>(H->work);
+  cx<R>* W = reinterpret_cast<cx<R>*>(H->bwork);
+  auto map = [&](const void* p) -> cx<R>* {
+    const cx<R>* c = reinterpret_cast<const cx<R>*>(p);
+    if (c >= base && c < base + went) return W + (size_t)(c - base) * nb;
+    return const_cast<cx<R>*>(c);  // a factor
+  };
+  const TreeGeom g = make_geom(H);
+  const dim3 tgrid((unsigned)((nleaf * n + 31) / 32), (unsigned)((nb + 31) / 32));
+  EngineScope engine(H);
+  const cx<R> one_ = mk<R>(R(1), R(0)), zero_ = mk<R>(R(0), R(0));
+  double fl = 0;
+  for (const ApplyOp& o : ops) {
+    const cx<R> alpha = mk<R>((R)o.ar, (R)o.ai);
+    switch (o.type) {
+      case 1:  // y <- f on the leaves
+        count_launch();
+        gather_block_kernel<R><<<tgrid, 256, 0, st>>>(g, f, N, nb, map(o.y));
+        break;
+      case 2:  // grid <- x
+        count_launch();
+        scatter_block_kernel<R><<<tgrid, 256, 0, st>>>(g, map(o.x), N, nb, q);
+        break;
+      case 3: {  // leaves: F <- f, r = X F (-> y0), r~ = U^T r (-> y)
+        cx<R>* F = W;
+        count_launch();
+        gather_block_kernel<R><<<tgrid, 256, 0, st>>>(g, f, N, nb, F);
+        cx<R>* Rl = map(o.y0);
+        gemm<R>(st, false, false, n, nb, n, one_, reinterpret_cast<const cx<R>*>(o.A), n, (long long)n * n, F, nb,
+                (long long)n * nb, zero_, Rl, nb, (long long)n * nb, (int)nleaf);
+        if (o.M > 0)
+          gemm<R>(st, false, false, o.M, nb, n, one_, reinterpret_cast<const cx<R>*>(o.x), n, 0, Rl, nb,
+                  (long long)n * nb, zero_, map(o.y), nb, (long long)o.M * nb, (int)nleaf);
+        fl += 8.0 * nleaf * nb * ((double)n * n + (double)o.M * n);
+        break;
+      }
+      case 4: {  // grid <- y0 + alpha A x (in place in y0: the list's last use of it)
+        cx<R>* Rl = map(o.y0);
+        if (o.K > 0)
+          gemm<R>(st, false, false, n, nb, o.K, alpha, reinterpret_cast<const cx<R>*>(o.A), o.K, (long long)n * o.K,
+                  map(o.x), nb, (long long)o.K * nb, one_, Rl, nb, (long long)n * nb, (int)nleaf);
+        count_launch();
+        scatter_block_kernel<R><<<tgrid, 256, 0, st>>>(g, Rl, N, nb, q);
+        fl += 8.0 * nleaf * nb * (double)n * o.K;
+        break;
+      }
+      default: {  // y = y0 + alpha A x
+        if (o.M <= 0 || o.batch <= 0) break;
+        cx<R>* y = map(o.y);
+        const cx<R>* y0 = o.y0 ? map(o.y0) : nullptr;
+        if (y0 != y && (y0 || o.K <= 0) &&
+            (rc = copy_rows<R>(y, o.sy * nb, y0, o.sy0 * nb, (long long)o.M * nb, o.batch, st)))
+          return rc;
+        if (o.K > 0)
+          gemm<R>(st, false, false, o.M, nb, o.K, alpha, reinterpret_cast<const cx<R>*>(o.A), o.lda, o.sA, map(o.x),
+                  nb, o.sx * nb, y0 ? one_ : zero_, y, nb, o.sy * nb, o.batch);
+        fl += 8.0 * o.batch * nb * (double)o.M * o.K;
+      }
+    }
+  }
+  if (flops) *flops = fl;
+  return check_launch("hbs_apply (block)");
+}
+
+// Operation list of the apply on the host (a few hundred entries: made per call).
+template <class R>
+std::vector<ApplyOp> block_ops(ls_handle* H, int transpose) {
+  return transpose ? apply_ops_transpose<R>(H) : apply_ops<R>(H);
+}
+
 }  // namespace
+
+int hbs_apply_block(ls_handle* H, const z64* f, z64* q, int nb, int transpose, cudaStream_t st) {
+  int rc;
+  if ((rc = level_transposes(H, st))) return rc;  // the lists read U^T and G^T
+  if (transpose && (rc = apply_transpose_init(H, st))) return rc;
+  const int tk = prof_begin(st);
+  double fl = 0;
+  rc = H->prec == LS_FP64 ? apply_block_t<double>(H, block_ops<double>(H, transpose), f, q, nb, st, &fl)
+                          : apply_block_t<float>(H, block_ops<float>(H, transpose), f, q, nb, st, &fl);
+  // bytes: every factor once (the inner levels' X twice) and the block's vectors in and out
+  prof_end(tk, PR_APPLY_BLOCK, st, H->bytes_apply + 32.0 * (nb - 1) * H->grid.nx * H->grid.ny, fl);
+  return rc;
+}
 
 int hbs_build(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
   return H->prec == LS_FP64 ? build_t<double>(H, st, wait_level) : build_t<float>(H, st, wait_level);
@@ -2987,9 +3174,27 @@ int simt_zgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, z64 alpha
   return check_launch("simt_zgemm");
 }
 
+int rhs_block_size(const ls_handle* H, int nrhs) {
+  if (H->opts.rhs_block > 0) return std::max(1, std::min(nrhs, H->opts.rhs_block));
+  // automatic: up to 256, and one slab of the block's grid vectors within 1 GiB
+  const long long N = (long long)H->grid.nx * H->grid.ny;
+  const long long fit = (1LL << 30) / (16LL * N);
+  return (int)std::max(1LL, std::min<long long>({(long long)nrhs, 256LL, fit}));
+}
+
 int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, int transpose, cudaStream_t st) {
   const long long N = (long long)H->grid.nx * H->grid.ny;
   int rc;
+  const int nbk = rhs_block_size(H, nrhs);
+  if (nbk > 1) {  // blocks of right-hand sides, each factor read once per block
+    for (int r0 = 0; r0 < nrhs; r0 += nbk) {
+      const int nb = std::min(nbk, nrhs - r0);
+      rc = nb > 1 ? hbs_apply_block(H, f + r0 * N, q + r0 * N, nb, transpose, st)
+                  : hbs_apply(H, f + r0 * N, q + r0 * N, 1, transpose, st);
+      if (rc) return rc;
+    }
+    return LS_OK;
+  }
   if ((rc = apply_persistent_init(H, st))) return rc;
   if (transpose) {
     if ((rc = apply_transpose_init(H, st))) return rc;

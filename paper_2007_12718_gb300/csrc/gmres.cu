@@ -447,6 +447,408 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, int t
   return inf.converged ? LS_OK : LS_ENOCONV;
 }
 
+
+// ------------------------------------------------- block GMRES
+// nb right-hand sides, each with its own Krylov space: the one-vector solver's
+// arithmetic (flexible right preconditioning, CGS2, complex Givens rotations,
+// zero initial guess, no restart) run side by side.  Each iteration applies the
+// preconditioner and the operator to the nb current vectors at once
+// (hbs_apply_block, conv_apply with nrhs = nb), so every factor and the kernel
+// spectrum are read once per iteration for the block.  A right-hand side whose
+// residual estimate reaches the tolerance is frozen (its later vectors are
+// zero, its kernels return early); the block stops when all are frozen or at
+// gmres_maxit.  Vectors: one slab of nb grid vectors per Krylov vector V_j and
+// per preconditioned vector Z_j, allocated as the iterations reach them; the
+// kernels find them through device tables of slab pointers.  Right-hand side r
+// is split into C chunks (block (c, r) of every grid); reductions run in a
+// fixed order, so results are reproducible.
+
+constexpr int kVG = 4;  // Krylov vectors per pass of the dot-product kernel
+
+struct BState {
+  double fnorm;
+  double resid;
+  int k;     // iterations taken (columns of H in use)
+  int done;  // frozen
+};
+
+__device__ __forceinline__ void chunk_of(long long N, int C, int c, long long& n0, long long& n1) {
+  const long long per = (N + C - 1) / C;
+  n0 = c * per;
+  n1 = min(N, n0 + per);
+}
+
+// block sum of a complex value over 256 threads in a fixed order; valid in thread 0
+__device__ __forceinline__ z64 block_sum256(z64 a, z64* red) {
+  a = warp_sum(a);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  z64 s = mk<double>(0.0, 0.0);
+  if (threadIdx.x == 0)
+    for (int w = 0; w < 8; ++w) s = s + red[w];
+  __syncthreads();
+  return s;
+}
+
+// nrm[r * C + c] = ||x_r||^2 over chunk c
+__global__ void __launch_bounds__(256) bnorm_kernel(const z64* __restrict__ x, long long N, int C, z64* __restrict__ nrm) {
+  __shared__ z64 red[8];
+  const int c = blockIdx.x, r = blockIdx.y;
+  long long n0, n1;
+  chunk_of(N, C, c, n0, n1);
+  const z64* xr = x + r * N;
+  z64 acc = mk<double>(0.0, 0.0);
+  for (long long n = n0 + threadIdx.x; n < n1; n += 256) fmac_(acc, xr[n], xr[n]);
+  const z64 s = block_sum256(acc, red);
+  if (threadIdx.x == 0) nrm[(long long)r * C + c] = s;
+}
+
+// ||f_r|| from the partials, state and g_r = (||f_r||, 0, ...); f_r = 0 is frozen at k = 0
+__global__ void binit_kernel(const z64* __restrict__ nrm, int C, BState* st, z64* g, int ldg) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= gridDim.x * blockDim.x) return;
+  double s = 0.0;
+  for (int c = 0; c < C; ++c) s += nrm[(long long)r * C + c].re;
+  const double fn = sqrt(s);
+  st[r].fnorm = fn;
+  st[r].resid = fn > 0.0 ? 1.0 : 0.0;
+  st[r].k = 0;
+  st[r].done = fn > 0.0 ? 0 : 1;
+  g[(long long)r * ldg] = mk<double>(fn, 0.0);
+}
+
+// V_0[r] = f_r / ||f_r|| (zero for f_r = 0)
+__global__ void __launch_bounds__(256) bscale_kernel(const z64* __restrict__ f, z64* __restrict__ v, long long N, int C,
+                                                     const BState* __restrict__ st) {
+  const int c = blockIdx.x, r = blockIdx.y;
+  long long n0, n1;
+  chunk_of(N, C, c, n0, n1);
+  const double fn = st[r].fnorm, s = fn > 0.0 ? 1.0 / fn : 0.0;
+  for (long long n = n0 + threadIdx.x; n < n1; n += 256) {
+    const z64 x = f[r * N + n];
+    v[r * N + n] = mk<double>(x.re * s, x.im * s);
+  }
+}
+
+// part[(r * ldp + i) * C + c] = sum over chunk c of conj(V_i[r]) w_r, i <= j
+__global__ void __launch_bounds__(256) bdots_kernel(const z64* const* __restrict__ Vt, int j, const z64* __restrict__ w,
+                                                    long long N, int C, int ldp, z64* __restrict__ part,
+                                                    const BState* __restrict__ st) {
+  __shared__ z64 red[kVG][8];
+  const int c = blockIdx.x, r = blockIdx.y;
+  if (st[r].done) return;
+  long long n0, n1;
+  chunk_of(N, C, c, n0, n1);
+  const z64* wr = w + r * N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i0 = 0; i0 <= j; i0 += kVG) {
+    const int ng = min(kVG, j + 1 - i0);
+    const z64* v[kVG];
+#pragma unroll
+    for (int q = 0; q < kVG; ++q) v[q] = (q < ng ? Vt[i0 + q] : Vt[i0]) + r * N;
+    z64 acc[kVG];
+#pragma unroll
+    for (int q = 0; q < kVG; ++q) acc[q] = mk<double>(0.0, 0.0);
+    for (long long n = n0 + threadIdx.x; n < n1; n += 256) {
+      const z64 x = wr[n];
+#pragma unroll
+      for (int q = 0; q < kVG; ++q)
+        if (q < ng) fmac_(acc[q], v[q][n], x);
+    }
+#pragma unroll
+    for (int q = 0; q < kVG; ++q) {
+      const z64 a = warp_sum(acc[q]);
+      if (lane == 0) red[q][warp] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < ng) {
+      z64 s = mk<double>(0.0, 0.0);
+      for (int w2 = 0; w2 < 8; ++w2) s = s + red[threadIdx.x][w2];
+      part[((long long)r * ldp + i0 + threadIdx.x) * C + c] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// h_i = sum_c part[r][i][c] (fixed order; block c = 0 adds it to column j of H_r),
+// then w_r -= sum_i V_i[r] h_i on chunk c; with nrm, the chunk's ||w_r||^2 -> nrm[r * C + c]
+__global__ void __launch_bounds__(256) bupdate_kernel(const z64* const* __restrict__ Vt, int j, z64* __restrict__ w,
+                                                      long long N, int C, int ldp, const z64* __restrict__ part,
+                                                      z64* __restrict__ Hm, int m, z64* __restrict__ nrm,
+                                                      const BState* __restrict__ st) {
+  extern __shared__ z64 h[];  // j + 1
+  __shared__ z64 red[8];
+  const int c = blockIdx.x, r = blockIdx.y;
+  if (st[r].done) return;
+  for (int i = threadIdx.x; i <= j; i += 256) {
+    z64 s = mk<double>(0.0, 0.0);
+    for (int cc = 0; cc < C; ++cc) s = s + part[((long long)r * ldp + i) * C + cc];
+    h[i] = s;
+    if (c == 0) {
+      z64* e = Hm + (long long)r * (m + 1) * m + (long long)i * m + j;
+      *e = *e + s;
+    }
+  }
+  __syncthreads();
+  long long n0, n1;
+  chunk_of(N, C, c, n0, n1);
+  z64* wr = w + r * N;
+  z64 acc = mk<double>(0.0, 0.0);
+  for (long long n = n0 + threadIdx.x; n < n1; n += 256) {
+    z64 x = wr[n];
+    for (int i = 0; i <= j; ++i) {
+      const z64 a = h[i], v = Vt[i][r * N + n];
+      x.re -= v.re * a.re - v.im * a.im;
+      x.im -= v.re * a.im + v.im * a.re;
+    }
+    wr[n] = x;
+    fmac_(acc, x, x);
+  }
+  if (nrm) {
+    const z64 s = block_sum256(acc, red);
+    if (threadIdx.x == 0) nrm[(long long)r * C + c] = s;
+  }
+}
+
+// ||w_r|| from the partials into H_r(j+1, j), the Givens step of column j, and the
+// freeze decision (residual estimate <= tol); one thread per right-hand side.
+__global__ void bgivens_kernel(const z64* __restrict__ nrm, int C, z64* Hm, int m, z64* cs, z64* sn, z64* g, BState* st,
+                               int j, double tol, int nb) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nb || st[r].done) return;
+  double s = 0.0;
+  for (int c = 0; c < C; ++c) s += nrm[(long long)r * C + c].re;
+  z64* H = Hm + (long long)r * (m + 1) * m;
+  H[(long long)(j + 1) * m + j] = mk<double>(sqrt(s), 0.0);
+  GmState gs{st[r].fnorm, st[r].resid, st[r].k};
+  givens_step(H, m, cs + (long long)r * m, sn + (long long)r * m, g + (long long)r * (m + 1), j, &gs);
+  st[r].resid = gs.resid;
+  st[r].k = gs.k;
+  if (gs.resid <= tol) st[r].done = 1;
+}
+
+// V_{j+1}[r] = w_r / ||w_r|| (the norm summed from the partials in the order of
+// bgivens_kernel: the Givens step has already rotated H_r(j+1, j) to zero);
+// zero for a frozen right-hand side
+__global__ void __launch_bounds__(256) bnormalize_kernel(const z64* __restrict__ w, z64* __restrict__ vn, long long N,
+                                                         int C, const z64* __restrict__ nrm,
+                                                         const BState* __restrict__ st) {
+  __shared__ double nr_s;
+  const int c = blockIdx.x, r = blockIdx.y;
+  long long n0, n1;
+  chunk_of(N, C, c, n0, n1);
+  if (threadIdx.x == 0) {
+    double s2 = 0.0;
+    for (int cc = 0; cc < C; ++cc) s2 += nrm[(long long)r * C + cc].re;
+    nr_s = sqrt(s2);
+  }
+  __syncthreads();
+  const double nr = nr_s;
+  const double s = (!st[r].done && nr > 0.0) ? 1.0 / nr : 0.0;
+  for (long long n = n0 + threadIdx.x; n < n1; n += 256) {
+    const z64 x = w[r * N + n];
+    vn[r * N + n] = mk<double>(x.re * s, x.im * s);
+  }
+}
+
+// y_r = H_r(0:k, 0:k)^-1 g_r(0:k), k = the right-hand side's iterations
+__global__ void bbacksolve_kernel(const z64* Hm, int m, const z64* g, z64* y, const BState* st, int nb) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nb) return;
+  const z64* H = Hm + (long long)r * (m + 1) * m;
+  const z64* gr = g + (long long)r * (m + 1);
+  z64* yr = y + (long long)r * (m + 1);
+  const int k = st[r].k;
+  for (int i = k - 1; i >= 0; --i) {
+    z64 s = gr[i];
+    for (int c = i + 1; c < k; ++c) s = s - H[(long long)i * m + c] * yr[c];
+    yr[i] = s * inv(H[(long long)i * m + i]);
+  }
+}
+
+// sigma_r = sum_{i < k_r} Z_i[r] y_r[i]
+__global__ void __launch_bounds__(256) bcombine_kernel(const z64* const* __restrict__ Zt, const z64* __restrict__ y,
+                                                       int m, z64* __restrict__ sigma, long long N, int C,
+                                                       const BState* __restrict__ st) {
+  const int c = blockIdx.x, r = blockIdx.y, k = st[r].k;
+  long long n0, n1;
+  chunk_of(N, C, c, n0, n1);
+  const z64* yr = y + (long long)r * (m + 1);
+  for (long long n = n0 + threadIdx.x; n < n1; n += 256) {
+    z64 acc = mk<double>(0.0, 0.0);
+    for (int i = 0; i < k; ++i) fma_(acc, Zt[i][r * N + n], yr[i]);
+    sigma[r * N + n] = acc;
+  }
+}
+
+// w = f - w and its chunk norms
+__global__ void __launch_bounds__(256) bresid_kernel(const z64* __restrict__ f, z64* __restrict__ w, long long N, int C,
+                                                     z64* __restrict__ nrm) {
+  __shared__ z64 red[8];
+  const int c = blockIdx.x, r = blockIdx.y;
+  long long n0, n1;
+  chunk_of(N, C, c, n0, n1);
+  z64 acc = mk<double>(0.0, 0.0);
+  for (long long n = n0 + threadIdx.x; n < n1; n += 256) {
+    const z64 d = f[r * N + n] - w[r * N + n];
+    w[r * N + n] = d;
+    fmac_(acc, d, d);
+  }
+  const z64 s = block_sum256(acc, red);
+  if (threadIdx.x == 0) nrm[(long long)r * C + c] = s;
+}
+
+// out[r] = sum_c nrm[r * C + c] (real part), fixed order
+__global__ void bsum_kernel(const z64* __restrict__ nrm, int C, double* __restrict__ out, int nb) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nb) return;
+  double s = 0.0;
+  for (int c = 0; c < C; ++c) s += nrm[(long long)r * C + c].re;
+  out[r] = s;
+}
+
+int solve_block(ls_handle* H, const z64* f, z64* sigma, int nb, ls_solve_info* info, int transpose, cudaStream_t st) {
+  const int mode = transpose ? CONV_TRANSPOSE : CONV_FORWARD;
+  const long long N = (long long)H->grid.nx * H->grid.ny;
+  const int m = H->opts.gmres_maxit;
+  // chunks per right-hand side: about eight blocks per SM over the block, at least 256 entries each
+  const int C = (int)std::max(1LL, std::min({(long long)kChunks, (8LL * H->nsm + nb - 1) / nb, (N + 255) / 256}));
+  const int ldp = m + 1;
+  // small state: H, cs, sn, g, y, dot partials, norm partials, states, slab tables, residual norms
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  };
+  const size_t oH = take(sizeof(z64) * nb * (size_t)(m + 1) * m), ocs = take(sizeof(z64) * nb * (size_t)m),
+               osn = take(sizeof(z64) * nb * (size_t)m), og = take(sizeof(z64) * nb * (size_t)(m + 1)),
+               oy = take(sizeof(z64) * nb * (size_t)(m + 1)), op = take(sizeof(z64) * nb * (size_t)ldp * C),
+               onr = take(sizeof(z64) * nb * (size_t)C), ost = take(sizeof(BState) * nb),
+               oVt = take(sizeof(z64*) * (size_t)(m + 1)), oZt = take(sizeof(z64*) * (size_t)m),
+               orn = take(sizeof(double) * nb), ow = take(sizeof(z64) * nb * (size_t)N);
+  int rc;
+  if (H->bgm_bytes < off) {
+    if (H->bgm) dfree(H->bgm);
+    H->bgm = nullptr;
+    H->bgm_bytes = 0;
+    if ((rc = dalloc(&H->bgm, off))) return rc;
+    H->bgm_bytes = off;
+  }
+  char* base = static_cast<char*>(H->bgm);
+  z64* Hm = reinterpret_cast<z64*>(base + oH);
+  z64* cs = reinterpret_cast<z64*>(base + ocs);
+  z64* sn = reinterpret_cast<z64*>(base + osn);
+  z64* g = reinterpret_cast<z64*>(base + og);
+  z64* y = reinterpret_cast<z64*>(base + oy);
+  z64* part = reinterpret_cast<z64*>(base + op);
+  z64* nrm = reinterpret_cast<z64*>(base + onr);
+  BState* bst = reinterpret_cast<BState*>(base + ost);
+  z64** Vt = reinterpret_cast<z64**>(base + oVt);
+  z64** Zt = reinterpret_cast<z64**>(base + oZt);
+  double* rn = reinterpret_cast<double*>(base + orn);
+  z64* w = reinterpret_cast<z64*>(base + ow);
+  // slabs of nb vectors: V_i at bslab[2 i], Z_i at bslab[2 i + 1]
+  const size_t slab = sizeof(z64) * (size_t)nb * N;
+  if (H->bslab_bytes < slab) {
+    for (void* p : H->bslab) dfree(p);
+    H->bslab.clear();
+    H->bslab_bytes = slab;
+  }
+  // pinned host scratch: the slab tables, the states, the residual norms
+  const size_t pin_tab = sizeof(z64*) * (size_t)(2 * m + 2), pin_st = sizeof(BState) * nb;
+  unsigned char* pin = static_cast<unsigned char*>(pinned_scratch(pin_tab + pin_st + sizeof(double) * nb + 64));
+  if (!pin) return LS_ENOMEM;
+  z64** hVt = reinterpret_cast<z64**>(pin);
+  z64** hZt = hVt + (m + 1);
+  BState* hst = reinterpret_cast<BState*>(pin + pin_tab);
+  double* hrn = reinterpret_cast<double*>(pin + pin_tab + pin_st);
+  int* derr = reinterpret_cast<int*>(pin + pin_tab + pin_st + sizeof(double) * nb);
+  auto slab_at = [&](int idx, z64** out) -> int {
+    while ((int)H->bslab.size() <= idx) {
+      void* p = nullptr;
+      int rc2 = dalloc(&p, slab);
+      if (rc2) return rc2;
+      H->bslab.push_back(p);
+    }
+    *out = static_cast<z64*>(H->bslab[idx]);
+    return LS_OK;
+  };
+  auto table = [&](z64** dtab, z64** htab, int i, z64* p) -> int {  // one entry, copied from pinned memory
+    htab[i] = p;
+    LS_CUDA_TRY(cudaMemcpyAsync(dtab + i, htab + i, sizeof(z64*), cudaMemcpyHostToDevice, st));
+    return LS_OK;
+  };
+  const dim3 grid(C, nb), g1((nb + 127) / 128);
+  LS_CUDA_TRY(cudaMemsetAsync(Hm, 0, sizeof(z64) * nb * (size_t)(m + 1) * m, st));
+  LS_CUDA_TRY(cudaMemsetAsync(g, 0, sizeof(z64) * nb * (size_t)(m + 1), st));
+  z64* V0;
+  if ((rc = slab_at(0, &V0)) || (rc = table(Vt, hVt, 0, V0))) return rc;
+  count_launch();
+  bnorm_kernel<<<grid, 256, 0, st>>>(f, N, C, nrm);
+  count_launch();
+  binit_kernel<<<nb, 1, 0, st>>>(nrm, C, bst, g, m + 1);
+  count_launch();
+  bscale_kernel<<<grid, 256, 0, st>>>(f, V0, N, C, bst);
+  int k_all = 0;
+  for (int j = 0; j < m; ++j) {
+    z64 *Vj = hVt[j], *Zj, *Vn;
+    if ((rc = slab_at(2 * j + 1, &Zj)) || (rc = table(Zt, hZt, j, Zj))) return rc;
+    if ((rc = slab_at(2 * j + 2, &Vn)) || (rc = table(Vt, hVt, j + 1, Vn))) return rc;
+    if ((rc = hbs_apply_block(H, Vj, Zj, nb, transpose, st))) return rc;
+    if ((rc = conv_apply(H, Zj, w, nb, mode, st))) return rc;
+    const int tk = prof_begin(st);
+    const z64* const* Vc = Vt;
+    for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+      count_launch();
+      bdots_kernel<<<grid, 256, 0, st>>>(Vc, j, w, N, C, ldp, part, bst);
+      count_launch();
+      bupdate_kernel<<<grid, 256, sizeof(z64) * (size_t)(j + 1), st>>>(Vc, j, w, N, C, ldp, part, Hm, m,
+                                                                       pass ? nrm : nullptr, bst);
+    }
+    count_launch();
+    bgivens_kernel<<<g1, 128, 0, st>>>(nrm, C, Hm, m, cs, sn, g, bst, j, H->opts.gmres_tol, nb);
+    count_launch();
+    bnormalize_kernel<<<grid, 256, 0, st>>>(w, Vn, N, C, nrm, bst);
+    prof_end(tk, PR_GMRES_BLOCK, st, 16.0 * N * nb * (4.0 * (j + 1) + 5.0), 16.0 * N * nb * (4.0 * (j + 1) + 1.0));
+    if ((rc = check_launch("block gmres iteration"))) return rc;
+    LS_CUDA_TRY(cudaMemcpyAsync(hst, bst, sizeof(BState) * nb, cudaMemcpyDeviceToHost, st));
+    LS_CUDA_TRY(cudaStreamSynchronize(st));
+    k_all = j + 1;
+    bool all = true;
+    for (int r = 0; r < nb; ++r) all = all && hst[r].done;
+    if (all) break;
+  }
+  (void)k_all;
+  count_launch();
+  bbacksolve_kernel<<<g1, 128, 0, st>>>(Hm, m, g, y, bst, nb);
+  count_launch();
+  bcombine_kernel<<<grid, 256, 0, st>>>(Zt, y, m, sigma, N, C, bst);
+  // true residuals ||f_r - A sigma_r|| / ||f_r||
+  if ((rc = conv_apply(H, sigma, w, nb, mode, st))) return rc;
+  count_launch();
+  bresid_kernel<<<grid, 256, 0, st>>>(f, w, N, C, nrm);
+  count_launch();
+  bsum_kernel<<<g1, 128, 0, st>>>(nrm, C, rn, nb);
+  LS_CUDA_TRY(cudaMemcpyAsync(hrn, rn, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+  LS_CUDA_TRY(cudaMemcpyAsync(hst, bst, sizeof(BState) * nb, cudaMemcpyDeviceToHost, st));
+  LS_CUDA_TRY(cudaMemcpyAsync(derr, H->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LS_CUDA_TRY(cudaStreamSynchronize(st));
+  if (*derr) return *derr;
+  if ((rc = check_launch("block gmres finish"))) return rc;
+  int worst = LS_OK;
+  for (int r = 0; r < nb; ++r) {
+    ls_solve_info inf;
+    const double fn = hst[r].fnorm;
+    inf.iterations = hst[r].k;
+    inf.resid_est = fn > 0.0 ? hst[r].resid : 0.0;
+    inf.resid_true = fn > 0.0 ? sqrt(hrn[r]) / fn : 0.0;
+    inf.converged = fn > 0.0 ? hst[r].resid <= H->opts.gmres_tol : 1;
+    if (!inf.converged) worst = LS_ENOCONV;
+    if (info) info[r] = inf;
+  }
+  return worst;
+}
 }  // namespace
 
 int gmres_solve(ls_handle* H, const z64* f, z64* sigma, int nrhs, ls_solve_info* info, int transpose,
@@ -463,8 +865,11 @@ int gmres_solve(ls_handle* H, const z64* f, z64* sigma, int nrhs, ls_solve_info*
   }
   host_mark("gmres_workspace");
   int worst = LS_OK;
-  for (int r = 0; r < nrhs; ++r) {
-    int rc = solve_one(H, f + r * N, sigma + r * N, info ? info + r : nullptr, transpose, st);
+  const int nbk = rhs_block_size(H, nrhs);
+  for (int r = 0; r < nrhs; r += nbk) {
+    const int nb = std::min(nbk, nrhs - r);
+    int rc = nb > 1 ? solve_block(H, f + r * N, sigma + r * N, nb, info ? info + r : nullptr, transpose, st)
+                    : solve_one(H, f + r * N, sigma + r * N, info ? info + r : nullptr, transpose, st);
     if (rc == LS_ENOCONV)
       worst = LS_ENOCONV;
     else if (rc)

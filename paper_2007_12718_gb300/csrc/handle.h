@@ -50,6 +50,8 @@ struct ls_handle {
   void* XBU = nullptr;          // per leaf s^2 x k_L: X B U (Algorithm 2, last step)
   void* work = nullptr;         // scratch for build and apply
   size_t work_bytes = 0;
+  void* bwork = nullptr;        // scratch of the apply to a block of right-hand sides (nb x work)
+  size_t bwork_bytes = 0;
   int* sync_buf = nullptr;      // grid-barrier counters + error flags
   int* d_err = nullptr;         // device status word (LS_ESINGULAR / LS_ETIMEOUT)
   cudaGraphExec_t apply_exec = nullptr;  // Algorithm 2 recorded as a CUDA graph
@@ -81,6 +83,12 @@ struct ls_handle {
   int gm_maxit = 0, gm_rhs = 0;
   void* gm = nullptr;
   size_t gm_bytes = 0;
+  // block GMRES (gmres_block.cu): small state, then one slab of nb vectors per
+  // Krylov vector V_j and preconditioned vector Z_j, allocated as iterations need them
+  void* bgm = nullptr;
+  size_t bgm_bytes = 0;
+  std::vector<void*> bslab;
+  size_t bslab_bytes = 0;
 };
 
 namespace ls {
@@ -135,6 +143,11 @@ int blocked_row_id(cx<R>* A, int m, int p, double eps, cudaStream_t st, cudaStre
 int hbs_build(ls_handle* H, cudaStream_t st, const LevelWait& wait_level = LevelWait());
 // q = M f, or q = M^T f when transpose (Algorithm 2 reversed, every factor transposed)
 int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, int transpose, cudaStream_t st);
+// the same for a block of nb right-hand sides at once (each factor read once for
+// the block, every product a batched GEMM with nb columns)
+int hbs_apply_block(ls_handle* H, const z64* f, z64* q, int nb, int transpose, cudaStream_t st);
+// right-hand sides per block of ls_apply / ls_solve (ls_opts.rhs_block; 0 = automatic)
+int rhs_block_size(const ls_handle* H, int nrhs);
 
 // tc_gemm.cu: complex FP32 GEMM on tcgen05 tensor cores (split: 0 tf32, 1 tf32x3)
 int tc_cgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, c32 alpha, const c32* A, int lda, long long sA,

@@ -366,6 +366,7 @@ void ls_default_opts(ls_opts* o) {
   o->top_uncompressed = 0;
   o->id_method = LS_ID_AUTO;
   o->wait_limit = 0;
+  o->rhs_block = 0;
 }
 
 const char* ls_strerror(int code) {
@@ -492,9 +493,12 @@ void ls_free(ls_handle* H) {
   f(H->XBUT);
   f(H->apply_ops_t);
   f(H->work);
+  f(H->bwork);
   f(H->sync_buf);
   f(H->d_err);
   f(H->gm);
+  f(H->bgm);
+  for (void* p : H->bslab) f(p);
   f(H->slots);
   f(H->apply_ops);
   f(H->apply_bar);
@@ -610,7 +614,8 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
       o.gmres_maxit < 1 || !(o.gmres_tol > 0) || (o.precision < LS_FP64 || o.precision > LS_TF32X3) ||
       o.precision == LS_TF32 ||
       o.proxy_width < 0 || o.merge_pivoting < 0 || o.merge_pivoting > 1 ||
-      o.top_uncompressed < 0 || o.id_method < LS_ID_AUTO || o.id_method > LS_ID_BLOCKED || o.wait_limit < 0) {
+      o.top_uncompressed < 0 || o.id_method < LS_ID_AUTO || o.id_method > LS_ID_BLOCKED || o.wait_limit < 0 ||
+      o.rhs_block < 0) {
     set_error("invalid ls_opts");
     return LS_EINVAL;
   }

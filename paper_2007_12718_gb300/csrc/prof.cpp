@@ -15,7 +15,8 @@ namespace {
 
 const char* kNames[PR_COUNT] = {"matvec_rows_fwd", "matvec_cols",  "matvec_rows_inv", "spectrum_setup",
                                 "cpqr_id",         "kernel_block", "leaf_build",      "merge_gemm",
-                                "merge_inverse",   "hbs_apply",    "gmres_orth"};
+                                "merge_inverse",   "hbs_apply",    "gmres_orth",      "hbs_apply_block",
+                                "gmres_block"};
 
 struct Pending {
   cudaEvent_t a, b;

@@ -19,6 +19,8 @@ enum ProfSlot {
   PR_MERGE_INV,
   PR_APPLY,
   PR_GMRES_ORTH,
+  PR_APPLY_BLOCK,
+  PR_GMRES_BLOCK,
   PR_COUNT
 };
 

@@ -113,6 +113,9 @@ WORKLOADS = {
     # N = 16,777,216, 400 wavelengths across
     "precond_n4096": dict(n=4096, kappa=800 * np.pi, b=lambda n: gaussian_family(n, 0), order_precond=4,
                           order_matvec=10, eps=1e-4, leaf=8),
+    # many incident fields on one factorisation: 256 plane waves, angles 2 pi j / 256
+    "multirhs_n512": dict(n=512, kappa=300.0, b=lambda n: gaussian_family(n, 0), order_precond=4,
+                          order_matvec=10, eps=1e-4, leaf=8, nrhs=256),
 }
 # The cavity sweep of Sec. 6.3 (preconditioned solver, 10 points per wavelength,
 # 100-point leaves): n = 80 2^j, kappa = 2 pi n / 10 (the domain is n / 10
