@@ -242,6 +242,67 @@ def adjoint_leg(ls, torch, dev, precision):
             "converged": bool(all(i["converged"] for i in infos))}
 
 
+# ------------------------------------------------------------ multi-RHS leg
+MRHS_TEXT = ("512x512 grid, kappa=300, b = seed-0 Gaussian family, 256 plane waves theta_j = 2 pi j/256 as one "
+             "block; one step = ls_build + ls_rhs_plane_wave + ls_solve (block GMRES to 1e-10 for every direction, "
+             "block apply: each factor read once per iteration for all 256) + ls_free")
+
+
+def multirhs_leg(ls, torch, dev, precision, flush, pk, tensor):
+    """Many incident fields on one factorisation, timed with CUDA events after one
+    warm-up step (inputs resident); the same with one right-hand side at a time for
+    comparison, and a profiled step for the phase rooflines."""
+    from paper_2007_12718_gb300 import inputs
+    w = inputs.WORKLOADS["multirhs_n512"]
+    n, kappa, nr = w["n"], w["kappa"], w["nrhs"]
+    h = 1.0 / n
+    th = inputs.plane_wave_angles(nr)
+    b = torch.from_numpy(w["b"](n)).to(dev)
+    F = torch.zeros(nr, n, n, dtype=torch.complex128, device=dev)
+    sig = torch.zeros_like(F)
+    stream = torch.cuda.current_stream()
+
+    def step(blk):
+        H = ls.ls_build(n, h, kappa, b, w["eps"], precision=precision, rhs_block=blk)
+        ls.ls_rhs_plane_wave(H, th, F)
+        infos = ls.ls_solve(H, F, sig)
+        ls.ls_free(H)
+        return infos
+
+    def timed(blk, profile=False):
+        if profile:
+            ls.ls_profile_reset()
+            ls.ls_profile_enable(True)
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = step(blk)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = None
+        if profile:
+            prof = ls.ls_profile_get()
+            ls.ls_profile_enable(False)
+        return e0.elapsed_time(e1) * 1e-3, infos, prof
+
+    step(0)
+    t, infos, _ = timed(0)
+    t1, infos1, _ = timed(1)
+    _, _, prof = timed(0, profile=True)
+    fams, phases, _ = rooflines(prof, pk, tensor, t, 1)
+    its = [i["iterations"] for i in infos]
+    return {"workload": "multirhs_n512", "description": MRHS_TEXT, "nrhs": nr, "ms_per_step": t * 1e3,
+            "value": nr * n * n / t / 1e6, "unit": "Mdof/s (directions x dofs, build + solve)",
+            "one_at_a_time": {"ms_per_step": t1 * 1e3, "value": nr * n * n / t1 / 1e6},
+            "iterations_min": min(its), "iterations_max": max(its),
+            "resid_true_max": max(i["resid_true"] for i in infos),
+            "converged": bool(all(i["converged"] for i in infos)),
+            "phase_rooflines": phases,
+            "kernel_rooflines": {k: {kk: (round(vv, 5) if isinstance(vv, float) else vv) for kk, vv in v.items()}
+                                 for k, v in fams.items()}}
+
+
 # ----------------------------------------------------------------------- ours
 class Leg:
     """One workload on the device: inputs resident, steps of build + solve + free."""
@@ -319,9 +380,9 @@ class Leg:
 PHASES = {
     "compress": ["cpqr_id"],
     "merges": ["leaf_build", "merge_gemm", "merge_inverse"],
-    "apply": ["hbs_apply"],
+    "apply": ["hbs_apply", "hbs_apply_block"],
     "matvec": ["matvec_rows_fwd", "matvec_cols", "matvec_rows_inv", "spectrum_setup"],
-    "gmres": ["gmres_orth"],
+    "gmres": ["gmres_orth", "gmres_block"],
 }
 
 
@@ -329,9 +390,9 @@ def family_peak(name, pk, tensor):
     """(bound, peak, unit, source) of a kernel family's roofline."""
     if name.startswith("matvec") or name == "spectrum_setup":
         return "alu", pk["fp64_tflops"], "TFLOP/s (FP64)", "of measured (ls_measure_peak FP64 FMA loop)"
-    if name in ("hbs_apply", "gmres_orth"):
+    if name in ("hbs_apply", "gmres_orth", "gmres_block"):
         return "hbm", pk["hbm_gbs"], "GB/s", pk["source"]
-    if name == "merge_gemm" and tensor:
+    if name in ("merge_gemm", "hbs_apply_block") and tensor:
         return ("tensor", pk["bf16_tflops"] / 2, "TFLOP/s (TF32 dense)",
                 pk["source"] + " bf16 x 1/2 (nominal tf32:bf16 ratio)")
     return "alu", pk["fp32_tflops"], "TFLOP/s (FP32)", "of measured (ls_measure_peak packed FP32 FMA loop)"
@@ -447,6 +508,8 @@ def run_ours(args, rank, world):
     adj = adjoint_leg(ls, torch, dev, PREC) if not args.no_adjoint else None
     if adj:
         secondary["differentiation_n512"] = adj
+    if not args.no_multirhs:
+        secondary["multirhs_n512"] = multirhs_leg(ls, torch, dev, PREC, flush, pk, tensor)
     cpu = cpu_baseline() if not args.no_cpu_baseline else None
     line = {"metric": METRIC, "value": value, "unit": "Mdof/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_mixed / args.steps * 1e3, "higher_is_better": True,
@@ -555,6 +618,8 @@ def main():
     ap.add_argument("--no-secondary", action="store_true", help="skip the 256^2 and 32^2 legs")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the differentiation workload (512x512 misfit gradient)")
+    ap.add_argument("--no-multirhs", action="store_true",
+                    help="skip the multi-right-hand-side workload (512x512, 256 plane waves in one block)")
     ap.add_argument("--top-uncompressed", type=int, default=1,
                     help="tree levels kept uncompressed at the top (U = I, the ID of full rank); measured faster at "
                          "2048^2 (1.20 s against 1.31 s per step) and at 256^2; 0 compresses every level")

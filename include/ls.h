@@ -79,6 +79,12 @@ typedef struct {
                          kernels) before it gives up and the call returns LS_ETIMEOUT; 0 =
                          default (2e7 polls, about a second).  After LS_ETIMEOUT the handle's
                          barrier state is spent: free the handle.                          */
+  int woodbury;       /* merges (Eq. 26): 1 = the Woodbury form where it pays (default): each
+                         level's sibling block is factored once, G ~ L R^T by a row ID at
+                         tolerance tol, and the merge inverts an r x r matrix instead of a
+                         k x k one (Sec. 4.1, the remark on the rank of G); used where
+                         k >= 192 and r <= k / 2.  0 = the Schur form everywhere; 2 = the
+                         Woodbury form at every level with r < k (small grids, tests).      */
   int rhs_block;      /* right-hand sides that ls_apply / ls_solve / ls_solve_transpose treat
                          as one block: the apply runs each product as a GEMM over the block
                          (every factor read once per block), GMRES keeps one Krylov space per
@@ -121,6 +127,8 @@ typedef struct {
   double bytes_apply;       /* algorithmic bytes read+written by one HBS apply */
   double factor_bytes;      /* device bytes held by the factors */
   int pivot_fallbacks;      /* merge levels whose check sent them to the row-pivoted inverse */
+  int sibling_ranks[32];    /* sibling_ranks[l] = r_l of the level's factored sibling block
+                               G ~ L R^T (Woodbury merge), 0 where the level keeps the Schur form */
   double probe_resid_max;   /* largest max_i |(Z W v - v)_i| over the merge inverses W = Z^-1
                                formed without interchanges, v a unit-modulus probe; W is accepted
                                when it is <= max(tol, 10 u k), u the unit roundoff, k the order */

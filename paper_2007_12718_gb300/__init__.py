@@ -50,7 +50,7 @@ class Opts(ctypes.Structure):
                 ("proxy_width", ctypes.c_int), ("precision", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("merge_pivoting", ctypes.c_int),
                 ("top_uncompressed", ctypes.c_int), ("id_method", ctypes.c_int), ("wait_limit", ctypes.c_int),
-                ("rhs_block", ctypes.c_int)]
+                ("woodbury", ctypes.c_int), ("rhs_block", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -62,7 +62,8 @@ class BuildInfo(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int), ("ranks", ctypes.c_int * 32), ("proxy_width", ctypes.c_int),
                 ("flops_build", ctypes.c_double), ("flops_compress", ctypes.c_double),
                 ("bytes_apply", ctypes.c_double), ("factor_bytes", ctypes.c_double),
-                ("pivot_fallbacks", ctypes.c_int), ("probe_resid_max", ctypes.c_double)]
+                ("pivot_fallbacks", ctypes.c_int), ("sibling_ranks", ctypes.c_int * 32),
+                ("probe_resid_max", ctypes.c_double)]
 
 
 class ProfileEntry(ctypes.Structure):
@@ -205,7 +206,8 @@ class Handle:
         return {"levels": bi.levels, "ranks": list(bi.ranks[: bi.levels + 1]), "proxy_width": bi.proxy_width,
                 "flops_build": bi.flops_build, "flops_compress": bi.flops_compress,
                 "bytes_apply": bi.bytes_apply, "factor_bytes": bi.factor_bytes,
-                "pivot_fallbacks": bi.pivot_fallbacks, "probe_resid_max": bi.probe_resid_max}
+                "pivot_fallbacks": bi.pivot_fallbacks, "probe_resid_max": bi.probe_resid_max,
+                "sibling_ranks": list(bi.sibling_ranks[: bi.levels + 1])}
 
 
 def default_opts():
@@ -216,13 +218,14 @@ def default_opts():
 
 def ls_build(n, h, kappa, b, tol, order_matvec=10, order_precond=4, leaf_side=8, proxy_width=0,
              precision=LS_FP32, gmres_maxit=100, gmres_tol=1e-10, x0=0.0, y0=0.0, ny=None, stream=None,
-             merge_pivoting=0, top_uncompressed=0, id_method=LS_ID_AUTO, wait_limit=0, rhs_block=0):
+             merge_pivoting=0, top_uncompressed=0, id_method=LS_ID_AUTO, wait_limit=0, rhs_block=0, woodbury=1):
     """Compress G and build the HBS inverse (Sec. 3.2, Algorithm 1); b is [ny][nx] float64.
-    rhs_block: right-hand sides per block of ls_apply / ls_solve (0 automatic, 1 one at a time)."""
+    rhs_block: right-hand sides per block of ls_apply / ls_solve (0 automatic, 1 one at a time).
+    woodbury: 1 = merges in the Woodbury form where the sibling block's rank is low, 0 = Schur form."""
     lib = load_library()
     g = Grid(n, n if ny is None else ny, h, x0, y0)
     o = Opts(order_matvec, order_precond, leaf_side, proxy_width, precision, gmres_maxit, gmres_tol,
-             merge_pivoting, top_uncompressed, id_method, wait_limit, rhs_block)
+             merge_pivoting, top_uncompressed, id_method, wait_limit, woodbury, rhs_block)
     bp, keep, _ = _ptr(b, np.float64)
     out = ctypes.c_void_p()
     _check(lib.ls_build(ctypes.byref(g), kappa, bp, tol, ctypes.byref(o), _stream(stream), ctypes.byref(out)),

@@ -1664,6 +1664,242 @@ int apply_prepare(ls_handle* H, cudaStream_t st) {
   return apply_persistent_init(H, st);
 }
 
+// ------------------------------------------------- Woodbury form of the merge
+// The sibling block of a level is close to low rank (its entries couple the
+// skeletons of two adjacent boxes, mostly through their shared side; Sec. 4.1,
+// the remark on Eq. (26)): G ~ L R^T with L, R of k x r, r ~ k/3, computed once
+// per level by a row ID of G (rows as candidates, tolerance eps in the
+// Frobenius norm): G ~ T G(J,:), L = T, R = G(J,:)^T.  Then G^T = R L^T, and
+// with A1 = S_a L, A2 = S_b R, C1 = L^T A1, C2 = R^T A2 (r x r),
+// M = (I - C2 C1)^-1, N = I + C1 M C2 = (I - C1 C2)^-1, the Woodbury identity
+// turns the Schur form X = [[I + Y1 W Y2, -Y1 W], [-W Y2, W]] (Y1 = S_a G,
+// Y2 = S_b G^T, W = (I - Y2 Y1)^-1) into
+//   W = I + A2 (C1 M) R^T,  -Y1 W = -A1 M R^T,  -W Y2 = -A2 N L^T,
+//   I + Y1 W Y2 = I + A1 (C2 N) L^T:
+// one inverse of order r instead of k, and ~6 k^2 r + 6 k r^2 flops of
+// products instead of ~6 k^3.  (The middle block of the paper's form carries
+// the children's S matrices: I + QP = [[I, R^T S_b R], [L^T S_a L, I]] in this
+// notation; C2 and C1 are its off-diagonal blocks.)
+
+// R[i][j] = G[J[j]][i]: the rows J of G, transposed (k x r).
+template <class R>
+__global__ void gather_rows_t_kernel(const cx<R>* __restrict__ G, int k, const int* __restrict__ J, int r,
+                                     cx<R>* __restrict__ Rt) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)k * r) return;
+  const int i = (int)(t / r), j = (int)(t % r);
+  Rt[t] = G[(long long)J[j] * k + i];
+}
+
+// Levels whose sibling block takes the Woodbury form: large enough that the
+// products dominate, and a rank at most half the order (else the Schur form
+// costs no more).
+constexpr int kWoodburyMinRank = 192;
+
+// L, R of level l's sibling block (once per level; lv.gr = -1 when the level
+// keeps the Schur form).
+template <class R>
+int sibling_lowrank(ls_handle* H, int l, cudaStream_t st) {
+  LevelData& lv = H->lev[l];
+  if (lv.gr != 0) return LS_OK;
+  const int k = lv.k;
+  const int mode = H->opts.woodbury;  // 0 off, 1 where it pays, 2 every level with r < k
+  if (mode == 0 || k == 0 || (mode == 1 && k < kWoodburyMinRank)) {
+    lv.gr = -1;
+    return LS_OK;
+  }
+  const size_t kk = (size_t)k * k;
+  cx<R>* A = nullptr;
+  cx<R>* T = nullptr;
+  int* dJ = nullptr;
+  int rc;
+  struct Free {
+    void** p[3];
+    ~Free() {
+      for (auto q : p)
+        if (*q) dfree(*q);
+    }
+  } fr{{(void**)&A, (void**)&T, (void**)&dJ}};
+  if ((rc = dalloc((void**)&A, sizeof(cx<R>) * kk)) || (rc = dalloc((void**)&T, sizeof(cx<R>) * kk))) return rc;
+  LS_CUDA_TRY(cudaMemcpyAsync(A, lv.Gsib, sizeof(cx<R>) * kk, cudaMemcpyDeviceToDevice, st));
+  int r = 0;
+  std::vector<int> J;
+  {
+    // the ID's interpolation matrix stays on the FP32 SIMT GEMMs (its residual
+    // decides the rank); the merges of a tf32x3 handle use the tensor cores
+    const int prev = g_tc_engine;
+    g_tc_engine = 0;
+    rc = blocked_row_id<R>(A, k, k, H->tol, st, nullptr, T, &r, &J);
+    g_tc_engine = prev;
+    if (rc) return rc;
+  }
+  if (r == 0 || (mode == 1 ? 2 * r > k : r >= k)) {
+    lv.gr = -1;
+    return LS_OK;
+  }
+  if ((rc = dalloc(&lv.GL, sizeof(cx<R>) * (size_t)k * r)) || (rc = dalloc(&lv.GR, sizeof(cx<R>) * (size_t)k * r)) ||
+      (rc = dalloc((void**)&dJ, sizeof(int) * r)))
+    return rc;
+  int* pin = static_cast<int*>(pinned_scratch(sizeof(int) * r));
+  if (!pin) return LS_ENOMEM;
+  memcpy(pin, J.data(), sizeof(int) * r);
+  LS_CUDA_TRY(cudaMemcpyAsync(dJ, pin, sizeof(int) * r, cudaMemcpyHostToDevice, st));
+  LS_CUDA_TRY(cudaMemcpyAsync(lv.GL, T, sizeof(cx<R>) * (size_t)k * r, cudaMemcpyDeviceToDevice, st));
+  count_launch();
+  gather_rows_t_kernel<R><<<(unsigned)(((long long)k * r + 255) / 256), 256, 0, st>>>(
+      reinterpret_cast<const cx<R>*>(lv.Gsib), k, dJ, r, reinterpret_cast<cx<R>*>(lv.GR));
+  if ((rc = check_launch("sibling low-rank factors"))) return rc;
+  LS_CUDA_TRY(cudaStreamSynchronize(st));  // pin and the temporaries are released on return
+  lv.gr = r;
+  H->flops_build += 8.0 * kk * r;
+  return LS_OK;
+}
+
+// Batched inverse of P matrices Z (n x n, row stride lda, stride sZ) in place:
+// without interchanges, probe-checked against a copy of Z, the row-pivoted
+// inverse as fallback (and as the only path when merge_pivoting = 1).  The
+// acceptance rule is the Schur form's: max_i |(Z W v - v)_i| <= max(tol, 10 u n).
+template <class R>
+int invert_checked(ls_handle* H, cx<R>* Z, int n, int lda, long long sZ, int P, void* scratch, size_t scratch_bytes,
+                   cudaStream_t st) {
+  if (H->opts.merge_pivoting == 1) return invert_batch<R>(H, Z, n, lda, sZ, P, scratch, scratch_bytes, st);
+  const long long nn = (long long)n * n;
+  cx<R>* Zc = reinterpret_cast<cx<R>*>(scratch);
+  cx<R>* pv = Zc + (size_t)P * nn;  // v (n), then u, t (P n each)
+  cx<R>* pu = pv + n;
+  cx<R>* pt = pu + (size_t)P * n;
+  void* scr2 = pt + (size_t)P * n;
+  const size_t used = sizeof(cx<R>) * ((size_t)P * nn + n + 2 * (size_t)P * n);
+  if (scratch_bytes < used + 256) {
+    set_last_error_text("merge inverse scratch too small");
+    return LS_EINVAL;
+  }
+  const size_t scr2_bytes = scratch_bytes - used;
+  int rc;
+  dim3 gc((unsigned)std::min<long long>(1024, (nn + 255) / 256), 1);
+  for (int b0 = 0; b0 < P; b0 += kMaxGridYZ) {
+    gc.y = std::min(kMaxGridYZ, P - b0);
+    count_launch();
+    copy_block_kernel<R><<<gc, 256, 0, st>>>(Zc + (size_t)b0 * nn, n, nn, Z + (size_t)b0 * sZ, lda, sZ, n, n);
+  }
+  LS_CUDA_TRY(cudaMemsetAsync(H->d_err + 2, 0, 2 * sizeof(int), st));
+  if (n <= gj_reg_max<R>()) {
+    if ((rc = invert_reg_nopiv<R>(Z, n, lda, sZ, P, H->d_err + 3, st))) return rc;
+  } else {
+    if ((rc = invert_batch_nopiv<R>(H, Z, n, lda, sZ, P, scr2, scr2_bytes, st))) return rc;
+  }
+  count_launch();
+  probe_vector_kernel<R><<<(n + 255) / 256, 256, 0, st>>>(pv, n);
+  gemv<R>(st, false, n, n, one<R>(), Z, lda, sZ, pv, 0, zero<R>(), pu, n, P);
+  gemv<R>(st, false, n, n, one<R>(), Zc, n, nn, pu, n, zero<R>(), pt, n, P);
+  count_launch();
+  probe_max_kernel<R><<<64, 256, 0, st>>>(pt, pv, n, (long long)P * n, H->d_err + 2);
+  int* flags = static_cast<int*>(pinned_scratch(2 * sizeof(int)));
+  if (!flags) return LS_ENOMEM;
+  LS_CUDA_TRY(cudaMemcpyAsync(flags, H->d_err + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  LS_CUDA_TRY(cudaStreamSynchronize(st));
+  float worst;
+  memcpy(&worst, &flags[0], sizeof(float));
+  H->probe_resid_max = std::max(H->probe_resid_max, (double)worst);
+  const double unit = sizeof(R) == 4 ? 5.96e-8 : 1.11e-16;
+  const double limit = std::max(H->tol, 10.0 * unit * n);
+  if (flags[1] != 0 || !((double)worst <= limit)) {
+    for (int b0 = 0; b0 < P; b0 += kMaxGridYZ) {
+      gc.y = std::min(kMaxGridYZ, P - b0);
+      count_launch();
+      copy_block_kernel<R><<<gc, 256, 0, st>>>(Z + (size_t)b0 * sZ, lda, sZ, Zc + (size_t)b0 * nn, n, nn, n, n);
+    }
+    if ((rc = invert_batch<R>(H, Z, n, lda, sZ, P, scr2, scr2_bytes, st))) return rc;
+    ++H->pivot_fallbacks;
+  }
+  return check_launch("merge inverse (checked)");
+}
+
+// X of the P parents of level l (children of rank kc, sibling factors of rank r)
+// in the Woodbury form above; the root keeps W, Y1 = A1 R^T, Y2 = A2 L^T.
+template <class R>
+int merge_woodbury(ls_handle* H, int l, cx<R>* X, const cx<R>* Sc, cudaStream_t st) {
+  const LevelData& ch = H->lev[l + 1];
+  const int P = 1 << l, kc = ch.k, n2 = 2 * kc, r = ch.gr;
+  const long long sX = (long long)n2 * n2, kk = (long long)kc * kc, kr = (long long)kc * r, rr = (long long)r * r;
+  const cx<R>* Lf = reinterpret_cast<const cx<R>*>(ch.GL);
+  const cx<R>* Rf = reinterpret_cast<const cx<R>*>(ch.GR);
+  // A1, A2, B (kc x r each), C1, C2, M, N, T (r x r each), then the inverse's scratch
+  const size_t inv_scr = sizeof(cx<R>) * (size_t)P * (2 * rr + 128 * 128 + 3 * 128 * (size_t)r + 4 * (size_t)r) +
+                         sizeof(int) * (size_t)P * (4 * (size_t)r + 256) + (1 << 16);
+  const size_t bytes = sizeof(cx<R>) * (size_t)P * (3 * kr + 5 * rr) + inv_scr;
+  void* work = nullptr;
+  int rc;
+  if ((rc = dalloc(&work, bytes))) return rc;
+  struct FreeOnExit {
+    void* p;
+    ~FreeOnExit() { dfree(p); }
+  } free_work{work};
+  cx<R>* A1 = reinterpret_cast<cx<R>*>(work);
+  cx<R>* A2 = A1 + (size_t)P * kr;
+  cx<R>* B = A2 + (size_t)P * kr;
+  cx<R>* C1 = B + (size_t)P * kr;
+  cx<R>* C2 = C1 + (size_t)P * rr;
+  cx<R>* Mm = C2 + (size_t)P * rr;
+  cx<R>* Nm = Mm + (size_t)P * rr;
+  cx<R>* Tm = Nm + (size_t)P * rr;
+  void* scratch = Tm + (size_t)P * rr;
+  cx<R>* X11 = X;
+  cx<R>* X12 = X + kc;
+  cx<R>* X21 = X + (size_t)kc * n2;
+  cx<R>* X22 = X21 + kc;
+  const cx<R> mone = mk<R>(R(-1), R(0)), on = one<R>(), ze = zero<R>();
+  auto ident = [&](cx<R>* D, int n, int ld, long long sD) {
+    const long long tot = (long long)P * n * n;
+    count_launch();
+    set_identity_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(D, n, ld, sD, P);
+  };
+  int tg = prof_begin(st);
+  gemm<R>(st, false, false, kc, r, kc, on, Sc, kc, 2 * kk, Lf, r, 0, ze, A1, r, kr, P);       // A1 = S_a L
+  gemm<R>(st, false, false, kc, r, kc, on, Sc + kk, kc, 2 * kk, Rf, r, 0, ze, A2, r, kr, P);  // A2 = S_b R
+  gemm<R>(st, true, false, r, r, kc, on, Lf, r, 0, A1, r, kr, ze, C1, r, rr, P);              // C1 = L^T A1
+  gemm<R>(st, true, false, r, r, kc, on, Rf, r, 0, A2, r, kr, ze, C2, r, rr, P);              // C2 = R^T A2
+  ident(Mm, r, r, rr);
+  gemm<R>(st, false, false, r, r, r, mone, C2, r, rr, C1, r, rr, on, Mm, r, rr, P);           // I - C2 C1
+  if ((rc = check_launch("woodbury merge"))) return rc;
+  prof_end(tg, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * (2.0 * kk + 4.0 * kr + 3.0 * rr),
+           P * 8.0 * (2.0 * kk * r + 2.0 * kr * r + (double)rr * r));
+  int ti = prof_begin(st);
+  if ((rc = invert_checked<R>(H, Mm, r, r, rr, P, scratch, inv_scr, st))) return rc;  // M
+  prof_end(ti, PR_MERGE_INV, st, sizeof(cx<R>) * P * 2.0 * rr, P * 8.0 * (double)rr * r);
+  if (l == 0) host_mark("root_inverse_checked");
+  tg = prof_begin(st);
+  double fl = 0;
+  gemm<R>(st, false, false, r, r, r, on, C1, r, rr, Mm, r, rr, ze, Tm, r, rr, P);              // C1 M
+  gemm<R>(st, false, false, kc, r, r, on, A2, r, kr, Tm, r, rr, ze, B, r, kr, P);              // A2 C1 M
+  ident(X22, kc, n2, sX);
+  gemm<R>(st, false, true, kc, kc, r, on, B, r, kr, Rf, r, 0, on, X22, n2, sX, P);             // W
+  fl += 8.0 * ((double)rr * r + (double)kr * r + (double)kk * r);
+  if (l == 0) {  // the root keeps Y1 = A1 R^T and Y2 = A2 L^T beside W
+    gemm<R>(st, false, true, kc, kc, r, on, A1, r, kr, Rf, r, 0, ze, X12, n2, sX, P);
+    gemm<R>(st, false, true, kc, kc, r, on, A2, r, kr, Lf, r, 0, ze, X21, n2, sX, P);
+    fl += 2 * 8.0 * (double)kk * r;
+    H->factor_bytes -= sizeof(cx<R>) * (double)kk;  // the X11 block is not read
+  } else {
+    gemm<R>(st, false, false, kc, r, r, on, A1, r, kr, Mm, r, rr, ze, B, r, kr, P);            // A1 M
+    gemm<R>(st, false, true, kc, kc, r, mone, B, r, kr, Rf, r, 0, ze, X12, n2, sX, P);         // -A1 M R^T
+    gemm<R>(st, false, false, r, r, r, on, Mm, r, rr, C2, r, rr, ze, Tm, r, rr, P);            // M C2
+    ident(Nm, r, r, rr);
+    gemm<R>(st, false, false, r, r, r, on, C1, r, rr, Tm, r, rr, on, Nm, r, rr, P);            // N
+    gemm<R>(st, false, false, kc, r, r, on, A2, r, kr, Nm, r, rr, ze, B, r, kr, P);            // A2 N
+    gemm<R>(st, false, true, kc, kc, r, mone, B, r, kr, Lf, r, 0, ze, X21, n2, sX, P);         // -A2 N L^T
+    gemm<R>(st, false, false, r, r, r, on, C2, r, rr, Nm, r, rr, ze, Tm, r, rr, P);            // C2 N
+    gemm<R>(st, false, false, kc, r, r, on, A1, r, kr, Tm, r, rr, ze, B, r, kr, P);            // A1 C2 N
+    ident(X11, kc, n2, sX);
+    gemm<R>(st, false, true, kc, kc, r, on, B, r, kr, Lf, r, 0, on, X11, n2, sX, P);           // I + A1 C2 N L^T
+    fl += 8.0 * (3.0 * rr * r + 3.0 * kr * r + 3.0 * (double)kk * r);
+  }
+  if ((rc = check_launch("woodbury merge blocks"))) return rc;
+  prof_end(tg, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * ((double)sX + 4.0 * kr), P * fl);
+  H->flops_build += P * (fl + 8.0 * (2.0 * kk * r + 2.0 * kr * r + 2.0 * (double)rr * r));
+  return LS_OK;
+}
+
 template <class R>
 int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
   const int L = H->L, n = H->s * H->s;
@@ -1714,31 +1950,38 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
   for (int l = L - 1; l >= 0; --l) {
     if ((rc = sibling_block(H, l + 1, st))) return rc;  // G of the two children (Eq. 15)
     if ((rc = level_transpose(H, l + 1, st))) return rc;  // U^T, G^T of level l + 1 for the apply
+    if ((rc = sibling_lowrank<R>(H, l + 1, st))) return rc;  // G = L R^T where the Woodbury form pays
     LevelData& lv = H->lev[l];
     const LevelData& ch = H->lev[l + 1];
     const int P = 1 << l, kc = ch.k, n2 = 2 * kc;
-    // scratch of X: the larger of (pivoted-inverse panels + pivots) and Y1, Y2, a
-    // copy of Z with the blocked-inverse panels (width <= 128); the S products get
-    // their own once this level's rank is known
-    size_t work_bytes;
-    {
+    const bool woodbury = kc > 0 && ch.gr > 0;
+    // scratch of X in the Schur form: the larger of (pivoted-inverse panels +
+    // pivots) and Y1, Y2, a copy of Z with the blocked-inverse panels (width <=
+    // 128); the S products get their own once this level's rank is known
+    size_t work_bytes = 0;
+    if (!woodbury) {
       const size_t Pz = (size_t)P, kz = (size_t)kc, nz = (size_t)n2;
       work_bytes = sizeof(cx<R>) * Pz * nz * nz + sizeof(int) * Pz * nz;
       work_bytes = std::max(work_bytes, sizeof(cx<R>) * Pz * (3 * kz * kz + 128 * 128 + 3 * 128 * kz) +
                                             sizeof(int) * Pz * (nz + 256) + 4096);
     }
     void* work = nullptr;
-    if ((rc = dalloc(&work, work_bytes))) return rc;
+    if (work_bytes && (rc = dalloc(&work, work_bytes))) return rc;
     struct FreeOnExit {
       void* p;
-      ~FreeOnExit() { dfree(p); }
+      ~FreeOnExit() {
+        if (p) dfree(p);
+      }
     } free_work{work};
     if ((rc = dalloc(&lv.X, sizeof(cx<R>) * (size_t)P * std::max(n2 * n2, 1)))) return rc;
     H->factor_bytes += sizeof(cx<R>) * (double)P * n2 * n2;
     cx<R>* X = reinterpret_cast<cx<R>*>(lv.X);
     const cx<R>* Sc = reinterpret_cast<const cx<R>*>(ch.S);
     const cx<R>* Gs = reinterpret_cast<const cx<R>*>(ch.Gsib);
-    if (kc > 0) {
+    if (woodbury) {
+      if (l == 0 && (rc = apply_prepare<R>(H, st))) return rc;
+      if ((rc = merge_woodbury<R>(H, l, X, Sc, st))) return rc;
+    } else if (kc > 0) {
       // Schur complement form of Eq. (26):  with Y1 = S_a G, Y2 = S_b G^T and
       // W = (I - Y2 Y1)^-1,  X = [[I + Y1 W Y2, -Y1 W], [-W Y2, W]].
       const long long sX = (long long)n2 * n2, kk = (long long)kc * kc;
@@ -1851,7 +2094,7 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
                  P * 3.0 * 8.0 * (double)kc * kc * kc);
       }
     }
-    H->flops_build += P * (6.0 * 8 * (double)kc * kc * kc + 8.0 * (double)kc * kc * kc);
+    if (!woodbury) H->flops_build += P * (6.0 * 8 * (double)kc * kc * kc + 8.0 * (double)kc * kc * kc);
     if (l == 0) break;
     if (wait_level && (rc = wait_level(l))) return rc;
     const int kp = lv.k;

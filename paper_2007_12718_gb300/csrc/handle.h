@@ -21,6 +21,9 @@ struct LevelData {
   void* GT = nullptr;    // k x k: Gsib transposed
   void* XT = nullptr;    // per node: X transposed (made on the first transposed apply)
   void* ST = nullptr;    // per node: S transposed (idem)
+  int gr = 0;            // rank of Gsib ~ GL GR^T (Woodbury merge); -1: the level keeps the Schur form
+  void* GL = nullptr;    // k x gr
+  void* GR = nullptr;    // k x gr
 };
 
 struct ls_handle {

@@ -366,6 +366,7 @@ void ls_default_opts(ls_opts* o) {
   o->top_uncompressed = 0;
   o->id_method = LS_ID_AUTO;
   o->wait_limit = 0;
+  o->woodbury = 1;
   o->rhs_block = 0;
 }
 
@@ -487,6 +488,8 @@ void ls_free(ls_handle* H) {
     f(lv.GT);
     f(lv.XT);
     f(lv.ST);
+    f(lv.GL);
+    f(lv.GR);
   }
   f(H->Gleaf);
   f(H->XBU);
@@ -615,7 +618,7 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
       o.precision == LS_TF32 ||
       o.proxy_width < 0 || o.merge_pivoting < 0 || o.merge_pivoting > 1 ||
       o.top_uncompressed < 0 || o.id_method < LS_ID_AUTO || o.id_method > LS_ID_BLOCKED || o.wait_limit < 0 ||
-      o.rhs_block < 0) {
+      o.rhs_block < 0 || o.woodbury < 0 || o.woodbury > 2) {
     set_error("invalid ls_opts");
     return LS_EINVAL;
   }
@@ -879,6 +882,7 @@ int ls_get_build_info(const ls_handle* H, ls_build_info* info) {
   info->bytes_apply = H->bytes_apply;
   info->factor_bytes = H->factor_bytes;
   info->pivot_fallbacks = H->pivot_fallbacks;
+  for (int l = 0; l <= H->L && l < 32; ++l) info->sibling_ranks[l] = std::max(0, H->lev[l].gr);
   info->probe_resid_max = H->probe_resid_max;
   return LS_OK;
 }

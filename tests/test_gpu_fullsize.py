@@ -58,7 +58,8 @@ def n256():
 
 @pytest.mark.parametrize("precision,kw", [(ls.LS_FP64, {}), (ls.LS_FP32, {}), (ls.LS_TF32X3, {}),
                                           (ls.LS_TF32X3, {"top_uncompressed": 1}),
-                                          (ls.LS_FP32, {"id_method": ls.LS_ID_GREEDY})])
+                                          (ls.LS_FP32, {"id_method": ls.LS_ID_GREEDY}),
+                                          (ls.LS_TF32X3, {"woodbury": 0}), (ls.LS_FP64, {"woodbury": 0})])
 def test_preconditioner_forward_error_n256(n256, precision, kw):
     n, eps = n256["n"], n256["eps"]
     H = ls.ls_build(n, 1.0 / n, n256["kappa"], n256["b"], eps, precision=precision, **kw)
