@@ -1751,7 +1751,7 @@ int sibling_lowrank(ls_handle* H, int l, cudaStream_t st) {
   if ((rc = check_launch("sibling low-rank factors"))) return rc;
   LS_CUDA_TRY(cudaStreamSynchronize(st));  // pin and the temporaries are released on return
   lv.gr = r;
-  H->flops_build += 8.0 * kk * r;
+  H->flops_sibling += 8.0 * kk * r;
   return LS_OK;
 }
 
@@ -1901,7 +1901,7 @@ int merge_woodbury(ls_handle* H, int l, cx<R>* X, const cx<R>* Sc, cudaStream_t 
 }
 
 template <class R>
-int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
+int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const LevelWait& wait_sibling) {
   const int L = H->L, n = H->s * H->s;
   int rc;
   struct EngineScope {
@@ -1948,9 +1948,13 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
   // needs this level's U, so the wait for compression level l sits before it
   // and X of level l is formed while level l is being compressed.
   for (int l = L - 1; l >= 0; --l) {
-    if ((rc = sibling_block(H, l + 1, st))) return rc;  // G of the two children (Eq. 15)
-    if ((rc = level_transpose(H, l + 1, st))) return rc;  // U^T, G^T of level l + 1 for the apply
-    if ((rc = sibling_lowrank<R>(H, l + 1, st))) return rc;  // G = L R^T where the Woodbury form pays
+    // G of the two children (Eq. 15), U^T and G^T for the apply, G = L R^T where the
+    // Woodbury form pays: made here, or by the pipeline's sibling worker
+    if (wait_sibling) {
+      if ((rc = wait_sibling(l + 1))) return rc;
+    } else if ((rc = sibling_prepare(H, l + 1, st))) {
+      return rc;
+    }
     LevelData& lv = H->lev[l];
     const LevelData& ch = H->lev[l + 1];
     const int P = 1 << l, kc = ch.k, n2 = 2 * kc;
@@ -2095,6 +2099,11 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
       }
     }
     if (!woodbury) H->flops_build += P * (6.0 * 8 * (double)kc * kc * kc + 8.0 * (double)kc * kc * kc);
+    {
+      char mark[48];
+      snprintf(mark, sizeof(mark), "merge_X_level_%d", l);
+      host_mark(mark);
+    }
     if (l == 0) break;
     if (wait_level && (rc = wait_level(l))) return rc;
     const int kp = lv.k;
@@ -3401,8 +3410,16 @@ int hbs_apply_block(ls_handle* H, const z64* f, z64* q, int nb, int transpose, c
   return rc;
 }
 
-int hbs_build(ls_handle* H, cudaStream_t st, const LevelWait& wait_level) {
-  return H->prec == LS_FP64 ? build_t<double>(H, st, wait_level) : build_t<float>(H, st, wait_level);
+int hbs_build(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const LevelWait& wait_sibling) {
+  return H->prec == LS_FP64 ? build_t<double>(H, st, wait_level, wait_sibling)
+                            : build_t<float>(H, st, wait_level, wait_sibling);
+}
+
+int sibling_prepare(ls_handle* H, int l, cudaStream_t st) {
+  int rc;
+  if ((rc = sibling_block(H, l, st))) return rc;
+  if ((rc = level_transpose(H, l, st))) return rc;
+  return H->prec == LS_FP64 ? sibling_lowrank<double>(H, l, st) : sibling_lowrank<float>(H, l, st);
 }
 
 int simt_cgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, c32 alpha, const c32* A, int lda, long long sA,

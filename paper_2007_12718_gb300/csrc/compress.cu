@@ -1383,6 +1383,11 @@ int compress_t(ls_handle* H, cudaStream_t st, const LevelDone& level_done, cudaS
       LS_CUDA_TRY(cudaStreamWaitEvent(su, e, 0));
       cudaEventDestroy(e);
     }
+    {
+      char mark[48];
+      snprintf(mark, sizeof(mark), "compressed_level_%d", l);
+      host_mark(mark);
+    }
     if (level_done) level_done(l);
     return LS_OK;
   };

@@ -70,6 +70,7 @@ struct ls_handle {
   int apply_nops_t = 0, apply_phases_t = 0;
   std::vector<int> apply_phase_end_t;  // host copy: index of the last operation of each phase
   double flops_build = 0, flops_compress = 0, bytes_apply = 0, factor_bytes = 0;
+  double flops_sibling = 0;     // the sibling blocks' low-rank factorisations (counted in flops_build)
   int pivot_fallbacks = 0;      // merge levels that needed the row-pivoted inverse
   double probe_resid_max = 0;   // largest probe residual max_i |(Z W v - v)_i| of the merge inverses
   long long spin_limit = ls::kSpinLimit;  // polls of a bounded device wait (ls_opts.wait_limit)
@@ -143,7 +144,12 @@ int blocked_row_id(cx<R>* A, int m, int p, double eps, cudaStream_t st, cudaStre
                    std::vector<int>* hp);
 
 // build.cu (Algorithm 1) and apply (Algorithm 2)
-int hbs_build(ls_handle* H, cudaStream_t st, const LevelWait& wait_level = LevelWait());
+// wait_level(l): the compression of level l is done; wait_sibling(l): level l's
+// sibling block, U^T, G^T and low-rank factors are made (sibling_prepare, by the
+// caller's worker); an empty hook makes the build wait or make them itself.
+int hbs_build(ls_handle* H, cudaStream_t st, const LevelWait& wait_level = LevelWait(),
+              const LevelWait& wait_sibling = LevelWait());
+int sibling_prepare(ls_handle* H, int l, cudaStream_t st);
 // q = M f, or q = M^T f when transpose (Algorithm 2 reversed, every factor transposed)
 int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, int transpose, cudaStream_t st);
 // the same for a block of nb right-hand sides at once (each factor read once for

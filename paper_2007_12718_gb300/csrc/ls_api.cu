@@ -538,12 +538,41 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
   LS_CUDA_TRY(cudaEventRecord(ev[0], st));  // kernel table, spectrum, b: ready for both stages
   LS_CUDA_TRY(cudaStreamWaitEvent(sc, ev[0], 0));
   LS_CUDA_TRY(cudaStreamWaitEvent(sm, ev[0], 0));
+  // ss: each level's sibling block, transposes and low-rank factors (sibling_prepare),
+  // made by a third thread as soon as the level is compressed
+  cudaStream_t ss = nullptr;
+  LS_CUDA_TRY(cudaStreamCreateWithPriority(&ss, cudaStreamNonBlocking, prio_low));
+  std::vector<cudaEvent_t> evs(L + 1, nullptr);
+  for (auto& e : evs) LS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   std::mutex mu;
   std::condition_variable cv;
-  int ready = L + 1;  // the lowest level index compressed so far (levels finish from L down to 1)
+  int ready = L + 1;      // the lowest level index compressed so far (levels finish from L down to 1)
+  int sib_ready = L + 1;  // the lowest level whose sibling data are made
   bool abort = false;
-  int mrc = LS_OK;
-  std::string merr;
+  int mrc = LS_OK, src = LS_OK;
+  std::string merr, serr;
+  std::thread sibling([&] {
+    ls::StreamScope scope(ss);
+    for (int l = L; l >= 1; --l) {
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return abort || ready <= l; });
+        if (abort) return;
+      }
+      int r = cudaStreamWaitEvent(ss, ev[l], 0) == cudaSuccess ? ls::sibling_prepare(H, l, ss) : LS_ECUDA;
+      if (!r && cudaEventRecord(evs[l], ss) != cudaSuccess) r = LS_ECUDA;
+      std::lock_guard<std::mutex> lk(mu);
+      if (r) {
+        src = r;
+        serr = ls_last_error();
+        abort = true;
+      } else {
+        sib_ready = l;
+      }
+      cv.notify_all();
+      if (r) return;
+    }
+  });
   std::thread merger([&] {
     ls::StreamScope scope(sm);
     auto wait_level = [&](int level) -> int {
@@ -555,10 +584,21 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
       LS_CUDA_TRY(cudaStreamWaitEvent(sm, ev[level], 0));
       return LS_OK;
     };
-    int r = ls::hbs_build(H, sm, wait_level);
+    auto wait_sibling = [&](int level) -> int {
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return abort || sib_ready <= level; });
+        if (abort) return LS_EINVAL;
+      }
+      LS_CUDA_TRY(cudaStreamWaitEvent(sm, evs[level], 0));
+      return LS_OK;
+    };
+    int r = ls::hbs_build(H, sm, wait_level, wait_sibling);
     if (r) merr = ls_last_error();
     std::lock_guard<std::mutex> lk(mu);
     mrc = r;
+    if (r) abort = true;
+    cv.notify_all();
   });
   auto level_done = [&](int level) {
     cudaEventRecord(ev[level], su);  // su has passed sc's work of this level (compress orders it)
@@ -581,7 +621,12 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
   }
   cv.notify_all();
   merger.join();
+  sibling.join();
   ls::host_mark("merges_joined");
+  if (!rc && src) {  // the sibling worker's failure aborted the merges
+    rc = src;
+    set_error(serr.c_str());
+  }
   if (!rc && mrc) {
     rc = mrc;
     set_error(merr.c_str());
@@ -592,10 +637,14 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
   cudaStreamWaitEvent(st, ev[L + 3], 0);
   cudaStreamWaitEvent(st, ev[L + 1], 0);
   cudaStreamWaitEvent(st, ev[L + 2], 0);
+  cudaEventRecord(evs[0], ss);
+  cudaStreamWaitEvent(st, evs[0], 0);
   for (auto& e : ev) cudaEventDestroy(e);
+  for (auto& e : evs) cudaEventDestroy(e);
   cudaStreamDestroy(sm);
   cudaStreamDestroy(sc);
   cudaStreamDestroy(su);
+  cudaStreamDestroy(ss);
   return rc;
 }
 
@@ -877,7 +926,7 @@ int ls_get_build_info(const ls_handle* H, ls_build_info* info) {
   info->levels = H->L;
   for (int l = 0; l <= H->L && l < 32; ++l) info->ranks[l] = H->lev[l].k;
   info->proxy_width = H->ring;
-  info->flops_build = H->flops_build;
+  info->flops_build = H->flops_build + H->flops_sibling;
   info->flops_compress = H->flops_compress;
   info->bytes_apply = H->bytes_apply;
   info->factor_bytes = H->factor_bytes;
