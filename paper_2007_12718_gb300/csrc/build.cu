@@ -1695,6 +1695,34 @@ __global__ void gather_rows_t_kernel(const cx<R>* __restrict__ G, int k, const i
 // products dominate, and a rank at most half the order (else the Schur form
 // costs no more).
 constexpr int kWoodburyMinRank = 192;
+// Sibling blocks from this order on are factored from a random sketch (Sec. 2.1,
+// the randomised ID): the row ID of Y = G Omega (k x s, Omega Gaussian) selects
+// the same kind of skeleton rows J and interpolation matrix T as the ID of G
+// itself (Y's rows are G's rows mixed by one fixed matrix), at s / k of the cost.
+constexpr int kSketchMinRank = 1024;
+
+// splitmix64 (Steele, Lea and Flood, 2014): a counter-based generator, one
+// 64-bit output per index.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Om[t] = complex Gaussian (Box-Muller on two 24-bit uniforms of splitmix64(seed + t)).
+template <class R>
+__global__ void gaussian_kernel(cx<R>* __restrict__ Om, long long n, unsigned long long seed) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const unsigned long long h = splitmix64(seed + (unsigned long long)t);
+  const float u1 = ((float)(h >> 40) + 1.0f) * (1.0f / 16777216.0f);  // (0, 1]
+  const float u2 = (float)(h & 0xFFFFFFull) * (1.0f / 16777216.0f);   // [0, 1)
+  const float rad = sqrtf(-2.0f * logf(u1));
+  float sn, cs;
+  sincospif(2.0f * u2, &sn, &cs);
+  Om[t] = mk<R>((R)(rad * cs), (R)(rad * sn));
+}
 
 // L, R of level l's sibling block (once per level; lv.gr = -1 when the level
 // keeps the Schur form).
@@ -1720,18 +1748,57 @@ int sibling_lowrank(ls_handle* H, int l, cudaStream_t st) {
         if (*q) dfree(*q);
     }
   } fr{{(void**)&A, (void**)&T, (void**)&dJ}};
-  if ((rc = dalloc((void**)&A, sizeof(cx<R>) * kk)) || (rc = dalloc((void**)&T, sizeof(cx<R>) * kk))) return rc;
-  LS_CUDA_TRY(cudaMemcpyAsync(A, lv.Gsib, sizeof(cx<R>) * kk, cudaMemcpyDeviceToDevice, st));
+  if ((rc = dalloc((void**)&T, sizeof(cx<R>) * kk))) return rc;
   int r = 0;
   std::vector<int> J;
-  {
-    // the ID's interpolation matrix stays on the FP32 SIMT GEMMs (its residual
-    // decides the rank); the merges of a tf32x3 handle use the tensor cores
-    const int prev = g_tc_engine;
+  // sketch width: from the ranks of the two levels below (the cuts alternate in
+  // direction), scaled to this order, with margin; no sketch where it would not
+  // be well below k
+  int sw = 0;
+  if (k >= kSketchMinRank) {
+    double pred = 0;
+    for (int d = 1; d <= 2 && l + d <= H->L; ++d) {
+      const LevelData& lo = H->lev[l + d];
+      if (lo.gr > 0 && lo.k > 0) pred = std::max(pred, (double)lo.gr * k / lo.k);
+    }
+    if (pred > 0) sw = (int)std::min<double>(k, 1.2 * pred + 64);
+    if (sw > 0.6 * k) sw = 0;
+  }
+  const int prev_engine = g_tc_engine;
+  if (sw > 0) {
+    cx<R>* Om = nullptr;
+    cx<R>* Y = nullptr;
+    const long long ks = (long long)k * sw;
+    if ((rc = dalloc((void**)&Om, sizeof(cx<R>) * ks)) || (rc = dalloc((void**)&Y, sizeof(cx<R>) * ks))) {
+      if (Om) dfree(Om);
+      return rc;
+    }
+    count_launch();
+    gaussian_kernel<R><<<(unsigned)((ks + 255) / 256), 256, 0, st>>>(Om, ks, 0x5EED0000ull + (unsigned long long)l);
+    // the sketch on the handle's GEMM engine (its rounding is far below the tolerance);
+    // the ID itself keeps the FP32 SIMT GEMMs (its residual decides the rank)
+    g_tc_engine = H->prec == LS_TF32X3 ? 2 : 0;
+    gemm<R>(st, false, false, k, sw, k, one<R>(), reinterpret_cast<const cx<R>*>(lv.Gsib), k, 0, Om, sw, 0, zero<R>(),
+            Y, sw, 0, 1);
+    g_tc_engine = 0;
+    rc = check_launch("sibling sketch");
+    if (!rc) rc = blocked_row_id<R>(Y, k, sw, H->tol, st, nullptr, T, &r, &J);
+    g_tc_engine = prev_engine;
+    LS_CUDA_TRY(cudaStreamSynchronize(st));
+    dfree(Om);
+    dfree(Y);
+    if (rc) return rc;
+    H->flops_sibling += 8.0 * ks * k + 8.0 * ks * r;
+    if (r > sw - 32) sw = 0;  // the sketch was too narrow for the rank: the ID of G itself
+  }
+  if (sw == 0) {
+    if ((rc = dalloc((void**)&A, sizeof(cx<R>) * kk))) return rc;
+    LS_CUDA_TRY(cudaMemcpyAsync(A, lv.Gsib, sizeof(cx<R>) * kk, cudaMemcpyDeviceToDevice, st));
     g_tc_engine = 0;
     rc = blocked_row_id<R>(A, k, k, H->tol, st, nullptr, T, &r, &J);
-    g_tc_engine = prev;
+    g_tc_engine = prev_engine;
     if (rc) return rc;
+    H->flops_sibling += 8.0 * kk * r;
   }
   if (r == 0 || (mode == 1 ? 2 * r > k : r >= k)) {
     lv.gr = -1;
@@ -1751,7 +1818,6 @@ int sibling_lowrank(ls_handle* H, int l, cudaStream_t st) {
   if ((rc = check_launch("sibling low-rank factors"))) return rc;
   LS_CUDA_TRY(cudaStreamSynchronize(st));  // pin and the temporaries are released on return
   lv.gr = r;
-  H->flops_sibling += 8.0 * kk * r;
   return LS_OK;
 }
 

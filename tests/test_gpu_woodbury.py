@@ -93,3 +93,22 @@ def test_woodbury_default_engages_at_256():
     assert top and all(0 < sr[l] <= rk[l] // 2 for l in top), (sr, rk)
     assert all(sr[l] == 0 for l in range(1, info["levels"] + 1) if rk[l] < 192)
     ls.ls_free(H)
+
+
+@pytest.mark.slow
+def test_sketched_sibling_factors_at_2048():
+    """The 2048^2 headline workload: the sibling blocks of order >= 1024 are factored
+    from a Gaussian sketch (Sec. 2.1); ranks stay within the Woodbury range and the
+    mixed solve still reaches 1e-10 in the headline's iteration count (7-8)."""
+    w = inputs.WORKLOADS["precond_n2048"]
+    n = w["n"]
+    H = ls.ls_build(n, 1.0 / n, w["kappa"], dev(w["b"](n)), w["eps"], precision=ls.LS_TF32X3, top_uncompressed=1)
+    info = H.info()
+    sr, rk = info["sibling_ranks"], info["ranks"]
+    assert all(0 < sr[l] <= rk[l] // 2 for l in range(1, 6)), (sr, rk)
+    f = ls.ls_rhs_plane_wave(H, [0.0], zeros(n, n))
+    sig = zeros(n, n)
+    si = ls.ls_solve(H, f, sig)[0]
+    assert si["converged"] and si["resid_true"] <= 1e-10 and si["iterations"] <= 8, si
+    assert info["pivot_fallbacks"] == 0
+    ls.ls_free(H)
