@@ -85,6 +85,13 @@ typedef struct {
                          k x k one (Sec. 4.1, the remark on the rank of G); used where
                          k >= 192 and r <= k / 2.  0 = the Schur form everywhere; 2 = the
                          Woodbury form at every level with r < k (small grids, tests).      */
+  int reuse_compression; /* 1 = keep the compression (per-level skeletons, U, sibling blocks and
+                         their factors) in a process-wide cache and take it from there when a
+                         later ls_build on the same device has the same kappa, h, grid, leaf
+                         side, tol, order_precond, ring, precision, top_uncompressed,
+                         id_method and woodbury: it does not depend on b (Sec. 3.2), so only
+                         the leaf build and the merges run.  0 = compress every time
+                         (default).  ls_compression_cache_clear releases the cache.       */
   int rhs_block;      /* right-hand sides that ls_apply / ls_solve / ls_solve_transpose treat
                          as one block: the apply runs each product as a GEMM over the block
                          (every factor read once per block), GMRES keeps one Krylov space per
@@ -132,6 +139,9 @@ typedef struct {
   double probe_resid_max;   /* largest max_i |(Z W v - v)_i| over the merge inverses W = Z^-1
                                formed without interchanges, v a unit-modulus probe; W is accepted
                                when it is <= max(tol, 10 u k), u the unit roundoff, k the order */
+  int compression_reused;   /* 1 if the compression came from the cache (reuse_compression)
+                               or from a file (ls_load) */
+  int nx, ny;               /* the grid */
 } ls_build_info;
 
 typedef struct ls_handle ls_handle; /* opaque, library-owned */
@@ -271,6 +281,24 @@ int ls_sync(ls_handle* h, void* stream);
 
 /* ls_build_info -- ranks, flop and byte counts of the built handle. */
 int ls_get_build_info(const ls_handle* h, ls_build_info* info);
+
+/* ls_compression_cache_clear -- release every compression kept by
+ * reuse_compression (device memory of every device that holds one). */
+void ls_compression_cache_clear(void);
+
+/* ls_save -- write a built handle to the file `path`: the inputs (grid, kappa,
+ * tol, options, b) and every factor (per level the skeleton, U, the sibling
+ * block and its low-rank factors, X and S; X B U of the leaves), so that
+ * ls_load can restore it without compressing or merging.  Binary, this
+ * library's layout (little-endian, native sizes), version-checked.
+ * Synchronises the stream.  LS_EINVAL if the file cannot be written. */
+int ls_save(const ls_handle* h, const char* path, void* stream);
+
+/* ls_load -- a handle from a file written by ls_save, on the current device:
+ * the set-up of ls_build (kernel table, FFT spectrum, b checked) and the
+ * stored factors uploaded; the apply and solve calls then behave as on the
+ * saved handle.  LS_EINVAL for a missing, truncated or foreign file. */
+int ls_load(const char* path, void* stream, ls_handle** out);
 
 /* ls_free -- release every resource of the handle (NULL is allowed). */
 void ls_free(ls_handle* h);

@@ -50,7 +50,7 @@ class Opts(ctypes.Structure):
                 ("proxy_width", ctypes.c_int), ("precision", ctypes.c_int), ("gmres_maxit", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("merge_pivoting", ctypes.c_int),
                 ("top_uncompressed", ctypes.c_int), ("id_method", ctypes.c_int), ("wait_limit", ctypes.c_int),
-                ("woodbury", ctypes.c_int), ("rhs_block", ctypes.c_int)]
+                ("woodbury", ctypes.c_int), ("reuse_compression", ctypes.c_int), ("rhs_block", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -63,7 +63,8 @@ class BuildInfo(ctypes.Structure):
                 ("flops_build", ctypes.c_double), ("flops_compress", ctypes.c_double),
                 ("bytes_apply", ctypes.c_double), ("factor_bytes", ctypes.c_double),
                 ("pivot_fallbacks", ctypes.c_int), ("sibling_ranks", ctypes.c_int * 32),
-                ("probe_resid_max", ctypes.c_double)]
+                ("probe_resid_max", ctypes.c_double), ("compression_reused", ctypes.c_int),
+                ("nx", ctypes.c_int), ("ny", ctypes.c_int)]
 
 
 class ProfileEntry(ctypes.Structure):
@@ -108,6 +109,12 @@ def load_library(path=LIB_PATH):
     lib.ls_get_build_info.restype = ip
     lib.ls_free.argtypes = [vp]
     lib.ls_free.restype = None
+    lib.ls_save.argtypes = [vp, ctypes.c_char_p, vp]
+    lib.ls_save.restype = ip
+    lib.ls_load.argtypes = [ctypes.c_char_p, vp, ctypes.POINTER(vp)]
+    lib.ls_load.restype = ip
+    lib.ls_compression_cache_clear.argtypes = []
+    lib.ls_compression_cache_clear.restype = None
     lib.ls_strerror.argtypes = [ip]
     lib.ls_strerror.restype = ctypes.c_char_p
     lib.ls_last_error.argtypes = []
@@ -207,7 +214,8 @@ class Handle:
                 "flops_build": bi.flops_build, "flops_compress": bi.flops_compress,
                 "bytes_apply": bi.bytes_apply, "factor_bytes": bi.factor_bytes,
                 "pivot_fallbacks": bi.pivot_fallbacks, "probe_resid_max": bi.probe_resid_max,
-                "sibling_ranks": list(bi.sibling_ranks[: bi.levels + 1])}
+                "sibling_ranks": list(bi.sibling_ranks[: bi.levels + 1]),
+                "compression_reused": bool(bi.compression_reused)}
 
 
 def default_opts():
@@ -218,19 +226,41 @@ def default_opts():
 
 def ls_build(n, h, kappa, b, tol, order_matvec=10, order_precond=4, leaf_side=8, proxy_width=0,
              precision=LS_FP32, gmres_maxit=100, gmres_tol=1e-10, x0=0.0, y0=0.0, ny=None, stream=None,
-             merge_pivoting=0, top_uncompressed=0, id_method=LS_ID_AUTO, wait_limit=0, rhs_block=0, woodbury=1):
+             merge_pivoting=0, top_uncompressed=0, id_method=LS_ID_AUTO, wait_limit=0, rhs_block=0, woodbury=1, reuse_compression=0):
     """Compress G and build the HBS inverse (Sec. 3.2, Algorithm 1); b is [ny][nx] float64.
     rhs_block: right-hand sides per block of ls_apply / ls_solve (0 automatic, 1 one at a time).
-    woodbury: 1 = merges in the Woodbury form where the sibling block's rank is low, 0 = Schur form."""
+    woodbury: 1 = merges in the Woodbury form where the sibling block's rank is low, 0 = Schur form.
+    reuse_compression: 1 = take the compression from (and keep it in) the process-wide cache."""
     lib = load_library()
     g = Grid(n, n if ny is None else ny, h, x0, y0)
     o = Opts(order_matvec, order_precond, leaf_side, proxy_width, precision, gmres_maxit, gmres_tol,
-             merge_pivoting, top_uncompressed, id_method, wait_limit, woodbury, rhs_block)
+             merge_pivoting, top_uncompressed, id_method, wait_limit, woodbury, reuse_compression, rhs_block)
     bp, keep, _ = _ptr(b, np.float64)
     out = ctypes.c_void_p()
     _check(lib.ls_build(ctypes.byref(g), kappa, bp, tol, ctypes.byref(o), _stream(stream), ctypes.byref(out)),
            "ls_build")
     return Handle(out, g.nx * g.ny)
+
+
+def ls_save(handle, path, stream=None):
+    """Write the built handle (inputs and every factor) to a file."""
+    _check(load_library().ls_save(handle.ptr, str(path).encode(), _stream(stream)), "ls_save")
+
+
+def ls_load(path, stream=None):
+    """A handle restored from a file of ls_save, on the current device."""
+    lib = load_library()
+    out = ctypes.c_void_p()
+    _check(lib.ls_load(str(path).encode(), _stream(stream), ctypes.byref(out)), "ls_load")
+    H = Handle(out, 0)
+    bi = BuildInfo()
+    _check(lib.ls_get_build_info(H.ptr, ctypes.byref(bi)), "ls_get_build_info")
+    H.n = bi.nx * bi.ny
+    return H
+
+
+def ls_compression_cache_clear():
+    load_library().ls_compression_cache_clear()
 
 
 def _nrhs(handle, nelem):

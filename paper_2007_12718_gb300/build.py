@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libls.so")
 SOURCES = ["ls_api.cu", "conv.cu", "compress.cu", "build.cu", "gmres.cu", "tc_gemm.cu", "adjoint.cu", "id_blocked.cu",
-           "peaks.cu", "quad.cpp", "prof.cpp"]
+           "peaks.cu", "persist.cu", "quad.cpp", "prof.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

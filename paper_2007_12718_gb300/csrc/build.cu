@@ -1966,6 +1966,18 @@ int merge_woodbury(ls_handle* H, int l, cx<R>* X, const cx<R>* Sc, cudaStream_t 
   return LS_OK;
 }
 
+// Bytes of one apply (Algorithm 2): every factor once, the X of levels L-1..1
+// a second time (the upward and the downward pass both apply it), the grid vectors.
+template <class R>
+void apply_bytes(ls_handle* H) {
+  double fb = H->factor_bytes;
+  for (int l = 1; l <= H->L - 1; ++l) {
+    const double n2 = 2.0 * H->lev[l + 1].k;
+    fb += sizeof(cx<R>) * (double)(1 << l) * n2 * n2;
+  }
+  H->bytes_apply = fb + (double)H->grid.nx * H->grid.ny * (16.0 * 2);
+}
+
 template <class R>
 int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const LevelWait& wait_sibling) {
   const int L = H->L, n = H->s * H->s;
@@ -2220,14 +2232,7 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const Le
   LS_CUDA_TRY(cudaStreamSynchronize(st));
   host_mark("build_checked");
   if (pin[0]) return pin[0];
-  // bytes of one apply (Algorithm 2): every factor once, the X of levels L-1..1
-  // a second time (the upward and the downward pass both apply it), the grid vectors
-  double fb = H->factor_bytes;
-  for (int l = 1; l <= L - 1; ++l) {
-    const double n2 = 2.0 * H->lev[l + 1].k;
-    fb += sizeof(cx<R>) * (double)(1 << l) * n2 * n2;
-  }
-  H->bytes_apply = fb + (double)H->grid.nx * H->grid.ny * (16.0 * 2);
+  apply_bytes<R>(H);
   return LS_OK;
 }
 
@@ -3479,6 +3484,18 @@ int hbs_apply_block(ls_handle* H, const z64* f, z64* q, int nb, int transpose, c
 int hbs_build(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const LevelWait& wait_sibling) {
   return H->prec == LS_FP64 ? build_t<double>(H, st, wait_level, wait_sibling)
                             : build_t<float>(H, st, wait_level, wait_sibling);
+}
+
+int hbs_finish(ls_handle* H, cudaStream_t st) {
+  int rc;
+  if (H->prec == LS_FP64) {
+    if ((rc = apply_prepare<double>(H, st))) return rc;
+    apply_bytes<double>(H);
+  } else {
+    if ((rc = apply_prepare<float>(H, st))) return rc;
+    apply_bytes<float>(H);
+  }
+  return check_launch("hbs_finish");
 }
 
 int sibling_prepare(ls_handle* H, int l, cudaStream_t st) {

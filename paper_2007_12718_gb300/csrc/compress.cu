@@ -1542,6 +1542,7 @@ int leaf_block(ls_handle* H, cudaStream_t st) {
 // level's skeleton (host), not its compression kernels.
 int sibling_block(ls_handle* H, int l, cudaStream_t st) {
   LevelData& lv = H->lev[l];
+  if (lv.Gsib) return LS_OK;  // made already (a reused compression)
   const int kk = lv.k;
   int oax, oay, obx, oby;
   if ((l - 1) % 2 == 0) {

@@ -71,6 +71,7 @@ struct ls_handle {
   std::vector<int> apply_phase_end_t;  // host copy: index of the last operation of each phase
   double flops_build = 0, flops_compress = 0, bytes_apply = 0, factor_bytes = 0;
   double flops_sibling = 0;     // the sibling blocks' low-rank factorisations (counted in flops_build)
+  int compression_reused = 0;   // the compression came from the cache or a file
   int pivot_fallbacks = 0;      // merge levels that needed the row-pivoted inverse
   double probe_resid_max = 0;   // largest probe residual max_i |(Z W v - v)_i| of the merge inverses
   long long spin_limit = ls::kSpinLimit;  // polls of a bounded device wait (ls_opts.wait_limit)
@@ -150,6 +151,16 @@ int blocked_row_id(cx<R>* A, int m, int p, double eps, cudaStream_t st, cudaStre
 int hbs_build(ls_handle* H, cudaStream_t st, const LevelWait& wait_level = LevelWait(),
               const LevelWait& wait_sibling = LevelWait());
 int sibling_prepare(ls_handle* H, int l, cudaStream_t st);
+// After the factors are in place (ls_load): the apply's workspace and operation
+// list, and the apply's byte count.
+int hbs_finish(ls_handle* H, cudaStream_t st);
+
+// persist.cu: the compression cache of reuse_compression.  cache_fetch copies a
+// matching entry's levels into H (*found = true); cache_store keeps a copy of H's.
+int cache_fetch(ls_handle* H, cudaStream_t st, bool* found);
+int cache_store(ls_handle* H, cudaStream_t st);
+int setup_handle(ls_handle* H, const ls_grid* grid, double kappa, const double* b, double tol, const ls_opts* opts,
+                 cudaStream_t st);
 // q = M f, or q = M^T f when transpose (Algorithm 2 reversed, every factor transposed)
 int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, int transpose, cudaStream_t st);
 // the same for a block of nb right-hand sides at once (each factor read once for

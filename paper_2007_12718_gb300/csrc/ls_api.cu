@@ -368,6 +368,7 @@ void ls_default_opts(ls_opts* o) {
   o->wait_limit = 0;
   o->woodbury = 1;
   o->rhs_block = 0;
+  o->reuse_compression = 0;
 }
 
 const char* ls_strerror(int code) {
@@ -653,6 +654,32 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
   ls::g_build_t0 = std::chrono::steady_clock::now();
   ls_handle* H = new ls_handle();
   *out = H;
+  int rc = ls::setup_handle(H, grid, kappa, b, tol, opts, st);
+  if (rc) return rc;
+  ls::SpinLimitScope spin_scope(H->spin_limit);
+  // the compression depends on kappa, h, the tree, tol, order and ring only: with
+  // reuse_compression a cached one replaces the IDs (Sec. 3.2)
+  bool reused = false;
+  if (H->opts.reuse_compression && (rc = ls::cache_fetch(H, st, &reused))) return rc;
+  ls::host_mark("setup_done");
+  if (reused) {
+    H->compression_reused = 1;
+    rc = ls::hbs_build(H, st);
+  } else {
+    rc = build_pipelined(H, st);
+    if (!rc && H->opts.reuse_compression) rc = ls::cache_store(H, st);
+  }
+  ls::host_mark("pipeline_done");
+  return rc;
+}
+
+}  // extern "C"
+
+// Everything of ls_build up to the factors: options, tree, ring, quadrature
+// corrections, b on the device (checked), kernel table, FFT spectrum (on a side
+// stream, waited for before returning).  ls_load uses it too.
+int ls::setup_handle(ls_handle* H, const ls_grid* grid, double kappa, const double* b, double tol,
+                     const ls_opts* opts, cudaStream_t st) {
   H->stream = st;
   H->grid = *grid;
   H->kappa = kappa;
@@ -667,7 +694,7 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
       o.precision == LS_TF32 ||
       o.proxy_width < 0 || o.merge_pivoting < 0 || o.merge_pivoting > 1 ||
       o.top_uncompressed < 0 || o.id_method < LS_ID_AUTO || o.id_method > LS_ID_BLOCKED || o.wait_limit < 0 ||
-      o.rhs_block < 0 || o.woodbury < 0 || o.woodbury > 2) {
+      o.rhs_block < 0 || o.woodbury < 0 || o.woodbury > 2 || o.reuse_compression < 0 || o.reuse_compression > 1) {
     set_error("invalid ls_opts");
     return LS_EINVAL;
   }
@@ -780,14 +807,13 @@ static int build_impl(const ls_grid* grid, double kappa, const double* b, double
     set_error("b must be finite and <= 1");
     return LS_EINVAL;
   }
-  ls::host_mark("setup_done");
-  rc = build_pipelined(H, st);
-  ls::host_mark("pipeline_done");
-  // long finished by now: the handle is complete on return, for any stream
-  cudaStreamSynchronize(H->side_stream);
+  // the spectrum is short next to any build: the handle is complete on return, for any stream
+  LS_CUDA_TRY(cudaStreamSynchronize(H->side_stream));
   cudaEventDestroy(ev_side);
-  return rc;
+  return LS_OK;
 }
+
+extern "C" {
 
 int ls_build(const ls_grid* grid, double kappa, const double* b, double tol, const ls_opts* opts, void* stream,
              ls_handle** out) {
@@ -933,6 +959,9 @@ int ls_get_build_info(const ls_handle* H, ls_build_info* info) {
   info->pivot_fallbacks = H->pivot_fallbacks;
   for (int l = 0; l <= H->L && l < 32; ++l) info->sibling_ranks[l] = std::max(0, H->lev[l].gr);
   info->probe_resid_max = H->probe_resid_max;
+  info->compression_reused = H->compression_reused;
+  info->nx = H->grid.nx;
+  info->ny = H->grid.ny;
   return LS_OK;
 }
 

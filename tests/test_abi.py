@@ -81,3 +81,14 @@ def test_no_gpu_build_fails_cleanly(lib):
     with pytest.raises(ls.LSError) as e:
         ls.ls_build(32, 1 / 32, 20.0, np.zeros((32, 32)), 1e-4)
     assert e.value.code in (ls.LS_ECUDA, ls.LS_ENOMEM)
+
+
+def test_load_refuses_missing_and_foreign_files(lib, tmp_path):
+    """ls_load checks the file before any device work."""
+    import ctypes
+    out = ctypes.c_void_p()
+    assert lib.ls_load(str(tmp_path / "absent").encode(), None, ctypes.byref(out)) == ls.LS_EINVAL
+    junk = tmp_path / "junk"
+    junk.write_bytes(b"not a handle file" * 10)
+    assert lib.ls_load(str(junk).encode(), None, ctypes.byref(out)) == ls.LS_EINVAL
+    assert not out.value
