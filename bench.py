@@ -444,8 +444,8 @@ def run_ours(args, rank, world):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     if args.precision == "fp64":
         raise SystemExit("--precision fp64 is for --sweep; the benchmark measures the FP64 path beside the mixed one")
-    PREC = {"fp32": ls.LS_FP32, "tf32x3": ls.LS_TF32X3}[args.precision]
-    tensor = args.precision == "tf32x3"
+    PREC = {"fp32": ls.LS_FP32, "tf32x3": ls.LS_TF32X3, "fp16split": ls.LS_FP16SPLIT}[args.precision]
+    tensor = args.precision in ("tf32x3", "fp16split")
     pk = measured_peaks(ls)
 
     main = Leg(ls, torch, dev, args.workload, PREC, top_uncompressed=args.top_uncompressed)
@@ -470,6 +470,16 @@ def run_ours(args, rank, world):
         t_fp64, info_fp64, _, _, _ = main.timed(args.fp64_steps, flush, stream, precision=ls.LS_FP64)
         fp64_steps = args.fp64_steps
         agree = float(torch.linalg.norm(main.sig - sig_mixed) / torch.linalg.norm(main.sig))
+    # the FP16 split-product engine on the same workload (one warm-up, one timed step)
+    f16 = None
+    if args.fp16_steps > 0:
+        main.step(ls.LS_FP16SPLIT)
+        t16, info16, _, _, _ = main.timed(args.fp16_steps, flush, stream, precision=ls.LS_FP16SPLIT)
+        f16 = {"value": main.N * args.fp16_steps / t16 / 1e6, "unit": "Mdof/s", "steps": args.fp16_steps,
+               "ms_per_step": t16 / args.fp16_steps * 1e3, "iterations": info16["iterations"],
+               "resid_true": info16["resid_true"],
+               "sigma_rel_diff_vs_mixed": float(torch.linalg.norm(main.sig - sig_mixed) / torch.linalg.norm(sig_mixed)),
+               "precision": "FP16 split products (kind::f16 hi/lo, power-of-two operand scales), FP32 HBS"}
     t_e2e, e2e_bytes = main.e2e(args.e2e_steps, flush) if args.e2e_steps > 0 else (0.0, None)
 
     t_mixed, t_fp64, t_e2e = max_over_ranks([t_mixed, t_fp64, t_e2e], world, dev)
@@ -525,6 +535,7 @@ def run_ours(args, rank, world):
                      "iterations": info_fp64["iterations"] if info_fp64 else None,
                      "resid_true": info_fp64["resid_true"] if info_fp64 else None,
                      "sigma_rel_diff_mixed_vs_fp64": agree},
+            "fp16split": f16,
             "roofline": roof, "phase_rooflines": phases, "e2e_roofline": e2e_roof,
             "kernel_rooflines": {k: {kk: (round(vv, 5) if isinstance(vv, float) else vv) for kk, vv in v.items()}
                                  for k, v in fams.items()},
@@ -553,7 +564,7 @@ def run_sweep(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    PREC = {"fp32": ls.LS_FP32, "tf32x3": ls.LS_TF32X3, "fp64": ls.LS_FP64}[args.precision]
+    PREC = {"fp32": ls.LS_FP32, "tf32x3": ls.LS_TF32X3, "fp16split": ls.LS_FP16SPLIT, "fp64": ls.LS_FP64}[args.precision]
     rows = []
     for j in range(args.sweep_first, args.sweep_levels):
         name = f"cavity_n{80 << j}"
@@ -614,6 +625,8 @@ def main():
     ap.add_argument("--fp64-warmup", type=int, default=0,
                     help="untimed FP64 steps first (the mixed warm-up already loaded every shared kernel)")
     ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the host-buffer end-to-end leg")
+    ap.add_argument("--fp16-steps", type=int, default=1,
+                    help="timed steps of the FP16 split-product leg on the headline workload (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the 256^2 and 32^2 legs")
     ap.add_argument("--no-adjoint", action="store_true",
@@ -629,7 +642,7 @@ def main():
     ap.add_argument("--sweep-first", type=int, default=0, help="first size of the sweep: n = 80 2^first")
     ap.add_argument("--sweep-maxit", type=int, default=100, help="GMRES iteration limit in the sweep (memory: "
                     "(maxit + 1) N complex128 twice)")
-    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "fp64"],
+    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "fp16split", "fp64"],
                     help="engine of the mixed path's merge GEMMs (FP32 storage in both); fp64 (the plain "
                          "FP64 path) only with --sweep")
     args = ap.parse_args()

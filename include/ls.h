@@ -46,14 +46,17 @@ enum {
 };
 
 /* Precision of the HBS preconditioner (compression, inverse build, apply).
- * The FFT matvec and GMRES are FP64 in every mode.  LS_FP32 and LS_TF32X3 store
- * the factors in FP32; they differ in the engine of the large merge GEMMs
- * (Eqs. 26-27): FP32 SIMT cores, or tensor cores with each operand split into
- * two tf32 terms (three products, ~FP32 accuracy).  LS_TF32 (one tf32 product,
- * ~1e-3 relative error) names a GEMM engine of ls_cgemm_c64 only: its
+ * The FFT matvec and GMRES are FP64 in every mode.  LS_FP32, LS_TF32X3 and
+ * LS_FP16SPLIT store the factors in FP32; they differ in the engine of the
+ * large merge GEMMs (Eqs. 26-27): FP32 SIMT cores; tensor cores with each
+ * operand split into two tf32 terms (three products, ~FP32 accuracy); tensor
+ * cores with each operand scaled by a power of two and split into two FP16
+ * terms (the FP16 split product: three kind::f16 products at twice the tf32
+ * rate, the same ~22 bits of each operand).  LS_TF32 (one tf32 product, ~1e-3
+ * relative error) names a GEMM engine of ls_cgemm_c64 only: its
  * preconditioner misses the HBS tolerance by orders of magnitude, so ls_build
  * rejects it (LS_EINVAL). */
-enum { LS_FP64 = 0, LS_FP32 = 1, LS_TF32 = 2, LS_TF32X3 = 3 };
+enum { LS_FP64 = 0, LS_FP32 = 1, LS_TF32 = 2, LS_TF32X3 = 3, LS_FP16SPLIT = 4 };
 
 typedef struct {
   int nx, ny;        /* grid size; a tree of square leaves must fit (see ls_build) */
@@ -66,7 +69,7 @@ typedef struct {
   int order_precond; /* order used inside the HBS compression: 4,6,8,10 (default 4)      */
   int leaf_side;     /* leaf box side s (s*s points per leaf, default 8)                  */
   int proxy_width;   /* proxy ring width in grid cells; 0 = from tol and order (default)  */
-  int precision;     /* LS_FP64, LS_FP32 or LS_TF32X3 (default LS_FP32)                    */
+  int precision;     /* LS_FP64, LS_FP32, LS_TF32X3 or LS_FP16SPLIT (default LS_FP32)       */
   int gmres_maxit;   /* default 100 (Sec. 6.3)                                            */
   double gmres_tol;  /* relative residual, default 1e-10 (Sec. 6.3)                       */
   int merge_pivoting; /* merge inverses: 0 = blocks without interchanges, checked, with the
@@ -355,7 +358,9 @@ long long ls_kernel_launches(void);
  * FP32 GEMM the HBS build uses for its merge products,
  *   C[b] = alpha op(A[b]) op(B[b]) + beta C[b],   b < batch,
  * row-major interleaved complex64, op = transpose (no conjugate) when ta/tb.
- * engine: 0 = FP32 SIMT, 1 = tcgen05 tf32, 2 = tcgen05 tf32x3.  alpha, beta:
+ * engine: 0 = FP32 SIMT, 1 = tcgen05 tf32, 2 = tcgen05 tf32x3, 3 = tcgen05
+ * f16x3 (the FP16 split product; A and B each scaled by one power of two from
+ * their largest entry over the batch).  alpha, beta:
  * {re, im} pairs.  All pointers on the device.  Returns LS_EINVAL for a bad
  * engine or size, LS_ETIMEOUT if a tensor-core wait gave up. */
 int ls_cgemm_c64(int engine, int ta, int tb, int M, int N, int K, const float* alpha, const void* A, int lda,

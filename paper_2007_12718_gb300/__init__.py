@@ -29,7 +29,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libls.so")
 
 LS_OK, LS_EINVAL, LS_ENOMEM, LS_ECUDA, LS_ESINGULAR, LS_ENOCONV, LS_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
-LS_FP64, LS_FP32, LS_TF32, LS_TF32X3 = 0, 1, 2, 3
+LS_FP64, LS_FP32, LS_TF32, LS_TF32X3, LS_FP16SPLIT = 0, 1, 2, 3, 4
 LS_ID_AUTO, LS_ID_GREEDY, LS_ID_BLOCKED = 0, 1, 2
 
 EXPORTED = ["ls_default_opts", "ls_build", "ls_apply", "ls_matvec", "ls_solve", "ls_rhs_plane_wave",
@@ -438,7 +438,7 @@ def ls_profile_get():
 
 def ls_cgemm_c64(engine, A, B, C, ta=False, tb=False, alpha=1.0, beta=0.0, stream=None):
     """C = alpha op(A) op(B) + beta C on batched complex64 device tensors [batch, rows, cols]
-    (engine 0 SIMT, 1 tcgen05 tf32, 2 tcgen05 tf32x3)."""
+    (engine 0 SIMT, 1 tcgen05 tf32, 2 tcgen05 tf32x3, 3 tcgen05 f16x3, the FP16 split product)."""
     import torch
     for t in (A, B, C):
         if not (isinstance(t, torch.Tensor) and t.dtype == torch.complex64 and t.is_cuda and t.is_contiguous()):

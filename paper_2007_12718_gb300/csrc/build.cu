@@ -291,8 +291,13 @@ __global__ void __launch_bounds__(256) gemm64x2_kernel(int M, int N, int K, c32 
 
 // Engine of the FP32 merge GEMMs for the build in progress on this thread:
 // 0 = SIMT FP32, 1 = tensor cores tf32, 2 = tensor cores tf32x3.
-thread_local int g_tc_engine = 0;
+thread_local int g_tc_engine = 0;  // 0 SIMT, 1 tf32, 2 tf32x3, 3 f16x3 (tc_cgemm's split + 1)
 thread_local int* g_tc_err = nullptr;
+
+// The tensor-core engine of a handle's precision mode (0: the SIMT kernels).
+int tc_engine_of(const ls_handle* H) {
+  return H->prec == LS_TF32 ? 1 : H->prec == LS_TF32X3 ? 2 : H->prec == LS_FP16SPLIT ? 3 : 0;
+}
 
 // Batches beyond the grid's y / z limit are launched in chunks.
 constexpr int kMaxGridYZ = 65535;
@@ -316,7 +321,7 @@ void gemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, cx<R> alpha, c
       (double)M * N * K * batch >= 3.3e7) {
     tc_cgemm(st, ta, tb, M, N, K, *reinterpret_cast<const c32*>(&alpha), reinterpret_cast<const c32*>(A), lda, sA,
              reinterpret_cast<const c32*>(B), ldb, sB, *reinterpret_cast<const c32*>(&beta),
-             reinterpret_cast<c32*>(C), ldc, sC, batch, g_tc_engine == 2 ? 1 : 0, g_tc_err, bd.lo, bd.hi);
+             reinterpret_cast<c32*>(C), ldc, sC, batch, g_tc_engine - 1, g_tc_err, bd.lo, bd.hi);
     return;
   }
   count_launch();
@@ -1777,7 +1782,7 @@ int sibling_lowrank(ls_handle* H, int l, cudaStream_t st) {
     gaussian_kernel<R><<<(unsigned)((ks + 255) / 256), 256, 0, st>>>(Om, ks, 0x5EED0000ull + (unsigned long long)l);
     // the sketch on the handle's GEMM engine (its rounding is far below the tolerance);
     // the ID itself keeps the FP32 SIMT GEMMs (its residual decides the rank)
-    g_tc_engine = H->prec == LS_TF32X3 ? 2 : 0;
+    g_tc_engine = tc_engine_of(H);
     gemm<R>(st, false, false, k, sw, k, one<R>(), reinterpret_cast<const cx<R>*>(lv.Gsib), k, 0, Om, sw, 0, zero<R>(),
             Y, sw, 0, 1);
     g_tc_engine = 0;
@@ -1984,7 +1989,7 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const Le
   int rc;
   struct EngineScope {
     explicit EngineScope(ls_handle* H) {
-      g_tc_engine = H->prec == LS_TF32 ? 1 : H->prec == LS_TF32X3 ? 2 : 0;
+      g_tc_engine = tc_engine_of(H);
       g_tc_err = H->d_err;
     }
     ~EngineScope() {
@@ -3359,7 +3364,7 @@ struct EngineScope {
   int prev_engine;
   int* prev_err;
   explicit EngineScope(const ls_handle* H) : prev_engine(g_tc_engine), prev_err(g_tc_err) {
-    g_tc_engine = H->prec == LS_TF32X3 ? 2 : 0;
+    g_tc_engine = tc_engine_of(H);
     g_tc_err = H->d_err;
   }
   ~EngineScope() {

@@ -440,7 +440,7 @@ int ls_row_id_ex(const void* A, int m, int p, double eps, int precision, int met
 int ls_cgemm_c64(int engine, int ta, int tb, int M, int N, int K, const float* alpha, const void* A, int lda,
                  long long sA, const void* B, int ldb, long long sB, const float* beta, void* C, int ldc,
                  long long sC, int batch, void* stream) {
-  if (engine < 0 || engine > 2 || M < 0 || N < 0 || K < 0 || batch < 0 || !alpha || !beta || !A || !B || !C)
+  if (engine < 0 || engine > 3 || M < 0 || N < 0 || K < 0 || batch < 0 || !alpha || !beta || !A || !B || !C)
     return LS_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   ls::StreamScope scope(st);
@@ -454,8 +454,7 @@ int ls_cgemm_c64(int engine, int ta, int tb, int M, int N, int K, const float* a
     if (cudaMalloc(&d_flag, sizeof(int)) != cudaSuccess) return LS_ENOMEM;
     cudaMemset(d_flag, 0, sizeof(int));
   }
-  int rc = ls::tc_cgemm(st, ta, tb, M, N, K, al, a, lda, sA, b, ldb, sB, be, c, ldc, sC, batch, engine == 2 ? 1 : 0,
-                        d_flag);
+  int rc = ls::tc_cgemm(st, ta, tb, M, N, K, al, a, lda, sA, b, ldb, sB, be, c, ldc, sC, batch, engine - 1, d_flag);
   if (rc) return rc;
   int flag = 0;
   LS_CUDA_TRY(cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -690,7 +689,7 @@ int ls::setup_handle(ls_handle* H, const ls_grid* grid, double kappa, const doub
     ls_default_opts(&H->opts);
   const ls_opts& o = H->opts;
   if (!valid_order(o.order_matvec) || !valid_order(o.order_precond) || o.order_precond == 2 || o.leaf_side < 2 ||
-      o.gmres_maxit < 1 || !(o.gmres_tol > 0) || (o.precision < LS_FP64 || o.precision > LS_TF32X3) ||
+      o.gmres_maxit < 1 || !(o.gmres_tol > 0) || (o.precision < LS_FP64 || o.precision > LS_FP16SPLIT) ||
       o.precision == LS_TF32 ||
       o.proxy_width < 0 || o.merge_pivoting < 0 || o.merge_pivoting > 1 ||
       o.top_uncompressed < 0 || o.id_method < LS_ID_AUTO || o.id_method > LS_ID_BLOCKED || o.wait_limit < 0 ||

@@ -12,6 +12,14 @@
 // and each real product P Q is P_hi Q_hi + P_hi Q_lo + P_lo Q_hi (the lo lo
 // term, ~2^-22 of |P||Q|, is dropped): twelve MMAs per k step instead of four.
 //
+// In f16x3 mode (the FP16 split product) the planes are FP16 instead, hi =
+// fp16(s x), lo = fp16(s x - hi), with s = 2^e per operand chosen from the
+// operand's largest magnitude (a pre-pass) so that s max|x| < 2^14: the
+// exponent range of FP16 then costs nothing, and hi + lo carries 22 bits of x
+// as tf32 hi + lo does; kind::f16 MMAs (k = 16 per instruction, twice the
+// tf32 rate) accumulate in FP32 and the epilogue multiplies by 1 / (sA sB),
+// exact powers of two.  A stage then holds 32 complex k in the same 64 KB.
+//
 // One CTA computes a 128 x 128 complex tile.  Eight converter warps read the
 // FP32 operands straight from global memory (per thread one row of op(A) and
 // one column of op(B), half of a stage's 16 complex k, coalesced for either
@@ -29,6 +37,8 @@
 
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 #include "handle.h"
 
 namespace ls {
@@ -36,13 +46,18 @@ namespace {
 
 constexpr int TC_BM = 128;                     // rows of C per tile
 constexpr int TC_BN = 128;                     // complex columns of C per tile
-constexpr int TC_BK = 16;                      // complex k per stage
+constexpr int TC_BK = 16;                      // complex k per stage (tf32; f16: twice as many)
 constexpr int TC_PLANE = TC_BM * TC_BK;        // floats per real plane (8 KB)
 constexpr int TC_STAGE = 8 * TC_PLANE;         // Ar hi/lo, Ai hi/lo, Br hi/lo, Bi hi/lo: 64 KB
 constexpr int TC_NS = 3;                       // stages in flight
 constexpr int TC_CONV = 256;                   // converter / epilogue threads (warps 0-7)
-constexpr int TC_KH = TC_BK / 2;               // complex k per converter thread and stage
 constexpr int TC_THREADS = TC_CONV + 32;       // + the MMA warp (warp 8)
+template <bool F16>
+struct TcK {
+  static constexpr int BK = F16 ? 2 * TC_BK : TC_BK;  // complex k per stage
+  static constexpr int KH = BK / 2;                   // complex k per converter thread and stage
+};
+constexpr int TC_KH_MAX = TcK<true>::KH;
 constexpr uint32_t TC_TMEM_COLS = 512;         // three 128-column accumulators
 constexpr long long kMbarSpin = 1LL << 26;
 
@@ -67,6 +82,16 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
 // Instruction descriptor: D = F32, A = B = TF32, both K-major.
 __host__ __device__ constexpr uint32_t make_idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// Instruction descriptor: D = F32, A = B = F16, both K-major.
+__host__ __device__ constexpr uint32_t make_idesc_f16(int M, int N) {
+  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// The same K-major no-swizzle layout for a 128 x 32 FP16 plane (in halves):
+// core matrix = 8 rows x 16 bytes (8 halves); LBO 128 B, SBO 512 B as above.
+__device__ __forceinline__ int kmaj16(int row, int k) {
+  return (row >> 3) * (2 * TC_BK * 8) + (k >> 3) * 64 + (row & 7) * 8 + (k & 7);
 }
 
 __device__ __forceinline__ float to_tf32(float x) {
@@ -96,12 +121,78 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd
       "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
 }
 
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+}
+
+template <bool F16>
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
+  if constexpr (F16)
+    mma_f16(tmem, ad, bd, idesc, accum);
+  else
+    mma_tf32(tmem, ad, bd, idesc, accum);
+}
+
+// The 16 complex values k = kb .. kb + 15 of one row, scaled by sc, as the four
+// FP16 planes (re hi, re lo, im hi, im lo) starting at plane p0 (two 16-byte
+// core-matrix rows per plane).
+__device__ __forceinline__ void store_row16(float* stage, int p0, int row, int kb, const c32 (&v)[TC_KH_MAX], float sc) {
+  __half* st = reinterpret_cast<__half*>(stage);
+  constexpr int PH = 2 * TC_PLANE;  // halves per plane
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    __align__(16) __half rh[8], rl[8], ih[8], il[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const c32 x = v[8 * q + e];
+      const float xr = x.re * sc, xi = x.im * sc;
+      const __half hr = __float2half_rn(xr), hi = __float2half_rn(xi);
+      rh[e] = hr;
+      ih[e] = hi;
+      rl[e] = __float2half_rn(xr - __half2float(hr));
+      il[e] = __float2half_rn(xi - __half2float(hi));
+    }
+    const int o = kmaj16(row, kb + 8 * q);
+    *reinterpret_cast<uint4*>(st + (p0 + 0) * PH + o) = *reinterpret_cast<const uint4*>(rh);
+    *reinterpret_cast<uint4*>(st + (p0 + 1) * PH + o) = *reinterpret_cast<const uint4*>(rl);
+    *reinterpret_cast<uint4*>(st + (p0 + 2) * PH + o) = *reinterpret_cast<const uint4*>(ih);
+    *reinterpret_cast<uint4*>(st + (p0 + 3) * PH + o) = *reinterpret_cast<const uint4*>(il);
+  }
+}
+
+// The FP16 operand scale 2^e with 2^e * mx < 2^14 (e = 0 for mx = 0 or not finite).
+__device__ __forceinline__ int f16_scale_exp(unsigned bits) {
+  const float mx = __uint_as_float(bits);
+  if (!(mx > 0.f) || !(mx < 3.0e38f)) return 0;
+  int e;
+  frexpf(mx, &e);  // mx < 2^e
+  return min(14 - e, 100);
+}
+
+// out[0] = max over the batch of max(|re|, |im|) of X (rows x cols, row stride
+// ld, batch stride sX), as float bits (non-negative floats order as unsigned).
+__global__ void absmax_kernel(const c32* __restrict__ X, int rows, int cols, int ld, long long sX, int batch,
+                              unsigned* out) {
+  const long long per = (long long)rows * cols, tot = per * batch;
+  float m = 0.f;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const long long b = t / per, r = (t % per) / cols, c = t % cols;
+    const c32 x = X[b * sX + r * ld + c];
+    m = fmaxf(m, fmaxf(fabsf(x.re), fabsf(x.im)));
+  }
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
+}
+
 // Store the 8 complex values k = kb .. kb + 7 of one row as the four planes
 // (re hi, re lo, im hi, im lo) starting at plane p0; without `split` only the
 // heads are stored.
-__device__ __forceinline__ void store_row(float* stage, int p0, int row, int kb, const c32 (&v)[TC_KH], bool split) {
+__device__ __forceinline__ void store_row(float* stage, int p0, int row, int kb, const c32 (&v)[TC_BK / 2], bool split) {
 #pragma unroll
-  for (int q = 0; q < TC_KH / 4; ++q) {
+  for (int q = 0; q < TC_BK / 8; ++q) {
     float4 rh, rl, ih, il;
     float* prh = &rh.x;
     float* prl = &rl.x;
@@ -127,13 +218,15 @@ __device__ __forceinline__ void store_row(float* stage, int p0, int row, int kb,
 }
 
 // C[b] (M x N complex) = alpha op(A[b]) op(B[b]) + beta C[b]; row-major
-// complex64 operands, op = transpose (no conjugate) when TA / TB.
-template <bool TA, bool TB>
+// complex64 operands, op = transpose (no conjugate) when TA / TB.  F16: the
+// FP16 split product, amax = {max|A|, max|B|} (float bits) from absmax_kernel.
+template <bool TA, bool TB, bool F16>
 __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K, c32 alpha, const c32* __restrict__ A,
                                                              int lda, long long sA, const c32* __restrict__ B, int ldb,
                                                              long long sB, c32 beta, c32* __restrict__ C, int ldc,
                                                              long long sC, int split, int band_lo, int band_hi,
-                                                             int* err) {
+                                                             int* err, const unsigned* __restrict__ amax) {
+  constexpr int BK = TcK<F16>::BK, KH = TcK<F16>::KH;
   extern __shared__ __align__(1024) unsigned char smraw[];
   float* stages = reinterpret_cast<float*>(smraw);  // TC_NS x TC_STAGE floats
   __shared__ __align__(8) uint64_t full_bar[TC_NS], empty_bar[TC_NS], done_bar;
@@ -144,8 +237,10 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K
   A += bz * sA;
   B += bz * sB;
   C += bz * sC;
-  const int S = (K + TC_BK - 1) / TC_BK;
-  const bool sp = split != 0;
+  const int S = (K + BK - 1) / BK;
+  const bool sp = F16 || split != 0;
+  const int ea = F16 ? f16_scale_exp(amax[0]) : 0, eb = F16 ? f16_scale_exp(amax[1]) : 0;
+  const float sa = ldexpf(1.f, ea), sb = ldexpf(1.f, eb);
 
   if (warp == 8) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -167,13 +262,13 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K
   const uint32_t tmem = tmem_base;
 
   if (warp < 8) {  // converters: row r of op(A) and of op(B)^T, k-half kh of every stage
-    const int r = tid & (TC_BM - 1), kh = (tid >> 7) * TC_KH;
+    const int r = tid & (TC_BM - 1), kh = (tid >> 7) * KH;
     const int ra = m0 + r, cb = n0 + r;
-    c32 va[TC_KH], vb[TC_KH];  // the operands of the next stage, loaded ahead
+    c32 va[TC_KH_MAX], vb[TC_KH_MAX];  // the operands of the next stage, loaded ahead (KH used)
     auto load = [&](int s) {
-      const int k0 = s * TC_BK + kh;
+      const int k0 = s * BK + kh;
 #pragma unroll
-      for (int j = 0; j < TC_KH; ++j) {
+      for (int j = 0; j < KH; ++j) {
         const int k = k0 + j;
         va[j] = (ra < M && k < K) ? (TA ? A[(long long)k * lda + ra] : A[(long long)ra * lda + k]) : mk<float>(0.f, 0.f);
         vb[j] = (cb < N && k < K) ? (TB ? B[(long long)cb * ldb + k] : B[(long long)k * ldb + cb]) : mk<float>(0.f, 0.f);
@@ -188,15 +283,20 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K
       }
       if (*(volatile int*)&s_fail) break;
       float* stage = stages + (size_t)bi * TC_STAGE;
-      store_row(stage, P_AR_HI, r, kh, va, sp);
-      store_row(stage, P_BR_HI, r, kh, vb, sp);
+      if constexpr (F16) {
+        store_row16(stage, P_AR_HI, r, kh, va, sa);
+        store_row16(stage, P_BR_HI, r, kh, vb, sb);
+      } else {
+        store_row(stage, P_AR_HI, r, kh, reinterpret_cast<const c32(&)[TC_BK / 2]>(va), sp);
+        store_row(stage, P_BR_HI, r, kh, reinterpret_cast<const c32(&)[TC_BK / 2]>(vb), sp);
+      }
       // generic-proxy stores -> visible to the tensor cores (async proxy)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[bi])) : "memory");
       if (s + 1 < S) load(s + 1);
     }
   } else if (lane == 0) {  // MMA issuer
-    const uint32_t idesc = make_idesc_tf32(TC_BM, TC_BN);
+    const uint32_t idesc = F16 ? make_idesc_f16(TC_BM, TC_BN) : make_idesc_tf32(TC_BM, TC_BN);
     const uint32_t acc_rr = tmem, acc_ii = tmem + 128, acc_im = tmem + 256;
     bool ok = true;
     for (int s = 0; s < S; ++s) {
@@ -208,26 +308,27 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t base = smem_u32(stages + (size_t)bi * TC_STAGE);
+      // one MMA k step covers 32 bytes of each row (8 tf32 or 16 f16): two core matrices
       auto pd = [&](int plane, int kk) { return make_desc(base + plane * TC_PLANE * 4 + kk * 256, 128, TC_BK * 8 * 4); };
 #pragma unroll
-      for (int kk = 0; kk < TC_BK / 8; ++kk) {
+      for (int kk = 0; kk < 2; ++kk) {
         const uint32_t first = (s == 0 && kk == 0) ? 0u : 1u;
         // Ar Br
-        mma_tf32(acc_rr, pd(P_AR_HI, kk), pd(P_BR_HI, kk), idesc, first);
+        mma<F16>(acc_rr, pd(P_AR_HI, kk), pd(P_BR_HI, kk), idesc, first);
         // Ai Bi
-        mma_tf32(acc_ii, pd(P_AI_HI, kk), pd(P_BI_HI, kk), idesc, first);
+        mma<F16>(acc_ii, pd(P_AI_HI, kk), pd(P_BI_HI, kk), idesc, first);
         // Ar Bi + Ai Br
-        mma_tf32(acc_im, pd(P_AR_HI, kk), pd(P_BI_HI, kk), idesc, first);
-        mma_tf32(acc_im, pd(P_AI_HI, kk), pd(P_BR_HI, kk), idesc, 1u);
+        mma<F16>(acc_im, pd(P_AR_HI, kk), pd(P_BI_HI, kk), idesc, first);
+        mma<F16>(acc_im, pd(P_AI_HI, kk), pd(P_BR_HI, kk), idesc, 1u);
         if (sp) {
-          mma_tf32(acc_rr, pd(P_AR_HI, kk), pd(P_BR_LO, kk), idesc, 1u);
-          mma_tf32(acc_rr, pd(P_AR_LO, kk), pd(P_BR_HI, kk), idesc, 1u);
-          mma_tf32(acc_ii, pd(P_AI_HI, kk), pd(P_BI_LO, kk), idesc, 1u);
-          mma_tf32(acc_ii, pd(P_AI_LO, kk), pd(P_BI_HI, kk), idesc, 1u);
-          mma_tf32(acc_im, pd(P_AR_HI, kk), pd(P_BI_LO, kk), idesc, 1u);
-          mma_tf32(acc_im, pd(P_AR_LO, kk), pd(P_BI_HI, kk), idesc, 1u);
-          mma_tf32(acc_im, pd(P_AI_HI, kk), pd(P_BR_LO, kk), idesc, 1u);
-          mma_tf32(acc_im, pd(P_AI_LO, kk), pd(P_BR_HI, kk), idesc, 1u);
+          mma<F16>(acc_rr, pd(P_AR_HI, kk), pd(P_BR_LO, kk), idesc, 1u);
+          mma<F16>(acc_rr, pd(P_AR_LO, kk), pd(P_BR_HI, kk), idesc, 1u);
+          mma<F16>(acc_ii, pd(P_AI_HI, kk), pd(P_BI_LO, kk), idesc, 1u);
+          mma<F16>(acc_ii, pd(P_AI_LO, kk), pd(P_BI_HI, kk), idesc, 1u);
+          mma<F16>(acc_im, pd(P_AR_HI, kk), pd(P_BI_LO, kk), idesc, 1u);
+          mma<F16>(acc_im, pd(P_AR_LO, kk), pd(P_BI_HI, kk), idesc, 1u);
+          mma<F16>(acc_im, pd(P_AI_HI, kk), pd(P_BR_LO, kk), idesc, 1u);
+          mma<F16>(acc_im, pd(P_AI_LO, kk), pd(P_BR_HI, kk), idesc, 1u);
         }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -299,11 +400,13 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K
       }
       asm volatile("bar.sync 1, %0;" ::"r"(TC_CONV) : "memory");  // the converter warps only
       const bool zb = (beta.re == 0.f && beta.im == 0.f);
+      // the FP16 operand scales, undone exactly (powers of two)
+      const c32 al = F16 ? mk<float>(ldexpf(alpha.re, -(ea + eb)), ldexpf(alpha.im, -(ea + eb))) : alpha;
       for (int e = tid; e < TC_BM * TC_BN; e += TC_CONV) {
         const int r = e / TC_BN, c = e % TC_BN, row = m0 + r, col = n0 + c;
         const bool band = (row >= band_lo && row < band_hi) || (col >= band_lo && col < band_hi);
         if (row < M && col < N && !band) {
-          c32 out = alpha * tile[r * TLD + c];
+          c32 out = al * tile[r * TLD + c];
           if (!zb) out = out + beta * C[(long long)row * ldc + col];
           C[(long long)row * ldc + col] = out;
         }
@@ -317,8 +420,23 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K
 
 }  // namespace
 
+template <bool TA, bool TB, bool F16>
+int launch_tc(cudaStream_t st, int M, int N, int K, c32 alpha, const c32* A, int lda, long long sA, const c32* B,
+              int ldb, long long sB, c32 beta, c32* C, int ldc, long long sC, int batch, int split, int* err,
+              int band_lo, int band_hi, const unsigned* amax) {
+  const size_t smem = sizeof(float) * (size_t)TC_NS * TC_STAGE;
+  LS_CUDA_TRY(cudaFuncSetAttribute((const void*)tc_gemm_kernel<TA, TB, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+  dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, batch);
+  count_launch();
+  tc_gemm_kernel<TA, TB, F16><<<grid, TC_THREADS, smem, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
+                                                              split, band_lo, band_hi, err, amax);
+  return check_launch("tc_cgemm");
+}
+
 // Host entry: same contract as the SIMT gemm (batched, row-major, op N/T, a
-// stride of 0 shares an operand across the batch).  split: 0 tf32, 1 tf32x3.
+// stride of 0 shares an operand across the batch).  split: 0 tf32, 1 tf32x3,
+// 2 f16x3 (the FP16 split product: a max-abs pre-pass over A and B, on st).
 // Entries in rows or columns [band_lo, band_hi) of C are left untouched.
 int tc_cgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, c32 alpha, const c32* A, int lda, long long sA,
              const c32* B, int ldb, long long sB, c32 beta, c32* C, int ldc, long long sC, int batch, int split,
@@ -332,27 +450,45 @@ int tc_cgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, c32 alpha, 
     }
     return LS_OK;
   }
-  const size_t smem = sizeof(float) * (size_t)TC_NS * TC_STAGE;
-  const void* fn = !ta && !tb ? (const void*)tc_gemm_kernel<false, false>
-                 : ta && !tb  ? (const void*)tc_gemm_kernel<true, false>
-                 : !ta && tb  ? (const void*)tc_gemm_kernel<false, true>
-                              : (const void*)tc_gemm_kernel<true, true>;
-  LS_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, batch);
-  count_launch();
+  int rc;
+  if (split == 2) {
+    StreamScope scope(st);  // the two maxima live on st
+    unsigned* amax = nullptr;
+    if ((rc = dalloc((void**)&amax, 2 * sizeof(unsigned)))) return rc;
+    LS_CUDA_TRY(cudaMemsetAsync(amax, 0, 2 * sizeof(unsigned), st));
+    // stored shapes: op(A) is M x K (A stored K x M when transposed), op(B) K x N
+    const int ar = ta ? K : M, ac = ta ? M : K, br = tb ? N : K, bc = tb ? K : N;
+    const int nbA = (int)std::min<long long>(1024, ((long long)ar * ac * (sA ? batch : 1) + 255) / 256);
+    const int nbB = (int)std::min<long long>(1024, ((long long)br * bc * (sB ? batch : 1) + 255) / 256);
+    count_launch(2);
+    absmax_kernel<<<nbA, 256, 0, st>>>(A, ar, ac, lda, sA, sA ? batch : 1, amax);
+    absmax_kernel<<<nbB, 256, 0, st>>>(B, br, bc, ldb, sB, sB ? batch : 1, amax + 1);
+    if (!ta && !tb)
+      rc = launch_tc<false, false, true>(st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, split,
+                                         err, band_lo, band_hi, amax);
+    else if (ta && !tb)
+      rc = launch_tc<true, false, true>(st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, split,
+                                        err, band_lo, band_hi, amax);
+    else if (!ta && tb)
+      rc = launch_tc<false, true, true>(st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, split,
+                                        err, band_lo, band_hi, amax);
+    else
+      rc = launch_tc<true, true, true>(st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, split, err,
+                                       band_lo, band_hi, amax);
+    dfree(amax);
+    return rc;
+  }
   if (!ta && !tb)
-    tc_gemm_kernel<false, false><<<grid, TC_THREADS, smem, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
-                                                                sC, split, band_lo, band_hi, err);
-  else if (ta && !tb)
-    tc_gemm_kernel<true, false><<<grid, TC_THREADS, smem, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
-                                                               sC, split, band_lo, band_hi, err);
-  else if (!ta && tb)
-    tc_gemm_kernel<false, true><<<grid, TC_THREADS, smem, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
-                                                               sC, split, band_lo, band_hi, err);
-  else
-    tc_gemm_kernel<true, true><<<grid, TC_THREADS, smem, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc,
-                                                              sC, split, band_lo, band_hi, err);
-  return check_launch("tc_cgemm");
+    return launch_tc<false, false, false>(st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, split,
+                                          err, band_lo, band_hi, nullptr);
+  if (ta && !tb)
+    return launch_tc<true, false, false>(st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, split,
+                                         err, band_lo, band_hi, nullptr);
+  if (!ta && tb)
+    return launch_tc<false, true, false>(st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, split,
+                                         err, band_lo, band_hi, nullptr);
+  return launch_tc<true, true, false>(st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, split, err,
+                                      band_lo, band_hi, nullptr);
 }
 
 }  // namespace ls

@@ -59,7 +59,7 @@ def test_block_apply_matches_one_at_a_time(precision, transpose):
     ls.ls_free(Hb)
 
 
-@pytest.mark.parametrize("precision", [ls.LS_FP64, ls.LS_FP32, ls.LS_TF32X3])
+@pytest.mark.parametrize("precision", [ls.LS_FP64, ls.LS_FP32, ls.LS_TF32X3, ls.LS_FP16SPLIT])
 def test_block_solve_vs_dense_lu(precision):
     n, kappa = 64, 40.0
     h = 1.0 / n

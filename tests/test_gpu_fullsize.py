@@ -8,7 +8,7 @@ without the GPU path.
   inverse, FP64 with the greedy CPQR, is ~9 eps off on a random f and ~80 eps
   on the plane-wave right-hand side): the GPU inverse must be within 5 eps or
   within 1.5x the oracle's own error on the same f, whichever is larger.
-* Mixed (tf32x3 / FP32 HBS) vs FP64 paths: the scattered fields u = (G+T) sigma
+* Mixed (tf32x3, FP16 split, FP32 HBS) vs FP64 paths: the scattered fields u = (G+T) sigma
   of the two GMRES solutions agree to 1e-9 (both are solves to 1e-10 of the
   same FP64 system; the preconditioner only changes the iterates).
 * The 2048^2 workload of the benchmark (kappa = 400 pi): the true residual of
@@ -59,7 +59,8 @@ def n256():
 @pytest.mark.parametrize("precision,kw", [(ls.LS_FP64, {}), (ls.LS_FP32, {}), (ls.LS_TF32X3, {}),
                                           (ls.LS_TF32X3, {"top_uncompressed": 1}),
                                           (ls.LS_FP32, {"id_method": ls.LS_ID_GREEDY}),
-                                          (ls.LS_TF32X3, {"woodbury": 0}), (ls.LS_FP64, {"woodbury": 0})])
+                                          (ls.LS_TF32X3, {"woodbury": 0}), (ls.LS_FP64, {"woodbury": 0}),
+                                          (ls.LS_FP16SPLIT, {}), (ls.LS_FP16SPLIT, {"top_uncompressed": 1})])
 def test_preconditioner_forward_error_n256(n256, precision, kw):
     n, eps = n256["n"], n256["eps"]
     H = ls.ls_build(n, 1.0 / n, n256["kappa"], n256["b"], eps, precision=precision, **kw)
@@ -79,7 +80,7 @@ def test_mixed_vs_fp64_fields_agree_n256():
     b = inputs.gaussian_family(n, 0)
     f = dev(nystrom.rhs(kappa, b, n, n, 1.0 / n).reshape(n, n))
     u = {}
-    for precision in (ls.LS_FP64, ls.LS_FP32, ls.LS_TF32X3):
+    for precision in (ls.LS_FP64, ls.LS_FP32, ls.LS_TF32X3, ls.LS_FP16SPLIT):
         H = ls.ls_build(n, 1.0 / n, kappa, b, 1e-4, precision=precision)
         sig = torch.zeros(n, n, dtype=torch.complex128, device=DEV)
         info = ls.ls_solve(H, f, sig)[0]
@@ -88,6 +89,7 @@ def test_mixed_vs_fp64_fields_agree_n256():
         ls.ls_free(H)
     assert rel(u[ls.LS_FP32], u[ls.LS_FP64]) <= 1e-9
     assert rel(u[ls.LS_TF32X3], u[ls.LS_FP64]) <= 1e-9
+    assert rel(u[ls.LS_FP16SPLIT], u[ls.LS_FP64]) <= 1e-9
 
 
 def test_precond_n2048_true_residual():

@@ -225,12 +225,16 @@ def test_precond_solve_full_size_n256():
         ls.ls_free(H)
 
 
-def test_tensor_core_build():
-    """Merge GEMMs on the tensor cores (tf32x3): the HBS inverse stays within 5 eps
-    of the dense inverse, and GMRES (FP64, FP64 matvec) reaches the dense solution."""
+@pytest.mark.parametrize("precision", [ls.LS_TF32X3, ls.LS_FP16SPLIT])
+def test_tensor_core_build(precision):
+    """The tensor-core precision modes (tf32x3, FP16 split) at the oracle size: the
+    HBS inverse stays within 5 eps of the dense inverse, and GMRES (FP64, FP64
+    matvec) reaches the dense solution.  (At 64^2 the products are below the
+    tensor cores' size threshold; the 256^2 tests of test_gpu_fullsize.py are
+    where they run.)"""
     n, kappa = 64, 40.0
     b = inputs.gaussian_family(n, 0)
-    H = build(n, kappa, b, 1e-4, precision=ls.LS_TF32X3)
+    H = build(n, kappa, b, 1e-4, precision=precision)
     A4 = nystrom.dense_operator(kappa, 1.0 / n, b, 4)
     f = inputs.random_complex((n, n), 1)
     q = host(ls.ls_apply(H, dev(f), torch.zeros(n, n, dtype=torch.complex128, device=DEV)))

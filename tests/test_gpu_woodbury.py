@@ -61,7 +61,7 @@ def test_woodbury_apply_vs_dense_inverse(n, precision, eps):
     ls.ls_free(H)
 
 
-@pytest.mark.parametrize("precision", [ls.LS_FP64, ls.LS_FP32, ls.LS_TF32X3])
+@pytest.mark.parametrize("precision", [ls.LS_FP64, ls.LS_FP32, ls.LS_TF32X3, ls.LS_FP16SPLIT])
 def test_woodbury_vs_schur_and_solve(precision):
     n, kappa, eps = 64, 40.0, 1e-4
     h = 1.0 / n
