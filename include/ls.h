@@ -145,6 +145,7 @@ typedef struct {
   int compression_reused;   /* 1 if the compression came from the cache (reuse_compression)
                                or from a file (ls_load) */
   int nx, ny;               /* the grid */
+  int nprob;                /* problems on the grid (ls_build_many) */
 } ls_build_info;
 
 typedef struct ls_handle ls_handle; /* opaque, library-owned */
@@ -169,6 +170,22 @@ void ls_default_opts(ls_opts* o);
  * meets a zero pivot, LS_ETIMEOUT if a device-side wait gave up. */
 int ls_build(const ls_grid* grid, double kappa, const double* b, double tol,
              const ls_opts* opts, void* stream, ls_handle** out);
+
+/* ls_build_many -- nprob independent problems on the same grid and kappa
+ * (potentials b_0 .. b_{nprob-1}, nprob * ny * nx doubles, host or device, in
+ * that order) in one handle: the compression does not depend on b and is made
+ * once (Sec. 3.2); the leaf builds and merges of all problems run as one
+ * forest of nprob trees, every level's nodes of every problem in the same
+ * batched launches, and so does the apply.  On such a handle every vector
+ * argument of ls_apply, ls_matvec, ls_field, ls_solve, ls_solve_transpose and
+ * ls_rhs_plane_wave holds nrhs sets of nprob grid vectors, [nrhs][nprob][ny][nx]
+ * (vector g of a set belongs to problem g), and ls_solve's info has nrhs *
+ * nprob entries in the same order; each problem is solved with its own
+ * operator and its own Krylov space (block GMRES).  The receiver calls and
+ * ls_matvec_noalloc take handles of one problem only (LS_EINVAL).  ls_build is
+ * ls_build_many with nprob = 1. */
+int ls_build_many(const ls_grid* grid, int nprob, double kappa, const double* b, double tol,
+                  const ls_opts* opts, void* stream, ls_handle** out);
 
 /* ls_apply -- q = M f, M ~ (I + B G_p)^-1 the HBS inverse (Algorithm 2,
  * Sec. 4.1); with transpose = 1, q = M^T f: the steps of Algorithm 2 in

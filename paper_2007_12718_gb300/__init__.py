@@ -64,7 +64,7 @@ class BuildInfo(ctypes.Structure):
                 ("bytes_apply", ctypes.c_double), ("factor_bytes", ctypes.c_double),
                 ("pivot_fallbacks", ctypes.c_int), ("sibling_ranks", ctypes.c_int * 32),
                 ("probe_resid_max", ctypes.c_double), ("compression_reused", ctypes.c_int),
-                ("nx", ctypes.c_int), ("ny", ctypes.c_int)]
+                ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nprob", ctypes.c_int)]
 
 
 class ProfileEntry(ctypes.Structure):
@@ -89,6 +89,8 @@ def load_library(path=LIB_PATH):
     lib.ls_default_opts.restype = None
     lib.ls_build.argtypes = [ctypes.POINTER(Grid), dp, vp, dp, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
     lib.ls_build.restype = ip
+    lib.ls_build_many.argtypes = [ctypes.POINTER(Grid), ip, dp, vp, dp, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+    lib.ls_build_many.restype = ip
     for name in ("ls_apply", "ls_matvec"):
         getattr(lib, name).argtypes = [vp, vp, vp, ip, ip, vp]
         getattr(lib, name).restype = ip
@@ -200,7 +202,8 @@ def _ptr(a, dtype, writable=False):
 class Handle:
     def __init__(self, ptr, n):
         self.ptr = ptr
-        self.n = n
+        self.n = n        # grid points of one problem
+        self.nprob = 1    # problems in the handle (ls_build with b of shape (nprob, ny, nx))
 
     def __del__(self):
         if getattr(self, "ptr", None) and _lib is not None:
@@ -215,7 +218,7 @@ class Handle:
                 "bytes_apply": bi.bytes_apply, "factor_bytes": bi.factor_bytes,
                 "pivot_fallbacks": bi.pivot_fallbacks, "probe_resid_max": bi.probe_resid_max,
                 "sibling_ranks": list(bi.sibling_ranks[: bi.levels + 1]),
-                "compression_reused": bool(bi.compression_reused)}
+                "compression_reused": bool(bi.compression_reused), "nprob": bi.nprob}
 
 
 def default_opts():
@@ -235,11 +238,16 @@ def ls_build(n, h, kappa, b, tol, order_matvec=10, order_precond=4, leaf_side=8,
     g = Grid(n, n if ny is None else ny, h, x0, y0)
     o = Opts(order_matvec, order_precond, leaf_side, proxy_width, precision, gmres_maxit, gmres_tol,
              merge_pivoting, top_uncompressed, id_method, wait_limit, woodbury, reuse_compression, rhs_block)
-    bp, keep, _ = _ptr(b, np.float64)
+    bp, keep, nb = _ptr(b, np.float64)
+    if nb % (g.nx * g.ny):
+        raise ValueError("b must hold whole grids")
+    nprob = nb // (g.nx * g.ny)  # b of shape (nprob, ny, nx): nprob problems in one handle
     out = ctypes.c_void_p()
-    _check(lib.ls_build(ctypes.byref(g), kappa, bp, tol, ctypes.byref(o), _stream(stream), ctypes.byref(out)),
-           "ls_build")
-    return Handle(out, g.nx * g.ny)
+    _check(lib.ls_build_many(ctypes.byref(g), nprob, kappa, bp, tol, ctypes.byref(o), _stream(stream),
+                             ctypes.byref(out)), "ls_build_many")
+    H = Handle(out, g.nx * g.ny)
+    H.nprob = nprob
+    return H
 
 
 def ls_save(handle, path, stream=None):
@@ -256,6 +264,7 @@ def ls_load(path, stream=None):
     bi = BuildInfo()
     _check(lib.ls_get_build_info(H.ptr, ctypes.byref(bi)), "ls_get_build_info")
     H.n = bi.nx * bi.ny
+    H.nprob = bi.nprob
     return H
 
 
@@ -264,9 +273,11 @@ def ls_compression_cache_clear():
 
 
 def _nrhs(handle, nelem):
-    if nelem % handle.n:
-        raise ValueError("vector size is not a multiple of the grid size")
-    return nelem // handle.n
+    """Sets of the handle's problems in a vector argument ([nrhs][nprob][ny][nx])."""
+    per = handle.n * getattr(handle, "nprob", 1)
+    if nelem % per:
+        raise ValueError("vector size is not a multiple of the grid size times the number of problems")
+    return nelem // per
 
 
 def ls_apply(handle, f, q, transpose=False, stream=None):
@@ -302,7 +313,7 @@ def ls_solve(handle, f, sigma, stream=None, allow_noconv=False):
     fp, k1, n = _ptr(f, np.complex128)
     sp_, k2, _ = _ptr(sigma, np.complex128, True)
     nr = _nrhs(handle, n)
-    infos = (SolveInfo * nr)()
+    infos = (SolveInfo * (nr * getattr(handle, "nprob", 1)))()
     _check(load_library().ls_solve(handle.ptr, fp, sp_, nr, infos, _stream(stream)), "ls_solve",
            allow=(LS_ENOCONV,) if allow_noconv else ())
     return _infos(infos)
@@ -313,7 +324,7 @@ def ls_solve_transpose(handle, f, sigma, stream=None, allow_noconv=False):
     fp, k1, n = _ptr(f, np.complex128)
     sp_, k2, _ = _ptr(sigma, np.complex128, True)
     nr = _nrhs(handle, n)
-    infos = (SolveInfo * nr)()
+    infos = (SolveInfo * (nr * getattr(handle, "nprob", 1)))()
     _check(load_library().ls_solve_transpose(handle.ptr, fp, sp_, nr, infos, _stream(stream)), "ls_solve_transpose",
            allow=(LS_ENOCONV,) if allow_noconv else ())
     return _infos(infos)

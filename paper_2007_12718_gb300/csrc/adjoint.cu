@@ -129,6 +129,10 @@ int receiver_adjoint(ls_handle* H, const z64* v, z64* g, int nrhs, cudaStream_t 
 using ls::z64;
 
 int ls_set_receivers(ls_handle* H, const double* rx, int nr, void* stream) {
+  if (H && H->nprob != 1) {
+    ls::set_last_error_text("receivers: handles of one problem only");
+    return LS_EINVAL;
+  }
   if (!H || nr < 0 || (nr > 0 && !rx)) return LS_EINVAL;
   if (int rc = ls::check_device(H)) return rc;
   ls::StreamScope scope((cudaStream_t)stream);
@@ -165,6 +169,10 @@ int ls_set_receivers(ls_handle* H, const double* rx, int nr, void* stream) {
 }
 
 int ls_receiver_field(ls_handle* H, const void* sigma, void* u, int nrhs, void* stream) {
+  if (H && H->nprob != 1) {
+    ls::set_last_error_text("receivers: handles of one problem only");
+    return LS_EINVAL;
+  }
   if (!H || !sigma || !u || nrhs < 1 || H->nrec < 1) return LS_EINVAL;
   if (int rc = ls::check_device(H)) return rc;
   ls::StreamScope scope((cudaStream_t)stream);
@@ -183,6 +191,10 @@ int ls_receiver_field(ls_handle* H, const void* sigma, void* u, int nrhs, void* 
 }
 
 int ls_receiver_adjoint(ls_handle* H, const void* v, void* g, int nrhs, void* stream) {
+  if (H && H->nprob != 1) {
+    ls::set_last_error_text("receivers: handles of one problem only");
+    return LS_EINVAL;
+  }
   if (!H || !v || !g || nrhs < 1 || H->nrec < 1) return LS_EINVAL;
   if (int rc = ls::check_device(H)) return rc;
   ls::StreamScope scope((cudaStream_t)stream);
@@ -203,6 +215,10 @@ int ls_receiver_adjoint(ls_handle* H, const void* v, void* g, int nrhs, void* st
 
 int ls_misfit_gradient(ls_handle* H, const double* thetas, int nrhs, const void* d, double* J, void* grad,
                        ls_solve_info* info, void* stream) {
+  if (H && H->nprob != 1) {
+    ls::set_last_error_text("misfit gradient: handles of one problem only");
+    return LS_EINVAL;
+  }
   if (!H || !thetas || nrhs < 1 || !d || !J || H->nrec < 1) return LS_EINVAL;
   if (int rc = ls::check_device(H)) return rc;
   const bool want_grad = grad != nullptr;  // without it only J: no adjoint solve

@@ -469,14 +469,20 @@ __device__ bool gj_inverse_smem(cx<R>* a, int n, int lda, int* piv, cx<R>* col) 
   return true;
 }
 
+// A handle holds G >= 1 problems on the same grid (a forest of G trees of the
+// same geometry, sharing the compression): the nodes of level l are indexed
+// g 2^l + j (problem g, node j of its tree), so the children of node i are 2i
+// and 2i + 1 across the whole forest, and the problems' grid vectors are stacked
+// as one grid of G ny rows.
 struct TreeGeom {
-  int L, s, nx;
+  int L, s, nx, ny, G;
   int cw[32], ch[32];  // child box dims for the cut l -> l+1
 };
 
+// Lower-left grid point of a leaf (leaf = g 2^L + j): rows of problem g start at g ny.
 __device__ __forceinline__ void leaf_origin(const TreeGeom& g, int leaf, int& ox, int& oy) {
   ox = 0;
-  oy = 0;
+  oy = (leaf >> g.L) * g.ny;
   for (int l = 0; l < g.L; ++l) {
     int bit = (leaf >> (g.L - 1 - l)) & 1;
     if (l % 2 == 0) {
@@ -1643,6 +1649,8 @@ TreeGeom make_geom(const ls_handle* H) {
   g.L = H->L;
   g.s = H->s;
   g.nx = H->grid.nx;
+  g.ny = H->grid.ny;
+  g.G = H->nprob;
   for (int l = 0; l < H->L; ++l) {
     g.cw[l] = H->lev[l + 1].w;
     g.ch[l] = H->lev[l + 1].h;
@@ -1661,8 +1669,8 @@ template <class R>
 int apply_prepare(ls_handle* H, cudaStream_t st) {
   if (H->work) return LS_OK;
   const int L = H->L, n = H->s * H->s;
-  size_t vec = (size_t)2 * ((size_t)1 << L) * n;
-  for (int l = 1; l <= L; ++l) vec += (size_t)3 * ((size_t)1 << l) * std::max(1, H->lev[l].k) * 2;
+  size_t vec = (size_t)2 * ((size_t)H->nprob << L) * n;
+  for (int l = 1; l <= L; ++l) vec += (size_t)3 * ((size_t)H->nprob << l) * std::max(1, H->lev[l].k) * 2;
   H->work_bytes = sizeof(cx<R>) * vec;
   int rc;
   if ((rc = dalloc(&H->work, H->work_bytes))) return rc;
@@ -1891,7 +1899,7 @@ int invert_checked(ls_handle* H, cx<R>* Z, int n, int lda, long long sZ, int P, 
 template <class R>
 int merge_woodbury(ls_handle* H, int l, cx<R>* X, const cx<R>* Sc, cudaStream_t st) {
   const LevelData& ch = H->lev[l + 1];
-  const int P = 1 << l, kc = ch.k, n2 = 2 * kc, r = ch.gr;
+  const int P = H->nprob << l, kc = ch.k, n2 = 2 * kc, r = ch.gr;
   const long long sX = (long long)n2 * n2, kk = (long long)kc * kc, kr = (long long)kc * r, rr = (long long)r * r;
   const cx<R>* Lf = reinterpret_cast<const cx<R>*>(ch.GL);
   const cx<R>* Rf = reinterpret_cast<const cx<R>*>(ch.GR);
@@ -1950,7 +1958,7 @@ int merge_woodbury(ls_handle* H, int l, cx<R>* X, const cx<R>* Sc, cudaStream_t 
     gemm<R>(st, false, true, kc, kc, r, on, A1, r, kr, Rf, r, 0, ze, X12, n2, sX, P);
     gemm<R>(st, false, true, kc, kc, r, on, A2, r, kr, Lf, r, 0, ze, X21, n2, sX, P);
     fl += 2 * 8.0 * (double)kk * r;
-    H->factor_bytes -= sizeof(cx<R>) * (double)kk;  // the X11 block is not read
+    H->factor_bytes -= sizeof(cx<R>) * (double)P * kk;  // the X11 blocks are not read
   } else {
     gemm<R>(st, false, false, kc, r, r, on, A1, r, kr, Mm, r, rr, ze, B, r, kr, P);            // A1 M
     gemm<R>(st, false, true, kc, kc, r, mone, B, r, kr, Rf, r, 0, ze, X12, n2, sX, P);         // -A1 M R^T
@@ -1978,7 +1986,7 @@ void apply_bytes(ls_handle* H) {
   double fb = H->factor_bytes;
   for (int l = 1; l <= H->L - 1; ++l) {
     const double n2 = 2.0 * H->lev[l + 1].k;
-    fb += sizeof(cx<R>) * (double)(1 << l) * n2 * n2;
+    fb += sizeof(cx<R>) * (double)(H->nprob << l) * n2 * n2;
   }
   H->bytes_apply = fb + (double)H->grid.nx * H->grid.ny * (16.0 * 2);
 }
@@ -2002,7 +2010,7 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const Le
   if (wait_level && (rc = wait_level(L))) return rc;
   LevelData& lf = H->lev[L];
   const int kL = lf.k;
-  const size_t nleaf = (size_t)1 << L;
+  const size_t nleaf = (size_t)H->nprob << L;
   if ((rc = dalloc(&lf.X, sizeof(cx<R>) * nleaf * n * n))) return rc;
   if ((rc = dalloc(&H->XBU, sizeof(cx<R>) * nleaf * n * std::max(kL, 1)))) return rc;
   if ((rc = dalloc(&lf.S, sizeof(cx<R>) * nleaf * std::max(kL * kL, 1)))) return rc;
@@ -2040,7 +2048,7 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const Le
     }
     LevelData& lv = H->lev[l];
     const LevelData& ch = H->lev[l + 1];
-    const int P = 1 << l, kc = ch.k, n2 = 2 * kc;
+    const int P = H->nprob << l, kc = ch.k, n2 = 2 * kc;
     const bool woodbury = kc > 0 && ch.gr > 0;
     // scratch of X in the Schur form: the larger of (pivoted-inverse panels +
     // pivots) and Y1, Y2, a copy of Z with the blocked-inverse panels (width <=
@@ -2169,7 +2177,7 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const Le
         copy_block_kernel<R><<<gc, 256, 0, st>>>(X12, n2, sX, Y1, kc, kk, kc, kc);
         if ((rc = check_launch("root blocks"))) return rc;
         prof_end(tg, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * 4.0 * kk, 0.0);
-        H->factor_bytes -= sizeof(cx<R>) * (double)kk;  // the X11 block is not read
+        H->factor_bytes -= sizeof(cx<R>) * (double)P * kk;  // the X11 blocks are not read
       } else {
         gemm<R>(st, false, false, kc, kc, kc, mone, X22, n2, sX, Y2, kc, kk, zero<R>(), X21, n2, sX, P);  // -W Y2
         gemm<R>(st, false, false, kc, kc, kc, mone, Y1, kc, kk, X22, n2, sX, zero<R>(), X12, n2, sX, P);  // -Y1 W
@@ -2309,7 +2317,7 @@ template <class R>
 __global__ void gather_leaves_kernel(TreeGeom g, const z64* const* __restrict__ fslot, cx<R>* __restrict__ F) {
   const int n = g.s * g.s;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  long long nl = 1LL << g.L;
+  long long nl = (long long)g.G << g.L;
   if (t >= nl * n) return;
   const z64* f = *fslot;
   int leaf = (int)(t / n), i = (int)(t % n);
@@ -2323,7 +2331,7 @@ template <class R>
 __global__ void scatter_leaves_kernel(TreeGeom g, const cx<R>* __restrict__ Q, z64* const* __restrict__ qslot) {
   const int n = g.s * g.s;
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  long long nl = 1LL << g.L;
+  long long nl = (long long)g.G << g.L;
   if (t >= nl * n) return;
   z64* q = *qslot;
   int leaf = (int)(t / n), i = (int)(t % n);
@@ -2469,14 +2477,14 @@ __global__ void set_slots_kernel(z64** slots, const z64* f, z64* q) {
 template <class R>
 int apply_core(ls_handle* H, z64** slots, cudaStream_t st) {
   const int L = H->L, n = H->s * H->s;
-  const long long nleaf = 1LL << L;
+  const long long nleaf = (long long)H->nprob << L;
   TreeGeom g = make_geom(H);
   cx<R>* F = reinterpret_cast<cx<R>*>(H->work);  // leaf blocks of f
   cx<R>* Rl = F + nleaf * n;                      // r = X f on the leaves
   cx<R>* p = Rl + nleaf * n;
   std::vector<cx<R>*> rt(L + 1), wt(L + 1), tmp(L + 1);
   for (int l = 1; l <= L; ++l) {
-    size_t sz = ((size_t)1 << l) * std::max(1, H->lev[l].k) * 2;
+    size_t sz = ((size_t)H->nprob << l) * std::max(1, H->lev[l].k) * 2;
     rt[l] = p;
     p += sz;
     wt[l] = p;
@@ -2505,7 +2513,7 @@ int apply_core(ls_handle* H, z64** slots, cudaStream_t st) {
   }
   // upward pass: r~_tau = U^T X [r~_a; r~_b]  (Eq. (28)); X [.;.] goes to the child-level scratch
   for (int l = L - 1; l >= 1; --l) {
-    const int P = 1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
+    const int P = H->nprob << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
     if (P >= kFusedMinNodes && sizeof(cx<R>) * 2 * n2 <= 48 * 1024) {
       count_launch();
       up_node_kernel<R><<<P, 256, sizeof(cx<R>) * 2 * n2, st>>>(n2, kp, reinterpret_cast<const cx<R>*>(H->lev[l].X),
@@ -2520,23 +2528,25 @@ int apply_core(ls_handle* H, z64** slots, cudaStream_t st) {
   }
   // root: q = X_0 [r~_a; r~_b];  w~_a = G q_b, w~_b = G^T q_a  (Eq. (29), Lemma 4.1)
   {
-    const int kc = H->lev[1].k, n2 = 2 * kc;
+    const int kc = H->lev[1].k, n2 = 2 * kc, G = H->nprob;  // one root per problem
+    const long long sX = (long long)n2 * n2;
+    const size_t pitch = sizeof(cx<R>) * n2, width = sizeof(cx<R>) * kc;
     cx<R>* qr = tmp[1];
     const cx<R>* G1 = reinterpret_cast<const cx<R>*>(H->lev[1].Gsib);
     const cx<R>* X0 = reinterpret_cast<const cx<R>*>(H->lev[0].X);  // [., Y1; Y2, W]
     cx<R>* tb = wt[1] + kc;
-    LS_CUDA_TRY(cudaMemcpyAsync(tb, rt[1] + kc, sizeof(cx<R>) * kc, cudaMemcpyDeviceToDevice, st));
-    gemv<R>(st, false, kc, kc, mone, X0 + (size_t)kc * n2, n2, 0, rt[1], 0, one<R>(), tb, 0, 1);  // r_b - Y2 r_a
-    gemv<R>(st, false, kc, kc, one<R>(), X0 + (size_t)kc * n2 + kc, n2, 0, tb, 0, zero<R>(), qr + kc, 0, 1);
-    LS_CUDA_TRY(cudaMemcpyAsync(qr, rt[1], sizeof(cx<R>) * kc, cudaMemcpyDeviceToDevice, st));
-    gemv<R>(st, false, kc, kc, mone, X0 + kc, n2, 0, qr + kc, 0, one<R>(), qr, 0, 1);  // q_a = r_a - Y1 q_b
-    gemv<R>(st, false, kc, kc, one<R>(), G1, kc, 0, qr + kc, 0, zero<R>(), wt[1], 0, 1);
-    gemv<R>(st, true, kc, kc, one<R>(), G1, kc, 0, qr, 0, zero<R>(), wt[1] + kc, 0, 1);
+    LS_CUDA_TRY(cudaMemcpy2DAsync(tb, pitch, rt[1] + kc, pitch, width, G, cudaMemcpyDeviceToDevice, st));
+    gemv<R>(st, false, kc, kc, mone, X0 + (size_t)kc * n2, n2, sX, rt[1], n2, one<R>(), tb, n2, G);  // r_b - Y2 r_a
+    gemv<R>(st, false, kc, kc, one<R>(), X0 + (size_t)kc * n2 + kc, n2, sX, tb, n2, zero<R>(), qr + kc, n2, G);
+    LS_CUDA_TRY(cudaMemcpy2DAsync(qr, pitch, rt[1], pitch, width, G, cudaMemcpyDeviceToDevice, st));
+    gemv<R>(st, false, kc, kc, mone, X0 + kc, n2, sX, qr + kc, n2, one<R>(), qr, n2, G);  // q_a = r_a - Y1 q_b
+    gemv<R>(st, false, kc, kc, one<R>(), G1, kc, 0, qr + kc, n2, zero<R>(), wt[1], n2, G);
+    gemv<R>(st, true, kc, kc, one<R>(), G1, kc, 0, qr, n2, zero<R>(), wt[1] + kc, n2, G);
   }
   // downward pass, l = 1 .. L-1:  q~ = X ([r~_a; r~_b] - diag(S_a,S_b) U w~),
   // then w~_children = offdiag(G) q~ + U w~ (Lemma 4.1)
   for (int l = 1; l <= L - 1; ++l) {
-    const int P = 1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
+    const int P = H->nprob << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
     const cx<R>* U = reinterpret_cast<const cx<R>*>(H->lev[l].U);
     const cx<R>* Sc = reinterpret_cast<const cx<R>*>(H->lev[l + 1].S);
     const cx<R>* X = reinterpret_cast<const cx<R>*>(H->lev[l].X);
@@ -2910,13 +2920,13 @@ int transpose_batch(bool fp64, const void* src, int M, int N, int batch, void* d
 template <class R>
 std::vector<ApplyOp> apply_ops(ls_handle* H) {
   const int L = H->L, n = H->s * H->s;
-  const long long nleaf = 1LL << L;
+  const long long nleaf = (long long)H->nprob << L;
   cx<R>* F = reinterpret_cast<cx<R>*>(H->work);
   cx<R>* Rl = F + nleaf * n;
   cx<R>* p = Rl + nleaf * n;
   std::vector<cx<R>*> rt(L + 1), wt(L + 1), tmp(L + 1);
   for (int l = 1; l <= L; ++l) {
-    size_t sz = ((size_t)1 << l) * std::max(1, H->lev[l].k) * 2;
+    size_t sz = ((size_t)H->nprob << l) * std::max(1, H->lev[l].k) * 2;
     rt[l] = p;
     p += sz;
     wt[l] = p;
@@ -2977,7 +2987,7 @@ std::vector<ApplyOp> apply_ops(ls_handle* H) {
   // an uncompressed level (U = I) skips its U and U^T products
   auto identity_u = [&](int l) { return l <= H->opts.top_uncompressed && H->lev[l].k == 2 * H->lev[l + 1].k; };
   for (int l = L - 1; l >= 1; --l) {                                                 // up pass (Eq. 28)
-    const int P = 1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
+    const int P = H->nprob << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
     if (identity_u(l)) {
       gemv(n2, n2, H->lev[l].X, n2, (long long)n2 * n2, rt[l + 1], n2, rt[l], n2, P, true);
       continue;
@@ -2986,16 +2996,17 @@ std::vector<ApplyOp> apply_ops(ls_handle* H) {
     gemv(kp, n2, H->lev[l].UT, n2, 0, tmp[l + 1], n2, rt[l], kp, P, true);
   }
   {                                                                                  // root (Eq. 29)
-    const int kc = H->lev[1].k, n2 = 2 * kc;
+    const int kc = H->lev[1].k, n2 = 2 * kc, G = H->nprob;                           // one root per problem
+    const long long sX = (long long)n2 * n2;
     const cx<R>* X0 = reinterpret_cast<const cx<R>*>(H->lev[0].X);  // [., Y1; Y2, W]
-    gemv(kc, kc, X0 + (size_t)kc * n2, n2, 0, rt[1], 0, wt[1] + kc, 0, 1, true, -1.0, rt[1] + kc, 0);  // r_b - Y2 r_a
-    gemv(kc, kc, X0 + (size_t)kc * n2 + kc, n2, 0, wt[1] + kc, 0, tmp[1] + kc, 0, 1, true);           // q_b = W (.)
-    gemv(kc, kc, X0 + kc, n2, 0, tmp[1] + kc, 0, tmp[1], 0, 1, true, -1.0, rt[1], 0);                 // q_a = r_a - Y1 q_b
-    gemv(kc, kc, H->lev[1].Gsib, kc, 0, tmp[1] + kc, 0, wt[1], 0, 1, false);
-    gemv(kc, kc, H->lev[1].GT, kc, 0, tmp[1], 0, wt[1] + kc, 0, 1, true);
+    gemv(kc, kc, X0 + (size_t)kc * n2, n2, sX, rt[1], n2, wt[1] + kc, n2, G, true, -1.0, rt[1] + kc, n2);  // r_b - Y2 r_a
+    gemv(kc, kc, X0 + (size_t)kc * n2 + kc, n2, sX, wt[1] + kc, n2, tmp[1] + kc, n2, G, true);            // q_b = W (.)
+    gemv(kc, kc, X0 + kc, n2, sX, tmp[1] + kc, n2, tmp[1], n2, G, true, -1.0, rt[1], n2);                  // q_a = r_a - Y1 q_b
+    gemv(kc, kc, H->lev[1].Gsib, kc, 0, tmp[1] + kc, n2, wt[1], n2, G, false);
+    gemv(kc, kc, H->lev[1].GT, kc, 0, tmp[1], n2, wt[1] + kc, n2, G, true);
   }
   for (int l = 1; l <= L - 1; ++l) {                                                 // down pass (Lemma 4.1)
-    const int P = 1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
+    const int P = H->nprob << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
     const cx<R>* Sc = reinterpret_cast<const cx<R>*>(H->lev[l + 1].S);
     cx<R>* Uw = wt[l + 1];  // U w~ (w~ itself when U = I)
     if (identity_u(l))
@@ -3039,13 +3050,13 @@ std::vector<ApplyOp> apply_ops(ls_handle* H) {
 template <class R>
 std::vector<ApplyOp> apply_ops_transpose(ls_handle* H) {
   const int L = H->L, n = H->s * H->s;
-  const long long nleaf = 1LL << L;
+  const long long nleaf = (long long)H->nprob << L;
   cx<R>* F = reinterpret_cast<cx<R>*>(H->work);
   cx<R>* Rl = F + nleaf * n;
   cx<R>* p = Rl + nleaf * n;
   std::vector<cx<R>*> rt(L + 1), wt(L + 1), tmp(L + 1);
   for (int l = 1; l <= L; ++l) {
-    size_t sz = ((size_t)1 << l) * std::max(1, H->lev[l].k) * 2;
+    size_t sz = ((size_t)H->nprob << l) * std::max(1, H->lev[l].k) * 2;
     rt[l] = p;
     p += sz;
     wt[l] = p;
@@ -3091,7 +3102,7 @@ std::vector<ApplyOp> apply_ops_transpose(ls_handle* H) {
   leafop(1, F, nullptr);                                                              // F <- g
   gemv(kL, n, H->XBUT, n, (long long)kL * n, F, n, wt[L], kL, (int)nleaf, true, -1.0);
   for (int l = L - 1; l >= 1; --l) {
-    const int P = 1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
+    const int P = H->nprob << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
     const cx<R>* STc = reinterpret_cast<const cx<R>*>(H->lev[l + 1].ST);
     gemv(kc, kc, H->lev[l + 1].Gsib, kc, 0, wt[l + 1] + kc, n2, tmp[l + 1], n2, P, false);       // Gamma w~
     gemv(kc, kc, H->lev[l + 1].GT, kc, 0, wt[l + 1], n2, tmp[l + 1] + kc, n2, P, true);
@@ -3102,18 +3113,19 @@ std::vector<ApplyOp> apply_ops_transpose(ls_handle* H) {
     gemv(kp, n2, H->lev[l].UT, n2, 0, tmp[l + 1], n2, wt[l], kp, P, true);            // w~_l
   }
   {
-    const int kc = H->lev[1].k, n2 = 2 * kc;
-    gemv(kc, kc, H->lev[1].Gsib, kc, 0, wt[1] + kc, 0, tmp[1], 0, 1, false);
-    gemv(kc, kc, H->lev[1].GT, kc, 0, wt[1], 0, tmp[1] + kc, 0, 1, true);
+    const int kc = H->lev[1].k, n2 = 2 * kc, G = H->nprob;  // one root per problem
+    const long long sX = (long long)n2 * n2;
+    gemv(kc, kc, H->lev[1].Gsib, kc, 0, wt[1] + kc, n2, tmp[1], n2, G, false);
+    gemv(kc, kc, H->lev[1].GT, kc, 0, wt[1], n2, tmp[1] + kc, n2, G, true);
     // r~_1 = X_0^T v with X_0 kept as [., Y1; Y2, W] (so X_0^T's blocks are [., Y2^T; Y1^T, W^T]):
     // [v_a - Y2^T u; u], u = W^T (v_b - Y1^T v_a)
     const cx<R>* XT0 = reinterpret_cast<const cx<R>*>(H->lev[0].XT);
-    gemv(kc, kc, XT0 + (size_t)kc * n2, n2, 0, tmp[1], 0, wt[1], 0, 1, true, -1.0, tmp[1] + kc, 0);
-    gemv(kc, kc, XT0 + (size_t)kc * n2 + kc, n2, 0, wt[1], 0, rt[1] + kc, 0, 1, true);
-    gemv(kc, kc, XT0 + kc, n2, 0, rt[1] + kc, 0, rt[1], 0, 1, true, -1.0, tmp[1], 0);
+    gemv(kc, kc, XT0 + (size_t)kc * n2, n2, sX, tmp[1], n2, wt[1], n2, G, true, -1.0, tmp[1] + kc, n2);
+    gemv(kc, kc, XT0 + (size_t)kc * n2 + kc, n2, sX, wt[1], n2, rt[1] + kc, n2, G, true);
+    gemv(kc, kc, XT0 + kc, n2, sX, rt[1] + kc, n2, rt[1], n2, G, true, -1.0, tmp[1], n2);
   }
   for (int l = 1; l <= L - 1; ++l) {
-    const int P = 1 << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
+    const int P = H->nprob << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
     gemv(n2, kp, H->lev[l].U, kp, 0, rt[l], kp, tmp[l + 1], n2, P, true);             // U r~_l
     gemv(n2, n2, H->lev[l].XT, n2, (long long)n2 * n2, tmp[l + 1], n2, rt[l + 1], n2, P, true, 1.0, rt[l + 1],
          n2);                                                                          // r~_{l+1} = t_l + X^T U r~_l
@@ -3236,7 +3248,7 @@ int apply_transpose_init(ls_handle* H, cudaStream_t st) {
   if ((rc = level_transposes(H, st))) return rc;
   for (int l = 0; l <= L; ++l) {
     LevelData& lv = H->lev[l];
-    const int nx = l == L ? n : 2 * H->lev[l + 1].k, P = 1 << l;
+    const int nx = l == L ? n : 2 * H->lev[l + 1].k, P = H->nprob << l;
     if (!lv.XT) {
       if ((rc = dalloc(&lv.XT, es * (size_t)P * std::max(nx * nx, 1)))) return rc;
       if ((rc = transpose_batch(fp64, lv.X, nx, nx, P, lv.XT, st))) return rc;
@@ -3247,8 +3259,8 @@ int apply_transpose_init(ls_handle* H, cudaStream_t st) {
     }
   }
   const int kL = H->lev[L].k;
-  if ((rc = dalloc(&H->XBUT, es * ((size_t)1 << L) * n * std::max(kL, 1)))) return rc;
-  if ((rc = transpose_batch(fp64, H->XBU, n, kL, 1 << L, H->XBUT, st))) return rc;
+  if ((rc = dalloc(&H->XBUT, es * ((size_t)H->nprob << L) * n * std::max(kL, 1)))) return rc;
+  if ((rc = transpose_batch(fp64, H->XBU, n, kL, H->nprob << L, H->XBUT, st))) return rc;
   std::vector<ApplyOp> ops = fp64 ? apply_ops_transpose<double>(H) : apply_ops_transpose<float>(H);
   if (sizeof(ApplyOp) * ops.size() > 200 * 1024) {
     set_last_error_text("tree too deep for the transposed apply");
@@ -3314,7 +3326,7 @@ __global__ void __launch_bounds__(256) gather_block_kernel(TreeGeom g, const z64
                                                            cx<R>* __restrict__ F) {
   __shared__ cx<R> tile[32][33];
   const int n = g.s * g.s;
-  const long long tot = (1LL << g.L) * n, e0 = (long long)blockIdx.x * 32;
+  const long long tot = ((long long)g.G << g.L) * n, e0 = (long long)blockIdx.x * 32;
   const int r0 = blockIdx.y * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const long long e = e0 + tx;
   long long gi = -1;
@@ -3337,7 +3349,7 @@ __global__ void __launch_bounds__(256) scatter_block_kernel(TreeGeom g, const cx
                                                             int nb, z64* __restrict__ q) {
   __shared__ cx<R> tile[32][33];
   const int n = g.s * g.s;
-  const long long tot = (1LL << g.L) * n, e0 = (long long)blockIdx.x * 32;
+  const long long tot = ((long long)g.G << g.L) * n, e0 = (long long)blockIdx.x * 32;
   const int r0 = blockIdx.y * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int ee = ty; ee < 32; ee += 8)
     if (e0 + ee < tot && r0 + tx < nb) tile[tx][ee] = Q[(e0 + ee) * nb + r0 + tx];
@@ -3354,8 +3366,8 @@ __global__ void __launch_bounds__(256) scatter_block_kernel(TreeGeom g, const cx
 
 // Entries of the one-vector apply workspace (its layout is fixed by apply_prepare).
 size_t apply_work_entries(const ls_handle* H) {
-  size_t vec = (size_t)2 * ((size_t)1 << H->L) * H->s * H->s;
-  for (int l = 1; l <= H->L; ++l) vec += (size_t)3 * ((size_t)1 << l) * std::max(1, H->lev[l].k) * 2;
+  size_t vec = (size_t)2 * ((size_t)H->nprob << H->L) * H->s * H->s;
+  for (int l = 1; l <= H->L; ++l) vec += (size_t)3 * ((size_t)H->nprob << l) * std::max(1, H->lev[l].k) * 2;
   return vec;
 }
 
@@ -3390,7 +3402,7 @@ template <class R>
 int apply_block_t(ls_handle* H, const std::vector<ApplyOp>& ops, const z64* f, z64* q, int nb, cudaStream_t st,
                   double* flops) {
   const int L = H->L, n = H->s * H->s;
-  const long long nleaf = 1LL << L, N = (long long)H->grid.nx * H->grid.ny;
+  const long long nleaf = (long long)H->nprob << L, N = (long long)H->nprob * H->grid.nx * H->grid.ny;
   const size_t went = apply_work_entries(H);
   const size_t need = sizeof(cx<R>) * went * (size_t)nb;
   int rc;
@@ -3524,21 +3536,27 @@ int simt_zgemm(cudaStream_t st, bool ta, bool tb, int M, int N, int K, z64 alpha
 
 int rhs_block_size(const ls_handle* H, int nrhs) {
   if (H->opts.rhs_block > 0) return std::max(1, std::min(nrhs, H->opts.rhs_block));
-  // automatic: up to 256, and one slab of the block's grid vectors within 1 GiB
-  const long long N = (long long)H->grid.nx * H->grid.ny;
+  // automatic: up to 256, and one slab of the block's vectors within 1 GiB
+  const long long N = (long long)H->nprob * H->grid.nx * H->grid.ny;
   const long long fit = (1LL << 30) / (16LL * N);
   return (int)std::max(1LL, std::min<long long>({(long long)nrhs, 256LL, fit}));
 }
 
-int hbs_apply(ls_handle* H, const z64* f, z64* q, int nrhs, int transpose, cudaStream_t st) {
-  const long long N = (long long)H->grid.nx * H->grid.ny;
+int hbs_apply(ls_handle* H, const z64* f, z64* q, int nvec, int transpose, cudaStream_t st) {
+  // nvec grid vectors = nvec / nprob vectors of the forest (one per problem each)
+  if (nvec % H->nprob) {
+    set_last_error_text("right-hand sides must come in whole sets of the handle's problems");
+    return LS_EINVAL;
+  }
+  const int nrhs = nvec / H->nprob;
+  const long long N = (long long)H->nprob * H->grid.nx * H->grid.ny;
   int rc;
   const int nbk = rhs_block_size(H, nrhs);
   if (nbk > 1) {  // blocks of right-hand sides, each factor read once per block
     for (int r0 = 0; r0 < nrhs; r0 += nbk) {
       const int nb = std::min(nbk, nrhs - r0);
       rc = nb > 1 ? hbs_apply_block(H, f + r0 * N, q + r0 * N, nb, transpose, st)
-                  : hbs_apply(H, f + r0 * N, q + r0 * N, 1, transpose, st);
+                  : hbs_apply(H, f + r0 * N, q + r0 * N, H->nprob, transpose, st);
       if (rc) return rc;
     }
     return LS_OK;

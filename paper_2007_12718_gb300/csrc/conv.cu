@@ -93,14 +93,16 @@ __global__ void twiddle_kernel(z64* tw, int L) {
 
 // Pass 1: rows. in: [rhs][nrow][ld_in] (first nvalid entries used); out: [rhs][nrow][L].
 // bsc (may be null): the input is scaled by kap2 * bsc[row][i] (the transposed
-// operator convolves B x).
+// operator convolves B x); right-hand side r takes the b of problem r mod nprob
+// (bsc holds nprob potentials of nrow x nvalid).
 __global__ void rows_fwd_kernel(const z64* in, int ld_in, int nvalid, long long in_rhs_stride, z64* out, long long out_rhs_stride, int L, int logL,
-                                const z64* __restrict__ tw, const double* __restrict__ bsc, double kap2) {
+                                const z64* __restrict__ tw, const double* __restrict__ bsc, double kap2, int nprob) {
   extern __shared__ z64 sm[];
   z64* s = sm;
   z64* stw = sm + L;
   int row = blockIdx.x, rhs = blockIdx.y;
   const z64* src = in + rhs * in_rhs_stride + (long long)row * ld_in;
+  if (bsc) bsc += (long long)(rhs % nprob) * gridDim.x * nvalid;
   for (int i = threadIdx.x; i < L / 2; i += blockDim.x) stw[i] = tw[i];
   for (int i = threadIdx.x; i < L; i += blockDim.x) {
     z64 v = i < nvalid ? src[i] : mk<double>(0.0, 0.0);
@@ -162,12 +164,13 @@ __global__ void cols_kernel(z64* __restrict__ W, long long rhs_stride, int Lx, i
 // (forward), y = x + conv (transpose: B was applied to the input), y = conv (field).
 __global__ void rows_inv_kernel(const z64* __restrict__ W, long long w_rhs_stride, int L, int logL,
                                 const z64* __restrict__ tw, const z64* __restrict__ x, const double* __restrict__ b,
-                                double kap2, int nx, long long g_rhs_stride, z64* __restrict__ y, int mode) {
+                                double kap2, int nx, long long g_rhs_stride, z64* __restrict__ y, int mode, int nprob) {
   extern __shared__ z64 sm[];
   z64* s = sm;
   z64* stw = sm + L;
   int row = blockIdx.x, rhs = blockIdx.y;
   const z64* src = W + rhs * w_rhs_stride + (long long)row * L;
+  b += (long long)(rhs % nprob) * gridDim.x * nx;  // the potential of this right-hand side's problem
   for (int i = threadIdx.x; i < L / 2; i += blockDim.x) stw[i] = tw[i];
   for (int i = threadIdx.x; i < L; i += blockDim.x) s[i] = src[i];
   __syncthreads();
@@ -290,7 +293,7 @@ int conv_setup(ls_handle* H, cudaStream_t st) {
   cudaFuncSetAttribute(rows_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
   count_launch();
   rows_fwd_kernel<<<dim3(H->Ly, 1), 256, smr, st>>>(full, H->Lx, H->Lx, 0, full, 0, H->Lx, H->logLx, H->tw_x,
-                                                    nullptr, 0.0);
+                                                    nullptr, 0.0, 1);
   int C = cols_per_block(H->Ly);
   LS_CUDA_TRY(launch_cols(C, H->Lx / C, 1, st, full, 0, H->Lx, H->logLx, H->Ly, H->Ly, H->logLy, H->tw_y, nullptr,
                           nxq, nyq, 1));
@@ -323,7 +326,7 @@ int conv_apply(ls_handle* H, const z64* x, z64* y, int nrhs, int mode, cudaStrea
   count_launch();
   rows_fwd_kernel<<<dim3(ny, nrhs), 256, smr, st>>>(x, nx, nx, g_stride, H->convbuf, w_stride, H->Lx, H->logLx,
                                                     H->tw_x, mode == CONV_TRANSPOSE ? H->b : nullptr,
-                                                    H->kappa * H->kappa);
+                                                    H->kappa * H->kappa, H->nprob);
   prof_end(tk, PR_MV_ROWS_FWD, st, R * (16.0 * N + 16.0 * W) + (mode == CONV_TRANSPOSE ? 8.0 * N : 0.0),
            R * 5.0 * W * H->logLx);
   int C = cols_per_block(H->Ly);
@@ -335,7 +338,7 @@ int conv_apply(ls_handle* H, const z64* x, z64* y, int nrhs, int mode, cudaStrea
   tk = prof_begin(st);
   count_launch();
   rows_inv_kernel<<<dim3(ny, nrhs), 256, smr, st>>>(H->convbuf, w_stride, H->Lx, H->logLx, H->tw_x, x, H->b,
-                                                    H->kappa * H->kappa, nx, g_stride, y, mode);
+                                                    H->kappa * H->kappa, nx, g_stride, y, mode, H->nprob);
   prof_end(tk, PR_MV_ROWS_INV, st,
            R * (16.0 * W + (mode == CONV_FIELD ? 16.0 : mode == CONV_TRANSPOSE ? 32.0 : 40.0) * N),
            R * 5.0 * W * H->logLx);
@@ -404,6 +407,10 @@ extern "C" int ls_matvec_noalloc(ls_handle* H, const void* xv, void* yv, int nrh
   using namespace ls;
   if (!H || !xv || !yv || nrhs < 1) return LS_EINVAL;
   if (int rc = check_device(H)) return rc;
+  if (H->nprob != 1) {
+    set_last_error_text("ls_matvec_noalloc: handles of one problem only");
+    return LS_EINVAL;
+  }
   const int nx = H->grid.nx, ny = H->grid.ny;
   const long long need = (long long)nrhs * ny * H->Lx;
   if (need > kNoAllocScratchElems) {
@@ -426,12 +433,12 @@ extern "C" int ls_matvec_noalloc(ls_handle* H, const void* xv, void* yv, int nrh
   LS_CUDA_TRY(cudaFuncSetAttribute(rows_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr));
   count_launch();
   rows_fwd_kernel<<<dim3(ny, nrhs), 256, smr, st>>>(x, nx, nx, g_stride, W, w_stride, H->Lx, H->logLx, H->tw_x,
-                                                    nullptr, 0.0);
+                                                    nullptr, 0.0, 1);
   int C = cols_per_block(H->Ly);
   LS_CUDA_TRY(launch_cols(C, H->Lx / C, nrhs, st, W, w_stride, H->Lx, H->logLx, ny, H->Ly, H->logLy, H->tw_y, H->spec,
                           H->Lx / 2, H->Ly / 2, 0));
   count_launch();
   rows_inv_kernel<<<dim3(ny, nrhs), 256, smr, st>>>(W, w_stride, H->Lx, H->logLx, H->tw_x, x, H->b, H->kappa * H->kappa,
-                                                    nx, g_stride, y, ls::CONV_FORWARD);
+                                                    nx, g_stride, y, ls::CONV_FORWARD, 1);
   return check_launch("ls_matvec_noalloc");
 }

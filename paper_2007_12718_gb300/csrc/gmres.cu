@@ -453,8 +453,11 @@ int solve_one(ls_handle* H, const z64* f, z64* sigma, ls_solve_info* info, int t
 // arithmetic (flexible right preconditioning, CGS2, complex Givens rotations,
 // zero initial guess, no restart) run side by side.  Each iteration applies the
 // preconditioner and the operator to the nb current vectors at once
-// (hbs_apply_block, conv_apply with nrhs = nb), so every factor and the kernel
-// spectrum are read once per iteration for the block.  A right-hand side whose
+// (hbs_apply, conv_apply with nrhs = nb), so every factor and the kernel
+// spectrum are read once per iteration for the block.  On a handle of several
+// problems the block holds whole sets of them, right-hand side r belonging to
+// problem r mod nprob (its own potential in the matvec, its own tree in the
+// apply).  A right-hand side whose
 // residual estimate reaches the tolerance is frozen (its later vectors are
 // zero, its kernels return early); the block stops when all are frozen or at
 // gmres_maxit.  Vectors: one slab of nb grid vectors per Krylov vector V_j and
@@ -795,7 +798,7 @@ int solve_block(ls_handle* H, const z64* f, z64* sigma, int nb, ls_solve_info* i
     z64 *Vj = hVt[j], *Zj, *Vn;
     if ((rc = slab_at(2 * j + 1, &Zj)) || (rc = table(Zt, hZt, j, Zj))) return rc;
     if ((rc = slab_at(2 * j + 2, &Vn)) || (rc = table(Vt, hVt, j + 1, Vn))) return rc;
-    if ((rc = hbs_apply_block(H, Vj, Zj, nb, transpose, st))) return rc;
+    if ((rc = hbs_apply(H, Vj, Zj, nb, transpose, st))) return rc;
     if ((rc = conv_apply(H, Zj, w, nb, mode, st))) return rc;
     const int tk = prof_begin(st);
     const z64* const* Vc = Vt;
@@ -865,7 +868,12 @@ int gmres_solve(ls_handle* H, const z64* f, z64* sigma, int nrhs, ls_solve_info*
   }
   host_mark("gmres_workspace");
   int worst = LS_OK;
-  const int nbk = rhs_block_size(H, nrhs);
+  // blocks of whole sets of the handle's problems (one right-hand side per problem each)
+  if (nrhs % H->nprob) {
+    set_last_error_text("right-hand sides must come in whole sets of the handle's problems");
+    return LS_EINVAL;
+  }
+  const int nbk = H->nprob * rhs_block_size(H, nrhs / H->nprob);
   for (int r = 0; r < nrhs; r += nbk) {
     const int nb = std::min(nbk, nrhs - r);
     int rc = nb > 1 ? solve_block(H, f + r * N, sigma + r * N, nb, info ? info + r : nullptr, transpose, st)

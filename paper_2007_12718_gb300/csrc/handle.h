@@ -33,6 +33,7 @@ struct ls_handle {
   double kappa = 0, tol = 0;
   ls_opts opts;
   int L = 0, s = 0, ring = 0;
+  int nprob = 1;  // problems on the grid (a forest of nprob trees sharing one compression)
   int prec = LS_FP32;
   int nsm = 0;  // SMs on the device
   ls::KernelSpec ks_prec, ks_mv;

@@ -648,11 +648,12 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
   return rc;
 }
 
-static int build_impl(const ls_grid* grid, double kappa, const double* b, double tol, const ls_opts* opts,
+static int build_impl(const ls_grid* grid, int nprob, double kappa, const double* b, double tol, const ls_opts* opts,
                       cudaStream_t st, ls_handle** out) {
   ls::g_build_t0 = std::chrono::steady_clock::now();
   ls_handle* H = new ls_handle();
   *out = H;
+  H->nprob = nprob;
   int rc = ls::setup_handle(H, grid, kappa, b, tol, opts, st);
   if (rc) return rc;
   ls::SpinLimitScope spin_scope(H->spin_limit);
@@ -767,7 +768,7 @@ int ls::setup_handle(ls_handle* H, const ls_grid* grid, double kappa, const doub
     }
   }
   int rc;
-  const long long N = (long long)grid->nx * grid->ny;
+  const long long N = (long long)grid->nx * grid->ny * H->nprob;  // the problems' potentials, stacked
   if ((rc = ls::dalloc((void**)&H->b, sizeof(double) * N))) return rc;
   LS_CUDA_TRY(cudaMemcpyAsync(H->b, b, sizeof(double) * N, cudaMemcpyDefault, st));
   if (ls::take_nan_b_fault()) {  // injected: as if b held a NaN
@@ -816,15 +817,21 @@ extern "C" {
 
 int ls_build(const ls_grid* grid, double kappa, const double* b, double tol, const ls_opts* opts, void* stream,
              ls_handle** out) {
+  return ls_build_many(grid, 1, kappa, b, tol, opts, stream, out);
+}
+
+int ls_build_many(const ls_grid* grid, int nprob, double kappa, const double* b, double tol, const ls_opts* opts,
+                  void* stream, ls_handle** out) {
   if (!out) return LS_EINVAL;
   *out = nullptr;
-  if (!grid || !b || !(kappa > 0) || !(tol > 0 && tol < 1) || grid->nx < 2 || grid->ny < 2 || !(grid->h > 0)) {
+  if (!grid || !b || !(kappa > 0) || !(tol > 0 && tol < 1) || grid->nx < 2 || grid->ny < 2 || !(grid->h > 0) ||
+      nprob < 1 || nprob > 65535) {
     set_error("invalid ls_build argument");
     return LS_EINVAL;
   }
   ls::StreamScope scope((cudaStream_t)stream);
   ls_handle* H = nullptr;
-  int rc = build_impl(grid, kappa, b, tol, opts, (cudaStream_t)stream, &H);
+  int rc = build_impl(grid, nprob, kappa, b, tol, opts, (cudaStream_t)stream, &H);
   if (rc) {
     cudaStreamSynchronize((cudaStream_t)stream);
     ls_free(H);
@@ -839,11 +846,12 @@ static int conv_entry(ls_handle* H, const void* x, void* y, int nrhs, int mode, 
   ls::StreamScope scope((cudaStream_t)stream);
   H->stream = (cudaStream_t)stream;
   cudaStream_t st = (cudaStream_t)stream;
-  size_t bytes = sizeof(ls::z64) * (size_t)H->grid.nx * H->grid.ny * nrhs;
+  const int nvec = nrhs * H->nprob;  // grid vectors: nrhs sets of the handle's problems
+  size_t bytes = sizeof(ls::z64) * (size_t)H->grid.nx * H->grid.ny * nvec;
   Staged sx, sy;
   int rc = stage_in(x, bytes, st, &sx);
   if (!rc) rc = stage_out_alloc(y, bytes, &sy);
-  if (!rc) rc = ls::conv_apply(H, sx.dev, sy.dev, nrhs, mode, st);
+  if (!rc) rc = ls::conv_apply(H, sx.dev, sy.dev, nvec, mode, st);
   if (!rc) rc = stage_out_finish(y, bytes, st, &sy);
   if (sx.owned || sy.owned) cudaStreamSynchronize(st);
   release(&sx);
@@ -867,11 +875,12 @@ int ls_apply(ls_handle* H, const void* f, void* q, int nrhs, int transpose, void
   ls::StreamScope scope((cudaStream_t)stream);
   H->stream = (cudaStream_t)stream;
   cudaStream_t st = (cudaStream_t)stream;
-  size_t bytes = sizeof(ls::z64) * (size_t)H->grid.nx * H->grid.ny * nrhs;
+  const int nvec = nrhs * H->nprob;  // grid vectors: nrhs sets of the handle's problems
+  size_t bytes = sizeof(ls::z64) * (size_t)H->grid.nx * H->grid.ny * nvec;
   Staged sf, sq;
   int rc = stage_in(f, bytes, st, &sf);
   if (!rc) rc = stage_out_alloc(q, bytes, &sq);
-  if (!rc) rc = ls::hbs_apply(H, sf.dev, sq.dev, nrhs, transpose, st);
+  if (!rc) rc = ls::hbs_apply(H, sf.dev, sq.dev, nvec, transpose, st);
   if (!rc) rc = stage_out_finish(q, bytes, st, &sq);
   if (sf.owned || sq.owned) cudaStreamSynchronize(st);
   release(&sf);
@@ -887,13 +896,14 @@ static int solve_entry(ls_handle* H, const void* f, void* sigma, int nrhs, ls_so
   ls::StreamScope scope((cudaStream_t)stream);
   H->stream = (cudaStream_t)stream;
   cudaStream_t st = (cudaStream_t)stream;
-  size_t bytes = sizeof(ls::z64) * (size_t)H->grid.nx * H->grid.ny * nrhs;
+  const int nvec = nrhs * H->nprob;  // grid vectors: nrhs sets of the handle's problems
+  size_t bytes = sizeof(ls::z64) * (size_t)H->grid.nx * H->grid.ny * nvec;
   Staged sf, ss;
   int rc = stage_in(f, bytes, st, &sf);
   if (!rc) rc = stage_out_alloc(sigma, bytes, &ss);
   int solve_rc = LS_OK;
   if (!rc) {
-    solve_rc = ls::gmres_solve(H, sf.dev, ss.dev, nrhs, info, transpose, st);
+    solve_rc = ls::gmres_solve(H, sf.dev, ss.dev, nvec, info, transpose, st);
     if (solve_rc != LS_OK && solve_rc != LS_ENOCONV) rc = solve_rc;
   }
   if (!rc) rc = stage_out_finish(sigma, bytes, st, &ss);
@@ -918,16 +928,18 @@ int ls_rhs_plane_wave(ls_handle* H, const double* thetas, void* f, int nrhs, voi
   H->stream = (cudaStream_t)stream;
   cudaStream_t st = (cudaStream_t)stream;
   const long long N = (long long)H->grid.nx * H->grid.ny;
-  size_t bytes = sizeof(ls::z64) * N * nrhs;
+  const int G = H->nprob;  // each angle gives one right-hand side per problem, with that problem's b
+  size_t bytes = sizeof(ls::z64) * N * G * nrhs;
   Staged sf;
   int rc = stage_out_alloc(f, bytes, &sf);
-  for (int r = 0; !rc && r < nrhs; ++r) {
-    count_launch();
-    rhs_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(H->b, H->grid.nx, H->grid.ny, H->grid.h, H->grid.x0,
-                                                          H->grid.y0, H->kappa, cos(thetas[r]), sin(thetas[r]),
-                                                          sf.dev + r * N);
-    rc = ls::check_launch("rhs");
-  }
+  for (int r = 0; !rc && r < nrhs; ++r)
+    for (int g = 0; !rc && g < G; ++g) {
+      count_launch();
+      rhs_kernel<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(H->b + g * N, H->grid.nx, H->grid.ny, H->grid.h,
+                                                            H->grid.x0, H->grid.y0, H->kappa, cos(thetas[r]),
+                                                            sin(thetas[r]), sf.dev + ((long long)r * G + g) * N);
+      rc = ls::check_launch("rhs");
+    }
   if (!rc) rc = stage_out_finish(f, bytes, st, &sf);
   release(&sf);
   return rc;
@@ -961,6 +973,7 @@ int ls_get_build_info(const ls_handle* H, ls_build_info* info) {
   info->compression_reused = H->compression_reused;
   info->nx = H->grid.nx;
   info->ny = H->grid.ny;
+  info->nprob = H->nprob;
   return LS_OK;
 }
 

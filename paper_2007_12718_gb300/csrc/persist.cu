@@ -168,7 +168,7 @@ int cache_store(ls_handle* H, cudaStream_t st) {
 // ------------------------------------------------------------- files
 namespace {
 
-constexpr char kMagic[8] = {'L', 'S', 'H', 'B', 'S', 'F', '0', '1'};
+constexpr char kMagic[8] = {'L', 'S', 'H', 'B', 'S', 'F', '0', '2'};
 
 struct FileHeader {
   char magic[8];
@@ -176,7 +176,7 @@ struct FileHeader {
   ls_grid grid;
   double kappa, tol;
   ls_opts opts;
-  int L, s, ring, prec;
+  int L, s, ring, prec, nprob;
   double flops_build, flops_compress, flops_sibling, factor_bytes, probe_resid_max;
   int pivot_fallbacks;
 };
@@ -192,7 +192,7 @@ struct LevelSizes {
 
 LevelSizes level_sizes(const ls_handle* H, int l) {
   const LevelData& lv = H->lev[l];
-  const size_t P = (size_t)1 << l;
+  const size_t P = (size_t)H->nprob << l;
   const size_t n2 = l == H->L ? (size_t)H->s * H->s : 2 * (size_t)H->lev[l + 1].k;
   LevelSizes z;
   z.U = l >= 1 ? (size_t)lv.m * lv.k : 0;
@@ -275,6 +275,7 @@ int ls_save(const ls_handle* H, const char* path, void* stream) {
   hd.s = H->s;
   hd.ring = H->ring;
   hd.prec = H->prec;
+  hd.nprob = H->nprob;
   hd.flops_build = H->flops_build;
   hd.flops_compress = H->flops_compress;
   hd.flops_sibling = H->flops_sibling;
@@ -288,7 +289,7 @@ int ls_save(const ls_handle* H, const char* path, void* stream) {
   void* bounce = ls::pinned_scratch(ls::kChunk);
   if (!bounce) return LS_ENOMEM;
   const size_t es = ls::elem_bytes(H);
-  const long long N = (long long)H->grid.nx * H->grid.ny;
+  const long long N = (long long)H->grid.nx * H->grid.ny * H->nprob;
   int rc;
   if ((rc = ls::write_dev(file.f, H->b, sizeof(double) * N, st, bounce))) return rc;
   // the level table and the skeletons, then every level's arrays (their sizes
@@ -320,7 +321,7 @@ int ls_save(const ls_handle* H, const char* path, void* stream) {
     if ((rc = ls::write_dev(file.f, lv.S, es * z.S, st, bounce))) return rc;
   }
   const size_t n = (size_t)H->s * H->s;
-  if ((rc = ls::write_dev(file.f, H->XBU, es * ((size_t)1 << H->L) * n * H->lev[H->L].k, st, bounce))) return rc;
+  if ((rc = ls::write_dev(file.f, H->XBU, es * ((size_t)H->nprob << H->L) * n * H->lev[H->L].k, st, bounce))) return rc;
   if (fflush(file.f) != 0) {
     ls::set_last_error_text("ls_save: write failed");
     return LS_EINVAL;
@@ -346,8 +347,8 @@ int ls_load(const char* path, void* stream, ls_handle** out) {
     ls::set_last_error_text("ls_load: not a file of ls_save (or of another version)");
     return LS_EINVAL;
   }
-  const long long N = (long long)hd.grid.nx * hd.grid.ny;
-  if (hd.grid.nx < 2 || hd.grid.ny < 2 || N > (1LL << 31)) {
+  const long long N = (long long)hd.grid.nx * hd.grid.ny * hd.nprob;
+  if (hd.grid.nx < 2 || hd.grid.ny < 2 || hd.nprob < 1 || N > (1LL << 33)) {
     ls::set_last_error_text("ls_load: bad grid in the file");
     return LS_EINVAL;
   }
@@ -357,6 +358,7 @@ int ls_load(const char* path, void* stream, ls_handle** out) {
     return LS_EINVAL;
   }
   ls_handle* H = new ls_handle();
+  H->nprob = hd.nprob;
   auto fail = [&](int rc) {
     cudaStreamSynchronize(st);
     ls_free(H);
@@ -415,7 +417,7 @@ int ls_load(const char* path, void* stream, ls_handle** out) {
     }
   }
   {
-    const size_t n = (size_t)H->s * H->s, e = ((size_t)1 << H->L) * n * H->lev[H->L].k;
+    const size_t n = (size_t)H->s * H->s, e = ((size_t)H->nprob << H->L) * n * H->lev[H->L].k;
     if ((rc = ls::dalloc(&H->XBU, es * std::max<size_t>(e, 1)))) return fail(rc);
     if (e && (rc = ls::read_dev(file.f, H->XBU, es * e, st, bounce))) return fail(rc);
   }

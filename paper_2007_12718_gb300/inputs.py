@@ -124,3 +124,18 @@ for _j in range(7):
     _n = 80 << _j
     WORKLOADS[f"cavity_n{_n}"] = dict(n=_n, kappa=2 * np.pi * _n / 10, b=lambda n: cavity(n), order_precond=4,
                                       order_matvec=10, eps=1e-4, leaf=10)
+
+
+def multiproblem_set(count=32, seed=7, sides=(64, 96, 128, 192), first_b_seed=100):
+    """Many independent problems of uneven sizes at 10 points per wavelength:
+    side n drawn from `sides` by default_rng(seed), kappa = 2 pi n / 10 (kappa h =
+    0.628 for all), potential gaussian_family(n, first_b_seed + i), leaf side 8
+    where n / 8 is a power of two times 8 and 12 otherwise (96 = 12 * 8, 192 = 12 * 16).
+    Returns a list of dicts (n, kappa, b_seed, leaf) in draw order."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, n in enumerate(rng.choice(np.array(sides), size=count)):
+        n = int(n)
+        leaf = 12 if n % 3 == 0 else 8
+        out.append(dict(n=n, kappa=2 * np.pi * n / 10, b_seed=first_b_seed + i, leaf=leaf))
+    return out
