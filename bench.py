@@ -303,6 +303,70 @@ def multirhs_leg(ls, torch, dev, precision, flush, pk, tensor):
                                  for k, v in fams.items()}}
 
 
+# --------------------------------------------------------- multi-problem leg
+MPROB_TEXT = ("32 independent problems, sides drawn from {64, 96, 128, 192} (default_rng(7)), kappa = 2 pi n/10 "
+              "(10 points per wavelength), b = Gaussian family seeds 100..131, theta = 0, leaf side 8 or 12; one "
+              "step = per side one ls_build_many (a forest of that side's problems: one compression, batched "
+              "merges) + ls_rhs_plane_wave + ls_solve (block GMRES, one right-hand side per problem) + ls_free")
+
+
+def multiproblem_leg(ls, torch, dev, precision, flush):
+    """Many independent problems of uneven sizes: grouped by side into forests,
+    timed with CUDA events after one warm-up step; the same problems one handle
+    each for comparison."""
+    from paper_2007_12718_gb300 import inputs
+    probs = inputs.multiproblem_set()
+    groups = {}
+    for p in probs:
+        groups.setdefault(p["n"], []).append(p)
+    data = {}
+    for n, grp in groups.items():
+        bs = torch.from_numpy(np.stack([inputs.gaussian_family(n, p["b_seed"]) for p in grp])).to(dev)
+        data[n] = (grp, bs, torch.zeros(len(grp), n, n, dtype=torch.complex128, device=dev),
+                   torch.zeros(len(grp), n, n, dtype=torch.complex128, device=dev))
+    stream = torch.cuda.current_stream()
+
+    def step(forest):
+        infos = []
+        for n, (grp, bs, F, sig) in data.items():
+            kw = dict(leaf_side=grp[0]["leaf"], precision=precision)
+            if forest:
+                H = ls.ls_build(n, 1.0 / n, grp[0]["kappa"], bs, 1e-4, **kw)
+                ls.ls_rhs_plane_wave(H, [0.0], F)
+                infos += ls.ls_solve(H, F, sig)
+                ls.ls_free(H)
+            else:
+                for g in range(len(grp)):
+                    H = ls.ls_build(n, 1.0 / n, grp[0]["kappa"], bs[g], 1e-4, **kw)
+                    ls.ls_rhs_plane_wave(H, [0.0], F[g])
+                    infos += ls.ls_solve(H, F[g], sig[g])
+                    ls.ls_free(H)
+        return infos
+
+    def timed(forest):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = step(forest)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) * 1e-3, infos
+
+    step(True)
+    step(False)
+    t, infos = timed(True)
+    t1, _ = timed(False)
+    dofs = sum(p["n"] ** 2 for p in probs)
+    return {"workload": "multiproblem_32", "description": MPROB_TEXT, "problems": len(probs),
+            "sides": {str(n): len(g) for n, g in sorted(groups.items())}, "dofs": dofs,
+            "ms_per_step": t * 1e3, "value": dofs / t / 1e6, "unit": "Mdof/s (all problems, build + solve)",
+            "one_handle_per_problem": {"ms_per_step": t1 * 1e3, "value": dofs / t1 / 1e6},
+            "converged": bool(all(i["converged"] for i in infos)),
+            "resid_true_max": max(i["resid_true"] for i in infos),
+            "iterations_max": max(i["iterations"] for i in infos)}
+
+
 # ----------------------------------------------------------------------- ours
 class Leg:
     """One workload on the device: inputs resident, steps of build + solve + free."""
@@ -520,6 +584,8 @@ def run_ours(args, rank, world):
         secondary["differentiation_n512"] = adj
     if not args.no_multirhs:
         secondary["multirhs_n512"] = multirhs_leg(ls, torch, dev, PREC, flush, pk, tensor)
+    if not args.no_multiproblem:
+        secondary["multiproblem_32"] = multiproblem_leg(ls, torch, dev, PREC, flush)
     cpu = cpu_baseline() if not args.no_cpu_baseline else None
     line = {"metric": METRIC, "value": value, "unit": "Mdof/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_mixed / args.steps * 1e3, "higher_is_better": True,
@@ -631,6 +697,8 @@ def main():
     ap.add_argument("--no-secondary", action="store_true", help="skip the 256^2 and 32^2 legs")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the differentiation workload (512x512 misfit gradient)")
+    ap.add_argument("--no-multiproblem", action="store_true",
+                    help="skip the many-problems workload (32 problems of sides 64..192)")
     ap.add_argument("--no-multirhs", action="store_true",
                     help="skip the multi-right-hand-side workload (512x512, 256 plane waves in one block)")
     ap.add_argument("--top-uncompressed", type=int, default=1,
