@@ -619,10 +619,15 @@ PAPER_CAVITY = {6400: (0.47, 0.20, 4), 25600: (1.64, 0.62, 5), 102400: (6.62, 2.
                 1638400: (190.38, 56.13, 9), 6553600: (829.48, 330.91, 13), 26214400: (5126.25, 2698.53, 22)}
 
 
+# The paper's lens table (Sec. 6.2 test problems, kappa = 300): N -> GMRES iterations.
+PAPER_LENS = {102400: 51, 409600: 9, 1638400: 7, 6553600: 7, 26214400: 9}
+
+
 def run_sweep(args):
-    """The cavity sweep of Sec. 6.3 on one GPU: for n = 80 2^j (kappa = 2 pi n / 10,
-    100-point leaves), one warm-up and `--steps` timed build + solve steps of the mixed
-    path; build and solve timed separately with CUDA events.  One JSON line."""
+    """A sweep of the paper's test problems on one GPU: the cavity of Sec. 6.3 (n = 80 2^j,
+    kappa = 2 pi n / 10) or the lens of Sec. 6.2 (n = 320 2^j, kappa = 300), 100-point
+    leaves; one warm-up and `--steps` timed build + solve steps of the mixed path; build
+    and solve timed separately with CUDA events.  One JSON line."""
     import torch
 
     import paper_2007_12718_gb300 as ls
@@ -632,8 +637,9 @@ def run_sweep(args):
     stream = torch.cuda.current_stream()
     PREC = {"fp32": ls.LS_FP32, "tf32x3": ls.LS_TF32X3, "fp16split": ls.LS_FP16SPLIT, "fp64": ls.LS_FP64}[args.precision]
     rows = []
-    for j in range(args.sweep_first, args.sweep_levels):
-        name = f"cavity_n{80 << j}"
+    lens = args.sweep == "lens"
+    for j in range(args.sweep_first, min(args.sweep_levels, 4) if lens else args.sweep_levels):
+        name = f"lens_n{320 << j}" if lens else f"cavity_n{80 << j}"
         n, kappa, b, w = workload(name)
         h = 1.0 / n
         bd = torch.from_numpy(b).to(dev)
@@ -664,18 +670,19 @@ def run_sweep(args):
         tb /= args.steps
         ts /= args.steps
         N = n * n
-        paper = PAPER_CAVITY.get(N)
+        paper = ({"iterations": PAPER_LENS[N]} if N in PAPER_LENS else None) if lens else PAPER_CAVITY.get(N)
+        if paper is not None and not lens:
+            paper = {"t_build_s": paper[0], "t_gmres_s": paper[1], "iterations": paper[2]}
         rows.append({"workload": name, "N": N, "kappa": kappa, "t_build_s": tb, "t_solve_s": ts,
                      "mdofs": N / (tb + ts) / 1e6, "iterations": info["iterations"],
                      "resid_true": info["resid_true"], "ranks_top": bi["ranks"][1:4],
                      "factor_GB": bi["factor_bytes"] / 1e9, "pivot_fallbacks": bi["pivot_fallbacks"],
-                     "probe_resid_max": bi["probe_resid_max"],
-                     "paper": None if paper is None else {"t_build_s": paper[0], "t_gmres_s": paper[1],
-                                                          "iterations": paper[2]}})
+                     "probe_resid_max": bi["probe_resid_max"], "paper": paper})
         print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
         del bd, f, sig
         torch.cuda.empty_cache()
-    print(json.dumps({"metric": METRIC, "sweep": "cavity, 10 points per wavelength (Sec. 6.3)", "unit": "Mdof/s",
+    print(json.dumps({"metric": METRIC, "sweep": ("lens, kappa = 300 (Sec. 6.2)" if lens else
+                                                  "cavity, 10 points per wavelength (Sec. 6.3)"), "unit": "Mdof/s",
                       "steps": args.steps, "warmup": 1, "precision": args.precision,
                       "top_levels_uncompressed": args.top_uncompressed, "rows": rows}), flush=True)
 
@@ -704,8 +711,9 @@ def main():
     ap.add_argument("--top-uncompressed", type=int, default=1,
                     help="tree levels kept uncompressed at the top (U = I, the ID of full rank); measured faster at "
                          "2048^2 (1.20 s against 1.31 s per step) and at 256^2; 0 compresses every level")
-    ap.add_argument("--sweep", action="store_true",
-                    help="run the cavity sweep of Sec. 6.3 (10 points per wavelength) instead of the benchmark")
+    ap.add_argument("--sweep", nargs="?", const="cavity", default=None, choices=["cavity", "lens"],
+                    help="run a sweep of the paper's test problems instead of the benchmark: the cavity of "
+                         "Sec. 6.3 (10 points per wavelength, default) or the lens of Sec. 6.2 (kappa = 300)")
     ap.add_argument("--sweep-levels", type=int, default=6, help="sizes of the sweep: n = 80, 160, ..., 80 2^(levels-1)")
     ap.add_argument("--sweep-first", type=int, default=0, help="first size of the sweep: n = 80 2^first")
     ap.add_argument("--sweep-maxit", type=int, default=100, help="GMRES iteration limit in the sweep (memory: "

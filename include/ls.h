@@ -37,7 +37,7 @@ extern "C" {
 
 enum {
   LS_OK = 0,
-  LS_EINVAL = -1,     /* bad argument (sizes, b not finite or b > 1, ...) */
+  LS_EINVAL = -1,     /* bad argument (sizes, b not finite, ...) */
   LS_ENOMEM = -2,     /* device allocation failed */
   LS_ECUDA = -3,      /* CUDA runtime error (see ls_last_error) */
   LS_ESINGULAR = -4,  /* zero pivot in a local inverse */
@@ -160,8 +160,10 @@ void ls_default_opts(ls_opts* o);
  *            leaf side s and some L >= 1 (cuts alternate vertical/horizontal,
  *            Sec. 3.2), e.g. nx = ny = s * 2^(L/2).
  *   kappa  : wavenumber > 0.
- *   b      : scattering potential, ny*nx doubles (host or device); finite and
- *            <= 1 (Sec. 1).
+ *   b      : scattering potential, ny*nx doubles (host or device), finite.
+ *            b <= 1 guarantees existence and uniqueness (Sec. 1); larger
+ *            values are accepted (the lens of Sec. 6.2 reaches 1.18), and a
+ *            singular system shows as LS_ENOCONV of the solve.
  *   tol    : HBS compression tolerance eps in (0, 1) (Eq. 11, with the local
  *            tolerance eps * ||proxy block||_F).
  *   opts   : NULL for defaults.

@@ -52,8 +52,7 @@ __global__ void rhs_kernel(const double* b, int nx, int ny, double h, double x0,
 __global__ void check_b_kernel(const double* b, long long n, int* bad) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= n) return;
-  double v = b[t];
-  if (!(v <= 1.0) || !isfinite(v)) atomicExch(bad, 1);
+  if (!isfinite(b[t])) atomicExch(bad, 1);
 }
 
 }  // namespace
@@ -804,7 +803,7 @@ int ls::setup_handle(ls_handle* H, const ls_grid* grid, double kappa, const doub
   const int bad = pin[0];
   if (bad) {
     cudaEventDestroy(ev_side);
-    set_error("b must be finite and <= 1");
+    set_error("b must be finite");
     return LS_EINVAL;
   }
   // the spectrum is short next to any build: the handle is complete on return, for any stream

@@ -13,7 +13,7 @@ those experiments:
   order from numpy.random.default_rng(seed); psi is a C-infinity cutoff that
   vanishes with all derivatives on the boundary of the unit square (ramp over
   a distance 0.1).  If max b >= 0.95 the field is scaled to max 0.95
-  (b <= 1 is required for uniqueness, Sec. 1).
+  (b <= 1 guarantees existence and uniqueness, Sec. 1).
 * ``constant_disk``   -- b = value inside a disk (closed-form pin).
 * ``plane_wave_angles`` / ``receivers_circle``.
 """
@@ -76,6 +76,17 @@ def cavity(n, centre=(0.5, 0.5)):
     return (1.0 - np.sin(0.5 * th) ** 500) * np.exp(-2000.0 * (0.1 - r2) ** 2)
 
 
+def lens(n, centre=(0.5, 0.5)):
+    """The vertically graded lens of the paper's Sec. 6.2 test problems,
+    b = 4 (x2 - 0.1) (1 - erf(25 (|x| - 0.3))), with x measured from the
+    domain centre (a disk of radius ~0.3 in the middle of the unit square);
+    b ranges over about [-2.69, 1.18], above the b <= 1 of the existence theorem."""
+    from scipy.special import erf
+    X, Y = grid_nodes(n)
+    dx, dy = X - centre[0], Y - centre[1]
+    return 4.0 * (dy - 0.1) * (1.0 - erf(25.0 * (np.sqrt(dx * dx + dy * dy) - 0.3)))
+
+
 def constant_disk(n, value, radius, centre=(0.5, 0.5)):
     X, Y = grid_nodes(n)
     return np.where((X - centre[0]) ** 2 + (Y - centre[1]) ** 2 < radius ** 2, value, 0.0)
@@ -117,6 +128,12 @@ WORKLOADS = {
     "multirhs_n512": dict(n=512, kappa=300.0, b=lambda n: gaussian_family(n, 0), order_precond=4,
                           order_matvec=10, eps=1e-4, leaf=8, nrhs=256),
 }
+# The lens of Sec. 6.2 at kappa = 300 (47.7 wavelengths across) on the grids of the
+# paper's lens table, 100-point leaves, eps 1e-4, order 4 / 10.
+for _j in range(4):
+    _n = 320 << _j
+    WORKLOADS[f"lens_n{_n}"] = dict(n=_n, kappa=300.0, b=lambda n: lens(n), order_precond=4,
+                                    order_matvec=10, eps=1e-4, leaf=10)
 # The cavity sweep of Sec. 6.3 (preconditioned solver, 10 points per wavelength,
 # 100-point leaves): n = 80 2^j, kappa = 2 pi n / 10 (the domain is n / 10
 # wavelengths across; kappa = 50.27 at n = 80), eps 1e-4, order 4 / 10.
