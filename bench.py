@@ -687,6 +687,61 @@ def run_sweep(args):
                       "top_levels_uncompressed": args.top_uncompressed, "rows": rows}), flush=True)
 
 
+def run_kernel_case(spec):
+    """One kernel family alone, for profiling (ncu) and its roofline:
+    gemm:M:N:K:ENGINE[:REPS]  the merge GEMM engine of ls_cgemm_c64 (0 SIMT, 2 tf32x3,
+                              3 f16x3) on seeded random complex64 operands;
+    id:M:P:R                   the blocked row ID (FP32) of a seeded M x P matrix of
+                              numerical rank about R (singular values 10^(-8 i / R)).
+    CUDA-event timing after two warm-up calls; one JSON line."""
+    import torch
+
+    import paper_2007_12718_gb300 as ls
+
+    torch.manual_seed(0)
+    part = spec.split(":")
+    dev = torch.device("cuda", 0)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    if part[0] == "gemm":
+        M, N, K, eng = (int(x) for x in part[1:5])
+        reps = int(part[5]) if len(part) > 5 else 5
+        A = torch.randn(1, M, K, dtype=torch.complex64, device=dev)
+        B = torch.randn(1, K, N, dtype=torch.complex64, device=dev)
+        C = torch.zeros(1, M, N, dtype=torch.complex64, device=dev)
+        for _ in range(2):
+            ls.ls_cgemm_c64(eng, A, B, C)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record()
+        for _ in range(reps):
+            ls.ls_cgemm_c64(eng, A, B, C)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out = {"case": spec, "ms": ms, "tflops_fp32_equiv": 8.0 * M * N * K / ms / 1e9,
+               "bytes_min": 8.0 * (M * K + K * N + M * N)}
+    elif part[0] == "id":
+        M, P, R = (int(x) for x in part[1:4])
+        G1 = torch.randn(M, R, dtype=torch.complex128, device=dev)
+        G2 = torch.randn(R, P, dtype=torch.complex128, device=dev)
+        d = torch.pow(10.0, -8.0 * torch.arange(R, device=dev, dtype=torch.float64) / R)
+        A = (G1 * d) @ G2
+        for _ in range(2):
+            ls.ls_row_id(A, 1e-4, precision=ls.LS_FP32, method=ls.LS_ID_BLOCKED)
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record()
+        k, _, _ = ls.ls_row_id(A, 1e-4, precision=ls.LS_FP32, method=ls.LS_ID_BLOCKED)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out = {"case": spec, "ms": ms, "k": k, "tflops_8mpk": 8.0 * M * P * k / ms / 1e9,
+               "note": "includes the FP64 -> FP32 conversion and the copy of U to the host"}
+    else:
+        raise SystemExit(f"unknown kernel case {spec}")
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -711,6 +766,8 @@ def main():
     ap.add_argument("--top-uncompressed", type=int, default=1,
                     help="tree levels kept uncompressed at the top (U = I, the ID of full rank); measured faster at "
                          "2048^2 (1.20 s against 1.31 s per step) and at 256^2; 0 compresses every level")
+    ap.add_argument("--kernel-case", default=None,
+                    help="time one kernel family alone (gemm:M:N:K:ENGINE[:REPS] or id:M:P:R) for profiling")
     ap.add_argument("--sweep", nargs="?", const="cavity", default=None, choices=["cavity", "lens"],
                     help="run a sweep of the paper's test problems instead of the benchmark: the cavity of "
                          "Sec. 6.3 (10 points per wavelength, default) or the lens of Sec. 6.2 (kappa = 300)")
@@ -726,6 +783,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.kernel_case:
+        run_kernel_case(args.kernel_case)
         return
     if args.sweep:
         run_sweep(args)

@@ -1660,6 +1660,7 @@ TreeGeom make_geom(const ls_handle* H) {
 
 int apply_persistent_init(ls_handle* H, cudaStream_t st);
 int level_transpose(ls_handle* H, int l, cudaStream_t st);
+int lowrank_transpose(ls_handle* H, int l, cudaStream_t st);
 
 // The apply's temporaries (one right-hand side: leaf blocks, per-level
 // expansions) and the persistent apply's transposes and operation list, made at
@@ -1671,6 +1672,7 @@ int apply_prepare(ls_handle* H, cudaStream_t st) {
   const int L = H->L, n = H->s * H->s;
   size_t vec = (size_t)2 * ((size_t)H->nprob << L) * n;
   for (int l = 1; l <= L; ++l) vec += (size_t)3 * ((size_t)H->nprob << l) * std::max(1, H->lev[l].k) * 2;
+  for (int l = 0; l < L; ++l) vec += ((size_t)H->nprob << l) * 2 * std::max(0, H->lev[l].xr);  // Q_R x per node
   H->work_bytes = sizeof(cx<R>) * vec;
   int rc;
   if ((rc = dalloc(&H->work, H->work_bytes))) return rc;
@@ -1831,6 +1833,7 @@ int sibling_lowrank(ls_handle* H, int l, cudaStream_t st) {
   if ((rc = check_launch("sibling low-rank factors"))) return rc;
   LS_CUDA_TRY(cudaStreamSynchronize(st));  // pin and the temporaries are released on return
   lv.gr = r;
+  if ((rc = lowrank_transpose(H, l, st))) return rc;
   return LS_OK;
 }
 
@@ -1895,18 +1898,23 @@ int invert_checked(ls_handle* H, cx<R>* Z, int n, int lda, long long sZ, int P, 
 }
 
 // X of the P parents of level l (children of rank kc, sibling factors of rank r)
-// in the Woodbury form above; the root keeps W, Y1 = A1 R^T, Y2 = A2 L^T.
+// in the Woodbury form above, kept factored: X = I + P_L Q_R with
+//   P_L = [[A1 (C2 N), -A1 M], [-A2 N, A2 (C1 M)]]   (2kc x 2r per node, in X)
+//   Q_R = diag(L^T, R^T)                             (the level's shared L, R),
+// since P_L Q_R = [[A1 C2 N L^T, -A1 M R^T], [-A2 N L^T, A2 C1 M R^T]] = X - I.
+// The apply and the S products use the factors; no 2kc x 2kc block is formed
+// (4 kc r entries per node instead of 4 kc^2).
 template <class R>
 int merge_woodbury(ls_handle* H, int l, cx<R>* X, const cx<R>* Sc, cudaStream_t st) {
   const LevelData& ch = H->lev[l + 1];
-  const int P = H->nprob << l, kc = ch.k, n2 = 2 * kc, r = ch.gr;
-  const long long sX = (long long)n2 * n2, kk = (long long)kc * kc, kr = (long long)kc * r, rr = (long long)r * r;
+  const int P = H->nprob << l, kc = ch.k, n2 = 2 * kc, r = ch.gr, r2 = 2 * r;
+  const long long sP = (long long)n2 * r2, kk = (long long)kc * kc, kr = (long long)kc * r, rr = (long long)r * r;
   const cx<R>* Lf = reinterpret_cast<const cx<R>*>(ch.GL);
   const cx<R>* Rf = reinterpret_cast<const cx<R>*>(ch.GR);
-  // A1, A2, B (kc x r each), C1, C2, M, N, T (r x r each), then the inverse's scratch
+  // A1, A2 (kc x r each), C1, C2, M, N, T (r x r each), then the inverse's scratch
   const size_t inv_scr = sizeof(cx<R>) * (size_t)P * (2 * rr + 128 * 128 + 3 * 128 * (size_t)r + 4 * (size_t)r) +
                          sizeof(int) * (size_t)P * (4 * (size_t)r + 256) + (1 << 16);
-  const size_t bytes = sizeof(cx<R>) * (size_t)P * (3 * kr + 5 * rr) + inv_scr;
+  const size_t bytes = sizeof(cx<R>) * (size_t)P * (2 * kr + 5 * rr) + inv_scr;
   void* work = nullptr;
   int rc;
   if ((rc = dalloc(&work, bytes))) return rc;
@@ -1916,17 +1924,12 @@ int merge_woodbury(ls_handle* H, int l, cx<R>* X, const cx<R>* Sc, cudaStream_t 
   } free_work{work};
   cx<R>* A1 = reinterpret_cast<cx<R>*>(work);
   cx<R>* A2 = A1 + (size_t)P * kr;
-  cx<R>* B = A2 + (size_t)P * kr;
-  cx<R>* C1 = B + (size_t)P * kr;
+  cx<R>* C1 = A2 + (size_t)P * kr;
   cx<R>* C2 = C1 + (size_t)P * rr;
   cx<R>* Mm = C2 + (size_t)P * rr;
   cx<R>* Nm = Mm + (size_t)P * rr;
   cx<R>* Tm = Nm + (size_t)P * rr;
   void* scratch = Tm + (size_t)P * rr;
-  cx<R>* X11 = X;
-  cx<R>* X12 = X + kc;
-  cx<R>* X21 = X + (size_t)kc * n2;
-  cx<R>* X22 = X21 + kc;
   const cx<R> mone = mk<R>(R(-1), R(0)), on = one<R>(), ze = zero<R>();
   auto ident = [&](cx<R>* D, int n, int ld, long long sD) {
     const long long tot = (long long)P * n * n;
@@ -1948,33 +1951,22 @@ int merge_woodbury(ls_handle* H, int l, cx<R>* X, const cx<R>* Sc, cudaStream_t 
   prof_end(ti, PR_MERGE_INV, st, sizeof(cx<R>) * P * 2.0 * rr, P * 8.0 * (double)rr * r);
   if (l == 0) host_mark("root_inverse_checked");
   tg = prof_begin(st);
-  double fl = 0;
-  gemm<R>(st, false, false, r, r, r, on, C1, r, rr, Mm, r, rr, ze, Tm, r, rr, P);              // C1 M
-  gemm<R>(st, false, false, kc, r, r, on, A2, r, kr, Tm, r, rr, ze, B, r, kr, P);              // A2 C1 M
-  ident(X22, kc, n2, sX);
-  gemm<R>(st, false, true, kc, kc, r, on, B, r, kr, Rf, r, 0, on, X22, n2, sX, P);             // W
-  fl += 8.0 * ((double)rr * r + (double)kr * r + (double)kk * r);
-  if (l == 0) {  // the root keeps Y1 = A1 R^T and Y2 = A2 L^T beside W
-    gemm<R>(st, false, true, kc, kc, r, on, A1, r, kr, Rf, r, 0, ze, X12, n2, sX, P);
-    gemm<R>(st, false, true, kc, kc, r, on, A2, r, kr, Lf, r, 0, ze, X21, n2, sX, P);
-    fl += 2 * 8.0 * (double)kk * r;
-    H->factor_bytes -= sizeof(cx<R>) * (double)P * kk;  // the X11 blocks are not read
-  } else {
-    gemm<R>(st, false, false, kc, r, r, on, A1, r, kr, Mm, r, rr, ze, B, r, kr, P);            // A1 M
-    gemm<R>(st, false, true, kc, kc, r, mone, B, r, kr, Rf, r, 0, ze, X12, n2, sX, P);         // -A1 M R^T
-    gemm<R>(st, false, false, r, r, r, on, Mm, r, rr, C2, r, rr, ze, Tm, r, rr, P);            // M C2
-    ident(Nm, r, r, rr);
-    gemm<R>(st, false, false, r, r, r, on, C1, r, rr, Tm, r, rr, on, Nm, r, rr, P);            // N
-    gemm<R>(st, false, false, kc, r, r, on, A2, r, kr, Nm, r, rr, ze, B, r, kr, P);            // A2 N
-    gemm<R>(st, false, true, kc, kc, r, mone, B, r, kr, Lf, r, 0, ze, X21, n2, sX, P);         // -A2 N L^T
-    gemm<R>(st, false, false, r, r, r, on, C2, r, rr, Nm, r, rr, ze, Tm, r, rr, P);            // C2 N
-    gemm<R>(st, false, false, kc, r, r, on, A1, r, kr, Tm, r, rr, ze, B, r, kr, P);            // A1 C2 N
-    ident(X11, kc, n2, sX);
-    gemm<R>(st, false, true, kc, kc, r, on, B, r, kr, Lf, r, 0, on, X11, n2, sX, P);           // I + A1 C2 N L^T
-    fl += 8.0 * (3.0 * rr * r + 3.0 * kr * r + 3.0 * (double)kk * r);
-  }
-  if ((rc = check_launch("woodbury merge blocks"))) return rc;
-  prof_end(tg, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * ((double)sX + 4.0 * kr), P * fl);
+  cx<R>* PTL = X;                     // rows 0..kc, columns 0..r of P_L
+  cx<R>* PTR = X + r;                 // rows 0..kc, columns r..2r
+  cx<R>* PBL = X + (size_t)kc * r2;   // rows kc..2kc, columns 0..r
+  cx<R>* PBR = PBL + r;               // rows kc..2kc, columns r..2r
+  gemm<R>(st, false, false, r, r, r, on, Mm, r, rr, C2, r, rr, ze, Tm, r, rr, P);             // M C2
+  ident(Nm, r, r, rr);
+  gemm<R>(st, false, false, r, r, r, on, C1, r, rr, Tm, r, rr, on, Nm, r, rr, P);             // N = I + C1 M C2
+  gemm<R>(st, false, false, r, r, r, on, C2, r, rr, Nm, r, rr, ze, Tm, r, rr, P);             // C2 N
+  gemm<R>(st, false, false, kc, r, r, on, A1, r, kr, Tm, r, rr, ze, PTL, r2, sP, P);          // A1 C2 N
+  gemm<R>(st, false, false, kc, r, r, mone, A1, r, kr, Mm, r, rr, ze, PTR, r2, sP, P);        // -A1 M
+  gemm<R>(st, false, false, kc, r, r, mone, A2, r, kr, Nm, r, rr, ze, PBL, r2, sP, P);        // -A2 N
+  gemm<R>(st, false, false, r, r, r, on, C1, r, rr, Mm, r, rr, ze, Tm, r, rr, P);             // C1 M
+  gemm<R>(st, false, false, kc, r, r, on, A2, r, kr, Tm, r, rr, ze, PBR, r2, sP, P);          // A2 C1 M
+  if ((rc = check_launch("woodbury merge factors"))) return rc;
+  const double fl = 8.0 * (4.0 * rr * r + 4.0 * kr * r);
+  prof_end(tg, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * ((double)sP + 2.0 * kr), P * fl);
   H->flops_build += P * (fl + 8.0 * (2.0 * kk * r + 2.0 * kr * r + 2.0 * (double)rr * r));
   return LS_OK;
 }
@@ -1985,8 +1977,8 @@ template <class R>
 void apply_bytes(ls_handle* H) {
   double fb = H->factor_bytes;
   for (int l = 1; l <= H->L - 1; ++l) {
-    const double n2 = 2.0 * H->lev[l + 1].k;
-    fb += sizeof(cx<R>) * (double)(H->nprob << l) * n2 * n2;
+    const double n2 = 2.0 * H->lev[l + 1].k, cols = H->lev[l].xr > 0 ? 2.0 * H->lev[l].xr : n2;
+    fb += sizeof(cx<R>) * (double)(H->nprob << l) * n2 * cols;
   }
   H->bytes_apply = fb + (double)H->grid.nx * H->grid.ny * (16.0 * 2);
 }
@@ -2068,8 +2060,11 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const Le
         if (p) dfree(p);
       }
     } free_work{work};
-    if ((rc = dalloc(&lv.X, sizeof(cx<R>) * (size_t)P * std::max(n2 * n2, 1)))) return rc;
-    H->factor_bytes += sizeof(cx<R>) * (double)P * n2 * n2;
+    // X per node: 2kc x 2kc, or its factor P_L (2kc x 2r) in the Woodbury form
+    lv.xr = woodbury ? ch.gr : 0;
+    const long long xcols = woodbury ? 2LL * ch.gr : n2;
+    if ((rc = dalloc(&lv.X, sizeof(cx<R>) * (size_t)P * std::max<long long>(n2 * xcols, 1)))) return rc;
+    H->factor_bytes += sizeof(cx<R>) * (double)P * n2 * xcols;
     cx<R>* X = reinterpret_cast<cx<R>*>(lv.X);
     const cx<R>* Sc = reinterpret_cast<const cx<R>*>(ch.S);
     const cx<R>* Gs = reinterpret_cast<const cx<R>*>(ch.Gsib);
@@ -2208,6 +2203,57 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const Le
     cx<R>* D = reinterpret_cast<cx<R>*>(work_s);           // P x n2 x kp
     cx<R>* E = D + (size_t)P * n2 * kp;
     int ts = prof_begin(st);
+    if (woodbury) {
+      // X = I + P_L Q_R, Q_R = diag(L^T, R^T) (the children's sibling factors)
+      const int r = ch.gr, r2 = 2 * r;
+      const long long sP = (long long)n2 * r2, kk = (long long)kc * kc;
+      const cx<R>* Lf = reinterpret_cast<const cx<R>*>(ch.GL);
+      const cx<R>* Rf = reinterpret_cast<const cx<R>*>(ch.GR);
+      cx<R>* Sl = reinterpret_cast<cx<R>*>(lv.S);
+      const cx<R> on = one<R>(), ze = zero<R>();
+      double fl;
+      if (l <= H->opts.top_uncompressed && kp == n2) {
+        // S = X diag(S_a, S_b) = diag(S_a, S_b) + P_L diag(L^T S_a, R^T S_b)
+        cx<R>* Z = D;  // L^T S_a and R^T S_b: P x r x kc each
+        gemm<R>(st, true, false, r, kc, kc, on, Lf, r, 0, Sc, kc, 2 * kk, ze, Z, kc, (long long)r * kc, P);
+        gemm<R>(st, true, false, r, kc, kc, on, Rf, r, 0, Sc + kk, kc, 2 * kk, ze, Z + (size_t)P * r * kc, kc,
+                (long long)r * kc, P);
+        LS_CUDA_TRY(cudaMemsetAsync(Sl, 0, sizeof(cx<R>) * (size_t)P * kp * kp, st));
+        // diag(S_a, S_b) into each node's S
+        for (int b0 = 0; b0 < P; b0 += kMaxGridYZ) {
+          dim3 gc((unsigned)std::min<long long>(1024, (kk + 255) / 256), std::min(kMaxGridYZ, P - b0));
+          count_launch(2);
+          copy_block_kernel<R><<<gc, 256, 0, st>>>(Sl + (size_t)b0 * kp * kp, kp, (long long)kp * kp,
+                                                   Sc + (size_t)b0 * 2 * kk, kc, 2 * kk, kc, kc);
+          copy_block_kernel<R><<<gc, 256, 0, st>>>(Sl + (size_t)b0 * kp * kp + (size_t)kc * kp + kc, kp,
+                                                   (long long)kp * kp, Sc + (size_t)b0 * 2 * kk + kk, kc, 2 * kk, kc,
+                                                   kc);
+        }
+        gemm<R>(st, false, false, n2, kc, r, on, X, r2, sP, Z, kc, (long long)r * kc, on, Sl, kp, (long long)kp * kp, P);
+        gemm<R>(st, false, false, n2, kc, r, on, X + r, r2, sP, Z + (size_t)P * r * kc, kc, (long long)r * kc, on,
+                Sl + kc, kp, (long long)kp * kp, P);
+        fl = P * (2.0 * 8 * (double)r * kc * kc + 2.0 * 8 * (double)n2 * r * kc);
+      } else {
+        // D = [S_a U_top ; S_b U_bot];  E = X D = D + P_L (Q_R D) (in D);  S = U^T E
+        gemm<R>(st, false, false, kc, kp, kc, on, Sc, kc, 2 * kk, U, kp, 0, ze, D, kp, (long long)n2 * kp, P);
+        gemm<R>(st, false, false, kc, kp, kc, on, Sc + kk, kc, 2 * kk, U + (size_t)kc * kp, kp, 0, ze,
+                D + (size_t)kc * kp, kp, (long long)n2 * kp, P);
+        cx<R>* F = E;  // Q_R D: P x 2r x kp
+        gemm<R>(st, true, false, r, kp, kc, on, Lf, r, 0, D, kp, (long long)n2 * kp, ze, F, kp, (long long)r2 * kp, P);
+        gemm<R>(st, true, false, r, kp, kc, on, Rf, r, 0, D + (size_t)kc * kp, kp, (long long)n2 * kp, ze,
+                F + (size_t)r * kp, kp, (long long)r2 * kp, P);
+        gemm<R>(st, false, false, n2, kp, r2, on, X, r2, sP, F, kp, (long long)r2 * kp, on, D, kp, (long long)n2 * kp,
+                P);
+        gemm<R>(st, true, false, kp, kp, n2, on, U, kp, 0, D, kp, (long long)n2 * kp, ze, Sl, kp, (long long)kp * kp,
+                P);
+        fl = P * (2.0 * 8 * (double)kc * kc * kp + 2.0 * 8 * (double)r * kc * kp + 8.0 * (double)n2 * r2 * kp +
+                  8.0 * (double)kp * n2 * kp);
+      }
+      if ((rc = check_launch("merge S (Woodbury)"))) return rc;
+      prof_end(ts, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * ((double)sP + 2.0 * kc * kc + (double)kp * kp), fl);
+      H->flops_build += fl;
+      continue;
+    }
     if (l <= H->opts.top_uncompressed && kp == n2) {
       // uncompressed level (U = I): S = X diag(S_a, S_b), two column blocks of X
       cx<R>* Sl = reinterpret_cast<cx<R>*>(lv.S);
@@ -2492,7 +2538,31 @@ int apply_core(ls_handle* H, z64** slots, cudaStream_t st) {
     tmp[l] = p;
     p += sz;
   }
+  std::vector<cx<R>*> ub(L + 1, nullptr);  // Q_R x of the levels whose X is factored
+  for (int l = 0; l < L; ++l)
+    if (H->lev[l].xr > 0) {
+      ub[l] = p;
+      p += ((size_t)H->nprob << l) * 2 * H->lev[l].xr;
+    }
   const cx<R> mone = mk<R>(R(-1), R(0));
+  // y[b] = X_l x[b] (2k_{l+1} entries per node): X itself, or I + P_L Q_R
+  auto xprod = [&](int l, const cx<R>* x, cx<R>* y) -> int {
+    const int kc = H->lev[l + 1].k, n2 = 2 * kc, P = H->nprob << l, r = H->lev[l].xr;
+    const cx<R>* X = reinterpret_cast<const cx<R>*>(H->lev[l].X);
+    if (r <= 0) {
+      gemv<R>(st, false, n2, n2, one<R>(), X, n2, (long long)n2 * n2, x, n2, zero<R>(), y, n2, P);
+      return LS_OK;
+    }
+    gemv<R>(st, false, r, kc, one<R>(), reinterpret_cast<const cx<R>*>(H->lev[l + 1].GLT), kc, 0, x, n2, zero<R>(),
+            ub[l], 2 * r, P);
+    gemv<R>(st, false, r, kc, one<R>(), reinterpret_cast<const cx<R>*>(H->lev[l + 1].GRT), kc, 0, x + kc, n2,
+            zero<R>(), ub[l] + r, 2 * r, P);
+    LS_CUDA_TRY(cudaMemcpy2DAsync(y, sizeof(cx<R>) * n2, x, sizeof(cx<R>) * n2, sizeof(cx<R>) * n2, P,
+                                  cudaMemcpyDeviceToDevice, st));
+    gemv<R>(st, false, n2, 2 * r, one<R>(), X, 2 * r, (long long)n2 * 2 * r, ub[l], 2 * r, one<R>(), y, n2, P);
+    return LS_OK;
+  };
+  int xrc;
   const LevelData& lf = H->lev[L];
   const int kL = lf.k;
   // nodes of a level with at least this many parents are applied by one block each
@@ -2514,6 +2584,12 @@ int apply_core(ls_handle* H, z64** slots, cudaStream_t st) {
   // upward pass: r~_tau = U^T X [r~_a; r~_b]  (Eq. (28)); X [.;.] goes to the child-level scratch
   for (int l = L - 1; l >= 1; --l) {
     const int P = H->nprob << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
+    if (H->lev[l].xr > 0) {
+      if ((xrc = xprod(l, rt[l + 1], tmp[l + 1]))) return xrc;
+      gemv<R>(st, true, kp, n2, one<R>(), reinterpret_cast<const cx<R>*>(H->lev[l].U), kp, 0, tmp[l + 1], n2,
+              zero<R>(), rt[l], kp, P);
+      continue;
+    }
     if (P >= kFusedMinNodes && sizeof(cx<R>) * 2 * n2 <= 48 * 1024) {
       count_launch();
       up_node_kernel<R><<<P, 256, sizeof(cx<R>) * 2 * n2, st>>>(n2, kp, reinterpret_cast<const cx<R>*>(H->lev[l].X),
@@ -2535,11 +2611,15 @@ int apply_core(ls_handle* H, z64** slots, cudaStream_t st) {
     const cx<R>* G1 = reinterpret_cast<const cx<R>*>(H->lev[1].Gsib);
     const cx<R>* X0 = reinterpret_cast<const cx<R>*>(H->lev[0].X);  // [., Y1; Y2, W]
     cx<R>* tb = wt[1] + kc;
-    LS_CUDA_TRY(cudaMemcpy2DAsync(tb, pitch, rt[1] + kc, pitch, width, G, cudaMemcpyDeviceToDevice, st));
-    gemv<R>(st, false, kc, kc, mone, X0 + (size_t)kc * n2, n2, sX, rt[1], n2, one<R>(), tb, n2, G);  // r_b - Y2 r_a
-    gemv<R>(st, false, kc, kc, one<R>(), X0 + (size_t)kc * n2 + kc, n2, sX, tb, n2, zero<R>(), qr + kc, n2, G);
-    LS_CUDA_TRY(cudaMemcpy2DAsync(qr, pitch, rt[1], pitch, width, G, cudaMemcpyDeviceToDevice, st));
-    gemv<R>(st, false, kc, kc, mone, X0 + kc, n2, sX, qr + kc, n2, one<R>(), qr, n2, G);  // q_a = r_a - Y1 q_b
+    if (H->lev[0].xr > 0) {
+      if ((xrc = xprod(0, rt[1], qr))) return xrc;
+    } else {
+      LS_CUDA_TRY(cudaMemcpy2DAsync(tb, pitch, rt[1] + kc, pitch, width, G, cudaMemcpyDeviceToDevice, st));
+      gemv<R>(st, false, kc, kc, mone, X0 + (size_t)kc * n2, n2, sX, rt[1], n2, one<R>(), tb, n2, G);  // r_b - Y2 r_a
+      gemv<R>(st, false, kc, kc, one<R>(), X0 + (size_t)kc * n2 + kc, n2, sX, tb, n2, zero<R>(), qr + kc, n2, G);
+      LS_CUDA_TRY(cudaMemcpy2DAsync(qr, pitch, rt[1], pitch, width, G, cudaMemcpyDeviceToDevice, st));
+      gemv<R>(st, false, kc, kc, mone, X0 + kc, n2, sX, qr + kc, n2, one<R>(), qr, n2, G);  // q_a = r_a - Y1 q_b
+    }
     gemv<R>(st, false, kc, kc, one<R>(), G1, kc, 0, qr + kc, n2, zero<R>(), wt[1], n2, G);
     gemv<R>(st, true, kc, kc, one<R>(), G1, kc, 0, qr, n2, zero<R>(), wt[1] + kc, n2, G);
   }
@@ -2551,7 +2631,7 @@ int apply_core(ls_handle* H, z64** slots, cudaStream_t st) {
     const cx<R>* Sc = reinterpret_cast<const cx<R>*>(H->lev[l + 1].S);
     const cx<R>* X = reinterpret_cast<const cx<R>*>(H->lev[l].X);
     const cx<R>* Gs = reinterpret_cast<const cx<R>*>(H->lev[l + 1].Gsib);
-    if (P >= kFusedMinNodes && sizeof(cx<R>) * (kp + 3 * n2) <= 48 * 1024) {
+    if (H->lev[l].xr <= 0 && P >= kFusedMinNodes && sizeof(cx<R>) * (kp + 3 * n2) <= 48 * 1024) {
       count_launch();
       down_node_kernel<R><<<P, 256, sizeof(cx<R>) * (kp + 3 * n2), st>>>(kc, kp, U, Sc, X, Gs, wt[l], rt[l + 1],
                                                                           wt[l + 1]);
@@ -2564,7 +2644,7 @@ int apply_core(ls_handle* H, z64** slots, cudaStream_t st) {
     gemv<R>(st, false, kc, kc, mone, Sc, kc, 2LL * kc * kc, Uw, n2, one<R>(), t, n2, P);
     gemv<R>(st, false, kc, kc, mone, Sc + (size_t)kc * kc, kc, 2LL * kc * kc, Uw + kc, n2, one<R>(), t + kc, n2, P);
     cx<R>* qbuf = rt[l + 1];  // q~ overwrites [r~_a; r~_b], which no later step reads
-    gemv<R>(st, false, n2, n2, one<R>(), X, n2, (long long)n2 * n2, t, n2, zero<R>(), qbuf, n2, P);
+    if ((xrc = xprod(l, t, qbuf))) return xrc;
     gemv<R>(st, false, kc, kc, one<R>(), Gs, kc, 0, qbuf + kc, n2, one<R>(), Uw, n2, P);
     gemv<R>(st, true, kc, kc, one<R>(), Gs, kc, 0, qbuf, n2, one<R>(), Uw + kc, n2, P);
   }
@@ -2934,6 +3014,12 @@ std::vector<ApplyOp> apply_ops(ls_handle* H) {
     tmp[l] = p;
     p += sz;
   }
+  std::vector<cx<R>*> ub(L + 1, nullptr);  // Q_R x of the levels whose X is factored
+  for (int l = 0; l < L; ++l)
+    if (H->lev[l].xr > 0) {
+      ub[l] = p;
+      p += ((size_t)H->nprob << l) * 2 * H->lev[l].xr;
+    }
   std::vector<ApplyOp> ops;
   auto gemv = [&](int M, int K, const void* A, int lda, long long sA, const void* x, long long sx, void* y,
                   long long sy, int batch, bool end, double ar = 1.0, const void* y0 = nullptr, long long sy0 = 0) {
@@ -2968,6 +3054,17 @@ std::vector<ApplyOp> apply_ops(ls_handle* H) {
     o.phase_end = end ? 1 : 0;
     ops.push_back(o);
   };
+  // y[b] = X_l x[b] (vectors of 2k_{l+1} entries, stride n2): X itself, or I + P_L Q_R
+  auto xprod = [&](int l, const cx<R>* x, cx<R>* y, bool end) {
+    const int kc = H->lev[l + 1].k, n2 = 2 * kc, P = H->nprob << l, r = H->lev[l].xr;
+    if (r <= 0) {
+      gemv(n2, n2, H->lev[l].X, n2, (long long)n2 * n2, x, n2, y, n2, P, end);
+      return;
+    }
+    gemv(r, kc, H->lev[l + 1].GLT, kc, 0, x, n2, ub[l], 2 * r, P, false);           // L^T x_a
+    gemv(r, kc, H->lev[l + 1].GRT, kc, 0, x + kc, n2, ub[l] + r, 2 * r, P, true);   // R^T x_b
+    gemv(n2, 2 * r, H->lev[l].X, 2 * r, (long long)n2 * 2 * r, ub[l], 2 * r, y, n2, P, end, 1.0, x, n2);
+  };
   const LevelData& lf = H->lev[L];
   const int kL = lf.k;
   {                                                                                  // leaves (Eq. 24)
@@ -2989,19 +3086,23 @@ std::vector<ApplyOp> apply_ops(ls_handle* H) {
   for (int l = L - 1; l >= 1; --l) {                                                 // up pass (Eq. 28)
     const int P = H->nprob << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
     if (identity_u(l)) {
-      gemv(n2, n2, H->lev[l].X, n2, (long long)n2 * n2, rt[l + 1], n2, rt[l], n2, P, true);
+      xprod(l, rt[l + 1], rt[l], true);
       continue;
     }
-    gemv(n2, n2, H->lev[l].X, n2, (long long)n2 * n2, rt[l + 1], n2, tmp[l + 1], n2, P, true);
+    xprod(l, rt[l + 1], tmp[l + 1], true);
     gemv(kp, n2, H->lev[l].UT, n2, 0, tmp[l + 1], n2, rt[l], kp, P, true);
   }
   {                                                                                  // root (Eq. 29)
     const int kc = H->lev[1].k, n2 = 2 * kc, G = H->nprob;                           // one root per problem
     const long long sX = (long long)n2 * n2;
-    const cx<R>* X0 = reinterpret_cast<const cx<R>*>(H->lev[0].X);  // [., Y1; Y2, W]
-    gemv(kc, kc, X0 + (size_t)kc * n2, n2, sX, rt[1], n2, wt[1] + kc, n2, G, true, -1.0, rt[1] + kc, n2);  // r_b - Y2 r_a
-    gemv(kc, kc, X0 + (size_t)kc * n2 + kc, n2, sX, wt[1] + kc, n2, tmp[1] + kc, n2, G, true);            // q_b = W (.)
-    gemv(kc, kc, X0 + kc, n2, sX, tmp[1] + kc, n2, tmp[1], n2, G, true, -1.0, rt[1], n2);                  // q_a = r_a - Y1 q_b
+    const cx<R>* X0 = reinterpret_cast<const cx<R>*>(H->lev[0].X);
+    if (H->lev[0].xr > 0) {  // q = X_0 [r_a; r_b] with X_0 = I + P_L Q_R
+      xprod(0, rt[1], tmp[1], true);
+    } else {                 // X_0 kept as [., Y1; Y2, W]
+      gemv(kc, kc, X0 + (size_t)kc * n2, n2, sX, rt[1], n2, wt[1] + kc, n2, G, true, -1.0, rt[1] + kc, n2);  // r_b - Y2 r_a
+      gemv(kc, kc, X0 + (size_t)kc * n2 + kc, n2, sX, wt[1] + kc, n2, tmp[1] + kc, n2, G, true);            // q_b = W (.)
+      gemv(kc, kc, X0 + kc, n2, sX, tmp[1] + kc, n2, tmp[1], n2, G, true, -1.0, rt[1], n2);                  // q_a = r_a - Y1 q_b
+    }
     gemv(kc, kc, H->lev[1].Gsib, kc, 0, tmp[1] + kc, n2, wt[1], n2, G, false);
     gemv(kc, kc, H->lev[1].GT, kc, 0, tmp[1], n2, wt[1] + kc, n2, G, true);
   }
@@ -3016,7 +3117,7 @@ std::vector<ApplyOp> apply_ops(ls_handle* H) {
     gemv(kc, kc, Sc, kc, 2LL * kc * kc, Uw, n2, tmp[l + 1], n2, P, false, -1.0, rt[l + 1], n2);
     gemv(kc, kc, Sc + (size_t)kc * kc, kc, 2LL * kc * kc, Uw + kc, n2, tmp[l + 1] + kc, n2, P, true, -1.0,
          rt[l + 1] + kc, n2);                                                        // t = r~ - diag(S) U w~
-    gemv(n2, n2, H->lev[l].X, n2, (long long)n2 * n2, tmp[l + 1], n2, rt[l + 1], n2, P, true);  // q~ = X t
+    xprod(l, tmp[l + 1], rt[l + 1], true);                                          // q~ = X t
     gemv(kc, kc, H->lev[l + 1].Gsib, kc, 0, rt[l + 1] + kc, n2, wt[l + 1], n2, P, false, 1.0, Uw, n2);
     gemv(kc, kc, H->lev[l + 1].GT, kc, 0, rt[l + 1], n2, wt[l + 1] + kc, n2, P, true, 1.0, Uw + kc, n2);
   }
@@ -3064,6 +3165,12 @@ std::vector<ApplyOp> apply_ops_transpose(ls_handle* H) {
     tmp[l] = p;
     p += sz;
   }
+  std::vector<cx<R>*> ub(L + 1, nullptr);  // P_L^T x of the levels whose X is factored
+  for (int l = 0; l < L; ++l)
+    if (H->lev[l].xr > 0) {
+      ub[l] = p;
+      p += ((size_t)H->nprob << l) * 2 * H->lev[l].xr;
+    }
   std::vector<ApplyOp> ops;
   auto gemv = [&](int M, int K, const void* A, int lda, long long sA, const void* x, long long sx, void* y,
                   long long sy, int batch, bool end, double ar = 1.0, const void* y0 = nullptr, long long sy0 = 0) {
@@ -3097,6 +3204,17 @@ std::vector<ApplyOp> apply_ops_transpose(ls_handle* H) {
     o.phase_end = 1;
     ops.push_back(o);
   };
+  // y[b] = X_l^T x[b]: X^T itself, or (I + P_L Q_R)^T = I + Q_R^T P_L^T
+  auto xprodT = [&](int l, const cx<R>* x, cx<R>* y, bool end) {
+    const int kc = H->lev[l + 1].k, n2 = 2 * kc, P = H->nprob << l, r = H->lev[l].xr;
+    if (r <= 0) {
+      gemv(n2, n2, H->lev[l].XT, n2, (long long)n2 * n2, x, n2, y, n2, P, end);
+      return;
+    }
+    gemv(2 * r, n2, H->lev[l].XLT, n2, (long long)2 * r * n2, x, n2, ub[l], 2 * r, P, true);  // u = P_L^T x
+    gemv(kc, r, H->lev[l + 1].GL, r, 0, ub[l], 2 * r, y, n2, P, false, 1.0, x, n2);          // x_a + L u_a
+    gemv(kc, r, H->lev[l + 1].GR, r, 0, ub[l] + r, 2 * r, y + kc, n2, P, end, 1.0, x + kc, n2);
+  };
   const LevelData& lf = H->lev[L];
   const int kL = lf.k;
   leafop(1, F, nullptr);                                                              // F <- g
@@ -3106,7 +3224,7 @@ std::vector<ApplyOp> apply_ops_transpose(ls_handle* H) {
     const cx<R>* STc = reinterpret_cast<const cx<R>*>(H->lev[l + 1].ST);
     gemv(kc, kc, H->lev[l + 1].Gsib, kc, 0, wt[l + 1] + kc, n2, tmp[l + 1], n2, P, false);       // Gamma w~
     gemv(kc, kc, H->lev[l + 1].GT, kc, 0, wt[l + 1], n2, tmp[l + 1] + kc, n2, P, true);
-    gemv(n2, n2, H->lev[l].XT, n2, (long long)n2 * n2, tmp[l + 1], n2, rt[l + 1], n2, P, true);  // t_l
+    xprodT(l, tmp[l + 1], rt[l + 1], true);                                           // t_l
     gemv(kc, kc, STc, kc, 2LL * kc * kc, rt[l + 1], n2, tmp[l + 1], n2, P, false, -1.0, wt[l + 1], n2);
     gemv(kc, kc, STc + (size_t)kc * kc, kc, 2LL * kc * kc, rt[l + 1] + kc, n2, tmp[l + 1] + kc, n2, P, true, -1.0,
          wt[l + 1] + kc, n2);                                                          // w~ - diag(S)^T t_l
@@ -3119,13 +3237,26 @@ std::vector<ApplyOp> apply_ops_transpose(ls_handle* H) {
     gemv(kc, kc, H->lev[1].GT, kc, 0, wt[1], n2, tmp[1] + kc, n2, G, true);
     // r~_1 = X_0^T v with X_0 kept as [., Y1; Y2, W] (so X_0^T's blocks are [., Y2^T; Y1^T, W^T]):
     // [v_a - Y2^T u; u], u = W^T (v_b - Y1^T v_a)
-    const cx<R>* XT0 = reinterpret_cast<const cx<R>*>(H->lev[0].XT);
-    gemv(kc, kc, XT0 + (size_t)kc * n2, n2, sX, tmp[1], n2, wt[1], n2, G, true, -1.0, tmp[1] + kc, n2);
-    gemv(kc, kc, XT0 + (size_t)kc * n2 + kc, n2, sX, wt[1], n2, rt[1] + kc, n2, G, true);
-    gemv(kc, kc, XT0 + kc, n2, sX, rt[1] + kc, n2, rt[1], n2, G, true, -1.0, tmp[1], n2);
+    if (H->lev[0].xr > 0) {
+      xprodT(0, tmp[1], rt[1], true);
+    } else {
+      const cx<R>* XT0 = reinterpret_cast<const cx<R>*>(H->lev[0].XT);
+      gemv(kc, kc, XT0 + (size_t)kc * n2, n2, sX, tmp[1], n2, wt[1], n2, G, true, -1.0, tmp[1] + kc, n2);
+      gemv(kc, kc, XT0 + (size_t)kc * n2 + kc, n2, sX, wt[1], n2, rt[1] + kc, n2, G, true);
+      gemv(kc, kc, XT0 + kc, n2, sX, rt[1] + kc, n2, rt[1], n2, G, true, -1.0, tmp[1], n2);
+    }
   }
   for (int l = 1; l <= L - 1; ++l) {
     const int P = H->nprob << l, kc = H->lev[l + 1].k, n2 = 2 * kc, kp = H->lev[l].k;
+    if (H->lev[l].xr > 0) {  // r~_{l+1} = t_l + v + Q_R^T P_L^T v, v = U r~_l
+      const int r = H->lev[l].xr;
+      gemv(n2, kp, H->lev[l].U, kp, 0, rt[l], kp, tmp[l + 1], n2, P, false);        // v
+      gemv(n2, kp, H->lev[l].U, kp, 0, rt[l], kp, rt[l + 1], n2, P, true, 1.0, rt[l + 1], n2);   // t_l + v
+      gemv(2 * r, n2, H->lev[l].XLT, n2, (long long)2 * r * n2, tmp[l + 1], n2, ub[l], 2 * r, P, true);
+      gemv(kc, r, H->lev[l + 1].GL, r, 0, ub[l], 2 * r, rt[l + 1], n2, P, false, 1.0, rt[l + 1], n2);
+      gemv(kc, r, H->lev[l + 1].GR, r, 0, ub[l] + r, 2 * r, rt[l + 1] + kc, n2, P, true, 1.0, rt[l + 1] + kc, n2);
+      continue;
+    }
     gemv(n2, kp, H->lev[l].U, kp, 0, rt[l], kp, tmp[l + 1], n2, P, true);             // U r~_l
     gemv(n2, n2, H->lev[l].XT, n2, (long long)n2 * n2, tmp[l + 1], n2, rt[l + 1], n2, P, true, 1.0, rt[l + 1],
          n2);                                                                          // r~_{l+1} = t_l + X^T U r~_l
@@ -3139,17 +3270,31 @@ std::vector<ApplyOp> apply_ops_transpose(ls_handle* H) {
 // U^T and G^T of every level (the apply reads every product row-wise).
 // U^T and G^T of level l (the build makes them as soon as U and G of the level
 // exist, off the end of the build).
+// L^T and R^T of level l's sibling factors (the Woodbury apply reads them row-wise).
+int lowrank_transpose(ls_handle* H, int l, cudaStream_t st) {
+  LevelData& lv = H->lev[l];
+  if (lv.gr <= 0 || lv.GLT) return LS_OK;
+  const bool fp64 = H->prec == LS_FP64;
+  const size_t es = fp64 ? sizeof(z64) : sizeof(c32);
+  int rc;
+  if ((rc = dalloc(&lv.GLT, es * (size_t)lv.k * lv.gr))) return rc;
+  if ((rc = dalloc(&lv.GRT, es * (size_t)lv.k * lv.gr))) return rc;
+  if ((rc = transpose_batch(fp64, lv.GL, lv.k, lv.gr, 1, lv.GLT, st))) return rc;
+  return transpose_batch(fp64, lv.GR, lv.k, lv.gr, 1, lv.GRT, st);
+}
+
 int level_transpose(ls_handle* H, int l, cudaStream_t st) {
   const bool fp64 = H->prec == LS_FP64;
   const size_t es = fp64 ? sizeof(z64) : sizeof(c32);
   LevelData& lv = H->lev[l];
-  if (lv.UT) return LS_OK;
+  if (lv.UT) return lowrank_transpose(H, l, st);
   const int m = l == H->L ? H->s * H->s : 2 * H->lev[l + 1].k, k = lv.k;
   int rc;
   if ((rc = dalloc(&lv.UT, es * (size_t)std::max(m * k, 1)))) return rc;
   if ((rc = dalloc(&lv.GT, es * (size_t)std::max(k * k, 1)))) return rc;
   if ((rc = transpose_batch(fp64, lv.U, m, k, 1, lv.UT, st))) return rc;
-  return transpose_batch(fp64, lv.Gsib, k, k, 1, lv.GT, st);
+  if ((rc = transpose_batch(fp64, lv.Gsib, k, k, 1, lv.GT, st))) return rc;
+  return lowrank_transpose(H, l, st);
 }
 
 int level_transposes(ls_handle* H, cudaStream_t st) {
@@ -3249,7 +3394,12 @@ int apply_transpose_init(ls_handle* H, cudaStream_t st) {
   for (int l = 0; l <= L; ++l) {
     LevelData& lv = H->lev[l];
     const int nx = l == L ? n : 2 * H->lev[l + 1].k, P = H->nprob << l;
-    if (!lv.XT) {
+    if (lv.xr > 0) {  // factored X: P_L^T per node
+      if (!lv.XLT) {
+        if ((rc = dalloc(&lv.XLT, es * (size_t)P * nx * 2 * lv.xr))) return rc;
+        if ((rc = transpose_batch(fp64, lv.X, nx, 2 * lv.xr, P, lv.XLT, st))) return rc;
+      }
+    } else if (!lv.XT) {
       if ((rc = dalloc(&lv.XT, es * (size_t)P * std::max(nx * nx, 1)))) return rc;
       if ((rc = transpose_batch(fp64, lv.X, nx, nx, P, lv.XT, st))) return rc;
     }
@@ -3368,6 +3518,7 @@ __global__ void __launch_bounds__(256) scatter_block_kernel(TreeGeom g, const cx
 size_t apply_work_entries(const ls_handle* H) {
   size_t vec = (size_t)2 * ((size_t)H->nprob << H->L) * H->s * H->s;
   for (int l = 1; l <= H->L; ++l) vec += (size_t)3 * ((size_t)H->nprob << l) * std::max(1, H->lev[l].k) * 2;
+  for (int l = 0; l < H->L; ++l) vec += ((size_t)H->nprob << l) * 2 * std::max(0, H->lev[l].xr);
   return vec;
 }
 

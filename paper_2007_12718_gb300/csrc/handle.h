@@ -24,6 +24,11 @@ struct LevelData {
   int gr = 0;            // rank of Gsib ~ GL GR^T (Woodbury merge); -1: the level keeps the Schur form
   void* GL = nullptr;    // k x gr
   void* GR = nullptr;    // k x gr
+  void* GLT = nullptr;   // gr x k: GL transposed (the apply reads every product row-wise)
+  void* GRT = nullptr;   // gr x k: GR transposed
+  int xr = 0;            // > 0: X of this level is kept as I + P_L Q_R, X holding P_L (2k' x 2xr per
+                         // node, k' the children's rank), Q_R = diag(GL^T, GR^T) of the children's level
+  void* XLT = nullptr;   // per node: P_L transposed (2xr x 2k'), for the transposed apply
 };
 
 struct ls_handle {

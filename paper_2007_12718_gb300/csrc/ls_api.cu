@@ -489,6 +489,9 @@ void ls_free(ls_handle* H) {
     f(lv.ST);
     f(lv.GL);
     f(lv.GR);
+    f(lv.GLT);
+    f(lv.GRT);
+    f(lv.XLT);
   }
   f(H->Gleaf);
   f(H->XBU);

@@ -168,7 +168,7 @@ int cache_store(ls_handle* H, cudaStream_t st) {
 // ------------------------------------------------------------- files
 namespace {
 
-constexpr char kMagic[8] = {'L', 'S', 'H', 'B', 'S', 'F', '0', '2'};
+constexpr char kMagic[8] = {'L', 'S', 'H', 'B', 'S', 'F', '0', '3'};
 
 struct FileHeader {
   char magic[8];
@@ -182,7 +182,7 @@ struct FileHeader {
 };
 
 struct FileLevel {
-  int m, k, ring, gr;
+  int m, k, ring, gr, xr;
 };
 
 // sizes (entries) of a level's arrays
@@ -198,7 +198,7 @@ LevelSizes level_sizes(const ls_handle* H, int l) {
   z.U = l >= 1 ? (size_t)lv.m * lv.k : 0;
   z.G = l >= 1 ? (size_t)lv.k * lv.k : 0;
   z.F = lv.gr > 0 ? (size_t)lv.k * lv.gr : 0;
-  z.X = P * n2 * n2;
+  z.X = P * n2 * (lv.xr > 0 ? 2 * (size_t)lv.xr : n2);
   z.S = l >= 1 ? P * (size_t)lv.k * lv.k : 0;
   return z;
 }
@@ -296,7 +296,7 @@ int ls_save(const ls_handle* H, const char* path, void* stream) {
   // depend on the next level's rank, so the loader reads the table first)
   for (int l = 0; l <= H->L; ++l) {
     const LevelData& lv = H->lev[l];
-    ls::FileLevel fl{lv.m, lv.k, lv.ring, lv.gr};
+    ls::FileLevel fl{lv.m, lv.k, lv.ring, lv.gr, lv.xr};
     if (fwrite(&fl, sizeof(fl), 1, file.f) != 1) {
       ls::set_last_error_text("ls_save: write failed");
       return LS_EINVAL;
@@ -380,7 +380,7 @@ int ls_load(const char* path, void* stream, ls_handle** out) {
       ls::set_last_error_text("ls_load: file truncated");
       return fail(LS_EINVAL);
     }
-    if (fl.k < 0 || fl.m < 0 || fl.gr > fl.k || (l >= 1 && fl.k > fl.m)) {
+    if (fl.k < 0 || fl.m < 0 || fl.gr > fl.k || fl.xr < 0 || (l >= 1 && fl.k > fl.m)) {
       ls::set_last_error_text("ls_load: bad level record");
       return fail(LS_EINVAL);
     }
@@ -388,6 +388,7 @@ int ls_load(const char* path, void* stream, ls_handle** out) {
     lv.k = fl.k;
     lv.ring = fl.ring;
     lv.gr = fl.gr;
+    lv.xr = fl.xr;
   }
   for (int l = 1; l <= H->L; ++l) {
     LevelData& lv = H->lev[l];
