@@ -86,7 +86,7 @@ typedef struct {
                          level's sibling block is factored once, G ~ L R^T by a row ID at
                          tolerance tol, and the merge inverts an r x r matrix instead of a
                          k x k one (Sec. 4.1, the remark on the rank of G); used where
-                         k >= 192 and r <= k / 2.  0 = the Schur form everywhere; 2 = the
+                         k >= 48 and r <= k / 2.  0 = the Schur form everywhere; 2 = the
                          Woodbury form at every level with r < k (small grids, tests).      */
   int reuse_compression; /* 1 = keep the compression (per-level skeletons, U, sibling blocks and
                          their factors) in a process-wide cache and take it from there when a

@@ -1709,7 +1709,7 @@ __global__ void gather_rows_t_kernel(const cx<R>* __restrict__ G, int k, const i
 // Levels whose sibling block takes the Woodbury form: large enough that the
 // products dominate, and a rank at most half the order (else the Schur form
 // costs no more).
-constexpr int kWoodburyMinRank = 192;
+constexpr int kWoodburyMinRank = 48;
 // Sibling blocks from this order on are factored from a random sketch (Sec. 2.1,
 // the randomised ID): the row ID of Y = G Omega (k x s, Omega Gaussian) selects
 // the same kind of skeleton rows J and interpolation matrix T as the ID of G
@@ -2752,7 +2752,46 @@ __device__ __forceinline__ void apply_rows(const ApplyOp& op, long long gw, long
   }
 }
 
-// Rows of more than 128 entries (rb = 32): split-K form.  A block takes a tile
+// Rows of more than 160 entries when there are at least two rows per warp of
+// the grid: one warp per row, eight chunks of 32 entries in flight per lane,
+// no block barrier (the split-K form below serves operations with few rows).
+template <class R>
+__device__ __forceinline__ void apply_rows_long(const ApplyOp& op, long long gw, long long nwarps, int lane) {
+  const cx<R>* A = reinterpret_cast<const cx<R>*>(op.A);
+  const cx<R>* X = reinterpret_cast<const cx<R>*>(op.x);
+  const cx<R>* Y0 = reinterpret_cast<const cx<R>*>(op.y0);
+  cx<R>* Y = reinterpret_cast<cx<R>*>(op.y);
+  const cx<R> alpha = mk<R>((R)op.ar, (R)op.ai);
+  const int K = op.K, M = op.M;
+  const long long rows = (long long)op.batch * M;
+  for (long long r = gw; r < rows; r += nwarps) {
+    const int b = (int)(r / M), i = (int)(r % M);
+    const cx<R>* a = A + b * op.sA + (long long)i * op.lda;
+    const cx<R>* xv = X + b * op.sx;
+    const cx<R> y0v = (Y0 && lane == 0) ? ldcg_cx(Y0 + b * op.sy0 + i) : mk<R>(0, 0);
+    cx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0);
+    int j = lane;
+    for (; j + 7 * 32 < K; j += 8 * 32) {
+      cx<R> av[8], xw[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) av[u] = a[j + 32 * u];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) xw[u] = ldcg_cx(xv + j + 32 * u);
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        fma_(acc0, av[u], xw[u]);
+        fma_(acc1, av[u + 1], xw[u + 1]);
+      }
+    }
+    for (; j < K; j += 32) fma_(acc0, a[j], ldcg_cx(xv + j));
+    cx<R> v = acc0 + acc1;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = v + shfl_xor(v, o);
+    if (lane == 0) Y[b * op.sy + i] = alpha * v + y0v;
+  }
+}
+
+// Rows of more than 160 entries (rb = 32): split-K form.  A block takes a tile
 // of RT consecutive rows; each warp one (row, 256-entry chunk) pair with all
 // eight of a lane's loads issued before the first multiply-add, so that one
 // memory round trip serves a whole tile even when the rows are too few to give
@@ -2947,6 +2986,8 @@ __global__ void __launch_bounds__(1024) apply_persistent_kernel(const ApplyOp* _
         apply_rows<R, 8>(op, gw, nwarps, lane);
       else if (op.rb == 16)
         apply_rows<R, 16>(op, gw, nwarps, lane);
+      else if (rows >= 2 * nwarps)
+        apply_rows_long<R>(op, gw, nwarps, lane);
       else
         apply_rows_split<R>(op, leaf_mem, lane);
     }

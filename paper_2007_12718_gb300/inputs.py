@@ -118,6 +118,8 @@ WORKLOADS = {
     # smaller sizes: the CPU oracle's bounded samples and intermediate checks
     "precond_n256_10ppw": dict(n=256, kappa=50 * np.pi, b=lambda n: gaussian_family(n, 0), order_precond=4,
                                order_matvec=10, eps=1e-4, leaf=8),
+    "precond_n512_10ppw": dict(n=512, kappa=100 * np.pi, b=lambda n: gaussian_family(n, 0), order_precond=4,
+                               order_matvec=10, eps=1e-4, leaf=8),
     "precond_n1024_10ppw": dict(n=1024, kappa=200 * np.pi, b=lambda n: gaussian_family(n, 0), order_precond=4,
                                 order_matvec=10, eps=1e-4, leaf=8),
     # the largest grid of the family the FFT matvec takes (padded rows of 8192):

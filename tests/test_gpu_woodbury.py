@@ -8,8 +8,8 @@ an r x r matrix.
   0 < r < k.
 * Woodbury and Schur forms agree to the tolerance on the same handle geometry, and
   a GMRES solve with the Woodbury preconditioner matches the oracle's dense LU.
-* Default (woodbury = 1) at 256^2: the top levels take the Woodbury form with
-  r <= k / 2.
+* Default (woodbury = 1) at 256^2: every level of rank >= 48 takes the Woodbury
+  form with r <= k / 2.
 """
 import numpy as np
 import pytest
@@ -89,9 +89,9 @@ def test_woodbury_default_engages_at_256():
     H = ls.ls_build(n, 1.0 / n, w["kappa"], w["b"](n), w["eps"], precision=ls.LS_TF32X3)
     info = H.info()
     sr, rk = info["sibling_ranks"], info["ranks"]
-    top = [l for l in range(1, info["levels"] + 1) if rk[l] >= 192]
+    top = [l for l in range(1, info["levels"] + 1) if rk[l] >= 48]
     assert top and all(0 < sr[l] <= rk[l] // 2 for l in top), (sr, rk)
-    assert all(sr[l] == 0 for l in range(1, info["levels"] + 1) if rk[l] < 192)
+    assert all(sr[l] == 0 for l in range(1, info["levels"] + 1) if rk[l] < 48)
     ls.ls_free(H)
 
 
