@@ -1971,6 +1971,71 @@ int merge_woodbury(ls_handle* H, int l, cx<R>* X, const cx<R>* Sc, cudaStream_t 
   return LS_OK;
 }
 
+// out[b](i, :) = src[b](idx[i], :), i < nidx, rows of `cols` entries.
+template <class R>
+__global__ void gather_rows_kernel(const cx<R>* __restrict__ src, long long sS, int lds, const int* __restrict__ idx,
+                                   int nidx, int cols, cx<R>* __restrict__ dst, long long sD, int ldd) {
+  const int b = blockIdx.y;
+  const long long tot = (long long)nidx * cols;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / cols), c = (int)(t % cols);
+    dst[b * sD + (long long)i * ldd + c] = src[b * sS + (long long)idx[i] * lds + c];
+  }
+}
+
+// S[b] = U^T E[b] (U: n2 x kp, E[b]: n2 x kp) for the ID's U, whose skeleton rows
+// J are the identity: U^T E = E(J, :) + T^T E(J^c, :), T = U(J^c, :) -- a product of
+// order (n2 - kp) instead of n2.  `scratch` holds P (n2 - kp) x kp entries.
+template <class R>
+int ut_product(ls_handle* H, int l, const cx<R>* E, int n2, int kp, cx<R>* S, int P, cx<R>* scratch,
+               cudaStream_t st, double* flops) {
+  const LevelData& lv = H->lev[l];
+  const cx<R>* U = reinterpret_cast<const cx<R>*>(lv.U);
+  if ((int)lv.piv.size() != kp || lv.m != n2) {
+    gemm<R>(st, true, false, kp, kp, n2, one<R>(), U, kp, 0, E, kp, (long long)n2 * kp, zero<R>(), S, kp,
+            (long long)kp * kp, P);
+    *flops = P * 8.0 * (double)kp * n2 * kp;
+    return check_launch("U^T E");
+  }
+  const int nc = n2 - kp;
+  std::vector<int> sel(lv.piv);
+  {
+    std::vector<char> in(n2, 0);
+    for (int a : sel) in[a] = 1;
+    for (int i = 0; i < n2; ++i)
+      if (!in[i]) sel.push_back(i);
+  }
+  int* dsel = nullptr;
+  cx<R>* T = nullptr;
+  int rc;
+  if ((rc = dalloc((void**)&dsel, sizeof(int) * n2))) return rc;
+  if ((rc = dalloc((void**)&T, sizeof(cx<R>) * std::max<size_t>((size_t)nc * kp, 1)))) {
+    dfree(dsel);
+    return rc;
+  }
+  // pageable source: the call returns once the indices are staged
+  LS_CUDA_TRY(cudaMemcpyAsync(dsel, sel.data(), sizeof(int) * n2, cudaMemcpyHostToDevice, st));
+  auto gather = [&](const cx<R>* src, long long sS, const int* idx, int nidx, cx<R>* dst, long long sD, int batch) {
+    for (int b0 = 0; b0 < batch; b0 += kMaxGridYZ) {
+      const dim3 g((unsigned)std::min<long long>(1024, ((long long)nidx * kp + 255) / 256), std::min(kMaxGridYZ, batch - b0));
+      count_launch();
+      gather_rows_kernel<R><<<g, 256, 0, st>>>(src + (size_t)b0 * sS, sS, kp, idx, nidx, kp, dst + (size_t)b0 * sD, sD,
+                                               kp);
+    }
+  };
+  gather(E, (long long)n2 * kp, dsel, kp, S, (long long)kp * kp, P);  // E(J, :)
+  if (nc > 0) {
+    gather(U, 0, dsel + kp, nc, T, 0, 1);                                       // T = U(J^c, :)
+    gather(E, (long long)n2 * kp, dsel + kp, nc, scratch, (long long)nc * kp, P);  // E(J^c, :)
+    gemm<R>(st, true, false, kp, kp, nc, one<R>(), T, kp, 0, scratch, kp, (long long)nc * kp, one<R>(), S, kp,
+            (long long)kp * kp, P);
+  }
+  dfree(T);
+  dfree(dsel);
+  *flops = P * 8.0 * (double)kp * nc * kp;
+  return check_launch("U^T E (skeleton rows)");
+}
+
 // Bytes of one apply (Algorithm 2): every factor once, the X of levels L-1..1
 // a second time (the upward and the downward pass both apply it), the grid vectors.
 template <class R>
@@ -2244,10 +2309,9 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const Le
                 F + (size_t)r * kp, kp, (long long)r2 * kp, P);
         gemm<R>(st, false, false, n2, kp, r2, on, X, r2, sP, F, kp, (long long)r2 * kp, on, D, kp, (long long)n2 * kp,
                 P);
-        gemm<R>(st, true, false, kp, kp, n2, on, U, kp, 0, D, kp, (long long)n2 * kp, ze, Sl, kp, (long long)kp * kp,
-                P);
-        fl = P * (2.0 * 8 * (double)kc * kc * kp + 2.0 * 8 * (double)r * kc * kp + 8.0 * (double)n2 * r2 * kp +
-                  8.0 * (double)kp * n2 * kp);
+        double fu = 0;
+        if ((rc = ut_product<R>(H, l, D, n2, kp, Sl, P, E, st, &fu))) return rc;
+        fl = P * (2.0 * 8 * (double)kc * kc * kp + 2.0 * 8 * (double)r * kc * kp + 8.0 * (double)n2 * r2 * kp) + fu;
       }
       if ((rc = check_launch("merge S (Woodbury)"))) return rc;
       prof_end(ts, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * ((double)sP + 2.0 * kc * kc + (double)kp * kp), fl);
@@ -2275,11 +2339,11 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const Le
     // E = X D ; S = U^T E
     gemm<R>(st, false, false, n2, kp, n2, one<R>(), X, n2, (long long)n2 * n2, D, kp, (long long)n2 * kp, zero<R>(),
             E, kp, (long long)n2 * kp, P);
-    gemm<R>(st, true, false, kp, kp, n2, one<R>(), U, kp, 0, E, kp, (long long)n2 * kp, zero<R>(),
-            reinterpret_cast<cx<R>*>(lv.S), kp, (long long)kp * kp, P);
+    double fu = 0;
+    if ((rc = ut_product<R>(H, l, E, n2, kp, reinterpret_cast<cx<R>*>(lv.S), P, D, st, &fu))) return rc;
     if ((rc = check_launch("merge S"))) return rc;
     {
-      double fl = P * (2.0 * 8 * (double)kc * kc * kp + 8.0 * (double)n2 * n2 * kp + 8.0 * (double)kp * n2 * kp);
+      double fl = P * (2.0 * 8 * (double)kc * kc * kp + 8.0 * (double)n2 * n2 * kp) + fu;
       prof_end(ts, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * ((double)n2 * n2 + 2.0 * kc * kc + (double)kp * kp), fl);
       H->flops_build += fl;
     }

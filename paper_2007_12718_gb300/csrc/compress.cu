@@ -1457,6 +1457,7 @@ int compress_t(ls_handle* H, cudaStream_t st, const LevelDone& level_done, cudaS
       return rc;
     ls::dfree(A);
     lv.k = k;
+    lv.piv.assign(hp.begin(), hp.begin() + k);
     lv.skel_x.resize(k);
     lv.skel_y.resize(k);
     for (int a = 0; a < k; ++a) {

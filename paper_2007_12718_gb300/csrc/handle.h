@@ -13,6 +13,7 @@ struct LevelData {
   int k = 0;         // skeleton rank k_l
   int ring = 0;      // proxy points of this level's ring
   std::vector<int> skel_x, skel_y;  // skeleton, local coordinates in a level-l box
+  std::vector<int> piv;              // the skeleton's rows among the level's m candidates (U(piv, :) = I)
   void* U = nullptr;     // m x k, row-major (precision of the preconditioner)
   void* Gsib = nullptr;  // k x k: G(skel_alpha, skel_beta) of two children on this level
   void* X = nullptr;     // per node: (s^2)^2 on the leaf level, (2 k_{l+1})^2 above

@@ -38,7 +38,7 @@ struct CacheKey {
 
 struct CacheLevel {
   int m = 0, k = 0, ring = 0, gr = 0;
-  std::vector<int> sx, sy;
+  std::vector<int> sx, sy, piv;
   void *U = nullptr, *G = nullptr, *GL = nullptr, *GR = nullptr;
 };
 
@@ -113,6 +113,7 @@ int cache_fetch(ls_handle* H, cudaStream_t st, bool* found) {
       lv.ring = c.ring;
       lv.skel_x = c.sx;
       lv.skel_y = c.sy;
+      lv.piv = c.piv;
       if ((rc = dup(&lv.U, c.U, es * (size_t)c.m * c.k, st))) return rc;
       if ((rc = dup(&lv.Gsib, c.G, es * (size_t)c.k * c.k, st))) return rc;
       lv.gr = c.gr;
@@ -149,6 +150,7 @@ int cache_store(ls_handle* H, cudaStream_t st) {
     c.gr = lv.gr;
     c.sx = lv.skel_x;
     c.sy = lv.skel_y;
+    c.piv = lv.piv;
     if ((rc = dup(&c.U, lv.U, es * (size_t)lv.m * lv.k, st))) break;
     if ((rc = dup(&c.G, lv.Gsib, es * (size_t)lv.k * lv.k, st))) break;
     if (lv.gr > 0) {
