@@ -440,7 +440,16 @@ class Leg:
         return t, {"h2d_bytes_per_step": self.N * 8 + self.N * 16, "d2h_bytes_per_step": self.N * 16}
 
 
-# phases of the method (Sec. 8(d) of the build's survey) and the kernel families of each
+# DRAM traffic of a kernel family per build + solve step, from one ncu capture of the same command
+# (dram__bytes_read.sum + dram__bytes_write.sum); keyed by (workload, precision, family).
+MEASURED_TRAFFIC = {
+    ("precond_n2048", "tf32x3", "merge_gemm"): {
+        "bytes": 101.84e9,
+        "note": "bytes per build + solve step of the 271 tcgen05 GEMM launches (ncu, one-pass metrics at full "
+                "size; profiles/tc_gemm_traffic_precond_n2048.md); ~300 algorithmic flops per DRAM byte"},
+}
+
+# phases of the method and the kernel families of each
 PHASES = {
     "compress": ["cpqr_id"],
     "merges": ["leaf_build", "merge_gemm", "merge_inverse"],
@@ -556,9 +565,12 @@ def run_ours(args, rank, world):
     fams, phases, e2e_roof = rooflines(prof, pk, tensor, t_mixed / args.steps, 1)
     top = max((k for k in fams if k not in ("hbs_apply", "gmres_orth")), key=lambda k: fams[k]["ms_per_step"])
     f = fams[top]
+    traffic = MEASURED_TRAFFIC.get((args.workload, args.precision, top))
     roof = {"bound": f["bound"], "kernel": top, "achieved": f["achieved"], "peak": f["peak"], "unit": f["unit"],
-            "frac": f["frac"], "traffic": None, "peak_source": f["peak_source"],
+            "frac": f["frac"], "traffic": traffic["bytes"] if traffic else None, "peak_source": f["peak_source"],
             "note": "achieved = the family's algorithmic work over its device time in the profiled pass"}
+    if traffic:
+        roof["traffic_note"] = traffic["note"]
 
     secondary = {}
     if not args.no_secondary:
