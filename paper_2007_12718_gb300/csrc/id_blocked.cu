@@ -383,8 +383,7 @@ __global__ void __launch_bounds__(1024) pchol_kernel(const cx<R>* __restrict__ g
   cx<R>* Lc = G + kPool * LG;                   // kPool x LL
   __shared__ R d[kPool];
   __shared__ int chosen[kPool], order[kB];
-  __shared__ int s_best, s_stop, s_be;
-  __shared__ R s_dbest, s_d0;
+  __shared__ int s_be;
   if (S->done) return;
   const int tid = threadIdx.x;
   const int np = S->npool, k = S->k;
@@ -421,57 +420,55 @@ __global__ void __launch_bounds__(1024) pchol_kernel(const cx<R>* __restrict__ g
   if (tid < kPool) d[tid] = tid < np ? G[tid * LG + tid].re : R(0);
   __syncthreads();
   const int jmax = min(kB, min(np, kmax - k));
-  int j = 0;
-  for (; j < jmax; ++j) {
-    if (tid < 32) {  // warp 0: argmax over the pool
+  // the greedy steps in warp 0 alone (lane i owns candidates i and i + 32): no block barrier
+  // per step; the same operations in the same order as a block-wide loop would take
+  if (tid < 32) {
+    const int lane = tid;
+    int j = 0;
+    R d0 = R(0);
+    for (; j < jmax; ++j) {
       R bv = R(-1);
       int bi = 0x7fffffff;
-      for (int i = tid; i < kPool; i += 32)
+      for (int i = lane; i < kPool; i += 32)
         if (!chosen[i] && (d[i] > bv || (d[i] == bv && i < bi))) {
           bv = d[i];
           bi = i;
         }
-      for (int o = 16; o; o >>= 1) {
-        const R ov = __shfl_down_sync(0xffffffffu, bv, o);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      for (int o = 16; o; o >>= 1) {  // every lane ends with the largest d (lowest index on ties)
+        const R ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ov > bv || (ov == bv && oi < bi)) {
           bv = ov;
           bi = oi;
         }
       }
-      if (tid == 0) {
-        if (j == 0) s_d0 = bv;
-        const bool stop = bi >= kPool || !(bv > R(0)) || (outside > 0 && (double)bv < kAlpha2 * outside) ||
-                          (j > 0 && (double)bv <= drange * (double)s_d0);
-        s_stop = stop ? 1 : 0;
-        s_best = bi;
-        s_dbest = bv;
+      if (j == 0) d0 = bv;
+      const bool stop = bi >= kPool || !(bv > R(0)) || (outside > 0 && (double)bv < kAlpha2 * outside) ||
+                        (j > 0 && (double)bv <= drange * (double)d0);
+      if (stop) break;
+      const int best = bi;
+      const R sd = sqrt(bv);
+      for (int i = lane; i < np; i += 32) {
+        cx<R> v = G[i * LG + best];  // <a_i, a_best>
+        for (int jj = 0; jj < j; ++jj) {
+          const cx<R> a = Lc[i * LL + jj], bc = Lc[best * LL + jj];
+          v.re -= a.re * bc.re + a.im * bc.im;  // v -= a conj(bc)
+          v.im -= a.im * bc.re - a.re * bc.im;
+        }
+        v = scale(v, R(1) / sd);
+        if (i == best) v = mk<R>(sd, R(0));
+        Lc[i * LL + j] = v;
       }
-    }
-    __syncthreads();
-    if (s_stop) break;
-    const int best = s_best;
-    const R sd = sqrt(s_dbest);
-    if (tid < np) {
-      cx<R> v = G[tid * LG + best];  // <a_i, a_best>
-      for (int jj = 0; jj < j; ++jj) {
-        const cx<R> a = Lc[tid * LL + jj], bc = Lc[best * LL + jj];
-        v.re -= a.re * bc.re + a.im * bc.im;  // v -= a conj(bc)
-        v.im -= a.im * bc.re - a.re * bc.im;
+      __syncwarp();
+      for (int i = lane; i < np; i += 32) d[i] = chosen[i] || i == best ? R(0) : d[i] - abs2(Lc[i * LL + j]);
+      if (lane == 0) {
+        chosen[best] = 1;
+        order[j] = best;
       }
-      v = scale(v, R(1) / sd);
-      if (tid == best) v = mk<R>(sd, R(0));
-      Lc[tid * LL + j] = v;
+      __syncwarp();
     }
-    __syncthreads();
-    if (tid < np) d[tid] = chosen[tid] || tid == best ? R(0) : d[tid] - abs2(Lc[tid * LL + j]);
-    if (tid == 0) {
-      chosen[best] = 1;
-      order[j] = best;
-    }
-    __syncthreads();
+    if (lane == 0) s_be = j;
   }
-  if (tid == 0) s_be = j;
   __syncthreads();
   const int be = s_be;
   for (int e = tid; e < kB * kB; e += 1024) {
@@ -485,35 +482,50 @@ __global__ void __launch_bounds__(1024) pchol_kernel(const cx<R>* __restrict__ g
   __shared__ int s_pool[kPool];
   if (tid < kPool) s_pool[tid] = S->pool[tid];
   __syncthreads();
-  if (tid == 0) {
-    int nu = 0;
-    for (int i = 0; i < be; ++i) s_upos[nu++] = k + i;
+  if (tid < 32) {  // warp 0; every lane follows the same (uniform) control flow
+    const int lane = tid;
+    int nu = be;
+    if (lane < be) s_upos[lane] = k + lane;  // be <= kB = 32
+    __syncwarp();
     for (int i = 0; i < be; ++i) {
+      // follow the earlier swaps: position k + t (t < i) now holds the row that sat at swp[t],
+      // and only later swaps can move it again
       int x = s_pool[order[i]];
-      for (int i2 = 0; i2 < i; ++i2)
-        if (x == k + i2) x = s_swp[i2];
-      s_swp[i] = x;
-      int ix = -1;
-      for (int t = 0; t < nu; ++t)
-        if (s_upos[t] == x) ix = t;
-      if (ix < 0) {
-        ix = nu;
-        s_upos[nu++] = x;
+      for (int lo = 0;;) {
+        const int t = x - k;
+        if (t < lo || t >= i) break;
+        x = s_swp[t];
+        lo = t + 1;
       }
-      s_ia[i] = i;  // position k + i is upos[i]
-      s_ix[i] = ix;
+      int ix = -1;  // x among the touched positions (a warp-wide search)
+      for (int base = 0; base < nu && ix < 0; base += 32) {
+        const int t = base + lane;
+        const unsigned hit = __ballot_sync(0xffffffffu, t < nu && s_upos[t] == x);
+        if (hit) ix = base + __ffs(hit) - 1;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        s_swp[i] = x;
+        if (ix < 0) s_upos[nu] = x;
+        s_ia[i] = i;  // position k + i is upos[i]
+        s_ix[i] = ix < 0 ? nu : ix;
+      }
+      if (ix < 0) ++nu;
+      __syncwarp();
     }
-    for (int t = 0; t < nu; ++t) s_cur[t] = t;
-    for (int i = 0; i < be; ++i) {
-      const int a = s_ia[i], b = s_ix[i];
-      const int tmp = s_cur[a];
-      s_cur[a] = s_cur[b];
-      s_cur[b] = tmp;
+    if (lane == 0) {
+      for (int t = 0; t < nu; ++t) s_cur[t] = t;
+      for (int i = 0; i < be; ++i) {
+        const int a = s_ia[i], b = s_ix[i];
+        const int tmp = s_cur[a];
+        s_cur[a] = s_cur[b];
+        s_cur[b] = tmp;
+      }
+      s_nu = nu;
+      S->be = be;
+      S->nu = nu;
+      if (be == 0) S->done = 1;  // no admissible pivot left (the Gram matrix is numerically zero)
     }
-    s_nu = nu;
-    S->be = be;
-    S->nu = nu;
-    if (be == 0) S->done = 1;  // no admissible pivot left (the Gram matrix is numerically zero)
   }
   __syncthreads();
   const int nu = s_nu;
