@@ -31,7 +31,9 @@ Parity pins (tests/test_oracle_hbs.py): the ID property U(J,:) = I and its
 accuracy on the full complement block; the Lemma 4.1 identity; the HBS inverse
 against the dense inverse (error ~ eps, -> 0 as eps -> 0); Table 1's proxy
 accuracy; the transposed apply by the bilinear identity y^T (M x) = (M^T y)^T x
-and against the dense transpose of M assembled column by column.
+and against the dense transpose of M assembled column by column; the Woodbury
+local solution operator against the inverse of Eq. (26) (and the block as printed,
+without the scattering matrices, against it: it fails).
 """
 import numpy as np
 import scipy.linalg as sla
@@ -125,6 +127,27 @@ def row_id(A, eps):
     U[perm[:k], np.arange(k)] = 1.0
     U[perm[k:], :] = T.T
     return perm[:k], U
+
+
+def woodbury_local_solution(S_a, S_b, L_ab, R_ab, L_ba, R_ba):
+    """Local solution operator of a parent by the Woodbury form of Sec. 4.1 (the
+    remark after Algorithm 2, Eq. blockinv): with low-rank sibling blocks
+    G_ab = L_ab R_ab^T and G_ba = L_ba R_ba^T (plain transposes: G is complex
+    symmetric), X = [[I, S_a G_ab], [S_b G_ba, I]]^-1 (Eq. (26)) is
+        X = I - P (I + Q P)^-1 Q,   P = diag(S_a L_ab, S_b L_ba),
+                                     Q = [[0, R_ab^T], [R_ba^T, 0]],
+    and the middle block I + Q P = [[I, R_ab^T S_b L_ba], [R_ba^T S_a L_ab, I]]
+    carries the children's scattering matrices (the printed block omits them)."""
+    k1, k2 = S_a.shape[0], S_b.shape[0]
+    r1, r2 = L_ab.shape[1], L_ba.shape[1]
+    P = np.zeros((k1 + k2, r1 + r2), dtype=complex)
+    P[:k1, :r1] = S_a @ L_ab
+    P[k1:, r1:] = S_b @ L_ba
+    Q = np.zeros((r1 + r2, k1 + k2), dtype=complex)
+    Q[:r1, k1:] = R_ab.T
+    Q[r1:, :k1] = R_ba.T
+    middle = np.eye(r1 + r2, dtype=complex) + Q @ P
+    return np.eye(k1 + k2, dtype=complex) - P @ np.linalg.solve(middle, Q)
 
 
 class Compression:

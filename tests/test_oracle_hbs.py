@@ -153,3 +153,28 @@ def test_cavity_preconditioned_iterations_match_paper():
     r = np.linalg.norm(f - nystrom.matvec_fft(spec, kappa, b, s)) / np.linalg.norm(f)
     assert r < 2e-10
     assert 3 <= k <= 5, k
+
+
+def test_woodbury_local_solution_is_inverse_of_eq26():
+    """Sec. 4.1, Eq. blockinv: with G_ab = L R^T of rank r the Woodbury form equals
+    [[I, S_a G_ab], [S_b G_ab^T, I]]^-1; the printed middle block
+    [[I, R_ba^T L_ba], [R_ab^T L_ab, I]] (no S) does not."""
+    rng = np.random.default_rng(3)
+    k, r = 40, 9
+    cplx = lambda *sh: rng.standard_normal(sh) + 1j * rng.standard_normal(sh)  # noqa: E731
+    S_a, S_b = 0.3 * cplx(k, k), 0.3 * cplx(k, k)
+    L, R = cplx(k, r), cplx(k, r)
+    G = L @ R.T
+    Z = np.block([[np.eye(k), S_a @ G], [S_b @ G.T, np.eye(k)]])
+    X = hbs.woodbury_local_solution(S_a, S_b, L, R, R, L)  # G_ba = G^T = R L^T
+    assert np.linalg.norm(X - np.linalg.inv(Z)) <= 1e-10 * np.linalg.norm(X)
+    # the block as printed (children's S left out) gives another matrix
+    P = np.zeros((2 * k, 2 * r), dtype=complex)
+    P[:k, :r] = S_a @ L
+    P[k:, r:] = S_b @ R
+    Q = np.zeros((2 * r, 2 * k), dtype=complex)
+    Q[:r, k:] = R.T
+    Q[r:, :k] = L.T
+    printed = np.block([[np.eye(r), L.T @ R], [R.T @ L, np.eye(r)]])
+    Xp = np.eye(2 * k) - P @ np.linalg.solve(printed, Q)
+    assert np.linalg.norm(Xp - np.linalg.inv(Z)) > 1e-2 * np.linalg.norm(X)
