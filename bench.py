@@ -635,6 +635,79 @@ PAPER_CAVITY = {6400: (0.47, 0.20, 4), 25600: (1.64, 0.62, 5), 102400: (6.62, 2.
 PAPER_LENS = {102400: 51, 409600: 9, 1638400: 7, 6553600: 7, 26214400: 9}
 
 
+# The paper's direct-solver tables (Sec. 6.1, Gaussian bump, kappa = 25): (eps, N) ->
+# (T_skel + T_build, T_apply, residual); 36-core workstation.
+PAPER_DIRECT = {
+    (1e-3, 6400): (1.75, 0.05, 7.74e-05), (1e-3, 25600): (7.28, 0.12, 5.71e-05),
+    (1e-3, 102400): (37.85, 0.48, 9.75e-05), (1e-3, 409600): (167.85, 2.00, 1.56e-04),
+    (1e-6, 6400): (3.16, 0.07, 9.54e-09), (1e-6, 25600): (16.00, 0.19, 7.13e-08),
+    (1e-6, 102400): (79.25, 0.76, 4.15e-08), (1e-6, 409600): (443.86, 6.58, 4.39e-08),
+    (1e-9, 6400): (4.04, 0.07, 1.57e-12), (1e-9, 25600): (23.39, 0.24, 3.37e-12),
+    (1e-9, 102400): (117.57, 1.04, 1.45e-11), (1e-9, 409600): (675.66, 6.82, 3.48e-09),
+    (1e-12, 6400): (4.40, 0.07, 1.87e-15), (1e-12, 25600): (23.70, 0.22, 3.80e-15),
+    (1e-12, 102400): (125.78, 1.00, 6.94e-15), (1e-12, 409600): (767.18, 5.98, 1.71e-14),
+}
+
+
+def run_direct_sweep(args):
+    """The direct solver of Sec. 6.1: b = 1.5 exp(-160 |x|^2), kappa = 25, 10th-order
+    corrections inside the HBS and in the operator, 100-point leaves, eps = 1e-3 ... 1e-12,
+    n = 80 2^j.  FP32 storage (tf32x3 merges) for eps = 1e-3, FP64 below.  Per size: build
+    time, one apply, and the residual ||f - A M f|| / ||f|| of the direct solution M f
+    (f = -kappa^2 b u_inc), CUDA events after one warm-up.  One JSON line."""
+    import torch
+
+    import paper_2007_12718_gb300 as ls
+    from paper_2007_12718_gb300 import inputs
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    rows = []
+    kappa = 25.0
+    for eps in (1e-3, 1e-6, 1e-9, 1e-12):
+        prec = ls.LS_TF32X3 if eps >= 1e-3 else ls.LS_FP64
+        for j in range(args.sweep_first, min(args.sweep_levels, 4)):  # n <= 640 (FP64 below 1e-6)
+            n = 80 << j
+            h = 1.0 / n
+            b = torch.from_numpy(inputs.gaussian_direct(n)).to(dev)
+            f = torch.zeros(n, n, dtype=torch.complex128, device=dev)
+            q = torch.zeros_like(f)
+            y = torch.zeros_like(f)
+            tb = ta = 0.0
+            for it in range(2):
+                torch.cuda.synchronize()
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record(stream)
+                H = ls.ls_build(n, h, kappa, b, eps, leaf_side=10, order_precond=10, order_matvec=10, precision=prec)
+                e[1].record(stream)
+                if it == 0:
+                    ls.ls_rhs_plane_wave(H, [0.0], f)
+                    ls.ls_apply(H, f, q)  # warm-up of the apply
+                    torch.cuda.synchronize()
+                    e[1].record(stream)
+                ls.ls_apply(H, f, q)
+                e[2].record(stream)
+                torch.cuda.synchronize()
+                if it == 1:
+                    tb, ta = e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / 1e3
+                    ls.ls_matvec(H, q, y)
+                    res = float(torch.linalg.norm(f - y) / torch.linalg.norm(f))
+                    bi = H.info()
+                ls.ls_free(H)
+            paper = PAPER_DIRECT.get((eps, n * n))
+            rows.append({"eps": eps, "N": n * n, "precision": "tf32x3" if prec == ls.LS_TF32X3 else "fp64",
+                         "t_build_s": tb, "t_apply_s": ta, "residual": res, "factor_GB": bi["factor_bytes"] / 1e9,
+                         "ranks_top": bi["ranks"][1:4],
+                         "paper": None if paper is None else {"t_skel_plus_build_s": paper[0], "t_apply_s": paper[1],
+                                                              "residual": paper[2]}})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            del b, f, q, y
+            torch.cuda.empty_cache()
+    print(json.dumps({"metric": METRIC, "sweep": "direct solver, Gaussian bump, kappa = 25 (Sec. 6.1)",
+                      "rows": rows}), flush=True)
+
+
 def run_sweep(args):
     """A sweep of the paper's test problems on one GPU: the cavity of Sec. 6.3 (n = 80 2^j,
     kappa = 2 pi n / 10) or the lens of Sec. 6.2 (n = 320 2^j, kappa = 300), 100-point
@@ -780,9 +853,10 @@ def main():
                          "2048^2 (1.20 s against 1.31 s per step) and at 256^2; 0 compresses every level")
     ap.add_argument("--kernel-case", default=None,
                     help="time one kernel family alone (gemm:M:N:K:ENGINE[:REPS] or id:M:P:R) for profiling")
-    ap.add_argument("--sweep", nargs="?", const="cavity", default=None, choices=["cavity", "lens"],
+    ap.add_argument("--sweep", nargs="?", const="cavity", default=None, choices=["cavity", "lens", "direct"],
                     help="run a sweep of the paper's test problems instead of the benchmark: the cavity of "
-                         "Sec. 6.3 (10 points per wavelength, default) or the lens of Sec. 6.2 (kappa = 300)")
+                         "Sec. 6.3 (10 points per wavelength, default), the lens of Sec. 6.2 (kappa = 300), or "
+                         "the direct solver of Sec. 6.1 (Gaussian bump, eps 1e-3 .. 1e-12)")
     ap.add_argument("--sweep-levels", type=int, default=6, help="sizes of the sweep: n = 80, 160, ..., 80 2^(levels-1)")
     ap.add_argument("--sweep-first", type=int, default=0, help="first size of the sweep: n = 80 2^first")
     ap.add_argument("--sweep-maxit", type=int, default=100, help="GMRES iteration limit in the sweep (memory: "
@@ -798,6 +872,9 @@ def main():
         return
     if args.kernel_case:
         run_kernel_case(args.kernel_case)
+        return
+    if args.sweep == "direct":
+        run_direct_sweep(args)
         return
     if args.sweep:
         run_sweep(args)

@@ -493,6 +493,25 @@ __device__ __forceinline__ void leaf_origin(const TreeGeom& g, int leaf, int& ox
   }
 }
 
+// Leaf matrices for the batched leaf build: X[leaf] = I + B G_leaf (Eq. (20) before
+// the inverse) and BU[leaf] = B U; one thread per entry of either.
+template <class R>
+__global__ void leaf_matrix_kernel(TreeGeom g, const double* __restrict__ b, double kap2, const cx<R>* __restrict__ Gleaf,
+                                   const cx<R>* __restrict__ U, int k, cx<R>* __restrict__ X, cx<R>* __restrict__ BU,
+                                   long long nleaf) {
+  const int n = g.s * g.s;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= nleaf * n * n) return;
+  const int leaf = (int)(t / ((long long)n * n)), i = (int)((t / n) % n), j = (int)(t % n);
+  int ox, oy;
+  leaf_origin(g, leaf, ox, oy);
+  const R bi = (R)(kap2 * b[(long long)(oy + i / g.s) * g.nx + ox + i % g.s]);
+  cx<R> v = scale(Gleaf[i * n + j], bi);
+  if (i == j) v.re += R(1);
+  X[t] = v;
+  if (j < k) BU[((long long)leaf * n + i) * k + j] = scale(U[i * k + j], bi);
+}
+
 // Leaf build (Algorithm 1, leaf loop): one block per leaf.
 template <class R>
 __global__ void __launch_bounds__(256) leaf_build_kernel(TreeGeom g, const double* __restrict__ b, double kap2,
@@ -2074,15 +2093,44 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const Le
   H->factor_bytes += sizeof(cx<R>) * nleaf * ((double)n * n + (double)n * kL + (double)kL * kL);
   TreeGeom g = make_geom(H);
   size_t smem = sizeof(cx<R>) * ((size_t)n * (n + 1) + (size_t)n * kL + n) + sizeof(R) * n + sizeof(int) * n + 64;
-  LS_CUDA_TRY(cudaFuncSetAttribute(leaf_build_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int tk = prof_begin(st);
-  count_launch();
-  leaf_build_kernel<R><<<(unsigned)nleaf, 256, smem, st>>>(g, H->b, H->kappa * H->kappa,
-                                                          reinterpret_cast<const cx<R>*>(H->Gleaf),
-                                                          reinterpret_cast<const cx<R>*>(lf.U), kL,
-                                                          reinterpret_cast<cx<R>*>(lf.X),
-                                                          reinterpret_cast<cx<R>*>(H->XBU),
-                                                          reinterpret_cast<cx<R>*>(lf.S), H->d_err);
+  if (smem <= 220 * 1024) {  // one block per leaf, everything in shared memory
+    LS_CUDA_TRY(cudaFuncSetAttribute(leaf_build_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    count_launch();
+    leaf_build_kernel<R><<<(unsigned)nleaf, 256, smem, st>>>(g, H->b, H->kappa * H->kappa,
+                                                            reinterpret_cast<const cx<R>*>(H->Gleaf),
+                                                            reinterpret_cast<const cx<R>*>(lf.U), kL,
+                                                            reinterpret_cast<cx<R>*>(lf.X),
+                                                            reinterpret_cast<cx<R>*>(H->XBU),
+                                                            reinterpret_cast<cx<R>*>(lf.S), H->d_err);
+  } else {  // large leaves (FP64, 100 points): batched inverse and GEMMs
+    cx<R>* Xl = reinterpret_cast<cx<R>*>(lf.X);
+    cx<R>* BU = nullptr;
+    const size_t ib = sizeof(cx<R>) * nleaf * ((size_t)n * 32 + 128) + sizeof(int) * nleaf * (n + 128) + (1 << 16);
+    void* scr = nullptr;
+    if ((rc = dalloc((void**)&BU, sizeof(cx<R>) * nleaf * n * std::max(kL, 1))) || (rc = dalloc(&scr, ib))) return rc;
+    struct FreeOnExit2 {
+      void* a;
+      void* b;
+      ~FreeOnExit2() {
+        dfree(a);
+        dfree(b);
+      }
+    } fr{BU, scr};
+    const long long tot = (long long)nleaf * n * n, totk = (long long)nleaf * n * kL;
+    count_launch(2);
+    leaf_matrix_kernel<R><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(g, H->b, H->kappa * H->kappa,
+                                                                       reinterpret_cast<const cx<R>*>(H->Gleaf),
+                                                                       reinterpret_cast<const cx<R>*>(lf.U), kL, Xl,
+                                                                       BU, (long long)nleaf);
+    if ((rc = invert_batch<R>(H, Xl, n, n, (long long)n * n, (int)nleaf, scr, ib, st))) return rc;
+    (void)totk;
+    gemm<R>(st, false, false, n, kL, n, one<R>(), Xl, n, (long long)n * n, BU, kL, (long long)n * kL, zero<R>(),
+            reinterpret_cast<cx<R>*>(H->XBU), kL, (long long)n * kL, (int)nleaf);  // X B U
+    gemm<R>(st, true, false, kL, kL, n, one<R>(), reinterpret_cast<const cx<R>*>(lf.U), kL, 0,
+            reinterpret_cast<const cx<R>*>(H->XBU), kL, (long long)n * kL, zero<R>(),
+            reinterpret_cast<cx<R>*>(lf.S), kL, (long long)kL * kL, (int)nleaf);  // U^T X B U
+  }
   if ((rc = check_launch("leaf_build"))) return rc;
   {
     double fl = nleaf * (8.0 * n * n * n + 8.0 * n * n * kL + 8.0 * kL * n * kL);

@@ -76,6 +76,13 @@ def cavity(n, centre=(0.5, 0.5)):
     return (1.0 - np.sin(0.5 * th) ** 500) * np.exp(-2000.0 * (0.1 - r2) ** 2)
 
 
+def gaussian_direct(n, centre=(0.5, 0.5)):
+    """The potential of the paper's direct-solver experiments (Sec. 6.1),
+    b = 1.5 exp(-160 |x|^2), x measured from the domain centre."""
+    X, Y = grid_nodes(n)
+    return 1.5 * np.exp(-160.0 * ((X - centre[0]) ** 2 + (Y - centre[1]) ** 2))
+
+
 def lens(n, centre=(0.5, 0.5)):
     """The vertically graded lens of the paper's Sec. 6.2 test problems,
     b = 4 (x2 - 0.1) (1 - erf(25 (|x| - 0.3))), with x measured from the
