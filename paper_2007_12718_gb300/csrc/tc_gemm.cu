@@ -22,9 +22,10 @@
 //
 // One CTA computes a 128 x 128 complex tile.  Eight converter warps read the
 // FP32 operands straight from global memory (per thread one row of op(A) and
-// one column of op(B), half of a stage's 16 complex k, coalesced for either
-// storage order; the next stage's values are loaded while the current ones are
-// converted), split them and store the planes in the K-major no-swizzle layout
+// one column of op(B), half of a stage's complex k: 16-byte loads where that
+// run is contiguous, element loads coalesced across the warp where it is not;
+// the next two stages' values (FP16: the next one) are loaded while the
+// current ones are converted), split them and store the planes in the K-major no-swizzle layout
 // of 8-row x 16-byte core matrices (a fence makes them visible to the tensor
 // cores), then arrive on the stage's "full" mbarrier; one thread of the ninth
 // warp issues the MMAs of a stage and commits them to its "empty" mbarrier.
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K
                                                              int lda, long long sA, const c32* __restrict__ B, int ldb,
                                                              long long sB, c32 beta, c32* __restrict__ C, int ldc,
                                                              long long sC, int split, int band_lo, int band_hi,
-                                                             int* err, const unsigned* __restrict__ amax) {
+                                                             int* err, const unsigned* __restrict__ amax, int vec) {
   constexpr int BK = TcK<F16>::BK, KH = TcK<F16>::KH;
   extern __shared__ __align__(1024) unsigned char smraw[];
   float* stages = reinterpret_cast<float*>(smraw);  // TC_NS x TC_STAGE floats
@@ -264,36 +265,83 @@ __global__ void __launch_bounds__(TC_THREADS) tc_gemm_kernel(int M, int N, int K
   if (warp < 8) {  // converters: row r of op(A) and of op(B)^T, k-half kh of every stage
     const int r = tid & (TC_BM - 1), kh = (tid >> 7) * KH;
     const int ra = m0 + r, cb = n0 + r;
-    c32 va[TC_KH_MAX], vb[TC_KH_MAX];  // the operands of the next stage, loaded ahead (KH used)
-    auto load = [&](int s) {
+    // The KH complex k of stage s for row ra of op(A) and column cb of op(B).
+    // Where that run is contiguous in memory (A not transposed, B transposed)
+    // and 16-byte aligned (vec bit 0 / bit 1), it is read as KH / 2 16-byte
+    // loads; otherwise element by element (coalesced across the warp).
+    auto load = [&](int s, c32* xa, c32* xb) {
       const int k0 = s * BK + kh;
+      const bool kfull = k0 + KH <= K;
+      if (!TA && (vec & 1) && kfull) {
+        const float4* p = reinterpret_cast<const float4*>(A + (long long)(ra < M ? ra : 0) * lda + k0);
 #pragma unroll
-      for (int j = 0; j < KH; ++j) {
-        const int k = k0 + j;
-        va[j] = (ra < M && k < K) ? (TA ? A[(long long)k * lda + ra] : A[(long long)ra * lda + k]) : mk<float>(0.f, 0.f);
-        vb[j] = (cb < N && k < K) ? (TB ? B[(long long)cb * ldb + k] : B[(long long)k * ldb + cb]) : mk<float>(0.f, 0.f);
+        for (int j = 0; j < KH / 2; ++j) {
+          const float4 t = ra < M ? __ldg(p + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+          xa[2 * j] = mk<float>(t.x, t.y);
+          xa[2 * j + 1] = mk<float>(t.z, t.w);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < KH; ++j) {
+          const int k = k0 + j;
+          xa[j] = (ra < M && k < K) ? (TA ? A[(long long)k * lda + ra] : A[(long long)ra * lda + k]) : mk<float>(0.f, 0.f);
+        }
+      }
+      if (TB && (vec & 2) && kfull) {
+        const float4* p = reinterpret_cast<const float4*>(B + (long long)(cb < N ? cb : 0) * ldb + k0);
+#pragma unroll
+        for (int j = 0; j < KH / 2; ++j) {
+          const float4 t = cb < N ? __ldg(p + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+          xb[2 * j] = mk<float>(t.x, t.y);
+          xb[2 * j + 1] = mk<float>(t.z, t.w);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < KH; ++j) {
+          const int k = k0 + j;
+          xb[j] = (cb < N && k < K) ? (TB ? B[(long long)cb * ldb + k] : B[(long long)k * ldb + cb]) : mk<float>(0.f, 0.f);
+        }
       }
     };
-    load(0);
-    for (int s = 0; s < S; ++s) {
+    // Stage s: wait until the MMAs have released its buffer, split and store
+    // the operands, make them visible to the tensor cores and arrive.
+    auto put = [&](int s, const c32* xa, const c32* xb) -> bool {
       const int bi = s % TC_NS;
       if (s >= TC_NS && !mbar_wait(smem_u32(&empty_bar[bi]), ((s / TC_NS) - 1) & 1)) {
         atomicExch(&s_fail, 1);
-        break;
+        return false;
       }
-      if (*(volatile int*)&s_fail) break;
+      if (*(volatile int*)&s_fail) return false;
       float* stage = stages + (size_t)bi * TC_STAGE;
       if constexpr (F16) {
-        store_row16(stage, P_AR_HI, r, kh, va, sa);
-        store_row16(stage, P_BR_HI, r, kh, vb, sb);
+        store_row16(stage, P_AR_HI, r, kh, *reinterpret_cast<const c32(*)[TC_KH_MAX]>(xa), sa);
+        store_row16(stage, P_BR_HI, r, kh, *reinterpret_cast<const c32(*)[TC_KH_MAX]>(xb), sb);
       } else {
-        store_row(stage, P_AR_HI, r, kh, reinterpret_cast<const c32(&)[TC_BK / 2]>(va), sp);
-        store_row(stage, P_BR_HI, r, kh, reinterpret_cast<const c32(&)[TC_BK / 2]>(vb), sp);
+        store_row(stage, P_AR_HI, r, kh, *reinterpret_cast<const c32(*)[TC_BK / 2]>(xa), sp);
+        store_row(stage, P_BR_HI, r, kh, *reinterpret_cast<const c32(*)[TC_BK / 2]>(xb), sp);
       }
       // generic-proxy stores -> visible to the tensor cores (async proxy)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[bi])) : "memory");
-      if (s + 1 < S) load(s + 1);
+      return true;
+    };
+    if constexpr (F16) {  // one stage loaded ahead (KH = 16 complex per operand)
+      c32 va[KH], vb[KH];
+      load(0, va, vb);
+      for (int s = 0; s < S; ++s) {
+        if (!put(s, va, vb)) break;
+        if (s + 1 < S) load(s + 1, va, vb);
+      }
+    } else {  // two stages loaded ahead, in two register sets
+      c32 va0[KH], vb0[KH], va1[KH], vb1[KH];
+      load(0, va0, vb0);
+      if (S > 1) load(1, va1, vb1);
+      for (int s = 0; s < S; s += 2) {
+        if (!put(s, va0, vb0)) break;
+        if (s + 2 < S) load(s + 2, va0, vb0);
+        if (s + 1 >= S || !put(s + 1, va1, vb1)) break;
+        if (s + 3 < S) load(s + 3, va1, vb1);
+      }
     }
   } else if (lane == 0) {  // MMA issuer
     const uint32_t idesc = F16 ? make_idesc_f16(TC_BM, TC_BN) : make_idesc_tf32(TC_BM, TC_BN);
@@ -429,8 +477,14 @@ int launch_tc(cudaStream_t st, int M, int N, int K, c32 alpha, const c32* A, int
                                    (int)smem));
   dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, batch);
   count_launch();
+  // 16-byte row loads where a row of op(A) / column of op(B) is contiguous and
+  // every such row of every batch entry starts on a 16-byte boundary
+  auto al16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+  int vec = 0;
+  if (!TA && al16(A) && lda % 2 == 0 && (sA % 2 == 0 || batch == 1)) vec |= 1;
+  if (TB && al16(B) && ldb % 2 == 0 && (sB % 2 == 0 || batch == 1)) vec |= 2;
   tc_gemm_kernel<TA, TB, F16><<<grid, TC_THREADS, smem, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC,
-                                                              split, band_lo, band_hi, err, amax);
+                                                              split, band_lo, band_hi, err, amax, vec);
   return check_launch("tc_cgemm");
 }
 

@@ -46,7 +46,7 @@ def _rand(shape, seed):
 @pytest.mark.parametrize("M,N,K,ta,tb,batch", [
     (128, 64, 16, False, False, 1), (200, 100, 50, False, True, 2), (1, 1, 1, False, False, 1),
     (130, 70, 33, True, False, 3), (300, 64, 764, False, False, 1), (64, 200, 96, True, True, 2),
-    (764, 130, 40, False, False, 1)])
+    (764, 130, 40, False, False, 1), (97, 50, 37, False, True, 2)])
 def test_cgemm_engines(engine, M, N, K, ta, tb, batch):
     A = _rand((batch, K, M) if ta else (batch, M, K), 1)
     B = _rand((batch, N, K) if tb else (batch, K, N), 2)
