@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "handle.h"
 #include "prof.h"
@@ -1758,6 +1759,13 @@ __global__ void gaussian_kernel(cx<R>* __restrict__ Om, long long n, unsigned lo
   Om[t] = mk<R>((R)(rad * cs), (R)(rad * sn));
 }
 
+// The sibling factorisations of even and odd levels may run on two threads.
+std::mutex g_sibling_flops_mu;
+void add_sibling_flops(ls_handle* H, double f) {
+  std::lock_guard<std::mutex> lk(g_sibling_flops_mu);
+  H->flops_sibling += f;
+}
+
 // L, R of level l's sibling block (once per level; lv.gr = -1 when the level
 // keeps the Schur form).
 template <class R>
@@ -1785,15 +1793,15 @@ int sibling_lowrank(ls_handle* H, int l, cudaStream_t st) {
   if ((rc = dalloc((void**)&T, sizeof(cx<R>) * kk))) return rc;
   int r = 0;
   std::vector<int> J;
-  // sketch width: from the ranks of the two levels below (the cuts alternate in
-  // direction), scaled to this order, with margin; no sketch where it would not
-  // be well below k
+  // sketch width: from the rank two levels below (the same cut direction; the
+  // level between may still be in the making on another stream), scaled to
+  // this order, with margin; no sketch where it would not be well below k
   int sw = 0;
   if (k >= kSketchMinRank) {
     double pred = 0;
-    for (int d = 1; d <= 2 && l + d <= H->L; ++d) {
-      const LevelData& lo = H->lev[l + d];
-      if (lo.gr > 0 && lo.k > 0) pred = std::max(pred, (double)lo.gr * k / lo.k);
+    if (l + 2 <= H->L) {
+      const LevelData& lo = H->lev[l + 2];
+      if (lo.gr > 0 && lo.k > 0) pred = (double)lo.gr * k / lo.k;
     }
     if (pred > 0) sw = (int)std::min<double>(k, 1.2 * pred + 64);
     if (sw > 0.6 * k) sw = 0;
@@ -1822,7 +1830,7 @@ int sibling_lowrank(ls_handle* H, int l, cudaStream_t st) {
     dfree(Om);
     dfree(Y);
     if (rc) return rc;
-    H->flops_sibling += 8.0 * ks * k + 8.0 * ks * r;
+    add_sibling_flops(H, 8.0 * ks * k + 8.0 * ks * r);
     if (r > sw - 32) sw = 0;  // the sketch was too narrow for the rank: the ID of G itself
   }
   if (sw == 0) {
@@ -1832,7 +1840,7 @@ int sibling_lowrank(ls_handle* H, int l, cudaStream_t st) {
     rc = blocked_row_id<R>(A, k, k, H->tol, st, nullptr, T, &r, &J);
     g_tc_engine = prev_engine;
     if (rc) return rc;
-    H->flops_sibling += 8.0 * kk * r;
+    add_sibling_flops(H, 8.0 * kk * r);
   }
   if (r == 0 || (mode == 1 ? 2 * r > k : r >= k)) {
     lv.gr = -1;
@@ -2000,6 +2008,127 @@ __global__ void gather_rows_kernel(const cx<R>* __restrict__ src, long long sS, 
     const int i = (int)(t / cols), c = (int)(t % cols);
     dst[b * sD + (long long)i * ldd + c] = src[b * sS + (long long)idx[i] * lds + c];
   }
+}
+
+// out[b](i, c) = src[b](i, idx[c]), i < rows, c < nidx.
+template <class R>
+__global__ void gather_cols_kernel(const cx<R>* __restrict__ src, long long sS, int lds, const int* __restrict__ idx,
+                                   int nidx, int rows, cx<R>* __restrict__ dst, long long sD, int ldd) {
+  const int b = blockIdx.y;
+  const long long tot = (long long)rows * nidx;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / nidx), c = (int)(t % nidx);
+    dst[b * sD + (long long)i * ldd + c] = src[b * sS + (long long)i * lds + idx[c]];
+  }
+}
+
+// The skeleton part of D[b] = diag(S_a, S_b) U (Sc[b] = S_a, S_b, kc x kc each;
+// U(J, :) = I): D(i, c) = S_h(i - h kc, piv[c] - h kc) where row i and pivot
+// piv[c] lie in the same half h, else 0.
+template <class R>
+__global__ void d_skeleton_kernel(const cx<R>* __restrict__ Sc, int kc, const int* __restrict__ piv, int kp,
+                                  cx<R>* __restrict__ D) {
+  const int b = blockIdx.y, n2 = 2 * kc;
+  const long long tot = (long long)n2 * kp, kk = (long long)kc * kc;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / kp), c = (int)(t % kp);
+    const int h = i >= kc, j = piv[c];
+    D[b * tot + t] = (j >= kc) == (bool)h ? Sc[b * 2 * kk + h * kk + (long long)(i - h * kc) * kc + (j - h * kc)]
+                                          : mk<R>(0, 0);
+  }
+}
+
+// D[b] = diag(S_a, S_b) U (n2 x kp) for the ID's U of level l:
+// D(:, c) picks column piv[c] of S_a or S_b, and the interpolation rows add
+// S_h(:, J^c_h) U(J^c_h, :) -- products of order |J^c_h| instead of kc.
+// Without the pivot list (a level kept uncompressed or restored without it)
+// the two full products.
+template <class R>
+int su_product(ls_handle* H, int l, const cx<R>* Sc, int kc, int kp, cx<R>* D, int P, cudaStream_t st,
+               double* flops) {
+  const LevelData& lv = H->lev[l];
+  const cx<R>* U = reinterpret_cast<const cx<R>*>(lv.U);
+  const int n2 = 2 * kc;
+  const long long kk = (long long)kc * kc;
+  if ((int)lv.piv.size() != kp || lv.m != n2) {
+    gemm<R>(st, false, false, kc, kp, kc, one<R>(), Sc, kc, 2 * kk, U, kp, 0, zero<R>(), D, kp, (long long)n2 * kp, P);
+    gemm<R>(st, false, false, kc, kp, kc, one<R>(), Sc + kk, kc, 2 * kk, U + (size_t)kc * kp, kp, 0, zero<R>(),
+            D + (size_t)kc * kp, kp, (long long)n2 * kp, P);
+    *flops = P * 2.0 * 8 * (double)kc * kc * kp;
+    return check_launch("S U");
+  }
+  // index list: piv (kp), then the top complement (columns of S_a), then the
+  // bottom complement (columns of S_b)
+  std::vector<int> idx(lv.piv);
+  std::vector<char> in(n2, 0);
+  for (int a : lv.piv) in[a] = 1;
+  int nct = 0, ncb = 0;
+  for (int i = 0; i < kc; ++i)
+    if (!in[i]) {
+      idx.push_back(i);
+      ++nct;
+    }
+  for (int i = kc; i < n2; ++i)
+    if (!in[i]) {
+      idx.push_back(i - kc);
+      ++ncb;
+    }
+  const int nc = nct + ncb;
+  int* didx = nullptr;
+  cx<R>* T = nullptr;  // U(J^c_top, :) then U(J^c_bot, :): nc x kp
+  cx<R>* G = nullptr;  // S_a(:, J^c_top) then S_b(:, J^c_bot): P x kc x nc
+  struct Free {
+    void** p[3];
+    ~Free() {
+      for (auto q : p)
+        if (*q) dfree(*q);
+    }
+  } fr{{(void**)&didx, (void**)&T, (void**)&G}};
+  int rc;
+  if ((rc = dalloc((void**)&didx, sizeof(int) * (kp + 2 * (size_t)nc + 1)))) return rc;
+  if ((rc = dalloc((void**)&T, sizeof(cx<R>) * std::max<size_t>((size_t)nc * kp, 1)))) return rc;
+  if ((rc = dalloc((void**)&G, sizeof(cx<R>) * std::max<size_t>((size_t)P * kc * nc, 1)))) return rc;
+  // U's rows of the complement, as row indices of U (the bottom ones shifted back by kc)
+  for (int i = 0; i < nc; ++i) idx.push_back(idx[kp + i] + (i >= nct ? kc : 0));
+  // pageable source: the call returns once the indices are staged
+  LS_CUDA_TRY(cudaMemcpyAsync(didx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, st));
+  const int* dpiv = didx;
+  const int* dct = didx + kp;
+  const int* dcb = dct + nct;
+  const int* drow = didx + kp + nc;
+  for (int b0 = 0; b0 < P; b0 += kMaxGridYZ) {
+    const int nb = std::min(kMaxGridYZ, P - b0);
+    const dim3 g((unsigned)std::min<long long>(1024, ((long long)n2 * kp + 255) / 256), nb);
+    count_launch();
+    d_skeleton_kernel<R><<<g, 256, 0, st>>>(Sc + (size_t)b0 * 2 * kk, kc, dpiv, kp, D + (size_t)b0 * n2 * kp);
+    if (nc > 0) {
+      const dim3 gg((unsigned)std::min<long long>(1024, ((long long)kc * nc + 255) / 256), nb);
+      if (nct > 0) {
+        count_launch();
+        gather_cols_kernel<R><<<gg, 256, 0, st>>>(Sc + (size_t)b0 * 2 * kk, 2 * kk, kc, dct, nct, kc,
+                                                  G + (size_t)b0 * kc * nc, (long long)kc * nc, nc);
+      }
+      if (ncb > 0) {
+        count_launch();
+        gather_cols_kernel<R><<<gg, 256, 0, st>>>(Sc + (size_t)b0 * 2 * kk + kk, 2 * kk, kc, dcb, ncb, kc,
+                                                  G + (size_t)b0 * kc * nc + nct, (long long)kc * nc, nc);
+      }
+    }
+  }
+  if (nc > 0) {
+    const dim3 gt((unsigned)std::min<long long>(1024, ((long long)nc * kp + 255) / 256), 1);
+    count_launch();
+    gather_rows_kernel<R><<<gt, 256, 0, st>>>(U, 0, kp, drow, nc, kp, T, 0, kp);
+    if (nct > 0)
+      gemm<R>(st, false, false, kc, kp, nct, one<R>(), G, nc, (long long)kc * nc, T, kp, 0, one<R>(), D, kp,
+              (long long)n2 * kp, P);
+    if (ncb > 0)
+      gemm<R>(st, false, false, kc, kp, ncb, one<R>(), G + nct, nc, (long long)kc * nc, T + (size_t)nct * kp, kp, 0,
+              one<R>(), D + (size_t)kc * kp, kp, (long long)n2 * kp, P);
+  }
+  if ((rc = check_launch("S U (skeleton columns)"))) return rc;
+  *flops = P * 8.0 * (double)kc * kp * nc;
+  return LS_OK;
 }
 
 // S[b] = U^T E[b] (U: n2 x kp, E[b]: n2 x kp) for the ID's U, whose skeleton rows
@@ -2312,8 +2441,7 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const Le
     void* work_s = nullptr;
     if ((rc = dalloc(&work_s, sizeof(cx<R>) * 2 * (size_t)P * n2 * kp))) return rc;
     FreeOnExit free_work_s{work_s};
-    const cx<R>* U = reinterpret_cast<const cx<R>*>(lv.U);  // n2 x kp
-    cx<R>* D = reinterpret_cast<cx<R>*>(work_s);           // P x n2 x kp
+    cx<R>* D = reinterpret_cast<cx<R>*>(work_s);  // P x n2 x kp
     cx<R>* E = D + (size_t)P * n2 * kp;
     int ts = prof_begin(st);
     if (woodbury) {
@@ -2348,9 +2476,8 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const Le
         fl = P * (2.0 * 8 * (double)r * kc * kc + 2.0 * 8 * (double)n2 * r * kc);
       } else {
         // D = [S_a U_top ; S_b U_bot];  E = X D = D + P_L (Q_R D) (in D);  S = U^T E
-        gemm<R>(st, false, false, kc, kp, kc, on, Sc, kc, 2 * kk, U, kp, 0, ze, D, kp, (long long)n2 * kp, P);
-        gemm<R>(st, false, false, kc, kp, kc, on, Sc + kk, kc, 2 * kk, U + (size_t)kc * kp, kp, 0, ze,
-                D + (size_t)kc * kp, kp, (long long)n2 * kp, P);
+        double fd = 0;
+        if ((rc = su_product<R>(H, l, Sc, kc, kp, D, P, st, &fd))) return rc;
         cx<R>* F = E;  // Q_R D: P x 2r x kp
         gemm<R>(st, true, false, r, kp, kc, on, Lf, r, 0, D, kp, (long long)n2 * kp, ze, F, kp, (long long)r2 * kp, P);
         gemm<R>(st, true, false, r, kp, kc, on, Rf, r, 0, D + (size_t)kc * kp, kp, (long long)n2 * kp, ze,
@@ -2359,7 +2486,7 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const Le
                 P);
         double fu = 0;
         if ((rc = ut_product<R>(H, l, D, n2, kp, Sl, P, E, st, &fu))) return rc;
-        fl = P * (2.0 * 8 * (double)kc * kc * kp + 2.0 * 8 * (double)r * kc * kp + 8.0 * (double)n2 * r2 * kp) + fu;
+        fl = P * (2.0 * 8 * (double)r * kc * kp + 8.0 * (double)n2 * r2 * kp) + fd + fu;
       }
       if ((rc = check_launch("merge S (Woodbury)"))) return rc;
       prof_end(ts, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * ((double)sP + 2.0 * kc * kc + (double)kp * kp), fl);
@@ -2380,10 +2507,8 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const Le
       continue;
     }
     // D = [S_a U_top ; S_b U_bot]
-    gemm<R>(st, false, false, kc, kp, kc, one<R>(), Sc, kc, 2LL * kc * kc, U, kp, 0, zero<R>(), D, kp,
-            (long long)n2 * kp, P);
-    gemm<R>(st, false, false, kc, kp, kc, one<R>(), Sc + (size_t)kc * kc, kc, 2LL * kc * kc, U + (size_t)kc * kp, kp,
-            0, zero<R>(), D + (size_t)kc * kp, kp, (long long)n2 * kp, P);
+    double fd = 0;
+    if ((rc = su_product<R>(H, l, Sc, kc, kp, D, P, st, &fd))) return rc;
     // E = X D ; S = U^T E
     gemm<R>(st, false, false, n2, kp, n2, one<R>(), X, n2, (long long)n2 * n2, D, kp, (long long)n2 * kp, zero<R>(),
             E, kp, (long long)n2 * kp, P);
@@ -2391,7 +2516,7 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const Le
     if ((rc = ut_product<R>(H, l, E, n2, kp, reinterpret_cast<cx<R>*>(lv.S), P, D, st, &fu))) return rc;
     if ((rc = check_launch("merge S"))) return rc;
     {
-      double fl = P * (2.0 * 8 * (double)kc * kc * kp + 8.0 * (double)n2 * n2 * kp) + fu;
+      double fl = P * (8.0 * (double)n2 * n2 * kp) + fd + fu;
       prof_end(ts, PR_MERGE_GEMM, st, sizeof(cx<R>) * P * ((double)n2 * n2 + 2.0 * kc * kc + (double)kp * kp), fl);
       H->flops_build += fl;
     }

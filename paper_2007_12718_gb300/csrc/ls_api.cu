@@ -540,41 +540,49 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
   LS_CUDA_TRY(cudaEventRecord(ev[0], st));  // kernel table, spectrum, b: ready for both stages
   LS_CUDA_TRY(cudaStreamWaitEvent(sc, ev[0], 0));
   LS_CUDA_TRY(cudaStreamWaitEvent(sm, ev[0], 0));
-  // ss: each level's sibling block, transposes and low-rank factors (sibling_prepare),
-  // made by a third thread as soon as the level is compressed
-  cudaStream_t ss = nullptr;
-  LS_CUDA_TRY(cudaStreamCreateWithPriority(&ss, cudaStreamNonBlocking, prio_low));
+  // ss[0], ss[1]: each level's sibling block, transposes and low-rank factors
+  // (sibling_prepare), made as soon as the level is compressed by two more
+  // threads, one for the even and one for the odd levels: the levels kept
+  // uncompressed at the top are ready together with the first compressed one
+  // below them, and their factorisations then run side by side
+  cudaStream_t ss[2] = {nullptr, nullptr};
+  for (auto& q : ss) LS_CUDA_TRY(cudaStreamCreateWithPriority(&q, cudaStreamNonBlocking, prio_low));
   std::vector<cudaEvent_t> evs(L + 1, nullptr);
   for (auto& e : evs) LS_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   std::mutex mu;
   std::condition_variable cv;
-  int ready = L + 1;      // the lowest level index compressed so far (levels finish from L down to 1)
-  int sib_ready = L + 1;  // the lowest level whose sibling data are made
+  int ready = L + 1;                    // the lowest level index compressed so far (levels finish from L down to 1)
+  std::vector<char> sib_done(L + 2, 0);  // the levels whose sibling data are made
   bool abort = false;
   int mrc = LS_OK, src = LS_OK;
   std::string merr, serr;
-  std::thread sibling([&] {
-    ls::StreamScope scope(ss);
+  auto sibling_worker = [&](int parity) {
+    cudaStream_t q = ss[parity];
+    ls::StreamScope scope(q);
     for (int l = L; l >= 1; --l) {
+      if ((l & 1) != parity) continue;
       {
         std::unique_lock<std::mutex> lk(mu);
         cv.wait(lk, [&] { return abort || ready <= l; });
         if (abort) return;
       }
-      int r = cudaStreamWaitEvent(ss, ev[l], 0) == cudaSuccess ? ls::sibling_prepare(H, l, ss) : LS_ECUDA;
-      if (!r && cudaEventRecord(evs[l], ss) != cudaSuccess) r = LS_ECUDA;
+      int r = cudaStreamWaitEvent(q, ev[l], 0) == cudaSuccess ? ls::sibling_prepare(H, l, q) : LS_ECUDA;
+      if (!r && cudaEventRecord(evs[l], q) != cudaSuccess) r = LS_ECUDA;
       std::lock_guard<std::mutex> lk(mu);
       if (r) {
-        src = r;
-        serr = ls_last_error();
+        if (!src) {
+          src = r;
+          serr = ls_last_error();
+        }
         abort = true;
       } else {
-        sib_ready = l;
+        sib_done[l] = 1;
       }
       cv.notify_all();
       if (r) return;
     }
-  });
+  };
+  std::thread sibling_even(sibling_worker, 0), sibling_odd(sibling_worker, 1);
   std::thread merger([&] {
     ls::StreamScope scope(sm);
     auto wait_level = [&](int level) -> int {
@@ -589,7 +597,7 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
     auto wait_sibling = [&](int level) -> int {
       {
         std::unique_lock<std::mutex> lk(mu);
-        cv.wait(lk, [&] { return abort || sib_ready <= level; });
+        cv.wait(lk, [&] { return abort || sib_done[level]; });
         if (abort) return LS_EINVAL;
       }
       LS_CUDA_TRY(cudaStreamWaitEvent(sm, evs[level], 0));
@@ -623,7 +631,8 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
   }
   cv.notify_all();
   merger.join();
-  sibling.join();
+  sibling_even.join();
+  sibling_odd.join();
   ls::host_mark("merges_joined");
   if (!rc && src) {  // the sibling worker's failure aborted the merges
     rc = src;
@@ -639,14 +648,16 @@ static int build_pipelined(ls_handle* H, cudaStream_t st) {
   cudaStreamWaitEvent(st, ev[L + 3], 0);
   cudaStreamWaitEvent(st, ev[L + 1], 0);
   cudaStreamWaitEvent(st, ev[L + 2], 0);
-  cudaEventRecord(evs[0], ss);
-  cudaStreamWaitEvent(st, evs[0], 0);
+  for (auto q : ss) {  // the wait takes the event's state at the call: one event serves both
+    cudaEventRecord(evs[0], q);
+    cudaStreamWaitEvent(st, evs[0], 0);
+  }
   for (auto& e : ev) cudaEventDestroy(e);
   for (auto& e : evs) cudaEventDestroy(e);
   cudaStreamDestroy(sm);
   cudaStreamDestroy(sc);
   cudaStreamDestroy(su);
-  cudaStreamDestroy(ss);
+  for (auto q : ss) cudaStreamDestroy(q);
   return rc;
 }
 
