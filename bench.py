@@ -849,8 +849,9 @@ def main():
     ap.add_argument("--no-multirhs", action="store_true",
                     help="skip the multi-right-hand-side workload (512x512, 256 plane waves in one block)")
     ap.add_argument("--top-uncompressed", type=int, default=1,
-                    help="tree levels kept uncompressed at the top (U = I, the ID of full rank); measured faster at "
-                         "2048^2 (1.20 s against 1.31 s per step) and at 256^2; 0 compresses every level")
+                    help="tree levels kept uncompressed at the top (U = I, the ID of full rank); at 2048^2 one "
+                         "level and two measure alike (0.636 and 0.632 s per step, two holding 2.4 GB more "
+                         "factors); 0 compresses every level")
     ap.add_argument("--kernel-case", default=None,
                     help="time one kernel family alone (gemm:M:N:K:ENGINE[:REPS] or id:M:P:R) for profiling")
     ap.add_argument("--sweep", nargs="?", const="cavity", default=None, choices=["cavity", "lens", "direct"],
