@@ -444,9 +444,14 @@ class Leg:
 # (dram__bytes_read.sum + dram__bytes_write.sum); keyed by (workload, precision, family).
 MEASURED_TRAFFIC = {
     ("precond_n2048", "tf32x3", "merge_gemm"): {
-        "bytes": 101.84e9,
+        "bytes": 99.18e9,
         "note": "bytes per build + solve step of the 271 tcgen05 GEMM launches (ncu, one-pass metrics at full "
-                "size; profiles/tc_gemm_traffic_precond_n2048.md); ~300 algorithmic flops per DRAM byte"},
+                "size; profiles/tc_gemm_traffic_precond_n2048.md); ~250 algorithmic flops per DRAM byte"},
+    ("precond_n2048", "tf32x3", "cpqr_id"): {
+        "bytes": 148.96e9,
+        "note": "bytes per build + solve step of the compression's blocked row IDs and interpolation matrices "
+                "(ncu, one-pass metrics at full size, split by stream; profiles/blocked_id_traffic_precond_n2048.md): "
+                "13.5x the algorithmic bytes, each block of 32 pivots passing over the trailing candidates"},
 }
 
 # phases of the method and the kernel families of each
