@@ -2223,7 +2223,15 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const Le
   TreeGeom g = make_geom(H);
   size_t smem = sizeof(cx<R>) * ((size_t)n * (n + 1) + (size_t)n * kL + n) + sizeof(R) * n + sizeof(int) * n + 64;
   int tk = prof_begin(st);
-  if (smem <= 220 * 1024) {  // one block per leaf, everything in shared memory
+  // Batched by default where the leaf order fits the register Gauss-Jordan
+  // (probe-checked, row-pivoted fallback) and where the fused kernel's shared
+  // memory would not fit; LS_LEAF_FUSED=1 (diagnostic) keeps the fused kernel.
+  static const bool force_fused = [] {
+    const char* v = getenv("LS_LEAF_FUSED");
+    return v && v[0] && v[0] != '0';
+  }();
+  const bool reg_inverse = n <= gj_reg_max<R>();
+  if (smem <= 220 * 1024 && (force_fused || !reg_inverse)) {  // one block per leaf, everything in shared memory
     LS_CUDA_TRY(cudaFuncSetAttribute(leaf_build_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     count_launch();
     leaf_build_kernel<R><<<(unsigned)nleaf, 256, smem, st>>>(g, H->b, H->kappa * H->kappa,
@@ -2232,10 +2240,14 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const Le
                                                             reinterpret_cast<cx<R>*>(lf.X),
                                                             reinterpret_cast<cx<R>*>(H->XBU),
                                                             reinterpret_cast<cx<R>*>(lf.S), H->d_err);
-  } else {  // large leaves (FP64, 100 points): batched inverse and GEMMs
+  } else {  // batched leaf matrices, inverses and GEMMs
     cx<R>* Xl = reinterpret_cast<cx<R>*>(lf.X);
     cx<R>* BU = nullptr;
-    const size_t ib = sizeof(cx<R>) * nleaf * ((size_t)n * 32 + 128) + sizeof(int) * nleaf * (n + 128) + (1 << 16);
+    // scratch of the checked inverse (a copy of the matrices, the probe vectors) or of
+    // the row-pivoted blocked one
+    const size_t ib = reg_inverse ? sizeof(cx<R>) * (nleaf * ((size_t)n * n + 2 * (size_t)n) + n) + (1 << 16)
+                                  : sizeof(cx<R>) * nleaf * ((size_t)n * 32 + 128) + sizeof(int) * nleaf * (n + 128) +
+                                        (1 << 16);
     void* scr = nullptr;
     if ((rc = dalloc((void**)&BU, sizeof(cx<R>) * nleaf * n * std::max(kL, 1))) || (rc = dalloc(&scr, ib))) return rc;
     struct FreeOnExit2 {
@@ -2252,7 +2264,9 @@ int build_t(ls_handle* H, cudaStream_t st, const LevelWait& wait_level, const Le
                                                                        reinterpret_cast<const cx<R>*>(H->Gleaf),
                                                                        reinterpret_cast<const cx<R>*>(lf.U), kL, Xl,
                                                                        BU, (long long)nleaf);
-    if ((rc = invert_batch<R>(H, Xl, n, n, (long long)n * n, (int)nleaf, scr, ib, st))) return rc;
+    if ((rc = reg_inverse ? invert_checked<R>(H, Xl, n, n, (long long)n * n, (int)nleaf, scr, ib, st)
+                          : invert_batch<R>(H, Xl, n, n, (long long)n * n, (int)nleaf, scr, ib, st)))
+      return rc;
     (void)totk;
     gemm<R>(st, false, false, n, kL, n, one<R>(), Xl, n, (long long)n * n, BU, kL, (long long)n * kL, zero<R>(),
             reinterpret_cast<cx<R>*>(H->XBU), kL, (long long)n * kL, (int)nleaf);  // X B U
