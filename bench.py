@@ -651,6 +651,8 @@ PAPER_DIRECT = {
     (1e-9, 102400): (117.57, 1.04, 1.45e-11), (1e-9, 409600): (675.66, 6.82, 3.48e-09),
     (1e-12, 6400): (4.40, 0.07, 1.87e-15), (1e-12, 25600): (23.70, 0.22, 3.80e-15),
     (1e-12, 102400): (125.78, 1.00, 6.94e-15), (1e-12, 409600): (767.18, 5.98, 1.71e-14),
+    (1e-3, 1638400): (845.19, 10.53, 5.77e-04), (1e-6, 1638400): (2791.95, 33.50, 3.14e-07),
+    (1e-9, 1638400): (4162.88, 67.17, 2.99e-09), (1e-12, 1638400): (4778.64, 47.13, 5.07e-14),
 }
 
 
@@ -670,9 +672,11 @@ def run_direct_sweep(args):
     stream = torch.cuda.current_stream()
     rows = []
     kappa = 25.0
-    for eps in (1e-3, 1e-6, 1e-9, 1e-12):
+    eps_list = [float(e) for e in args.sweep_eps.split(",")] if args.sweep_eps else [1e-3, 1e-6, 1e-9, 1e-12]
+    for eps in eps_list:
         prec = ls.LS_TF32X3 if eps >= 1e-3 else ls.LS_FP64
-        for j in range(args.sweep_first, min(args.sweep_levels, 4)):  # n <= 640 (FP64 below 1e-6)
+        # n <= 640 by default; 1280 (the paper's largest, 1,638,400 unknowns) with --sweep-levels 5
+        for j in range(args.sweep_first, min(args.sweep_levels, 5) if args.sweep_eps else min(args.sweep_levels, 4)):
             n = 80 << j
             h = 1.0 / n
             b = torch.from_numpy(inputs.gaussian_direct(n)).to(dev)
@@ -865,6 +869,9 @@ def main():
                          "the direct solver of Sec. 6.1 (Gaussian bump, eps 1e-3 .. 1e-12)")
     ap.add_argument("--sweep-levels", type=int, default=6, help="sizes of the sweep: n = 80, 160, ..., 80 2^(levels-1)")
     ap.add_argument("--sweep-first", type=int, default=0, help="first size of the sweep: n = 80 2^first")
+    ap.add_argument("--sweep-eps", default=None,
+                    help="direct sweep only: comma-separated tolerances (default 1e-3,1e-6,1e-9,1e-12, n <= 640); "
+                         "with it, --sweep-levels 5 reaches n = 1280")
     ap.add_argument("--sweep-maxit", type=int, default=100, help="GMRES iteration limit in the sweep (memory: "
                     "(maxit + 1) N complex128 twice)")
     ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32x3", "fp16split", "fp64"],
